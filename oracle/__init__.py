@@ -1,0 +1,210 @@
+"""CPU oracle of the band-FHT + bend-limited DP method (arXiv 1912.01884).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the library's product path never
+does, and shares no code with it.  The arithmetic lives in ``oracle.c``
+(plain C loops, double precision plus a float32 copy of the recursion and the
+DP); this module compiles it with gcc and marshals numpy arrays.
+
+Function map (paper passages in the C file's comments):
+  off_table        Sec. 2.1, dyadic line pattern of the FHT (refs [10], [34])
+  fht_direct       Sec. 2.1, Hough images by direct summation along each line
+  fht_recursive    Sec. 2.1, Hough images by the dyadic recursion
+  dp               Sec. 2.2-2.3, Eqs. 3-4 with the bend window (RangeMaxQ)
+  backtrack        Sec. 2.2 Eq. 5, main problem steps 2-3
+  path_score       Sec. 2.1, sum along a given polyline (plain definition)
+  brute            every admissible polyline, tiny images only
+  detect / detect_f32   the whole method (CPU baseline)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_F64P = ctypes.POINTER(ctypes.c_double)
+_F32P = ctypes.POINTER(ctypes.c_float)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, no fast-math,
+    no floating-point contraction).  Returns the library path."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_off_table.argtypes = [ctypes.c_int, _I32P]
+            lib.oracle_fht_direct_f64.argtypes = [_F64P, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, _F64P]
+            lib.oracle_fht_recursive_f64.argtypes = [_F64P, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, _F64P]
+            lib.oracle_fht_recursive_f32.argtypes = [_F32P, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, _F32P]
+            lib.oracle_dp_f64.argtypes = [_F64P] + [ctypes.c_int] * 4 + [_F64P]
+            lib.oracle_dp_f32.argtypes = [_F32P] + [ctypes.c_int] * 4 + [_F32P]
+            lib.oracle_backtrack_f64.argtypes = [_F64P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
+            lib.oracle_backtrack_f64.restype = ctypes.c_double
+            lib.oracle_backtrack_f32.argtypes = [_F32P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
+            lib.oracle_backtrack_f32.restype = ctypes.c_double
+            lib.oracle_path_score_f64.argtypes = [_F64P] + [ctypes.c_int] * 4 + [_I32P]
+            lib.oracle_path_score_f64.restype = ctypes.c_double
+            lib.oracle_brute_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
+                                             + [_I32P, _I32P, ctypes.POINTER(ctypes.c_long)])
+            lib.oracle_brute_f64.restype = ctypes.c_double
+            lib.oracle_detect_f64.argtypes = [_F64P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
+            lib.oracle_detect_f64.restype = ctypes.c_double
+            lib.oracle_detect_f32.argtypes = [_F32P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
+            lib.oracle_detect_f32.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(img) -> np.ndarray:
+    return np.ascontiguousarray(img, dtype=np.float64)
+
+
+def _band_rows(img, k):
+    h, w = img.shape
+    if k < 1 or h % k:
+        raise ValueError("h must be a multiple of k")
+    n = h // k
+    if n & (n - 1):
+        raise ValueError("h/k must be a power of two")
+    return h, w, n
+
+
+def off_table(n: int) -> np.ndarray:
+    """[n][n] int32: off[s, y] = column offset of the shift-s line on row y."""
+    out = np.zeros((n, n), dtype=np.int32)
+    if _load().oracle_off_table(n, _p(out, ctypes.c_int32)) != 0:
+        raise ValueError("n must be a power of two")
+    return out
+
+
+def fht_direct(img, k: int) -> np.ndarray:
+    """[k][2][n][W] float64 Hough images by direct summation (cyclic in W)."""
+    img = _f64(img)
+    h, w, n = _band_rows(img, k)
+    H = np.empty((k, 2, n, w + n), dtype=np.float64)
+    _load().oracle_fht_direct_f64(_p(img, ctypes.c_double), h, w, k, _p(H, ctypes.c_double))
+    return H
+
+
+def fht_recursive(img, k: int, dtype=np.float64) -> np.ndarray:
+    """[k][2][n][W] Hough images by the dyadic recursion, in float64 or in
+    float32 (the float32 summation tree the CUDA float path follows)."""
+    dtype = np.dtype(dtype)
+    src = np.ascontiguousarray(img, dtype=dtype)
+    h, w, n = _band_rows(src, k)
+    H = np.empty((k, 2, n, w + n), dtype=dtype)
+    lib = _load()
+    if dtype == np.float64:
+        lib.oracle_fht_recursive_f64(_p(src, ctypes.c_double), h, w, k, _p(H, ctypes.c_double))
+    elif dtype == np.float32:
+        lib.oracle_fht_recursive_f32(_p(src, ctypes.c_float), h, w, k, _p(H, ctypes.c_float))
+    else:
+        raise TypeError("float64 or float32")
+    return H
+
+
+def dp(H: np.ndarray, h: int, w: int, k: int, B: int) -> np.ndarray:
+    """[k][2n-1][w] DP values from Hough images (float64 or float32)."""
+    n = h // k
+    V = np.empty((k, 2 * n - 1, w), dtype=H.dtype)
+    H = np.ascontiguousarray(H)
+    lib = _load()
+    if H.dtype == np.float64:
+        lib.oracle_dp_f64(_p(H, ctypes.c_double), h, w, k, B, _p(V, ctypes.c_double))
+    elif H.dtype == np.float32:
+        lib.oracle_dp_f32(_p(H, ctypes.c_float), h, w, k, B, _p(V, ctypes.c_float))
+    else:
+        raise TypeError("float64 or float32")
+    return V
+
+
+def backtrack(V: np.ndarray, h: int, w: int, k: int, B: int):
+    """(x[k+1], d[k], score) read back from the DP values."""
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    V = np.ascontiguousarray(V)
+    lib = _load()
+    if V.dtype == np.float64:
+        s = lib.oracle_backtrack_f64(_p(V, ctypes.c_double), h, w, k, B,
+                                     _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    else:
+        s = lib.oracle_backtrack_f32(_p(V, ctypes.c_float), h, w, k, B,
+                                     _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def path_score(img, k: int, x0: int, ds) -> float:
+    """Sum of the pixels along the polyline (x0, d_0..d_{k-1}), float64;
+    -inf if it is not admissible."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    d = np.ascontiguousarray(ds, dtype=np.int32)
+    return _load().oracle_path_score_f64(_p(img, ctypes.c_double), h, w, k, int(x0),
+                                         _p(d, ctypes.c_int32))
+
+
+def brute(img, k: int, B: int):
+    """(x, d, score, visited) of the lexicographically smallest optimum over
+    every admissible polyline.  Tiny images only."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    visited = ctypes.c_long(0)
+    s = _load().oracle_brute_f64(_p(img, ctypes.c_double), h, w, k, B,
+                                 _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32),
+                                 ctypes.byref(visited))
+    return xs, ds, s, visited.value
+
+
+def detect(img, k: int, B: int):
+    """The whole method in float64: (x[k+1], d[k], score)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_f64(_p(img, ctypes.c_double), h, w, k, B,
+                                  _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def detect_f32(img, k: int, B: int):
+    """The whole method with float32 arithmetic and decisions (the decisions
+    the float path of the library must reproduce): (x, d, score)."""
+    src = np.ascontiguousarray(img, dtype=np.float32)
+    h, w, _ = _band_rows(src, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_f32(_p(src, ctypes.c_float), h, w, k, B,
+                                  _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s

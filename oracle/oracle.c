@@ -1,0 +1,401 @@
+/*
+ * CPU oracle for the band-FHT + bend-limited DP method of
+ * "A Method of Detecting End-To-End Curves of Limited Curvature"
+ * (Panfilova, Aliev, Kunina, Postnikov, Nikolaev; arXiv 1912.01884).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: it exists so that tests, the smoke check and the CPU
+ * baseline of the benchmark can compare the CUDA library against a plain,
+ * slow, obviously correct restatement of the method.  It shares no code,
+ * header, table or constant with the CUDA sources.
+ *
+ * Everything is plain loops in double precision (exact for every integer
+ * image the library accepts), plus a float32 copy of the FHT recursion and of
+ * the DP: the float path of the library takes its argmax decisions in float32,
+ * so the oracle takes the same decisions in the same precision.
+ *
+ * Conventions (the paper is silent or garbled on each; the readings are the
+ * ones listed with the design notes):
+ *   n = h/k rows per band, a power of two; W = w + n (Sec. 2.1: each band is
+ *   extended to the right by h/k zero columns).
+ *   A link of band i runs from column x_i on the band's first row to column
+ *   x_i + d on its last row, |d| <= n-1 (45 degrees, Sec. 2 def. 2).  The
+ *   paper's "shift" is n - d (Eq. 1, Eq. 2); the oracle uses d directly.
+ *   Dyadic pattern off_s(y) of a line of shift s >= 0 over m rows:
+ *     m == 1: off_0(0) = 0
+ *     else:   first m/2 rows follow off_{s>>1} over m/2 rows, the last m/2
+ *             rows follow ceil(s/2) + off_{s>>1} over m/2 rows.
+ *   Hough images (Sec. 2.1), cyclic over the padded width W:
+ *     H+(x, s) = sum_y P(y, (x + off_s(y)) mod W)
+ *     H-(x, s) = sum_y P(y, (x - off_s(y)) mod W)
+ *   and H(x, d) = H+(x, d) for d >= 0, H-(x, -d) for d < 0.
+ *   Hough array layout: H[band][sign][s][x], sign 0 = "+", 1 = "-",
+ *   s in [0, n), x in [0, W).
+ *   Value array layout: V[band][d + n - 1][x], x in [0, w).
+ *   Dead states (no admissible continuation) hold -infinity.
+ *   Ties resolve to the lexicographically smallest (x_0, d_0, ..., d_{k-1})
+ *   with d ordered numerically.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_NEG (-INFINITY)
+
+/* ---------------------------------------------------------------------------
+ * Sec. 2.1 (FHT of each band, refs [10], [34]): the dyadic line pattern.
+ * off(m, s, y) is the column offset, on row y, of the line of shift s over m
+ * rows.  Written straight from the recursive definition above.
+ * ------------------------------------------------------------------------ */
+static int off_rec(int m, int s, int y) {
+    if (m == 1) return 0;
+    int half = m / 2;
+    int s_half = s >> 1;
+    if (y < half) return off_rec(half, s_half, y);
+    return (s - s_half) + off_rec(half, s_half, y - half);
+}
+
+/* off[s * n + y] = off_s(y) for s, y in [0, n).  Returns 0, or -1 when n is
+ * not a power of two. */
+int oracle_off_table(int n, int32_t *off) {
+    if (n < 1 || (n & (n - 1)) != 0) return -1;
+    for (int s = 0; s < n; ++s)
+        for (int y = 0; y < n; ++y) off[(size_t)s * n + y] = off_rec(n, s, y);
+    return 0;
+}
+
+/* Pixel of band b, row y, padded column c in [0, W): zero in the padding. */
+static double band_pixel(const double *img, int w, int n, int b, int y, int c) {
+    if (c >= w) return 0.0;
+    return img[((size_t)b * n + y) * w + c];
+}
+
+static int mod_w(long v, int W) {
+    long r = v % W;
+    return (int)(r < 0 ? r + W : r);
+}
+
+/* ---------------------------------------------------------------------------
+ * Sec. 2.1: the Hough images H_0..H_{k-1} by DIRECT summation along every
+ * dyadic line of every zero-padded band (the definition itself, O(n^2 W)).
+ * img: h x w row-major doubles.  H: [k][2][n][W].
+ * ------------------------------------------------------------------------ */
+int oracle_fht_direct_f64(const double *img, int h, int w, int k, double *H) {
+    if (k < 1 || h % k != 0) return -1;
+    int n = h / k;
+    if ((n & (n - 1)) != 0) return -1;
+    int W = w + n;
+    int32_t *off = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * n);
+    if (!off) return -2;
+    oracle_off_table(n, off);
+    for (int b = 0; b < k; ++b)
+        for (int sign = 0; sign < 2; ++sign)
+            for (int s = 0; s < n; ++s)
+                for (int x = 0; x < W; ++x) {
+                    double acc = 0.0;
+                    for (int y = 0; y < n; ++y) {
+                        long o = off[(size_t)s * n + y];
+                        int c = mod_w(sign == 0 ? x + o : x - o, W);
+                        acc += band_pixel(img, w, n, b, y, c);
+                    }
+                    H[(((size_t)b * 2 + sign) * n + s) * W + x] = acc;
+                }
+    free(off);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Sec. 2.1 (FHT, refs [10], [34]): the same Hough images by the dyadic
+ * recursion.  A sub-band of m rows is the union of its top half (A) and its
+ * bottom half (B); its line of shift s is A's line of shift s>>1 followed by
+ * B's line of shift s>>1 moved ceil(s/2) columns (right for "+", left for
+ * "-").  So out(x, s) = A(x, s>>1) + B(x +/- ceil(s/2), s>>1), cyclic in W.
+ * In float32 this fixes the summation tree: every value is (top half) +
+ * (bottom half), recursively, which is the order the CUDA path must follow.
+ * ------------------------------------------------------------------------ */
+#define ORACLE_DEFINE_FHT_RECURSIVE(T, SUFFIX)                                   \
+    /* out: [m][W] for the rows [y0, y0 + m) of band b, one sign. */             \
+    static void fht_rec_##SUFFIX(const T *img, int w, int n, int W, int b,       \
+                                 int sign, int y0, int m, T *out) {              \
+        if (m == 1) {                                                            \
+            for (int x = 0; x < W; ++x)                                          \
+                out[x] = (x < w) ? img[((size_t)b * n + y0) * w + x] : (T)0;     \
+            return;                                                              \
+        }                                                                        \
+        int half = m / 2;                                                        \
+        T *top = (T *)malloc(sizeof(T) * (size_t)half * W);                      \
+        T *bot = (T *)malloc(sizeof(T) * (size_t)half * W);                      \
+        fht_rec_##SUFFIX(img, w, n, W, b, sign, y0, half, top);                  \
+        fht_rec_##SUFFIX(img, w, n, W, b, sign, y0 + half, half, bot);           \
+        for (int s = 0; s < m; ++s) {                                            \
+            int s_half = s >> 1;                                                 \
+            int move = s - s_half;                                               \
+            for (int x = 0; x < W; ++x) {                                        \
+                int xb = mod_w(sign == 0 ? (long)x + move : (long)x - move, W);  \
+                out[(size_t)s * W + x] =                                         \
+                    top[(size_t)s_half * W + x] + bot[(size_t)s_half * W + xb];  \
+            }                                                                    \
+        }                                                                        \
+        free(top);                                                               \
+        free(bot);                                                               \
+    }                                                                            \
+    int oracle_fht_recursive_##SUFFIX(const T *img, int h, int w, int k, T *H) { \
+        if (k < 1 || h % k != 0) return -1;                                      \
+        int n = h / k;                                                           \
+        if ((n & (n - 1)) != 0) return -1;                                       \
+        int W = w + n;                                                           \
+        for (int b = 0; b < k; ++b)                                              \
+            for (int sign = 0; sign < 2; ++sign)                                 \
+                fht_rec_##SUFFIX(img, w, n, W, b, sign, 0, n,                    \
+                                 H + ((size_t)b * 2 + sign) * n * W);            \
+        return 0;                                                                \
+    }
+
+ORACLE_DEFINE_FHT_RECURSIVE(double, f64)
+ORACLE_DEFINE_FHT_RECURSIVE(float, f32)
+
+/* ---------------------------------------------------------------------------
+ * Sec. 2.2-2.3 (Eqs. 3-4, RangeMaxQ): the bottom-up max-plus DP over the
+ * bands, with the bend restriction |d_{i+1} - d_i| <= B (the integer form of
+ * the bend window; B >= 2n-2 is the unrestricted Subproblem 2).
+ *   V_{k-1}(x, d) = H_{k-1}(x, d)                  if x + d in [0, w)
+ *   V_i(x, d)     = H_i(x, d) + max_{|e-d|<=B} V_{i+1}(x + d, e)
+ *                                                  if x + d in [0, w)
+ *   dead otherwise (and dead when every e in the window is dead).
+ * The window maximum is a plain scan over the window (no range-max
+ * structure: the structure only changes the cost, not the result).
+ * H: [k][2][n][W], V: [k][2n-1][w].
+ * ------------------------------------------------------------------------ */
+#define ORACLE_DEFINE_DP(T, SUFFIX)                                              \
+    static T hough_at_##SUFFIX(const T *H, int n, int W, int b, int x, int d) {  \
+        int sign = d >= 0 ? 0 : 1;                                               \
+        int s = d >= 0 ? d : -d;                                                 \
+        return H[(((size_t)b * 2 + sign) * n + s) * W + x];                      \
+    }                                                                            \
+    int oracle_dp_##SUFFIX(const T *H, int h, int w, int k, int B, T *V) {       \
+        if (k < 1 || h % k != 0 || B < 0) return -1;                             \
+        int n = h / k;                                                           \
+        int W = w + n;                                                           \
+        int D = 2 * n - 1;                                                       \
+        for (int b = k - 1; b >= 0; --b)                                         \
+            for (int d = -(n - 1); d <= n - 1; ++d)                              \
+                for (int x = 0; x < w; ++x) {                                    \
+                    T *out = &V[((size_t)b * D + (d + n - 1)) * w + x];          \
+                    int xn = x + d;                                              \
+                    if (xn < 0 || xn >= w) {                                     \
+                        *out = (T)ORACLE_NEG;                                    \
+                        continue;                                                \
+                    }                                                            \
+                    T hv = hough_at_##SUFFIX(H, n, W, b, x, d);                  \
+                    if (b == k - 1) {                                            \
+                        *out = hv;                                               \
+                        continue;                                                \
+                    }                                                            \
+                    T best = (T)ORACLE_NEG;                                      \
+                    for (int e = d - B; e <= d + B; ++e) {                       \
+                        if (e < -(n - 1) || e > n - 1) continue;                 \
+                        T v = V[((size_t)(b + 1) * D + (e + n - 1)) * w + xn];   \
+                        if (v > best) best = v;                                  \
+                    }                                                            \
+                    *out = (best == (T)ORACLE_NEG) ? (T)ORACLE_NEG : hv + best;  \
+                }                                                                \
+        return 0;                                                                \
+    }
+
+ORACLE_DEFINE_DP(double, f64)
+ORACLE_DEFINE_DP(float, f32)
+
+/* ---------------------------------------------------------------------------
+ * Sec. 2.2 Eq. 5 and the main problem (steps 2-3): pick the best top point
+ * and read the polyline back band by band.
+ *   (x_0, d_0) = lexicographically smallest argmax of V_0 over x, d.
+ *   x_{i+1} = x_i + d_i (Eq. 2 / Eq. 5 with shift = n - d).
+ *   d_{i+1} = smallest e with |e - d_i| <= B maximising V_{i+1}(x_{i+1}, e).
+ * Because V_{i+1}(x, e) is the exact best continuation, this greedy choice
+ * yields the lexicographically smallest optimal polyline.
+ * x: k+1 vertices, d: k displacements.  Returns the optimal score.
+ * ------------------------------------------------------------------------ */
+#define ORACLE_DEFINE_BACKTRACK(T, SUFFIX)                                       \
+    double oracle_backtrack_##SUFFIX(const T *V, int h, int w, int k, int B,     \
+                                     int32_t *xs, int32_t *ds) {                 \
+        int n = h / k;                                                           \
+        int D = 2 * n - 1;                                                       \
+        T best = (T)ORACLE_NEG;                                                  \
+        int bx = 0, bd = 0;                                                      \
+        for (int x = 0; x < w; ++x)                                              \
+            for (int d = -(n - 1); d <= n - 1; ++d) {                            \
+                T v = V[((size_t)0 * D + (d + n - 1)) * w + x];                  \
+                if (v > best) {                                                  \
+                    best = v;                                                    \
+                    bx = x;                                                      \
+                    bd = d;                                                      \
+                }                                                                \
+            }                                                                    \
+        xs[0] = bx;                                                              \
+        ds[0] = bd;                                                              \
+        for (int i = 1; i < k; ++i) {                                            \
+            int xi = xs[i - 1] + ds[i - 1];                                      \
+            xs[i] = xi;                                                          \
+            T bv = (T)ORACLE_NEG;                                                \
+            int be = 0;                                                          \
+            for (int e = ds[i - 1] - B; e <= ds[i - 1] + B; ++e) {               \
+                if (e < -(n - 1) || e > n - 1) continue;                         \
+                T v = V[((size_t)i * D + (e + n - 1)) * w + xi];                 \
+                if (v > bv) {                                                    \
+                    bv = v;                                                      \
+                    be = e;                                                      \
+                }                                                                \
+            }                                                                    \
+            ds[i] = be;                                                          \
+        }                                                                        \
+        xs[k] = xs[k - 1] + ds[k - 1];                                           \
+        return (double)best;                                                     \
+    }
+
+ORACLE_DEFINE_BACKTRACK(double, f64)
+ORACLE_DEFINE_BACKTRACK(float, f32)
+
+/* ---------------------------------------------------------------------------
+ * Sec. 2.1 (the query of Subproblem 1) by the plain definition: the sum of
+ * the pixels along the polyline, link by link, row by row (double).
+ * Returns -infinity if a vertex leaves [0, w) or |d_i| > n-1.
+ * ------------------------------------------------------------------------ */
+double oracle_path_score_f64(const double *img, int h, int w, int k, int x0,
+                             const int32_t *ds) {
+    int n = h / k;
+    int32_t *off = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * n);
+    if (!off) return ORACLE_NEG;
+    oracle_off_table(n, off);
+    double acc = 0.0;
+    int x = x0;
+    if (x < 0 || x >= w) acc = ORACLE_NEG;
+    for (int i = 0; i < k && acc != ORACLE_NEG; ++i) {
+        int d = ds[i];
+        int s = d >= 0 ? d : -d;
+        if (s > n - 1 || x + d < 0 || x + d >= w) {
+            acc = ORACLE_NEG;
+            break;
+        }
+        for (int y = 0; y < n; ++y) {
+            int c = x + (d >= 0 ? 1 : -1) * off[(size_t)s * n + y];
+            acc += img[((size_t)i * n + y) * w + c];
+        }
+        x += d;
+    }
+    free(off);
+    return acc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Brute force over every admissible polyline (tiny images only): x_0 in
+ * [0, w), each d_i in [-(n-1), n-1], vertices in [0, w), |d_{i+1}-d_i| <= B.
+ * Enumerated in lexicographic order; the first strictly better score wins, so
+ * the result is the lexicographically smallest optimum.  The score of each
+ * candidate is recomputed from scratch by oracle_path_score_f64.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const double *img;
+    int h, w, k, n, B;
+    int32_t *cur_d;
+    int cur_x0;
+    double best;
+    int32_t *best_x;
+    int32_t *best_d;
+    long visited;
+} brute_state;
+
+static void brute_rec(brute_state *st, int i, int x) {
+    int n = st->n;
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        if (i > 0) {
+            int prev = st->cur_d[i - 1];
+            if (d < prev - st->B || d > prev + st->B) continue;
+        }
+        if (x + d < 0 || x + d >= st->w) continue;
+        st->cur_d[i] = d;
+        if (i + 1 < st->k) {
+            brute_rec(st, i + 1, x + d);
+        } else {
+            st->visited++;
+            double sc = oracle_path_score_f64(st->img, st->h, st->w, st->k,
+                                              st->cur_x0, st->cur_d);
+            if (sc > st->best) {
+                st->best = sc;
+                int xx = st->cur_x0;
+                for (int j = 0; j < st->k; ++j) {
+                    st->best_x[j] = xx;
+                    st->best_d[j] = st->cur_d[j];
+                    xx += st->cur_d[j];
+                }
+                st->best_x[st->k] = xx;
+            }
+        }
+    }
+}
+
+double oracle_brute_f64(const double *img, int h, int w, int k, int B,
+                        int32_t *xs, int32_t *ds, long *visited) {
+    brute_state st;
+    st.img = img;
+    st.h = h;
+    st.w = w;
+    st.k = k;
+    st.n = h / k;
+    st.B = B;
+    st.cur_d = (int32_t *)calloc((size_t)k, sizeof(int32_t));
+    st.best = ORACLE_NEG;
+    st.best_x = xs;
+    st.best_d = ds;
+    st.visited = 0;
+    for (int x0 = 0; x0 < w; ++x0) {
+        st.cur_x0 = x0;
+        brute_rec(&st, 0, x0);
+    }
+    free(st.cur_d);
+    if (visited) *visited = st.visited;
+    return st.best;
+}
+
+/* ---------------------------------------------------------------------------
+ * The whole method (FHT recursion, DP, backtrack) in double: the CPU
+ * baseline.  Scratch is allocated here; returns the optimal score.
+ * ------------------------------------------------------------------------ */
+double oracle_detect_f64(const double *img, int h, int w, int k, int B,
+                         int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * (2 * n - 1) * w);
+    if (!H || !V) {
+        free(H);
+        free(V);
+        return NAN;
+    }
+    oracle_fht_recursive_f64(img, h, w, k, H);
+    oracle_dp_f64(H, h, w, k, B, V);
+    double s = oracle_backtrack_f64(V, h, w, k, B, xs, ds);
+    free(H);
+    free(V);
+    return s;
+}
+
+/* The same in float32: the decisions the float path of the library takes. */
+double oracle_detect_f32(const float *img, int h, int w, int k, int B,
+                         int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    float *H = (float *)malloc(sizeof(float) * (size_t)k * 2 * n * W);
+    float *V = (float *)malloc(sizeof(float) * (size_t)k * (2 * n - 1) * w);
+    if (!H || !V) {
+        free(H);
+        free(V);
+        return NAN;
+    }
+    oracle_fht_recursive_f32(img, h, w, k, H);
+    oracle_dp_f32(H, h, w, k, B, V);
+    double s = oracle_backtrack_f32(V, h, w, k, B, xs, ds);
+    free(H);
+    free(V);
+    return s;
+}
