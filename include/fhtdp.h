@@ -1,0 +1,138 @@
+/*
+ * fhtdp: detection of end-to-end curves of limited curvature on one GB300.
+ *
+ * C ABI of the library (libfhtdp.so).  It implements the data-parallel core
+ * of "A Method of Detecting End-To-End Curves of Limited Curvature"
+ * (Panfilova, Aliev, Kunina, Postnikov, Nikolaev, arXiv 1912.01884): a Fast
+ * Hough Transform of each of the k horizontal bands of an image (Sec. 2.1), a
+ * bottom-up max-plus dynamic programme over the bands with a bend limit
+ * (Sec. 2.2-2.3, Eqs. 3-4), and the read-back of the best k-link polyline
+ * (Eq. 5 and the main problem's steps 2-3).
+ *
+ * Conventions shared by every call
+ *   h, w      image height and width in pixels; h = k * n with n a power of
+ *             two (n rows per band, 1 <= n <= 256); 1 <= w.
+ *   pitch     row stride of the image in ELEMENTS (>= w).
+ *   dtype     FHTDP_U8 (uint8 pixels), FHTDP_I32 (int32 pixels) or FHTDP_F32
+ *             (float pixels).  Integer images accumulate in int32 (exact as
+ *             long as max|pixel| * h < 2^31, which the caller guarantees);
+ *             float images accumulate in float32 with a fixed summation tree
+ *             (each Hough value is the pairwise sum, top half + bottom half,
+ *             of its band rows).
+ *   W = w + n the width of a band after it is zero-padded on the right by
+ *             h/k columns (Sec. 2.1).
+ *   A link of band i joins column x_i on the band's first row to column
+ *   x_{i+1} = x_i + d_i on its last row, |d_i| <= n-1 (the paper's shift of
+ *   Eq. 1 is n - d_i); the pixels it covers follow the FHT's dyadic pattern.
+ *   Every vertex x_0..x_k lies in [0, w).  The bend limit is the integer
+ *   range |d_{i+1} - d_i| <= B (B >= 2n-2 means unrestricted, Sec. 2.2).
+ *   Among optimal polylines the lexicographically smallest
+ *   (x_0, d_0, ..., d_{k-1}) is returned (d ordered numerically).
+ *   Scores are int32 for integer images and float for float images.
+ *
+ * Memory and streams
+ *   Every pointer argument named img, hough, V, ws, x_out, d_out, score_out
+ *   is DEVICE memory owned by the caller; the library never allocates device
+ *   memory and never synchronises the stream.  All work is enqueued on
+ *   `stream` (0 = legacy default stream) and results are valid once the
+ *   stream has reached them.
+ *
+ * Errors
+ *   Every call returns an fhtdp status.  Bad arguments return FHTDP_EINVAL
+ *   before anything is enqueued; a workspace that is too small returns
+ *   FHTDP_EWORKSPACE; a CUDA launch error returns FHTDP_ECUDA.  The message of
+ *   the last failure on the calling thread is returned by fhtdp_last_error().
+ *   No C++ exception crosses this interface.
+ */
+#ifndef FHTDP_H
+#define FHTDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fhtdp_status {
+    FHTDP_OK = 0,
+    FHTDP_EINVAL = 1,     /* invalid argument (nothing was enqueued) */
+    FHTDP_EWORKSPACE = 2, /* workspace missing or smaller than required */
+    FHTDP_ECUDA = 3,      /* a CUDA call failed; see fhtdp_last_error() */
+    FHTDP_ETIMEOUT = 4    /* a bounded device-side wait gave up */
+};
+
+enum fhtdp_dtype { FHTDP_U8 = 0, FHTDP_I32 = 1, FHTDP_F32 = 2 };
+
+/* Message of the last failed call on this thread ("" if none).  The string
+ * stays valid until the next call on the same thread. */
+const char *fhtdp_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int fhtdp_version(void);
+
+/* Number of CUDA kernel launches the library has enqueued in this process
+ * (all threads, all devices), for accounting by benchmarks. */
+uint64_t fhtdp_launch_count(void);
+
+/* Bytes of a Hough / DP-value array of the given shape:
+ * k * 2 * n * (w + n) elements of 4 bytes (int32 or float).
+ * Returns 0 for invalid shapes. */
+size_t fhtdp_hough_bytes(int dtype, int h, int w, int k);
+
+/* Sec. 2.1 (Subproblem 1): the Hough images H_0..H_{k-1} of the k
+ * zero-padded bands, for mostly vertical lines of both slope signs.
+ *   img    [h rows][pitch] pixels of `dtype` (device).
+ *   hough  output, [k][2][n][W] int32 (integer images) or float (float
+ *          images), x fastest (device, fhtdp_hough_bytes()).  Element
+ *          [i][0][s][x] is the sum along the line from (x, first row of band
+ *          i) moving s columns right over the band; [i][1][s][x] the same
+ *          moving left; columns are taken modulo W (cyclic FHT), so for
+ *          x in [0, w) and an end column inside the image it is the plain sum.
+ *   ws     device workspace of at least fhtdp_fht_workspace_bytes() bytes
+ *          (stage ping-pong buffer), overwritten.
+ */
+size_t fhtdp_fht_workspace_bytes(int dtype, int h, int w, int k);
+int fhtdp_fht_bands(const void *img, int dtype, int h, int w, int pitch, int k,
+                    void *hough, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Sec. 2.2-2.3, Eqs. 3-4: the bottom-up DP, in place over the Hough images
+ * exactly as the paper updates H_{i-1} with the best continuation.
+ *   hough  in: output of fhtdp_fht_bands.  out: DP values V_i(x, d) = best
+ *          sum of a polyline that starts with link (x, d) in band i and ends
+ *          on the image's last row; V_i(x, +s) at [i][0][s][x], V_i(x, -s)
+ *          at [i][1][s][x] (s = 0 stored in both), x in [0, w).  Dead states
+ *          (end vertex outside [0, w), or no admissible continuation) and
+ *          the padding columns [w, W) hold INT32_MIN / -infinity.
+ *   B      bend limit, >= 0.
+ */
+int fhtdp_polyline_dp(void *hough, int dtype, int h, int w, int k, int B, cudaStream_t stream);
+
+/* Eq. 5 and the main problem, steps 2-3: the best top point and the read-back
+ * of its polyline from DP values laid out as fhtdp_polyline_dp leaves them.
+ *   x_out  k+1 int32 vertices x_0..x_k (device).
+ *   d_out  k int32 displacements d_i = x_{i+1} - x_i (device).
+ *   score_out  one int32 (integer images) or float (float images) (device).
+ */
+int fhtdp_backtrack(const void *V, int dtype, int h, int w, int k, int B,
+                    int32_t *x_out, int32_t *d_out, void *score_out, cudaStream_t stream);
+
+/* The whole method on one image (Sec. 2.1-2.3 and the main problem): the
+ * band FHTs, the bend-limited DP and the read-back, through the fused engine
+ * (the Hough images never reach global memory).
+ *   ws     device workspace of at least fhtdp_workspace_bytes() bytes.
+ *   Outputs as for fhtdp_backtrack.  Returns FHTDP_ETIMEOUT if a device-side
+ *   dependency wait gave up (the outputs are then undefined).
+ */
+size_t fhtdp_workspace_bytes(int dtype, int h, int w, int k, int B);
+int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, int k, int B,
+                          int32_t *x_out, int32_t *d_out, void *score_out,
+                          void *ws, size_t ws_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHTDP_H */

@@ -1,0 +1,197 @@
+"""fhtdp: end-to-end curves of limited curvature (arXiv 1912.01884) on GB300.
+
+Thin Python binding of the C-ABI library ``libfhtdp.so`` (declared in
+``include/fhtdp.h``).  This module only marshals arguments: PyTorch tensors
+provide device memory and the current CUDA stream, and every step of the
+method runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library cannot be loaded the calls raise.
+
+Calls (same names as the C entry points, without the ``fhtdp_`` prefix):
+  fht_bands(img, k)                  Sec. 2.1, Hough images [k, 2, n, w+n]
+  polyline_dp(hough, h, w, k, B)     Sec. 2.2-2.3, Eqs. 3-4, in place
+  backtrack(V, h, w, k, B)           Eq. 5 / main problem: (x, d, score)
+  detect_polyline(img, k, B)         the whole method: (x, d, score)
+The raw ctypes handle with the exact C signatures is ``lib()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+__all__ = ["load", "lib", "build", "FhtdpError", "fht_bands", "polyline_dp", "backtrack",
+           "detect_polyline", "workspace_bytes", "launch_count", "hough_bytes", "fht_workspace_bytes",
+           "DTYPE_U8", "DTYPE_I32", "DTYPE_F32", "STATUS"]
+
+DTYPE_U8, DTYPE_I32, DTYPE_F32 = 0, 1, 2
+STATUS = {0: "FHTDP_OK", 1: "FHTDP_EINVAL", 2: "FHTDP_EWORKSPACE", 3: "FHTDP_ECUDA",
+          4: "FHTDP_ETIMEOUT"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FhtdpError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(code, code), message))
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+_SIGS = {
+    "fhtdp_last_error": (ctypes.c_char_p, []),
+    "fhtdp_version": (ctypes.c_int, []),
+    "fhtdp_launch_count": (ctypes.c_uint64, []),
+    "fhtdp_hough_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
+    "fhtdp_fht_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
+    "fhtdp_fht_bands": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
+                        + [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_polyline_dp": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
+                          + [ctypes.c_void_p]),
+    "fhtdp_backtrack": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
+                        + [ctypes.c_void_p] * 4),
+    "fhtdp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 5),
+    "fhtdp_detect_polyline": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
+                              + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
+}
+
+
+def load():
+    """Load libfhtdp.so (building it in-tree if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            handle = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def lib():
+    return load()
+
+
+def _check(code: int):
+    if code != 0:
+        raise FhtdpError(code, lib().fhtdp_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.uint8: DTYPE_U8, torch.int32: DTYPE_I32, torch.float32: DTYPE_F32}
+    if t.dtype not in m:
+        raise TypeError("image dtype must be uint8, int32 or float32, got %s" % t.dtype)
+    return m[t.dtype]
+
+
+def _acc_dtype(code: int):
+    torch = _torch()
+    return torch.float32 if code == DTYPE_F32 else torch.int32
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _image(img):
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("image must be 2-D with unit column stride")
+    return img.shape[0], img.shape[1], img.stride(0)
+
+
+def launch_count() -> int:
+    """Kernel launches the library has enqueued in this process."""
+    return lib().fhtdp_launch_count()
+
+
+def hough_bytes(dtype: int, h: int, w: int, k: int) -> int:
+    return lib().fhtdp_hough_bytes(dtype, h, w, k)
+
+
+def fht_workspace_bytes(dtype: int, h: int, w: int, k: int) -> int:
+    return lib().fhtdp_fht_workspace_bytes(dtype, h, w, k)
+
+
+def workspace_bytes(dtype: int, h: int, w: int, k: int, B: int) -> int:
+    return lib().fhtdp_workspace_bytes(dtype, h, w, k, B)
+
+
+def fht_bands(img, k: int, out=None, ws=None, stream=None):
+    """Hough images of the k bands: tensor [k, 2, n, w + n] (int32 or float32)."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _dtype_code(img)
+    if h % k:
+        raise ValueError("h must be a multiple of k")
+    n = h // k
+    if out is None:
+        out = torch.empty((k, 2, n, w + n), dtype=_acc_dtype(code), device=img.device)
+    need = fht_workspace_bytes(code, h, w, k)
+    if ws is None and need:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    _check(lib().fhtdp_fht_bands(img.data_ptr(), code, h, w, pitch, k, out.data_ptr(),
+                                 ws.data_ptr() if ws is not None else None,
+                                 ws.numel() if ws is not None else 0, _stream(stream)))
+    return out
+
+
+def polyline_dp(hough, h: int, w: int, k: int, B: int, stream=None):
+    """Bend-limited DP in place over the Hough images; returns the tensor."""
+    torch = _torch()
+    code = DTYPE_F32 if hough.dtype == torch.float32 else DTYPE_I32
+    _check(lib().fhtdp_polyline_dp(hough.data_ptr(), code, h, w, k, B, _stream(stream)))
+    return hough
+
+
+def _outputs(k, code, device):
+    torch = _torch()
+    x = torch.empty(k + 1, dtype=torch.int32, device=device)
+    d = torch.empty(k, dtype=torch.int32, device=device)
+    score = torch.empty(1, dtype=_acc_dtype(code), device=device)
+    return x, d, score
+
+
+def backtrack(V, h: int, w: int, k: int, B: int, out=None, stream=None):
+    """(x[k+1], d[k], score[1]) device tensors from DP values."""
+    torch = _torch()
+    code = DTYPE_F32 if V.dtype == torch.float32 else DTYPE_I32
+    x, d, score = out if out is not None else _outputs(k, code, V.device)
+    _check(lib().fhtdp_backtrack(V.data_ptr(), code, h, w, k, B, x.data_ptr(), d.data_ptr(),
+                                 score.data_ptr(), _stream(stream)))
+    return x, d, score
+
+
+def detect_polyline(img, k: int, B: int, out=None, ws=None, stream=None):
+    """The whole method on one device image: (x[k+1], d[k], score[1])."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _dtype_code(img)
+    need = workspace_bytes(code, h, w, k, B)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_polyline(None, code, h, w, pitch, k, B, None, None, None,
+                                           None, 0, _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    x, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_polyline(img.data_ptr(), code, h, w, pitch, k, B, x.data_ptr(),
+                                       d.data_ptr(), score.data_ptr(), ws.data_ptr(), ws.numel(),
+                                       _stream(stream)))
+    return x, d, score

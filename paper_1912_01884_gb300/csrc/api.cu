@@ -1,0 +1,167 @@
+// C-ABI entry points: argument validation, dispatch on the pixel type, and
+// error reporting.  No exception and no allocation happens here.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+namespace fhtdp {
+
+namespace {
+thread_local char g_last_error[512] = "";
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+int launched(const char *what) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cuda_status(cudaGetLastError(), what);
+}
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_status(cudaError_t err, const char *what) {
+    if (err == cudaSuccess) return FHTDP_OK;
+    return set_error(FHTDP_ECUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+bool make_shape(int h, int w, int k, Shape *out) {
+    if (h < 1 || w < 1 || k < 1 || h % k != 0) return false;
+    int n = h / k;
+    if (n > 256 || (n & (n - 1)) != 0) return false;
+    if (w > (1 << 20) || h > (1 << 20)) return false;
+    Shape s;
+    s.h = h;
+    s.w = w;
+    s.k = k;
+    s.n = n;
+    s.W = w + n;
+    s.D = 2 * n - 1;
+    s.log2n = 0;
+    while ((1 << s.log2n) < n) ++s.log2n;
+    *out = s;
+    return true;
+}
+
+namespace {
+
+int bad_shape(int h, int w, int k) {
+    return set_error(FHTDP_EINVAL,
+                     "invalid shape h=%d w=%d k=%d: need h = k*n with n a power of two "
+                     "in [1, 256], 1 <= w <= 2^20, h <= 2^20",
+                     h, w, k);
+}
+
+bool valid_dtype(int dtype) { return dtype == FHTDP_U8 || dtype == FHTDP_I32 || dtype == FHTDP_F32; }
+
+size_t hough_elems(const Shape &s) { return (size_t)s.k * 2 * s.n * s.W; }
+
+}  // namespace
+}  // namespace fhtdp
+
+using namespace fhtdp;
+
+extern "C" {
+
+const char *fhtdp_last_error(void) { return g_last_error; }
+
+int fhtdp_version(void) { return 100; }
+
+uint64_t fhtdp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+size_t fhtdp_hough_bytes(int dtype, int h, int w, int k) {
+    Shape s;
+    if (!valid_dtype(dtype) || !make_shape(h, w, k, &s)) return 0;
+    return hough_elems(s) * 4;
+}
+
+size_t fhtdp_fht_workspace_bytes(int dtype, int h, int w, int k) {
+    Shape s;
+    if (!valid_dtype(dtype) || !make_shape(h, w, k, &s)) return 0;
+    return s.log2n >= 2 ? hough_elems(s) * 4 : 0;
+}
+
+int fhtdp_fht_bands(const void *img, int dtype, int h, int w, int pitch, int k, void *hough,
+                    void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (!img || !hough) return set_error(FHTDP_EINVAL, "null img or hough pointer");
+    size_t need = fhtdp_fht_workspace_bytes(dtype, h, w, k);
+    if (need && (!ws || ws_bytes < need))
+        return set_error(FHTDP_EWORKSPACE, "fht workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    switch (dtype) {
+        case FHTDP_U8:
+            return launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s,
+                                                       (int32_t *)hough, (int32_t *)ws, stream);
+        case FHTDP_I32:
+            return launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s,
+                                                       (int32_t *)hough, (int32_t *)ws, stream);
+        default:
+            return launch_fht_stages<float, float>((const float *)img, pitch, s, (float *)hough,
+                                                   (float *)ws, stream);
+    }
+}
+
+int fhtdp_polyline_dp(void *hough, int dtype, int h, int w, int k, int B, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (!hough) return set_error(FHTDP_EINVAL, "null hough pointer");
+    if (dtype == FHTDP_F32) return launch_dp_inplace<float>((float *)hough, s, B, stream);
+    return launch_dp_inplace<int32_t>((int32_t *)hough, s, B, stream);
+}
+
+int fhtdp_backtrack(const void *V, int dtype, int h, int w, int k, int B, int32_t *x_out,
+                    int32_t *d_out, void *score_out, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (!V || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null V or output pointer");
+    if (dtype == FHTDP_F32)
+        return launch_backtrack<float>((const float *)V, s, B, x_out, d_out, (float *)score_out,
+                                       stream);
+    return launch_backtrack<int32_t>((const int32_t *)V, s, B, x_out, d_out,
+                                     (int32_t *)score_out, stream);
+}
+
+size_t fhtdp_workspace_bytes(int dtype, int h, int w, int k, int B) {
+    Shape s;
+    if (!valid_dtype(dtype) || !make_shape(h, w, k, &s) || B < 0) return 0;
+    return engine_workspace_bytes(dtype, s, B);
+}
+
+int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, int k, int B,
+                          int32_t *x_out, int32_t *d_out, void *score_out, void *ws,
+                          size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (!img || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    size_t need = engine_workspace_bytes(dtype, s, B);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, ws_bytes, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Shared definitions of the CUDA sources (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "fhtdp.h"
+
+namespace fhtdp {
+
+// Sentinel of a dead DP state: no admissible polyline continues from it.
+// It never takes part in an addition.
+template <typename T>
+struct Dead;
+template <>
+struct Dead<int32_t> {
+    __host__ __device__ static constexpr int32_t value() { return INT32_MIN; }
+};
+template <>
+struct Dead<float> {
+    __device__ static float value() { return __int_as_float(0xff800000u); }
+};
+
+// Shape of one image's problem.
+struct Shape {
+    int h, w, k, n, W, D;  // D = 2n - 1 displacement values
+    int log2n;
+};
+
+// Host helpers (api.cu).
+int set_error(int code, const char *fmt, ...);
+// Checks a launch and counts it (fhtdp_launch_count).
+int launched(const char *what);
+int cuda_status(cudaError_t err, const char *what);
+bool make_shape(int h, int w, int k, Shape *out);
+
+// Kernels launched by the API layer.
+template <typename In, typename Acc>
+int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc *tmp,
+                      cudaStream_t stream);
+template <typename Acc>
+int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream);
+template <typename Acc>
+int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_t *d_out,
+                     Acc *score_out, cudaStream_t stream);
+
+}  // namespace fhtdp

@@ -1,0 +1,126 @@
+// Band FHT, one dyadic level per launch (the standalone fhtdp_fht_bands).
+//
+// Sec. 2.1 (refs [10], [34]): the Hough image of a band is built bottom-up
+// over sub-bands of 1, 2, 4, ..., n rows.  Merging the top half A and the
+// bottom half B of a sub-band of m rows gives, for every shift s in [0, m),
+//   out(x, s) = A(x, s>>1) + B(x +/- ceil(s/2), s>>1)      (columns mod W)
+// with "+" for lines moving right and "-" for lines moving left.  The sum
+// tree is therefore fixed (top half + bottom half at every level), which
+// makes the float path reproducible bit for bit.
+//
+// Layout of every level: [band][sign][row][x], x fastest; at the level of
+// m-row sub-bands, row j*m + s holds shift s of sub-band j, so the last level
+// (m = n, one sub-band) is exactly the [k][2][n][W] Hough layout.
+// Each level is a coalesced streaming pass: a warp reads a contiguous row
+// segment of A and a contiguous (shifted) segment of B.
+#include "common.cuh"
+
+namespace fhtdp {
+namespace {
+
+template <typename In, typename Acc>
+__device__ __forceinline__ Acc band_pixel(const In *img, int pitch, int w, int row, int col) {
+    return col < w ? static_cast<Acc>(img[(size_t)row * pitch + col]) : Acc(0);
+}
+
+__device__ __forceinline__ int wrap(int x, int W) {
+    return x >= W ? x - W : (x < 0 ? x + W : x);
+}
+
+// n == 1: the band is a single row, and both "signs" are the padded row.
+template <typename In, typename Acc>
+__global__ void fht_single_row_kernel(const In *img, int pitch, Shape s, Acc *out) {
+    const size_t total = (size_t)s.k * 2 * s.W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % s.W);
+        int band = (int)(i / s.W) / 2;
+        out[i] = band_pixel<In, Acc>(img, pitch, s.w, band, x);
+    }
+}
+
+// Level of 2-row sub-bands, read straight from the image (zero padding is
+// the predicate col < w, never stored).
+template <typename In, typename Acc>
+__global__ void fht_level2_kernel(const In *img, int pitch, Shape s, Acc *out) {
+    const size_t total = (size_t)s.k * 2 * s.n * s.W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % s.W);
+        size_t r = i / s.W;
+        int row = (int)(r % s.n);
+        int bs = (int)(r / s.n);
+        int sign = bs & 1, band = bs >> 1;
+        int sh = row & 1;                       // shift within the 2-row sub-band
+        int ya = band * s.n + (row & ~1);       // top row of the sub-band
+        int xb = wrap(sign == 0 ? x + sh : x - sh, s.W);
+        out[i] = band_pixel<In, Acc>(img, pitch, s.w, ya, x) +
+                 band_pixel<In, Acc>(img, pitch, s.w, ya + 1, xb);
+    }
+}
+
+// Level of m-row sub-bands (m >= 4) from the level of m/2-row sub-bands.
+template <typename Acc>
+__global__ void fht_level_kernel(const Acc *__restrict__ src, Shape s, int m,
+                                 Acc *__restrict__ dst) {
+    const size_t total = (size_t)s.k * 2 * s.n * s.W;
+    const int half = m >> 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % s.W);
+        size_t r = i / s.W;
+        int row = (int)(r % s.n);
+        size_t bs = r / s.n;
+        int sign = (int)(bs & 1);
+        int j0 = row & ~(m - 1);                // first row of the sub-band
+        int sh = row & (m - 1);                 // shift in [0, m)
+        int move = sh - (sh >> 1);              // ceil(sh / 2)
+        int xb = wrap(sign == 0 ? x + move : x - move, s.W);
+        const Acc *base = src + bs * s.n * (size_t)s.W;
+        Acc a = base[(size_t)(j0 + (sh >> 1)) * s.W + x];
+        Acc b = base[(size_t)(j0 + half + (sh >> 1)) * s.W + xb];
+        dst[i] = a + b;
+    }
+}
+
+int grid_for(size_t total) {
+    size_t blocks = (total + 255) / 256;
+    size_t cap = 152 * 16;
+    return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+}  // namespace
+
+template <typename In, typename Acc>
+int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc *tmp,
+                      cudaStream_t stream) {
+    if (s.n == 1) {
+        size_t total = (size_t)s.k * 2 * s.W;
+        fht_single_row_kernel<In, Acc><<<grid_for(total), 256, 0, stream>>>(img, pitch, s, hough);
+        return launched("fht_single_row_kernel");
+    }
+    const size_t total = (size_t)s.k * 2 * s.n * s.W;
+    const int levels = s.log2n;
+    // Level l (sub-bands of 2^l rows) writes to hough when (levels - l) is
+    // even, so that the last level lands in hough.
+    auto dst_of = [&](int l) { return ((levels - l) % 2 == 0) ? hough : tmp; };
+    fht_level2_kernel<In, Acc><<<grid_for(total), 256, 0, stream>>>(img, pitch, s, dst_of(1));
+    int st = launched("fht_level2_kernel");
+    if (st) return st;
+    for (int l = 2; l <= levels; ++l) {
+        fht_level_kernel<Acc><<<grid_for(total), 256, 0, stream>>>(dst_of(l - 1), s, 1 << l,
+                                                                   dst_of(l));
+        st = launched("fht_level_kernel");
+        if (st) return st;
+    }
+    return FHTDP_OK;
+}
+
+template int launch_fht_stages<uint8_t, int32_t>(const uint8_t *, int, const Shape &, int32_t *,
+                                                 int32_t *, cudaStream_t);
+template int launch_fht_stages<int32_t, int32_t>(const int32_t *, int, const Shape &, int32_t *,
+                                                 int32_t *, cudaStream_t);
+template int launch_fht_stages<float, float>(const float *, int, const Shape &, float *, float *,
+                                             cudaStream_t);
+
+}  // namespace fhtdp
