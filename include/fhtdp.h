@@ -131,6 +131,47 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
                           int32_t *x_out, int32_t *d_out, void *score_out,
                           void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Status of the last detection run that used this workspace (a single image
+ * or a batch): FHTDP_OK, or FHTDP_ETIMEOUT if one of its bounded device-side
+ * waits gave up (its outputs are then undefined).  Synchronises `stream`
+ * (one 4-byte device-to-host copy). */
+int fhtdp_workspace_status(const void *ws, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: many images of different h, w, k and B (one pixel type) in ONE
+ * persistent kernel launch.  Work items (image, band, column tile) are taken
+ * from a device-side queue, so the band chains of different images overlap
+ * and the GPU stays busy; a run is one memset and one kernel launch and may
+ * be captured in a CUDA graph.  Each image's result is the same as
+ * fhtdp_detect_polyline's.
+ * ---------------------------------------------------------------------- */
+typedef struct fhtdp_image {
+    const void *img;     /* device pixels [h][pitch] of the batch's dtype */
+    int h, w, pitch, k, B;
+    int32_t *x_out;      /* device, k+1 vertices */
+    int32_t *d_out;      /* device, k displacements */
+    void *score_out;     /* device, one int32 (integer images) or float */
+} fhtdp_image;
+
+typedef struct fhtdp_batch_plan fhtdp_batch_plan;
+
+/* Validates every image (FHTDP_EINVAL names the first bad one), lays out its
+ * scratch and orders the work queue.  The plan is a host object owned by the
+ * caller (fhtdp_batch_plan_destroy); `images` is copied. */
+int fhtdp_batch_plan_create(const fhtdp_image *images, int count, int dtype,
+                            fhtdp_batch_plan **plan_out);
+/* Device workspace the plan needs (bytes). */
+size_t fhtdp_batch_workspace_bytes(const fhtdp_batch_plan *plan);
+/* Binds the plan to a workspace: enqueues one host-to-device copy of the
+ * image table into `ws` (from memory held by the plan; keep the plan alive
+ * until the copy has run).  Call once per workspace, before the runs. */
+int fhtdp_batch_upload(fhtdp_batch_plan *plan, void *ws, size_t ws_bytes, cudaStream_t stream);
+/* Runs the whole batch on `stream`: one memset and one kernel launch. */
+int fhtdp_batch_run(const fhtdp_batch_plan *plan, void *ws, cudaStream_t stream);
+/* Number of work items (image, band, column tile) of a run. */
+long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
+void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

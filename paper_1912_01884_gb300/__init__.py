@@ -22,7 +22,8 @@ import threading
 from . import _build
 
 __all__ = ["load", "lib", "build", "FhtdpError", "fht_bands", "polyline_dp", "backtrack",
-           "detect_polyline", "workspace_bytes", "launch_count", "hough_bytes", "fht_workspace_bytes",
+           "detect_polyline", "workspace_bytes", "launch_count", "BatchPlan", "Image",
+           "workspace_status", "hough_bytes", "fht_workspace_bytes",
            "DTYPE_U8", "DTYPE_I32", "DTYPE_F32", "STATUS"]
 
 DTYPE_U8, DTYPE_I32, DTYPE_F32 = 0, 1, 2
@@ -58,7 +59,24 @@ _SIGS = {
     "fhtdp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 5),
     "fhtdp_detect_polyline": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                               + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_batch_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_void_p)]),
+    "fhtdp_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "fhtdp_batch_items": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "fhtdp_batch_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
+    "fhtdp_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_batch_plan_destroy": (None, [ctypes.c_void_p]),
 }
+
+
+class Image(ctypes.Structure):
+    """struct fhtdp_image of the C ABI."""
+    _fields_ = [("img", ctypes.c_void_p), ("h", ctypes.c_int), ("w", ctypes.c_int),
+                ("pitch", ctypes.c_int), ("k", ctypes.c_int), ("B", ctypes.c_int),
+                ("x_out", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("score_out", ctypes.c_void_p)]
 
 
 def load():
@@ -177,6 +195,72 @@ def backtrack(V, h: int, w: int, k: int, B: int, out=None, stream=None):
     _check(lib().fhtdp_backtrack(V.data_ptr(), code, h, w, k, B, x.data_ptr(), d.data_ptr(),
                                  score.data_ptr(), _stream(stream)))
     return x, d, score
+
+
+def workspace_status(ws, stream=None) -> int:
+    """Status of the last run that used `ws` (synchronises the stream):
+    0, or raises FhtdpError (FHTDP_ETIMEOUT when a device-side wait gave up)."""
+    _check(lib().fhtdp_workspace_status(ws.data_ptr(), _stream(stream)))
+    return 0
+
+
+class BatchPlan:
+    """Many images of one pixel type in one persistent launch.
+
+    ``images`` are 2-D CUDA tensors, ``ks`` and ``Bs`` their band counts and
+    bend limits.  Outputs ``x[i]``, ``d[i]``, ``score[i]`` are allocated here,
+    or are the rows of ``out = (X, D, S)``; ``run()`` enqueues the whole batch
+    (one memset, one kernel) and may be captured in a CUDA graph."""
+
+    def __init__(self, images, ks, Bs, ws=None, stream=None, out=None):
+        torch = _torch()
+        if not images:
+            raise ValueError("empty batch")
+        code = _dtype_code(images[0])
+        dev = images[0].device
+        self.images = list(images)
+        self.x, self.d, self.score = [], [], []
+        arr = (Image * len(images))()
+        for i, (img, k, B) in enumerate(zip(images, ks, Bs)):
+            if _dtype_code(img) != code:
+                raise TypeError("one pixel type per batch")
+            h, w, pitch = _image(img)
+            x, d, sc = (out[0][i], out[1][i], out[2][i]) if out is not None else \
+                _outputs(k, code, dev)
+            self.x.append(x)
+            self.d.append(d)
+            self.score.append(sc)
+            arr[i] = Image(img.data_ptr(), h, w, pitch, k, B, x.data_ptr(), d.data_ptr(),
+                           sc.data_ptr())
+        self._arr = arr
+        handle = ctypes.c_void_p()
+        _check(lib().fhtdp_batch_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(images),
+                                             code, ctypes.byref(handle)))
+        self._plan = handle
+        need = lib().fhtdp_batch_workspace_bytes(handle)
+        self.ws = ws if ws is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+        if self.ws.numel() < need:
+            raise ValueError("workspace too small")
+        self.items = lib().fhtdp_batch_items(handle)
+        _check(lib().fhtdp_batch_upload(handle, self.ws.data_ptr(), self.ws.numel(),
+                                        _stream(stream)))
+
+    def run(self, stream=None):
+        _check(lib().fhtdp_batch_run(self._plan, self.ws.data_ptr(), _stream(stream)))
+
+    def status(self, stream=None):
+        return workspace_status(self.ws, stream)
+
+    def close(self):
+        if self._plan:
+            lib().fhtdp_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def detect_polyline(img, k: int, B: int, out=None, ws=None, stream=None):

@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <new>
 
 #include "common.cuh"
 #include "engine.cuh"
@@ -162,6 +163,60 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
     return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, ws_bytes, stream);
+}
+
+int fhtdp_workspace_status(const void *ws, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!ws) return set_error(FHTDP_EINVAL, "null workspace");
+    return engine_status(ws, stream);
+}
+
+struct fhtdp_batch_plan {
+    BatchPlan *impl;
+};
+
+int fhtdp_batch_plan_create(const fhtdp_image *images, int count, int dtype,
+                            fhtdp_batch_plan **plan_out) {
+    g_last_error[0] = 0;
+    if (!plan_out) return set_error(FHTDP_EINVAL, "null plan_out");
+    *plan_out = nullptr;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    BatchPlan *impl = nullptr;
+    int st = batch_create(images, count, dtype, &impl);
+    if (st) return st;
+    fhtdp_batch_plan *p = new (std::nothrow) fhtdp_batch_plan{impl};
+    if (!p) {
+        batch_destroy(impl);
+        return set_error(FHTDP_EINVAL, "out of host memory");
+    }
+    *plan_out = p;
+    return FHTDP_OK;
+}
+
+size_t fhtdp_batch_workspace_bytes(const fhtdp_batch_plan *plan) {
+    return plan ? batch_workspace_bytes(plan->impl) : 0;
+}
+
+long long fhtdp_batch_items(const fhtdp_batch_plan *plan) {
+    return plan ? batch_items(plan->impl) : 0;
+}
+
+int fhtdp_batch_upload(fhtdp_batch_plan *plan, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    return batch_upload(plan->impl, ws, ws_bytes, stream);
+}
+
+int fhtdp_batch_run(const fhtdp_batch_plan *plan, void *ws, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    return batch_run(plan->impl, ws, stream);
+}
+
+void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan) {
+    if (!plan) return;
+    batch_destroy(plan->impl);
+    delete plan;
 }
 
 }  // extern "C"

@@ -1,37 +1,1142 @@
-// Detection engine, first version: the level-by-level FHT, the in-place DP
-// and the read-back, composed on one stream.
+// Fused detection engine: band FHT + bend-limited DP + read-back in one
+// persistent kernel.
+//
+// Work items are (image, band, column tile) taken from a device-side queue
+// in which every item comes after the band+1 tiles it depends on.  An item
+//   1. computes the Hough values of its band for its T output columns in
+//      shared memory (Sec. 2.1): the band strip with its n-1 column halo is
+//      loaded, and the log2(n) dyadic levels are merged in place;
+//   2. waits until the three tiles of band+1 that it depends on have
+//      published their window maxima (bounded spin, see wait_flag);
+//   3. forms V_b(x, e) = H_b(x, e) + M_{b+1}(x + e, e) (Eqs. 3-4) and the
+//      bend-window maxima M_b(x, c) = max_{|e - c| <= B} V_b(x, e)
+//      (Sec. 2.3, RangeMaxQ) with the van Herk / Gil-Werman block method,
+//      carrying the argmax in the low bits of an integer key; it writes M_b
+//      (to an L2-resident ping-pong buffer, skewed so that the consumer's
+//      gather M_b(x + d, d) is a contiguous row read) and the argmax byte
+//      bp_b(x, c), then publishes its flag;
+//   4. on band 0 it reduces V_0 to the lexicographically smallest argmax
+//      (main problem, steps 2-3); the last band-0 tile of an image reads the
+//      polyline back through bp (Eq. 5).
+// The Hough images and the DP values never reach global memory.
+//
+// Pixel types: uint8 images keep both slope halves of a Hough value in one
+// 32-bit word (two 16-bit lanes: sums of at most 128 uint8 pixels fit), so
+// one shared-memory access and one integer add serve both halves.  The "-"
+// half is computed on the mirrored strip, so both halves use the same
+// merge.  int32 and float images run the halves one after the other.
+#include <algorithm>
+#include <climits>
+#include <cstddef>
+#include <new>
+#include <type_traits>
+#include <vector>
+
 #include "engine.cuh"
 
 namespace fhtdp {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kTile = 128;             // output columns of one item
+constexpr int kQ = kThreads / kTile;   // threads sharing a column in the DP
+constexpr int kMaxBandFused = 128;     // band heights handled by the fused kernel
+constexpr int kMOff = 128;             // column offset of the skewed M layout
+constexpr int kPad = 16;               // dead rows around V (uint8 path)
+constexpr int kFastB = 16;             // largest bend kept entirely in registers
+
+struct ImgDesc {
+    const void *img;
+    long long pitch;          // row stride in elements
+    int h, w, k, n, log2n, B, tiles;
+    long long item0;          // first work item of this image
+    void *mbuf[2];            // ping-pong window maxima, [D][mpitch] of Acc
+    int mpitch;
+    uint8_t *bp;              // [k][D][w] argmax e + n - 1 of each window
+    int *flags;               // [k][tiles] publication flags
+    unsigned long long *best; // lexicographic argmax key of V_0
+    int *done;                // band-0 tiles finished
+    int32_t *x_out, *d_out;
+    void *score_out;
+};
+
+struct Ctl {
+    int queue;   // next work item
+    int status;  // FHTDP_OK or FHTDP_ETIMEOUT
+    int pad[62];
+};
+
+// One work item of a batch: image index, band, column tile.
+struct Item {
+    int image, band, tile, pad;
+};
+
+struct LaunchArgs {
+    ImgDesc one;              // single-image launches
+    const ImgDesc *many;      // batched launches (device array), or null
+    const Item *order;        // batched launches: the queue, item by item
+    int count;
+    long long items;
+    Ctl *ctl;
+    long long wait_cycles;
+};
+
+// ---------------------------------------------------------------------------
+// Value <-> order-preserving integers.
+__device__ __forceinline__ uint32_t ord32(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t ord32(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+template <typename Acc>
+__device__ __forceinline__ Acc from_ord32(uint32_t o);
+template <>
+__device__ __forceinline__ int32_t from_ord32<int32_t>(uint32_t o) {
+    return (int32_t)(o ^ 0x80000000u);
+}
+template <>
+__device__ __forceinline__ float from_ord32<float>(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+template <typename W>
+__device__ __forceinline__ W from_bits(uint32_t b);
+template <>
+__device__ __forceinline__ uint32_t from_bits<uint32_t>(uint32_t b) { return b; }
+template <>
+__device__ __forceinline__ int32_t from_bits<int32_t>(uint32_t b) { return (int32_t)b; }
+template <>
+__device__ __forceinline__ float from_bits<float>(uint32_t b) { return __uint_as_float(b); }
+__device__ __forceinline__ uint32_t to_bits(uint32_t v) { return v; }
+__device__ __forceinline__ uint32_t to_bits(int32_t v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t to_bits(float v) { return __float_as_uint(v); }
+
+// Window keys: a value and its displacement index e + n - 1 (< 512) in one
+// integer whose maximum is the largest value with the smallest index.
+template <typename Acc, typename Key>
+struct KeyOps;
+template <>
+struct KeyOps<int32_t, int32_t> {   // non-negative values below 2^22
+    __device__ static int32_t dead() { return INT32_MIN; }
+    __device__ static int32_t make(int32_t v, int e) { return (v << 9) | (511 - e); }
+    __device__ static int32_t value(int32_t k) { return k >> 9; }
+    __device__ static int index(int32_t k) { return 511 - (k & 511); }
+};
+template <typename Acc>
+struct KeyOps<Acc, long long> {
+    __device__ static long long dead() { return LLONG_MIN; }
+    __device__ static long long make(Acc v, int e) {
+        int32_t so = (int32_t)(ord32(v) ^ 0x80000000u);
+        return ((long long)so << 9) | (511 - e);
+    }
+    __device__ static Acc value(long long k) {
+        return from_ord32<Acc>((uint32_t)(int32_t)(k >> 9) ^ 0x80000000u);
+    }
+    __device__ static int index(long long k) { return 511 - (int)(k & 511); }
+};
+
+template <typename T>
+__device__ __forceinline__ T kmax(T a, T b) {
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ int brev(int r, int bits) {
+    return bits ? (int)(__brev((unsigned)r) >> (32 - bits)) : 0;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait on a publication flag: gives up after `limit` cycles, or at
+// once when another wait of this launch has already given up.
+__device__ bool wait_flag(const int *flag, const Ctl *ctl, long long limit) {
+    long long t0 = clock64();
+    while (ld_acquire(flag) == 0) {
+        if (*(volatile const int *)&ctl->status != FHTDP_OK) return false;
+        if (clock64() - t0 > limit) return false;
+        __nanosleep(100);
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t pix_u8(const uint8_t *row, int col, int w) {
+    return (col >= 0 && col < w) ? (uint32_t)row[col] : 0u;
+}
+template <typename In>
+__device__ __forceinline__ In pix(const In *row, int col, int w) {
+    return (col >= 0 && col < w) ? row[col] : In(0);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory FHT of one band strip (Sec. 2.1).  F holds n rows of `pitch`
+// words (pitch >= T + n + 8, a multiple of 4).  Row y of the strip is loaded
+// into row y; after the level of m-row sub-bands, row j*m + brev(s) holds
+// shift s of sub-band j, so at the end row brev(s) holds the Hough row of
+// shift s.  Merging at level m pairs row A = j*m + r with row B = j*m + m/2 + r
+// (r = brev(s') over log2(m)-1 bits):
+//   A <- A(u) + B(u + s'),   B <- A(u) + B(u + s' + 1)
+// i.e. out(u, 2s') and out(u, 2s'+1) of the recursion.  A warp owns a row
+// pair and sweeps its columns left to right, 128 at a time (4 per lane, with
+// 16-byte shared loads and stores; the shift modulo 4 is warp-uniform and
+// selects a fixed register pattern): column u of row B is only read by
+// columns <= u, so the update is in place.  Columns past the level's valid
+// width are computed from stale words and are never read by valid ones.
+template <typename W, int Q>
+__device__ __forceinline__ void merge4(const uint4 &a4, const uint4 &b0, const uint4 &b1,
+                                       uint4 &oa, uint4 &ob) {
+    const W a[4] = {from_bits<W>(a4.x), from_bits<W>(a4.y), from_bits<W>(a4.z),
+                    from_bits<W>(a4.w)};
+    const W b[8] = {from_bits<W>(b0.x), from_bits<W>(b0.y), from_bits<W>(b0.z),
+                    from_bits<W>(b0.w), from_bits<W>(b1.x), from_bits<W>(b1.y),
+                    from_bits<W>(b1.z), from_bits<W>(b1.w)};
+    oa.x = to_bits(a[0] + b[Q + 0]);
+    oa.y = to_bits(a[1] + b[Q + 1]);
+    oa.z = to_bits(a[2] + b[Q + 2]);
+    oa.w = to_bits(a[3] + b[Q + 3]);
+    ob.x = to_bits(a[0] + b[Q + 1]);
+    ob.y = to_bits(a[1] + b[Q + 2]);
+    ob.z = to_bits(a[2] + b[Q + 3]);
+    ob.w = to_bits(a[3] + b[Q + 4]);
+}
+
+template <typename W>
+__device__ void fht_levels(W *F, int pitch, int n, int log2n, int T) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = kThreads / 32;
+    for (int l = 1; l <= log2n; ++l) {
+        const int m = 1 << l, half = m >> 1;
+        const int width = T + n - m;
+        for (int p = warp; p < n / 2; p += nwarps) {
+            const int j = p >> (l - 1), r = p & (half - 1);
+            const int sp = brev(r, l - 1);
+            const int q = sp & 3;   // warp-uniform
+            W *A = F + (size_t)(j * m + r) * pitch;
+            W *Brow = F + (size_t)(j * m + half + r) * pitch;
+            const W *Bq = Brow + (sp - q);
+            for (int u0 = 0; u0 < width; u0 += 128) {
+                const int u = u0 + 4 * lane;
+                const bool live = u < width;
+                uint4 oa = make_uint4(0, 0, 0, 0), ob = oa;
+                if (live) {
+                    const uint4 a4 = *(const uint4 *)&A[u];
+                    const uint4 b0 = *(const uint4 *)&Bq[u];
+                    const uint4 b1 = *(const uint4 *)&Bq[u + 4];
+                    switch (q) {
+                        case 0: merge4<W, 0>(a4, b0, b1, oa, ob); break;
+                        case 1: merge4<W, 1>(a4, b0, b1, oa, ob); break;
+                        case 2: merge4<W, 2>(a4, b0, b1, oa, ob); break;
+                        default: merge4<W, 3>(a4, b0, b1, oa, ob); break;
+                    }
+                }
+                __syncwarp();
+                if (live) {
+                    *(uint4 *)&A[u] = oa;
+                    *(uint4 *)&Brow[u] = ob;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Window maxima of one column (Sec. 2.3): M(c) = max_{|e-c|<=B} V(e) for c in
+// [c0, c1], as keys carrying the argmax.  Blocks of length L = 2B+1 start at
+// c0 - B; M(c0 + (q-1)L + i) = max(S_{q-1}[i], G_q[i-1]) with S the in-block
+// suffix maximum and G the in-block prefix maximum (van Herk / Gil-Werman),
+// or S_{q-1}[0] for i = 0.  Register version: L <= LMAX, every value of the
+// column range read once from shared memory.
+template <int LMAX, typename Key, typename VGet, typename Emit>
+__device__ __forceinline__ void window_regs(int c0, int c1, int B, Key dead, VGet vkey,
+                                            Emit emit) {
+    const int L = 2 * B + 1;
+    Key S[LMAX], Vb[LMAX];
+    const int a0 = c0 - B;
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) Vb[i] = i < L ? vkey(a0 + i) : dead;
+    Key run = dead;
+#pragma unroll
+    for (int i = LMAX - 1; i >= 0; --i) {
+        if (i < L) run = kmax(run, Vb[i]);
+        S[i] = run;
+    }
+    for (int c = c0, base = a0 + L; c <= c1; c += L, base += L) {
+        Key G = dead;
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i) {
+            if (i < L) {
+                const Key v = vkey(base + i);
+                Vb[i] = v;
+                const Key m = i == 0 ? S[0] : kmax(S[i], G);
+                G = kmax(G, v);
+                if (c + i <= c1) emit(c + i, m);
+            }
+        }
+        run = dead;
+#pragma unroll
+        for (int i = LMAX - 1; i >= 0; --i) {
+            if (i < L) run = kmax(run, Vb[i]);
+            S[i] = run;
+        }
+    }
+}
+
+// Two-pass version for any L: pass 1 stores the in-block suffix maxima
+// S(e), e in [c0-B, c1-B], through sput/sget; pass 2 runs the in-block prefix
+// maximum G(c+B) and combines.  Blocks are aligned at `a` (a <= c0 - B).
+template <typename Key, typename VGet, typename SPut, typename SGet, typename Emit>
+__device__ __forceinline__ void window_two_pass(int c0, int c1, int B, int a, int lo, int hi,
+                                                Key dead, VGet vkey, SPut sput, SGet sget,
+                                                Emit emit) {
+    const int L = 2 * B + 1;
+    int e = a + ((c1 - B - a) / L + 1) * L - 1;   // end of the block of c1-B
+    if (e > hi) e = hi;
+    int pos = (e - a) % L;
+    Key run = dead;
+    for (; e >= c0 - B; --e) {
+        const Key v = vkey(e);
+        run = pos == L - 1 ? v : kmax(run, v);
+        if (e <= c1 - B) sput(e, run);
+        pos = pos == 0 ? L - 1 : pos - 1;
+    }
+    int g = a + ((c0 + B - a) / L) * L;   // start of the block of c0+B
+    if (g < lo) g = lo;
+    pos = (g - a) % L;
+    Key gr = dead;
+    for (; g <= c1 + B; ++g) {
+        const Key v = vkey(g);
+        gr = pos == 0 ? v : kmax(gr, v);
+        pos = pos == L - 1 ? 0 : pos + 1;
+        if (g >= c0 + B) emit(g - B, kmax(sget(g - 2 * B), gr));
+    }
+}
+
+// Eq. 5: the polyline from the best top point, one backpointer per band.
+template <typename Acc>
+__device__ void readback(const ImgDesc &im, const LaunchArgs &args) {
+    const int n = im.n, D = 2 * n - 1;
+    __threadfence();
+    const unsigned long long key = atomicAdd(im.best, 0ull);
+    const unsigned lin = 0xffffffffu - (unsigned)(key & 0xffffffffu);
+    int xx = (int)(lin >> 9), d = (int)(lin & 511) - (n - 1);
+    im.x_out[0] = xx;
+    im.d_out[0] = d;
+    *(Acc *)im.score_out = from_ord32<Acc>((uint32_t)(key >> 32));
+    for (int i = 1; i < im.k; ++i) {
+        xx += d;
+        // Only reachable with inconsistent DP data (a wait gave up): stop
+        // instead of reading outside bp.
+        if (xx < 0 || xx >= im.w || d < -(n - 1) || d > n - 1) {
+            atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+            return;
+        }
+        const int e = __ldcg(im.bp + ((size_t)i * D + (d + n - 1)) * im.w + xx);
+        d = e - (n - 1);
+        im.x_out[i] = xx;
+        im.d_out[i] = d;
+    }
+    im.x_out[im.k] = xx + d;
+}
+
+// Band 0: fold this tile's best (value, x, d) key into the image's and, on
+// the image's last band-0 tile, read the polyline back.
+template <typename Acc>
+__device__ void finish_band0(unsigned long long best, const ImgDesc &im, const LaunchArgs &args) {
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = best > other ? best : other;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int prev = atomicAdd(im.done, 1);
+        if (prev == im.tiles - 1) readback<Acc>(im, args);
+    }
+}
+
+__device__ __forceinline__ unsigned long long argmax_key(uint32_t ordv, int x, int eidx) {
+    return ((unsigned long long)ordv << 32) | (0xffffffffu - (unsigned)(x * 512 + eidx));
+}
+
+// Waits for the three band+1 tiles whose window maxima a tile of `band` reads.
+__device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
+    if (band >= im.k - 1) return;
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int c = max(tile - 1, 0); c <= min(tile + 1, im.tiles - 1) && ok; ++c)
+            ok = wait_flag(im.flags + (size_t)(band + 1) * im.tiles + c, args.ctl,
+                           args.wait_cycles);
+        if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ void publish(const ImgDesc &im, int band, int tile) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(im.flags + (size_t)band * im.tiles + tile, 1);
+    }
+}
+
+// Stores M_b(x, c) (skewed so that the consumer reads M(x + d, d) as row d,
+// column x) and its argmax byte.
+template <typename Acc, typename Key>
+__device__ __forceinline__ void store_window(const ImgDesc &im, Acc *mnext, uint8_t *bp, int x,
+                                             int c, Key mk) {
+    using KO = KeyOps<Acc, Key>;
+    const int n = im.n;
+    const bool dead = mk == KO::dead();
+    mnext[(size_t)(c + n - 1) * im.mpitch + kMOff + x - c] = dead ? Dead<Acc>::value()
+                                                                  : KO::value(mk);
+    bp[(size_t)(c + n - 1) * im.w + x] = (uint8_t)(dead ? 0 : KO::index(mk));
+}
+
+// ---------------------------------------------------------------------------
+// uint8 images.  Shared memory: region A holds the FHT strip F, later V in
+// natural displacement order with kPad dead rows on both sides; region Hc
+// holds the compact packed Hough words, later the generic window's S.
+template <typename Key>
+struct U8Path {
+    using Acc = int32_t;
+    using KO = KeyOps<int32_t, Key>;
+    static constexpr int kRounds = sizeof(Key) == 4 ? 2 : 4;
+
+    __host__ __device__ static int fpitch(int n) { return (kTile + n + 8 + 3) & ~3; }
+    __host__ __device__ static int frows(int n) { return n < 2 ? 2 : n; }
+    __host__ __device__ static size_t a_bytes(int n) {
+        size_t f = (size_t)frows(n) * fpitch(n) * 4;
+        size_t v = (size_t)(2 * n - 1 + 2 * kPad) * kTile * 4;
+        return ((f > v ? f : v) + 15) / 16 * 16;
+    }
+    __host__ __device__ static size_t hc_bytes(int n) {
+        size_t hc = (size_t)n * kTile * 4;
+        size_t s = (size_t)((2 * n - 1 + kRounds - 1) / kRounds) * kTile * sizeof(Key);
+        return hc > s ? hc : s;
+    }
+    static size_t smem_bytes(int n) { return a_bytes(n) + hc_bytes(n); }
+
+    // Four pixels [c, c+4) of a row as one little-endian word, zero outside
+    // [0, w).  c is a multiple of 4; `aligned` says rows start on 4 bytes.
+    __device__ static uint32_t load4(const uint8_t *row, int c, int w, bool aligned) {
+        if (aligned && c >= 0 && c + 4 <= w) return __ldg((const uint32_t *)(row + c));
+        uint32_t v = 0;
+        for (int j = 0; j < 4; ++j) v |= pix_u8(row, c + j, w) << (8 * j);
+        return v;
+    }
+
+    __device__ static void fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0) {
+        const int n = im.n, T = kTile, pitch = fpitch(n);
+        const int G = (T + n - 1 + 3) / 4;   // groups of 4 strip columns per row
+        const uint8_t *base = (const uint8_t *)im.img + (size_t)band * n * im.pitch;
+        const bool aligned = ((uintptr_t)im.img % 4 == 0) && (im.pitch % 4 == 0);
+        // Word u of strip row y = pixel (y, x0 + u) | pixel (y, x0 + T - 1 - u) << 16.
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < n * G; idx += kThreads) {
+            const int y = idx / G, u0 = 4 * (idx - y * G);
+            const uint8_t *row = base + (size_t)y * im.pitch;
+            const uint32_t lo4 = load4(row, x0 + u0, im.w, aligned);
+            const uint32_t hi4 = load4(row, x0 + T - 4 - u0, im.w, aligned);
+            uint4 out;
+            out.x = __byte_perm(lo4, hi4, 0x0700) & 0x00ff00ffu;
+            out.y = __byte_perm(lo4, hi4, 0x0601) & 0x00ff00ffu;
+            out.z = __byte_perm(lo4, hi4, 0x0502) & 0x00ff00ffu;
+            out.w = __byte_perm(lo4, hi4, 0x0403) & 0x00ff00ffu;
+            *(uint4 *)&F[(size_t)y * pitch + u0] = out;
+        }
+        __syncthreads();
+        fht_levels<uint32_t>(F, pitch, n, im.log2n, T);
+        // Compact: Hc[s][u] = packed Hough word of shift s at tile column u.
+        for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
+            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            *(uint4 *)&Hc[s * T + u0] = *(const uint4 *)&F[(size_t)brev(s, im.log2n) * pitch + u0];
+        }
+        __syncthreads();
+    }
+
+    // V rows: V(e) of tile column u at Vn[(e + n - 1 + kPad) * T + u].
+    __device__ static unsigned long long form_v(int32_t *Vn, const uint32_t *Hc,
+                                                const ImgDesc &im, int band, const Acc *mprev,
+                                                int x0) {
+        const int n = im.n, T = kTile, D = 2 * n - 1;
+        const bool last = band == im.k - 1;
+        const Acc dead = Dead<Acc>::value();
+        unsigned long long best = 0;
+        if (band != 0) {
+            for (int idx = threadIdx.x; idx < 2 * kPad * (T / 4); idx += kThreads) {
+                const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
+                const int row = r < kPad ? r : r - kPad + kPad + D;
+                *(int4 *)&Vn[row * T + u0] = make_int4(dead, dead, dead, dead);
+            }
+        }
+#pragma unroll 2
+        for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
+            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            const uint4 hw = *(const uint4 *)&Hc[s * T + u0];
+            const uint32_t hws[4] = {hw.x, hw.y, hw.z, hw.w};
+            // "+" half: column x0 + u0 + j, displacement +s.
+            const int xp = x0 + u0;
+            int4 mp = make_int4(0, 0, 0, 0), mm = mp;
+            if (!last) {
+                mp = __ldcg((const int4 *)(mprev + (size_t)(s + n - 1) * im.mpitch + kMOff + xp));
+                if (s > 0)
+                    mm = __ldcg((const int4 *)(mprev + (size_t)(n - 1 - s) * im.mpitch + kMOff +
+                                               x0 + T - 4 - u0));
+            }
+            const int mps[4] = {mp.x, mp.y, mp.z, mp.w};
+            const int mms[4] = {mm.x, mm.y, mm.z, mm.w};   // column x0 + T - 4 - u0 + t
+            int vp[4], vm[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = xp + j;
+                const bool ok = x < im.w && x + s < im.w;
+                const int m = mps[j];
+                vp[j] = !ok ? dead : last ? (int)(hws[j] & 0xffffu)
+                                          : (m == dead ? dead : (int)(hws[j] & 0xffffu) + m);
+                // "-" half of word j: column x0 + T - 1 - u0 - j, displacement -s.
+                const int xm = x0 + T - 1 - u0 - j;
+                const bool okm = s > 0 && xm < im.w && xm - s >= 0;
+                const int mmv = mms[3 - j];
+                vm[j] = !okm ? dead : last ? (int)(hws[j] >> 16)
+                                           : (mmv == dead ? dead : (int)(hws[j] >> 16) + mmv);
+            }
+            if (band == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (vp[j] != dead) {
+                        const unsigned long long k = argmax_key(ord32(vp[j]), xp + j, s + n - 1);
+                        best = best > k ? best : k;
+                    }
+                    if (vm[j] != dead) {
+                        const unsigned long long k =
+                            argmax_key(ord32(vm[j]), x0 + T - 1 - u0 - j, n - 1 - s);
+                        best = best > k ? best : k;
+                    }
+                }
+            } else {
+                *(int4 *)&Vn[(s + n - 1 + kPad) * T + u0] = make_int4(vp[0], vp[1], vp[2], vp[3]);
+                if (s > 0)
+                    *(int4 *)&Vn[(n - 1 - s + kPad) * T + (T - 4 - u0)] =
+                        make_int4(vm[3], vm[2], vm[1], vm[0]);
+            }
+        }
+        return best;
+    }
+
+    __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
+                                   const LaunchArgs &args) {
+        const int n = im.n, T = kTile, D = 2 * n - 1;
+        const int x0 = tile * T;
+        uint32_t *F = (uint32_t *)smem;
+        int32_t *Vn = (int32_t *)smem;
+        uint32_t *Hc = (uint32_t *)(smem + a_bytes(n));
+        fht(F, Hc, im, band, x0);
+        wait_deps(im, band, tile, args);
+        const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
+        Acc *mnext = (Acc *)im.mbuf[band & 1];
+        const unsigned long long best = form_v(Vn, Hc, im, band, mprev, x0);
+        if (band == 0) {
+            finish_band0<Acc>(best, im, args);
+            return;
+        }
+        __syncthreads();
+
+        const int u = threadIdx.x % T, qd = threadIdx.x / T;
+        const int x = x0 + u;
+        const int B = im.B;   // already clamped to 2n-2
+        const int lo = -(n - 1), hi = n - 1;
+        uint8_t *bp = im.bp + (size_t)band * D * im.w;
+        const int32_t *col = Vn + u;
+        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
+        if (sizeof(Key) == 4 && B <= kFastB) {
+            // V rows [lo - kPad, hi + kPad] exist (dead outside [lo, hi]);
+            // the register window never reads below c0 - B >= lo - kPad, and
+            // reads above hi are replaced by dead keys.
+            auto vkey = [&](int e) -> Key {
+                if (e > hi) return KO::dead();
+                const int v = col[(e + n - 1 + kPad) * T];
+                return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
+            };
+            const int c0 = lo + (qd * D) / kQ, c1 = lo + ((qd + 1) * D) / kQ - 1;
+            if (c0 <= c1 && x < im.w) {
+                if (B <= 4)
+                    window_regs<9, Key>(c0, c1, B, KO::dead(), vkey, emit);
+                else if (B <= 8)
+                    window_regs<17, Key>(c0, c1, B, KO::dead(), vkey, emit);
+                else
+                    window_regs<33, Key>(c0, c1, B, KO::dead(), vkey, emit);
+            }
+        } else {
+            auto vkey = [&](int e) -> Key {
+                if (e < lo || e > hi) return KO::dead();
+                const int v = col[(e + n - 1 + kPad) * T];
+                return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
+            };
+            Key *S = (Key *)Hc;
+            for (int round = 0; round < kRounds; ++round) {
+                const int P0 = lo + (round * D) / kRounds;
+                const int P1 = lo + ((round + 1) * D) / kRounds - 1;
+                const int span = P1 - P0 + 1;
+                const int c0 = P0 + (qd * span) / kQ, c1 = P0 + ((qd + 1) * span) / kQ - 1;
+                const int srow0 = P0 - B;   // S(e) at row e - srow0
+                auto sput = [&](int e, Key v) { S[(size_t)(e - srow0) * T + u] = v; };
+                auto sget = [&](int e) { return S[(size_t)(e - srow0) * T + u]; };
+                if (c0 <= c1 && x < im.w)
+                    window_two_pass<Key>(c0, c1, B, lo - B, lo, hi, KO::dead(), vkey, sput, sget,
+                                         emit);
+                __syncthreads();
+            }
+        }
+        publish(im, band, tile);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// int32 / float images: the halves run one after the other in F; the "+"
+// half is kept in Hp.  V is formed in place (V(+s) over Hp, V(-s) over the
+// mirrored "-" half in F), and the window's S lives in the columns
+// [T, 2T) of F.
+template <typename In, typename Acc, typename Key>
+struct WidePath {
+    using KO = KeyOps<Acc, Key>;
+    static constexpr int kRounds = sizeof(Key) == 4 ? 2 : 4;
+
+    __host__ __device__ static int fpitch(int n) {
+        int p = (kTile + n + 8 + 3) & ~3;
+        return p > 2 * kTile ? p : 2 * kTile;
+    }
+    __host__ __device__ static int frows(int n) { return n < 2 ? 2 : n; }
+    __host__ __device__ static size_t f_bytes(int n) { return (size_t)frows(n) * fpitch(n) * 4; }
+    static size_t smem_bytes(int n) { return f_bytes(n) + (size_t)n * kTile * 4; }
+
+    // Pixels [c, c+4) of a row, zero outside [0, w); c is a multiple of 4.
+    __device__ static void load4(const In *row, int c, int w, bool aligned, Acc out[4]) {
+        if (aligned && c >= 0 && c + 4 <= w) {
+            const int4 v = __ldg((const int4 *)(row + c));
+            out[0] = from_bits<Acc>((uint32_t)v.x);
+            out[1] = from_bits<Acc>((uint32_t)v.y);
+            out[2] = from_bits<Acc>((uint32_t)v.z);
+            out[3] = from_bits<Acc>((uint32_t)v.w);
+            return;
+        }
+        for (int j = 0; j < 4; ++j) out[j] = (Acc)pix(row, c + j, w);
+    }
+
+    __device__ static void fht(Acc *F, Acc *Hp, const ImgDesc &im, int band, int x0) {
+        const int n = im.n, T = kTile, pitch = fpitch(n);
+        const int G = (T + n - 1 + 3) / 4;
+        const In *base = (const In *)im.img + (size_t)band * n * im.pitch;
+        const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 4 == 0);
+        for (int sign = 0; sign < 2; ++sign) {
+            // "+": word u = pixel x0 + u; "-": word u = pixel x0 + T - 1 - u.
+#pragma unroll 4
+            for (int idx = threadIdx.x; idx < n * G; idx += kThreads) {
+                const int y = idx / G, u0 = 4 * (idx - y * G);
+                const In *row = base + (size_t)y * im.pitch;
+                Acc v[4];
+                load4(row, sign == 0 ? x0 + u0 : x0 + T - 4 - u0, im.w, aligned, v);
+                float4 o;
+                if (sign == 0)
+                    o = make_float4(__uint_as_float(to_bits(v[0])), __uint_as_float(to_bits(v[1])),
+                                    __uint_as_float(to_bits(v[2])), __uint_as_float(to_bits(v[3])));
+                else
+                    o = make_float4(__uint_as_float(to_bits(v[3])), __uint_as_float(to_bits(v[2])),
+                                    __uint_as_float(to_bits(v[1])), __uint_as_float(to_bits(v[0])));
+                *(float4 *)&F[(size_t)y * pitch + u0] = o;
+            }
+            __syncthreads();
+            fht_levels<Acc>(F, pitch, n, im.log2n, T);
+            if (sign == 0) {
+                for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
+                    const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
+                    *(float4 *)&Hp[r * T + u0] = *(const float4 *)&F[(size_t)r * pitch + u0];
+                }
+                __syncthreads();
+            }
+        }
+    }
+
+    // V(x0 + u, e) after form_v; e inside [-(n-1), n-1].
+    __device__ static Acc vval(const Acc *F, const Acc *Hp, int pitch, int log2n, int u, int e) {
+        if (e >= 0) return Hp[(size_t)brev(e, log2n) * kTile + u];
+        return F[(size_t)brev(-e, log2n) * pitch + (kTile - 1 - u)];
+    }
+
+    __device__ static Acc link_value(Acc h, const ImgDesc &im, int band, const Acc *mprev, int x,
+                                     int e) {
+        const Acc dead = Dead<Acc>::value();
+        const bool ok = x < im.w && x + e >= 0 && x + e < im.w;
+        if (!ok) return dead;
+        if (band == im.k - 1) return h;
+        const Acc m = __ldcg(mprev + (size_t)(e + im.n - 1) * im.mpitch + kMOff + x);
+        return m == dead ? dead : h + m;
+    }
+
+    __device__ static unsigned long long form_v(Acc *F, Acc *Hp, const ImgDesc &im, int band,
+                                                const Acc *mprev, int x0) {
+        const int n = im.n, T = kTile, pitch = fpitch(n);
+        unsigned long long best = 0;
+#pragma unroll 4
+        for (int idx = threadIdx.x; idx < n * T; idx += kThreads) {
+            const int slot = idx / T, up = idx - slot * T;
+            const int s = brev(slot, im.log2n);
+            const int xp = x0 + up, xm = x0 + T - 1 - up;
+            const Acc vp = link_value(Hp[idx], im, band, mprev, xp, s);
+            const Acc vm = s > 0 ? link_value(F[(size_t)slot * pitch + up], im, band, mprev, xm, -s)
+                                 : Dead<Acc>::value();
+            if (band == 0) {
+                const Acc dead = Dead<Acc>::value();
+                if (vp != dead) {
+                    const unsigned long long k = argmax_key(ord32(vp), xp, s + n - 1);
+                    best = best > k ? best : k;
+                }
+                if (vm != dead) {
+                    const unsigned long long k = argmax_key(ord32(vm), xm, n - 1 - s);
+                    best = best > k ? best : k;
+                }
+            } else {
+                Hp[idx] = vp;
+                F[(size_t)slot * pitch + up] = vm;
+            }
+        }
+        return best;
+    }
+
+    __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
+                                   const LaunchArgs &args) {
+        const int n = im.n, T = kTile, D = 2 * n - 1;
+        const int pitch = fpitch(n);
+        const int x0 = tile * T;
+        Acc *F = (Acc *)smem;
+        Acc *Hp = (Acc *)(smem + f_bytes(n));
+        fht(F, Hp, im, band, x0);
+        wait_deps(im, band, tile, args);
+        const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
+        Acc *mnext = (Acc *)im.mbuf[band & 1];
+        const unsigned long long best = form_v(F, Hp, im, band, mprev, x0);
+        if (band == 0) {
+            finish_band0<Acc>(best, im, args);
+            return;
+        }
+        __syncthreads();
+
+        const int u = threadIdx.x % T, qd = threadIdx.x / T;
+        const int x = x0 + u;
+        const int B = im.B;
+        const int lo = -(n - 1), hi = n - 1;
+        uint8_t *bp = im.bp + (size_t)band * D * im.w;
+        auto vkey = [&](int e) -> Key {
+            if (e < lo || e > hi) return KO::dead();
+            const Acc v = vval(F, Hp, pitch, im.log2n, u, e);
+            return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
+        };
+        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
+        // S(row, u): a Key per (row, column) packed into the columns [T, 2T) of F.
+        auto s_at = [&](int row) -> Key * {
+            const int wi = (row * T + u) * (int)(sizeof(Key) / 4);
+            return (Key *)(F + (size_t)(wi / T) * pitch + T + (wi % T));
+        };
+        for (int round = 0; round < kRounds; ++round) {
+            const int P0 = lo + (round * D) / kRounds;
+            const int P1 = lo + ((round + 1) * D) / kRounds - 1;
+            const int span = P1 - P0 + 1;
+            const int c0 = P0 + (qd * span) / kQ, c1 = P0 + ((qd + 1) * span) / kQ - 1;
+            const int srow0 = P0 - B;
+            auto sput = [&](int e, Key v) { *s_at(e - srow0) = v; };
+            auto sget = [&](int e) { return *s_at(e - srow0); };
+            if (c0 <= c1 && x < im.w)
+                window_two_pass<Key>(c0, c1, B, lo - B, lo, hi, KO::dead(), vkey, sput, sget,
+                                         emit);
+            __syncthreads();
+        }
+        publish(im, band, tile);
+    }
+};
+
+template <typename In, typename Acc, typename Key>
+struct PathOf {
+    using type = WidePath<In, Acc, Key>;
+};
+template <typename Key>
+struct PathOf<uint8_t, int32_t, Key> {
+    using type = U8Path<Key>;
+};
+
+template <typename In, typename Acc, typename Key>
+__global__ void __launch_bounds__(kThreads, 1) engine_kernel(LaunchArgs args) {
+    using P = typename PathOf<In, Acc, Key>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&args.ctl->queue, 1);
+        __syncthreads();
+        const long long item = s_item;
+        __syncthreads();
+        if (item >= args.items) break;
+        const ImgDesc *imp = &args.one;
+        int band, tile;
+        if (args.many) {
+            const Item it = args.order[item];
+            imp = &args.many[it.image];
+            band = it.band;
+            tile = it.tile;
+        } else {
+            band = imp->k - 1 - (int)(item / imp->tiles);
+            tile = (int)(item % imp->tiles);
+        }
+        P::process(*imp, band, tile, smem_raw, args);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+//
+// Workspace of a run: [Ctl][per-image counters: flags, best, done][image
+// table][per-image M ping-pong buffers and backpointers].  The first two
+// parts are cleared by one memset per run; the table is written once by
+// fhtdp_batch_upload (single-image runs pass their descriptor by value).
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct ImgPlan {
+    fhtdp_image io;
+    Shape s;
+    int B, tiles, mpitch;
+    long long item0;
+    size_t flags, best, done;   // offsets in the counter region
+    size_t m0, m1, bp;          // offsets in the data region
+};
+
+struct RunLayout {
+    size_t zero_bytes;   // Ctl + counters
+    size_t table_off, table_bytes;
+    size_t order_off, order_bytes;
+    size_t data_off, total;
+    long long items;
+    int max_n, max_h;
+};
+
+int tiles_of(const Shape &s) { return (s.w + kTile - 1) / kTile; }
+
+RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
+    RunLayout L{};
+    size_t off = sizeof(Ctl);
+    long long items = 0;
+    for (auto &p : imgs) {
+        p.tiles = tiles_of(p.s);
+        // Row reads of M go up to 4 words past the last tile's columns.
+        p.mpitch = (int)align_up((size_t)kMOff + p.s.w + kTile + 4, 32);
+        p.item0 = items;
+        items += (long long)p.s.k * p.tiles;
+        p.flags = off;
+        off = align_up(off + (size_t)p.s.k * p.tiles * 4, 8);
+        p.best = off;
+        off += 8;
+        p.done = off;
+        off = align_up(off + 4, 8);
+        L.max_n = std::max(L.max_n, p.s.n);
+        L.max_h = std::max(L.max_h, p.s.h);
+    }
+    L.zero_bytes = align_up(off, 256);
+    L.table_off = L.zero_bytes;
+    L.table_bytes = with_table ? align_up(sizeof(ImgDesc) * imgs.size(), 256) : 0;
+    L.order_off = L.table_off + L.table_bytes;
+    L.order_bytes = with_table ? align_up(sizeof(Item) * (size_t)items, 256) : 0;
+    size_t d = 0;
+    for (auto &p : imgs) {
+        p.m0 = d;
+        d = align_up(d + (size_t)p.s.D * p.mpitch * 4, 256);
+        p.m1 = d;
+        d = align_up(d + (size_t)p.s.D * p.mpitch * 4, 256);
+        p.bp = d;
+        d = align_up(d + (size_t)p.s.k * p.s.D * p.s.w, 256);
+    }
+    L.data_off = L.order_off + L.order_bytes;
+    L.total = L.data_off + d;
+    L.items = items;
+    return L;
+}
+
+ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws) {
+    ImgDesc im{};
+    im.img = p.io.img;
+    im.pitch = p.io.pitch;
+    im.h = p.s.h;
+    im.w = p.s.w;
+    im.k = p.s.k;
+    im.n = p.s.n;
+    im.log2n = p.s.log2n;
+    im.B = p.B;
+    im.tiles = p.tiles;
+    im.item0 = p.item0;
+    char *data = ws + L.data_off;
+    im.mbuf[0] = data + p.m0;
+    im.mbuf[1] = data + p.m1;
+    im.mpitch = p.mpitch;
+    im.bp = (uint8_t *)(data + p.bp);
+    im.flags = (int *)(ws + p.flags);
+    im.best = (unsigned long long *)(ws + p.best);
+    im.done = (int *)(ws + p.done);
+    im.x_out = p.io.x_out;
+    im.d_out = p.io.d_out;
+    im.score_out = p.io.score_out;
+    return im;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+template <typename In, typename Acc, typename Key>
+int launch_kernel(const LaunchArgs &args, int max_n, cudaStream_t stream) {
+    using P = typename PathOf<In, Acc, Key>::type;
+    const size_t smem = P::smem_bytes(max_n);
+    auto kern = engine_kernel<In, Acc, Key>;
+    static int smem_set = 0;   // dynamic shared memory enabled for this kernel
+    if ((int)smem > smem_set) {
+        int st = cuda_status(cudaFuncSetAttribute(kern,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P::smem_bytes(kMaxBandFused)),
+                             "cudaFuncSetAttribute");
+        if (st) return st;
+        smem_set = (int)P::smem_bytes(kMaxBandFused);
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = (long long)num_sms() * per_sm;
+    if (grid > args.items) grid = args.items;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kThreads, smem, stream>>>(args);
+    return launched("engine_kernel");
+}
+
+int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, cudaStream_t stream) {
+    switch (dtype) {
+        case FHTDP_U8:
+            if (255LL * max_h < (1LL << 22))
+                return launch_kernel<uint8_t, int32_t, int32_t>(args, max_n, stream);
+            return launch_kernel<uint8_t, int32_t, long long>(args, max_n, stream);
+        case FHTDP_I32:
+            return launch_kernel<int32_t, int32_t, long long>(args, max_n, stream);
+        default:
+            return launch_kernel<float, float, long long>(args, max_n, stream);
+    }
+}
+
+LaunchArgs base_args(const RunLayout &L, char *ws, int count) {
+    LaunchArgs args{};
+    args.count = count;
+    args.items = L.items;
+    args.ctl = (Ctl *)ws;
+    args.wait_cycles = 4000000000LL;   // about two seconds at GB300 clocks
+    return args;
+}
+
+int run_fallback(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
+                 int32_t *d_out, void *score_out, void *ws, cudaStream_t stream) {
+    // 256-row bands: the level-by-level FHT, the in-place DP and the
+    // single-block read-back.
+    int st = cuda_status(cudaMemsetAsync(ws, 0, sizeof(Ctl), stream), "cudaMemsetAsync");
+    if (st) return st;
+    size_t hough = (size_t)s.k * 2 * s.n * s.W;
+    char *base = (char *)ws + 256;
+    if (dtype == FHTDP_F32) {
+        float *H = (float *)base, *tmp = H + hough;
+        st = launch_fht_stages<float, float>((const float *)img, pitch, s, H, tmp, stream);
+        if (!st) st = launch_dp_inplace<float>(H, s, B, stream);
+        if (!st) st = launch_backtrack<float>(H, s, B, x_out, d_out, (float *)score_out, stream);
+        return st;
+    }
+    int32_t *H = (int32_t *)base, *tmp = H + hough;
+    if (dtype == FHTDP_U8)
+        st = launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream);
+    else
+        st = launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
+    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
+    if (!st) st = launch_backtrack<int32_t>(H, s, B, x_out, d_out, (int32_t *)score_out, stream);
+    return st;
+}
+
+ImgPlan single_plan(const void *img, int pitch, const Shape &s, int B, int32_t *x_out,
+                    int32_t *d_out, void *score_out) {
+    ImgPlan p{};
+    p.io.img = img;
+    p.io.h = s.h;
+    p.io.w = s.w;
+    p.io.pitch = pitch;
+    p.io.k = s.k;
+    p.io.B = B;
+    p.io.x_out = x_out;
+    p.io.d_out = d_out;
+    p.io.score_out = score_out;
+    p.s = s;
+    p.B = B < 2 * s.n - 2 ? B : 2 * s.n - 2;   // wider windows change nothing
+    return p;
+}
+
+}  // namespace
+
+// The host-side plan of a batch.
+struct BatchPlan {
+    int dtype;
+    std::vector<ImgPlan> imgs;
+    RunLayout L;
+    std::vector<ImgDesc> staging;   // image table as uploaded
+    std::vector<Item> order;        // work queue as uploaded
+    void *bound_ws = nullptr;
+};
+
+// Queue order of a batch.  Images are taken in groups whose band levels
+// hold about `target` tiles each; inside a group the items go band level by
+// band level (the last band of every image first), image by image, tile by
+// tile.  Every item therefore comes after the band+1 tiles it waits for, so
+// the queue cannot deadlock, and the band chains of a whole group advance
+// together instead of one image at a time.  Groups bound the number of
+// images in flight, so their M buffers stay in L2.
+std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target) {
+    std::vector<Item> order;
+    size_t first = 0;
+    while (first < imgs.size()) {
+        size_t last = first;
+        long long per_level = 0;
+        while (last < imgs.size() && (last == first || per_level < target)) {
+            per_level += imgs[last].tiles;
+            ++last;
+        }
+        int levels = 0;
+        for (size_t i = first; i < last; ++i) levels = std::max(levels, imgs[i].s.k);
+        for (int lv = 0; lv < levels; ++lv)
+            for (size_t i = first; i < last; ++i) {
+                if (lv >= imgs[i].s.k) continue;
+                for (int t = 0; t < imgs[i].tiles; ++t)
+                    order.push_back(Item{(int)i, imgs[i].s.k - 1 - lv, t, 0});
+            }
+        first = last;
+    }
+    return order;
+}
 
 size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
     (void)dtype;
-    (void)B;
-    size_t hough = (size_t)s.k * 2 * s.n * s.W * 4;
-    return 2 * hough;
+    if (s.n > kMaxBandFused) return 256 + 2 * (size_t)s.k * 2 * s.n * s.W * 4;
+    std::vector<ImgPlan> one{single_plan(nullptr, s.w, s, B, nullptr, nullptr, nullptr)};
+    return plan_layout(one, false).total;
 }
 
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                   int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream) {
     (void)ws_bytes;
-    size_t hough = (size_t)s.k * 2 * s.n * s.W;
-    int st;
-    if (dtype == FHTDP_F32) {
-        float *H = (float *)ws, *tmp = H + hough;
-        st = launch_fht_stages<float, float>((const float *)img, pitch, s, H, tmp, stream);
-        if (!st) st = launch_dp_inplace<float>(H, s, B, stream);
-        if (!st) st = launch_backtrack<float>(H, s, B, x_out, d_out, (float *)score_out, stream);
-    } else {
-        int32_t *H = (int32_t *)ws, *tmp = H + hough;
-        if (dtype == FHTDP_U8)
-            st = launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream);
-        else
-            st = launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
-        if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
-        if (!st)
-            st = launch_backtrack<int32_t>(H, s, B, x_out, d_out, (int32_t *)score_out, stream);
-    }
-    return st;
+    if (s.n > kMaxBandFused)
+        return run_fallback(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, stream);
+    std::vector<ImgPlan> one{single_plan(img, pitch, s, B, x_out, d_out, score_out)};
+    RunLayout L = plan_layout(one, false);
+    char *base = (char *)ws;
+    int st = cuda_status(cudaMemsetAsync(base, 0, L.zero_bytes, stream), "cudaMemsetAsync");
+    if (st) return st;
+    LaunchArgs args = base_args(L, base, 1);
+    args.one = make_desc(one[0], L, base);
+    args.many = nullptr;
+    args.order = nullptr;
+    return dispatch(dtype, L.max_h, args, L.max_n, stream);
 }
+
+int engine_status(const void *ws, cudaStream_t stream) {
+    int status = 0;
+    int st = cuda_status(cudaMemcpyAsync(&status, (const char *)ws + offsetof(Ctl, status),
+                                         sizeof(int), cudaMemcpyDeviceToHost, stream),
+                         "cudaMemcpyAsync");
+    if (st) return st;
+    st = cuda_status(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    if (st) return st;
+    if (status != FHTDP_OK) return set_error(status, "a device-side wait gave up");
+    return FHTDP_OK;
+}
+
+int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **out) {
+    if (count < 1 || !images) return set_error(FHTDP_EINVAL, "empty batch");
+    BatchPlan *plan = new (std::nothrow) BatchPlan();
+    if (!plan) return set_error(FHTDP_EINVAL, "out of host memory");
+    plan->dtype = dtype;
+    for (int i = 0; i < count; ++i) {
+        const fhtdp_image &io = images[i];
+        Shape s;
+        if (!make_shape(io.h, io.w, io.k, &s) || io.pitch < io.w || io.B < 0 || !io.img ||
+            !io.x_out || !io.d_out || !io.score_out) {
+            delete plan;
+            return set_error(FHTDP_EINVAL,
+                             "image %d: invalid (h=%d w=%d pitch=%d k=%d B=%d or null pointer)",
+                             i, io.h, io.w, io.pitch, io.k, io.B);
+        }
+        if (s.n > kMaxBandFused) {
+            delete plan;
+            return set_error(FHTDP_EINVAL,
+                             "image %d: bands of %d rows are not supported in batches (max %d)",
+                             i, s.n, kMaxBandFused);
+        }
+        plan->imgs.push_back(single_plan(io.img, io.pitch, s, io.B, io.x_out, io.d_out,
+                                         io.score_out));
+    }
+    plan->L = plan_layout(plan->imgs, true);
+    plan->order = queue_order(plan->imgs, (long long)num_sms() * 3 / 2);
+    *out = plan;
+    return FHTDP_OK;
+}
+
+size_t batch_workspace_bytes(const BatchPlan *plan) { return plan ? plan->L.total : 0; }
+
+long long batch_items(const BatchPlan *plan) { return plan ? plan->L.items : 0; }
+
+int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
+    if (ws_bytes < plan->L.total)
+        return set_error(FHTDP_EWORKSPACE, "batch workspace needs %zu bytes, got %zu",
+                         plan->L.total, ws_bytes);
+    plan->staging.clear();
+    for (auto &p : plan->imgs) plan->staging.push_back(make_desc(p, plan->L, (char *)ws));
+    plan->bound_ws = ws;
+    int st = cuda_status(cudaMemcpyAsync((char *)ws + plan->L.table_off, plan->staging.data(),
+                                         sizeof(ImgDesc) * plan->staging.size(),
+                                         cudaMemcpyHostToDevice, stream),
+                         "cudaMemcpyAsync");
+    if (st) return st;
+    return cuda_status(cudaMemcpyAsync((char *)ws + plan->L.order_off, plan->order.data(),
+                                       sizeof(Item) * plan->order.size(),
+                                       cudaMemcpyHostToDevice, stream),
+                       "cudaMemcpyAsync");
+}
+
+int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
+    if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
+    if (ws != plan->bound_ws)
+        return set_error(FHTDP_EINVAL, "workspace differs from the one given to fhtdp_batch_upload");
+    char *base = (char *)ws;
+    int st = cuda_status(cudaMemsetAsync(base, 0, plan->L.zero_bytes, stream), "cudaMemsetAsync");
+    if (st) return st;
+    LaunchArgs args = base_args(plan->L, base, (int)plan->imgs.size());
+    args.many = (const ImgDesc *)(base + plan->L.table_off);
+    args.order = (const Item *)(base + plan->L.order_off);
+    return dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, stream);
+}
+
+void batch_destroy(BatchPlan *plan) { delete plan; }
 
 }  // namespace fhtdp

@@ -5,7 +5,16 @@
 
 namespace fhtdp {
 
+struct BatchPlan;
+
 size_t engine_workspace_bytes(int dtype, const Shape &s, int B);
+int engine_status(const void *ws, cudaStream_t stream);
+int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **out);
+size_t batch_workspace_bytes(const BatchPlan *plan);
+long long batch_items(const BatchPlan *plan);
+int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream);
+int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream);
+void batch_destroy(BatchPlan *plan);
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                   int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream);
 

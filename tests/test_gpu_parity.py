@@ -204,3 +204,73 @@ def test_detect_rejects_bad_arguments_on_device(lib):
     with pytest.raises(lib.FhtdpError) as e:
         lib.detect_polyline(img, 4, 1, ws=torch.empty(8, dtype=torch.uint8, device="cuda"))
     assert e.value.code == 2
+
+
+# --------------------------------------------------------------------------
+# Batches: one persistent launch over many images of different shapes
+# --------------------------------------------------------------------------
+def _batch_parity(lib, wls):
+    imgs = [to_device(wl.img) for wl in wls]
+    plan = lib.BatchPlan(imgs, [wl.k for wl in wls], [wl.B for wl in wls])
+    plan.run()
+    plan.status()
+    for i, wl in enumerate(wls):
+        x = plan.x[i].cpu().numpy()
+        d = plan.d[i].cpu().numpy()
+        s = plan.score[i].cpu().numpy()[0]
+        check_path(wl.img, wl.k, wl.B, x, d)
+        if wl.img.dtype == np.float32:
+            xo, do, so = oracle.detect_f32(wl.img, wl.k, wl.B)
+            assert np.float32(s) == np.float32(so), i
+        else:
+            xo, do, so = oracle.detect(wl.img, wl.k, wl.B)
+            assert int(s) == int(so), i
+        assert list(x) == list(xo) and list(d) == list(do), i
+    return plan
+
+
+def test_batch_of_mixed_shapes_matches_oracle(lib):
+    shapes = [(256, 256, 4, 8), (512, 300, 8, 4), (1024, 130, 16, 12), (128, 1000, 1, 0),
+              (64, 37, 4, 100), (16, 5, 16, 2), (768, 512, 6, 16), (2048, 77, 32, 3)]
+    wls = [synth.plain_uniform(40 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(shapes)]
+    plan = _batch_parity(lib, wls)
+    # a second run of the same plan gives the same results
+    first = [t.clone() for t in plan.x]
+    plan.run()
+    for a, b in zip(first, plan.x):
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_batch_of_float_images_matches_oracle(lib):
+    wls = [synth.ridge_response(60 + j, 256 * (1 + j % 3), 200 + 96 * j, 2 * (1 + j % 3), 6)
+           for j in range(5)]
+    _batch_parity(lib, wls)
+
+
+def test_batch_mixed_sizes_sample_up_to_128_row_bands(lib):
+    """The mixed-size batch (h 512..4096, w 512..3072, n 32..128, B = n/8):
+    every image through one launch, checked against the oracle."""
+    shapes = [s for s in synth.mixed_batch_shapes(0) if s[0] // s[2] <= 128][:24]
+    wls = [synth.plain_uniform(j, h, w, k, B) for j, (h, w, k, B) in enumerate(shapes)]
+    _batch_parity(lib, wls)
+
+
+def test_batch_run_is_captured_in_a_cuda_graph(lib):
+    import torch
+    wls = [synth.plain_uniform(70 + j, 256, 256 + 64 * j, 4, 8) for j in range(4)]
+    imgs = [to_device(wl.img) for wl in wls]
+    plan = lib.BatchPlan(imgs, [4] * 4, [8] * 4)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        plan.run(stream=stream)
+    for t in plan.x + plan.d + plan.score:
+        t.fill_(-7)
+    g.replay()
+    torch.cuda.synchronize()
+    for i, wl in enumerate(wls):
+        xo, do, so = oracle.detect(wl.img, 4, 8)
+        assert list(plan.x[i].cpu().numpy()) == list(xo)
+        assert list(plan.d[i].cpu().numpy()) == list(do)
+        assert int(plan.score[i].cpu().numpy()[0]) == int(so)
