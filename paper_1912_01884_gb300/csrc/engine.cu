@@ -251,27 +251,27 @@ __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T) {
 // [c0, c1], as keys carrying the argmax.  Blocks of length L = 2B+1 start at
 // c0 - B; M(c0 + (q-1)L + i) = max(S_{q-1}[i], G_q[i-1]) with S the in-block
 // suffix maximum and G the in-block prefix maximum (van Herk / Gil-Werman),
-// or S_{q-1}[0] for i = 0.  Register version: L <= LMAX, every value of the
-// column range read once from shared memory.
-template <int LMAX, typename Key, typename VGet, typename Emit>
+// or S_{q-1}[0] for i = 0.  Register version: L <= LMAX (L == LMAX when
+// kExact), every value of the column range read once from shared memory.
+template <int LMAX, bool kExact, typename Key, typename VGet, typename Emit>
 __device__ __forceinline__ void window_regs(int c0, int c1, int B, Key dead, VGet vkey,
                                             Emit emit) {
-    const int L = 2 * B + 1;
+    const int L = kExact ? LMAX : 2 * B + 1;
     Key S[LMAX], Vb[LMAX];
     const int a0 = c0 - B;
 #pragma unroll
-    for (int i = 0; i < LMAX; ++i) Vb[i] = i < L ? vkey(a0 + i) : dead;
+    for (int i = 0; i < LMAX; ++i) Vb[i] = (kExact || i < L) ? vkey(a0 + i) : dead;
     Key run = dead;
 #pragma unroll
     for (int i = LMAX - 1; i >= 0; --i) {
-        if (i < L) run = kmax(run, Vb[i]);
+        if (kExact || i < L) run = kmax(run, Vb[i]);
         S[i] = run;
     }
     for (int c = c0, base = a0 + L; c <= c1; c += L, base += L) {
         Key G = dead;
 #pragma unroll
         for (int i = 0; i < LMAX; ++i) {
-            if (i < L) {
+            if (kExact || i < L) {
                 const Key v = vkey(base + i);
                 Vb[i] = v;
                 const Key m = i == 0 ? S[0] : kmax(S[i], G);
@@ -282,7 +282,7 @@ __device__ __forceinline__ void window_regs(int c0, int c1, int B, Key dead, VGe
         run = dead;
 #pragma unroll
         for (int i = LMAX - 1; i >= 0; --i) {
-            if (i < L) run = kmax(run, Vb[i]);
+            if (kExact || i < L) run = kmax(run, Vb[i]);
             S[i] = run;
         }
     }
@@ -411,7 +411,8 @@ struct U8Path {
     using KO = KeyOps<int32_t, Key>;
     static constexpr int kRounds = sizeof(Key) == 4 ? 2 : 4;
 
-    __host__ __device__ static int fpitch(int n) { return (kTile + n + 8 + 3) & ~3; }
+    // Strip rows hold T + n + 15 loaded words; the merges read up to T + n + 4.
+    __host__ __device__ static int fpitch(int n) { return (kTile + n + 16 + 3) & ~3; }
     __host__ __device__ static int frows(int n) { return n < 2 ? 2 : n; }
     __host__ __device__ static size_t a_bytes(int n) {
         size_t f = (size_t)frows(n) * fpitch(n) * 4;
@@ -434,24 +435,44 @@ struct U8Path {
         return v;
     }
 
+    // Sixteen pixels [c, c+16) of a row, zero outside [0, w); c is a multiple
+    // of 16; `aligned` says rows start on 16 bytes.
+    __device__ static uint4 load16(const uint8_t *row, int c, int w, bool aligned) {
+        if (aligned && c >= 0 && c + 16 <= w) return __ldg((const uint4 *)(row + c));
+        uint4 v;
+        v.x = load4(row, c, w, false);
+        v.y = load4(row, c + 4, w, false);
+        v.z = load4(row, c + 8, w, false);
+        v.w = load4(row, c + 12, w, false);
+        return v;
+    }
+
     __device__ static void fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0) {
         const int n = im.n, T = kTile, pitch = fpitch(n);
-        const int G = (T + n - 1 + 3) / 4;   // groups of 4 strip columns per row
+        const int G = (T + n - 1 + 15) / 16;   // groups of 16 strip columns per row
         const uint8_t *base = (const uint8_t *)im.img + (size_t)band * n * im.pitch;
-        const bool aligned = ((uintptr_t)im.img % 4 == 0) && (im.pitch % 4 == 0);
-        // Word u of strip row y = pixel (y, x0 + u) | pixel (y, x0 + T - 1 - u) << 16.
+        const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 16 == 0);
+        // Word u of strip row y = pixel (y, x0 + u) | pixel (y, x0 + T - 1 - u) << 16:
+        // the 16 words [u0, u0+16) take bytes 0..15 of the pixels at x0 + u0 and
+        // bytes 15..0 of the pixels at x0 + T - 16 - u0.
 #pragma unroll 4
         for (int idx = threadIdx.x; idx < n * G; idx += kThreads) {
-            const int y = idx / G, u0 = 4 * (idx - y * G);
+            const int y = idx / G, u0 = 16 * (idx - y * G);
             const uint8_t *row = base + (size_t)y * im.pitch;
-            const uint32_t lo4 = load4(row, x0 + u0, im.w, aligned);
-            const uint32_t hi4 = load4(row, x0 + T - 4 - u0, im.w, aligned);
-            uint4 out;
-            out.x = __byte_perm(lo4, hi4, 0x0700) & 0x00ff00ffu;
-            out.y = __byte_perm(lo4, hi4, 0x0601) & 0x00ff00ffu;
-            out.z = __byte_perm(lo4, hi4, 0x0502) & 0x00ff00ffu;
-            out.w = __byte_perm(lo4, hi4, 0x0403) & 0x00ff00ffu;
-            *(uint4 *)&F[(size_t)y * pitch + u0] = out;
+            const uint4 lo = load16(row, x0 + u0, im.w, aligned);
+            const uint4 hi = load16(row, x0 + T - 16 - u0, im.w, aligned);
+            const uint32_t los[4] = {lo.x, lo.y, lo.z, lo.w};
+            const uint32_t his[4] = {hi.w, hi.z, hi.y, hi.x};
+            uint32_t *dst = &F[(size_t)y * pitch + u0];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                uint4 out;
+                out.x = __byte_perm(los[g], his[g], 0x0700) & 0x00ff00ffu;
+                out.y = __byte_perm(los[g], his[g], 0x0601) & 0x00ff00ffu;
+                out.z = __byte_perm(los[g], his[g], 0x0502) & 0x00ff00ffu;
+                out.w = __byte_perm(los[g], his[g], 0x0403) & 0x00ff00ffu;
+                *(uint4 *)&dst[4 * g] = out;
+            }
         }
         __syncthreads();
         fht_levels<uint32_t>(F, pitch, n, im.log2n, T);
@@ -478,7 +499,7 @@ struct U8Path {
                 *(int4 *)&Vn[row * T + u0] = make_int4(dead, dead, dead, dead);
             }
         }
-#pragma unroll 2
+#pragma unroll 4
         for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
             const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
             const uint4 hw = *(const uint4 *)&Hc[s * T + u0];
@@ -499,15 +520,17 @@ struct U8Path {
             for (int j = 0; j < 4; ++j) {
                 const int x = xp + j;
                 const bool ok = x < im.w && x + s < im.w;
+                // A window maximum below zero marks a dead continuation
+                // (uint8 sums are never negative).
                 const int m = mps[j];
                 vp[j] = !ok ? dead : last ? (int)(hws[j] & 0xffffu)
-                                          : (m == dead ? dead : (int)(hws[j] & 0xffffu) + m);
+                                          : (m < 0 ? dead : (int)(hws[j] & 0xffffu) + m);
                 // "-" half of word j: column x0 + T - 1 - u0 - j, displacement -s.
                 const int xm = x0 + T - 1 - u0 - j;
                 const bool okm = s > 0 && xm < im.w && xm - s >= 0;
                 const int mmv = mms[3 - j];
                 vm[j] = !okm ? dead : last ? (int)(hws[j] >> 16)
-                                           : (mmv == dead ? dead : (int)(hws[j] >> 16) + mmv);
+                                           : (mmv < 0 ? dead : (int)(hws[j] >> 16) + mmv);
             }
             if (band == 0) {
 #pragma unroll
@@ -523,6 +546,15 @@ struct U8Path {
                     }
                 }
             } else {
+                if constexpr (sizeof(Key) == 4) {
+                    // Store window keys: value << 9 | (511 - (e + n - 1)); dead
+                    // stays INT32_MIN.
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        vp[j] = vp[j] == dead ? dead : KO::make(vp[j], s + n - 1);
+                        vm[j] = vm[j] == dead ? dead : KO::make(vm[j], n - 1 - s);
+                    }
+                }
                 *(int4 *)&Vn[(s + n - 1 + kPad) * T + u0] = make_int4(vp[0], vp[1], vp[2], vp[3]);
                 if (s > 0)
                     *(int4 *)&Vn[(n - 1 - s + kPad) * T + (T - 4 - u0)] =
@@ -536,7 +568,7 @@ struct U8Path {
                                    const LaunchArgs &args) {
         const int n = im.n, T = kTile, D = 2 * n - 1;
         const int x0 = tile * T;
-        uint32_t *F = (uint32_t *)smem;
+        uint32_t *F = (uint32_t *)smem;  // the strip, then V
         int32_t *Vn = (int32_t *)smem;
         uint32_t *Hc = (uint32_t *)(smem + a_bytes(n));
         fht(F, Hc, im, band, x0);
@@ -556,29 +588,48 @@ struct U8Path {
         const int lo = -(n - 1), hi = n - 1;
         uint8_t *bp = im.bp + (size_t)band * D * im.w;
         const int32_t *col = Vn + u;
-        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
-        if (sizeof(Key) == 4 && B <= kFastB) {
-            // V rows [lo - kPad, hi + kPad] exist (dead outside [lo, hi]);
-            // the register window never reads below c0 - B >= lo - kPad, and
-            // reads above hi are replaced by dead keys.
-            auto vkey = [&](int e) -> Key {
-                if (e > hi) return KO::dead();
-                const int v = col[(e + n - 1 + kPad) * T];
-                return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
-            };
-            const int c0 = lo + (qd * D) / kQ, c1 = lo + ((qd + 1) * D) / kQ - 1;
-            if (c0 <= c1 && x < im.w) {
-                if (B <= 4)
-                    window_regs<9, Key>(c0, c1, B, KO::dead(), vkey, emit);
-                else if (B <= 8)
-                    window_regs<17, Key>(c0, c1, B, KO::dead(), vkey, emit);
-                else
-                    window_regs<33, Key>(c0, c1, B, KO::dead(), vkey, emit);
+        if constexpr (sizeof(Key) == 4) {
+            if (B <= kFastB) {
+                // Shared memory holds keys.  V rows [lo - kPad, hi + kPad] exist
+                // (dead outside [lo, hi]); the register window never reads
+                // below c0 - B >= lo - kPad, and reads above hi are dead.
+                const int32_t *kcol = col + (n - 1 + kPad) * T;
+                auto vkey = [&](int e) -> Key { return e > hi ? KO::dead() : kcol[e * T]; };
+                // M(x, c) = key >> 9 (negative when dead), bp = its index.
+                Acc *mcol = mnext + (size_t)(n - 1) * im.mpitch + kMOff + x;
+                uint8_t *bcol = bp + (size_t)(n - 1) * im.w + x;
+                const long long mstep = im.mpitch - 1, bstep = im.w;
+                auto emit = [&](int c, Key mk) {
+                    mcol[c * mstep] = mk >> 9;
+                    bcol[c * bstep] = (uint8_t)(~mk & 511);
+                };
+                const int c0 = lo + (qd * D) / kQ, c1 = lo + ((qd + 1) * D) / kQ - 1;
+                if (c0 <= c1 && x < im.w) {
+                    const Key dk = KO::dead();
+                    switch (B) {
+                        case 4: window_regs<9, true, Key>(c0, c1, B, dk, vkey, emit); break;
+                        case 8: window_regs<17, true, Key>(c0, c1, B, dk, vkey, emit); break;
+                        case 12: window_regs<25, true, Key>(c0, c1, B, dk, vkey, emit); break;
+                        case 16: window_regs<33, true, Key>(c0, c1, B, dk, vkey, emit); break;
+                        default:
+                            if (B < 4)
+                                window_regs<9, false, Key>(c0, c1, B, dk, vkey, emit);
+                            else if (B < 8)
+                                window_regs<17, false, Key>(c0, c1, B, dk, vkey, emit);
+                            else
+                                window_regs<33, false, Key>(c0, c1, B, dk, vkey, emit);
+                    }
+                }
+                publish(im, band, tile);
+                return;
             }
-        } else {
+        }
+        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
+        {
             auto vkey = [&](int e) -> Key {
                 if (e < lo || e > hi) return KO::dead();
                 const int v = col[(e + n - 1 + kPad) * T];
+                if constexpr (sizeof(Key) == 4) return v;   // stored as keys
                 return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
             };
             Key *S = (Key *)Hc;
