@@ -206,10 +206,10 @@ __device__ __forceinline__ void merge4(const uint4 &a4, const uint4 &b0, const u
 }
 
 template <typename W>
-__device__ void fht_levels(W *F, int pitch, int n, int log2n, int T) {
+__device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first = 1) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = kThreads / 32;
-    for (int l = 1; l <= log2n; ++l) {
+    for (int l = first; l <= log2n; ++l) {
         const int m = 1 << l, half = m >> 1;
         const int width = T + n - m;
         for (int p = warp; p < n / 2; p += nwarps) {
@@ -244,6 +244,117 @@ __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T) {
         }
         __syncthreads();
     }
+}
+
+// Two dyadic levels in one shared-memory pass: four consecutive sub-bands
+// J0..J3 of m rows, all at shift q, give the shifts 4q..4q+3 of the merged
+// sub-band of 4m rows.  With A = (J0, J1) and B = (J2, J3) merged first,
+//   out(u, 4q+0) = [J0(u) + J1(u+q)]   + [J2(u+2q)   + J3(u+3q)]
+//   out(u, 4q+1) = [J0(u) + J1(u+q)]   + [J2(u+2q+1) + J3(u+3q+1)]
+//   out(u, 4q+2) = [J0(u) + J1(u+q+1)] + [J2(u+2q+1) + J3(u+3q+2)]
+//   out(u, 4q+3) = [J0(u) + J1(u+q+1)] + [J2(u+2q+2) + J3(u+3q+3)]
+// (the same summation tree as two radix-2 levels).  Shift 4q+r goes to the
+// row of J_{brev2(r)} at the same in-sub-band slot, so the pass is in place
+// under the same left-to-right sweep rule.  O1..O3 are the word offsets of
+// u+q, u+2q, u+3q inside their 16-byte-aligned loads.
+template <typename W, int O1, int O2, int O3>
+__device__ __forceinline__ void merge4x4(const uint4 &j0, const uint4 *j1, const uint4 *j2,
+                                         const uint4 *j3, uint4 *out) {
+    const W a[4] = {from_bits<W>(j0.x), from_bits<W>(j0.y), from_bits<W>(j0.z),
+                    from_bits<W>(j0.w)};
+    W b1[8], b2[8], b3[12];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        b1[4 * k + 0] = from_bits<W>(j1[k].x);
+        b1[4 * k + 1] = from_bits<W>(j1[k].y);
+        b1[4 * k + 2] = from_bits<W>(j1[k].z);
+        b1[4 * k + 3] = from_bits<W>(j1[k].w);
+        b2[4 * k + 0] = from_bits<W>(j2[k].x);
+        b2[4 * k + 1] = from_bits<W>(j2[k].y);
+        b2[4 * k + 2] = from_bits<W>(j2[k].z);
+        b2[4 * k + 3] = from_bits<W>(j2[k].w);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        b3[4 * k + 0] = from_bits<W>(j3[k].x);
+        b3[4 * k + 1] = from_bits<W>(j3[k].y);
+        b3[4 * k + 2] = from_bits<W>(j3[k].z);
+        b3[4 * k + 3] = from_bits<W>(j3[k].w);
+    }
+    uint32_t o[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const W A0 = a[t] + b1[O1 + t], A1 = a[t] + b1[O1 + t + 1];
+        const W B0 = b2[O2 + t] + b3[O3 + t];
+        const W B1 = b2[O2 + t + 1] + b3[O3 + t + 1];
+        const W B2 = b2[O2 + t + 1] + b3[O3 + t + 2];
+        const W B3 = b2[O2 + t + 2] + b3[O3 + t + 3];
+        o[0][t] = to_bits(A0 + B0);
+        o[1][t] = to_bits(A0 + B1);
+        o[2][t] = to_bits(A1 + B2);
+        o[3][t] = to_bits(A1 + B3);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) out[r] = make_uint4(o[r][0], o[r][1], o[r][2], o[r][3]);
+}
+
+// Levels l+1 and l+2 (sub-bands of m = 2^l rows merged into 4m rows).
+template <typename W>
+__device__ void fht_radix4(W *F, int pitch, int n, int l, int T) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = kThreads / 32;
+    const int m = 1 << l;
+    const int width = T + n - 4 * m;
+    for (int p = warp; p < n / 4; p += nwarps) {
+        const int g4 = p >> l, r = p & (m - 1);
+        const int q = brev(r, l);
+        const int o = q & 3;   // warp-uniform
+        W *J[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) J[t] = F + (size_t)((4 * g4 + t) * m + r) * pitch;
+        const W *B1 = J[1] + (q - (q & 3));
+        const W *B2 = J[2] + (2 * q - ((2 * q) & 3));
+        const W *B3 = J[3] + (3 * q - ((3 * q) & 3));
+        for (int u0 = 0; u0 < width; u0 += 128) {
+            const int u = u0 + 4 * lane;
+            const bool live = u < width;
+            uint4 out[4];
+            if (live) {
+                const uint4 j0 = *(const uint4 *)&J[0][u];
+                const uint4 j1[2] = {*(const uint4 *)&B1[u], *(const uint4 *)&B1[u + 4]};
+                const uint4 j2[2] = {*(const uint4 *)&B2[u], *(const uint4 *)&B2[u + 4]};
+                const uint4 j3[3] = {*(const uint4 *)&B3[u], *(const uint4 *)&B3[u + 4],
+                                     *(const uint4 *)&B3[u + 8]};
+                switch (o) {
+                    case 0: merge4x4<W, 0, 0, 0>(j0, j1, j2, j3, out); break;
+                    case 1: merge4x4<W, 1, 2, 3>(j0, j1, j2, j3, out); break;
+                    case 2: merge4x4<W, 2, 0, 2>(j0, j1, j2, j3, out); break;
+                    default: merge4x4<W, 3, 2, 1>(j0, j1, j2, j3, out); break;
+                }
+            }
+            __syncwarp();
+            if (live) {
+                *(uint4 *)&J[0][u] = out[0];   // shift 4q+0 -> row of J0
+                *(uint4 *)&J[2][u] = out[1];   // shift 4q+1 -> row of J2 (brev2(1) = 2)
+                *(uint4 *)&J[1][u] = out[2];   // shift 4q+2 -> row of J1
+                *(uint4 *)&J[3][u] = out[3];   // shift 4q+3 -> row of J3
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// All levels from `first` (sub-bands of 2^(first-1) rows already merged),
+// two at a time where possible.
+template <typename W>
+__device__ void fht_merge(W *F, int pitch, int n, int log2n, int T, int first) {
+    int l = first - 1;   // current sub-band size 2^l
+    while (l + 2 <= log2n) {
+        fht_radix4<W>(F, pitch, n, l, T);
+        l += 2;
+    }
+    if (l < log2n) fht_levels<W>(F, pitch, n, log2n, T, l + 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -447,8 +558,10 @@ struct U8Path {
         return v;
     }
 
-    __device__ static void fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0) {
-        const int n = im.n, T = kTile, pitch = fpitch(n);
+    // The packed strip, word u of row y = pixel (y, x0 + u) | pixel
+    // (y, x0 + T - 1 - u) << 16 (bands of 1 or 2 rows).
+    __device__ static void load_strip(uint32_t *F, int pitch, const ImgDesc &im, int band, int x0) {
+        const int n = im.n, T = kTile;
         const int G = (T + n - 1 + 15) / 16;   // groups of 16 strip columns per row
         const uint8_t *base = (const uint8_t *)im.img + (size_t)band * n * im.pitch;
         const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 16 == 0);
@@ -475,7 +588,100 @@ struct U8Path {
             }
         }
         __syncthreads();
-        fht_levels<uint32_t>(F, pitch, n, im.log2n, T);
+    }
+
+    // Eight pixels [c, c+8) of a row, zero outside [0, w); c is a multiple of
+    // 8; `aligned` says rows start on 8 bytes.
+    __device__ static uint2 load8(const uint8_t *row, int c, int w, bool aligned) {
+        if (aligned && c >= 0 && c + 8 <= w) return __ldg((const uint2 *)(row + c));
+        return make_uint2(load4(row, c, w, false), load4(row, c + 4, w, false));
+    }
+
+    // Packed strip word of column u: pixel x0 + u | pixel x0 + T - 1 - u << 16.
+    __device__ static uint32_t strip_word(const uint8_t *row, int x0, int u, int w) {
+        return pix_u8(row, x0 + u, w) | (pix_u8(row, x0 + kTile - 1 - u, w) << 16);
+    }
+
+    // Levels 1 and 2 in registers, straight from the pixels: a thread takes 4
+    // band rows (a 4-row sub-band g) and 8 strip columns [8c, 8c+8) plus the 3
+    // columns after them (from the next lane, which holds chunk c+1), and
+    // stores the 4 shifts of the sub-band to rows 4g + brev2(s).
+    __device__ static void fht_regs(uint32_t *F, int pitch, const ImgDesc &im, int band, int x0) {
+        const int n = im.n, T = kTile;
+        const int C8 = (T + n - 4 + 7) / 8;   // chunks covering the level-2 width
+        const int tasks = (n / 4) * C8;
+        const uint8_t *base = (const uint8_t *)im.img + (size_t)band * n * im.pitch;
+        const bool aligned = ((uintptr_t)im.img % 8 == 0) && (im.pitch % 8 == 0);
+        const int lane = threadIdx.x & 31;
+        for (int t0 = 0; t0 < tasks; t0 += kThreads) {   // uniform: every lane shuffles
+            const int t = t0 + threadIdx.x;
+            const bool live = t < tasks;
+            const int g = live ? t / C8 : 0, c = live ? t - g * C8 : 0;
+            uint32_t P[4][11];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint8_t *row = base + (size_t)(4 * g + r) * im.pitch;
+                const uint2 lo = live ? load8(row, x0 + 8 * c, im.w, aligned) : make_uint2(0, 0);
+                const uint2 hi =
+                    live ? load8(row, x0 + T - 8 - 8 * c, im.w, aligned) : make_uint2(0, 0);
+                const uint32_t los[2] = {lo.x, lo.y}, his[2] = {hi.y, hi.x};
+#pragma unroll
+                for (int gg = 0; gg < 2; ++gg) {
+                    P[r][4 * gg + 0] = __byte_perm(los[gg], his[gg], 0x0700) & 0x00ff00ffu;
+                    P[r][4 * gg + 1] = __byte_perm(los[gg], his[gg], 0x0601) & 0x00ff00ffu;
+                    P[r][4 * gg + 2] = __byte_perm(los[gg], his[gg], 0x0502) & 0x00ff00ffu;
+                    P[r][4 * gg + 3] = __byte_perm(los[gg], his[gg], 0x0403) & 0x00ff00ffu;
+                }
+#pragma unroll
+                for (int j = 0; j < 3; ++j) P[r][8 + j] = __shfl_down_sync(0xffffffffu, P[r][j], 1);
+                // The next chunk of this sub-band is in the next warp: read it.
+                if (live && lane == 31 && c + 1 < C8)
+                    for (int j = 0; j < 3; ++j) P[r][8 + j] = strip_word(row, x0, 8 * c + 8 + j, im.w);
+            }
+            // Level 1: rows (0,1) -> A_s', rows (2,3) -> B_s', s' in {0,1}.
+            uint32_t A0[8], A1[8], B0[10], B1[10];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                A0[u] = P[0][u] + P[1][u];
+                A1[u] = P[0][u] + P[1][u + 1];
+            }
+#pragma unroll
+            for (int v = 0; v < 10; ++v) {
+                B0[v] = P[2][v] + P[3][v];
+                B1[v] = P[2][v] + P[3][v + 1];
+            }
+            if (live) {
+                // Level 2: shift s -> A_{s>>1}(u) + B_{s>>1}(u + ceil(s/2)).
+                uint32_t *row0 = F + (size_t)(4 * g) * pitch + 8 * c;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int u = 4 * h;
+                    *(uint4 *)&row0[u] = make_uint4(A0[u] + B0[u], A0[u + 1] + B0[u + 1],
+                                                    A0[u + 2] + B0[u + 2], A0[u + 3] + B0[u + 3]);
+                    *(uint4 *)&row0[2 * pitch + u] =
+                        make_uint4(A0[u] + B0[u + 1], A0[u + 1] + B0[u + 2],
+                                   A0[u + 2] + B0[u + 3], A0[u + 3] + B0[u + 4]);
+                    *(uint4 *)&row0[pitch + u] =
+                        make_uint4(A1[u] + B1[u + 1], A1[u + 1] + B1[u + 2],
+                                   A1[u + 2] + B1[u + 3], A1[u + 3] + B1[u + 4]);
+                    *(uint4 *)&row0[3 * pitch + u] =
+                        make_uint4(A1[u] + B1[u + 2], A1[u + 1] + B1[u + 3],
+                                   A1[u + 2] + B1[u + 4], A1[u + 3] + B1[u + 5]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    __device__ static void fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0) {
+        const int n = im.n, T = kTile, pitch = fpitch(n);
+        if (n >= 4) {
+            fht_regs(F, pitch, im, band, x0);
+            fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3);
+        } else {
+            load_strip(F, pitch, im, band, x0);
+            fht_levels<uint32_t>(F, pitch, n, im.log2n, T);
+        }
         // Compact: Hc[s][u] = packed Hough word of shift s at tile column u.
         for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
             const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
