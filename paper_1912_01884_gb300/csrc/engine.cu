@@ -32,6 +32,9 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "engine.cuh"
 
 namespace fhtdp {
@@ -46,6 +49,8 @@ constexpr int kPad = 16;               // dead rows around V (uint8 path)
 constexpr int kFastB = 16;             // largest bend kept entirely in registers
 
 struct ImgDesc {
+    CUtensorMap tmap;         // 2-D map of the image (uint8 images), box 128 x n
+    int use_tma;              // strip loads through tmap
     const void *img;
     long long pitch;          // row stride in elements
     int h, w, k, n, log2n, B, tiles;
@@ -163,6 +168,80 @@ __device__ bool wait_flag(const int *flag, const Ctl *ctl, long long limit) {
         __nanosleep(100);
     }
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-memory-access (TMA) copies into shared memory, completed on an
+// mbarrier.  Every wait is bounded like the flag waits.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+            smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+// Waits for the phase `parity` of `bar` to complete; false after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// 2-D tile (x, y) of a tensor map into shared memory.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+// Per-CTA state of the asynchronous copies and of the queue: the next work
+// item is taken before the current one finishes, so that its band strip can
+// be copied while the current item computes its window maxima.
+struct NextItem {
+    long long item;
+    int prefetched;   // its strip copy has been issued on the strip barrier
+};
+struct Pipe {
+    uint64_t *bar;        // strip barrier
+    uint32_t phase;       // parity of its next completion
+    NextItem *next;       // shared: the CTA's next item
+};
+
+__device__ __forceinline__ void decode_item(const LaunchArgs &args, long long item,
+                                            const ImgDesc **imp, int *band, int *tile) {
+    if (args.many) {
+        const Item it = args.order[item];
+        *imp = &args.many[it.image];
+        *band = it.band;
+        *tile = it.tile;
+    } else {
+        *imp = &args.one;
+        *band = args.one.k - 1 - (int)(item / args.one.tiles);
+        *tile = (int)(item % args.one.tiles);
+    }
 }
 
 __device__ __forceinline__ uint32_t pix_u8(const uint8_t *row, int col, int w) {
@@ -458,8 +537,9 @@ __device__ void readback(const ImgDesc &im, const LaunchArgs &args) {
 
 // Band 0: fold this tile's best (value, x, d) key into the image's and, on
 // the image's last band-0 tile, read the polyline back.
-template <typename Acc>
-__device__ void finish_band0(unsigned long long best, const ImgDesc &im, const LaunchArgs &args) {
+template <typename Acc, typename Hook>
+__device__ void finish_band0(unsigned long long best, const ImgDesc &im, const LaunchArgs &args,
+                             Hook hook) {
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
         best = best > other ? best : other;
@@ -467,6 +547,7 @@ __device__ void finish_band0(unsigned long long best, const ImgDesc &im, const L
     if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
     __syncthreads();
     if (threadIdx.x == 0) {
+        hook();
         __threadfence();
         int prev = atomicAdd(im.done, 1);
         if (prev == im.tiles - 1) readback<Acc>(im, args);
@@ -528,14 +609,18 @@ struct U8Path {
     __host__ __device__ static size_t a_bytes(int n) {
         size_t f = (size_t)frows(n) * fpitch(n) * 4;
         size_t v = (size_t)(2 * n - 1 + 2 * kPad) * kTile * 4;
-        return ((f > v ? f : v) + 15) / 16 * 16;
+        return ((f > v ? f : v) + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
     }
     __host__ __device__ static size_t hc_bytes(int n) {
         size_t hc = (size_t)n * kTile * 4;
         size_t s = (size_t)((2 * n - 1 + kRounds - 1) / kRounds) * kTile * sizeof(Key);
         return hc > s ? hc : s;
     }
-    static size_t smem_bytes(int n) { return a_bytes(n) + hc_bytes(n); }
+    // Hc sits at a fixed offset (the largest band height's region A), so that
+    // the strip of a next item with another band height can be staged there
+    // while the current item still uses region A.
+    __host__ __device__ static size_t hc_offset() { return a_bytes(kMaxBandFused); }
+    static size_t smem_bytes(int) { return hc_offset() + hc_bytes(kMaxBandFused); }
 
     // Four pixels [c, c+4) of a row as one little-endian word, zero outside
     // [0, w).  c is a multiple of 4; `aligned` says rows start on 4 bytes.
@@ -597,21 +682,48 @@ struct U8Path {
         return make_uint2(load4(row, c, w, false), load4(row, c + 4, w, false));
     }
 
-    // Packed strip word of column u: pixel x0 + u | pixel x0 + T - 1 - u << 16.
-    __device__ static uint32_t strip_word(const uint8_t *row, int x0, int u, int w) {
-        return pix_u8(row, x0 + u, w) | (pix_u8(row, x0 + kTile - 1 - u, w) << 16);
-    }
+    // Pixels of the band straight from global memory.
+    struct GlobalPixels {
+        const uint8_t *base;
+        long long pitch;
+        int w;
+        bool aligned;
+        __device__ uint2 load8(int row, int X) const {
+            return U8Path::load8(base + (size_t)row * pitch, X, w, aligned);
+        }
+        __device__ uint32_t byte(int row, int X) const {
+            return pix_u8(base + (size_t)row * pitch, X, w);
+        }
+    };
+    // Pixels of the band from the strip staged by TMA: box b holds the strip
+    // columns [xs + 128b, xs + 128b + 128) of the n band rows, 128 bytes per
+    // row; columns outside the image were filled with zeros.  Reads outside
+    // the staged columns (they only feed columns past the valid width) are
+    // clamped into it.
+    struct StagedPixels {
+        const uint8_t *st;
+        int n, xs, last;   // last = staged bytes per row - 8
+        __device__ int clamp(int sc) const { return sc < 0 ? 0 : (sc > last ? last : sc); }
+        __device__ uint2 load8(int row, int X) const {
+            const int sc = clamp(X - xs);
+            return *(const uint2 *)(st + (size_t)(sc >> 7) * n * 128 + row * 128 + (sc & 127));
+        }
+        __device__ uint32_t byte(int row, int X) const {
+            const int sc = clamp(X - xs);
+            return st[(size_t)(sc >> 7) * n * 128 + row * 128 + (sc & 127)];
+        }
+    };
 
     // Levels 1 and 2 in registers, straight from the pixels: a thread takes 4
     // band rows (a 4-row sub-band g) and 8 strip columns [8c, 8c+8) plus the 3
     // columns after them (from the next lane, which holds chunk c+1), and
     // stores the 4 shifts of the sub-band to rows 4g + brev2(s).
-    __device__ static void fht_regs(uint32_t *F, int pitch, const ImgDesc &im, int band, int x0) {
+    template <typename Src>
+    __device__ static void fht_regs(uint32_t *F, int pitch, const ImgDesc &im, const Src &src,
+                                    int x0) {
         const int n = im.n, T = kTile;
         const int C8 = (T + n - 4 + 7) / 8;   // chunks covering the level-2 width
         const int tasks = (n / 4) * C8;
-        const uint8_t *base = (const uint8_t *)im.img + (size_t)band * n * im.pitch;
-        const bool aligned = ((uintptr_t)im.img % 8 == 0) && (im.pitch % 8 == 0);
         const int lane = threadIdx.x & 31;
         for (int t0 = 0; t0 < tasks; t0 += kThreads) {   // uniform: every lane shuffles
             const int t = t0 + threadIdx.x;
@@ -620,10 +732,9 @@ struct U8Path {
             uint32_t P[4][11];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const uint8_t *row = base + (size_t)(4 * g + r) * im.pitch;
-                const uint2 lo = live ? load8(row, x0 + 8 * c, im.w, aligned) : make_uint2(0, 0);
-                const uint2 hi =
-                    live ? load8(row, x0 + T - 8 - 8 * c, im.w, aligned) : make_uint2(0, 0);
+                const int y = 4 * g + r;
+                const uint2 lo = live ? src.load8(y, x0 + 8 * c) : make_uint2(0, 0);
+                const uint2 hi = live ? src.load8(y, x0 + T - 8 - 8 * c) : make_uint2(0, 0);
                 const uint32_t los[2] = {lo.x, lo.y}, his[2] = {hi.y, hi.x};
 #pragma unroll
                 for (int gg = 0; gg < 2; ++gg) {
@@ -636,7 +747,10 @@ struct U8Path {
                 for (int j = 0; j < 3; ++j) P[r][8 + j] = __shfl_down_sync(0xffffffffu, P[r][j], 1);
                 // The next chunk of this sub-band is in the next warp: read it.
                 if (live && lane == 31 && c + 1 < C8)
-                    for (int j = 0; j < 3; ++j) P[r][8 + j] = strip_word(row, x0, 8 * c + 8 + j, im.w);
+                    for (int j = 0; j < 3; ++j) {
+                        const int u = 8 * c + 8 + j;
+                        P[r][8 + j] = src.byte(y, x0 + u) | (src.byte(y, x0 + T - 1 - u) << 16);
+                    }
             }
             // Level 1: rows (0,1) -> A_s', rows (2,3) -> B_s', s' in {0,1}.
             uint32_t A0[8], A1[8], B0[10], B1[10];
@@ -673,10 +787,48 @@ struct U8Path {
         __syncthreads();
     }
 
-    __device__ static void fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0) {
+    // Staged strip: columns [x0 - noff, x0 + T + noff) in boxes of 128.
+    __host__ __device__ static int strip_off(int n) { return (n + 15) & ~15; }
+    __host__ __device__ static int strip_boxes(int n) {
+        return (kTile + 2 * strip_off(n) + 127) / 128;
+    }
+
+    __host__ __device__ static bool strip_by_tma(const ImgDesc &im) {
+        return im.use_tma && im.n >= 4;
+    }
+    // One thread: the band strip of (band, tile) through TMA into `st` (the
+    // Hc region, free until the compaction), zero-filled outside the image.
+    __device__ static void issue_strip(const ImgDesc &im, int band, int tile, void *st,
+                                       Pipe &pipe) {
+        const int n = im.n, xs = tile * kTile - strip_off(n), nb = strip_boxes(n);
+        fence_proxy_async_smem();
+        mbar_expect_tx(pipe.bar, (uint32_t)(nb * n * 128));
+        for (int b = 0; b < nb; ++b)
+            tma_load_2d((uint8_t *)st + (size_t)b * n * 128, &im.tmap, xs + 128 * b, band * n,
+                        pipe.bar);
+    }
+
+    // Returns false if the strip copy did not complete in time.
+    __device__ static bool fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0,
+                               Pipe &pipe, bool prefetched, const LaunchArgs &args) {
         const int n = im.n, T = kTile, pitch = fpitch(n);
-        if (n >= 4) {
-            fht_regs(F, pitch, im, band, x0);
+        if (strip_by_tma(im)) {
+            const int xs = x0 - strip_off(n), nb = strip_boxes(n);
+            uint8_t *st = (uint8_t *)Hc;
+            if (threadIdx.x == 0 && !prefetched) issue_strip(im, band, x0 / kTile, st, pipe);
+            const bool ok = mbar_wait(pipe.bar, pipe.phase, args.wait_cycles);
+            pipe.phase ^= 1u;
+            if (!ok) {
+                if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                return false;
+            }
+            fht_regs(F, pitch, im, StagedPixels{st, n, xs, nb * 128 - 8}, x0);
+            fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3);
+        } else if (n >= 4) {
+            const GlobalPixels src{(const uint8_t *)im.img + (size_t)band * n * im.pitch,
+                                   im.pitch, im.w,
+                                   ((uintptr_t)im.img % 8 == 0) && (im.pitch % 8 == 0)};
+            fht_regs(F, pitch, im, src, x0);
             fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3);
         } else {
             load_strip(F, pitch, im, band, x0);
@@ -688,12 +840,13 @@ struct U8Path {
             *(uint4 *)&Hc[s * T + u0] = *(const uint4 *)&F[(size_t)brev(s, im.log2n) * pitch + u0];
         }
         __syncthreads();
+        return true;
     }
 
     // V rows: V(e) of tile column u at Vn[(e + n - 1 + kPad) * T + u].
     __device__ static unsigned long long form_v(int32_t *Vn, const uint32_t *Hc,
-                                                const ImgDesc &im, int band, const Acc *mprev,
-                                                int x0) {
+                                                const ImgDesc &im, int band, int x0,
+                                                const int32_t *mprev) {
         const int n = im.n, T = kTile, D = 2 * n - 1;
         const bool last = band == im.k - 1;
         const Acc dead = Dead<Acc>::value();
@@ -770,23 +923,44 @@ struct U8Path {
         return best;
     }
 
-    __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
-                                   const LaunchArgs &args) {
+    // Thread 0: takes the next work item and, when its strip can go to Hc
+    // now (Hc is not needed any more by this item), issues the strip copy.
+    __device__ static void take_next(const LaunchArgs &args, Pipe &pipe, void *Hc, bool hc_free) {
+        const long long nx = atomicAdd(&args.ctl->queue, 1);
+        int pf = 0;
+        if (hc_free && nx < args.items) {
+            const ImgDesc *nim;
+            int nband, ntile;
+            decode_item(args, nx, &nim, &nband, &ntile);
+            if (strip_by_tma(*nim)) {
+                issue_strip(*nim, nband, ntile, Hc, pipe);
+                pf = 1;
+            }
+        }
+        pipe.next->item = nx;
+        pipe.next->prefetched = pf;
+    }
+
+    __device__ static bool process(const ImgDesc &im, int band, int tile, unsigned char *smem,
+                                   const LaunchArgs &args, Pipe &pipe, bool prefetched) {
         const int n = im.n, T = kTile, D = 2 * n - 1;
         const int x0 = tile * T;
         uint32_t *F = (uint32_t *)smem;  // the strip, then V
         int32_t *Vn = (int32_t *)smem;
-        uint32_t *Hc = (uint32_t *)(smem + a_bytes(n));
-        fht(F, Hc, im, band, x0);
+        uint32_t *Hc = (uint32_t *)(smem + hc_offset());
+        if (!fht(F, Hc, im, band, x0, pipe, prefetched, args)) return false;
         wait_deps(im, band, tile, args);
         const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
         Acc *mnext = (Acc *)im.mbuf[band & 1];
-        const unsigned long long best = form_v(Vn, Hc, im, band, mprev, x0);
+        const unsigned long long best = form_v(Vn, Hc, im, band, x0, mprev);
+        const bool fast = sizeof(Key) == 4 && im.B <= kFastB;
         if (band == 0) {
-            finish_band0<Acc>(best, im, args);
-            return;
+            finish_band0<Acc>(best, im, args, [&] { take_next(args, pipe, Hc, true); });
+            return true;
         }
         __syncthreads();
+        // Hc is free from here on unless the window needs it for S.
+        if (threadIdx.x == 0) take_next(args, pipe, Hc, fast);
 
         const int u = threadIdx.x % T, qd = threadIdx.x / T;
         const int x = x0 + u;
@@ -827,7 +1001,7 @@ struct U8Path {
                     }
                 }
                 publish(im, band, tile);
-                return;
+                return true;
             }
         }
         auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
@@ -854,6 +1028,7 @@ struct U8Path {
             }
         }
         publish(im, band, tile);
+        return true;
     }
 };
 
@@ -968,8 +1143,8 @@ struct WidePath {
         return best;
     }
 
-    __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
-                                   const LaunchArgs &args) {
+    __device__ static bool process(const ImgDesc &im, int band, int tile, unsigned char *smem,
+                                   const LaunchArgs &args, Pipe &pipe, bool) {
         const int n = im.n, T = kTile, D = 2 * n - 1;
         const int pitch = fpitch(n);
         const int x0 = tile * T;
@@ -980,9 +1155,13 @@ struct WidePath {
         const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
         Acc *mnext = (Acc *)im.mbuf[band & 1];
         const unsigned long long best = form_v(F, Hp, im, band, mprev, x0);
+        auto take_next = [&] {
+            pipe.next->item = atomicAdd(&args.ctl->queue, 1);
+            pipe.next->prefetched = 0;
+        };
         if (band == 0) {
-            finish_band0<Acc>(best, im, args);
-            return;
+            finish_band0<Acc>(best, im, args, take_next);
+            return true;
         }
         __syncthreads();
 
@@ -1016,6 +1195,8 @@ struct WidePath {
             __syncthreads();
         }
         publish(im, band, tile);
+        if (threadIdx.x == 0) take_next();
+        return true;
     }
 };
 
@@ -1029,28 +1210,29 @@ struct PathOf<uint8_t, int32_t, Key> {
 };
 
 template <typename In, typename Acc, typename Key>
-__global__ void __launch_bounds__(kThreads, 1) engine_kernel(LaunchArgs args) {
+__global__ void __launch_bounds__(kThreads, 1)
+    engine_kernel(const __grid_constant__ LaunchArgs args) {
     using P = typename PathOf<In, Acc, Key>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ long long s_item;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ NextItem s_next;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_next.item = atomicAdd(&args.ctl->queue, 1);
+        s_next.prefetched = 0;
+    }
+    __syncthreads();
+    Pipe pipe{&s_bar, 0u, &s_next};
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&args.ctl->queue, 1);
-        __syncthreads();
-        const long long item = s_item;
-        __syncthreads();
+        const long long item = s_next.item;
+        const bool prefetched = s_next.prefetched != 0;
+        __syncthreads();   // thread 0 rewrites s_next inside process
         if (item >= args.items) break;
-        const ImgDesc *imp = &args.one;
+        const ImgDesc *imp;
         int band, tile;
-        if (args.many) {
-            const Item it = args.order[item];
-            imp = &args.many[it.image];
-            band = it.band;
-            tile = it.tile;
-        } else {
-            band = imp->k - 1 - (int)(item / imp->tiles);
-            tile = (int)(item % imp->tiles);
-        }
-        P::process(*imp, band, tile, smem_raw, args);
+        decode_item(args, item, &imp, &band, &tile);
+        if (!P::process(*imp, band, tile, smem_raw, args, pipe, prefetched)) return;
         __syncthreads();
     }
 }
@@ -1123,8 +1305,45 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
     return L;
 }
 
-ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws) {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D uint8 tensor map of an image, box of 128 columns x n rows, zero fill
+// outside the image.  False when the image cannot be described (the strip is
+// then read with plain loads).
+bool encode_strip_map(CUtensorMap *map, const void *img, int h, int w, long long pitch, int n) {
+    if ((uintptr_t)img % 16 != 0 || pitch % 16 != 0 || n < 4 || n > 256) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {128u, (cuuint32_t)n};
+    cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(img), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     ImgDesc im{};
+    im.use_tma = dtype == FHTDP_U8 &&
+                 encode_strip_map(&im.tmap, p.io.img, p.s.h, p.s.w, p.io.pitch, p.s.n);
     im.img = p.io.img;
     im.pitch = p.io.pitch;
     im.h = p.s.h;
@@ -1310,7 +1529,7 @@ int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, 
     int st = cuda_status(cudaMemsetAsync(base, 0, L.zero_bytes, stream), "cudaMemsetAsync");
     if (st) return st;
     LaunchArgs args = base_args(L, base, 1);
-    args.one = make_desc(one[0], L, base);
+    args.one = make_desc(one[0], L, base, dtype);
     args.many = nullptr;
     args.order = nullptr;
     return dispatch(dtype, L.max_h, args, L.max_n, stream);
@@ -1368,7 +1587,8 @@ int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream
         return set_error(FHTDP_EWORKSPACE, "batch workspace needs %zu bytes, got %zu",
                          plan->L.total, ws_bytes);
     plan->staging.clear();
-    for (auto &p : plan->imgs) plan->staging.push_back(make_desc(p, plan->L, (char *)ws));
+    for (auto &p : plan->imgs)
+        plan->staging.push_back(make_desc(p, plan->L, (char *)ws, plan->dtype));
     plan->bound_ws = ws;
     int st = cuda_status(cudaMemcpyAsync((char *)ws + plan->L.table_off, plan->staging.data(),
                                          sizeof(ImgDesc) * plan->staging.size(),
