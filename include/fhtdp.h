@@ -131,6 +131,30 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
                           int32_t *x_out, int32_t *d_out, void *score_out,
                           void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/* fhtdp_detect_polyline without a caller workspace.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory (hosts that own all device memory themselves, or real-time loops in
+ * which a cudaMalloc, which may synchronise the device, is not allowed).  It
+ * allocates nothing: its scratch is a fixed array of
+ * FHTDP_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits.  Arguments, outputs and results
+ * are those of fhtdp_detect_polyline.
+ *   - Images whose scratch (fhtdp_workspace_bytes) exceeds the array are
+ *     rejected with FHTDP_EWORKSPACE before anything is enqueued (a 2048x2048
+ *     uint8 image with 128-row bands needs about 12.5 MiB).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array, and it keeps the last call's contents;
+ *     each call clears the parts that must start at zero.  Calls whose work
+ *     overlaps on the GPU (different streams, or different host threads on the
+ *     same device without ordering) race on the array: order them on one
+ *     stream.
+ *   - fhtdp_workspace_status is not available for these calls. */
+#define FHTDP_NOALLOC_SCRATCH_BYTES (16u << 20)
+int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, int w, int pitch, int k,
+                                  int B, int32_t *x_out, int32_t *d_out, void *score_out,
+                                  cudaStream_t stream);
+
 /* Status of the last detection run that used this workspace (a single image
  * or a batch): FHTDP_OK, or FHTDP_ETIMEOUT if one of its bounded device-side
  * waits gave up (its outputs are then undefined).  Synchronises `stream`

@@ -22,7 +22,8 @@ import threading
 from . import _build
 
 __all__ = ["load", "lib", "build", "FhtdpError", "fht_bands", "polyline_dp", "backtrack",
-           "detect_polyline", "workspace_bytes", "launch_count", "BatchPlan", "Image",
+           "detect_polyline", "detect_polyline_noalloc", "workspace_bytes", "launch_count",
+           "BatchPlan", "Image",
            "workspace_status", "hough_bytes", "fht_workspace_bytes",
            "DTYPE_U8", "DTYPE_I32", "DTYPE_F32", "STATUS"]
 
@@ -60,6 +61,8 @@ _SIGS = {
     "fhtdp_detect_polyline": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                               + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_detect_polyline_noalloc": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
+                                      + [ctypes.c_void_p] * 4),
     "fhtdp_batch_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_void_p)]),
     "fhtdp_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
@@ -261,6 +264,19 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def detect_polyline_noalloc(img, k: int, B: int, out=None, stream=None):
+    """detect_polyline for callers that cannot allocate device memory: the
+    scratch is a fixed array inside the library (FHTDP_NOALLOC_SCRATCH_BYTES).
+    Calls that overlap on the GPU race on that array."""
+    h, w, pitch = _image(img)
+    code = _dtype_code(img)
+    x, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_polyline_noalloc(img.data_ptr(), code, h, w, pitch, k, B,
+                                               x.data_ptr(), d.data_ptr(), score.data_ptr(),
+                                               _stream(stream)))
+    return x, d, score
 
 
 def detect_polyline(img, k: int, B: int, out=None, ws=None, stream=None):
