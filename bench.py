@@ -32,9 +32,11 @@ N_BAND = H // K
 METRIC = "Mpix/s end-to-end band-FHT+DP (exact) and % HBM roofline; batched/learned vs plain"
 WORKLOAD = "u8 2048x2048, k=16 bands of 128 rows, bend |d_{i+1}-d_i|<=16, Gaussian noise + 3 polylines"
 
-# DRAM bytes per launch of the dominant kernel from the last ncu capture of
-# the same kernel build (null until captured for the current kernel).
-NCU_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per image of engine_kernel<uint8> from the ncu
+# capture summarised in profiles/engine_kernel_u8_2048x2048_k16_B16.md
+# (48 images per launch); a launch's traffic is this times its images.  Set to
+# None whenever the kernel changes until it is captured again.
+NCU_TRAFFIC_BYTES_PER_IMAGE = (264.419328e6 + 1391.033e6) / 48
 
 
 def algorithmic_bytes_per_image(h=H, w=W_IMG, k=K, bpp=1):
@@ -290,7 +292,8 @@ def run_ours(args):
                        "B": B, "pixel": "u8", "parallelism": "images sharded over ranks",
                        "l2": "inputs %d MB per step > 129 MB L2, no flush" % (h2d // 2**20)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": NCU_TRAFFIC_BYTES,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": (NCU_TRAFFIC_BYTES_PER_IMAGE * I
+                                     if NCU_TRAFFIC_BYTES_PER_IMAGE else None),
                          "peak_kind": peak_kind,
                          "kernel": "engine_kernel (one persistent launch per step)"},
             "single_image_ms": statistics.median(lat),
