@@ -127,6 +127,23 @@ def make_images(count, first_seed):
     return [synth.plain_gaussian(first_seed + j, H, W_IMG, K, B).img for j in range(count)]
 
 
+def image_seeds(images, seed, rank):
+    """Seeds of the images of one rank: every rank takes its own images
+    (weak scaling; the images are independent problems)."""
+    first = seed * 1000003 + rank * 10007
+    return [first + j for j in range(images)]
+
+
+def max_over_ranks(value, dist, device):
+    """The slowest rank's time (the only cross-rank reduction of the run)."""
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(budget_s=12.0, max_images=8, seed=0):
     """The oracle as it stands, single-threaded, on a bounded sample of the
     workload's images."""
@@ -185,7 +202,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     fd.load()
     I = args.images
-    imgs = make_images(I, args.seed * 1000003 + rank * 10007)
+    from paper_1912_01884_gb300 import synth
+    imgs = [synth.plain_gaussian(sd, H, W_IMG, K, B).img for sd in image_seeds(I, args.seed, rank)]
     host = torch.from_numpy(np.stack(imgs)).pin_memory()
     dimg = host.to(dev)
     xs = torch.empty((I, K + 1), dtype=torch.int32, device=dev)
@@ -225,11 +243,7 @@ def run_ours(args):
     launches = fd.launch_count() - l0
     clocks = sampler.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
     pix = I * H * W_IMG * world * args.steps
     value = pix / total_s / 1e6
 
@@ -254,11 +268,7 @@ def run_ours(args):
         stream.synchronize()
         e2e_ev.append((e0, e1))
     barrier()
-    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist, dev)
     e2e_value = pix / e2e_s / 1e6
 
     # --- roofline of the engine kernel (one launch per step) --------------

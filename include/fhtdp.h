@@ -161,6 +161,15 @@ int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, int w, int 
  * (one 4-byte device-to-host copy). */
 int fhtdp_workspace_status(const void *ws, cudaStream_t stream);
 
+/* Test hook for failure detection (no counterpart in the paper): the next
+ * fused-engine run started from this host thread (fhtdp_detect_polyline or
+ * fhtdp_batch_run) never publishes the window maxima of column tile `tile` of
+ * band `band` of its first image, and its device-side waits give up after
+ * `wait_cycles` SM cycles instead of about two seconds.  The run then ends with
+ * FHTDP_ETIMEOUT in fhtdp_workspace_status and undefined outputs; the CUDA
+ * context stays usable.  Nothing faults or hangs. */
+void fhtdp_debug_inject(int band, int tile, long long wait_cycles);
+
 /* ------------------------------------------------------------------------
  * Batches: many images of different h, w, k and B (one pixel type) in ONE
  * persistent kernel launch.  Work items (image, band, column tile) are taken

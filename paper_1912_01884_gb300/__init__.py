@@ -61,6 +61,7 @@ _SIGS = {
     "fhtdp_detect_polyline": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                               + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_debug_inject": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong]),
     "fhtdp_detect_polyline_noalloc": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                                       + [ctypes.c_void_p] * 4),
     "fhtdp_batch_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,

@@ -165,6 +165,10 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
     return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, ws_bytes, stream);
 }
 
+void fhtdp_debug_inject(int band, int tile, long long wait_cycles) {
+    debug_inject(band, tile, wait_cycles);
+}
+
 int fhtdp_workspace_status(const void *ws, cudaStream_t stream) {
     g_last_error[0] = 0;
     if (!ws) return set_error(FHTDP_EINVAL, "null workspace");

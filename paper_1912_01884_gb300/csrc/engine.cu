@@ -84,6 +84,9 @@ struct LaunchArgs {
     long long items;
     Ctl *ctl;
     long long wait_cycles;
+    // Fault injection for tests (fhtdp_debug_inject): the tile (band, tile)
+    // of the first image never publishes; -1 disables.
+    int skip_band, skip_tile;
 };
 
 // ---------------------------------------------------------------------------
@@ -572,8 +575,10 @@ __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArg
     __syncthreads();
 }
 
-__device__ void publish(const ImgDesc &im, int band, int tile) {
+__device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
     __syncthreads();
+    const ImgDesc &first = args.many ? args.many[0] : args.one;
+    if (band == args.skip_band && tile == args.skip_tile && im.flags == first.flags) return;
     if (threadIdx.x == 0) {
         __threadfence();
         st_release(im.flags + (size_t)band * im.tiles + tile, 1);
@@ -1000,7 +1005,7 @@ struct U8Path {
                                 window_regs<33, false, Key>(c0, c1, B, dk, vkey, emit);
                     }
                 }
-                publish(im, band, tile);
+                publish(im, band, tile, args);
                 return true;
             }
         }
@@ -1027,7 +1032,7 @@ struct U8Path {
                 __syncthreads();
             }
         }
-        publish(im, band, tile);
+        publish(im, band, tile, args);
         return true;
     }
 };
@@ -1194,7 +1199,7 @@ struct WidePath {
                                          emit);
             __syncthreads();
         }
-        publish(im, band, tile);
+        publish(im, band, tile, args);
         if (threadIdx.x == 0) take_next();
         return true;
     }
@@ -1418,12 +1423,29 @@ int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, cudaStream
     }
 }
 
+// Test hook state (per host thread), consumed by the next run.
+thread_local int g_inject_band = -1, g_inject_tile = -1;
+thread_local long long g_inject_wait = 0;
+
+void consume_injection(LaunchArgs *args) {
+    if (g_inject_band >= 0) {
+        args->skip_band = g_inject_band;
+        args->skip_tile = g_inject_tile;
+        args->wait_cycles = g_inject_wait;
+    }
+    g_inject_band = g_inject_tile = -1;
+    g_inject_wait = 0;
+}
+
 LaunchArgs base_args(const RunLayout &L, char *ws, int count) {
     LaunchArgs args{};
     args.count = count;
     args.items = L.items;
     args.ctl = (Ctl *)ws;
     args.wait_cycles = 4000000000LL;   // about two seconds at GB300 clocks
+    args.skip_band = -1;
+    args.skip_tile = -1;
+    consume_injection(&args);
     return args;
 }
 
@@ -1615,5 +1637,11 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
 }
 
 void batch_destroy(BatchPlan *plan) { delete plan; }
+
+void debug_inject(int band, int tile, long long wait_cycles) {
+    g_inject_band = band;
+    g_inject_tile = tile;
+    g_inject_wait = wait_cycles > 0 ? wait_cycles : 1;
+}
 
 }  // namespace fhtdp
