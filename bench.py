@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Throughput of end-to-end curve detection (band FHT + bend-limited DP +
-read-back) on synthetic 2048x2048 uint8 images, k=16 bands of 128 rows, bend
-range 16, in Mpix/s.
+read-back) in Mpix/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload plain2048|mixed|float8192|plain256] [--images I]
 
-A step is one pass of the whole method over a batch of --images distinct
-seeded images per GPU (inputs already resident in HBM; the batch is larger
-than the 129 MB L2, so no flush is needed between steps).  Under torchrun
-each rank takes its own images (weak scaling, no data-path collective).
-Rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle (the
-paper's method as a plain C program) on a bounded sample of the same
-workload on the host cores.
+Default workload: synthetic 2048x2048 uint8 images, k=16 bands of 128 rows,
+bend range 16.  A step is one pass of the whole method over a batch of
+--images distinct seeded images per GPU: one persistent kernel launch, inputs
+already resident in HBM.  Each batch is larger than the 129 MB L2, so no
+flush is needed between steps.  Under torchrun each rank takes its own
+images (weak scaling, no data-path collective) and rank 0 prints one JSON
+line.  ``--impl reference`` times the CPU oracle (the method as a plain C
+program) on a bounded sample of the same workload on the host cores; the
+paper has no code of its own to run.
 """
 from __future__ import annotations
 
@@ -27,19 +29,32 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-H, W_IMG, K, B = 2048, 2048, 16, 16
-N_BAND = H // K
 METRIC = "Mpix/s end-to-end band-FHT+DP (exact) and % HBM roofline; batched/learned vs plain"
-WORKLOAD = "u8 2048x2048, k=16 bands of 128 rows, bend |d_{i+1}-d_i|<=16, Gaussian noise + 3 polylines"
 
-# DRAM bytes (read + write) per image of engine_kernel<uint8> from the ncu
-# capture summarised in profiles/engine_kernel_u8_2048x2048_k16_B16.md
-# (48 images per launch); a launch's traffic is this times its images.  Set to
-# None whenever the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES_PER_IMAGE = (264.419328e6 + 1391.033e6) / 48
+WORKLOADS = {
+    "plain2048": dict(
+        desc="u8 2048x2048, k=16 bands of 128 rows, bend |d_{i+1}-d_i|<=16, Gaussian noise + 3 "
+             "polylines", images=32, dtype="u8"),
+    "mixed": dict(
+        desc="mixed batch: u8, h in 512..4096, w in 512..3072 (step 256), band height 32..256, "
+             "bend = band/8, uniform noise + 1 polyline", images=256, dtype="u8"),
+    "float8192": dict(
+        desc="f32 8192x8192 ridge response, k=64 bands of 128 rows, bend 24", images=1,
+        dtype="f32"),
+    "plain256": dict(
+        desc="u8 256x256, k=4 bands of 64 rows, bend 8, uniform noise + 1 polyline", images=2048,
+        dtype="u8"),
+}
+
+# DRAM bytes (read + write) per image of engine_kernel<uint8> on the default
+# workload from the ncu capture summarised in
+# profiles/engine_kernel_u8_2048x2048_k16_B16.md (48 images per launch); a
+# launch's traffic is this times its images.  None for other workloads, and
+# to be reset whenever the kernel changes until it is captured again.
+NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (264.419328e6 + 1391.033e6) / 48}
 
 
-def algorithmic_bytes_per_image(h=H, w=W_IMG, k=K, bpp=1):
+def algorithmic_bytes(h, w, k, bpp):
     """Bytes the method must move per image: read the image once, write and
     read one 4-byte DP value per state (x, d) of every band, and the path."""
     n = h // k
@@ -51,7 +66,8 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--images", type=int, default=32, help="images per step per GPU")
+    ap.add_argument("--workload", default="plain2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--images", type=int, default=0, help="images per step per GPU")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU baseline leg")
@@ -122,11 +138,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_images(count, first_seed):
-    from paper_1912_01884_gb300 import synth
-    return [synth.plain_gaussian(first_seed + j, H, W_IMG, K, B).img for j in range(count)]
-
-
 def image_seeds(images, seed, rank):
     """Seeds of the images of one rank: every rank takes its own images
     (weak scaling; the images are independent problems)."""
@@ -144,20 +155,37 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
-def cpu_baseline(budget_s=12.0, max_images=8, seed=0):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload's images."""
+def make_workload(name, images, seed, rank):
+    """[(img, k, B)] of one rank."""
+    from paper_1912_01884_gb300 import synth
+    seeds = image_seeds(images, seed, rank)
+    if name == "plain2048":
+        return [(w.img, w.k, w.B) for w in (synth.plain_gaussian(s) for s in seeds)]
+    if name == "plain256":
+        return [(w.img, w.k, w.B) for w in (synth.plain_uniform(s, 256, 256, 4, 8) for s in seeds)]
+    if name == "float8192":
+        return [(w.img, w.k, w.B) for w in (synth.ridge_response(s) for s in seeds)]
+    shapes = synth.mixed_batch_shapes(seed * 7919 + rank, images)
+    return [(synth.plain_uniform(s, h, w, k, B).img, k, B)
+            for s, (h, w, k, B) in zip(seeds, shapes)]
+
+
+def oracle_rate(items, budget_s):
+    """The oracle as it stands, one thread, on images of the workload until
+    `budget_s` has passed: (Mpix/s, images done)."""
+    import numpy as np
     import oracle
-    imgs = make_images(max_images, 900000 + seed)
-    done, t0 = 0, time.perf_counter()
-    for img in imgs:
-        oracle.detect(img, K, B)
+    done, pix, t0 = 0, 0, time.perf_counter()
+    for img, k, B in items:
+        if img.dtype == np.float32:
+            oracle.detect_f32(img, k, B)
+        else:
+            oracle.detect(img, k, B)
         done += 1
+        pix += img.size
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return {"value": done * H * W_IMG / dt / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of the workload's 2048x2048 images, whole method, one thread" % done}
+    return pix / (time.perf_counter() - t0) / 1e6, done
 
 
 def run_reference(args):
@@ -166,21 +194,24 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    imgs = make_images(args.steps + args.warmup, 700000 + args.seed)
-    for img in imgs[:args.warmup]:
-        oracle.detect(img, K, B)
+    spec = WORKLOADS[args.workload]
+    items = make_workload(args.workload, args.steps + args.warmup, 700000 + args.seed, 0)
+    for item in items[:args.warmup]:
+        oracle_rate([item], 0)
     t0 = time.perf_counter()
-    for img in imgs[args.warmup:]:
-        oracle.detect(img, K, B)
+    pix = 0
+    for item in items[args.warmup:]:
+        oracle_rate([item], 0)
+        pix += item[0].size
     dt = time.perf_counter() - t0
-    value = args.steps * H * W_IMG / dt / 1e6
+    value = pix / dt / 1e6
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "images_per_step": 1, "h": H, "w": W_IMG, "k": K,
-                   "B": B, "pixel": "u8"},
+        "vs_baseline": None, "dtype": "f64" if spec["dtype"] == "u8" else "f32",
+        "data": "synthetic",
+        "config": {"workload": spec["desc"], "images_per_step": 1},
         "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                          "sample": "1 image of the workload per step, whole method, one thread"},
         "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
@@ -201,17 +232,37 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     fd.load()
-    I = args.images
-    from paper_1912_01884_gb300 import synth
-    imgs = [synth.plain_gaussian(sd, H, W_IMG, K, B).img for sd in image_seeds(I, args.seed, rank)]
-    host = torch.from_numpy(np.stack(imgs)).pin_memory()
-    dimg = host.to(dev)
-    xs = torch.empty((I, K + 1), dtype=torch.int32, device=dev)
-    ds = torch.empty((I, K), dtype=torch.int32, device=dev)
-    sc = torch.empty((I, 1), dtype=torch.int32, device=dev)
+    spec = WORKLOADS[args.workload]
+    I = args.images or spec["images"]
+    items = make_workload(args.workload, I, args.seed, rank)
+    tdt = torch.float32 if spec["dtype"] == "f32" else torch.uint8
+    esize = 4 if spec["dtype"] == "f32" else 1
+
+    # Inputs: one pinned host buffer and one device buffer, image after image
+    # (each image 256-byte aligned); outputs in flat device buffers.
+    offs, total = [], 0
+    for img, _, _ in items:
+        offs.append(total)
+        total += (img.size * esize + 255) // 256 * 256
+    host_bytes = torch.empty(total, dtype=torch.uint8).pin_memory()
+    for (img, _, _), o in zip(items, offs):
+        host_bytes[o:o + img.size * esize].view(tdt).view(img.shape).copy_(torch.from_numpy(img))
+    dev_bytes = host_bytes.to(dev)
+    views_d = [dev_bytes[o:o + img.size * esize].view(tdt).view(img.shape)
+               for (img, _, _), o in zip(items, offs)]
+    ks = [k for _, k, _ in items]
+    Bs = [B for _, _, B in items]
+    xs = torch.empty(sum(k + 1 for k in ks), dtype=torch.int32, device=dev)
+    ds = torch.empty(sum(ks), dtype=torch.int32, device=dev)
+    sc = torch.empty(len(items), dtype=torch.float32 if tdt == torch.float32 else torch.int32,
+                     device=dev)
+    xo = np.cumsum([0] + [k + 1 for k in ks])
+    do = np.cumsum([0] + ks)
+    outs = ([xs[xo[i]:xo[i + 1]] for i in range(len(items))],
+            [ds[do[i]:do[i + 1]] for i in range(len(items))],
+            [sc[i:i + 1] for i in range(len(items))])
     stream = torch.cuda.current_stream(dev)
-    plan = fd.BatchPlan([dimg[i] for i in range(I)], [K] * I, [B] * I, out=(xs, ds, sc),
-                        stream=stream)
+    plan = fd.BatchPlan(views_d, ks, Bs, out=outs, stream=stream)
     hx = torch.empty_like(xs, device="cpu").pin_memory()
     hd = torch.empty_like(ds, device="cpu").pin_memory()
     hs = torch.empty_like(sc, device="cpu").pin_memory()
@@ -244,22 +295,22 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
-    pix = I * H * W_IMG * world * args.steps
+    pix_rank = sum(img.size for img, _, _ in items)
+    pix = pix_rank * world * args.steps
     value = pix / total_s / 1e6
 
     # --- end to end through the public API: H2D + detect + D2H -----------
-    h2d = host.numel() * host.element_size()
+    h2d = dev_bytes.numel()
     d2h = (hx.numel() + hd.numel() + hs.numel()) * 4
     for _ in range(2):
-        dimg.copy_(host, non_blocking=True)
+        dev_bytes.copy_(host_bytes, non_blocking=True)
         step()
     barrier()
-    t0 = time.perf_counter()
     e2e_ev = []
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        dimg.copy_(host, non_blocking=True)
+        dev_bytes.copy_(host_bytes, non_blocking=True)
         step()
         hx.copy_(xs, non_blocking=True)
         hd.copy_(ds, non_blocking=True)
@@ -271,22 +322,26 @@ def run_ours(args):
     e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist, dev)
     e2e_value = pix / e2e_s / 1e6
 
-    # --- roofline of the engine kernel (one launch per step) --------------
+    # --- roofline of the engine kernel (one persistent launch per step) ---
     hbm, peak_kind = peaks()
-    alg = algorithmic_bytes_per_image() * I
+    alg = sum(algorithmic_bytes(img.shape[0], img.shape[1], k, esize) for img, k, _ in items)
     per_launch_s = total_s / args.steps
     achieved = alg / per_launch_s / 1e9
+    traffic = NCU_TRAFFIC_BYTES_PER_IMAGE.get(args.workload)
 
     # --- single-image latency (one image per launch, same kernels) --------
-    ws1 = torch.empty(fd.workspace_bytes(fd.DTYPE_U8, H, W_IMG, K, B), dtype=torch.uint8,
-                      device=dev)
+    img0, k0, B0 = views_d[0], ks[0], Bs[0]
+    ws1 = torch.empty(fd.workspace_bytes(fd.DTYPE_F32 if tdt == torch.float32 else fd.DTYPE_U8,
+                                         img0.shape[0], img0.shape[1], k0, B0),
+                      dtype=torch.uint8, device=dev)
+    one = (outs[0][0], outs[1][0], outs[2][0])
     for _ in range(3):
-        fd.detect_polyline(dimg[0], K, B, out=(xs[0], ds[0], sc[0]), ws=ws1, stream=stream)
+        fd.detect_polyline(img0, k0, B0, out=one, ws=ws1, stream=stream)
     lat = []
-    for i in range(min(I, 16)):
+    for _ in range(8):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        fd.detect_polyline(dimg[i], K, B, out=(xs[i], ds[i], sc[i]), ws=ws1, stream=stream)
+        fd.detect_polyline(img0, k0, B0, out=one, ws=ws1, stream=stream)
         e1.record(stream)
         e1.synchronize()
         lat.append(e0.elapsed_time(e1))
@@ -297,13 +352,15 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "images_per_step": I, "h": H, "w": W_IMG, "k": K,
-                       "B": B, "pixel": "u8", "parallelism": "images sharded over ranks",
-                       "l2": "inputs %d MB per step > 129 MB L2, no flush" % (h2d // 2**20)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": (NCU_TRAFFIC_BYTES_PER_IMAGE * I
-                                     if NCU_TRAFFIC_BYTES_PER_IMAGE else None),
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if tdt == torch.float32 else "int32", "data": "synthetic",
+            "config": {"workload": spec["desc"], "images_per_step": len(items),
+                       "pixels_per_step": pix_rank, "parallelism": "images sharded over ranks",
+                       "l2": "inputs %d MB per step %s 129 MB L2, no flush"
+                             % (h2d // 2**20, ">" if h2d > 129e6 else "<")},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm,
+                         "traffic": traffic * len(items) if traffic else None,
                          "peak_kind": peak_kind,
                          "kernel": "engine_kernel (one persistent launch per step)"},
             "single_image_ms": statistics.median(lat),
@@ -313,7 +370,10 @@ def run_ours(args):
             "clocks": clocks,
         }
         if world == 1 and not args.skip_cpu:
-            out["cpu_baseline"] = cpu_baseline(seed=args.seed)
+            rate, done = oracle_rate(make_workload(args.workload, 8, 900000 + args.seed, 0), 12.0)
+            out["cpu_baseline"] = {
+                "value": rate, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                "sample": "%d images of the workload, whole method, one thread" % done}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

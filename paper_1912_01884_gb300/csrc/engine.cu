@@ -1496,7 +1496,9 @@ ImgPlan single_plan(const void *img, int pitch, const Shape &s, int B, int32_t *
 // The host-side plan of a batch.
 struct BatchPlan {
     int dtype;
-    std::vector<ImgPlan> imgs;
+    std::vector<ImgPlan> imgs;      // images of the fused launch
+    std::vector<ImgPlan> separate;  // 256-row bands: run with the standalone kernels
+    size_t separate_off = 0;        // their shared scratch (one image at a time)
     RunLayout L;
     std::vector<ImgDesc> staging;   // image table as uploaded
     std::vector<Item> order;        // work queue as uploaded
@@ -1584,16 +1586,18 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
                              "image %d: invalid (h=%d w=%d pitch=%d k=%d B=%d or null pointer)",
                              i, io.h, io.w, io.pitch, io.k, io.B);
         }
-        if (s.n > kMaxBandFused) {
-            delete plan;
-            return set_error(FHTDP_EINVAL,
-                             "image %d: bands of %d rows are not supported in batches (max %d)",
-                             i, s.n, kMaxBandFused);
-        }
-        plan->imgs.push_back(single_plan(io.img, io.pitch, s, io.B, io.x_out, io.d_out,
-                                         io.score_out));
+        ImgPlan p = single_plan(io.img, io.pitch, s, io.B, io.x_out, io.d_out, io.score_out);
+        if (s.n > kMaxBandFused)
+            plan->separate.push_back(p);
+        else
+            plan->imgs.push_back(p);
     }
     plan->L = plan_layout(plan->imgs, true);
+    // Scratch of the standalone path, reused image after image (stream order).
+    size_t sep = 0;
+    for (auto &p : plan->separate) sep = std::max(sep, engine_workspace_bytes(dtype, p.s, p.io.B));
+    plan->separate_off = align_up(plan->L.total, 256);
+    if (sep) plan->L.total = plan->separate_off + sep;
     plan->order = queue_order(plan->imgs, (long long)num_sms() * 3 / 2);
     *out = plan;
     return FHTDP_OK;
@@ -1630,10 +1634,21 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
     char *base = (char *)ws;
     int st = cuda_status(cudaMemsetAsync(base, 0, plan->L.zero_bytes, stream), "cudaMemsetAsync");
     if (st) return st;
-    LaunchArgs args = base_args(plan->L, base, (int)plan->imgs.size());
-    args.many = (const ImgDesc *)(base + plan->L.table_off);
-    args.order = (const Item *)(base + plan->L.order_off);
-    return dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, stream);
+    if (!plan->imgs.empty()) {
+        LaunchArgs args = base_args(plan->L, base, (int)plan->imgs.size());
+        args.many = (const ImgDesc *)(base + plan->L.table_off);
+        args.order = (const Item *)(base + plan->L.order_off);
+        st = dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, stream);
+        if (st) return st;
+    }
+    // Images with 256-row bands: the level-by-level FHT, the in-place DP and
+    // the one-block read-back, in stream order on the shared scratch.
+    for (const auto &p : plan->separate) {
+        st = run_fallback(p.io.img, plan->dtype, p.io.pitch, p.s, p.io.B, p.io.x_out, p.io.d_out,
+                          p.io.score_out, base + plan->separate_off, stream);
+        if (st) return st;
+    }
+    return FHTDP_OK;
 }
 
 void batch_destroy(BatchPlan *plan) { delete plan; }

@@ -274,3 +274,15 @@ def test_batch_run_is_captured_in_a_cuda_graph(lib):
         assert list(plan.x[i].cpu().numpy()) == list(xo)
         assert list(plan.d[i].cpu().numpy()) == list(do)
         assert int(plan.score[i].cpu().numpy()[0]) == int(so)
+
+
+def test_batch_mixed_sizes_including_256_row_bands(lib):
+    """Mixed-size batch images of every band height (32..256) in one run."""
+    shapes = [s for s in synth.mixed_batch_shapes(1) if s[0] * s[1] <= 1536 * 1024]
+    by_n = {}
+    for s in shapes:
+        by_n.setdefault(s[0] // s[2], []).append(s)
+    picked = [s for n in sorted(by_n) for s in by_n[n][:3]]
+    assert any(s[0] // s[2] == 256 for s in picked)
+    wls = [synth.plain_uniform(100 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(picked)]
+    _batch_parity(lib, wls)
