@@ -44,6 +44,10 @@ WORKLOADS = {
     "plain256": dict(
         desc="u8 256x256, k=4 bands of 64 rows, bend 8, uniform noise + 1 polyline", images=2048,
         dtype="u8"),
+    "learned1024": dict(
+        desc="u8 1024x1024 lanes over textured noise, k=16 bands of 64 rows, bend 12: learned "
+             "window proposal (4-layer 32-channel bf16 CNN on the 4x downsample, windows of 16) "
+             "+ pruned DP + full-DP fallback, against the plain DP", images=512, dtype="u8"),
 }
 
 # DRAM bytes (read + write) per image of engine_kernel<uint8> on the default
@@ -379,10 +383,90 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    """Trains the proposal network on images labelled by the exact method,
+    then times the plain DP and the learned pipeline on held-out batches and
+    reports the exact-optimum hit rate and the score gap."""
+    import numpy as np
+    import torch
+
+    import paper_1912_01884_gb300 as fd
+    from paper_1912_01884_gb300 import learned
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fd.load()
+    h = w = 1024
+    k, B = 16, 12
+    batch = args.images or WORKLOADS["learned1024"]["images"]
+    train_steps = max(1, 49152 // batch)
+    model = learned.LaneProposer(seed=args.seed)
+    t0 = time.perf_counter()
+    losses = []
+    for step in range(train_steps):
+        imgs = learned.lane_images(10 * args.seed + 1000 + step, batch, h, w, k, B)
+        _, d, _ = learned.exact_paths(imgs, k, B)
+        labels = torch.from_numpy(learned.bins_of(d.cpu().numpy()).astype(np.int32)).cuda()
+        losses.append(float(model.train_step(imgs, labels, k).cpu()))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    plain_ms, learned_ms, hits, total, fallbacks, gaps = [], [], 0, 0, 0, []
+    for j in range(args.warmup + args.steps):
+        imgs = learned.lane_images(10**6 + 97 * args.seed + j, batch, h, w, k, B)
+        plan = fd.BatchPlan([imgs[i] for i in range(batch)], [k] * batch, [B] * batch)
+        plan.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.run()
+        e1.record()
+        torch.cuda.synchronize()
+        xe, de, se = torch.stack(plan.x), torch.stack(plan.d), torch.cat(plan.score)
+        t1 = time.perf_counter()
+        x, d, s, fb = learned.detect_learned(model, imgs, k, B)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if j < args.warmup:
+            continue
+        plain_ms.append(e0.elapsed_time(e1))
+        learned_ms.append((t2 - t1) * 1e3)
+        same = (s == se) & (x == xe).all(1) & (d == de).all(1)
+        hits += int(same.sum())
+        total += batch
+        fallbacks += int(fb.sum())
+        sd, se_ = s.double().cpu().numpy(), se.double().cpu().numpy()
+        gaps.extend(((se_ - sd) / se_).tolist())
+    pix = batch * h * w
+    plain = pix / (np.mean(plain_ms) / 1e3) / 1e6
+    value = pix / (np.mean(learned_ms) / 1e3) / 1e6
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(learned_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32 DP, bf16 CNN",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["learned1024"]["desc"], "images_per_step": batch},
+            "learned": {"plain_dp_mpix_s": plain, "learned_pipeline_mpix_s": value,
+                        "speedup_vs_plain": value / plain,
+                        "exact_optimum_hit_rate": hits / total,
+                        "fallback_rate": fallbacks / total,
+                        "score_gap_mean": float(np.mean(gaps)), "score_gap_max": float(np.max(gaps)),
+                        "train_images": train_steps * batch, "train_seconds": train_s,
+                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-5:])),
+                        "timing": "plain: CUDA events around one persistent launch; learned: "
+                                  "wall clock of CNN + windows + pruned DP + host fallback "
+                                  "decision + fallback DP"},
+        }), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "learned1024":
+        run_learned(args)
     else:
         run_ours(args)
 

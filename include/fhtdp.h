@@ -155,6 +155,52 @@ int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, int w, int 
                                   int B, int32_t *x_out, int32_t *d_out, void *score_out,
                                   cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Learned window proposal (no counterpart in the paper): a 4-layer,
+ * 32-channel 3x3 CNN on the 4x4-downsampled image predicts, for each band, a
+ * bin of 4 displacements; the DP then searches only a window around it
+ * (fhtdp_image.d_window), with the full DP as the fallback.  Activations are
+ * NHWC bf16 (C = 32; the input has C = 1), weights bf16 [tap = 3*ky+kx][ci][co]
+ * (the single-channel first layer: [16][32], taps 9..15 zero), FP32
+ * accumulation on the tensor cores, FP32 master weights.  All pointers are
+ * device memory owned by the caller; w must be a multiple of 64 and the
+ * dilation at most 8.
+ * ---------------------------------------------------------------------- */
+/* uint8 [n][h][w] -> bf16 [n][h/4][w/4], the 4x4 mean divided by 255. */
+int fhtdp_cnn_downsample4(const uint8_t *img, int n, int h, int w, void *out, cudaStream_t stream);
+/* y = act(conv3x3_dil(x, wt) + bias), act = ReLU when relu != 0; cin 1 or 32,
+ * cout 32, zero padding ("same"). */
+int fhtdp_cnn_conv3x3(const void *x, int cin, int n, int h, int w, int dil, const void *wt,
+                      const float *bias, int relu, void *y, cudaStream_t stream);
+/* dx = gradient of a 32-channel layer's input from the gradient dz of its
+ * pre-activation output; wflip is caller scratch of 9*32*32 bf16. */
+int fhtdp_cnn_conv3x3_dgrad(const void *dz, int n, int h, int w, int dil, const void *wt,
+                            void *wflip, void *dx, cudaStream_t stream);
+/* dy *= (y > 0): the ReLU of a layer, in place, from its output y. */
+int fhtdp_cnn_relu_backward(const void *y, void *dy, long long count, cudaStream_t stream);
+/* dw += sum over pixels of x(shifted by the tap) * dz (FP32 [taps][cin][32]),
+ * db += sum of dz (FP32 [32], may be NULL).  Accumulates: clear first. */
+int fhtdp_cnn_conv3x3_wgrad(const void *x, int cin, int n, int h, int w, int dil, const void *dz,
+                            float *dw, float *db, cudaStream_t stream);
+/* Band head: pooled[n][b][c] = log-sum-exp of logits[n][rows of band b][:][c];
+ * loss += scale * cross-entropy(softmax(pooled), labels[n][b]) (labels may
+ * be NULL), dlogits = its gradient (may be NULL), pred[n][b] = argmax_c
+ * pooled (may be NULL). */
+int fhtdp_cnn_band_head(const void *logits, int n, int h, int w, int bands,
+                        const int32_t *labels, float scale, void *dlogits, float *loss,
+                        int32_t *pred, cudaStream_t stream);
+/* One Adam step (step >= 1) on FP32 parameters p with moments m, v and
+ * gradient g; also writes the bf16 copy wb (may be NULL). */
+int fhtdp_cnn_adam(float *p, float *m, float *v, const float *g, int count, float lr, float b1,
+                   float b2, float eps, int step, void *wb, cudaStream_t stream);
+/* bf16 copy of FP32 values. */
+int fhtdp_cnn_to_bf16(const float *src, void *dst, int count, cudaStream_t stream);
+/* Pruned-DP windows from predicted bins: bin c covers displacements d with
+ * d + 64 in [4c, 4c+3]; win[i] = that range widened by `margin` on each side,
+ * clipped to [-(n-1), n-1]. */
+int fhtdp_cnn_bin_windows(const int32_t *pred, int count, int n, int margin, int32_t *win,
+                          cudaStream_t stream);
+
 /* Status of the last detection run that used this workspace (a single image
  * or a batch): FHTDP_OK, or FHTDP_ETIMEOUT if one of its bounded device-side
  * waits gave up (its outputs are then undefined).  Synchronises `stream`
@@ -184,6 +230,13 @@ typedef struct fhtdp_image {
     int32_t *x_out;      /* device, k+1 vertices */
     int32_t *d_out;      /* device, k displacements */
     void *score_out;     /* device, one int32 (integer images) or float */
+    /* Optional (NULL = none): device [k][2] int32, the allowed displacements
+     * [lo_i, hi_i] of each band's link.  With it the DP searches only those
+     * links (the pruned DP of the learned proposal, which the paper does not
+     * have) and returns the best polyline inside the windows; if there is none,
+     * the score is INT32_MIN / -infinity and every vertex -1.  Bands of at most
+     * 128 rows. */
+    const int32_t *d_window;
 } fhtdp_image;
 
 typedef struct fhtdp_batch_plan fhtdp_batch_plan;

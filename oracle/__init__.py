@@ -14,6 +14,8 @@ Function map (paper passages in the C file's comments):
   backtrack        Sec. 2.2 Eq. 5, main problem steps 2-3
   path_score       Sec. 2.1, sum along a given polyline (plain definition)
   brute            every admissible polyline, tiny images only
+  detect_windowed  the DP restricted to per-band displacement windows (the
+                   pruned DP of the learned proposal, not in the paper)
   detect / detect_f32   the whole method (CPU baseline)
 """
 from __future__ import annotations
@@ -77,6 +79,13 @@ def _load():
             lib.oracle_detect_f64.restype = ctypes.c_double
             lib.oracle_detect_f32.argtypes = [_F32P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
             lib.oracle_detect_f32.restype = ctypes.c_double
+            lib.oracle_detect_win_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
+                                                  + [_I32P, _I32P, _I32P])
+            lib.oracle_detect_win_f64.restype = ctypes.c_double
+            lib.oracle_brute_win_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
+                                                 + [_I32P, _I32P, _I32P,
+                                                    ctypes.POINTER(ctypes.c_long)])
+            lib.oracle_brute_win_f64.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -196,6 +205,35 @@ def detect(img, k: int, B: int):
     s = _load().oracle_detect_f64(_p(img, ctypes.c_double), h, w, k, B,
                                   _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
     return xs, ds, s
+
+
+def detect_windowed(img, k: int, B: int, win):
+    """The method restricted to per-band displacement windows win[k][2]
+    (the pruned DP of the learned proposal): (x, d, score); x = -1 and score
+    -inf when no admissible polyline lies inside the windows."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    wn = np.ascontiguousarray(win, dtype=np.int32).reshape(k, 2)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_win_f64(_p(img, ctypes.c_double), h, w, k, B,
+                                      _p(wn, ctypes.c_int32), _p(xs, ctypes.c_int32),
+                                      _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def brute_windowed(img, k: int, B: int, win):
+    """Brute force over the admissible polylines inside the windows."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    wn = np.ascontiguousarray(win, dtype=np.int32).reshape(k, 2)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    visited = ctypes.c_long(0)
+    s = _load().oracle_brute_win_f64(_p(img, ctypes.c_double), h, w, k, B,
+                                     _p(wn, ctypes.c_int32), _p(xs, ctypes.c_int32),
+                                     _p(ds, ctypes.c_int32), ctypes.byref(visited))
+    return xs, ds, s, visited.value
 
 
 def detect_f32(img, k: int, B: int):

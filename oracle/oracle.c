@@ -167,13 +167,17 @@ ORACLE_DEFINE_FHT_RECURSIVE(float, f32)
  * structure: the structure only changes the cost, not the result).
  * H: [k][2][n][W], V: [k][2n-1][w].
  * ------------------------------------------------------------------------ */
+/* win (optional, NULL = none): [k][2] allowed displacements [lo_i, hi_i] of
+ * each band; links outside are dead.  This restriction is the pruned DP of
+ * the learned window proposal, which is not part of the paper. */
 #define ORACLE_DEFINE_DP(T, SUFFIX)                                              \
     static T hough_at_##SUFFIX(const T *H, int n, int W, int b, int x, int d) {  \
         int sign = d >= 0 ? 0 : 1;                                               \
         int s = d >= 0 ? d : -d;                                                 \
         return H[(((size_t)b * 2 + sign) * n + s) * W + x];                      \
     }                                                                            \
-    int oracle_dp_##SUFFIX(const T *H, int h, int w, int k, int B, T *V) {       \
+    int oracle_dp_win_##SUFFIX(const T *H, int h, int w, int k, int B,           \
+                               const int32_t *win, T *V) {                       \
         if (k < 1 || h % k != 0 || B < 0) return -1;                             \
         int n = h / k;                                                           \
         int W = w + n;                                                           \
@@ -183,7 +187,8 @@ ORACLE_DEFINE_FHT_RECURSIVE(float, f32)
                 for (int x = 0; x < w; ++x) {                                    \
                     T *out = &V[((size_t)b * D + (d + n - 1)) * w + x];          \
                     int xn = x + d;                                              \
-                    if (xn < 0 || xn >= w) {                                     \
+                    int outside = win && (d < win[2 * b] || d > win[2 * b + 1]); \
+                    if (xn < 0 || xn >= w || outside) {                          \
                         *out = (T)ORACLE_NEG;                                    \
                         continue;                                                \
                     }                                                            \
@@ -201,6 +206,9 @@ ORACLE_DEFINE_FHT_RECURSIVE(float, f32)
                     *out = (best == (T)ORACLE_NEG) ? (T)ORACLE_NEG : hv + best;  \
                 }                                                                \
         return 0;                                                                \
+    }                                                                            \
+    int oracle_dp_##SUFFIX(const T *H, int h, int w, int k, int B, T *V) {       \
+        return oracle_dp_win_##SUFFIX(H, h, w, k, B, NULL, V);                   \
     }
 
 ORACLE_DEFINE_DP(double, f64)
@@ -232,6 +240,11 @@ ORACLE_DEFINE_DP(float, f32)
                     bd = d;                                                      \
                 }                                                                \
             }                                                                    \
+        if (best == (T)ORACLE_NEG) { /* no admissible polyline */               \
+            for (int i = 0; i <= k; ++i) xs[i] = -1;                             \
+            for (int i = 0; i < k; ++i) ds[i] = 0;                               \
+            return (double)ORACLE_NEG;                                           \
+        }                                                                        \
         xs[0] = bx;                                                              \
         ds[0] = bd;                                                              \
         for (int i = 1; i < k; ++i) {                                            \
@@ -296,6 +309,7 @@ double oracle_path_score_f64(const double *img, int h, int w, int k, int x0,
  * ------------------------------------------------------------------------ */
 typedef struct {
     const double *img;
+    const int32_t *win;
     int h, w, k, n, B;
     int32_t *cur_d;
     int cur_x0;
@@ -313,6 +327,7 @@ static void brute_rec(brute_state *st, int i, int x) {
             if (d < prev - st->B || d > prev + st->B) continue;
         }
         if (x + d < 0 || x + d >= st->w) continue;
+        if (st->win && (d < st->win[2 * i] || d > st->win[2 * i + 1])) continue;
         st->cur_d[i] = d;
         if (i + 1 < st->k) {
             brute_rec(st, i + 1, x + d);
@@ -334,10 +349,11 @@ static void brute_rec(brute_state *st, int i, int x) {
     }
 }
 
-double oracle_brute_f64(const double *img, int h, int w, int k, int B,
-                        int32_t *xs, int32_t *ds, long *visited) {
+double oracle_brute_win_f64(const double *img, int h, int w, int k, int B,
+                            const int32_t *win, int32_t *xs, int32_t *ds, long *visited) {
     brute_state st;
     st.img = img;
+    st.win = win;
     st.h = h;
     st.w = w;
     st.k = k;
@@ -354,7 +370,16 @@ double oracle_brute_f64(const double *img, int h, int w, int k, int B,
     }
     free(st.cur_d);
     if (visited) *visited = st.visited;
+    if (st.best == ORACLE_NEG) {
+        for (int i = 0; i <= k; ++i) xs[i] = -1;
+        for (int i = 0; i < k; ++i) ds[i] = 0;
+    }
     return st.best;
+}
+
+double oracle_brute_f64(const double *img, int h, int w, int k, int B,
+                        int32_t *xs, int32_t *ds, long *visited) {
+    return oracle_brute_win_f64(img, h, w, k, B, NULL, xs, ds, visited);
 }
 
 /* ---------------------------------------------------------------------------
@@ -374,6 +399,26 @@ double oracle_detect_f64(const double *img, int h, int w, int k, int B,
     }
     oracle_fht_recursive_f64(img, h, w, k, H);
     oracle_dp_f64(H, h, w, k, B, V);
+    double s = oracle_backtrack_f64(V, h, w, k, B, xs, ds);
+    free(H);
+    free(V);
+    return s;
+}
+
+/* The method restricted to per-band displacement windows (win [k][2]). */
+double oracle_detect_win_f64(const double *img, int h, int w, int k, int B,
+                             const int32_t *win, int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * (2 * n - 1) * w);
+    if (!H || !V) {
+        free(H);
+        free(V);
+        return NAN;
+    }
+    oracle_fht_recursive_f64(img, h, w, k, H);
+    oracle_dp_win_f64(H, h, w, k, B, win, V);
     double s = oracle_backtrack_f64(V, h, w, k, B, xs, ds);
     free(H);
     free(V);

@@ -72,6 +72,25 @@ _SIGS = {
                                           ctypes.c_void_p]),
     "fhtdp_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fhtdp_batch_plan_destroy": (None, [ctypes.c_void_p]),
+    "fhtdp_cnn_downsample4": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 3
+                              + [ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_cnn_conv3x3": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
+                          + [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.c_void_p]),
+    "fhtdp_cnn_conv3x3_dgrad": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4
+                                + [ctypes.c_void_p] * 4),
+    "fhtdp_cnn_relu_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_longlong, ctypes.c_void_p]),
+    "fhtdp_cnn_conv3x3_wgrad": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
+                                + [ctypes.c_void_p] * 4),
+    "fhtdp_cnn_band_head": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4
+                            + [ctypes.c_void_p, ctypes.c_float] + [ctypes.c_void_p] * 4),
+    "fhtdp_cnn_adam": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_float] * 4
+                       + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_cnn_to_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p]),
+    "fhtdp_cnn_bin_windows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -80,7 +99,7 @@ class Image(ctypes.Structure):
     _fields_ = [("img", ctypes.c_void_p), ("h", ctypes.c_int), ("w", ctypes.c_int),
                 ("pitch", ctypes.c_int), ("k", ctypes.c_int), ("B", ctypes.c_int),
                 ("x_out", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
-                ("score_out", ctypes.c_void_p)]
+                ("score_out", ctypes.c_void_p), ("d_window", ctypes.c_void_p)]
 
 
 def load():
@@ -213,10 +232,12 @@ class BatchPlan:
 
     ``images`` are 2-D CUDA tensors, ``ks`` and ``Bs`` their band counts and
     bend limits.  Outputs ``x[i]``, ``d[i]``, ``score[i]`` are allocated here,
-    or are the rows of ``out = (X, D, S)``; ``run()`` enqueues the whole batch
-    (one memset, one kernel) and may be captured in a CUDA graph."""
+    or are the rows of ``out = (X, D, S)``; ``windows[i]`` (optional) is a
+    device int32 [k][2] tensor of allowed displacements per band (pruned DP).
+    ``run()`` enqueues the whole batch (one memset, one kernel) and may be
+    captured in a CUDA graph."""
 
-    def __init__(self, images, ks, Bs, ws=None, stream=None, out=None):
+    def __init__(self, images, ks, Bs, ws=None, stream=None, out=None, windows=None):
         torch = _torch()
         if not images:
             raise ValueError("empty batch")
@@ -234,8 +255,10 @@ class BatchPlan:
             self.x.append(x)
             self.d.append(d)
             self.score.append(sc)
+            win = windows[i] if windows is not None else None
             arr[i] = Image(img.data_ptr(), h, w, pitch, k, B, x.data_ptr(), d.data_ptr(),
-                           sc.data_ptr())
+                           sc.data_ptr(), win.data_ptr() if win is not None else None)
+        self.windows = windows
         self._arr = arr
         handle = ctypes.c_void_p()
         _check(lib().fhtdp_batch_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(images),

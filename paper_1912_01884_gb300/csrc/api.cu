@@ -6,6 +6,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "cnn.cuh"
 #include "engine.cuh"
 
 namespace fhtdp {
@@ -163,6 +164,80 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
     return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Learned window proposal.
+int fhtdp_cnn_downsample4(const uint8_t *img, int n, int h, int w, void *out,
+                          cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!img || !out || n < 1 || h < 4 || w < 4 || h % 4 || w % 4)
+        return set_error(FHTDP_EINVAL, "downsample: need h, w multiples of 4 and non-null buffers");
+    return cnn_downsample4(img, n, h, w, out, stream);
+}
+
+int fhtdp_cnn_conv3x3(const void *x, int cin, int n, int h, int w, int dil, const void *wt,
+                      const float *bias, int relu, void *y, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!x || !wt || !y || n < 1 || (cin != 1 && cin != 32) || !cnn_shape_ok(h, w, dil))
+        return set_error(FHTDP_EINVAL,
+                         "conv3x3: need cin 1 or 32, w a multiple of 64, 1 <= dil <= 8");
+    return cnn_conv3x3(x, cin, n, h, w, dil, wt, bias, relu, y, stream);
+}
+
+int fhtdp_cnn_conv3x3_dgrad(const void *dz, int n, int h, int w, int dil, const void *wt,
+                            void *wflip, void *dx, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!dz || !wt || !wflip || !dx || n < 1 || !cnn_shape_ok(h, w, dil))
+        return set_error(FHTDP_EINVAL, "conv3x3_dgrad: bad arguments");
+    int st = cnn_flip_transpose(wt, wflip, stream);
+    if (st) return st;
+    return cnn_conv3x3(dz, 32, n, h, w, dil, wflip, nullptr, 0, dx, stream);
+}
+
+int fhtdp_cnn_relu_backward(const void *y, void *dy, long long count, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!y || !dy || count < 0) return set_error(FHTDP_EINVAL, "relu_backward: bad arguments");
+    return cnn_relu_backward(y, dy, count, stream);
+}
+
+int fhtdp_cnn_conv3x3_wgrad(const void *x, int cin, int n, int h, int w, int dil, const void *dz,
+                            float *dw, float *db, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!x || !dz || !dw || n < 1 || (cin != 1 && cin != 32) || !cnn_shape_ok(h, w, dil))
+        return set_error(FHTDP_EINVAL, "conv3x3_wgrad: bad arguments");
+    return cnn_wgrad(x, cin, n, h, w, dil, dz, dw, db, stream);
+}
+
+int fhtdp_cnn_band_head(const void *logits, int n, int h, int w, int bands,
+                        const int32_t *labels, float scale, void *dlogits, float *loss,
+                        int32_t *pred, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!logits || n < 1 || bands < 1 || h % bands || w < 1)
+        return set_error(FHTDP_EINVAL, "band_head: bad arguments");
+    return cnn_band_head(logits, n, h, w, bands, labels, scale, dlogits, loss, pred, stream);
+}
+
+int fhtdp_cnn_adam(float *p, float *m, float *v, const float *g, int count, float lr, float b1,
+                   float b2, float eps, int step, void *wb, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!p || !m || !v || !g || count < 1 || step < 1)
+        return set_error(FHTDP_EINVAL, "adam: bad arguments");
+    return cnn_adam(p, m, v, g, count, lr, b1, b2, eps, step, wb, stream);
+}
+
+int fhtdp_cnn_to_bf16(const float *src, void *dst, int count, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!src || !dst || count < 1) return set_error(FHTDP_EINVAL, "to_bf16: bad arguments");
+    return cnn_to_bf16(src, dst, count, stream);
+}
+
+int fhtdp_cnn_bin_windows(const int32_t *pred, int count, int n, int margin, int32_t *win,
+                          cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!pred || !win || count < 1 || n < 1 || margin < 0)
+        return set_error(FHTDP_EINVAL, "bin_windows: bad arguments");
+    return cnn_bin_windows(pred, count, n, margin, win, stream);
 }
 
 void fhtdp_debug_inject(int band, int tile, long long wait_cycles) {

@@ -63,6 +63,7 @@ struct ImgDesc {
     int *done;                // band-0 tiles finished
     int32_t *x_out, *d_out;
     void *score_out;
+    const int32_t *win;       // optional [k][2]: allowed displacements of each band
 };
 
 struct Ctl {
@@ -207,9 +208,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 // 2-D tile (x, y) of a tensor map into shared memory.
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
@@ -511,12 +509,30 @@ __device__ __forceinline__ void window_two_pass(int c0, int c1, int B, int a, in
     }
 }
 
+// Allowed displacements of a band: [lo, hi] (the whole range unless the
+// image carries windows, as for the pruned DP of the learned proposal).
+__device__ __forceinline__ void band_window(const ImgDesc &im, int band, int *lo, int *hi) {
+    int a = -(im.n - 1), b = im.n - 1;
+    if (im.win) {
+        a = max(a, __ldg(im.win + 2 * band));
+        b = min(b, __ldg(im.win + 2 * band + 1));
+    }
+    *lo = a;
+    *hi = b;
+}
+
 // Eq. 5: the polyline from the best top point, one backpointer per band.
 template <typename Acc>
 __device__ void readback(const ImgDesc &im, const LaunchArgs &args) {
     const int n = im.n, D = 2 * n - 1;
     __threadfence();
     const unsigned long long key = atomicAdd(im.best, 0ull);
+    if (key == 0) {   // no admissible polyline inside the windows
+        *(Acc *)im.score_out = Dead<Acc>::value();
+        for (int i = 0; i <= im.k; ++i) im.x_out[i] = -1;
+        for (int i = 0; i < im.k; ++i) im.d_out[i] = 0;
+        return;
+    }
     const unsigned lin = 0xffffffffu - (unsigned)(key & 0xffffffffu);
     int xx = (int)(lin >> 9), d = (int)(lin & 511) - (n - 1);
     im.x_out[0] = xx;
@@ -855,6 +871,8 @@ struct U8Path {
         const int n = im.n, T = kTile, D = 2 * n - 1;
         const bool last = band == im.k - 1;
         const Acc dead = Dead<Acc>::value();
+        int wlo, whi;
+        band_window(im, band, &wlo, &whi);
         unsigned long long best = 0;
         if (band != 0) {
             for (int idx = threadIdx.x; idx < 2 * kPad * (T / 4); idx += kThreads) {
@@ -883,7 +901,7 @@ struct U8Path {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int x = xp + j;
-                const bool ok = x < im.w && x + s < im.w;
+                const bool ok = x < im.w && x + s < im.w && s >= wlo && s <= whi;
                 // A window maximum below zero marks a dead continuation
                 // (uint8 sums are never negative).
                 const int m = mps[j];
@@ -891,7 +909,7 @@ struct U8Path {
                                           : (m < 0 ? dead : (int)(hws[j] & 0xffffu) + m);
                 // "-" half of word j: column x0 + T - 1 - u0 - j, displacement -s.
                 const int xm = x0 + T - 1 - u0 - j;
-                const bool okm = s > 0 && xm < im.w && xm - s >= 0;
+                const bool okm = s > 0 && xm < im.w && xm - s >= 0 && -s >= wlo && -s <= whi;
                 const int mmv = mms[3 - j];
                 vm[j] = !okm ? dead : last ? (int)(hws[j] >> 16)
                                            : (mmv < 0 ? dead : (int)(hws[j] >> 16) + mmv);
@@ -988,7 +1006,11 @@ struct U8Path {
                     mcol[c * mstep] = mk >> 9;
                     bcol[c * bstep] = (uint8_t)(~mk & 511);
                 };
-                const int c0 = lo + (qd * D) / kQ, c1 = lo + ((qd + 1) * D) / kQ - 1;
+                // Only the consumer band's allowed displacements are needed.
+                int clo, chi;
+                band_window(im, band - 1, &clo, &chi);
+                const int c0 = max(lo + (qd * D) / kQ, clo);
+                const int c1 = min(lo + ((qd + 1) * D) / kQ - 1, chi);
                 if (c0 <= c1 && x < im.w) {
                     const Key dk = KO::dead();
                     switch (B) {
@@ -1022,7 +1044,10 @@ struct U8Path {
                 const int P0 = lo + (round * D) / kRounds;
                 const int P1 = lo + ((round + 1) * D) / kRounds - 1;
                 const int span = P1 - P0 + 1;
-                const int c0 = P0 + (qd * span) / kQ, c1 = P0 + ((qd + 1) * span) / kQ - 1;
+                int clo, chi;
+            band_window(im, band - 1, &clo, &chi);
+            const int c0 = max(P0 + (qd * span) / kQ, clo);
+            const int c1 = min(P0 + ((qd + 1) * span) / kQ - 1, chi);
                 const int srow0 = P0 - B;   // S(e) at row e - srow0
                 auto sput = [&](int e, Key v) { S[(size_t)(e - srow0) * T + u] = v; };
                 auto sget = [&](int e) { return S[(size_t)(e - srow0) * T + u]; };
@@ -1109,9 +1134,9 @@ struct WidePath {
     }
 
     __device__ static Acc link_value(Acc h, const ImgDesc &im, int band, const Acc *mprev, int x,
-                                     int e) {
+                                     int e, int wlo, int whi) {
         const Acc dead = Dead<Acc>::value();
-        const bool ok = x < im.w && x + e >= 0 && x + e < im.w;
+        const bool ok = x < im.w && x + e >= 0 && x + e < im.w && e >= wlo && e <= whi;
         if (!ok) return dead;
         if (band == im.k - 1) return h;
         const Acc m = __ldcg(mprev + (size_t)(e + im.n - 1) * im.mpitch + kMOff + x);
@@ -1121,14 +1146,17 @@ struct WidePath {
     __device__ static unsigned long long form_v(Acc *F, Acc *Hp, const ImgDesc &im, int band,
                                                 const Acc *mprev, int x0) {
         const int n = im.n, T = kTile, pitch = fpitch(n);
+        int wlo, whi;
+        band_window(im, band, &wlo, &whi);
         unsigned long long best = 0;
 #pragma unroll 4
         for (int idx = threadIdx.x; idx < n * T; idx += kThreads) {
             const int slot = idx / T, up = idx - slot * T;
             const int s = brev(slot, im.log2n);
             const int xp = x0 + up, xm = x0 + T - 1 - up;
-            const Acc vp = link_value(Hp[idx], im, band, mprev, xp, s);
-            const Acc vm = s > 0 ? link_value(F[(size_t)slot * pitch + up], im, band, mprev, xm, -s)
+            const Acc vp = link_value(Hp[idx], im, band, mprev, xp, s, wlo, whi);
+            const Acc vm = s > 0 ? link_value(F[(size_t)slot * pitch + up], im, band, mprev, xm, -s,
+                                              wlo, whi)
                                  : Dead<Acc>::value();
             if (band == 0) {
                 const Acc dead = Dead<Acc>::value();
@@ -1190,7 +1218,10 @@ struct WidePath {
             const int P0 = lo + (round * D) / kRounds;
             const int P1 = lo + ((round + 1) * D) / kRounds - 1;
             const int span = P1 - P0 + 1;
-            const int c0 = P0 + (qd * span) / kQ, c1 = P0 + ((qd + 1) * span) / kQ - 1;
+            int clo, chi;
+            band_window(im, band - 1, &clo, &chi);
+            const int c0 = max(P0 + (qd * span) / kQ, clo);
+            const int c1 = min(P0 + ((qd + 1) * span) / kQ - 1, chi);
             const int srow0 = P0 - B;
             auto sput = [&](int e, Key v) { *s_at(e - srow0) = v; };
             auto sget = [&](int e) { return *s_at(e - srow0); };
@@ -1370,6 +1401,7 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     im.x_out = p.io.x_out;
     im.d_out = p.io.d_out;
     im.score_out = p.io.score_out;
+    im.win = p.io.d_window;
     return im;
 }
 
@@ -1587,6 +1619,13 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
                              i, io.h, io.w, io.pitch, io.k, io.B);
         }
         ImgPlan p = single_plan(io.img, io.pitch, s, io.B, io.x_out, io.d_out, io.score_out);
+        p.io.d_window = io.d_window;
+        if (io.d_window && s.n > kMaxBandFused) {
+            delete plan;
+            return set_error(FHTDP_EINVAL,
+                             "image %d: displacement windows need bands of at most %d rows", i,
+                             kMaxBandFused);
+        }
         if (s.n > kMaxBandFused)
             plan->separate.push_back(p);
         else

@@ -257,3 +257,27 @@ def test_float32_decisions_score_within_tolerance_of_float64(seed):
     assert abs(s32 - s64) <= 1e-5 * abs(s64)
     # the float32 choice is optimal to within the tolerance in exact arithmetic
     assert abs(oracle.path_score(wl.img, wl.k, x32[0], d32) - s64) <= 1e-5 * abs(s64)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_windowed_dp_equals_windowed_brute_force(seed):
+    """The DP restricted to per-band displacement windows (the pruned DP of
+    the learned proposal) against brute force over the polylines inside the
+    windows, including windows that leave no admissible polyline."""
+    rng = np.random.default_rng(50 + seed)
+    h, w, k = 16, 7, 4
+    n = h // k
+    img = rng.integers(0, 4, (h, w)).astype(np.float64)
+    for B in (0, 1, 3, 6):
+        for _ in range(6):
+            lo = rng.integers(-(n - 1), n, k)
+            hi = lo + rng.integers(0, 4, k)
+            win = np.stack([lo, hi], axis=1)
+            xb, db, sb, _ = oracle.brute_windowed(img, k, B, win)
+            x, d, s = oracle.detect_windowed(img, k, B, win)
+            assert s == sb and list(x) == list(xb) and list(d) == list(db), (B, win)
+            if s != -np.inf:
+                assert all(win[i, 0] <= d[i] <= win[i, 1] for i in range(k))
+    # the full window is the unrestricted method
+    full = np.tile([-(n - 1), n - 1], (k, 1))
+    assert oracle.detect_windowed(img, k, 2, full)[2] == oracle.detect(img, k, 2)[2]
