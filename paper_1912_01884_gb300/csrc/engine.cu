@@ -50,7 +50,9 @@ constexpr int kFastB = 16;             // largest bend kept entirely in register
 
 struct ImgDesc {
     CUtensorMap tmap;         // 2-D map of the image (uint8 images), box 128 x n
+    CUtensorMap mtmap;        // 2-D map of both M buffers, [2D][mpitch] int32, box 128 x D
     int use_tma;              // strip loads through tmap
+    int use_mtma;             // M tiles through mtmap (uint8 images)
     const void *img;
     long long pitch;          // row stride in elements
     int h, w, k, n, log2n, B, tiles;
@@ -125,7 +127,7 @@ __device__ __forceinline__ uint32_t to_bits(float v) { return __float_as_uint(v)
 template <typename Acc, typename Key>
 struct KeyOps;
 template <>
-struct KeyOps<int32_t, int32_t> {   // non-negative values below 2^22
+struct KeyOps<int32_t, int32_t> {   // non-negative values below 2^22; dead keys < 0
     __device__ static int32_t dead() { return INT32_MIN; }
     __device__ static int32_t make(int32_t v, int e) { return (v << 9) | (511 - e); }
     __device__ static int32_t value(int32_t k) { return k >> 9; }
@@ -209,6 +211,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Orders global data observed through the generic proxy (M published by
+// other CTAs) before this thread's later TMA reads of it.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 // 2-D tile (x, y) of a tensor map into shared memory.
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             uint64_t *bar) {
@@ -228,6 +235,8 @@ struct NextItem {
 struct Pipe {
     uint64_t *bar;        // strip barrier
     uint32_t phase;       // parity of its next completion
+    uint64_t *mbar;       // M tile barrier
+    uint32_t mphase;      // parity of its next completion
     NextItem *next;       // shared: the CTA's next item
 };
 
@@ -578,7 +587,10 @@ __device__ __forceinline__ unsigned long long argmax_key(uint32_t ordv, int x, i
 }
 
 // Waits for the three band+1 tiles whose window maxima a tile of `band` reads.
-__device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
+// `after` runs on thread 0 once the flags are seen (or the wait gave up).
+template <typename After>
+__device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args,
+                          After after) {
     if (band >= im.k - 1) return;
     if (threadIdx.x == 0) {
         bool ok = true;
@@ -587,18 +599,29 @@ __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArg
                            args.wait_cycles);
         if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
         __threadfence();
+        after();
     }
     __syncthreads();
 }
+__device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
+    wait_deps(im, band, tile, args, [] {});
+}
 
-__device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
+// `before` runs on thread 0 after the CTA barrier, before the flag.
+template <typename Before>
+__device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args,
+                        Before before) {
     __syncthreads();
+    if (threadIdx.x == 0) before();
     const ImgDesc &first = args.many ? args.many[0] : args.one;
     if (band == args.skip_band && tile == args.skip_tile && im.flags == first.flags) return;
     if (threadIdx.x == 0) {
         __threadfence();
         st_release(im.flags + (size_t)band * im.tiles + tile, 1);
     }
+}
+__device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
+    publish(im, band, tile, args, [] {});
 }
 
 // Stores M_b(x, c) (skewed so that the consumer reads M(x + d, d) as row d,
@@ -865,36 +888,104 @@ struct U8Path {
     }
 
     // V rows: V(e) of tile column u at Vn[(e + n - 1 + kPad) * T + u].
+    // M buffer words.  With 32-bit keys a window maximum is kept as its key
+    // with the index bits cleared, M' = value << 9 (negative when dead), so
+    // that a V key is M' + (H << 9 | index); 64-bit keys keep the value.
+    __device__ static int32_t mstore(Key mk) {
+        if constexpr (sizeof(Key) == 4) return mk & ~511;
+        else return mk < 0 ? Dead<int32_t>::value() : KO::value(mk);
+    }
+    __device__ static int32_t mval(int32_t w) {
+        if constexpr (sizeof(Key) == 4) return w >> 9;
+        else return w;
+    }
+    // The kPad dead rows above and below the V rows.
+    __device__ static void dead_pad(int32_t *Vn, int n) {
+        const int T = kTile, D = 2 * n - 1;
+        const int32_t dead = Dead<int32_t>::value();
+        for (int idx = threadIdx.x; idx < 2 * kPad * (T / 4); idx += kThreads) {
+            const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
+            const int row = r < kPad ? r : r + D;
+            *(int4 *)&Vn[row * T + u0] = make_int4(dead, dead, dead, dead);
+        }
+    }
+    // V keys of an interior tile, in place over the M' tile copied by TMA
+    // (none in the last band): V key(c) = M'(c) + (H(c) << 9 | 511 - (c + n - 1)).
+    // A dead M' (negative) gives a negative key.
+    __device__ static void form_v_interior(int32_t *Vn, const uint32_t *Hc, int n, bool last) {
+        const int T = kTile, kc = 512 - n;   // 511 - (c + n - 1) = kc - c
+        for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
+            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            const uint4 hw = *(const uint4 *)&Hc[s * T + u0];
+            int4 *pp = (int4 *)&Vn[(s + n - 1 + kPad) * T + u0];
+            int4 *pm = (int4 *)&Vn[(n - 1 - s + kPad) * T + (T - 4 - u0)];
+            int4 mp = make_int4(0, 0, 0, 0), mm = mp;
+            if (!last) {
+                mp = *pp;
+                if (s > 0) mm = *pm;
+            }
+            const int kp = kc - s, km = kc + s;
+            *pp = make_int4(mp.x + (int)(hw.x & 0xffffu) * 512 + kp,
+                            mp.y + (int)(hw.y & 0xffffu) * 512 + kp,
+                            mp.z + (int)(hw.z & 0xffffu) * 512 + kp,
+                            mp.w + (int)(hw.w & 0xffffu) * 512 + kp);
+            // "-" half of word j is column T - 1 - u0 - j, at pm lane 3 - j.
+            if (s > 0)
+                *pm = make_int4(mm.x + (int)(hw.w >> 16) * 512 + km,
+                                mm.y + (int)(hw.z >> 16) * 512 + km,
+                                mm.z + (int)(hw.y >> 16) * 512 + km,
+                                mm.w + (int)(hw.x >> 16) * 512 + km);
+        }
+    }
+    // With msmem the M tile was copied by TMA into the V rows (row e of M at
+    // V row e + kPad), and V is formed in place; otherwise M is read from L2.
     __device__ static unsigned long long form_v(int32_t *Vn, const uint32_t *Hc,
                                                 const ImgDesc &im, int band, int x0,
-                                                const int32_t *mprev) {
-        const int n = im.n, T = kTile, D = 2 * n - 1;
+                                                const int32_t *mprev, bool msmem) {
+        const int n = im.n, T = kTile;
         const bool last = band == im.k - 1;
         const Acc dead = Dead<Acc>::value();
         int wlo, whi;
         band_window(im, band, &wlo, &whi);
         unsigned long long best = 0;
-        if (band != 0) {
-            for (int idx = threadIdx.x; idx < 2 * kPad * (T / 4); idx += kThreads) {
-                const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
-                const int row = r < kPad ? r : r - kPad + kPad + D;
-                *(int4 *)&Vn[row * T + u0] = make_int4(dead, dead, dead, dead);
+        // The M loads of a batch of iterations are issued before any of its
+        // shared stores, so their L2 round trips overlap.
+        constexpr int kIt = kMaxBandFused * (kTile / 4) / kThreads;
+        constexpr int kLB = 4;
+        const int tasks = n * (T / 4);
+#pragma unroll 1
+        for (int b0 = 0; b0 < kIt; b0 += kLB) {
+        if (threadIdx.x + b0 * kThreads >= tasks) break;
+        int4 mpa[kLB], mma[kLB];
+#pragma unroll
+        for (int i = 0; i < kLB; ++i) {
+            const int idx = threadIdx.x + (b0 + i) * kThreads;
+            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            mpa[i] = make_int4(0, 0, 0, 0);
+            mma[i] = mpa[i];
+            if (!last && idx < tasks) {
+                if (msmem) {
+                    mpa[i] = *(const int4 *)&Vn[(s + n - 1 + kPad) * T + u0];
+                    if (s > 0) mma[i] = *(const int4 *)&Vn[(n - 1 - s + kPad) * T + T - 4 - u0];
+                } else {
+                    mpa[i] = __ldcg((const int4 *)(mprev + (size_t)(s + n - 1) * im.mpitch +
+                                                   kMOff + x0 + u0));
+                    if (s > 0)
+                        mma[i] = __ldcg((const int4 *)(mprev + (size_t)(n - 1 - s) * im.mpitch +
+                                                       kMOff + x0 + T - 4 - u0));
+                }
             }
         }
-#pragma unroll 4
-        for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
+#pragma unroll
+        for (int it = 0; it < kLB; ++it) {
+            const int idx = threadIdx.x + (b0 + it) * kThreads;
+            if (idx >= tasks) break;
             const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
             const uint4 hw = *(const uint4 *)&Hc[s * T + u0];
             const uint32_t hws[4] = {hw.x, hw.y, hw.z, hw.w};
             // "+" half: column x0 + u0 + j, displacement +s.
             const int xp = x0 + u0;
-            int4 mp = make_int4(0, 0, 0, 0), mm = mp;
-            if (!last) {
-                mp = __ldcg((const int4 *)(mprev + (size_t)(s + n - 1) * im.mpitch + kMOff + xp));
-                if (s > 0)
-                    mm = __ldcg((const int4 *)(mprev + (size_t)(n - 1 - s) * im.mpitch + kMOff +
-                                               x0 + T - 4 - u0));
-            }
+            const int4 mp = mpa[it], mm = mma[it];
             const int mps[4] = {mp.x, mp.y, mp.z, mp.w};
             const int mms[4] = {mm.x, mm.y, mm.z, mm.w};   // column x0 + T - 4 - u0 + t
             int vp[4], vm[4];
@@ -904,13 +995,13 @@ struct U8Path {
                 const bool ok = x < im.w && x + s < im.w && s >= wlo && s <= whi;
                 // A window maximum below zero marks a dead continuation
                 // (uint8 sums are never negative).
-                const int m = mps[j];
+                const int m = mval(mps[j]);
                 vp[j] = !ok ? dead : last ? (int)(hws[j] & 0xffffu)
                                           : (m < 0 ? dead : (int)(hws[j] & 0xffffu) + m);
                 // "-" half of word j: column x0 + T - 1 - u0 - j, displacement -s.
                 const int xm = x0 + T - 1 - u0 - j;
                 const bool okm = s > 0 && xm < im.w && xm - s >= 0 && -s >= wlo && -s <= whi;
-                const int mmv = mms[3 - j];
+                const int mmv = mval(mms[3 - j]);
                 vm[j] = !okm ? dead : last ? (int)(hws[j] >> 16)
                                            : (mmv < 0 ? dead : (int)(hws[j] >> 16) + mmv);
             }
@@ -943,6 +1034,7 @@ struct U8Path {
                         make_int4(vm[3], vm[2], vm[1], vm[0]);
             }
         }
+        }
         return best;
     }
 
@@ -964,6 +1056,7 @@ struct U8Path {
         pipe.next->prefetched = pf;
     }
 
+
     __device__ static bool process(const ImgDesc &im, int band, int tile, unsigned char *smem,
                                    const LaunchArgs &args, Pipe &pipe, bool prefetched) {
         const int n = im.n, T = kTile, D = 2 * n - 1;
@@ -972,17 +1065,43 @@ struct U8Path {
         int32_t *Vn = (int32_t *)smem;
         uint32_t *Hc = (uint32_t *)(smem + hc_offset());
         if (!fht(F, Hc, im, band, x0, pipe, prefetched, args)) return false;
-        wait_deps(im, band, tile, args);
+        // The M tile of the band below comes by TMA into the V rows once its
+        // producers have published (F is free: the FHT ended in Hc).
+        const bool msmem = im.use_mtma && band < im.k - 1;
+        wait_deps(im, band, tile, args, [&] {
+            if (!msmem) return;
+            fence_proxy_async_global();
+            fence_proxy_async_smem();
+            mbar_expect_tx(pipe.mbar, (uint32_t)(T * D * 4));
+            tma_load_2d(Vn + kPad * T, &im.mtmap, kMOff + x0, ((band + 1) & 1) * D, pipe.mbar);
+        });
+        if (band != 0) dead_pad(Vn, n);
+        if (msmem) {
+            const bool ok = mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles);
+            pipe.mphase ^= 1u;
+            if (!ok) {
+                if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                return false;
+            }
+        }
         const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
         Acc *mnext = (Acc *)im.mbuf[band & 1];
-        const unsigned long long best = form_v(Vn, Hc, im, band, x0, mprev);
         const bool fast = sizeof(Key) == 4 && im.B <= kFastB;
+        // Interior tiles (every x - s and x + s of the tile inside the image)
+        // of a band without windows need no masks.
+        const bool interior = sizeof(Key) == 4 && band != 0 && !im.win && (msmem || band == im.k - 1) &&
+                              x0 >= n - 1 && x0 + T + n - 2 < im.w;
+        unsigned long long best = 0;
+        if (interior)
+            form_v_interior(Vn, Hc, n, band == im.k - 1);
+        else
+            best = form_v(Vn, Hc, im, band, x0, mprev, msmem);
         if (band == 0) {
             finish_band0<Acc>(best, im, args, [&] { take_next(args, pipe, Hc, true); });
             return true;
         }
         __syncthreads();
-        // Hc is free from here on unless the window needs it for S.
+        // Hc is free from here on unless the window reads H or S from it.
         if (threadIdx.x == 0) take_next(args, pipe, Hc, fast);
 
         const int u = threadIdx.x % T, qd = threadIdx.x / T;
@@ -998,12 +1117,12 @@ struct U8Path {
                 // below c0 - B >= lo - kPad, and reads above hi are dead.
                 const int32_t *kcol = col + (n - 1 + kPad) * T;
                 auto vkey = [&](int e) -> Key { return e > hi ? KO::dead() : kcol[e * T]; };
-                // M(x, c) = key >> 9 (negative when dead), bp = its index.
+                // M'(x, c) = key & ~511 (negative when dead), bp = its index.
                 Acc *mcol = mnext + (size_t)(n - 1) * im.mpitch + kMOff + x;
                 uint8_t *bcol = bp + (size_t)(n - 1) * im.w + x;
                 const long long mstep = im.mpitch - 1, bstep = im.w;
                 auto emit = [&](int c, Key mk) {
-                    mcol[c * mstep] = mk >> 9;
+                    mcol[c * mstep] = mk & ~511;
                     bcol[c * bstep] = (uint8_t)(~mk & 511);
                 };
                 // Only the consumer band's allowed displacements are needed.
@@ -1031,7 +1150,10 @@ struct U8Path {
                 return true;
             }
         }
-        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
+        auto emit = [&](int c, Key mk) {
+            mnext[(size_t)(c + n - 1) * im.mpitch + kMOff + x - c] = mstore(mk);
+            bp[(size_t)(c + n - 1) * im.w + x] = (uint8_t)(mk < 0 ? 0 : KO::index(mk));
+        };
         {
             auto vkey = [&](int e) -> Key {
                 if (e < lo || e > hi) return KO::dead();
@@ -1251,15 +1373,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     using P = typename PathOf<In, Acc, Key>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(8) uint64_t s_mbar;
     __shared__ NextItem s_next;
     if (threadIdx.x == 0) {
         mbar_init(&s_bar, 1);
+        mbar_init(&s_mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_next.item = atomicAdd(&args.ctl->queue, 1);
         s_next.prefetched = 0;
     }
     __syncthreads();
-    Pipe pipe{&s_bar, 0u, &s_next};
+    Pipe pipe{&s_bar, 0u, &s_mbar, 0u, &s_next};
     for (;;) {
         const long long item = s_next.item;
         const bool prefetched = s_next.prefetched != 0;
@@ -1328,10 +1452,9 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
     L.order_bytes = with_table ? align_up(sizeof(Item) * (size_t)items, 256) : 0;
     size_t d = 0;
     for (auto &p : imgs) {
-        p.m0 = d;
-        d = align_up(d + (size_t)p.s.D * p.mpitch * 4, 256);
-        p.m1 = d;
-        d = align_up(d + (size_t)p.s.D * p.mpitch * 4, 256);
+        p.m0 = d;   // the two M buffers are adjacent: one tensor map covers both
+        p.m1 = d + (size_t)p.s.D * p.mpitch * 4;
+        d = align_up(p.m1 + (size_t)p.s.D * p.mpitch * 4, 256);
         p.bp = d;
         d = align_up(d + (size_t)p.s.k * p.s.D * p.s.w, 256);
     }
@@ -1376,10 +1499,27 @@ bool encode_strip_map(CUtensorMap *map, const void *img, int h, int w, long long
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D int32 tensor map of an image's two adjacent M buffers ([2D][mpitch]),
+// box of 128 columns x D rows: one copy brings a tile's whole M_{b+1}.
+bool encode_m_map(CUtensorMap *map, void *m0, int D, int mpitch) {
+    if ((uintptr_t)m0 % 16 != 0 || mpitch % 4 != 0 || D > 256) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)mpitch, (cuuint64_t)(2 * D)};
+    cuuint64_t strides[1] = {(cuuint64_t)mpitch * 4};
+    cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)D};
+    cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, m0, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     ImgDesc im{};
     im.use_tma = dtype == FHTDP_U8 &&
                  encode_strip_map(&im.tmap, p.io.img, p.s.h, p.s.w, p.io.pitch, p.s.n);
+    im.use_mtma = dtype == FHTDP_U8 && p.s.n <= kMaxBandFused && ws &&
+                  encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch);
     im.img = p.io.img;
     im.pitch = p.io.pitch;
     im.h = p.s.h;
@@ -1445,7 +1585,9 @@ int launch_kernel(const LaunchArgs &args, int max_n, cudaStream_t stream) {
 int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, cudaStream_t stream) {
     switch (dtype) {
         case FHTDP_U8:
-            if (255LL * max_h < (1LL << 22))
+            // 32-bit keys: values below 2^22, and dead keys (negative) that
+            // take on at most 512 * (255 h + k) over the bands stay negative.
+            if (256LL * max_h < (1LL << 22))
                 return launch_kernel<uint8_t, int32_t, int32_t>(args, max_n, stream);
             return launch_kernel<uint8_t, int32_t, long long>(args, max_n, stream);
         case FHTDP_I32:
@@ -1543,15 +1685,21 @@ struct BatchPlan {
 // tile.  Every item therefore comes after the band+1 tiles it waits for, so
 // the queue cannot deadlock, and the band chains of a whole group advance
 // together instead of one image at a time.  Groups bound the number of
-// images in flight, so their M buffers stay in L2.
+// images in flight, so their M buffers stay in L2.  The batch is split into
+// round(total / target) groups of about equal width, so that no narrow
+// remainder group runs its band chain alone at the end.
 std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target) {
     std::vector<Item> order;
+    long long total = 0;
+    for (const ImgPlan &p : imgs) total += p.tiles;
+    const long long groups = std::max(1LL, (total + target / 2) / std::max(1LL, target));
     size_t first = 0;
-    while (first < imgs.size()) {
+    long long done = 0;
+    for (long long g = 1; first < imgs.size(); ++g) {
+        const long long goal = total * g / groups;
         size_t last = first;
-        long long per_level = 0;
-        while (last < imgs.size() && (last == first || per_level < target)) {
-            per_level += imgs[last].tiles;
+        while (last < imgs.size() && (last == first || done + imgs[last].tiles / 2 < goal)) {
+            done += imgs[last].tiles;
             ++last;
         }
         int levels = 0;
@@ -1637,7 +1785,7 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
     for (auto &p : plan->separate) sep = std::max(sep, engine_workspace_bytes(dtype, p.s, p.io.B));
     plan->separate_off = align_up(plan->L.total, 256);
     if (sep) plan->L.total = plan->separate_off + sep;
-    plan->order = queue_order(plan->imgs, (long long)num_sms() * 3 / 2);
+    plan->order = queue_order(plan->imgs, (long long)num_sms());
     *out = plan;
     return FHTDP_OK;
 }
