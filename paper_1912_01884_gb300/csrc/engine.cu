@@ -294,13 +294,17 @@ __device__ __forceinline__ void merge4(const uint4 &a4, const uint4 &b0, const u
     ob.w = to_bits(a[3] + b[Q + 4]);
 }
 
+// With `out`, the last level writes shift s to row s of out (pitch T)
+// instead of in place.
 template <typename W>
-__device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first = 1) {
+__device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first = 1,
+                           W *out = nullptr) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = kThreads / 32;
     for (int l = first; l <= log2n; ++l) {
         const int m = 1 << l, half = m >> 1;
         const int width = T + n - m;
+        const bool to_out = out && l == log2n;
         for (int p = warp; p < n / 2; p += nwarps) {
             const int j = p >> (l - 1), r = p & (half - 1);
             const int sp = brev(r, l - 1);
@@ -322,6 +326,13 @@ __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first =
                         case 2: merge4<W, 2>(a4, b0, b1, oa, ob); break;
                         default: merge4<W, 3>(a4, b0, b1, oa, ob); break;
                     }
+                }
+                if (to_out) {   // one sub-band: shifts 2sp, 2sp+1 at width T
+                    if (live) {
+                        *(uint4 *)&out[(size_t)(2 * sp) * T + u] = oa;
+                        *(uint4 *)&out[(size_t)(2 * sp + 1) * T + u] = ob;
+                    }
+                    continue;
                 }
                 __syncwarp();
                 if (live) {
@@ -387,9 +398,10 @@ __device__ __forceinline__ void merge4x4(const uint4 &j0, const uint4 *j1, const
     for (int r = 0; r < 4; ++r) out[r] = make_uint4(o[r][0], o[r][1], o[r][2], o[r][3]);
 }
 
-// Levels l+1 and l+2 (sub-bands of m = 2^l rows merged into 4m rows).
+// Levels l+1 and l+2 (sub-bands of m = 2^l rows merged into 4m rows).  With
+// `out` (only when 4m = n) shift s goes to row s of out (pitch T).
 template <typename W>
-__device__ void fht_radix4(W *F, int pitch, int n, int l, int T) {
+__device__ void fht_radix4(W *F, int pitch, int n, int l, int T, W *out = nullptr) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = kThreads / 32;
     const int m = 1 << l;
@@ -407,7 +419,7 @@ __device__ void fht_radix4(W *F, int pitch, int n, int l, int T) {
         for (int u0 = 0; u0 < width; u0 += 128) {
             const int u = u0 + 4 * lane;
             const bool live = u < width;
-            uint4 out[4];
+            uint4 o4[4];
             if (live) {
                 const uint4 j0 = *(const uint4 *)&J[0][u];
                 const uint4 j1[2] = {*(const uint4 *)&B1[u], *(const uint4 *)&B1[u + 4]};
@@ -415,18 +427,25 @@ __device__ void fht_radix4(W *F, int pitch, int n, int l, int T) {
                 const uint4 j3[3] = {*(const uint4 *)&B3[u], *(const uint4 *)&B3[u + 4],
                                      *(const uint4 *)&B3[u + 8]};
                 switch (o) {
-                    case 0: merge4x4<W, 0, 0, 0>(j0, j1, j2, j3, out); break;
-                    case 1: merge4x4<W, 1, 2, 3>(j0, j1, j2, j3, out); break;
-                    case 2: merge4x4<W, 2, 0, 2>(j0, j1, j2, j3, out); break;
-                    default: merge4x4<W, 3, 2, 1>(j0, j1, j2, j3, out); break;
+                    case 0: merge4x4<W, 0, 0, 0>(j0, j1, j2, j3, o4); break;
+                    case 1: merge4x4<W, 1, 2, 3>(j0, j1, j2, j3, o4); break;
+                    case 2: merge4x4<W, 2, 0, 2>(j0, j1, j2, j3, o4); break;
+                    default: merge4x4<W, 3, 2, 1>(j0, j1, j2, j3, o4); break;
                 }
+            }
+            if (out) {
+                if (live) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) *(uint4 *)&out[(size_t)(4 * q + t) * T + u] = o4[t];
+                }
+                continue;
             }
             __syncwarp();
             if (live) {
-                *(uint4 *)&J[0][u] = out[0];   // shift 4q+0 -> row of J0
-                *(uint4 *)&J[2][u] = out[1];   // shift 4q+1 -> row of J2 (brev2(1) = 2)
-                *(uint4 *)&J[1][u] = out[2];   // shift 4q+2 -> row of J1
-                *(uint4 *)&J[3][u] = out[3];   // shift 4q+3 -> row of J3
+                *(uint4 *)&J[0][u] = o4[0];   // shift 4q+0 -> row of J0
+                *(uint4 *)&J[2][u] = o4[1];   // shift 4q+1 -> row of J2 (brev2(1) = 2)
+                *(uint4 *)&J[1][u] = o4[2];   // shift 4q+2 -> row of J1
+                *(uint4 *)&J[3][u] = o4[3];   // shift 4q+3 -> row of J3
             }
             __syncwarp();
         }
@@ -435,15 +454,18 @@ __device__ void fht_radix4(W *F, int pitch, int n, int l, int T) {
 }
 
 // All levels from `first` (sub-bands of 2^(first-1) rows already merged),
-// two at a time where possible.
+// two at a time where possible.  With `out` the last level writes shift s to
+// row s of out; returns whether there was a level to do so.
 template <typename W>
-__device__ void fht_merge(W *F, int pitch, int n, int log2n, int T, int first) {
+__device__ bool fht_merge(W *F, int pitch, int n, int log2n, int T, int first,
+                          W *out = nullptr) {
     int l = first - 1;   // current sub-band size 2^l
     while (l + 2 <= log2n) {
-        fht_radix4<W>(F, pitch, n, l, T);
+        fht_radix4<W>(F, pitch, n, l, T, l + 2 == log2n ? out : nullptr);
         l += 2;
     }
-    if (l < log2n) fht_levels<W>(F, pitch, n, log2n, T, l + 1);
+    if (l < log2n) fht_levels<W>(F, pitch, n, log2n, T, l + 1, out);
+    return first <= log2n;
 }
 
 // ---------------------------------------------------------------------------
@@ -856,6 +878,7 @@ struct U8Path {
     __device__ static bool fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0,
                                Pipe &pipe, bool prefetched, const LaunchArgs &args) {
         const int n = im.n, T = kTile, pitch = fpitch(n);
+        bool compact;
         if (strip_by_tma(im)) {
             const int xs = x0 - strip_off(n), nb = strip_boxes(n);
             uint8_t *st = (uint8_t *)Hc;
@@ -867,23 +890,29 @@ struct U8Path {
                 return false;
             }
             fht_regs(F, pitch, im, StagedPixels{st, n, xs, nb * 128 - 8}, x0);
-            fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3);
+            compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3, Hc);
         } else if (n >= 4) {
             const GlobalPixels src{(const uint8_t *)im.img + (size_t)band * n * im.pitch,
                                    im.pitch, im.w,
                                    ((uintptr_t)im.img % 8 == 0) && (im.pitch % 8 == 0)};
             fht_regs(F, pitch, im, src, x0);
-            fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3);
+            compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3, Hc);
         } else {
             load_strip(F, pitch, im, band, x0);
-            fht_levels<uint32_t>(F, pitch, n, im.log2n, T);
+            compact = im.log2n == 0;
+            fht_levels<uint32_t>(F, pitch, n, im.log2n, T, 1, Hc);
         }
-        // Compact: Hc[s][u] = packed Hough word of shift s at tile column u.
-        for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
-            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
-            *(uint4 *)&Hc[s * T + u0] = *(const uint4 *)&F[(size_t)brev(s, im.log2n) * pitch + u0];
+        // The last level wrote Hc[s][u] = packed Hough word of shift s at tile
+        // column u; where the FHT had no merge level (n = 1, or n = 4 done in
+        // registers) the words are copied from their bit-reversed rows.
+        if (compact) {
+            for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
+                const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+                *(uint4 *)&Hc[s * T + u0] =
+                    *(const uint4 *)&F[(size_t)brev(s, im.log2n) * pitch + u0];
+            }
+            __syncthreads();
         }
-        __syncthreads();
         return true;
     }
 
