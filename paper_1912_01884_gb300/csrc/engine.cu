@@ -74,9 +74,10 @@ struct Ctl {
     int pad[62];
 };
 
-// One work item of a batch: image index, band, column tile.
+// One work item of a batch: image index, band, column tile, and the image's
+// band height n with bit 16 set when its strips go through TMA.
 struct Item {
-    int image, band, tile, pad;
+    int image, band, tile, nflags;
 };
 
 struct LaunchArgs {
@@ -231,7 +232,17 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 struct NextItem {
     long long item;
     int prefetched;   // its strip copy has been issued on the strip barrier
+    int pad;
+    Item it;          // its order entry (batches), copied by cp.async
 };
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
 struct Pipe {
     uint64_t *bar;        // strip barrier
     uint32_t phase;       // parity of its next completion
@@ -240,17 +251,25 @@ struct Pipe {
     NextItem *next;       // shared: the CTA's next item
 };
 
-__device__ __forceinline__ void decode_item(const LaunchArgs &args, long long item,
-                                            const ImgDesc **imp, int *band, int *tile) {
+// Thread 0: records the item taken from the queue and starts copying its
+// order entry (completed by cp_async_wait_all before anyone reads it).
+__device__ __forceinline__ void stage_next(const LaunchArgs &args, NextItem *next,
+                                           long long item) {
+    next->item = item;
+    next->prefetched = 0;
+    if (args.many && item < args.items) cp_async16(&next->it, &args.order[item]);
+}
+// The staged item (item < items).
+__device__ __forceinline__ void decode_staged(const LaunchArgs &args, const NextItem &nx,
+                                              const ImgDesc **imp, int *band, int *tile) {
     if (args.many) {
-        const Item it = args.order[item];
-        *imp = &args.many[it.image];
-        *band = it.band;
-        *tile = it.tile;
+        *imp = &args.many[nx.it.image];
+        *band = nx.it.band;
+        *tile = nx.it.tile;
     } else {
         *imp = &args.one;
-        *band = args.one.k - 1 - (int)(item / args.one.tiles);
-        *tile = (int)(item % args.one.tiles);
+        *band = args.one.k - 1 - (int)(nx.item / args.one.tiles);
+        *tile = (int)(nx.item % args.one.tiles);
     }
 }
 
@@ -864,13 +883,13 @@ struct U8Path {
     }
     // One thread: the band strip of (band, tile) through TMA into `st` (the
     // Hc region, free until the compaction), zero-filled outside the image.
-    __device__ static void issue_strip(const ImgDesc &im, int band, int tile, void *st,
-                                       Pipe &pipe) {
-        const int n = im.n, xs = tile * kTile - strip_off(n), nb = strip_boxes(n);
+    __device__ static void issue_strip(const CUtensorMap *map, int n, int band, int tile,
+                                       void *st, Pipe &pipe) {
+        const int xs = tile * kTile - strip_off(n), nb = strip_boxes(n);
         fence_proxy_async_smem();
         mbar_expect_tx(pipe.bar, (uint32_t)(nb * n * 128));
         for (int b = 0; b < nb; ++b)
-            tma_load_2d((uint8_t *)st + (size_t)b * n * 128, &im.tmap, xs + 128 * b, band * n,
+            tma_load_2d((uint8_t *)st + (size_t)b * n * 128, map, xs + 128 * b, band * n,
                         pipe.bar);
     }
 
@@ -882,7 +901,8 @@ struct U8Path {
         if (strip_by_tma(im)) {
             const int xs = x0 - strip_off(n), nb = strip_boxes(n);
             uint8_t *st = (uint8_t *)Hc;
-            if (threadIdx.x == 0 && !prefetched) issue_strip(im, band, x0 / kTile, st, pipe);
+            if (threadIdx.x == 0 && !prefetched)
+                issue_strip(&im.tmap, n, band, x0 / kTile, st, pipe);
             const bool ok = mbar_wait(pipe.bar, pipe.phase, args.wait_cycles);
             pipe.phase ^= 1u;
             if (!ok) {
@@ -1069,20 +1089,33 @@ struct U8Path {
 
     // Thread 0: takes the next work item and, when its strip can go to Hc
     // now (Hc is not needed any more by this item), issues the strip copy.
+    // Thread 0, once Hc is free: the strip copy of the next item (taken from
+    // the queue at the start of this one and staged after its FHT).
     __device__ static void take_next(const LaunchArgs &args, Pipe &pipe, void *Hc, bool hc_free) {
-        const long long nx = atomicAdd(&args.ctl->queue, 1);
-        int pf = 0;
-        if (hc_free && nx < args.items) {
-            const ImgDesc *nim;
-            int nband, ntile;
-            decode_item(args, nx, &nim, &nband, &ntile);
-            if (strip_by_tma(*nim)) {
-                issue_strip(*nim, nband, ntile, Hc, pipe);
-                pf = 1;
-            }
+        NextItem &nx = *pipe.next;
+        if (!hc_free || nx.item >= args.items) return;
+        const CUtensorMap *map;
+        int n, band, tile;
+        bool tma;
+        if (args.many) {
+            cp_async_wait_all();
+            const Item it = nx.it;
+            map = &args.many[it.image].tmap;
+            n = it.nflags & 0xffff;
+            tma = (it.nflags >> 16) & 1;
+            band = it.band;
+            tile = it.tile;
+        } else {
+            map = &args.one.tmap;
+            n = args.one.n;
+            tma = args.one.use_tma;
+            band = args.one.k - 1 - (int)(nx.item / args.one.tiles);
+            tile = (int)(nx.item % args.one.tiles);
         }
-        pipe.next->item = nx;
-        pipe.next->prefetched = pf;
+        if (tma && n >= 4) {
+            issue_strip(map, n, band, tile, Hc, pipe);
+            nx.prefetched = 1;
+        }
     }
 
 
@@ -1093,7 +1126,11 @@ struct U8Path {
         uint32_t *F = (uint32_t *)smem;  // the strip, then V
         int32_t *Vn = (int32_t *)smem;
         uint32_t *Hc = (uint32_t *)(smem + hc_offset());
+        // The next item is taken now; its result is only read after the FHT.
+        long long claimed = 0;
+        if (threadIdx.x == 0) claimed = atomicAdd(&args.ctl->queue, 1);
         if (!fht(F, Hc, im, band, x0, pipe, prefetched, args)) return false;
+        if (threadIdx.x == 0) stage_next(args, pipe.next, claimed);
         // The M tile of the band below comes by TMA into the V rows once its
         // producers have published (F is free: the FHT ended in Hc).
         const bool msmem = im.use_mtma && band < im.k - 1;
@@ -1339,10 +1376,7 @@ struct WidePath {
         const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
         Acc *mnext = (Acc *)im.mbuf[band & 1];
         const unsigned long long best = form_v(F, Hp, im, band, mprev, x0);
-        auto take_next = [&] {
-            pipe.next->item = atomicAdd(&args.ctl->queue, 1);
-            pipe.next->prefetched = 0;
-        };
+        auto take_next = [&] { stage_next(args, pipe.next, atomicAdd(&args.ctl->queue, 1)); };
         if (band == 0) {
             finish_band0<Acc>(best, im, args, take_next);
             return true;
@@ -1403,25 +1437,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ NextItem s_next;
+    __shared__ __align__(16) NextItem s_next;
     if (threadIdx.x == 0) {
         mbar_init(&s_bar, 1);
         mbar_init(&s_mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_next.item = atomicAdd(&args.ctl->queue, 1);
-        s_next.prefetched = 0;
+        stage_next(args, &s_next, atomicAdd(&args.ctl->queue, 1));
+        cp_async_wait_all();
     }
     __syncthreads();
     Pipe pipe{&s_bar, 0u, &s_mbar, 0u, &s_next};
     for (;;) {
         const long long item = s_next.item;
         const bool prefetched = s_next.prefetched != 0;
+        const ImgDesc *imp = nullptr;
+        int band = 0, tile = 0;
+        if (item < args.items) decode_staged(args, s_next, &imp, &band, &tile);
         __syncthreads();   // thread 0 rewrites s_next inside process
         if (item >= args.items) break;
-        const ImgDesc *imp;
-        int band, tile;
-        decode_item(args, item, &imp, &band, &tile);
         if (!P::process(*imp, band, tile, smem_raw, args, pipe, prefetched)) return;
+        if (threadIdx.x == 0) cp_async_wait_all();
         __syncthreads();
     }
 }
@@ -1831,6 +1866,8 @@ int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream
     plan->staging.clear();
     for (auto &p : plan->imgs)
         plan->staging.push_back(make_desc(p, plan->L, (char *)ws, plan->dtype));
+    for (Item &it : plan->order)
+        it.nflags = plan->imgs[it.image].s.n | (plan->staging[it.image].use_tma ? 1 << 16 : 0);
     plan->bound_ws = ws;
     int st = cuda_status(cudaMemcpyAsync((char *)ws + plan->L.table_off, plan->staging.data(),
                                          sizeof(ImgDesc) * plan->staging.size(),
