@@ -164,6 +164,9 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
 
 // Bounded wait on a publication flag: gives up after `limit` cycles, or at
 // once when another wait of this launch has already given up.
@@ -629,18 +632,26 @@ __device__ __forceinline__ unsigned long long argmax_key(uint32_t ordv, int x, i
 
 // Waits for the three band+1 tiles whose window maxima a tile of `band` reads.
 // `after` runs on thread 0 once the flags are seen (or the wait gave up).
+// Lanes 0..2 of warp 0 poll the three flags at the same time; the warp
+// barrier passes their acquisitions on to lane 0 and, through the CTA barrier,
+// to every thread.
 template <typename After>
 __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args,
                           After after) {
     if (band >= im.k - 1) return;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int c = tile - 1 + (int)threadIdx.x;
         bool ok = true;
-        for (int c = max(tile - 1, 0); c <= min(tile + 1, im.tiles - 1) && ok; ++c)
+        if (threadIdx.x < 3 && c >= 0 && c < im.tiles)
             ok = wait_flag(im.flags + (size_t)(band + 1) * im.tiles + c, args.ctl,
                            args.wait_cycles);
-        if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
-        __threadfence();
-        after();
+        __syncwarp();
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) {
+            if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+            fence_acq_rel_gpu();
+            after();
+        }
     }
     __syncthreads();
 }
@@ -649,17 +660,17 @@ __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArg
 }
 
 // `before` runs on thread 0 after the CTA barrier, before the flag.
+// Every warp fences its own M and bp stores as soon as it is done, so that
+// the release by thread 0 after the CTA barrier has little left to wait for.
 template <typename Before>
 __device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args,
                         Before before) {
+    fence_acq_rel_gpu();
     __syncthreads();
     if (threadIdx.x == 0) before();
     const ImgDesc &first = args.many ? args.many[0] : args.one;
     if (band == args.skip_band && tile == args.skip_tile && im.flags == first.flags) return;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(im.flags + (size_t)band * im.tiles + tile, 1);
-    }
+    if (threadIdx.x == 0) st_release(im.flags + (size_t)band * im.tiles + tile, 1);
 }
 __device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
     publish(im, band, tile, args, [] {});
