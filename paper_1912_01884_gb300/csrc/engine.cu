@@ -632,24 +632,40 @@ __device__ __forceinline__ unsigned long long argmax_key(uint32_t ordv, int x, i
 
 // Waits for the three band+1 tiles whose window maxima a tile of `band` reads.
 // `after` runs on thread 0 once the flags are seen (or the wait gave up).
-// Lanes 0..2 of warp 0 poll the three flags at the same time; the warp
-// barrier passes their acquisitions on to lane 0 and, through the CTA barrier,
-// to every thread.
+// Lanes 0..2 of warp 0: the flag of band+1 tile (tile - 1 + lane), read
+// without ordering ahead of time (1 where there is nothing to wait for).
+__device__ __forceinline__ int peek_dep(const ImgDesc &im, int band, int tile) {
+    const int c = tile - 1 + (int)threadIdx.x;
+    if (threadIdx.x >= 3 || band >= im.k - 1 || c < 0 || c >= im.tiles) return 1;
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];"
+                 : "=r"(v)
+                 : "l"(im.flags + (size_t)(band + 1) * im.tiles + c)
+                 : "memory");
+    return v;
+}
+
+// Lanes 0..2 of warp 0 poll the three flags at the same time (a flag already
+// seen set by peek_dep is not read again: the fence that follows makes that
+// read an acquisition); the warp barrier passes the acquisitions on to lane 0
+// and, through the CTA barrier, to every thread.
 template <typename After>
 __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args,
-                          After after) {
+                          After after, int seen = 0) {
     if (band >= im.k - 1) return;
     if (threadIdx.x < 32) {
         const int c = tile - 1 + (int)threadIdx.x;
         bool ok = true;
-        if (threadIdx.x < 3 && c >= 0 && c < im.tiles)
-            ok = wait_flag(im.flags + (size_t)(band + 1) * im.tiles + c, args.ctl,
-                           args.wait_cycles);
+        if (threadIdx.x < 3 && c >= 0 && c < im.tiles) {
+            if (!seen)
+                ok = wait_flag(im.flags + (size_t)(band + 1) * im.tiles + c, args.ctl,
+                               args.wait_cycles);
+            fence_acq_rel_gpu();
+        }
         __syncwarp();
         ok = __all_sync(0xffffffffu, ok);
         if (threadIdx.x == 0) {
             if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
-            fence_acq_rel_gpu();
             after();
         }
     }
@@ -1140,8 +1156,8 @@ struct U8Path {
         // The next item is taken now; its result is only read after the FHT.
         long long claimed = 0;
         if (threadIdx.x == 0) claimed = atomicAdd(&args.ctl->queue, 1);
+        const int seen = threadIdx.x < 32 ? peek_dep(im, band, tile) : 0;
         if (!fht(F, Hc, im, band, x0, pipe, prefetched, args)) return false;
-        if (threadIdx.x == 0) stage_next(args, pipe.next, claimed);
         // The M tile of the band below comes by TMA into the V rows once its
         // producers have published (F is free: the FHT ended in Hc).
         const bool msmem = im.use_mtma && band < im.k - 1;
@@ -1151,7 +1167,9 @@ struct U8Path {
             fence_proxy_async_smem();
             mbar_expect_tx(pipe.mbar, (uint32_t)(T * D * 4));
             tma_load_2d(Vn + kPad * T, &im.mtmap, kMOff + x0, ((band + 1) & 1) * D, pipe.mbar);
-        });
+        }, seen);
+        // (After the fences of wait_deps, which would otherwise wait for it.)
+        if (threadIdx.x == 0) stage_next(args, pipe.next, claimed);
         if (band != 0) dead_pad(Vn, n);
         if (msmem) {
             const bool ok = mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles);
