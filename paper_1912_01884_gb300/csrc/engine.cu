@@ -59,7 +59,7 @@ struct ImgDesc {
     long long item0;          // first work item of this image
     void *mbuf[2];            // ping-pong window maxima, [D][mpitch] of Acc
     int mpitch;
-    uint8_t *bp;              // [k][D][w] argmax e + n - 1 of each window
+    uint8_t *bp;              // argmax index of each window, see bp_byte
     int *flags;               // [k][tiles] publication flags
     unsigned long long *best; // lexicographic argmax key of V_0
     int *done;                // band-0 tiles finished
@@ -67,6 +67,15 @@ struct ImgDesc {
     void *score_out;
     const int32_t *win;       // optional [k][2]: allowed displacements of each band
 };
+
+// Backpointers: per band, ceil(D/4) groups of w 32-bit words; byte (e & 3)
+// of word (band, e >> 2, x) is the argmax index of the window of state
+// (x, e), e = c + n - 1.  Four displacements of a column share a word, so
+// the window, which runs along e for a fixed x, stores a word per four.
+__host__ __device__ inline int bp_groups(int n) { return (2 * n - 1 + 3) / 4; }
+__device__ __forceinline__ size_t bp_byte(const ImgDesc &im, int band, int e, int x) {
+    return (((size_t)band * bp_groups(im.n) + (e >> 2)) * im.w + x) * 4 + (e & 3);
+}
 
 struct Ctl {
     int queue;   // next work item
@@ -532,6 +541,63 @@ __device__ __forceinline__ void window_regs(int c0, int c1, int B, Key dead, VGe
     }
 }
 
+// The register window of the uint8 path for L = 2B+1 in {9, 17, 25, 33}
+// (L = 1 mod 4) over at most 64 displacements: outputs j = c - ca, ca at a
+// bp word boundary.  kcol[c * kTile] is the V key of displacement c (dead
+// pad rows outside [lo, hi]); output j stores M' = key & ~511 to
+// mcol[j * mstride] and its index byte into bp word bcol[(j >> 2) * bstride].
+// The blocks are unrolled, so each byte's place in its word is a constant.
+template <int L>
+__device__ __forceinline__ void window_u8(int ca, int c1, const int32_t *kcol, int32_t *mcol,
+                                          int mstride, uint32_t *bcol, int bstride) {
+    constexpr int B = (L - 1) / 2;
+    constexpr int NB = (64 + L - 1) / L;
+    static_assert(L % 4 == 1, "block starts must keep the byte phase");
+    int32_t S[L], Vb[L];
+    const int32_t *kp = kcol + (ca - B) * kTile;
+#pragma unroll
+    for (int i = 0; i < L; ++i) Vb[i] = kp[i * kTile];
+    int32_t run = INT32_MIN;
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i) {
+        run = max(run, Vb[i]);
+        S[i] = run;
+    }
+    const int last = c1 - ca;
+    uint32_t word = 0;
+    int32_t *mp = mcol;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (k * L > last) break;
+        const int32_t *vp = kcol + (ca + k * L + B + 1) * kTile;
+        int32_t G = INT32_MIN;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const int j = k * L + i;
+            const int32_t v = vp[i * kTile];
+            Vb[i] = v;
+            const int32_t m = i == 0 ? S[0] : max(S[i], G);
+            G = max(G, v);
+            if (j <= last) {
+                *mp = m & ~511;
+                const uint32_t b = ~(uint32_t)m & 0xffu;
+                word = (j & 3) == 0 ? b : word | (b << (8 * (j & 3)));
+                if ((j & 3) == 3) bcol[(j >> 2) * bstride] = word;
+            }
+            mp += mstride;
+        }
+        if (k + 1 < NB) {
+            run = INT32_MIN;
+#pragma unroll
+            for (int i = L - 1; i >= 0; --i) {
+                run = max(run, Vb[i]);
+                S[i] = run;
+            }
+        }
+    }
+    if ((last & 3) != 3) bcol[(last >> 2) * bstride] = word;
+}
+
 // Two-pass version for any L: pass 1 stores the in-block suffix maxima
 // S(e), e in [c0-B, c1-B], through sput/sget; pass 2 runs the in-block prefix
 // maximum G(c+B) and combines.  Blocks are aligned at `a` (a <= c0 - B).
@@ -577,7 +643,7 @@ __device__ __forceinline__ void band_window(const ImgDesc &im, int band, int *lo
 // Eq. 5: the polyline from the best top point, one backpointer per band.
 template <typename Acc>
 __device__ void readback(const ImgDesc &im, const LaunchArgs &args) {
-    const int n = im.n, D = 2 * n - 1;
+    const int n = im.n;
     __threadfence();
     const unsigned long long key = atomicAdd(im.best, 0ull);
     if (key == 0) {   // no admissible polyline inside the windows
@@ -599,7 +665,7 @@ __device__ void readback(const ImgDesc &im, const LaunchArgs &args) {
             atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
             return;
         }
-        const int e = __ldcg(im.bp + ((size_t)i * D + (d + n - 1)) * im.w + xx);
+        const int e = __ldcg(im.bp + bp_byte(im, i, d + n - 1, xx));
         d = e - (n - 1);
         im.x_out[i] = xx;
         im.d_out[i] = d;
@@ -695,14 +761,14 @@ __device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs 
 // Stores M_b(x, c) (skewed so that the consumer reads M(x + d, d) as row d,
 // column x) and its argmax byte.
 template <typename Acc, typename Key>
-__device__ __forceinline__ void store_window(const ImgDesc &im, Acc *mnext, uint8_t *bp, int x,
+__device__ __forceinline__ void store_window(const ImgDesc &im, Acc *mnext, int band, int x,
                                              int c, Key mk) {
     using KO = KeyOps<Acc, Key>;
     const int n = im.n;
     const bool dead = mk == KO::dead();
     mnext[(size_t)(c + n - 1) * im.mpitch + kMOff + x - c] = dead ? Dead<Acc>::value()
                                                                   : KO::value(mk);
-    bp[(size_t)(c + n - 1) * im.w + x] = (uint8_t)(dead ? 0 : KO::index(mk));
+    im.bp[bp_byte(im, band, c + n - 1, x)] = (uint8_t)(dead ? 0 : KO::index(mk));
 }
 
 // ---------------------------------------------------------------------------
@@ -1203,42 +1269,49 @@ struct U8Path {
         const int x = x0 + u;
         const int B = im.B;   // already clamped to 2n-2
         const int lo = -(n - 1), hi = n - 1;
-        uint8_t *bp = im.bp + (size_t)band * D * im.w;
         const int32_t *col = Vn + u;
         if constexpr (sizeof(Key) == 4) {
             if (B <= kFastB) {
                 // Shared memory holds keys.  V rows [lo - kPad, hi + kPad] exist
-                // (dead outside [lo, hi]); the register window never reads
-                // below c0 - B >= lo - kPad, and reads above hi are dead.
+                // (dead outside [lo, hi]), and B <= kPad: the register window
+                // reads them without bounds checks.
                 const int32_t *kcol = col + (n - 1 + kPad) * T;
-                auto vkey = [&](int e) -> Key { return e > hi ? KO::dead() : kcol[e * T]; };
                 // M'(x, c) = key & ~511 (negative when dead), bp = its index.
                 Acc *mcol = mnext + (size_t)(n - 1) * im.mpitch + kMOff + x;
-                uint8_t *bcol = bp + (size_t)(n - 1) * im.w + x;
-                const long long mstep = im.mpitch - 1, bstep = im.w;
-                auto emit = [&](int c, Key mk) {
-                    mcol[c * mstep] = mk & ~511;
-                    bcol[c * bstep] = (uint8_t)(~mk & 511);
-                };
-                // Only the consumer band's allowed displacements are needed.
+                const int mstep = im.mpitch - 1;
+                // Quarters of the displacement indices e = c + n - 1, cut at
+                // multiples of 4 (whole bp words).  Only the consumer band's
+                // allowed displacements are needed; a thread starts at the word
+                // boundary below them (the extra maxima are never read).
+                const int Q = ((D + 3) / 4 + 3) & ~3;
                 int clo, chi;
                 band_window(im, band - 1, &clo, &chi);
-                const int c0 = max(lo + (qd * D) / kQ, clo);
-                const int c1 = min(lo + ((qd + 1) * D) / kQ - 1, chi);
-                if (c0 <= c1 && x < im.w) {
-                    const Key dk = KO::dead();
+                const int ea = max(qd * Q, (clo + n - 1) & ~3);
+                const int e1 = min(min((qd + 1) * Q, D) - 1, chi + n - 1);
+                if (ea <= e1 && x < im.w) {
+                    const int ca = ea - (n - 1), c1 = e1 - (n - 1);
+                    uint32_t *bw = (uint32_t *)im.bp +
+                                   ((size_t)band * bp_groups(n) + (ea >> 2)) * im.w + x;
+                    int32_t *ma = mcol + (long long)ca * mstep;
                     switch (B) {
-                        case 4: window_regs<9, true, Key>(c0, c1, B, dk, vkey, emit); break;
-                        case 8: window_regs<17, true, Key>(c0, c1, B, dk, vkey, emit); break;
-                        case 12: window_regs<25, true, Key>(c0, c1, B, dk, vkey, emit); break;
-                        case 16: window_regs<33, true, Key>(c0, c1, B, dk, vkey, emit); break;
-                        default:
+                        case 4: window_u8<9>(ca, c1, kcol, ma, mstep, bw, im.w); break;
+                        case 8: window_u8<17>(ca, c1, kcol, ma, mstep, bw, im.w); break;
+                        case 12: window_u8<25>(ca, c1, kcol, ma, mstep, bw, im.w); break;
+                        case 16: window_u8<33>(ca, c1, kcol, ma, mstep, bw, im.w); break;
+                        default: {
+                            const Key dk = KO::dead();
+                            auto vkey = [&](int e) -> Key { return kcol[e * T]; };
+                            auto emit = [&](int c, Key mk) {
+                                mcol[(long long)c * mstep] = mk & ~511;
+                                im.bp[bp_byte(im, band, c + n - 1, x)] = (uint8_t)(~mk & 255);
+                            };
                             if (B < 4)
-                                window_regs<9, false, Key>(c0, c1, B, dk, vkey, emit);
+                                window_regs<9, false, Key>(ca, c1, B, dk, vkey, emit);
                             else if (B < 8)
-                                window_regs<17, false, Key>(c0, c1, B, dk, vkey, emit);
+                                window_regs<17, false, Key>(ca, c1, B, dk, vkey, emit);
                             else
-                                window_regs<33, false, Key>(c0, c1, B, dk, vkey, emit);
+                                window_regs<33, false, Key>(ca, c1, B, dk, vkey, emit);
+                        }
                     }
                 }
                 publish(im, band, tile, args);
@@ -1247,7 +1320,7 @@ struct U8Path {
         }
         auto emit = [&](int c, Key mk) {
             mnext[(size_t)(c + n - 1) * im.mpitch + kMOff + x - c] = mstore(mk);
-            bp[(size_t)(c + n - 1) * im.w + x] = (uint8_t)(mk < 0 ? 0 : KO::index(mk));
+            im.bp[bp_byte(im, band, c + n - 1, x)] = (uint8_t)(mk < 0 ? 0 : KO::index(mk));
         };
         {
             auto vkey = [&](int e) -> Key {
@@ -1416,13 +1489,12 @@ struct WidePath {
         const int x = x0 + u;
         const int B = im.B;
         const int lo = -(n - 1), hi = n - 1;
-        uint8_t *bp = im.bp + (size_t)band * D * im.w;
         auto vkey = [&](int e) -> Key {
             if (e < lo || e > hi) return KO::dead();
             const Acc v = vval(F, Hp, pitch, im.log2n, u, e);
             return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
         };
-        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, bp, x, c, mk); };
+        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, band, x, c, mk); };
         // S(row, u): a Key per (row, column) packed into the columns [T, 2T) of F.
         auto s_at = [&](int row) -> Key * {
             const int wi = (row * T + u) * (int)(sizeof(Key) / 4);
@@ -1549,7 +1621,7 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
         p.m1 = d + (size_t)p.s.D * p.mpitch * 4;
         d = align_up(p.m1 + (size_t)p.s.D * p.mpitch * 4, 256);
         p.bp = d;
-        d = align_up(d + (size_t)p.s.k * p.s.D * p.s.w, 256);
+        d = align_up(d + (size_t)p.s.k * bp_groups(p.s.n) * 4 * p.s.w, 256);
     }
     L.data_off = L.order_off + L.order_bytes;
     L.total = L.data_off + d;
