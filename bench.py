@@ -55,7 +55,7 @@ WORKLOADS = {
 # profiles/engine_kernel_u8_2048x2048_k16_B16.md (48 images per launch); a
 # launch's traffic is this times its images.  None for other workloads, and
 # to be reset whenever the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (264.419328e6 + 1391.033e6) / 48}
+NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (212.667904e6 + 709.79968e6) / 48}
 
 
 def algorithmic_bytes(h, w, k, bpp):
