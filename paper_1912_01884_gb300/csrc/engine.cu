@@ -890,7 +890,97 @@ struct U8Path {
             const int sc = clamp(X - xs);
             return st[(size_t)(sc >> 7) * n * 128 + row * 128 + (sc & 127)];
         }
+        // 4 bytes at a 4-aligned column inside the staged range (a word
+        // never straddles two boxes).
+        __device__ uint32_t word(int row, int X) const {
+            const int sc = X - xs;
+            return *(const uint32_t *)(st + (size_t)(sc >> 7) * n * 128 + row * 128 + (sc & 127));
+        }
     };
+
+    // Packed words of N consecutive columns of band row y: word j holds the
+    // pixel of column Xp + j (low half) and that of column Xm + 11 - j (high
+    // half, the mirrored "-" direction), Xp and Xm 4-aligned, N <= 12.
+    template <int N>
+    __device__ static void row_words(const StagedPixels &src, int y, int Xp, int Xm,
+                                     uint32_t (&P)[N]) {
+        constexpr int NW = (N + 3) / 4;
+        uint32_t pw[NW], mw[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            pw[k] = src.word(y, Xp + 4 * k);
+            mw[k] = src.word(y, Xm + 4 * (2 - k));
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            P[j] = __byte_perm(pw[j / 4], mw[j / 4], (j & 3) | ((7 - (j & 3)) << 8)) & 0x00ff00ffu;
+    }
+
+    // One level-1 + level-2 step in registers on four rows r0..r0+3 of a
+    // sub-band: out[s][u] (s < 4, u < W) from pixel rows of W, W+1, W+2, W+3
+    // columns.
+    template <int W>
+    __device__ static void levels12(const StagedPixels &src, int y0, int Xp, int Xm,
+                                    uint32_t (&out)[4][W]) {
+        uint32_t A[2][W], Bq[2][W + 2];
+        {
+            uint32_t p0[W], p1[W + 1];
+            row_words(src, y0, Xp, Xm, p0);
+            row_words(src, y0 + 1, Xp, Xm, p1);
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                A[0][u] = p0[u] + p1[u];
+                A[1][u] = p0[u] + p1[u + 1];
+            }
+        }
+        {
+            uint32_t p2[W + 2], p3[W + 3];
+            row_words(src, y0 + 2, Xp, Xm, p2);
+            row_words(src, y0 + 3, Xp, Xm, p3);
+#pragma unroll
+            for (int u = 0; u < W + 2; ++u) {
+                Bq[0][u] = p2[u] + p3[u];
+                Bq[1][u] = p2[u] + p3[u + 1];
+            }
+        }
+        // shift s: A_{s>>1}(u) + B_{s>>1}(u + ceil(s/2))
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            out[0][u] = A[0][u] + Bq[0][u];
+            out[1][u] = A[0][u] + Bq[0][u + 1];
+            out[2][u] = A[1][u] + Bq[1][u + 1];
+            out[3][u] = A[1][u] + Bq[1][u + 2];
+        }
+    }
+
+    // Levels 1-3 in registers, straight from the staged pixels (n >= 8): a
+    // thread takes an 8-row sub-band g and the 4 columns [4c, 4c+4) of the
+    // level-3 width; its top four rows are needed at 4..7 columns, the bottom
+    // four at 8..11.  Shift s of the sub-band goes to row 8g + brev3(s).
+    __device__ static void fht_regs8(uint32_t *F, int pitch, const ImgDesc &im,
+                                     const StagedPixels &src, int x0) {
+        const int n = im.n, T = kTile;
+        const int C4 = (T + n - 8 + 3) / 4;
+        const int tasks = (n / 8) * C4;
+        for (int t = threadIdx.x; t < tasks; t += kThreads) {
+            const int g = t / C4, c = t - g * C4;
+            const int Xp = x0 + 4 * c, Xm = x0 + T - 12 - 4 * c;
+            uint32_t B2[4][8], T2[4][4];
+            levels12<8>(src, 8 * g + 4, Xp, Xm, B2);
+            levels12<4>(src, 8 * g, Xp, Xm, T2);
+            uint32_t *row0 = F + (size_t)(8 * g) * pitch + 4 * c;
+            // shift s: T2_{s>>1}(u) + B2_{s>>1}(u + ceil(s/2)), row brev3(s)
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int h = s >> 1, o = (s + 1) >> 1;
+                const int r = ((s & 1) << 2) | (s & 2) | ((s >> 2) & 1);
+                *(uint4 *)&row0[(size_t)r * pitch] =
+                    make_uint4(T2[h][0] + B2[h][o + 0], T2[h][1] + B2[h][o + 1],
+                               T2[h][2] + B2[h][o + 2], T2[h][3] + B2[h][o + 3]);
+            }
+        }
+        __syncthreads();
+    }
 
     // Levels 1 and 2 in registers, straight from the pixels: a thread takes 4
     // band rows (a 4-row sub-band g) and 8 strip columns [8c, 8c+8) plus the 3
@@ -1002,8 +1092,14 @@ struct U8Path {
                 if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
                 return false;
             }
-            fht_regs(F, pitch, im, StagedPixels{st, n, xs, nb * 128 - 8}, x0);
-            compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3, Hc);
+            const StagedPixels src{st, n, xs, nb * 128 - 8};
+            if (n >= 8) {
+                fht_regs8(F, pitch, im, src, x0);
+                compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 4, Hc);
+            } else {
+                fht_regs(F, pitch, im, src, x0);
+                compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3, Hc);
+            }
         } else if (n >= 4) {
             const GlobalPixels src{(const uint8_t *)im.img + (size_t)band * n * im.pitch,
                                    im.pitch, im.w,
