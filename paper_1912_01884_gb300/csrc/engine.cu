@@ -43,6 +43,14 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kTile = 128;             // output columns of one item
 constexpr int kQ = kThreads / kTile;   // threads sharing a column in the DP
+// The uint8 engine adds a fifth warpgroup whose first warp runs the control
+// of the work items (queue, dependency flags, copies, publication) so that
+// its waits stay off the compute warps' path; the other three warps exit.
+constexpr int kWsThreads = kThreads + 128;
+constexpr int kCtlSync = kThreads + 32;   // compute threads + the control warp
+// Named barriers: 1 among the compute threads; 2..5 between them and the
+// control warp (compute threads arrive, the control warp waits, or back).
+constexpr int kBarCompute = 1, kBarFhtDone = 2, kBarHcFree = 3, kBarWinDone = 4, kBarNext = 5;
 constexpr int kMaxBandFused = 128;     // band heights handled by the fused kernel
 constexpr int kMOff = 128;             // column offset of the skewed M layout
 constexpr int kPad = 16;               // dead rows around V (uint8 path)
@@ -176,6 +184,17 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 __device__ __forceinline__ void fence_acq_rel_gpu() {
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
+// Barrier of the kThreads compute threads (every thread of the 512-thread
+// kernel; the compute warps of the uint8 kernel).
+__device__ __forceinline__ void csync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kBarCompute), "n"(kThreads) : "memory");
+}
+__device__ __forceinline__ void nb_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nb_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 
 // Bounded wait on a publication flag: gives up after `limit` cycles, or at
 // once when another wait of this launch has already given up.
@@ -197,6 +216,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(
+                     smem_addr(bar))
                  : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -241,6 +265,13 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 // Per-CTA state of the asynchronous copies and of the queue: the next work
 // item is taken before the current one finishes, so that its band strip can
 // be copied while the current item computes its window maxima.
+// The item the control warp hands to the compute warps of the uint8 engine.
+struct WsSlot {
+    long long item;
+    const ImgDesc *im;
+    int band, tile, prefetched;
+};
+
 struct NextItem {
     long long item;
     int prefetched;   // its strip copy has been issued on the strip barrier
@@ -373,7 +404,7 @@ __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first =
                 __syncwarp();
             }
         }
-        __syncthreads();
+        csync();
     }
 }
 
@@ -481,7 +512,7 @@ __device__ void fht_radix4(W *F, int pitch, int n, int l, int T, W *out = nullpt
             __syncwarp();
         }
     }
-    __syncthreads();
+    csync();
 }
 
 // All levels from `first` (sub-bands of 2^(first-1) rows already merged),
@@ -683,7 +714,7 @@ __device__ void finish_band0(unsigned long long best, const ImgDesc &im, const L
         best = best > other ? best : other;
     }
     if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
-    __syncthreads();
+    csync();
     if (threadIdx.x == 0) {
         hook();
         __threadfence();
@@ -698,18 +729,6 @@ __device__ __forceinline__ unsigned long long argmax_key(uint32_t ordv, int x, i
 
 // Waits for the three band+1 tiles whose window maxima a tile of `band` reads.
 // `after` runs on thread 0 once the flags are seen (or the wait gave up).
-// Lanes 0..2 of warp 0: the flag of band+1 tile (tile - 1 + lane), read
-// without ordering ahead of time (1 where there is nothing to wait for).
-__device__ __forceinline__ int peek_dep(const ImgDesc &im, int band, int tile) {
-    const int c = tile - 1 + (int)threadIdx.x;
-    if (threadIdx.x >= 3 || band >= im.k - 1 || c < 0 || c >= im.tiles) return 1;
-    int v;
-    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];"
-                 : "=r"(v)
-                 : "l"(im.flags + (size_t)(band + 1) * im.tiles + c)
-                 : "memory");
-    return v;
-}
 
 // Lanes 0..2 of warp 0 poll the three flags at the same time (a flag already
 // seen set by peek_dep is not read again: the fence that follows makes that
@@ -735,7 +754,7 @@ __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArg
             after();
         }
     }
-    __syncthreads();
+    csync();
 }
 __device__ void wait_deps(const ImgDesc &im, int band, int tile, const LaunchArgs &args) {
     wait_deps(im, band, tile, args, [] {});
@@ -748,7 +767,7 @@ template <typename Before>
 __device__ void publish(const ImgDesc &im, int band, int tile, const LaunchArgs &args,
                         Before before) {
     fence_acq_rel_gpu();
-    __syncthreads();
+    csync();
     if (threadIdx.x == 0) before();
     const ImgDesc &first = args.many ? args.many[0] : args.one;
     if (band == args.skip_band && tile == args.skip_tile && im.flags == first.flags) return;
@@ -850,7 +869,7 @@ struct U8Path {
                 *(uint4 *)&dst[4 * g] = out;
             }
         }
-        __syncthreads();
+        csync();
     }
 
     // Eight pixels [c, c+8) of a row, zero outside [0, w); c is a multiple of
@@ -979,7 +998,7 @@ struct U8Path {
                                T2[h][2] + B2[h][o + 2], T2[h][3] + B2[h][o + 3]);
             }
         }
-        __syncthreads();
+        csync();
     }
 
     // Levels 1 and 2 in registers, straight from the pixels: a thread takes 4
@@ -1052,7 +1071,7 @@ struct U8Path {
                 }
             }
         }
-        __syncthreads();
+        csync();
     }
 
     // Staged strip: columns [x0 - noff, x0 + T + noff) in boxes of 128.
@@ -1120,7 +1139,7 @@ struct U8Path {
                 *(uint4 *)&Hc[s * T + u0] =
                     *(const uint4 *)&F[(size_t)brev(s, im.log2n) * pitch + u0];
             }
-            __syncthreads();
+            csync();
         }
         return true;
     }
@@ -1278,69 +1297,25 @@ struct U8Path {
 
     // Thread 0: takes the next work item and, when its strip can go to Hc
     // now (Hc is not needed any more by this item), issues the strip copy.
-    // Thread 0, once Hc is free: the strip copy of the next item (taken from
-    // the queue at the start of this one and staged after its FHT).
-    __device__ static void take_next(const LaunchArgs &args, Pipe &pipe, void *Hc, bool hc_free) {
-        NextItem &nx = *pipe.next;
-        if (!hc_free || nx.item >= args.items) return;
-        const CUtensorMap *map;
-        int n, band, tile;
-        bool tma;
-        if (args.many) {
-            cp_async_wait_all();
-            const Item it = nx.it;
-            map = &args.many[it.image].tmap;
-            n = it.nflags & 0xffff;
-            tma = (it.nflags >> 16) & 1;
-            band = it.band;
-            tile = it.tile;
-        } else {
-            map = &args.one.tmap;
-            n = args.one.n;
-            tma = args.one.use_tma;
-            band = args.one.k - 1 - (int)(nx.item / args.one.tiles);
-            tile = (int)(nx.item % args.one.tiles);
-        }
-        if (tma && n >= 4) {
-            issue_strip(map, n, band, tile, Hc, pipe);
-            nx.prefetched = 1;
-        }
-    }
-
-
-    __device__ static bool process(const ImgDesc &im, int band, int tile, unsigned char *smem,
+    // The compute warps' part of a work item.  The control warp issued the
+    // item's strip copy; after the FHT it copies the M tile (or, where there
+    // is none, just signals that the producers' flags were seen) on the M
+    // barrier.  A wait that gives up sets ETIMEOUT and the item carries on,
+    // so that every signal to the control warp is still given.
+    __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
                                    const LaunchArgs &args, Pipe &pipe, bool prefetched) {
         const int n = im.n, T = kTile, D = 2 * n - 1;
         const int x0 = tile * T;
         uint32_t *F = (uint32_t *)smem;  // the strip, then V
         int32_t *Vn = (int32_t *)smem;
         uint32_t *Hc = (uint32_t *)(smem + hc_offset());
-        // The next item is taken now; its result is only read after the FHT.
-        long long claimed = 0;
-        if (threadIdx.x == 0) claimed = atomicAdd(&args.ctl->queue, 1);
-        const int seen = threadIdx.x < 32 ? peek_dep(im, band, tile) : 0;
-        if (!fht(F, Hc, im, band, x0, pipe, prefetched, args)) return false;
-        // The M tile of the band below comes by TMA into the V rows once its
-        // producers have published (F is free: the FHT ended in Hc).
+        fht(F, Hc, im, band, x0, pipe, prefetched, args);
+        nb_arrive(kBarFhtDone, kCtlSync);   // F is free for the M tile
         const bool msmem = im.use_mtma && band < im.k - 1;
-        wait_deps(im, band, tile, args, [&] {
-            if (!msmem) return;
-            fence_proxy_async_global();
-            fence_proxy_async_smem();
-            mbar_expect_tx(pipe.mbar, (uint32_t)(T * D * 4));
-            tma_load_2d(Vn + kPad * T, &im.mtmap, kMOff + x0, ((band + 1) & 1) * D, pipe.mbar);
-        }, seen);
-        // (After the fences of wait_deps, which would otherwise wait for it.)
-        if (threadIdx.x == 0) stage_next(args, pipe.next, claimed);
         if (band != 0) dead_pad(Vn, n);
-        if (msmem) {
-            const bool ok = mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles);
-            pipe.mphase ^= 1u;
-            if (!ok) {
-                if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
-                return false;
-            }
-        }
+        if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles) && threadIdx.x == 0)
+            atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+        pipe.mphase ^= 1u;
         const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
         Acc *mnext = (Acc *)im.mbuf[band & 1];
         const bool fast = sizeof(Key) == 4 && im.B <= kFastB;
@@ -1354,12 +1329,20 @@ struct U8Path {
         else
             best = form_v(Vn, Hc, im, band, x0, mprev, msmem);
         if (band == 0) {
-            finish_band0<Acc>(best, im, args, [&] { take_next(args, pipe, Hc, true); });
-            return true;
+            // The tile's best key; the control warp counts the tile and reads
+            // the polyline back after the image's last one.
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = best > other ? best : other;
+            }
+            if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
+            nb_arrive(kBarHcFree, kCtlSync);
+            nb_arrive(kBarWinDone, kCtlSync);
+            return;
         }
-        __syncthreads();
-        // Hc is free from here on unless the window reads H or S from it.
-        if (threadIdx.x == 0) take_next(args, pipe, Hc, fast);
+        csync();
+        // Hc is free from here on unless the window reads S from it.
+        if (fast) nb_arrive(kBarHcFree, kCtlSync);
 
         const int u = threadIdx.x % T, qd = threadIdx.x / T;
         const int x = x0 + u;
@@ -1410,8 +1393,8 @@ struct U8Path {
                         }
                     }
                 }
-                publish(im, band, tile, args);
-                return true;
+                nb_arrive(kBarWinDone, kCtlSync);
+                return;
             }
         }
         auto emit = [&](int c, Key mk) {
@@ -1440,11 +1423,112 @@ struct U8Path {
                 if (c0 <= c1 && x < im.w)
                     window_two_pass<Key>(c0, c1, B, lo - B, lo, hi, KO::dead(), vkey, sput, sget,
                                          emit);
-                __syncthreads();
+                csync();
             }
         }
-        publish(im, band, tile, args);
-        return true;
+        nb_arrive(kBarHcFree, kCtlSync);
+        nb_arrive(kBarWinDone, kCtlSync);
+    }
+
+    // An item as the control warp sees it.
+    struct Ctrl {
+        long long item;
+        const ImgDesc *im;
+        int band, tile, n;
+        bool tma;   // its strip goes through TMA
+    };
+    __device__ static Ctrl decode(const LaunchArgs &args, long long item) {
+        Ctrl c{item, nullptr, 0, 0, 0, false};
+        if (item >= args.items) return c;
+        if (args.many) {
+            const Item it = args.order[item];
+            c.im = &args.many[it.image];
+            c.band = it.band;
+            c.tile = it.tile;
+            c.n = it.nflags & 0xffff;
+            c.tma = ((it.nflags >> 16) & 1) && c.n >= 4;
+        } else {
+            c.im = &args.one;
+            c.band = args.one.k - 1 - (int)(item / args.one.tiles);
+            c.tile = (int)(item % args.one.tiles);
+            c.n = args.one.n;
+            c.tma = args.one.use_tma && c.n >= 4;
+        }
+        return c;
+    }
+    // Lane 0: the item's strip copy into Hc, and its slot for the compute warps.
+    __device__ static void hand_over(const Ctrl &c, WsSlot *slot, void *Hc, Pipe &pipe) {
+        if (c.im && c.tma) issue_strip(&c.im->tmap, c.n, c.band, c.tile, Hc, pipe);
+        slot->item = c.item;
+        slot->im = c.im;
+        slot->band = c.band;
+        slot->tile = c.tile;
+        slot->prefetched = c.im && c.tma;
+    }
+
+    // The control warp: takes the items from the queue one ahead of the
+    // compute warps, copies each strip as soon as Hc is free, waits for an
+    // item's producers during its FHT, copies its M tile as soon as the FHT is
+    // done, and releases its flag once its window maxima are stored (band 0:
+    // counts the tile and reads the polyline back after the image's last).
+    __device__ static void control(const LaunchArgs &args, unsigned char *smem, WsSlot *slot,
+                                   Pipe &pipe) {
+        const int lane = threadIdx.x & 31;
+        uint32_t *Hc = (uint32_t *)(smem + hc_offset());
+        int32_t *Vn = (int32_t *)smem;
+        long long first = 0;
+        if (lane == 0) first = atomicAdd(&args.ctl->queue, 1);
+        Ctrl cur = decode(args, __shfl_sync(0xffffffffu, first, 0));
+        if (lane == 0) hand_over(cur, slot, Hc, pipe);
+        nb_arrive(kBarNext, kCtlSync);
+        while (cur.item < args.items) {
+            long long nx = 0;
+            if (lane == 0) nx = atomicAdd(&args.ctl->queue, 1);
+            const Ctrl next = decode(args, __shfl_sync(0xffffffffu, nx, 0));
+            const ImgDesc &im = *cur.im;
+            const int n = im.n, D = 2 * n - 1;
+            // Lanes 0..2: the three band+1 tiles this tile reads.
+            bool ok = true;
+            const int c = cur.tile - 1 + lane;
+            if (cur.band < im.k - 1 && lane < 3 && c >= 0 && c < im.tiles) {
+                ok = wait_flag(im.flags + (size_t)(cur.band + 1) * im.tiles + c, args.ctl,
+                               args.wait_cycles);
+                fence_acq_rel_gpu();
+            }
+            __syncwarp();
+            ok = __all_sync(0xffffffffu, ok);
+            nb_sync(kBarFhtDone, kCtlSync);
+            if (lane == 0) {
+                if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                if (im.use_mtma && cur.band < im.k - 1) {
+                    fence_proxy_async_global();
+                    fence_proxy_async_smem();
+                    mbar_expect_tx(pipe.mbar, (uint32_t)(kTile * D * 4));
+                    tma_load_2d(Vn + kPad * kTile, &im.mtmap, kMOff + cur.tile * kTile,
+                                ((cur.band + 1) & 1) * D, pipe.mbar);
+                } else {
+                    mbar_arrive(pipe.mbar);
+                }
+            }
+            nb_sync(kBarHcFree, kCtlSync);
+            if (lane == 0) hand_over(next, slot, Hc, pipe);
+            nb_arrive(kBarNext, kCtlSync);
+            nb_sync(kBarWinDone, kCtlSync);
+            if (lane == 0) {
+                const ImgDesc &first_im = args.many ? args.many[0] : args.one;
+                if (cur.band != 0) {
+                    if (!(cur.band == args.skip_band && cur.tile == args.skip_tile &&
+                          im.flags == first_im.flags)) {
+                        fence_acq_rel_gpu();
+                        st_release(im.flags + (size_t)cur.band * im.tiles + cur.tile, 1);
+                    }
+                } else {
+                    __threadfence();
+                    if (atomicAdd(im.done, 1) == im.tiles - 1) readback<Acc>(im, args);
+                }
+            }
+            cur = next;
+        }
     }
 };
 
@@ -1501,14 +1585,14 @@ struct WidePath {
                                     __uint_as_float(to_bits(v[1])), __uint_as_float(to_bits(v[0])));
                 *(float4 *)&F[(size_t)y * pitch + u0] = o;
             }
-            __syncthreads();
+            csync();
             fht_levels<Acc>(F, pitch, n, im.log2n, T);
             if (sign == 0) {
                 for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
                     const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
                     *(float4 *)&Hp[r * T + u0] = *(const float4 *)&F[(size_t)r * pitch + u0];
                 }
-                __syncthreads();
+                csync();
             }
         }
     }
@@ -1579,7 +1663,7 @@ struct WidePath {
             finish_band0<Acc>(best, im, args, take_next);
             return true;
         }
-        __syncthreads();
+        csync();
 
         const int u = threadIdx.x % T, qd = threadIdx.x / T;
         const int x = x0 + u;
@@ -1610,7 +1694,7 @@ struct WidePath {
             if (c0 <= c1 && x < im.w)
                 window_two_pass<Key>(c0, c1, B, lo - B, lo, hi, KO::dead(), vkey, sput, sget,
                                          emit);
-            __syncthreads();
+            csync();
         }
         publish(im, band, tile, args);
         if (threadIdx.x == 0) take_next();
@@ -1619,18 +1703,9 @@ struct WidePath {
 };
 
 template <typename In, typename Acc, typename Key>
-struct PathOf {
-    using type = WidePath<In, Acc, Key>;
-};
-template <typename Key>
-struct PathOf<uint8_t, int32_t, Key> {
-    using type = U8Path<Key>;
-};
-
-template <typename In, typename Acc, typename Key>
 __global__ void __launch_bounds__(kThreads, 1)
     engine_kernel(const __grid_constant__ LaunchArgs args) {
-    using P = typename PathOf<In, Acc, Key>::type;
+    using P = WidePath<In, Acc, Key>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_mbar;
@@ -1642,7 +1717,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         stage_next(args, &s_next, atomicAdd(&args.ctl->queue, 1));
         cp_async_wait_all();
     }
-    __syncthreads();
+    csync();
     Pipe pipe{&s_bar, 0u, &s_mbar, 0u, &s_next};
     for (;;) {
         const long long item = s_next.item;
@@ -1650,11 +1725,43 @@ __global__ void __launch_bounds__(kThreads, 1)
         const ImgDesc *imp = nullptr;
         int band = 0, tile = 0;
         if (item < args.items) decode_staged(args, s_next, &imp, &band, &tile);
-        __syncthreads();   // thread 0 rewrites s_next inside process
+        csync();   // thread 0 rewrites s_next inside process
         if (item >= args.items) break;
         if (!P::process(*imp, band, tile, smem_raw, args, pipe, prefetched)) return;
         if (threadIdx.x == 0) cp_async_wait_all();
-        __syncthreads();
+        csync();
+    }
+}
+
+// The uint8 engine: four compute warpgroups (112 registers a thread) and a
+// control warp (32 registers; the rest of its warpgroup exits at once).  The
+// register split adds up to the launch's 640 x 96.
+template <typename Key>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    engine_kernel_u8(const __grid_constant__ LaunchArgs args) {
+    using P = U8Path<Key>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(16) WsSlot s_slot;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        mbar_init(&s_mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    Pipe pipe{&s_bar, 0u, &s_mbar, 0u, nullptr};
+    if (threadIdx.x < kThreads) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 112;" ::: "memory");
+        for (;;) {
+            nb_sync(kBarNext, kCtlSync);
+            const WsSlot sl = s_slot;
+            if (sl.item >= args.items) break;
+            P::process(*sl.im, sl.band, sl.tile, smem_raw, args, pipe, sl.prefetched != 0);
+        }
+    } else {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 32;" ::: "memory");
+        if (threadIdx.x < kCtlSync) P::control(args, smem_raw, &s_slot, pipe);
     }
 }
 
@@ -1821,7 +1928,7 @@ int num_sms() {
 
 template <typename In, typename Acc, typename Key>
 int launch_kernel(const LaunchArgs &args, int max_n, cudaStream_t stream) {
-    using P = typename PathOf<In, Acc, Key>::type;
+    using P = WidePath<In, Acc, Key>;
     const size_t smem = P::smem_bytes(max_n);
     auto kern = engine_kernel<In, Acc, Key>;
     static int smem_set = 0;   // dynamic shared memory enabled for this kernel
@@ -1843,14 +1950,34 @@ int launch_kernel(const LaunchArgs &args, int max_n, cudaStream_t stream) {
     return launched("engine_kernel");
 }
 
+template <typename Key>
+int launch_kernel_u8(const LaunchArgs &args, int max_n, cudaStream_t stream) {
+    using P = U8Path<Key>;
+    const size_t smem = P::smem_bytes(max_n);
+    auto kern = engine_kernel_u8<Key>;
+    static int smem_set = 0;   // dynamic shared memory enabled for this kernel
+    if ((int)smem > smem_set) {
+        int st = cuda_status(cudaFuncSetAttribute(kern,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)P::smem_bytes(kMaxBandFused)),
+                             "cudaFuncSetAttribute");
+        if (st) return st;
+        smem_set = (int)P::smem_bytes(kMaxBandFused);
+    }
+    long long grid = num_sms();
+    if (grid > args.items) grid = args.items;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kWsThreads, smem, stream>>>(args);
+    return launched("engine_kernel_u8");
+}
+
 int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, cudaStream_t stream) {
     switch (dtype) {
         case FHTDP_U8:
             // 32-bit keys: values below 2^22, and dead keys (negative) that
             // take on at most 512 * (255 h + k) over the bands stay negative.
-            if (256LL * max_h < (1LL << 22))
-                return launch_kernel<uint8_t, int32_t, int32_t>(args, max_n, stream);
-            return launch_kernel<uint8_t, int32_t, long long>(args, max_n, stream);
+            if (256LL * max_h < (1LL << 22)) return launch_kernel_u8<int32_t>(args, max_n, stream);
+            return launch_kernel_u8<long long>(args, max_n, stream);
         case FHTDP_I32:
             return launch_kernel<int32_t, int32_t, long long>(args, max_n, stream);
         default:
