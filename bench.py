@@ -50,12 +50,12 @@ WORKLOADS = {
              "+ pruned DP + full-DP fallback, against the plain DP", images=512, dtype="u8"),
 }
 
-# DRAM bytes (read + write) per image of engine_kernel<uint8> on the default
+# DRAM bytes (read + write) per image of engine_kernel_u8 on the default
 # workload from the ncu capture summarised in
 # profiles/engine_kernel_u8_2048x2048_k16_B16.md (48 images per launch); a
 # launch's traffic is this times its images.  None for other workloads, and
 # to be reset whenever the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (212.667904e6 + 709.79968e6) / 48}
+NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (214.150144e6 + 770.339328e6) / 48}
 
 
 def algorithmic_bytes(h, w, k, bpp):
@@ -366,7 +366,7 @@ def run_ours(args):
                          "frac": achieved / hbm,
                          "traffic": traffic * len(items) if traffic else None,
                          "peak_kind": peak_kind,
-                         "kernel": "engine_kernel (one persistent launch per step)"},
+                         "kernel": "engine_kernel_u8 (one persistent launch per step)"},
             "single_image_ms": statistics.median(lat),
             "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
