@@ -1563,84 +1563,122 @@ struct WidePath {
         for (int j = 0; j < 4; ++j) out[j] = (Acc)pix(row, c + j, w);
     }
 
+    // The "+" half first: its last level writes Hp[s][u] (natural shift
+    // order); then the "-" half, which stays in F with shift s in row
+    // brev(s).  The strip loads of a thread are issued in batches before any
+    // of their shared stores, so that their latencies overlap.
     __device__ static void fht(Acc *F, Acc *Hp, const ImgDesc &im, int band, int x0) {
         const int n = im.n, T = kTile, pitch = fpitch(n);
         const int G = (T + n - 1 + 3) / 4;
         const In *base = (const In *)im.img + (size_t)band * n * im.pitch;
         const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 4 == 0);
+        constexpr int kLB = 8;
         for (int sign = 0; sign < 2; ++sign) {
             // "+": word u = pixel x0 + u; "-": word u = pixel x0 + T - 1 - u.
-#pragma unroll 4
-            for (int idx = threadIdx.x; idx < n * G; idx += kThreads) {
-                const int y = idx / G, u0 = 4 * (idx - y * G);
-                const In *row = base + (size_t)y * im.pitch;
-                Acc v[4];
-                load4(row, sign == 0 ? x0 + u0 : x0 + T - 4 - u0, im.w, aligned, v);
-                float4 o;
-                if (sign == 0)
-                    o = make_float4(__uint_as_float(to_bits(v[0])), __uint_as_float(to_bits(v[1])),
-                                    __uint_as_float(to_bits(v[2])), __uint_as_float(to_bits(v[3])));
-                else
-                    o = make_float4(__uint_as_float(to_bits(v[3])), __uint_as_float(to_bits(v[2])),
-                                    __uint_as_float(to_bits(v[1])), __uint_as_float(to_bits(v[0])));
-                *(float4 *)&F[(size_t)y * pitch + u0] = o;
+            for (int b0 = threadIdx.x; b0 < n * G; b0 += kLB * kThreads) {
+                Acc v[kLB][4];
+#pragma unroll
+                for (int i = 0; i < kLB; ++i) {
+                    const int idx = b0 + i * kThreads;
+                    if (idx < n * G) {
+                        const int y = idx / G, u0 = 4 * (idx - y * G);
+                        load4(base + (size_t)y * im.pitch, sign == 0 ? x0 + u0 : x0 + T - 4 - u0,
+                              im.w, aligned, v[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kLB; ++i) {
+                    const int idx = b0 + i * kThreads;
+                    if (idx < n * G) {
+                        const int y = idx / G, u0 = 4 * (idx - y * G);
+                        const bool fw = sign == 0;
+                        *(float4 *)&F[(size_t)y * pitch + u0] =
+                            make_float4(__uint_as_float(to_bits(fw ? v[i][0] : v[i][3])),
+                                        __uint_as_float(to_bits(fw ? v[i][1] : v[i][2])),
+                                        __uint_as_float(to_bits(fw ? v[i][2] : v[i][1])),
+                                        __uint_as_float(to_bits(fw ? v[i][3] : v[i][0])));
+                    }
+                }
             }
             csync();
-            fht_levels<Acc>(F, pitch, n, im.log2n, T);
             if (sign == 0) {
-                for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
-                    const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
-                    *(float4 *)&Hp[r * T + u0] = *(const float4 *)&F[(size_t)r * pitch + u0];
+                if (!fht_merge<Acc>(F, pitch, n, im.log2n, T, 1, Hp)) {   // n = 1
+                    for (int idx = threadIdx.x; idx < T / 4; idx += kThreads)
+                        *(float4 *)&Hp[4 * idx] = *(const float4 *)&F[4 * idx];
+                    csync();
                 }
-                csync();
+            } else {
+                fht_merge<Acc>(F, pitch, n, im.log2n, T, 1);
             }
         }
     }
 
     // V(x0 + u, e) after form_v; e inside [-(n-1), n-1].
     __device__ static Acc vval(const Acc *F, const Acc *Hp, int pitch, int log2n, int u, int e) {
-        if (e >= 0) return Hp[(size_t)brev(e, log2n) * kTile + u];
+        if (e >= 0) return Hp[(size_t)e * kTile + u];
         return F[(size_t)brev(-e, log2n) * pitch + (kTile - 1 - u)];
     }
 
-    __device__ static Acc link_value(Acc h, const ImgDesc &im, int band, const Acc *mprev, int x,
-                                     int e, int wlo, int whi) {
+    // V = H + M_{b+1}(x + e, e) (dead outside the image or the window); m is
+    // the M word of (x, e), loaded ahead by the caller (ignored in the last
+    // band, which has no M).
+    __device__ static Acc link_value(Acc h, Acc m, const ImgDesc &im, int band, int x, int e,
+                                     int wlo, int whi) {
         const Acc dead = Dead<Acc>::value();
         const bool ok = x < im.w && x + e >= 0 && x + e < im.w && e >= wlo && e <= whi;
         if (!ok) return dead;
         if (band == im.k - 1) return h;
-        const Acc m = __ldcg(mprev + (size_t)(e + im.n - 1) * im.mpitch + kMOff + x);
         return m == dead ? dead : h + m;
     }
 
+    // The M loads of a batch of iterations are issued before any of its
+    // shared stores (every address lies inside the M buffer).
     __device__ static unsigned long long form_v(Acc *F, Acc *Hp, const ImgDesc &im, int band,
                                                 const Acc *mprev, int x0) {
         const int n = im.n, T = kTile, pitch = fpitch(n);
+        const bool last = band == im.k - 1;
         int wlo, whi;
         band_window(im, band, &wlo, &whi);
         unsigned long long best = 0;
-#pragma unroll 4
-        for (int idx = threadIdx.x; idx < n * T; idx += kThreads) {
-            const int slot = idx / T, up = idx - slot * T;
-            const int s = brev(slot, im.log2n);
-            const int xp = x0 + up, xm = x0 + T - 1 - up;
-            const Acc vp = link_value(Hp[idx], im, band, mprev, xp, s, wlo, whi);
-            const Acc vm = s > 0 ? link_value(F[(size_t)slot * pitch + up], im, band, mprev, xm, -s,
-                                              wlo, whi)
-                                 : Dead<Acc>::value();
-            if (band == 0) {
-                const Acc dead = Dead<Acc>::value();
-                if (vp != dead) {
-                    const unsigned long long k = argmax_key(ord32(vp), xp, s + n - 1);
-                    best = best > k ? best : k;
+        constexpr int kLB = 8;
+        const Acc dead = Dead<Acc>::value();
+        for (int b0 = threadIdx.x; b0 < n * T; b0 += kLB * kThreads) {
+            Acc mp[kLB], mm[kLB];
+#pragma unroll
+            for (int i = 0; i < kLB; ++i) {
+                const int idx = b0 + i * kThreads;
+                mp[i] = mm[i] = dead;
+                if (idx < n * T && !last) {
+                    const int s = idx / T, up = idx - s * T;
+                    mp[i] = __ldcg(mprev + (size_t)(s + n - 1) * im.mpitch + kMOff + x0 + up);
+                    mm[i] = __ldcg(mprev + (size_t)(n - 1 - s) * im.mpitch + kMOff + x0 + T - 1 -
+                                   up);
                 }
-                if (vm != dead) {
-                    const unsigned long long k = argmax_key(ord32(vm), xm, n - 1 - s);
-                    best = best > k ? best : k;
+            }
+#pragma unroll
+            for (int i = 0; i < kLB; ++i) {
+                const int idx = b0 + i * kThreads;
+                if (idx >= n * T) break;
+                const int s = idx / T, up = idx - s * T;
+                const int slot = brev(s, im.log2n);
+                const int xp = x0 + up, xm = x0 + T - 1 - up;
+                const Acc vp = link_value(Hp[idx], mp[i], im, band, xp, s, wlo, whi);
+                const Acc vm = s > 0 ? link_value(F[(size_t)slot * pitch + up], mm[i], im, band,
+                                                  xm, -s, wlo, whi)
+                                     : dead;
+                if (band == 0) {
+                    if (vp != dead) {
+                        const unsigned long long k = argmax_key(ord32(vp), xp, s + n - 1);
+                        best = best > k ? best : k;
+                    }
+                    if (vm != dead) {
+                        const unsigned long long k = argmax_key(ord32(vm), xm, n - 1 - s);
+                        best = best > k ? best : k;
+                    }
+                } else {
+                    Hp[idx] = vp;
+                    F[(size_t)slot * pitch + up] = vm;
                 }
-            } else {
-                Hp[idx] = vp;
-                F[(size_t)slot * pitch + up] = vm;
             }
         }
         return best;
