@@ -69,6 +69,162 @@ __global__ void dp_band_kernel(Acc *hv, Shape s, int band, int B) {
     }
 }
 
+// The same DP with the bend-window maxima taken once per column instead of
+// once per state (for callers that can give a scratch buffer Mw of
+// (2n-1) x W values): Mw(x, e) = max over |e' - e| <= B of V_{b+1}(x, e').
+// A block loads C columns x all displacements of V_{b+1} (with dead rows
+// beyond [-(n-1), n-1]) into shared memory and takes the window maxima by
+// doubling: after step j a row holds the maximum of 2^j consecutive rows, and
+// a window of L = 2B+1 rows is the maximum of two such runs.  Max is exact,
+// so the values are those of the scan.
+template <typename Acc>
+__global__ void dp_window_kernel(const Acc *hv, Shape s, int band1, int B, int C, Acc *Mw) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const int D = 2 * s.n - 1, R = D + 2 * B;
+    Acc *a = (Acc *)raw, *b = a + (size_t)R * C;
+    const int x0 = blockIdx.x * C;
+    const Acc dead = Dead<Acc>::value();
+    for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
+        const int r = i / C, c = i - r * C;
+        const int e = r - B - (s.n - 1), x = x0 + c;
+        a[i] = (e >= -(s.n - 1) && e <= s.n - 1 && x < s.w) ? hv[cell<Acc>(s, band1, x, e)] : dead;
+    }
+    __syncthreads();
+    const int L = 2 * B + 1;
+    int len = 1;
+    for (; 2 * len <= L; len *= 2) {
+        for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
+            const int r = i / C;
+            b[i] = r + len < R ? vmax(a[i], a[i + len * C]) : a[i];
+        }
+        __syncthreads();
+        Acc *t = a;
+        a = b;
+        b = t;
+    }
+    // Window of e (padded row e + n - 1 + B): rows [e + n - 1, e + n - 1 + 2B].
+    for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+        const int r = i / C, c = i - r * C, x = x0 + c;
+        if (x >= s.w) continue;
+        Mw[(size_t)r * s.W + x] = vmax(a[r * C + c], a[(r + L - len) * C + c]);
+    }
+}
+
+// Band `band` < k-1 from the window maxima of band+1.
+template <typename Acc>
+__global__ void dp_combine_kernel(Acc *hv, Shape s, int band, const Acc *Mw) {
+    const size_t per_band = (size_t)2 * s.n * s.W;
+    const Acc dead = Dead<Acc>::value();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_band;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % s.W);
+        const int r = (int)(i / s.W);
+        const int sh = r % s.n, sign = r / s.n;
+        const int d = sign ? -sh : sh;
+        const size_t idx = (size_t)band * per_band + i;
+        const int xn = x + d;
+        if (x >= s.w || xn < 0 || xn >= s.w) {
+            hv[idx] = dead;
+            continue;
+        }
+        const Acc best = Mw[(size_t)(d + s.n - 1) * s.W + xn];
+        hv[idx] = (best == dead) ? dead : hv[idx] + best;
+    }
+}
+
+// Order-preserving 32-bit image of a value (negative zero counts as zero).
+__device__ __forceinline__ uint32_t vord(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t vord(float f) {
+    const uint32_t b = __float_as_uint(f == 0.0f ? 0.0f : f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+template <typename Acc>
+__device__ __forceinline__ Acc vfrom(uint32_t o);
+template <>
+__device__ __forceinline__ int32_t vfrom<int32_t>(uint32_t o) {
+    return (int32_t)(o ^ 0x80000000u);
+}
+template <>
+__device__ __forceinline__ float vfrom<float>(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Grid-wide argmax of V_0 as one 64-bit key: the value's order image above
+// the complement of the lexicographic index x * D + (d + n - 1), so that the
+// largest key is the largest value at the smallest index (*key starts at 0).
+template <typename Acc>
+__global__ void argmax_kernel(const Acc *V, Shape s, unsigned long long *key) {
+    const Acc dead = Dead<Acc>::value();
+    unsigned long long best = 0;
+    const int total = s.w * s.D;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i / s.w, x = i - e * s.w;   // x fastest: coalesced rows
+        const Acc v = V[cell<Acc>(s, 0, x, e - (s.n - 1))];
+        if (v == dead) continue;
+        const unsigned long long k = ((unsigned long long)vord(v) << 32) |
+                                     (0xffffffffu - (unsigned)(x * s.D + e));
+        best = best > k ? best : k;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = best > other ? best : other;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+// One warp: the read-back from the argmax key (Eq. 5); every band's window
+// is scanned by the lanes, the first maximum kept.  No admissible state
+// (key 0): x = -1 everywhere and a dead score.
+template <typename Acc>
+__global__ void readback_kernel(const Acc *V, Shape s, int B, const unsigned long long *key,
+                                int32_t *x_out, int32_t *d_out, Acc *score_out) {
+    const int lane = threadIdx.x;
+    const Acc dead = Dead<Acc>::value();
+    const unsigned long long kv = *key;
+    if (kv == 0) {
+        if (lane == 0) {
+            *score_out = dead;
+            for (int i = 0; i <= s.k; ++i) x_out[i] = -1;
+            for (int i = 0; i < s.k; ++i) d_out[i] = 0;
+        }
+        return;
+    }
+    const unsigned lin = 0xffffffffu - (unsigned)(kv & 0xffffffffu);
+    int x = (int)(lin / s.D), d = (int)(lin % s.D) - (s.n - 1);
+    if (lane == 0) {
+        x_out[0] = x;
+        d_out[0] = d;
+        *score_out = vfrom<Acc>((uint32_t)(kv >> 32));
+    }
+    for (int i = 1; i < s.k; ++i) {
+        x += d;
+        const int lo = max(d - B, -(s.n - 1)), hi = min(d + B, s.n - 1);
+        Acc bv = dead;
+        int be = INT_MAX;
+        for (int e = lo + lane; e <= hi; e += 32) {
+            const Acc v = V[cell<Acc>(s, i, x, e)];
+            if (v > bv) {
+                bv = v;
+                be = e;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const Acc ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oe = __shfl_xor_sync(0xffffffffu, be, o);
+            if (ov > bv || (ov == bv && oe < be)) {
+                bv = ov;
+                be = oe;
+            }
+        }
+        d = be == INT_MAX ? lo : be;
+        if (lane == 0) {
+            x_out[i] = x;
+            d_out[i] = d;
+        }
+    }
+    if (lane == 0) x_out[s.k] = x + d;
+}
+
 // One block: lexicographically smallest argmax of V_0, then the read-back.
 template <typename Acc>
 __global__ void backtrack_kernel(const Acc *V, Shape s, int B, int32_t *x_out, int32_t *d_out,
@@ -146,6 +302,34 @@ int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream) {
 }
 
 template <typename Acc>
+int launch_dp_window(Acc *hv, const Shape &s, int B, Acc *Mw, cudaStream_t stream) {
+    const size_t per_band = (size_t)2 * s.n * s.W;
+    const int D = 2 * s.n - 1;
+    // A window beyond the displacement range covers all of it.
+    const int Bc = B < D - 1 ? B : D - 1;
+    const int R = D + 2 * Bc;
+    int C = 32;
+    while (C > 1 && (size_t)2 * R * C * sizeof(Acc) > 200 * 1024) C /= 2;
+    const size_t smem = (size_t)2 * R * C * sizeof(Acc);
+    int st = cuda_status(cudaFuncSetAttribute(dp_window_kernel<Acc>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "cudaFuncSetAttribute");
+    if (st) return st;
+    dp_last_band_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
+    st = launched("dp_last_band_kernel");
+    for (int band = s.k - 2; band >= 0 && !st; --band) {
+        dp_window_kernel<Acc><<<(s.w + C - 1) / C, 512, smem, stream>>>(hv, s, band + 1, Bc, C,
+                                                                          Mw);
+        st = launched("dp_window_kernel");
+        if (st) break;
+        dp_combine_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s, band, Mw);
+        st = launched("dp_combine_kernel");
+    }
+    return st;
+}
+
+template <typename Acc>
 int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_t *d_out,
                      Acc *score_out, cudaStream_t stream) {
     backtrack_kernel<Acc><<<1, 1024, 0, stream>>>(V, s, B, x_out, d_out, score_out);
@@ -154,6 +338,23 @@ int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_
 
 template int launch_dp_inplace<int32_t>(int32_t *, const Shape &, int, cudaStream_t);
 template int launch_dp_inplace<float>(float *, const Shape &, int, cudaStream_t);
+template <typename Acc>
+int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long *key,
+                         int32_t *x_out, int32_t *d_out, Acc *score_out, cudaStream_t stream) {
+    argmax_kernel<Acc><<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key);
+    int st = launched("argmax_kernel");
+    if (st) return st;
+    readback_kernel<Acc><<<1, 32, 0, stream>>>(V, s, B, key, x_out, d_out, score_out);
+    return launched("readback_kernel");
+}
+
+template int launch_backtrack_key<int32_t>(const int32_t *, const Shape &, int,
+                                           unsigned long long *, int32_t *, int32_t *, int32_t *,
+                                           cudaStream_t);
+template int launch_backtrack_key<float>(const float *, const Shape &, int, unsigned long long *,
+                                         int32_t *, int32_t *, float *, cudaStream_t);
+template int launch_dp_window<int32_t>(int32_t *, const Shape &, int, int32_t *, cudaStream_t);
+template int launch_dp_window<float>(float *, const Shape &, int, float *, cudaStream_t);
 template int launch_backtrack<int32_t>(const int32_t *, const Shape &, int, int32_t *, int32_t *,
                                        int32_t *, cudaStream_t);
 template int launch_backtrack<float>(const float *, const Shape &, int, int32_t *, int32_t *,
