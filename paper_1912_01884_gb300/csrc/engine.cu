@@ -2106,11 +2106,19 @@ struct BatchPlan {
     int dtype;
     std::vector<ImgPlan> imgs;      // images of the fused launch
     std::vector<ImgPlan> separate;  // 256-row bands: run with the standalone kernels
-    size_t separate_off = 0;        // their shared scratch (one image at a time)
+    size_t separate_off = 0;        // their scratch: `lanes` slices of sep_bytes
+    size_t sep_bytes = 0;
+    int lanes = 0;                  // streams the separate images are spread over
+    std::vector<cudaStream_t> side; // one non-blocking stream per lane
+    std::vector<cudaEvent_t> ev;    // fork + one join per lane
     RunLayout L;
     std::vector<ImgDesc> staging;   // image table as uploaded
     std::vector<Item> order;        // work queue as uploaded
     void *bound_ws = nullptr;
+    ~BatchPlan() {
+        for (cudaStream_t st : side) cudaStreamDestroy(st);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
 };
 
 // Queue order of a batch.  Images are taken in groups whose band levels
@@ -2214,11 +2222,30 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
             plan->imgs.push_back(p);
     }
     plan->L = plan_layout(plan->imgs, true);
-    // Scratch of the standalone path, reused image after image (stream order).
+    // Scratch of the standalone path: up to 4 lanes, each a stream that runs
+    // its images one after the other on its own slice.
     size_t sep = 0;
     for (auto &p : plan->separate) sep = std::max(sep, engine_workspace_bytes(dtype, p.s, p.io.B));
+    plan->sep_bytes = align_up(sep, 256);
+    plan->lanes = (int)std::min<size_t>(4, plan->separate.size());
     plan->separate_off = align_up(plan->L.total, 256);
-    if (sep) plan->L.total = plan->separate_off + sep;
+    if (sep) plan->L.total = plan->separate_off + plan->sep_bytes * plan->lanes;
+    for (int l = 0; l < plan->lanes; ++l) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete plan;
+            return cuda_status(cudaGetLastError(), "cudaStreamCreateWithFlags");
+        }
+        plan->side.push_back(st);
+    }
+    for (int l = 0; plan->lanes && l <= plan->lanes; ++l) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            delete plan;
+            return cuda_status(cudaGetLastError(), "cudaEventCreateWithFlags");
+        }
+        plan->ev.push_back(e);
+    }
     plan->order = queue_order(plan->imgs, (long long)num_sms());
     *out = plan;
     return FHTDP_OK;
@@ -2257,21 +2284,38 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
     char *base = (char *)ws;
     int st = cuda_status(cudaMemsetAsync(base, 0, plan->L.zero_bytes, stream), "cudaMemsetAsync");
     if (st) return st;
-    if (!plan->imgs.empty()) {
+    // Images with 256-row bands: the standalone kernels, spread over the
+    // plan's lanes (forked from and joined back into `stream` by events, so
+    // the run stays one stream-ordered operation for the caller).
+    if (plan->lanes) {
+        st = cuda_status(cudaEventRecord(plan->ev[0], stream), "cudaEventRecord");
+        for (int l = 0; l < plan->lanes && !st; ++l)
+            st = cuda_status(cudaStreamWaitEvent(plan->side[l], plan->ev[0], 0),
+                             "cudaStreamWaitEvent");
+        for (size_t i = 0; i < plan->separate.size() && !st; ++i) {
+            const ImgPlan &p = plan->separate[i];
+            const int l = (int)(i % plan->lanes);
+            st = run_fallback(p.io.img, plan->dtype, p.io.pitch, p.s, p.io.B, p.io.x_out,
+                              p.io.d_out, p.io.score_out,
+                              base + plan->separate_off + plan->sep_bytes * l, plan->side[l]);
+        }
+    }
+    if (!plan->imgs.empty() && !st) {
         LaunchArgs args = base_args(plan->L, base, (int)plan->imgs.size());
         args.many = (const ImgDesc *)(base + plan->L.table_off);
         args.order = (const Item *)(base + plan->L.order_off);
         st = dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, stream);
-        if (st) return st;
     }
-    // Images with 256-row bands: the level-by-level FHT, the in-place DP and
-    // the one-block read-back, in stream order on the shared scratch.
-    for (const auto &p : plan->separate) {
-        st = run_fallback(p.io.img, plan->dtype, p.io.pitch, p.s, p.io.B, p.io.x_out, p.io.d_out,
-                          p.io.score_out, base + plan->separate_off, stream);
-        if (st) return st;
+    // Join the lanes back (also after an error, so that `stream` never runs
+    // ahead of work it forked).
+    for (int l = 0; l < plan->lanes; ++l) {
+        int js = cuda_status(cudaEventRecord(plan->ev[1 + l], plan->side[l]), "cudaEventRecord");
+        if (!js)
+            js = cuda_status(cudaStreamWaitEvent(stream, plan->ev[1 + l], 0),
+                             "cudaStreamWaitEvent");
+        if (!st) st = js;
     }
-    return FHTDP_OK;
+    return st ? st : FHTDP_OK;
 }
 
 void batch_destroy(BatchPlan *plan) { delete plan; }
