@@ -83,6 +83,38 @@ __global__ void fht_level_kernel(const Acc *__restrict__ src, Shape s, int m,
     }
 }
 
+// Two levels in one pass: sub-bands of M = 4m rows from the level of m-row
+// sub-bands J0..J3.  With S the shift, s2 = S >> 1 and q = S >> 2,
+//   out(x, S) = [J0(x, q) + J1(x +/- ceil(s2/2), q)]
+//             + [J2(x', q) + J3(x' +/- ceil(s2/2), q)],   x' = x +/- ceil(S/2),
+// the same sum tree as the two radix-2 levels (so float sums are unchanged).
+template <typename Acc>
+__global__ void fht_level4_kernel(const Acc *__restrict__ src, Shape s, int M,
+                                  Acc *__restrict__ dst) {
+    const size_t total = (size_t)s.k * 2 * s.n * s.W;
+    const int m = M >> 2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % s.W);
+        const size_t r = i / s.W;
+        const int row = (int)(r % s.n);
+        const size_t bs = r / s.n;
+        const int sign = (int)(bs & 1);
+        const int j0 = row & ~(M - 1);
+        const int S = row & (M - 1), s2 = S >> 1, q = S >> 2;
+        const int c2 = s2 - (s2 >> 1), cS = S - (S >> 1);
+        const int x1 = wrap(sign == 0 ? x + c2 : x - c2, s.W);
+        const int xp = wrap(sign == 0 ? x + cS : x - cS, s.W);
+        const int x3 = wrap(sign == 0 ? xp + c2 : xp - c2, s.W);
+        const Acc *base = src + bs * s.n * (size_t)s.W;
+        const Acc a0 = base[(size_t)(j0 + q) * s.W + x];
+        const Acc a1 = base[(size_t)(j0 + m + q) * s.W + x1];
+        const Acc a2 = base[(size_t)(j0 + 2 * m + q) * s.W + xp];
+        const Acc a3 = base[(size_t)(j0 + 3 * m + q) * s.W + x3];
+        dst[i] = (a0 + a1) + (a2 + a3);
+    }
+}
+
 int grid_for(size_t total) {
     size_t blocks = (total + 255) / 256;
     size_t cap = 152 * 16;
@@ -101,19 +133,26 @@ int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc 
     }
     const size_t total = (size_t)s.k * 2 * s.n * s.W;
     const int levels = s.log2n;
-    // Level l (sub-bands of 2^l rows) writes to hough when (levels - l) is
-    // even, so that the last level lands in hough.
-    auto dst_of = [&](int l) { return ((levels - l) % 2 == 0) ? hough : tmp; };
-    fht_level2_kernel<In, Acc><<<grid_for(total), 256, 0, stream>>>(img, pitch, s, dst_of(1));
+    // Passes: level 1 from the image, then two levels at a time, then one
+    // if a level is left.  The passes alternate between tmp and hough so
+    // that the last one lands in hough.
+    const int passes = 1 + (levels - 1) / 2 + (levels - 1) % 2;
+    int pass = 0;
+    auto dst_of = [&](int p) { return ((passes - 1 - p) % 2 == 0) ? hough : tmp; };
+    fht_level2_kernel<In, Acc><<<grid_for(total), 256, 0, stream>>>(img, pitch, s, dst_of(0));
     int st = launched("fht_level2_kernel");
-    if (st) return st;
-    for (int l = 2; l <= levels; ++l) {
-        fht_level_kernel<Acc><<<grid_for(total), 256, 0, stream>>>(dst_of(l - 1), s, 1 << l,
-                                                                   dst_of(l));
-        st = launched("fht_level_kernel");
-        if (st) return st;
+    int l = 1;
+    for (; l + 2 <= levels && !st; l += 2, ++pass) {
+        fht_level4_kernel<Acc><<<grid_for(total), 256, 0, stream>>>(dst_of(pass), s, 1 << (l + 2),
+                                                                    dst_of(pass + 1));
+        st = launched("fht_level4_kernel");
     }
-    return FHTDP_OK;
+    if (l < levels && !st) {
+        fht_level_kernel<Acc><<<grid_for(total), 256, 0, stream>>>(dst_of(pass), s, 1 << levels,
+                                                                   dst_of(pass + 1));
+        st = launched("fht_level_kernel");
+    }
+    return st;
 }
 
 template int launch_fht_stages<uint8_t, int32_t>(const uint8_t *, int, const Shape &, int32_t *,
