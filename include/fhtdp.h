@@ -256,6 +256,20 @@ int fhtdp_batch_upload(fhtdp_batch_plan *plan, void *ws, size_t ws_bytes, cudaSt
 int fhtdp_batch_run(const fhtdp_batch_plan *plan, void *ws, cudaStream_t stream);
 /* Number of work items (image, band, column tile) of a run. */
 long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
+/* Tunes the plan's work-queue order on its bound workspace (after
+ * fhtdp_batch_upload): the queue takes images in groups whose band levels
+ * hold about `target` column tiles, so that the band chains of a group advance
+ * together; wider groups wait less for dependencies, narrower ones keep fewer
+ * window-maximum buffers in L2.  The call runs the batch `reps` times (plus one
+ * warm-up) for each of a few widths between half and three times the SM count
+ * (and the whole batch as one group), keeps the fastest, uploads its order and
+ * writes its width to *target_out (may be NULL).  The outputs are those of an
+ * ordinary run.  It synchronises `stream` (not for use under stream capture).
+ * Column tile width and FHT fusion depth are fixed by the kernel's shared
+ * memory layout and are not tuned.  The paper has no counterpart: it tunes the
+ * GPU schedule of its method, not the method. */
+int fhtdp_batch_autotune(fhtdp_batch_plan *plan, void *ws, int reps, cudaStream_t stream,
+                         long long *target_out);
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan);
 
 #ifdef __cplusplus

@@ -71,6 +71,8 @@ _SIGS = {
     "fhtdp_batch_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
     "fhtdp_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "fhtdp_batch_plan_destroy": (None, [ctypes.c_void_p]),
     "fhtdp_cnn_downsample4": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 3
                               + [ctypes.c_void_p, ctypes.c_void_p]),
@@ -277,6 +279,14 @@ class BatchPlan:
 
     def status(self, stream=None):
         return workspace_status(self.ws, stream)
+
+    def autotune(self, reps=3, stream=None):
+        """Picks the work-queue group width by timing runs (synchronises the
+        stream); returns the chosen width in column tiles per band level."""
+        t = ctypes.c_longlong(0)
+        _check(lib().fhtdp_batch_autotune(self._plan, self.ws.data_ptr(), int(reps),
+                                          _stream(stream), ctypes.byref(t)))
+        return t.value
 
     def close(self):
         if self._plan:

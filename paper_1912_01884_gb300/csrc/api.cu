@@ -292,6 +292,13 @@ int fhtdp_batch_run(const fhtdp_batch_plan *plan, void *ws, cudaStream_t stream)
     return batch_run(plan->impl, ws, stream);
 }
 
+int fhtdp_batch_autotune(fhtdp_batch_plan *plan, void *ws, int reps, cudaStream_t stream,
+                         long long *target_out) {
+    g_last_error[0] = 0;
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    return batch_autotune(plan->impl, ws, reps, stream, target_out);
+}
+
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan) {
     if (!plan) return;
     batch_destroy(plan->impl);

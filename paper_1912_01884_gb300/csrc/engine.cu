@@ -2115,6 +2115,7 @@ struct BatchPlan {
     std::vector<ImgDesc> staging;   // image table as uploaded
     std::vector<Item> order;        // work queue as uploaded
     void *bound_ws = nullptr;
+    long long target = 0;           // queue group width (tiles per band level)
     ~BatchPlan() {
         for (cudaStream_t st : side) cudaStreamDestroy(st);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -2246,9 +2247,16 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
         }
         plan->ev.push_back(e);
     }
-    plan->order = queue_order(plan->imgs, (long long)num_sms());
+    plan->target = num_sms();
+    plan->order = queue_order(plan->imgs, plan->target);
     *out = plan;
     return FHTDP_OK;
+}
+
+// Each queue entry carries its image's band height and TMA flag.
+void set_nflags(BatchPlan *plan) {
+    for (Item &it : plan->order)
+        it.nflags = plan->imgs[it.image].s.n | (plan->staging[it.image].use_tma ? 1 << 16 : 0);
 }
 
 size_t batch_workspace_bytes(const BatchPlan *plan) { return plan ? plan->L.total : 0; }
@@ -2263,8 +2271,7 @@ int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream
     plan->staging.clear();
     for (auto &p : plan->imgs)
         plan->staging.push_back(make_desc(p, plan->L, (char *)ws, plan->dtype));
-    for (Item &it : plan->order)
-        it.nflags = plan->imgs[it.image].s.n | (plan->staging[it.image].use_tma ? 1 << 16 : 0);
+    set_nflags(plan);
     plan->bound_ws = ws;
     int st = cuda_status(cudaMemcpyAsync((char *)ws + plan->L.table_off, plan->staging.data(),
                                          sizeof(ImgDesc) * plan->staging.size(),
@@ -2316,6 +2323,72 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
         if (!st) st = js;
     }
     return st ? st : FHTDP_OK;
+}
+
+// Times the bound batch for a few queue group widths (from half a wave to the
+// whole batch in one group: fewer, wider groups wait less for dependencies
+// but keep more window-maximum buffers in flight in L2), keeps the fastest
+// and uploads its order.  Synchronises `stream` after every candidate.
+int batch_autotune(BatchPlan *plan, void *ws, int reps, cudaStream_t stream, long long *chosen) {
+    if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
+    if (ws != plan->bound_ws)
+        return set_error(FHTDP_EINVAL, "workspace differs from the one given to fhtdp_batch_upload");
+    if (reps < 1) reps = 1;
+    long long total = 0;
+    for (const ImgPlan &p : plan->imgs) total += p.tiles;
+    const long long sms = num_sms();
+    if (plan->imgs.empty() || total == 0) {
+        if (chosen) *chosen = plan->target;
+        return FHTDP_OK;
+    }
+    // Candidates by the number of groups they give, each width once.
+    std::vector<long long> cands;
+    std::vector<long long> groups_seen;
+    const long long widths[] = {sms / 2, 3 * sms / 4, sms, 3 * sms / 2, 2 * sms, 3 * sms, total};
+    for (long long t : widths) {
+        if (t < 1) continue;
+        const long long g = std::max(1LL, (total + t / 2) / t);
+        if (std::find(groups_seen.begin(), groups_seen.end(), g) != groups_seen.end()) continue;
+        groups_seen.push_back(g);
+        cands.push_back(t);
+    }
+    char *base = (char *)ws;
+    auto upload = [&](long long t) {
+        plan->order = queue_order(plan->imgs, t);
+        set_nflags(plan);
+        return cuda_status(cudaMemcpyAsync(base + plan->L.order_off, plan->order.data(),
+                                           sizeof(Item) * plan->order.size(),
+                                           cudaMemcpyHostToDevice, stream),
+                           "cudaMemcpyAsync");
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = cuda_status(cudaEventCreate(&e0), "cudaEventCreate");
+    if (!st) st = cuda_status(cudaEventCreate(&e1), "cudaEventCreate");
+    long long best_t = plan->target;
+    float best_ms = -1.0f;
+    for (size_t c = 0; c < cands.size() && !st; ++c) {
+        st = upload(cands[c]);
+        if (!st) st = batch_run(plan, ws, stream);   // warm-up
+        if (!st) st = cuda_status(cudaEventRecord(e0, stream), "cudaEventRecord");
+        for (int r = 0; r < reps && !st; ++r) st = batch_run(plan, ws, stream);
+        if (!st) st = cuda_status(cudaEventRecord(e1, stream), "cudaEventRecord");
+        if (!st) st = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.0f;
+        if (!st) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (!st && (best_ms < 0.0f || ms < best_ms)) {
+            best_ms = ms;
+            best_t = cands[c];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // Whatever happened, leave the plan and the workspace with one order.
+    const int us = upload(best_t);
+    if (!st) st = us;
+    if (!st) st = cuda_status(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    plan->target = best_t;
+    if (chosen) *chosen = best_t;
+    return st;
 }
 
 void batch_destroy(BatchPlan *plan) { delete plan; }

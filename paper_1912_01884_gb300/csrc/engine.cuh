@@ -14,6 +14,7 @@ size_t batch_workspace_bytes(const BatchPlan *plan);
 long long batch_items(const BatchPlan *plan);
 int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream);
 int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream);
+int batch_autotune(BatchPlan *plan, void *ws, int reps, cudaStream_t stream, long long *chosen);
 void batch_destroy(BatchPlan *plan);
 void debug_inject(int band, int tile, long long wait_cycles);
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,

@@ -213,6 +213,11 @@ def _batch_parity(lib, wls):
     imgs = [to_device(wl.img) for wl in wls]
     plan = lib.BatchPlan(imgs, [wl.k for wl in wls], [wl.B for wl in wls])
     plan.run()
+    _check_batch(plan, wls)
+    return plan
+
+
+def _check_batch(plan, wls):
     plan.status()
     for i, wl in enumerate(wls):
         x = plan.x[i].cpu().numpy()
@@ -226,7 +231,6 @@ def _batch_parity(lib, wls):
             xo, do, so = oracle.detect(wl.img, wl.k, wl.B)
             assert int(s) == int(so), i
         assert list(x) == list(xo) and list(d) == list(do), i
-    return plan
 
 
 def test_batch_of_mixed_shapes_matches_oracle(lib):
@@ -239,6 +243,24 @@ def test_batch_of_mixed_shapes_matches_oracle(lib):
     plan.run()
     for a, b in zip(first, plan.x):
         assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_batch_autotune_keeps_exact_results(lib):
+    """The queue tuner times a few group widths and keeps one; the batch it
+    leaves behind gives the oracle's results, also with a 256-row-band image
+    (side stream) in the batch."""
+    shapes = [(256, 256, 4, 8), (512, 300, 8, 4), (1024, 130, 16, 12), (768, 512, 6, 16),
+              (512, 700, 2, 32), (2048, 77, 32, 3)]
+    wls = [synth.plain_uniform(70 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(shapes)]
+    imgs = [to_device(wl.img) for wl in wls]
+    plan = lib.BatchPlan(imgs, [wl.k for wl in wls], [wl.B for wl in wls])
+    width = plan.autotune(reps=1)
+    assert width >= 1
+    _check_batch(plan, wls)   # outputs of the tuner's last run
+    for t in plan.x:
+        t.fill_(-7)
+    plan.run()
+    _check_batch(plan, wls)
 
 
 def test_batch_of_float_images_matches_oracle(lib):
