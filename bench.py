@@ -306,26 +306,52 @@ def run_ours(args):
     value = pix / total_s / 1e6
 
     # --- end to end through the public API: H2D + detect + D2H -----------
+    # Every step copies its inputs from pinned host memory and reads its
+    # results back inside the timed region.  Two input buffers (and a plan on
+    # each) let the copy of step i+1 run on a copy stream while step i
+    # computes; events order each buffer's copy, use and re-use.
     h2d = dev_bytes.numel()
     d2h = (hx.numel() + hd.numel() + hs.numel()) * 4
-    for _ in range(2):
-        dev_bytes.copy_(host_bytes, non_blocking=True)
-        step()
-    barrier()
-    e2e_ev = []
-    for _ in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dev_bytes.copy_(host_bytes, non_blocking=True)
-        step()
-        hx.copy_(xs, non_blocking=True)
-        hd.copy_(ds, non_blocking=True)
-        hs.copy_(sc, non_blocking=True)
-        e1.record(stream)
+    dev_bytes2 = torch.empty_like(dev_bytes)
+    views_d2 = [dev_bytes2[o:o + img.size * esize].view(tdt).view(img.shape)
+                for (img, _, _), o in zip(items, offs)]
+    plan2 = fd.BatchPlan(views_d2, ks, Bs, out=outs, stream=stream)
+    plan2.autotune(reps=1, stream=stream)
+    plans, bufs = (plan, plan2), (dev_bytes, dev_bytes2)
+    copy_stream = torch.cuda.Stream(dev)
+
+    def e2e_run(nsteps):
+        copied = [torch.cuda.Event() for _ in range(2)]
+        used = [torch.cuda.Event() for _ in range(2)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        copy_stream.wait_event(t0)
+        with torch.cuda.stream(copy_stream):
+            bufs[0].copy_(host_bytes, non_blocking=True)
+        copied[0].record(copy_stream)
+        for i in range(nsteps):
+            b = i % 2
+            if i + 1 < nsteps:   # next step's inputs, once that buffer is free
+                nb = 1 - b
+                if i >= 1:
+                    copy_stream.wait_event(used[nb])
+                with torch.cuda.stream(copy_stream):
+                    bufs[nb].copy_(host_bytes, non_blocking=True)
+                copied[nb].record(copy_stream)
+            stream.wait_event(copied[b])
+            plans[b].run(stream=stream)
+            used[b].record(stream)
+            hx.copy_(xs, non_blocking=True)
+            hd.copy_(ds, non_blocking=True)
+            hs.copy_(sc, non_blocking=True)
+        t1.record(stream)
         stream.synchronize()
-        e2e_ev.append((e0, e1))
+        return t0.elapsed_time(t1) / 1e3
+
+    e2e_run(2)
     barrier()
-    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist, dev)
+    e2e_s = max_over_ranks(e2e_run(args.steps), dist, dev)
+    barrier()
     e2e_value = pix / e2e_s / 1e6
 
     # --- roofline of the engine kernel (one persistent launch per step) ---

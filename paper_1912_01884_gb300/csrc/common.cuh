@@ -42,9 +42,6 @@ int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc 
                       cudaStream_t stream);
 template <typename Acc>
 int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream);
-// The DP with the window maxima taken per column into Mw ((2n-1) x W values).
-template <typename Acc>
-int launch_dp_window(Acc *hv, const Shape &s, int B, Acc *Mw, cudaStream_t stream);
 // The read-back with a grid-wide argmax into *key (zero before the call).
 template <typename Acc>
 int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long *key,

@@ -8,8 +8,8 @@
 // is the maximum of V_0, and the polyline is read back band by band.
 //
 // These kernels keep the paper's layout and in-place update (one launch per
-// band, the window maximum as a scan over the window).  They are the simple
-// reference-shaped path; the fused engine (engine.cu) is the fast one.
+// band).  They are the modular path and the one for 256-row bands; the fused
+// engine (engine.cu) is the fast one for bands of up to 128 rows.
 #include <climits>
 
 #include "common.cuh"
@@ -45,90 +45,69 @@ __global__ void dp_last_band_kernel(Acc *hv, Shape s) {
     }
 }
 
-// Band `band` < k-1, given V of band+1 already in place.
-template <typename Acc>
-__global__ void dp_band_kernel(Acc *hv, Shape s, int band, int B) {
-    const size_t per_band = (size_t)2 * s.n * s.W;
-    const Acc dead = Dead<Acc>::value();
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_band;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % s.W);
-        int r = (int)(i / s.W);
-        int sh = r % s.n, sign = r / s.n;
-        int d = sign ? -sh : sh;
-        size_t idx = (size_t)band * per_band + i;
-        int xn = x + d;
-        if (x >= s.w || xn < 0 || xn >= s.w) {
-            hv[idx] = dead;
-            continue;
-        }
-        int lo = max(d - B, -(s.n - 1)), hi = min(d + B, s.n - 1);
-        Acc best = dead;
-        for (int e = lo; e <= hi; ++e) best = vmax(best, hv[cell<Acc>(s, band + 1, xn, e)]);
-        hv[idx] = (best == dead) ? dead : hv[idx] + best;
-    }
-}
 
-// The same DP with the bend-window maxima taken once per column instead of
-// once per state (for callers that can give a scratch buffer Mw of
-// (2n-1) x W values): Mw(x, e) = max over |e' - e| <= B of V_{b+1}(x, e').
-// A block loads C columns x all displacements of V_{b+1} (with dead rows
-// beyond [-(n-1), n-1]) into shared memory and takes the window maxima by
-// doubling: after step j a row holds the maximum of 2^j consecutive rows, and
-// a window of L = 2B+1 rows is the maximum of two such runs.  Max is exact,
-// so the values are those of the scan.
+// Band `band` < k-1, given V of band+1 already in place, with the bend-window
+// maxima taken once per column instead of once per state.  A block owns the
+// continuation columns xn in [xn0, xn0 + C) (the grid covers xn in
+// [-(n-1), W + n - 1), so every state (x, d), x in [0, W), has exactly one
+// owner xn = x + d).  It loads V_{b+1}(xn, e) for all e (dead rows beyond
+// [-(n-1), n-1]) into shared memory, takes the window maxima over
+// |e - d| <= B by doubling (after step j a row holds the maximum of 2^j
+// consecutive rows; a window of L = 2B+1 rows is the maximum of two such
+// runs) and writes V_b(x, d) = H_b(x, d) + M in place.  Max is exact, so the
+// values are those of the scan over the window.
 template <typename Acc>
-__global__ void dp_window_kernel(const Acc *hv, Shape s, int band1, int B, int C, Acc *Mw) {
+__global__ void dp_band_tiled_kernel(Acc *hv, Shape s, int band, int B, int C) {
     extern __shared__ __align__(16) unsigned char raw[];
     const int D = 2 * s.n - 1, R = D + 2 * B;
     Acc *a = (Acc *)raw, *b = a + (size_t)R * C;
-    const int x0 = blockIdx.x * C;
+    const int xn0 = (int)blockIdx.x * C - (s.n - 1);
     const Acc dead = Dead<Acc>::value();
-    for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
-        const int r = i / C, c = i - r * C;
-        const int e = r - B - (s.n - 1), x = x0 + c;
-        a[i] = (e >= -(s.n - 1) && e <= s.n - 1 && x < s.w) ? hv[cell<Acc>(s, band1, x, e)] : dead;
-    }
-    __syncthreads();
-    const int L = 2 * B + 1;
-    int len = 1;
-    for (; 2 * len <= L; len *= 2) {
+    const bool any_live = xn0 + C > 0 && xn0 < s.w;
+    if (any_live) {
         for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
-            const int r = i / C;
-            b[i] = r + len < R ? vmax(a[i], a[i + len * C]) : a[i];
+            const int r = i / C, c = i - r * C;
+            const int e = r - B - (s.n - 1), xn = xn0 + c;
+            a[i] = (e >= -(s.n - 1) && e <= s.n - 1 && xn >= 0 && xn < s.w)
+                       ? hv[cell<Acc>(s, band + 1, xn, e)]
+                       : dead;
         }
         __syncthreads();
-        Acc *t = a;
-        a = b;
-        b = t;
-    }
-    // Window of e (padded row e + n - 1 + B): rows [e + n - 1, e + n - 1 + 2B].
-    for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-        const int r = i / C, c = i - r * C, x = x0 + c;
-        if (x >= s.w) continue;
-        Mw[(size_t)r * s.W + x] = vmax(a[r * C + c], a[(r + L - len) * C + c]);
-    }
-}
-
-// Band `band` < k-1 from the window maxima of band+1.
-template <typename Acc>
-__global__ void dp_combine_kernel(Acc *hv, Shape s, int band, const Acc *Mw) {
-    const size_t per_band = (size_t)2 * s.n * s.W;
-    const Acc dead = Dead<Acc>::value();
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_band;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % s.W);
-        const int r = (int)(i / s.W);
-        const int sh = r % s.n, sign = r / s.n;
-        const int d = sign ? -sh : sh;
-        const size_t idx = (size_t)band * per_band + i;
-        const int xn = x + d;
-        if (x >= s.w || xn < 0 || xn >= s.w) {
-            hv[idx] = dead;
-            continue;
+        const int L = 2 * B + 1;
+        int len = 1;
+        for (; 2 * len <= L; len *= 2) {
+            for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
+                const int r = i / C;
+                b[i] = r + len < R ? vmax(a[i], a[i + len * C]) : a[i];
+            }
+            __syncthreads();
+            Acc *t = a;
+            a = b;
+            b = t;
         }
-        const Acc best = Mw[(size_t)(d + s.n - 1) * s.W + xn];
-        hv[idx] = (best == dead) ? dead : hv[idx] + best;
+        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+            const int r = i / C, c = i - r * C;
+            const int d = r - (s.n - 1), xn = xn0 + c, x = xn - d;
+            if (x < 0 || x >= s.W) continue;
+            const size_t idx = cell<Acc>(s, band, x, d);
+            // d = 0 has a second copy, row 0 of the "-" half.
+            const size_t dup = ((size_t)band * 2 + 1) * s.n * s.W + x;
+            Acc v = dead;
+            if (x < s.w && xn >= 0 && xn < s.w) {
+                const Acc best = vmax(a[r * C + c], a[(r + L - len) * C + c]);
+                v = (best == dead) ? dead : hv[idx] + best;
+            }
+            hv[idx] = v;
+            if (d == 0) hv[dup] = v;
+        }
+    } else {
+        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+            const int r = i / C, c = i - r * C;
+            const int d = r - (s.n - 1), x = xn0 + c - d;
+            if (x < 0 || x >= s.W) continue;
+            hv[cell<Acc>(s, band, x, d)] = dead;
+            if (d == 0) hv[((size_t)band * 2 + 1) * s.n * s.W + x] = dead;
+        }
     }
 }
 
@@ -292,18 +271,6 @@ int grid_for(size_t total) {
 template <typename Acc>
 int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream) {
     const size_t per_band = (size_t)2 * s.n * s.W;
-    dp_last_band_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
-    int st = launched("dp_last_band_kernel");
-    for (int band = s.k - 2; band >= 0 && !st; --band) {
-        dp_band_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s, band, B);
-        st = launched("dp_band_kernel");
-    }
-    return st;
-}
-
-template <typename Acc>
-int launch_dp_window(Acc *hv, const Shape &s, int B, Acc *Mw, cudaStream_t stream) {
-    const size_t per_band = (size_t)2 * s.n * s.W;
     const int D = 2 * s.n - 1;
     // A window beyond the displacement range covers all of it.
     const int Bc = B < D - 1 ? B : D - 1;
@@ -311,20 +278,17 @@ int launch_dp_window(Acc *hv, const Shape &s, int B, Acc *Mw, cudaStream_t strea
     int C = 32;
     while (C > 1 && (size_t)2 * R * C * sizeof(Acc) > 200 * 1024) C /= 2;
     const size_t smem = (size_t)2 * R * C * sizeof(Acc);
-    int st = cuda_status(cudaFuncSetAttribute(dp_window_kernel<Acc>,
+    int st = cuda_status(cudaFuncSetAttribute(dp_band_tiled_kernel<Acc>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem),
                          "cudaFuncSetAttribute");
     if (st) return st;
     dp_last_band_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
     st = launched("dp_last_band_kernel");
+    const int blocks = (s.W + 2 * (s.n - 1) + C - 1) / C;
     for (int band = s.k - 2; band >= 0 && !st; --band) {
-        dp_window_kernel<Acc><<<(s.w + C - 1) / C, 512, smem, stream>>>(hv, s, band + 1, Bc, C,
-                                                                          Mw);
-        st = launched("dp_window_kernel");
-        if (st) break;
-        dp_combine_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s, band, Mw);
-        st = launched("dp_combine_kernel");
+        dp_band_tiled_kernel<Acc><<<blocks, 512, smem, stream>>>(hv, s, band, Bc, C);
+        st = launched("dp_band_tiled_kernel");
     }
     return st;
 }
@@ -336,8 +300,6 @@ int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_
     return launched("backtrack_kernel");
 }
 
-template int launch_dp_inplace<int32_t>(int32_t *, const Shape &, int, cudaStream_t);
-template int launch_dp_inplace<float>(float *, const Shape &, int, cudaStream_t);
 template <typename Acc>
 int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long *key,
                          int32_t *x_out, int32_t *d_out, Acc *score_out, cudaStream_t stream) {
@@ -348,13 +310,13 @@ int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long
     return launched("readback_kernel");
 }
 
+template int launch_dp_inplace<int32_t>(int32_t *, const Shape &, int, cudaStream_t);
+template int launch_dp_inplace<float>(float *, const Shape &, int, cudaStream_t);
 template int launch_backtrack_key<int32_t>(const int32_t *, const Shape &, int,
                                            unsigned long long *, int32_t *, int32_t *, int32_t *,
                                            cudaStream_t);
 template int launch_backtrack_key<float>(const float *, const Shape &, int, unsigned long long *,
                                          int32_t *, int32_t *, float *, cudaStream_t);
-template int launch_dp_window<int32_t>(int32_t *, const Shape &, int, int32_t *, cudaStream_t);
-template int launch_dp_window<float>(float *, const Shape &, int, float *, cudaStream_t);
 template int launch_backtrack<int32_t>(const int32_t *, const Shape &, int, int32_t *, int32_t *,
                                        int32_t *, cudaStream_t);
 template int launch_backtrack<float>(const float *, const Shape &, int, int32_t *, int32_t *,

@@ -2051,9 +2051,9 @@ LaunchArgs base_args(const RunLayout &L, char *ws, int count) {
 
 int run_fallback(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                  int32_t *d_out, void *score_out, void *ws, cudaStream_t stream) {
-    // 256-row bands: the level-by-level FHT, the DP with per-column window
-    // maxima (in the FHT's ping-pong half of the workspace) and the read-back
-    // from a grid-wide argmax.
+    // 256-row bands: the standalone FHT (two levels per pass), the in-place
+    // DP with per-column window maxima and the read-back from a grid-wide
+    // argmax.
     int st = cuda_status(cudaMemsetAsync(ws, 0, sizeof(Ctl), stream), "cudaMemsetAsync");
     if (st) return st;
     size_t hough = (size_t)s.k * 2 * s.n * s.W;
@@ -2064,7 +2064,7 @@ int run_fallback(const void *img, int dtype, int pitch, const Shape &s, int B, i
     if (dtype == FHTDP_F32) {
         float *H = (float *)base, *tmp = H + hough;
         st = launch_fht_stages<float, float>((const float *)img, pitch, s, H, tmp, stream);
-        if (!st) st = launch_dp_window<float>(H, s, B, tmp, stream);
+        if (!st) st = launch_dp_inplace<float>(H, s, B, stream);
         if (!st)
             st = launch_backtrack_key<float>(H, s, B, key, x_out, d_out, (float *)score_out,
                                              stream);
@@ -2075,7 +2075,7 @@ int run_fallback(const void *img, int dtype, int pitch, const Shape &s, int B, i
         st = launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream);
     else
         st = launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
-    if (!st) st = launch_dp_window<int32_t>(H, s, B, tmp, stream);
+    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
     if (!st)
         st = launch_backtrack_key<int32_t>(H, s, B, key, x_out, d_out, (int32_t *)score_out,
                                            stream);
