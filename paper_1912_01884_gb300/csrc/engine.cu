@@ -2101,6 +2101,9 @@ ImgPlan single_plan(const void *img, int pitch, const Shape &s, int B, int32_t *
 
 }  // namespace
 
+// Streams over which a batch spreads its images with 256-row bands.
+constexpr int kSideLanes = 4;
+
 // The host-side plan of a batch.
 struct BatchPlan {
     int dtype;
@@ -2223,12 +2226,12 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
             plan->imgs.push_back(p);
     }
     plan->L = plan_layout(plan->imgs, true);
-    // Scratch of the standalone path: up to 4 lanes, each a stream that runs
-    // its images one after the other on its own slice.
+    // Scratch of the standalone path: up to kSideLanes lanes, each a stream
+    // that runs its images one after the other on its own slice.
     size_t sep = 0;
     for (auto &p : plan->separate) sep = std::max(sep, engine_workspace_bytes(dtype, p.s, p.io.B));
     plan->sep_bytes = align_up(sep, 256);
-    plan->lanes = (int)std::min<size_t>(4, plan->separate.size());
+    plan->lanes = (int)std::min<size_t>(kSideLanes, plan->separate.size());
     plan->separate_off = align_up(plan->L.total, 256);
     if (sep) plan->L.total = plan->separate_off + plan->sep_bytes * plan->lanes;
     for (int l = 0; l < plan->lanes; ++l) {
