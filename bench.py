@@ -55,7 +55,7 @@ WORKLOADS = {
 # profiles/engine_kernel_u8_2048x2048_k16_B16.md (48 images per launch); a
 # launch's traffic is this times its images.  None for other workloads, and
 # to be reset whenever the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (214.150144e6 + 770.339328e6) / 48}
+NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (299.827456e6 + 1571.180e6) / 48}
 
 
 def algorithmic_bytes(h, w, k, bpp):
