@@ -65,3 +65,21 @@ def test_fht_and_dp_reject_bad_arguments(lib):
     assert L.fhtdp_polyline_dp(None, 0, 64, 10, 4, 1, None) == 1
     assert L.fhtdp_polyline_dp(ctypes.c_void_p(16), 0, 64, 10, 4, -2, None) == 1
     assert L.fhtdp_backtrack(None, 0, 64, 10, 4, 1, None, None, None, None) == 1
+
+
+def test_batch_autotune_rejects_bad_arguments(lib):
+    """The queue tuner checks its plan and workspace on the host: without a
+    plan, or with a workspace the plan was not bound to (no upload), it
+    returns FHTDP_EINVAL before any launch."""
+    L = lib.lib()
+    width = ctypes.c_longlong(-1)
+    assert L.fhtdp_batch_autotune(None, ctypes.c_void_p(16), 1, None, ctypes.byref(width)) == 1
+    img = lib.Image(16, 64, 40, 40, 4, 2, 16, 16, 16, None)   # never dereferenced
+    plan = ctypes.c_void_p()
+    assert L.fhtdp_batch_plan_create(ctypes.byref(img), 1, 0, ctypes.byref(plan)) == 0
+    try:
+        r = L.fhtdp_batch_autotune(plan, ctypes.c_void_p(256), 1, None, ctypes.byref(width))
+        assert r == 1 and "workspace" in L.fhtdp_last_error().decode()
+        assert width.value == -1
+    finally:
+        L.fhtdp_batch_plan_destroy(plan)
