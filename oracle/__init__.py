@@ -17,6 +17,11 @@ Function map (paper passages in the C file's comments):
   detect_windowed  the DP restricted to per-band displacement windows (the
                    pruned DP of the learned proposal, not in the paper)
   detect / detect_f32   the whole method (CPU baseline)
+  gauss_rows       Sec. 2.3 main problem step 1, row-wise Gaussian smoothing
+  angle_window     Sec. 2.3 Eqs. 6-7, the bend-angle range of displacements
+  dp_angle / backtrack_angle / detect_angle
+                   the main problem with the angle restriction
+  brute_angle      every polyline passing the direct angle test, tiny images
 """
 from __future__ import annotations
 
@@ -86,6 +91,19 @@ def _load():
                                                  + [_I32P, _I32P, _I32P,
                                                     ctypes.POINTER(ctypes.c_long)])
             lib.oracle_brute_win_f64.restype = ctypes.c_double
+            lib.oracle_gauss_rows_f64.argtypes = [_F64P] + [ctypes.c_int] * 3 + [_F64P]
+            lib.oracle_angle_window.argtypes = [ctypes.c_int, ctypes.c_double, _I32P]
+            lib.oracle_dp_angle_f64.argtypes = [_F64P] + [ctypes.c_int] * 3 + [_I32P, _F64P]
+            lib.oracle_backtrack_angle_f64.argtypes = ([_F64P] + [ctypes.c_int] * 3
+                                                       + [_I32P, _I32P, _I32P])
+            lib.oracle_backtrack_angle_f64.restype = ctypes.c_double
+            lib.oracle_brute_angle_f64.argtypes = ([_F64P] + [ctypes.c_int] * 3
+                                                   + [ctypes.c_double, _I32P, _I32P,
+                                                      ctypes.POINTER(ctypes.c_long)])
+            lib.oracle_brute_angle_f64.restype = ctypes.c_double
+            lib.oracle_detect_angle_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
+                                                    + [ctypes.c_double, _I32P, _I32P])
+            lib.oracle_detect_angle_f64.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -245,4 +263,77 @@ def detect_f32(img, k: int, B: int):
     ds = np.zeros(k, dtype=np.int32)
     s = _load().oracle_detect_f32(_p(src, ctypes.c_float), h, w, k, B,
                                   _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def gauss_rows(img, r: int) -> np.ndarray:
+    """Every row convolved with the binomial weights C(2r, r+t), |t| <= r,
+    zero outside the row (unnormalised), float64."""
+    img = _f64(img)
+    h, w = img.shape
+    out = np.empty_like(img)
+    if _load().oracle_gauss_rows_f64(_p(img, ctypes.c_double), h, w, int(r),
+                                     _p(out, ctypes.c_double)):
+        raise ValueError("r must be >= 0")
+    return out
+
+
+def angle_window(n: int, gamma: float) -> np.ndarray:
+    """[2n-1][2] int32: the range [lo(d), hi(d)] of next displacements whose
+    bend angle from d is at most gamma (Eqs. 6-7), row d + n - 1."""
+    out = np.zeros((2 * n - 1, 2), dtype=np.int32)
+    if _load().oracle_angle_window(int(n), float(gamma), _p(out, ctypes.c_int32)):
+        raise ValueError("n >= 1 and gamma >= 0 required")
+    return out
+
+
+def dp_angle(H: np.ndarray, h: int, w: int, k: int, lohi) -> np.ndarray:
+    """V[k][2n-1][w] of the angle-restricted DP over Hough images H."""
+    n = h // k
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    t = np.ascontiguousarray(lohi, dtype=np.int32)
+    V = np.empty((k, 2 * n - 1, w), dtype=np.float64)
+    if _load().oracle_dp_angle_f64(_p(H, ctypes.c_double), h, w, k, _p(t, ctypes.c_int32),
+                                   _p(V, ctypes.c_double)):
+        raise ValueError("bad shape")
+    return V
+
+
+def backtrack_angle(V: np.ndarray, h: int, w: int, k: int, lohi):
+    """(x[k+1], d[k], score) read back from V with the angle windows."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    t = np.ascontiguousarray(lohi, dtype=np.int32)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_backtrack_angle_f64(_p(V, ctypes.c_double), h, w, k,
+                                           _p(t, ctypes.c_int32), _p(xs, ctypes.c_int32),
+                                           _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def brute_angle(img, k: int, gamma: float):
+    """Brute force over every polyline whose bend angles pass the direct
+    test |atan(d'/n) - atan(d/n)| <= gamma: (x, d, score, visited)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    visited = ctypes.c_long(0)
+    s = _load().oracle_brute_angle_f64(_p(img, ctypes.c_double), h, w, k, float(gamma),
+                                       _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32),
+                                       ctypes.byref(visited))
+    return xs, ds, s, visited.value
+
+
+def detect_angle(img, k: int, r: int, gamma: float):
+    """The main problem in float64: Gaussian rows (half-width r), band FHT,
+    angle-restricted DP, read-back.  (x[k+1], d[k], score of the smoothed
+    image)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_angle_f64(_p(img, ctypes.c_double), h, w, k, int(r),
+                                        float(gamma), _p(xs, ctypes.c_int32),
+                                        _p(ds, ctypes.c_int32))
     return xs, ds, s

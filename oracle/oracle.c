@@ -444,3 +444,235 @@ double oracle_detect_f32(const float *img, int h, int w, int k, int B,
     free(V);
     return s;
 }
+
+/* ---------------------------------------------------------------------------
+ * The main problem (Sec. 2.3: the Welsh M-estimate of the polyline).
+ *
+ * Step 1: every row convolved with a one-dimensional Gaussian.  Reading: the
+ * discrete Gaussian of half-width r, i.e. the binomial weights C(2r, r + t),
+ * t in [-r, r], unnormalised (the common factor 4^r scales every polyline
+ * sum alike and leaves the argmax unchanged); zero outside [0, w).  A uint8
+ * image then gives exact integers.
+ *   out(y, x) = sum_t C(2r, r + t) * img(y, x + t)
+ * ------------------------------------------------------------------------ */
+static double binom(int a, int b) {
+    double c = 1.0;
+    for (int i = 1; i <= b; ++i) c = c * (a - b + i) / i;
+    return c;
+}
+
+int oracle_gauss_rows_f64(const double *img, int h, int w, int r, double *out) {
+    if (r < 0) return -1;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            double acc = 0.0;
+            for (int t = -r; t <= r; ++t) {
+                int c = x + t;
+                if (c < 0 || c >= w) continue;
+                acc += binom(2 * r, r + t) * img[(size_t)y * w + c];
+            }
+            out[(size_t)y * w + x] = acc;
+        }
+    return 0;
+}
+
+/* Step 2's bending-angle restriction (Sec. 2.3, Fig. 5).  A link of
+ * displacement d over a band of n rows has inclination atan(d / n) from the
+ * vertical (the paper's shift = h + h tg(phi) with h the band height, so
+ * d = n tg(phi)); the bend angle between consecutive links d, e is
+ * |atan(e / n) - atan(d / n)|, and e is admissible after d when that is at
+ * most gamma.  Every |e| <= n - 1 already has its inclination inside
+ * [-pi/4, pi/4], the second condition of Eqs. 6-7.  This is the plain
+ * definition, evaluated in double pair by pair; since atan is increasing the
+ * admissible e form one interval (the union of the ranges of Eqs. 6 and 7),
+ * stored as lohi: [2n-1][2], entry d + n - 1 = {lo(d), hi(d)}. */
+int oracle_angle_window(int n, double gamma, int32_t *lohi) {
+    if (n < 1 || !(gamma >= 0.0)) return -1;
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        int lo = n, hi = -n;
+        for (int e = -(n - 1); e <= n - 1; ++e) {
+            double bend = fabs(atan((double)e / n) - atan((double)d / n));
+            if (bend <= gamma) {
+                if (e < lo) lo = e;
+                if (e > hi) hi = e;
+            }
+        }
+        lohi[2 * (d + n - 1)] = lo;
+        lohi[2 * (d + n - 1) + 1] = hi;
+    }
+    return 0;
+}
+
+/* The DP of Sec. 2.3 (the RangeMaxQ steps): as oracle_dp_f64, with the
+ * continuation window of displacement d being [lo(d), hi(d)] from lohi
+ * instead of [d - B, d + B]; the window maximum is a plain scan. */
+int oracle_dp_angle_f64(const double *H, int h, int w, int k, const int32_t *lohi,
+                        double *V) {
+    if (k < 1 || h % k != 0) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    for (int b = k - 1; b >= 0; --b)
+        for (int d = -(n - 1); d <= n - 1; ++d)
+            for (int x = 0; x < w; ++x) {
+                double *out = &V[((size_t)b * D + (d + n - 1)) * w + x];
+                int xn = x + d;
+                if (xn < 0 || xn >= w) {
+                    *out = ORACLE_NEG;
+                    continue;
+                }
+                double hv = hough_at_f64(H, n, W, b, x, d);
+                if (b == k - 1) {
+                    *out = hv;
+                    continue;
+                }
+                double best = ORACLE_NEG;
+                for (int e = lohi[2 * (d + n - 1)]; e <= lohi[2 * (d + n - 1) + 1]; ++e) {
+                    double v = V[((size_t)(b + 1) * D + (e + n - 1)) * w + xn];
+                    if (v > best) best = v;
+                }
+                *out = (best == ORACLE_NEG) ? ORACLE_NEG : hv + best;
+            }
+    return 0;
+}
+
+/* Step 3 and the read-back (Eq. 5) with the angle windows: the
+ * lexicographically smallest argmax of V_0, then band by band the smallest
+ * e in [lo(d_{i-1}), hi(d_{i-1})] maximising V_i(x_i, e). */
+double oracle_backtrack_angle_f64(const double *V, int h, int w, int k, const int32_t *lohi,
+                                  int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int D = 2 * n - 1;
+    double best = ORACLE_NEG;
+    int bx = 0, bd = 0;
+    for (int x = 0; x < w; ++x)
+        for (int d = -(n - 1); d <= n - 1; ++d) {
+            double v = V[(size_t)(d + n - 1) * w + x];
+            if (v > best) {
+                best = v;
+                bx = x;
+                bd = d;
+            }
+        }
+    if (best == ORACLE_NEG) {
+        for (int i = 0; i <= k; ++i) xs[i] = -1;
+        for (int i = 0; i < k; ++i) ds[i] = 0;
+        return ORACLE_NEG;
+    }
+    xs[0] = bx;
+    ds[0] = bd;
+    for (int i = 1; i < k; ++i) {
+        int xi = xs[i - 1] + ds[i - 1];
+        xs[i] = xi;
+        int p = ds[i - 1] + n - 1;
+        double bv = ORACLE_NEG;
+        int be = lohi[2 * p];
+        for (int e = lohi[2 * p]; e <= lohi[2 * p + 1]; ++e) {
+            double v = V[((size_t)i * D + (e + n - 1)) * w + xi];
+            if (v > bv) {
+                bv = v;
+                be = e;
+            }
+        }
+        ds[i] = be;
+    }
+    xs[k] = xs[k - 1] + ds[k - 1];
+    return best;
+}
+
+/* Brute force over every polyline whose consecutive links satisfy the bend
+ * angle restriction tested directly, |atan(d_{i+1}/n) - atan(d_i/n)| <=
+ * gamma (no window table), vertices in [0, w); lexicographic enumeration,
+ * first strict maximum kept.  Tiny images only. */
+typedef struct {
+    const double *img;
+    int h, w, k, n;
+    double gamma;
+    int32_t *cur_d;
+    int cur_x0;
+    double best;
+    int32_t *best_x;
+    int32_t *best_d;
+    long visited;
+} brute_angle_state;
+
+static void brute_angle_rec(brute_angle_state *st, int i, int x) {
+    int n = st->n;
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        if (i > 0) {
+            double diff = atan((double)d / n) - atan((double)st->cur_d[i - 1] / n);
+            if (fabs(diff) > st->gamma) continue;
+        }
+        if (x + d < 0 || x + d >= st->w) continue;
+        st->cur_d[i] = d;
+        if (i + 1 < st->k) {
+            brute_angle_rec(st, i + 1, x + d);
+        } else {
+            st->visited++;
+            double sc = oracle_path_score_f64(st->img, st->h, st->w, st->k, st->cur_x0,
+                                              st->cur_d);
+            if (sc > st->best) {
+                st->best = sc;
+                int xx = st->cur_x0;
+                for (int j = 0; j < st->k; ++j) {
+                    st->best_x[j] = xx;
+                    st->best_d[j] = st->cur_d[j];
+                    xx += st->cur_d[j];
+                }
+                st->best_x[st->k] = xx;
+            }
+        }
+    }
+}
+
+double oracle_brute_angle_f64(const double *img, int h, int w, int k, double gamma,
+                              int32_t *xs, int32_t *ds, long *visited) {
+    brute_angle_state st;
+    st.img = img;
+    st.h = h;
+    st.w = w;
+    st.k = k;
+    st.n = h / k;
+    st.gamma = gamma;
+    st.cur_d = (int32_t *)calloc((size_t)k, sizeof(int32_t));
+    st.best = ORACLE_NEG;
+    st.best_x = xs;
+    st.best_d = ds;
+    st.visited = 0;
+    for (int x0 = 0; x0 < w; ++x0) {
+        st.cur_x0 = x0;
+        brute_angle_rec(&st, 0, x0);
+    }
+    free(st.cur_d);
+    if (visited) *visited = st.visited;
+    if (st.best == ORACLE_NEG) {
+        for (int i = 0; i <= k; ++i) xs[i] = -1;
+        for (int i = 0; i < k; ++i) ds[i] = 0;
+    }
+    return st.best;
+}
+
+/* The whole main problem in double: smoothing (half-width r), band FHT, the
+ * angle-restricted DP and the read-back.  Returns the optimal score of the
+ * smoothed image. */
+double oracle_detect_angle_f64(const double *img, int h, int w, int k, int r, double gamma,
+                               int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    double *S = (double *)malloc(sizeof(double) * (size_t)h * w);
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * (2 * n - 1) * w);
+    int32_t *lohi = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * n - 1));
+    double s = NAN;
+    if (S && H && V && lohi && oracle_gauss_rows_f64(img, h, w, r, S) == 0 &&
+        oracle_angle_window(n, gamma, lohi) == 0) {
+        oracle_fht_recursive_f64(S, h, w, k, H);
+        oracle_dp_angle_f64(H, h, w, k, lohi, V);
+        s = oracle_backtrack_angle_f64(V, h, w, k, lohi, xs, ds);
+    }
+    free(S);
+    free(H);
+    free(V);
+    free(lohi);
+    return s;
+}
