@@ -3,7 +3,7 @@
 read-back) in Mpix/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload plain2048|mixed|float8192|plain256] [--images I]
+                    [--workload plain2048|mixed|float8192|plain256|angle2048] [--images I]
 
 Default workload: synthetic 2048x2048 uint8 images, k=16 bands of 128 rows,
 bend range 16.  A step is one pass of the whole method over a batch of
@@ -44,6 +44,10 @@ WORKLOADS = {
     "plain256": dict(
         desc="u8 256x256, k=4 bands of 64 rows, bend 8, uniform noise + 1 polyline", images=2048,
         dtype="u8"),
+    "angle2048": dict(
+        desc="main problem: u8 2048x2048 bent edges with salt noise, rows smoothed with the "
+             "binomial Gaussian r=2, k=16 bands of 128 rows, bend angle <= 10 degrees",
+        images=32, dtype="u8"),
     "learned1024": dict(
         desc="u8 1024x1024 lanes over textured noise, k=16 bands of 64 rows, bend 12: learned "
              "window proposal (4-layer 32-channel bf16 CNN on the 4x downsample, windows of 16) "
@@ -56,6 +60,12 @@ WORKLOADS = {
 # launch's traffic is this times its images.  None for other workloads, and
 # to be reset whenever the kernel changes until it is captured again.
 NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (299.827456e6 + 1571.180e6) / 48}
+
+
+# The main problem's smoothing half-width and bend angle (the paper's
+# Fig. 3 example bends by at most 10 degrees).
+ANGLE_R = 2
+ANGLE_GAMMA = 0.17453292519943295   # 10 degrees in radians
 
 
 def algorithmic_bytes(h, w, k, bpp):
@@ -169,6 +179,8 @@ def make_workload(name, images, seed, rank):
         return [(w.img, w.k, w.B) for w in (synth.plain_uniform(s, 256, 256, 4, 8) for s in seeds)]
     if name == "float8192":
         return [(w.img, w.k, w.B) for w in (synth.ridge_response(s) for s in seeds)]
+    if name == "angle2048":
+        return [(w.img, w.k, None) for w in (synth.bent_edges(s) for s in seeds)]
     shapes = synth.mixed_batch_shapes(seed * 7919 + rank, images)
     return [(synth.plain_uniform(s, h, w, k, B).img, k, B)
             for s, (h, w, k, B) in zip(seeds, shapes)]
@@ -181,7 +193,9 @@ def oracle_rate(items, budget_s):
     import oracle
     done, pix, t0 = 0, 0, time.perf_counter()
     for img, k, B in items:
-        if img.dtype == np.float32:
+        if B is None:
+            oracle.detect_angle(img, k, ANGLE_R, ANGLE_GAMMA)
+        elif img.dtype == np.float32:
             oracle.detect_f32(img, k, B)
         else:
             oracle.detect(img, k, B)
@@ -412,6 +426,182 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+ANGLE_LANES = 4   # streams over which one step spreads its images
+
+
+def run_angle(args):
+    """The main problem (smoothing + band FHT + bend-angle DP + read-back) on
+    a batch of images per step.  Each image is one fhtdp_detect_polyline_angle
+    call (24 launches); a step spreads the images over ANGLE_LANES streams,
+    each with its own workspace, and is captured once as a CUDA graph that
+    every timed step replays."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1912_01884_gb300 as fd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    fd.load()
+    spec = WORKLOADS["angle2048"]
+    I = args.images or spec["images"]
+    items = make_workload("angle2048", I, args.seed, rank)
+    h, w = items[0][0].shape
+    k = items[0][1]
+    host = torch.empty((I, h, w), dtype=torch.uint8).pin_memory()
+    for j, (img, _, _) in enumerate(items):
+        host[j].copy_(torch.from_numpy(img))
+    imgs = host.to(dev)
+    xs = torch.empty((I, k + 1), dtype=torch.int32, device=dev)
+    ds = torch.empty((I, k), dtype=torch.int32, device=dev)
+    sc = torch.empty((I, 1), dtype=torch.int32, device=dev)
+    need = fd.angle_workspace_bytes(fd.DTYPE_U8, h, w, k, ANGLE_R)
+    lanes = min(ANGLE_LANES, I)
+    wss = [torch.empty(need, dtype=torch.uint8, device=dev) for _ in range(lanes)]
+    main = torch.cuda.Stream(dev)      # graphs are captured off the default stream
+    torch.cuda.set_stream(main)
+    side = [torch.cuda.Stream(dev) for _ in range(lanes)]
+
+    def enqueue(src):
+        # fork: every lane waits for the main stream, runs its images, joins
+        for ln in range(lanes):
+            side[ln].wait_stream(main)
+            for j in range(ln, I, lanes):
+                fd.detect_polyline_angle(src[j], k, ANGLE_R, ANGLE_GAMMA,
+                                         out=(xs[j], ds[j], sc[j]), ws=wss[ln], stream=side[ln])
+        for ln in range(lanes):
+            main.wait_stream(side[ln])
+
+    enqueue(imgs)   # untimed: first-use set-up outside the capture
+    torch.cuda.synchronize(dev)
+    l0 = fd.launch_count()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=main):
+        enqueue(imgs)
+    launches_per_step = fd.launch_count() - l0
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        graph.replay()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for e0, e1 in ev:
+        e0.record(main)
+        graph.replay()
+        e1.record(main)
+    barrier()
+    clocks = sampler.stop()
+    total_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
+    pix_rank = I * h * w
+    value = pix_rank * world * args.steps / total_s / 1e6
+
+    # End to end: each step copies its images from pinned host memory, runs
+    # the graph on them and reads every result back, all inside the timed
+    # region (copies on the main stream, ordered before the graph).
+    hx = torch.empty_like(xs, device="cpu").pin_memory()
+    hd = torch.empty_like(ds, device="cpu").pin_memory()
+    hs = torch.empty_like(sc, device="cpu").pin_memory()
+
+    def e2e_run(nsteps):
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(main)
+        for _ in range(nsteps):
+            imgs.copy_(host, non_blocking=True)
+            graph.replay()
+            hx.copy_(xs, non_blocking=True)
+            hd.copy_(ds, non_blocking=True)
+            hs.copy_(sc, non_blocking=True)
+        t1.record(main)
+        main.synchronize()
+        return t0.elapsed_time(t1) / 1e3
+
+    e2e_run(1)
+    barrier()
+    e2e_s = max_over_ranks(e2e_run(args.steps), dist, dev)
+    e2e_value = pix_rank * world * args.steps / e2e_s / 1e6
+
+    # Stage times on one image through the modular calls (one stream), to
+    # find the dominant kernel and its roofline.
+    ws_tmp = torch.empty(fd.fht_workspace_bytes(fd.DTYPE_I32, h, w, k), dtype=torch.uint8,
+                         device=dev)
+    smooth = torch.empty((h, w), dtype=torch.int32, device=dev)
+    hough = torch.empty((k, 2, h // k, w + h // k), dtype=torch.int32, device=dev)
+    one = (xs[0], ds[0], sc[0])
+    stages = {
+        "gauss_rows": lambda: fd.gauss_rows(imgs[0], ANGLE_R, out=smooth, stream=main),
+        "fht_bands": lambda: fd.fht_bands(smooth, k, out=hough, ws=ws_tmp, stream=main),
+        "dp_angle": lambda: fd.polyline_dp_angle(hough, h, w, k, ANGLE_GAMMA, stream=main),
+        "backtrack": lambda: fd.backtrack_angle(hough, h, w, k, ANGLE_GAMMA, out=one,
+                                                stream=main),
+    }
+    stage_ms = {name: [] for name in stages}
+    for rep in range(6):
+        for name, fn in stages.items():
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            fn()
+            b.record(main)
+            b.synchronize()
+            if rep >= 2:
+                stage_ms[name].append(a.elapsed_time(b))
+    stage_ms = {name: statistics.median(v) for name, v in stage_ms.items()}
+    n = h // k
+    D = 2 * n - 1
+    # minimal DRAM bytes of each stage run on its own
+    stage_bytes = {
+        "gauss_rows": h * w * (1 + 4),
+        "fht_bands": h * w * 4 + k * 2 * n * (w + n) * 4,
+        "dp_angle": (k - 1) * 3 * D * w * 4,
+        "backtrack": D * w * 4,
+    }
+    top = max(stage_ms, key=stage_ms.get)
+    hbm, peak_kind = peaks()
+    achieved = stage_bytes[top] / (stage_ms[top] / 1e3) / 1e9
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": spec["desc"], "images_per_step": I,
+                       "pixels_per_step": pix_rank, "parallelism": "images sharded over ranks",
+                       "lanes": lanes, "r": ANGLE_R, "gamma_rad": ANGLE_GAMMA,
+                       "l2": "inputs %d MB per step %s 129 MB L2, no flush"
+                             % (host.numel() // 2**20, ">" if host.numel() > 129e6 else "<")},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "%s (stage of one image, all its launches)" % top},
+            "stages_ms_one_image": stage_ms,
+            "pipeline_frac_of_hbm": sum(algorithmic_bytes(h, w, k, 1) for _ in range(I))
+                                    / (total_s / args.steps) / 1e9 / hbm,
+            "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": host.numel(),
+                    "d2h_bytes_per_step": (hx.numel() + hd.numel() + hs.numel()) * 4},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks,
+        }
+        if world == 1 and not args.skip_cpu:
+            rate, done = oracle_rate(make_workload("angle2048", 12, 900000 + args.seed, 0), 12.0)
+            out["cpu_baseline"] = {
+                "value": rate, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+                "sample": "%d images of the workload, whole method, one thread" % done}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_learned(args):
     """Trains the proposal network on images labelled by the exact method,
     then times the plain DP and the learned pipeline on held-out batches and
@@ -494,6 +684,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "angle2048":
+        run_angle(args)
     elif args.workload == "learned1024":
         run_learned(args)
     else:

@@ -156,6 +156,58 @@ int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, int w, int 
                                   cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * The main problem of Sec. 2.3 (the Welsh M-estimate of a k-link polyline
+ * with a bending-angle limit).  Step 1 convolves every row with a discrete
+ * Gaussian; steps 2-3 run the DP and the read-back with the bend-angle
+ * windows of Eqs. 6-7 instead of the integer limit B.
+ *
+ *   Gaussian  the binomial weights C(2r, r+t), |t| <= r (the discrete
+ *             Gaussian of variance r/2), not normalised: every polyline sum
+ *             is scaled by the same 4^r, which leaves the optimum unchanged
+ *             and keeps integer arithmetic exact.  Pixels outside the row
+ *             count as zero.  0 <= r <= 12; r = 0 is no smoothing.
+ *   gamma     the largest bending angle in radians (>= 0, finite).  A link
+ *             of displacement d has inclination atan(d/n) from the vertical;
+ *             the next link's e is admissible when
+ *             |atan(e/n) - atan(d/n)| <= gamma, evaluated in double (Fig. 5,
+ *             Eqs. 6-7; the pi/4 limit of Eqs. 6-7 is |e| <= n-1).
+ *             gamma = 0 keeps the displacement fixed; gamma >= pi/2 admits
+ *             every e.
+ *   dtype     FHTDP_U8 or FHTDP_I32 (integer images; FHTDP_F32 returns
+ *             FHTDP_EINVAL).  Sums are int32: uint8 images need
+ *             255 * 4^r * h < 2^31 (checked); int32 images need
+ *             max|pixel| * 4^r * h < 2^31 (the caller guarantees it).
+ *   Scores are int32 and refer to the smoothed image.  Ties are broken as in
+ *   fhtdp_detect_polyline (the lexicographically smallest polyline).
+ * ---------------------------------------------------------------------- */
+/* The window of every displacement, on the host: lohi[2n-1][2] (HOST
+ * memory, written by the call), row d + n - 1 = {lo(d), hi(d)}.  n is a
+ * power of two in [1, 256]. */
+int fhtdp_angle_window(int n, double gamma, int32_t *lohi);
+
+/* Step 1: out[y][x] = sum_t C(2r, r+t) img[y][x+t] (device; out is a dense
+ * int32 [h][w] array, pitch w, that must not overlap img). */
+int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r, int32_t *out,
+                     cudaStream_t stream);
+
+/* Step 2: the DP of fhtdp_polyline_dp over int32 Hough images (laid out as
+ * fhtdp_fht_bands leaves them), in place, with the bend-angle windows. */
+int fhtdp_polyline_dp_angle(void *hough, int dtype, int h, int w, int k, double gamma,
+                            cudaStream_t stream);
+
+/* Step 3: the read-back of fhtdp_backtrack with the bend-angle windows. */
+int fhtdp_backtrack_angle(const void *V, int dtype, int h, int w, int k, double gamma,
+                          int32_t *x_out, int32_t *d_out, void *score_out, cudaStream_t stream);
+
+/* Steps 1-3 on one image: smoothing, band FHTs, the angle DP and the
+ * read-back.  ws: device workspace of at least fhtdp_angle_workspace_bytes()
+ * bytes (0 for invalid arguments).  Outputs as for fhtdp_backtrack. */
+size_t fhtdp_angle_workspace_bytes(int dtype, int h, int w, int k, int r);
+int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pitch, int k,
+                                int r, double gamma, int32_t *x_out, int32_t *d_out,
+                                void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Learned window proposal (no counterpart in the paper): a 4-layer,
  * 32-channel 3x3 CNN on the 4x4-downsampled image predicts, for each band, a
  * bin of 4 displacements; the DP then searches only a window around it

@@ -74,6 +74,17 @@ _SIGS = {
     "fhtdp_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "fhtdp_batch_plan_destroy": (None, [ctypes.c_void_p]),
+    "fhtdp_angle_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
+    "fhtdp_gauss_rows": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
+                         + [ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_polyline_dp_angle": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4
+                                + [ctypes.c_double, ctypes.c_void_p]),
+    "fhtdp_backtrack_angle": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4
+                              + [ctypes.c_double] + [ctypes.c_void_p] * 4),
+    "fhtdp_angle_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 5),
+    "fhtdp_detect_polyline_angle": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
+                                    + [ctypes.c_double] + [ctypes.c_void_p] * 4
+                                    + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_cnn_downsample4": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 3
                               + [ctypes.c_void_p, ctypes.c_void_p]),
     "fhtdp_cnn_conv3x3": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
@@ -328,4 +339,76 @@ def detect_polyline(img, k: int, B: int, out=None, ws=None, stream=None):
     _check(lib().fhtdp_detect_polyline(img.data_ptr(), code, h, w, pitch, k, B, x.data_ptr(),
                                        d.data_ptr(), score.data_ptr(), ws.data_ptr(), ws.numel(),
                                        _stream(stream)))
+    return x, d, score
+
+
+# ---------------------------------------------------------------------------
+# The main problem (Sec. 2.3): row smoothing and bend-angle windows.
+
+def angle_window(n: int, gamma: float):
+    """numpy int32 [2n-1][2]: row d + n - 1 holds the range of next
+    displacements whose bend angle from d is at most gamma (host call)."""
+    import numpy as np
+    out = np.zeros((2 * n - 1, 2), dtype=np.int32)
+    _check(lib().fhtdp_angle_window(int(n), float(gamma), out.ctypes.data))
+    return out
+
+
+def _int_image_code(img) -> int:
+    code = _dtype_code(img)
+    if code == DTYPE_F32:
+        raise TypeError("the angle path takes uint8 or int32 images")
+    return code
+
+
+def gauss_rows(img, r: int, out=None, stream=None):
+    """Every row convolved with the binomial weights C(2r, r+t): int32 [h, w]."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _int_image_code(img)
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    _check(lib().fhtdp_gauss_rows(img.data_ptr(), code, h, w, pitch, int(r), out.data_ptr(),
+                                  _stream(stream)))
+    return out
+
+
+def polyline_dp_angle(hough, h: int, w: int, k: int, gamma: float, stream=None):
+    """The DP with bend-angle windows in place over int32 Hough images."""
+    _check(lib().fhtdp_polyline_dp_angle(hough.data_ptr(), DTYPE_I32, h, w, k, float(gamma),
+                                         _stream(stream)))
+    return hough
+
+
+def backtrack_angle(V, h: int, w: int, k: int, gamma: float, out=None, stream=None):
+    """(x[k+1], d[k], score[1]) read back with the bend-angle windows."""
+    x, d, score = out if out is not None else _outputs(k, DTYPE_I32, V.device)
+    _check(lib().fhtdp_backtrack_angle(V.data_ptr(), DTYPE_I32, h, w, k, float(gamma),
+                                       x.data_ptr(), d.data_ptr(), score.data_ptr(),
+                                       _stream(stream)))
+    return x, d, score
+
+
+def angle_workspace_bytes(dtype: int, h: int, w: int, k: int, r: int) -> int:
+    return lib().fhtdp_angle_workspace_bytes(dtype, h, w, k, r)
+
+
+def detect_polyline_angle(img, k: int, r: int, gamma: float, out=None, ws=None, stream=None):
+    """Steps 1-3 of the main problem on one device image (uint8 or int32):
+    (x[k+1], d[k], score[1]), the score of the smoothed image."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _int_image_code(img)
+    need = angle_workspace_bytes(code, h, w, k, r)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_polyline_angle(None, code, h, w, pitch, k, int(r),
+                                                 float(gamma), None, None, None, None, 0,
+                                                 _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    x, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_polyline_angle(img.data_ptr(), code, h, w, pitch, k, int(r),
+                                             float(gamma), x.data_ptr(), d.data_ptr(),
+                                             score.data_ptr(), ws.data_ptr(), ws.numel(),
+                                             _stream(stream)))
     return x, d, score

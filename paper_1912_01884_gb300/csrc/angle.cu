@@ -1,0 +1,77 @@
+// The main problem of Sec. 2.3 on one image: row smoothing (step 1), the band
+// FHTs, the DP with bend-angle windows (step 2) and the read-back (step 3).
+// Host side only: the window table and the sequence of launches.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace fhtdp {
+
+// Fig. 5: a link of displacement d over n rows has inclination atan(d / n);
+// the bend angle between links d and e is |atan(e / n) - atan(d / n)|.  As
+// atan is increasing, the admissible e for one d form an interval (the
+// union of the ranges of Eqs. 6 and 7), and both of its ends are
+// non-decreasing in d, so one sweep with two pointers finds every interval.
+// The comparison is the definition itself, evaluated in double.
+bool make_angle_table(int n, double gamma, AngleTable *t) {
+    if (!(gamma >= 0.0) || !std::isfinite(gamma) || n < 1 || 2 * n - 1 > kMaxD) return false;
+    const int D = 2 * n - 1;
+    double a[kMaxD];
+    for (int i = 0; i < D; ++i) a[i] = std::atan((double)(i - (n - 1)) / n);
+    int lo = 0, hi = 0, maxlen = 1;
+    for (int i = 0; i < D; ++i) {
+        while (a[i] - a[lo] > gamma) ++lo;
+        if (hi < i) hi = i;
+        while (hi + 1 < D && a[hi + 1] - a[i] <= gamma) ++hi;
+        t->lo[i] = (int16_t)(lo - (n - 1));
+        t->hi[i] = (int16_t)(hi - (n - 1));
+        if (hi - lo + 1 > maxlen) maxlen = hi - lo + 1;
+    }
+    for (int i = D; i < kMaxD; ++i) t->lo[i] = t->hi[i] = 0;
+    t->n = n;
+    t->maxlen = maxlen;
+    return true;
+}
+
+namespace {
+constexpr size_t kAngleHead = 256;   // the argmax key, cleared by every call
+
+size_t round_up(size_t v) { return (v + 255) & ~(size_t)255; }
+}  // namespace
+
+// [head][smoothed image h*w int32][Hough/V k*2n*W int32][FHT scratch, same]
+size_t angle_workspace_bytes(const Shape &s) {
+    const size_t hough = (size_t)s.k * 2 * s.n * s.W * 4;
+    return kAngleHead + round_up((size_t)s.h * s.w * 4) + 2 * round_up(hough);
+}
+
+int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
+                 const AngleTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                 void *ws, cudaStream_t stream) {
+    char *base = (char *)ws;
+    unsigned long long *key = (unsigned long long *)base;
+    int32_t *smooth = (int32_t *)(base + kAngleHead);
+    int32_t *H = (int32_t *)(base + kAngleHead + round_up((size_t)s.h * s.w * 4));
+    int32_t *tmp = H + round_up((size_t)s.k * 2 * s.n * s.W * 4) / 4;
+    int st = cuda_status(cudaMemsetAsync(base, 0, kAngleHead, stream), "cudaMemsetAsync");
+    if (st) return st;
+    if (r == 0) {   // no smoothing: the FHT reads the image itself
+        st = dtype == FHTDP_U8
+                 ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp,
+                                                       stream)
+                 : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp,
+                                                       stream);
+    } else {
+        st = dtype == FHTDP_U8
+                 ? launch_gauss_rows<uint8_t>((const uint8_t *)img, pitch, s.h, s.w, r, smooth,
+                                              stream)
+                 : launch_gauss_rows<int32_t>((const int32_t *)img, pitch, s.h, s.w, r, smooth,
+                                              stream);
+        if (!st) st = launch_fht_stages<int32_t, int32_t>(smooth, s.w, s, H, tmp, stream);
+    }
+    if (!st) st = launch_dp_angle(H, s, t, stream);
+    if (!st) st = launch_backtrack_angle_key(H, s, t, key, x_out, d_out, score_out, stream);
+    return st;
+}
+
+}  // namespace fhtdp

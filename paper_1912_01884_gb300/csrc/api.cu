@@ -1,6 +1,7 @@
 // C-ABI entry points: argument validation, dispatch on the pixel type, and
 // error reporting.  No exception and no allocation happens here.
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <new>
@@ -164,6 +165,112 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
     return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, ws_bytes, stream);
+}
+
+// ---------------------------------------------------------------------------
+// The main problem (Sec. 2.3): smoothing and bend-angle windows.
+namespace {
+int check_angle_common(int dtype, int h, int w, int k, double gamma, Shape *s) {
+    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
+        return set_error(FHTDP_EINVAL, "the angle path takes integer images (dtype %d)", dtype);
+    if (!make_shape(h, w, k, s)) return bad_shape(h, w, k);
+    if (!(gamma >= 0.0) || !std::isfinite(gamma))
+        return set_error(FHTDP_EINVAL, "bend angle gamma must be finite and >= 0");
+    return FHTDP_OK;
+}
+int check_gauss(int dtype, int h, int r) {
+    if (r < 0 || r > kMaxGaussR)
+        return set_error(FHTDP_EINVAL, "smoothing half-width r=%d outside [0, %d]", r, kMaxGaussR);
+    if (dtype == FHTDP_U8 && 255.0 * std::ldexp(1.0, 2 * r) * h >= 2147483648.0)
+        return set_error(FHTDP_EINVAL, "255 * 4^r * h >= 2^31: int32 sums could overflow");
+    return FHTDP_OK;
+}
+}  // namespace
+
+int fhtdp_angle_window(int n, double gamma, int32_t *lohi) {
+    g_last_error[0] = 0;
+    if (n < 1 || n > 256 || (n & (n - 1)) || !lohi)
+        return set_error(FHTDP_EINVAL, "angle window: n a power of two in [1, 256], non-null lohi");
+    AngleTable t;
+    if (!make_angle_table(n, gamma, &t))
+        return set_error(FHTDP_EINVAL, "bend angle gamma must be finite and >= 0");
+    for (int i = 0; i < 2 * n - 1; ++i) {
+        lohi[2 * i] = t.lo[i];
+        lohi[2 * i + 1] = t.hi[i];
+    }
+    return FHTDP_OK;
+}
+
+int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r, int32_t *out,
+                     cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
+        return set_error(FHTDP_EINVAL, "smoothing takes integer images (dtype %d)", dtype);
+    if (h < 1 || w < 1 || h > (1 << 20) || w > (1 << 20))
+        return set_error(FHTDP_EINVAL, "invalid image %d x %d", h, w);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (!img || !out) return set_error(FHTDP_EINVAL, "null img or out pointer");
+    int st = check_gauss(dtype, h, r);
+    if (st) return st;
+    if (dtype == FHTDP_U8)
+        return launch_gauss_rows<uint8_t>((const uint8_t *)img, pitch, h, w, r, out, stream);
+    return launch_gauss_rows<int32_t>((const int32_t *)img, pitch, h, w, r, out, stream);
+}
+
+int fhtdp_polyline_dp_angle(void *hough, int dtype, int h, int w, int k, double gamma,
+                            cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    int st = check_angle_common(dtype, h, w, k, gamma, &s);
+    if (st) return st;
+    if (!hough) return set_error(FHTDP_EINVAL, "null hough pointer");
+    AngleTable t;
+    make_angle_table(s.n, gamma, &t);
+    return launch_dp_angle((int32_t *)hough, s, t, stream);
+}
+
+int fhtdp_backtrack_angle(const void *V, int dtype, int h, int w, int k, double gamma,
+                          int32_t *x_out, int32_t *d_out, void *score_out, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    int st = check_angle_common(dtype, h, w, k, gamma, &s);
+    if (st) return st;
+    if (!V || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null V or output pointer");
+    AngleTable t;
+    make_angle_table(s.n, gamma, &t);
+    return launch_backtrack_angle((const int32_t *)V, s, t, x_out, d_out, (int32_t *)score_out,
+                                  stream);
+}
+
+size_t fhtdp_angle_workspace_bytes(int dtype, int h, int w, int k, int r) {
+    Shape s;
+    if ((dtype != FHTDP_U8 && dtype != FHTDP_I32) || !make_shape(h, w, k, &s) || r < 0 ||
+        r > kMaxGaussR)
+        return 0;
+    return angle_workspace_bytes(s);
+}
+
+int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pitch, int k,
+                                int r, double gamma, int32_t *x_out, int32_t *d_out,
+                                void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    int st = check_angle_common(dtype, h, w, k, gamma, &s);
+    if (st) return st;
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    st = check_gauss(dtype, h, r);
+    if (st) return st;
+    if (!img || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    size_t need = angle_workspace_bytes(s);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    AngleTable t;
+    make_angle_table(s.n, gamma, &t);
+    return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, (int32_t *)score_out, ws,
+                        stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,6 +29,21 @@ struct Shape {
     int log2n;
 };
 
+// The bend-angle window of every displacement (Sec. 2.3, Fig. 5, Eqs. 6-7):
+// entry d + n - 1 holds the range [lo, hi] of next displacements e with
+// |atan(e/n) - atan(d/n)| <= gamma.  Passed to kernels by value.
+constexpr int kMaxD = 511;
+struct AngleTable {
+    int16_t lo[kMaxD], hi[kMaxD];
+    int n;
+    int maxlen;  // the longest window, hi - lo + 1
+};
+// Fills *t for bands of n rows; false if gamma is negative or not finite.
+bool make_angle_table(int n, double gamma, AngleTable *t);
+
+// Largest half-width of the row smoothing (binomial weights up to C(24, 12)).
+constexpr int kMaxGaussR = 12;
+
 // Host helpers (api.cu).
 int set_error(int code, const char *fmt, ...);
 // Checks a launch and counts it (fhtdp_launch_count).
@@ -49,5 +64,22 @@ int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long
 template <typename Acc>
 int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_t *d_out,
                      Acc *score_out, cudaStream_t stream);
+
+// The main problem (Sec. 2.3): row smoothing of an integer image into a dense
+// int32 [h][w] image, the DP with bend-angle windows, and its read-backs.
+template <typename In>
+int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *out,
+                      cudaStream_t stream);
+int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream);
+int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const AngleTable &t,
+                               unsigned long long *key, int32_t *x_out, int32_t *d_out,
+                               int32_t *score_out, cudaStream_t stream);
+int launch_backtrack_angle(const int32_t *V, const Shape &s, const AngleTable &t,
+                           int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                           cudaStream_t stream);
+size_t angle_workspace_bytes(const Shape &s);
+int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
+                 const AngleTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                 void *ws, cudaStream_t stream);
 
 }  // namespace fhtdp

@@ -29,6 +29,19 @@ __device__ __forceinline__ Acc vmax(Acc a, Acc b) {
     return a > b ? a : b;
 }
 
+// Continuation windows of the read-back: the integer bend limit |e - d| <= B,
+// or the bend-angle table of the main problem.
+struct BendWin {
+    int B, n;
+    __device__ int lo(int d) const { return max(d - B, -(n - 1)); }
+    __device__ int hi(int d) const { return min(d + B, n - 1); }
+};
+struct AngleWin {
+    AngleTable t;
+    __device__ int lo(int d) const { return t.lo[d + t.n - 1]; }
+    __device__ int hi(int d) const { return t.hi[d + t.n - 1]; }
+};
+
 // Band k-1: V = H where the link ends inside the image, dead elsewhere.
 template <typename Acc>
 __global__ void dp_last_band_kernel(Acc *hv, Shape s) {
@@ -111,6 +124,74 @@ __global__ void dp_band_tiled_kernel(Acc *hv, Shape s, int band, int B, int C) {
     }
 }
 
+// The DP step with the bend-angle windows of the main problem (Sec. 2.3,
+// RangeMaxQ over the range of Eqs. 6-7): V_b(x, d) = H_b(x, d) +
+// max_{lo(d) <= e <= hi(d)} V_{b+1}(x + d, e).  Same tiling as
+// dp_band_tiled_kernel (a block owns continuation columns xn), but the
+// windows differ in length, so each one is answered as a range-maximum query
+// on a sparse table: after doubling step j a row holds the maximum of 2^j
+// consecutive rows, and a window of length L with 2^j <= L < 2^(j+1) is the
+// maximum of the runs starting at lo and at hi - 2^j + 1.  The windows of
+// level j are answered before step j+1 overwrites the runs, so two buffers
+// suffice.  Max is exact: the values are those of the scan over the window.
+__global__ void dp_band_angle_kernel(int32_t *hv, Shape s, int band, AngleTable t, int C) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const int D = s.D;
+    int32_t *a = (int32_t *)raw, *b = a + (size_t)D * C;
+    int16_t *slo = (int16_t *)(b + (size_t)D * C), *shi = slo + D;
+    const int xn0 = (int)blockIdx.x * C - (s.n - 1);
+    const int32_t dead = Dead<int32_t>::value();
+    const size_t dup_row = ((size_t)band * 2 + 1) * s.n * s.W;   // d = 0, "-" half
+    if (!(xn0 + C > 0 && xn0 < s.w)) {
+        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+            const int r = i / C, c = i - r * C;
+            const int d = r - (s.n - 1), x = xn0 + c - d;
+            if (x < 0 || x >= s.W) continue;
+            hv[cell<int32_t>(s, band, x, d)] = dead;
+            if (d == 0) hv[dup_row + x] = dead;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        slo[i] = t.lo[i];
+        shi[i] = t.hi[i];
+    }
+    for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+        const int r = i / C, c = i - r * C;
+        const int xn = xn0 + c;
+        a[i] = (xn >= 0 && xn < s.w) ? hv[cell<int32_t>(s, band + 1, xn, r - (s.n - 1))] : dead;
+    }
+    __syncthreads();
+    for (int len = 1;; len *= 2) {
+        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+            const int r = i / C, c = i - r * C;
+            const int lo = slo[r] + s.n - 1, hi = shi[r] + s.n - 1;
+            const int L = hi - lo + 1;
+            if (L < len || L >= 2 * len) continue;
+            const int d = r - (s.n - 1), xn = xn0 + c, x = xn - d;
+            if (x < 0 || x >= s.W) continue;
+            const size_t idx = cell<int32_t>(s, band, x, d);
+            int32_t v = dead;
+            if (x < s.w && xn >= 0 && xn < s.w) {
+                const int32_t best = vmax(a[lo * C + c], a[(hi - len + 1) * C + c]);
+                v = (best == dead) ? dead : hv[idx] + best;
+            }
+            hv[idx] = v;
+            if (d == 0) hv[dup_row + x] = v;
+        }
+        if (2 * len > t.maxlen) break;
+        __syncthreads();
+        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
+            const int r = i / C;
+            b[i] = r + len < D ? vmax(a[i], a[i + len * C]) : a[i];
+        }
+        __syncthreads();
+        int32_t *tmp = a;
+        a = b;
+        b = tmp;
+    }
+}
+
 // Order-preserving 32-bit image of a value (negative zero counts as zero).
 __device__ __forceinline__ uint32_t vord(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
 __device__ __forceinline__ uint32_t vord(float f) {
@@ -154,8 +235,8 @@ __global__ void argmax_kernel(const Acc *V, Shape s, unsigned long long *key) {
 // One warp: the read-back from the argmax key (Eq. 5); every band's window
 // is scanned by the lanes, the first maximum kept.  No admissible state
 // (key 0): x = -1 everywhere and a dead score.
-template <typename Acc>
-__global__ void readback_kernel(const Acc *V, Shape s, int B, const unsigned long long *key,
+template <typename Acc, typename Win>
+__global__ void readback_kernel(const Acc *V, Shape s, Win win, const unsigned long long *key,
                                 int32_t *x_out, int32_t *d_out, Acc *score_out) {
     const int lane = threadIdx.x;
     const Acc dead = Dead<Acc>::value();
@@ -177,7 +258,7 @@ __global__ void readback_kernel(const Acc *V, Shape s, int B, const unsigned lon
     }
     for (int i = 1; i < s.k; ++i) {
         x += d;
-        const int lo = max(d - B, -(s.n - 1)), hi = min(d + B, s.n - 1);
+        const int lo = win.lo(d), hi = win.hi(d);
         Acc bv = dead;
         int be = INT_MAX;
         for (int e = lo + lane; e <= hi; e += 32) {
@@ -205,8 +286,8 @@ __global__ void readback_kernel(const Acc *V, Shape s, int B, const unsigned lon
 }
 
 // One block: lexicographically smallest argmax of V_0, then the read-back.
-template <typename Acc>
-__global__ void backtrack_kernel(const Acc *V, Shape s, int B, int32_t *x_out, int32_t *d_out,
+template <typename Acc, typename Win>
+__global__ void backtrack_kernel(const Acc *V, Shape s, Win win, int32_t *x_out, int32_t *d_out,
                                  Acc *score_out) {
     __shared__ Acc sv[1024];
     __shared__ int si[1024];
@@ -243,7 +324,7 @@ __global__ void backtrack_kernel(const Acc *V, Shape s, int B, int32_t *x_out, i
     *score_out = sv[0];
     for (int i = 1; i < s.k; ++i) {
         x += d;
-        int lo = max(d - B, -(s.n - 1)), hi = min(d + B, s.n - 1);
+        int lo = win.lo(d), hi = win.hi(d);
         Acc bv = dead;
         int be = lo;
         for (int e = lo; e <= hi; ++e) {
@@ -296,7 +377,8 @@ int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream) {
 template <typename Acc>
 int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_t *d_out,
                      Acc *score_out, cudaStream_t stream) {
-    backtrack_kernel<Acc><<<1, 1024, 0, stream>>>(V, s, B, x_out, d_out, score_out);
+    backtrack_kernel<Acc, BendWin><<<1, 1024, 0, stream>>>(V, s, BendWin{B, s.n}, x_out, d_out,
+                                                            score_out);
     return launched("backtrack_kernel");
 }
 
@@ -306,8 +388,62 @@ int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long
     argmax_kernel<Acc><<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key);
     int st = launched("argmax_kernel");
     if (st) return st;
-    readback_kernel<Acc><<<1, 32, 0, stream>>>(V, s, B, key, x_out, d_out, score_out);
+    readback_kernel<Acc, BendWin><<<1, 32, 0, stream>>>(V, s, BendWin{B, s.n}, key, x_out, d_out,
+                                                         score_out);
     return launched("readback_kernel");
+}
+
+// Continuation columns per block of the angle DP: the widest tile (up to 32
+// columns, 128-byte row segments) that still gives two blocks per SM.
+static int angle_tile_columns(const Shape &s) {
+    const int span = s.W + 2 * (s.n - 1);
+    int C = 32;
+    while (C > 8 && (span + C - 1) / C < 2 * 152) C /= 2;
+    while (C > 1 && ((size_t)2 * s.D * C * 4 + 4 * s.D) > 200 * 1024) C /= 2;
+    return C;
+}
+
+int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream) {
+    const size_t per_band = (size_t)2 * s.n * s.W;
+    const int C = angle_tile_columns(s);
+    const size_t smem = (size_t)2 * s.D * C * 4 + 4 * (size_t)s.D;
+    static int smem_set = 48 * 1024;   // dynamic shared memory enabled so far
+    int st = FHTDP_OK;
+    if ((int)smem > smem_set) {
+        st = cuda_status(cudaFuncSetAttribute(dp_band_angle_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "cudaFuncSetAttribute");
+        if (st) return st;
+        smem_set = (int)smem;
+    }
+    dp_last_band_kernel<int32_t><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
+    st = launched("dp_last_band_kernel");
+    const int blocks = (s.W + 2 * (s.n - 1) + C - 1) / C;
+    for (int band = s.k - 2; band >= 0 && !st; --band) {
+        dp_band_angle_kernel<<<blocks, 256, smem, stream>>>(hv, s, band, t, C);
+        st = launched("dp_band_angle_kernel");
+    }
+    return st;
+}
+
+int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const AngleTable &t,
+                               unsigned long long *key, int32_t *x_out, int32_t *d_out,
+                               int32_t *score_out, cudaStream_t stream) {
+    argmax_kernel<int32_t><<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key);
+    int st = launched("argmax_kernel");
+    if (st) return st;
+    readback_kernel<int32_t, AngleWin><<<1, 32, 0, stream>>>(V, s, AngleWin{t}, key, x_out,
+                                                             d_out, score_out);
+    return launched("readback_kernel");
+}
+
+int launch_backtrack_angle(const int32_t *V, const Shape &s, const AngleTable &t,
+                           int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                           cudaStream_t stream) {
+    backtrack_kernel<int32_t, AngleWin><<<1, 1024, 0, stream>>>(V, s, AngleWin{t}, x_out,
+                                                                d_out, score_out);
+    return launched("backtrack_kernel");
 }
 
 template int launch_dp_inplace<int32_t>(int32_t *, const Shape &, int, cudaStream_t);

@@ -121,7 +121,57 @@ int grid_for(size_t total) {
     return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
 }
 
+// Binomial weights C(2r, r + t), |t| <= r, by value.
+struct GaussWeights {
+    int32_t c[2 * kMaxGaussR + 1];
+};
+
+constexpr int kGaussSeg = 1024;   // output columns per block (4 per thread)
+
+// Main problem, step 1 (Sec. 2.3): every row convolved with the discrete
+// Gaussian of half-width r, the unnormalised binomial weights (integer
+// arithmetic, so the sums are exact); pixels outside the row count as zero.
+// A block stages one row segment and its 2r-pixel halo in shared memory as
+// int32 and writes kGaussSeg outputs of the dense [h][w] result.
+template <typename In>
+__global__ void gauss_rows_kernel(const In *__restrict__ img, int pitch, int w, int r,
+                                  GaussWeights g, int32_t *__restrict__ out) {
+    __shared__ int32_t seg[kGaussSeg + 2 * kMaxGaussR];
+    const int y = blockIdx.x;
+    const int x0 = blockIdx.y * kGaussSeg;
+    const In *row = img + (size_t)y * pitch;
+    for (int i = threadIdx.x; i < kGaussSeg + 2 * r; i += blockDim.x) {
+        const int c = x0 - r + i;
+        seg[i] = (c >= 0 && c < w) ? (int32_t)row[c] : 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kGaussSeg; i += blockDim.x) {
+        const int x = x0 + i;
+        if (x >= w) break;
+        int32_t acc = 0;
+        for (int t = 0; t <= 2 * r; ++t) acc += g.c[t] * seg[i + t];
+        out[(size_t)y * w + x] = acc;
+    }
+}
+
 }  // namespace
+
+template <typename In>
+int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *out,
+                      cudaStream_t stream) {
+    GaussWeights g{};
+    g.c[0] = 1;
+    for (int j = 1; j <= 2 * r; ++j)   // row 2r of Pascal's triangle
+        g.c[j] = (int32_t)((int64_t)g.c[j - 1] * (2 * r - j + 1) / j);
+    dim3 grid((unsigned)h, (unsigned)((w + kGaussSeg - 1) / kGaussSeg));   // rows in x: h <= 2^20
+    gauss_rows_kernel<In><<<grid, 256, 0, stream>>>(img, pitch, w, r, g, out);
+    return launched("gauss_rows_kernel");
+}
+
+template int launch_gauss_rows<uint8_t>(const uint8_t *, int, int, int, int, int32_t *,
+                                        cudaStream_t);
+template int launch_gauss_rows<int32_t>(const int32_t *, int, int, int, int, int32_t *,
+                                        cudaStream_t);
 
 template <typename In, typename Acc>
 int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc *tmp,

@@ -237,6 +237,40 @@ def mixed_batch(seed: int, count: int = 256, shapes=None):
     return [plain_uniform(seed * 100003 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(shapes)]
 
 
+def bent_edges(seed: int, h: int = 2048, w: int = 2048, k: int = 16, lines: int = 2,
+               max_slope: float = 0.6, value: int = 70, salt: float = 0.004) -> Workload:
+    """A bent-document-boundary image (Sec. 3, Fig. 3) for the main problem:
+    Gaussian background (mean 30, sd 12, clipped to [0, 255]), `lines` smooth
+    mostly-vertical curves x(y) = x0 + a y + b sin(2 pi y / period + phase)
+    with |dx/dy| <= max_slope, each a 3-pixel ridge adding `value`, 0.6 *
+    `value` and 0.2 * `value` at column offsets 0, +-1, +-2, and spiky noise:
+    a fraction `salt` of all pixels set to 255 (the outliers the Welsh
+    estimate is robust to).  `B` is -1: the image is solved with a bend angle,
+    not an integer bend limit; `planted` holds the curves' columns per row."""
+    rng = Rng(seed, 6)
+    bg = np.clip(np.rint(30.0 + 12.0 * rng.normal(h * w)), 0, 255)
+    img = bg.astype(np.int64).reshape(h, w)
+    y = np.arange(h, dtype=np.float64)
+    planted = []
+    for _ in range(lines):
+        period = h * (0.5 + rng.uniform(1)[0])
+        b = (0.25 + 0.5 * rng.uniform(1)[0]) * max_slope * period / (2 * math.pi)
+        a = (rng.uniform(1)[0] * 2 - 1) * 0.25 * max_slope
+        phase = 2 * math.pi * rng.uniform(1)[0]
+        x = a * y + b * np.sin(2 * math.pi * y / period + phase)
+        x0 = w * (0.2 + 0.6 * rng.uniform(1)[0]) - 0.5 * (x.max() + x.min())
+        cols = np.rint(x0 + x).astype(np.int64)
+        for off, frac in ((0, 1.0), (-1, 0.6), (1, 0.6), (-2, 0.2), (2, 0.2)):
+            c = cols + off
+            ok = (c >= 0) & (c < w)
+            img[np.arange(h)[ok], c[ok]] += int(round(value * frac))
+        planted.append(cols)
+    spikes = rng.uniform(h * w) < salt
+    img = np.clip(img, 0, 255).reshape(-1)
+    img[spikes] = 255
+    return Workload(img.reshape(h, w).astype(np.uint8), k, -1, planted)
+
+
 # The five workloads of the benchmark suite, by name.
 WORKLOADS = {
     "u8_256x256_k4_B8": lambda seed: plain_uniform(seed, 256, 256, 4, 8),

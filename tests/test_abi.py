@@ -83,3 +83,48 @@ def test_batch_autotune_rejects_bad_arguments(lib):
         assert width.value == -1
     finally:
         L.fhtdp_batch_plan_destroy(plan)
+
+
+def test_angle_window_is_computed_on_the_host_like_the_oracle(lib):
+    """The library's bend-angle table (a host computation, no GPU) equals the
+    oracle's pair-by-pair definition, boundary angles included."""
+    import math
+    import numpy as np
+    import oracle
+    for n in (1, 2, 8, 64, 128, 256):
+        for g in (0.0, 0.02, math.radians(10), 0.3, 1.0, math.pi / 2, 3.0,
+                  math.atan(1 / n), math.atan(5 / n) - math.atan(2 / n)):
+            assert np.array_equal(lib.angle_window(n, g), oracle.angle_window(n, g)), (n, g)
+    L = lib.lib()
+    buf = (ctypes.c_int32 * 2)()
+    assert L.fhtdp_angle_window(3, 0.1, buf) == 1          # n not a power of two
+    assert L.fhtdp_angle_window(512, 0.1, buf) == 1        # n > 256
+    assert L.fhtdp_angle_window(1, -0.5, buf) == 1
+    assert L.fhtdp_angle_window(1, float("inf"), buf) == 1
+    assert L.fhtdp_angle_window(1, 0.1, None) == 1
+
+
+def test_angle_entries_reject_bad_arguments_before_launch(lib):
+    L = lib.lib()
+    fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
+    assert L.fhtdp_angle_workspace_bytes(0, 64, 10, 4, 2) > 0
+    assert L.fhtdp_angle_workspace_bytes(2, 64, 10, 4, 2) == 0      # float images
+    assert L.fhtdp_angle_workspace_bytes(0, 64, 10, 4, 13) == 0     # r > 12
+    args = (fake, fake, fake, fake, 1 << 30, None)
+    assert L.fhtdp_detect_polyline_angle(fake, 2, 64, 10, 10, 4, 2, 0.3, *args) == 1
+    assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, -1, 0.3, *args) == 1
+    assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, 2, -0.3, *args) == 1
+    assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, 2, float("nan"), *args) == 1
+    assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 9, 4, 2, 0.3, *args) == 1   # pitch
+    assert L.fhtdp_detect_polyline_angle(None, 0, 64, 10, 10, 4, 2, 0.3, *args) == 1
+    assert L.fhtdp_detect_polyline_angle(fake, 0, 4096, 8, 8, 16, 10, 0.3, *args) == 1
+    assert "4^r" in L.fhtdp_last_error().decode()
+    r = L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, 2, 0.3, fake, fake, fake, fake,
+                                      64, None)
+    assert r == 2 and "workspace" in L.fhtdp_last_error().decode()
+    assert L.fhtdp_gauss_rows(fake, 2, 4, 4, 4, 1, fake, None) == 1
+    assert L.fhtdp_gauss_rows(fake, 0, 4, 4, 3, 1, fake, None) == 1
+    assert L.fhtdp_gauss_rows(None, 0, 4, 4, 4, 1, fake, None) == 1
+    assert L.fhtdp_polyline_dp_angle(None, 0, 64, 10, 4, 0.3, None) == 1
+    assert L.fhtdp_polyline_dp_angle(fake, 0, 96, 10, 1, 0.3, None) == 1
+    assert L.fhtdp_backtrack_angle(fake, 0, 64, 10, 4, 0.3, None, fake, fake, None) == 1
