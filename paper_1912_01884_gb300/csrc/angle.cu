@@ -37,12 +37,16 @@ namespace {
 constexpr size_t kAngleHead = 256;   // the argmax key, cleared by every call
 
 size_t round_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// The smoothed image is stored only for one-row bands (otherwise the
+// smoothing is part of the first FHT level).
+size_t smooth_bytes(const Shape &s) { return s.n == 1 ? round_up((size_t)s.h * s.w * 4) : 0; }
 }  // namespace
 
-// [head][smoothed image h*w int32][Hough/V k*2n*W int32][FHT scratch, same]
+// [head][smoothed image h*w int32, n = 1 only][Hough/V k*2n*W int32][FHT scratch, same]
 size_t angle_workspace_bytes(const Shape &s) {
     const size_t hough = (size_t)s.k * 2 * s.n * s.W * 4;
-    return kAngleHead + round_up((size_t)s.h * s.w * 4) + 2 * round_up(hough);
+    return kAngleHead + smooth_bytes(s) + 2 * round_up(hough);
 }
 
 int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
@@ -51,7 +55,7 @@ int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
     char *base = (char *)ws;
     unsigned long long *key = (unsigned long long *)base;
     int32_t *smooth = (int32_t *)(base + kAngleHead);
-    int32_t *H = (int32_t *)(base + kAngleHead + round_up((size_t)s.h * s.w * 4));
+    int32_t *H = (int32_t *)(base + kAngleHead + smooth_bytes(s));
     int32_t *tmp = H + round_up((size_t)s.k * 2 * s.n * s.W * 4) / 4;
     int st = cuda_status(cudaMemsetAsync(base, 0, kAngleHead, stream), "cudaMemsetAsync");
     if (st) return st;
@@ -61,7 +65,13 @@ int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
                                                        stream)
                  : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp,
                                                        stream);
-    } else {
+    } else if (s.n >= 2) {   // smoothing fused into the first FHT level
+        st = dtype == FHTDP_U8
+                 ? launch_fht_stages_gauss<uint8_t>((const uint8_t *)img, pitch, s, r, H, tmp,
+                                                    stream)
+                 : launch_fht_stages_gauss<int32_t>((const int32_t *)img, pitch, s, r, H, tmp,
+                                                    stream);
+    } else {   // one-row bands: smooth into the workspace, then the FHT
         st = dtype == FHTDP_U8
                  ? launch_gauss_rows<uint8_t>((const uint8_t *)img, pitch, s.h, s.w, r, smooth,
                                               stream)

@@ -70,6 +70,11 @@ int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_
 template <typename In>
 int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *out,
                       cudaStream_t stream);
+// The band FHTs of the smoothed image without storing it: the smoothing is
+// fused into the first level (bands of n >= 2 rows).
+template <typename In>
+int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, int32_t *hough,
+                            int32_t *tmp, cudaStream_t stream);
 int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream);
 int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const AngleTable &t,
                                unsigned long long *key, int32_t *x_out, int32_t *d_out,

@@ -127,68 +127,84 @@ __global__ void dp_band_tiled_kernel(Acc *hv, Shape s, int band, int B, int C) {
 // The DP step with the bend-angle windows of the main problem (Sec. 2.3,
 // RangeMaxQ over the range of Eqs. 6-7): V_b(x, d) = H_b(x, d) +
 // max_{lo(d) <= e <= hi(d)} V_{b+1}(x + d, e).  Same tiling as
-// dp_band_tiled_kernel (a block owns continuation columns xn), but the
-// windows differ in length, so each one is answered as a range-maximum query
-// on a sparse table: after doubling step j a row holds the maximum of 2^j
-// consecutive rows, and a window of length L with 2^j <= L < 2^(j+1) is the
-// maximum of the runs starting at lo and at hi - 2^j + 1.  The windows of
-// level j are answered before step j+1 overwrites the runs, so two buffers
-// suffice.  Max is exact: the values are those of the scan over the window.
-__global__ void dp_band_angle_kernel(int32_t *hv, Shape s, int band, AngleTable t, int C) {
-    extern __shared__ __align__(16) unsigned char raw[];
+// dp_band_tiled_kernel (a block owns C continuation columns xn, and with
+// them the states x = xn - d), but the windows differ in length, so each one
+// is answered as a range-maximum query on a sparse table kept whole in
+// shared memory: level j holds, for every row, the maximum of the 2^j rows
+// from it on, and a window of length L with 2^j <= L < 2^(j+1) is the
+// maximum of the level-j runs starting at lo and at hi - 2^j + 1.  Max is
+// exact: the values are those of the scan over the window.
+//
+// A thread owns column c = tid % C and rows r = tid / C + 32 u, u < RPT
+// (32 * RPT >= 2n - 1): its window bounds and H_b values stay in registers,
+// all its loads are issued before the first shared-memory store, and the
+// results leave as plain stores.  `levels` = floor(log2(longest window)) + 1.
+template <int C, int RPT>
+__global__ void __launch_bounds__(32 * C)
+dp_band_angle_kernel(int32_t *hv, Shape s, int band, AngleTable t, int levels) {
+    extern __shared__ __align__(16) int32_t sm[];
     const int D = s.D;
-    int32_t *a = (int32_t *)raw, *b = a + (size_t)D * C;
-    int16_t *slo = (int16_t *)(b + (size_t)D * C), *shi = slo + D;
-    const int xn0 = (int)blockIdx.x * C - (s.n - 1);
+    const int c = threadIdx.x % C, r0 = threadIdx.x / C;
+    const int xn0 = (int)blockIdx.x * C - (s.n - 1), xn = xn0 + c;
     const int32_t dead = Dead<int32_t>::value();
     const size_t dup_row = ((size_t)band * 2 + 1) * s.n * s.W;   // d = 0, "-" half
     if (!(xn0 + C > 0 && xn0 < s.w)) {
-        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-            const int r = i / C, c = i - r * C;
-            const int d = r - (s.n - 1), x = xn0 + c - d;
-            if (x < 0 || x >= s.W) continue;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
+            if (r >= D || x < 0 || x >= s.W) continue;
             hv[cell<int32_t>(s, band, x, d)] = dead;
             if (d == 0) hv[dup_row + x] = dead;
         }
         return;
     }
-    for (int i = threadIdx.x; i < D; i += blockDim.x) {
-        slo[i] = t.lo[i];
-        shi[i] = t.hi[i];
+    const bool live_col = xn >= 0 && xn < s.w;
+    int32_t va[RPT], hb[RPT];
+    uint32_t lh[RPT];   // window rows lo | hi << 16
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
+        va[u] = dead;
+        hb[u] = 0;
+        lh[u] = 0;
+        if (r < D) {
+            if (live_col) va[u] = hv[cell<int32_t>(s, band + 1, xn, d)];
+            if (live_col && x >= 0 && x < s.w) hb[u] = hv[cell<int32_t>(s, band, x, d)];
+            lh[u] = (uint32_t)(t.lo[r] + s.n - 1) | (uint32_t)(t.hi[r] + s.n - 1) << 16;
+        }
     }
-    for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-        const int r = i / C, c = i - r * C;
-        const int xn = xn0 + c;
-        a[i] = (xn >= 0 && xn < s.w) ? hv[cell<int32_t>(s, band + 1, xn, r - (s.n - 1))] : dead;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int r = r0 + 32 * u;
+        if (r < D) sm[r * C + c] = va[u];
+    }
+    for (int j = 1; j < levels; ++j) {
+        __syncthreads();
+        const int len = 1 << (j - 1);
+        const int32_t *src = sm + (size_t)(j - 1) * D * C;
+        int32_t *dst = sm + (size_t)j * D * C;
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int r = r0 + 32 * u;
+            if (r < D) dst[r * C + c] = r + len < D ? vmax(src[r * C + c], src[(r + len) * C + c])
+                                                    : src[r * C + c];
+        }
     }
     __syncthreads();
-    for (int len = 1;; len *= 2) {
-        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-            const int r = i / C, c = i - r * C;
-            const int lo = slo[r] + s.n - 1, hi = shi[r] + s.n - 1;
-            const int L = hi - lo + 1;
-            if (L < len || L >= 2 * len) continue;
-            const int d = r - (s.n - 1), xn = xn0 + c, x = xn - d;
-            if (x < 0 || x >= s.W) continue;
-            const size_t idx = cell<int32_t>(s, band, x, d);
-            int32_t v = dead;
-            if (x < s.w && xn >= 0 && xn < s.w) {
-                const int32_t best = vmax(a[lo * C + c], a[(hi - len + 1) * C + c]);
-                v = (best == dead) ? dead : hv[idx] + best;
-            }
-            hv[idx] = v;
-            if (d == 0) hv[dup_row + x] = v;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
+        if (r >= D || x < 0 || x >= s.W) continue;
+        int32_t v = dead;
+        if (x < s.w && live_col) {
+            const int lo = (int)(lh[u] & 0xffffu), hi = (int)(lh[u] >> 16);
+            const int j = 31 - __clz(hi - lo + 1);
+            const int32_t *T = sm + (size_t)j * D * C;
+            const int32_t best = vmax(T[lo * C + c], T[(hi - (1 << j) + 1) * C + c]);
+            v = (best == dead) ? dead : hb[u] + best;
         }
-        if (2 * len > t.maxlen) break;
-        __syncthreads();
-        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-            const int r = i / C;
-            b[i] = r + len < D ? vmax(a[i], a[i + len * C]) : a[i];
-        }
-        __syncthreads();
-        int32_t *tmp = a;
-        a = b;
-        b = tmp;
+        hv[cell<int32_t>(s, band, x, d)] = v;
+        if (d == 0) hv[dup_row + x] = v;
     }
 }
 
@@ -393,38 +409,49 @@ int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long
     return launched("readback_kernel");
 }
 
-// Continuation columns per block of the angle DP: the widest tile (up to 32
-// columns, 128-byte row segments) that still gives two blocks per SM.
-static int angle_tile_columns(const Shape &s) {
-    const int span = s.W + 2 * (s.n - 1);
-    int C = 32;
-    while (C > 8 && (span + C - 1) / C < 2 * 152) C /= 2;
-    while (C > 1 && ((size_t)2 * s.D * C * 4 + 4 * s.D) > 200 * 1024) C /= 2;
-    return C;
-}
-
-int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream) {
-    const size_t per_band = (size_t)2 * s.n * s.W;
-    const int C = angle_tile_columns(s);
-    const size_t smem = (size_t)2 * s.D * C * 4 + 4 * (size_t)s.D;
-    static int smem_set = 48 * 1024;   // dynamic shared memory enabled so far
-    int st = FHTDP_OK;
+namespace {
+template <int C, int RPT>
+int launch_dp_angle_tiles(int32_t *hv, const Shape &s, const AngleTable &t,
+                          cudaStream_t stream) {
+    int levels = 1;
+    while ((2 << (levels - 1)) <= t.maxlen) ++levels;   // floor(log2(maxlen)) + 1
+    const size_t smem = (size_t)levels * s.D * C * 4;   // at most 9 * 511 * 8 * 4 = 147 KB
+    static int smem_set = 48 * 1024;                    // dynamic shared memory enabled so far
     if ((int)smem > smem_set) {
-        st = cuda_status(cudaFuncSetAttribute(dp_band_angle_kernel,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem),
-                         "cudaFuncSetAttribute");
+        int st = cuda_status(cudaFuncSetAttribute(dp_band_angle_kernel<C, RPT>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem),
+                             "cudaFuncSetAttribute");
         if (st) return st;
         smem_set = (int)smem;
     }
-    dp_last_band_kernel<int32_t><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
-    st = launched("dp_last_band_kernel");
     const int blocks = (s.W + 2 * (s.n - 1) + C - 1) / C;
+    int st = FHTDP_OK;
     for (int band = s.k - 2; band >= 0 && !st; --band) {
-        dp_band_angle_kernel<<<blocks, 256, smem, stream>>>(hv, s, band, t, C);
+        dp_band_angle_kernel<C, RPT><<<blocks, 32 * C, smem, stream>>>(hv, s, band, t, levels);
         st = launched("dp_band_angle_kernel");
     }
     return st;
+}
+
+template <int C>
+int launch_dp_angle_c(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream) {
+    if (s.D <= 32 * 4) return launch_dp_angle_tiles<C, 4>(hv, s, t, stream);
+    if (s.D <= 32 * 8 || C > 8) return launch_dp_angle_tiles<C, 8>(hv, s, t, stream);
+    return launch_dp_angle_tiles<8, 16>(hv, s, t, stream);   // 256-row bands
+}
+}  // namespace
+
+int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream) {
+    const size_t per_band = (size_t)2 * s.n * s.W;
+    dp_last_band_kernel<int32_t><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
+    int st = launched("dp_last_band_kernel");
+    if (st) return st;
+    // 16 continuation columns per block (64-byte row segments) while that
+    // still gives two blocks per SM, else 8.
+    const int span = s.W + 2 * (s.n - 1);
+    if ((span + 15) / 16 >= 2 * 152 && s.D <= 32 * 8) return launch_dp_angle_c<16>(hv, s, t, stream);
+    return launch_dp_angle_c<8>(hv, s, t, stream);
 }
 
 int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const AngleTable &t,

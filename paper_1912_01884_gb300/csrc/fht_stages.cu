@@ -39,22 +39,23 @@ __global__ void fht_single_row_kernel(const In *img, int pitch, Shape s, Acc *ou
     }
 }
 
+// Every pass below gives one block one row of its output level ([band]
+// [sign][row], blockIdx.x, up to 2h rows) and its threads the columns, so the
+// row's shifts are computed once and each column costs only its loads.
+
 // Level of 2-row sub-bands, read straight from the image (zero padding is
 // the predicate col < w, never stored).
 template <typename In, typename Acc>
 __global__ void fht_level2_kernel(const In *img, int pitch, Shape s, Acc *out) {
-    const size_t total = (size_t)s.k * 2 * s.n * s.W;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % s.W);
-        size_t r = i / s.W;
-        int row = (int)(r % s.n);
-        int bs = (int)(r / s.n);
-        int sign = bs & 1, band = bs >> 1;
-        int sh = row & 1;                       // shift within the 2-row sub-band
-        int ya = band * s.n + (row & ~1);       // top row of the sub-band
-        int xb = wrap(sign == 0 ? x + sh : x - sh, s.W);
-        out[i] = band_pixel<In, Acc>(img, pitch, s.w, ya, x) +
+    const int r = blockIdx.x;
+    const int row = r % s.n, bs = r / s.n;
+    const int sign = bs & 1, band = bs >> 1;
+    const int sh = row & 1;                     // shift within the 2-row sub-band
+    const int ya = band * s.n + (row & ~1);     // top row of the sub-band
+    Acc *dst = out + (size_t)r * s.W;
+    for (int x = threadIdx.x; x < s.W; x += blockDim.x) {
+        const int xb = wrap(sign == 0 ? x + sh : x - sh, s.W);
+        dst[x] = band_pixel<In, Acc>(img, pitch, s.w, ya, x) +
                  band_pixel<In, Acc>(img, pitch, s.w, ya + 1, xb);
     }
 }
@@ -63,23 +64,20 @@ __global__ void fht_level2_kernel(const In *img, int pitch, Shape s, Acc *out) {
 template <typename Acc>
 __global__ void fht_level_kernel(const Acc *__restrict__ src, Shape s, int m,
                                  Acc *__restrict__ dst) {
-    const size_t total = (size_t)s.k * 2 * s.n * s.W;
-    const int half = m >> 1;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % s.W);
-        size_t r = i / s.W;
-        int row = (int)(r % s.n);
-        size_t bs = r / s.n;
-        int sign = (int)(bs & 1);
-        int j0 = row & ~(m - 1);                // first row of the sub-band
-        int sh = row & (m - 1);                 // shift in [0, m)
-        int move = sh - (sh >> 1);              // ceil(sh / 2)
-        int xb = wrap(sign == 0 ? x + move : x - move, s.W);
-        const Acc *base = src + bs * s.n * (size_t)s.W;
-        Acc a = base[(size_t)(j0 + (sh >> 1)) * s.W + x];
-        Acc b = base[(size_t)(j0 + half + (sh >> 1)) * s.W + xb];
-        dst[i] = a + b;
+    const int r = blockIdx.x;
+    const int row = r % s.n, bs = r / s.n;
+    const int sign = bs & 1;
+    const int j0 = row & ~(m - 1);              // first row of the sub-band
+    const int sh = row & (m - 1);               // shift in [0, m)
+    const int move = sh - (sh >> 1);            // ceil(sh / 2)
+    const Acc *base = src + (size_t)bs * s.n * s.W;
+    const Acc *ra = base + (size_t)(j0 + (sh >> 1)) * s.W;
+    const Acc *rb = base + (size_t)(j0 + (m >> 1) + (sh >> 1)) * s.W;
+    Acc *out = dst + (size_t)r * s.W;
+#pragma unroll 4
+    for (int x = threadIdx.x; x < s.W; x += blockDim.x) {
+        const int xb = wrap(sign == 0 ? x + move : x - move, s.W);
+        out[x] = ra[x] + rb[xb];
     }
 }
 
@@ -91,27 +89,111 @@ __global__ void fht_level_kernel(const Acc *__restrict__ src, Shape s, int m,
 template <typename Acc>
 __global__ void fht_level4_kernel(const Acc *__restrict__ src, Shape s, int M,
                                   Acc *__restrict__ dst) {
-    const size_t total = (size_t)s.k * 2 * s.n * s.W;
     const int m = M >> 2;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % s.W);
-        const size_t r = i / s.W;
-        const int row = (int)(r % s.n);
-        const size_t bs = r / s.n;
-        const int sign = (int)(bs & 1);
-        const int j0 = row & ~(M - 1);
-        const int S = row & (M - 1), s2 = S >> 1, q = S >> 2;
-        const int c2 = s2 - (s2 >> 1), cS = S - (S >> 1);
+    const int r = blockIdx.x;
+    const int row = r % s.n, bs = r / s.n;
+    const int sign = bs & 1;
+    const int j0 = row & ~(M - 1);
+    const int S = row & (M - 1), s2 = S >> 1, q = S >> 2;
+    const int c2 = s2 - (s2 >> 1), cS = S - (S >> 1);
+    const Acc *base = src + (size_t)bs * s.n * s.W;
+    const Acc *r0 = base + (size_t)(j0 + q) * s.W;
+    const Acc *r1 = base + (size_t)(j0 + m + q) * s.W;
+    const Acc *r2 = base + (size_t)(j0 + 2 * m + q) * s.W;
+    const Acc *r3 = base + (size_t)(j0 + 3 * m + q) * s.W;
+    Acc *out = dst + (size_t)r * s.W;
+#pragma unroll 4
+    for (int x = threadIdx.x; x < s.W; x += blockDim.x) {
         const int x1 = wrap(sign == 0 ? x + c2 : x - c2, s.W);
         const int xp = wrap(sign == 0 ? x + cS : x - cS, s.W);
         const int x3 = wrap(sign == 0 ? xp + c2 : xp - c2, s.W);
-        const Acc *base = src + bs * s.n * (size_t)s.W;
-        const Acc a0 = base[(size_t)(j0 + q) * s.W + x];
-        const Acc a1 = base[(size_t)(j0 + m + q) * s.W + x1];
-        const Acc a2 = base[(size_t)(j0 + 2 * m + q) * s.W + xp];
-        const Acc a3 = base[(size_t)(j0 + 3 * m + q) * s.W + x3];
-        dst[i] = (a0 + a1) + (a2 + a3);
+        out[x] = (r0[x] + r1[x1]) + (r2[xp] + r3[x3]);
+    }
+}
+
+// Binomial weights C(2r, r + t), |t| <= r, by value.
+struct GaussWeights {
+    int32_t c[2 * kMaxGaussR + 1];
+};
+
+GaussWeights binomial_weights(int r) {
+    GaussWeights g{};
+    g.c[0] = 1;
+    for (int j = 1; j <= 2 * r; ++j)   // row 2r of Pascal's triangle
+        g.c[j] = (int32_t)((int64_t)g.c[j - 1] * (2 * r - j + 1) / j);
+    return g;
+}
+
+// Pixel c of an image row after the row smoothing (zero in the padding
+// columns c >= w and outside the row).
+template <typename In>
+__device__ __forceinline__ int32_t smoothed(const In *row, int w, int r, const GaussWeights &g,
+                                            int c) {
+    if (c >= w) return 0;
+    int32_t acc = 0;
+    for (int t = -r; t <= r; ++t) {
+        const int cc = c + t;
+        if (cc >= 0 && cc < w) acc += g.c[t + r] * (int32_t)row[cc];
+    }
+    return acc;
+}
+
+constexpr int kL2Chunk = 1024;   // columns per block of the smoothing level-2 pass
+
+// Main problem, step 1 fused into the first FHT level: a block takes one
+// pair of image rows (the 2-row sub-band j of a band) and kL2Chunk columns.
+// It stages both raw rows over the chunk and its halo (1 + r columns each
+// side, zero outside the image) in shared memory, smooths the top row A at x
+// and the bottom row B at x-1..x+chunk (columns mod W; a column that wraps
+// around is smoothed from global memory), and writes the four level-2 rows
+// of the pair: shifts 0 and 1 of both signs, A(x) + B(x) and A(x) + B(x +/- 1).
+template <typename In>
+__global__ void fht_level2_gauss_kernel(const In *img, int pitch, Shape s, int r,
+                                        GaussWeights g, int32_t *out) {
+    constexpr int kRaw = kL2Chunk + 2 + 2 * kMaxGaussR;
+    __shared__ int32_t rawa[kRaw], rawb[kRaw], sa[kL2Chunk], sb[kL2Chunk + 2];
+    const int half = s.n >> 1;
+    const int pair = blockIdx.x;
+    const int band = pair / half, j = pair - band * half;
+    const int ya = band * s.n + 2 * j;
+    const int x0 = blockIdx.y * kL2Chunk;
+    const int cols = min(kL2Chunk, s.W - x0);
+    const int base = x0 - 1 - r;   // image column of rawa[0] / rawb[0]
+    const In *ra = img + (size_t)ya * pitch, *rb = ra + pitch;
+    for (int i = threadIdx.x; i < cols + 2 + 2 * r; i += blockDim.x) {
+        const int c = base + i;
+        const bool in = c >= 0 && c < s.w;
+        rawa[i] = in ? (int32_t)ra[c] : 0;
+        rawb[i] = in ? (int32_t)rb[c] : 0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cols + 2; i += blockDim.x) {
+        const int c = x0 - 1 + i, cw = wrap(c, s.W);
+        int32_t vb = 0;
+        if (cw != c) {
+            vb = smoothed(rb, s.w, r, g, cw);
+        } else if (c < s.w) {
+            for (int t = 0; t <= 2 * r; ++t) vb += g.c[t] * rawb[i + t];
+        }
+        sb[i] = vb;
+        if (i < cols && c + 1 < s.w) {
+            int32_t va = 0;
+            for (int t = 0; t <= 2 * r; ++t) va += g.c[t] * rawa[i + 1 + t];
+            sa[i] = va;
+        } else if (i < cols) {
+            sa[i] = 0;
+        }
+    }
+    __syncthreads();
+    int32_t *plus = out + ((size_t)(band * 2) * s.n + 2 * j) * s.W;
+    int32_t *minus = out + ((size_t)(band * 2 + 1) * s.n + 2 * j) * s.W;
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+        const int x = x0 + i;
+        const int32_t A = sa[i], B = sb[i + 1];
+        plus[x] = A + B;
+        plus[s.W + x] = A + sb[i + 2];
+        minus[x] = A + B;
+        minus[s.W + x] = A + sb[i];
     }
 }
 
@@ -120,11 +202,6 @@ int grid_for(size_t total) {
     size_t cap = 152 * 16;
     return (int)(blocks < cap ? (blocks ? blocks : 1) : cap);
 }
-
-// Binomial weights C(2r, r + t), |t| <= r, by value.
-struct GaussWeights {
-    int32_t c[2 * kMaxGaussR + 1];
-};
 
 constexpr int kGaussSeg = 1024;   // output columns per block (4 per thread)
 
@@ -159,10 +236,7 @@ __global__ void gauss_rows_kernel(const In *__restrict__ img, int pitch, int w, 
 template <typename In>
 int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *out,
                       cudaStream_t stream) {
-    GaussWeights g{};
-    g.c[0] = 1;
-    for (int j = 1; j <= 2 * r; ++j)   // row 2r of Pascal's triangle
-        g.c[j] = (int32_t)((int64_t)g.c[j - 1] * (2 * r - j + 1) / j);
+    const GaussWeights g = binomial_weights(r);
     dim3 grid((unsigned)h, (unsigned)((w + kGaussSeg - 1) / kGaussSeg));   // rows in x: h <= 2^20
     gauss_rows_kernel<In><<<grid, 256, 0, stream>>>(img, pitch, w, r, g, out);
     return launched("gauss_rows_kernel");
@@ -173,6 +247,39 @@ template int launch_gauss_rows<uint8_t>(const uint8_t *, int, int, int, int, int
 template int launch_gauss_rows<int32_t>(const int32_t *, int, int, int, int, int32_t *,
                                         cudaStream_t);
 
+namespace {
+// The passes after level 2 (which the caller wrote into pass_dst(s, 0, ...)):
+// two levels at a time, then one if a level is left.  The passes alternate
+// between tmp and hough so that the last one lands in hough.
+int fht_passes(const Shape &s) {
+    const int levels = s.log2n;
+    return 1 + (levels - 1) / 2 + (levels - 1) % 2;
+}
+template <typename Acc>
+Acc *pass_dst(const Shape &s, int p, Acc *hough, Acc *tmp) {
+    return ((fht_passes(s) - 1 - p) % 2 == 0) ? hough : tmp;
+}
+template <typename Acc>
+int fht_upper_levels(const Shape &s, Acc *hough, Acc *tmp, cudaStream_t stream) {
+    const int rows = s.k * 2 * s.n;
+    const int levels = s.log2n;
+    int st = FHTDP_OK, pass = 0, l = 1;
+    for (; l + 2 <= levels && !st; l += 2, ++pass) {
+        fht_level4_kernel<Acc><<<rows, 256, 0, stream>>>(pass_dst(s, pass, hough, tmp), s,
+                                                          1 << (l + 2),
+                                                          pass_dst(s, pass + 1, hough, tmp));
+        st = launched("fht_level4_kernel");
+    }
+    if (l < levels && !st) {
+        fht_level_kernel<Acc><<<rows, 256, 0, stream>>>(pass_dst(s, pass, hough, tmp), s,
+                                                         1 << levels,
+                                                         pass_dst(s, pass + 1, hough, tmp));
+        st = launched("fht_level_kernel");
+    }
+    return st;
+}
+}  // namespace
+
 template <typename In, typename Acc>
 int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc *tmp,
                       cudaStream_t stream) {
@@ -181,30 +288,26 @@ int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc 
         fht_single_row_kernel<In, Acc><<<grid_for(total), 256, 0, stream>>>(img, pitch, s, hough);
         return launched("fht_single_row_kernel");
     }
-    const size_t total = (size_t)s.k * 2 * s.n * s.W;
-    const int levels = s.log2n;
-    // Passes: level 1 from the image, then two levels at a time, then one
-    // if a level is left.  The passes alternate between tmp and hough so
-    // that the last one lands in hough.
-    const int passes = 1 + (levels - 1) / 2 + (levels - 1) % 2;
-    int pass = 0;
-    auto dst_of = [&](int p) { return ((passes - 1 - p) % 2 == 0) ? hough : tmp; };
-    fht_level2_kernel<In, Acc><<<grid_for(total), 256, 0, stream>>>(img, pitch, s, dst_of(0));
+    fht_level2_kernel<In, Acc><<<s.k * 2 * s.n, 256, 0, stream>>>(img, pitch, s,
+                                                                  pass_dst(s, 0, hough, tmp));
     int st = launched("fht_level2_kernel");
-    int l = 1;
-    for (; l + 2 <= levels && !st; l += 2, ++pass) {
-        fht_level4_kernel<Acc><<<grid_for(total), 256, 0, stream>>>(dst_of(pass), s, 1 << (l + 2),
-                                                                    dst_of(pass + 1));
-        st = launched("fht_level4_kernel");
-    }
-    if (l < levels && !st) {
-        fht_level_kernel<Acc><<<grid_for(total), 256, 0, stream>>>(dst_of(pass), s, 1 << levels,
-                                                                   dst_of(pass + 1));
-        st = launched("fht_level_kernel");
-    }
-    return st;
+    return st ? st : fht_upper_levels<Acc>(s, hough, tmp, stream);
 }
 
+template <typename In>
+int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, int32_t *hough,
+                            int32_t *tmp, cudaStream_t stream) {
+    dim3 grid((unsigned)(s.k * (s.n / 2)), (unsigned)((s.W + kL2Chunk - 1) / kL2Chunk));
+    fht_level2_gauss_kernel<In><<<grid, 256, 0, stream>>>(img, pitch, s, r, binomial_weights(r),
+                                                          pass_dst(s, 0, hough, tmp));
+    int st = launched("fht_level2_gauss_kernel");
+    return st ? st : fht_upper_levels<int32_t>(s, hough, tmp, stream);
+}
+
+template int launch_fht_stages_gauss<uint8_t>(const uint8_t *, int, const Shape &, int, int32_t *,
+                                              int32_t *, cudaStream_t);
+template int launch_fht_stages_gauss<int32_t>(const int32_t *, int, const Shape &, int, int32_t *,
+                                              int32_t *, cudaStream_t);
 template int launch_fht_stages<uint8_t, int32_t>(const uint8_t *, int, const Shape &, int32_t *,
                                                  int32_t *, cudaStream_t);
 template int launch_fht_stages<int32_t, int32_t>(const int32_t *, int, const Shape &, int32_t *,
