@@ -22,6 +22,9 @@ Function map (paper passages in the C file's comments):
   dp_angle / backtrack_angle / detect_angle
                    the main problem with the angle restriction
   brute_angle      every polyline passing the direct angle test, tiny images
+  dp_through / detect_through / brute_through
+                   Sec. 2.2-2.3 Subproblems 2-3: the extreme polyline through a
+                   given point on a band border
 """
 from __future__ import annotations
 
@@ -104,6 +107,14 @@ def _load():
             lib.oracle_detect_angle_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
                                                     + [ctypes.c_double, _I32P, _I32P])
             lib.oracle_detect_angle_f64.restype = ctypes.c_double
+            lib.oracle_dp_through_f64.argtypes = [_F64P] + [ctypes.c_int] * 6 + [_F64P]
+            lib.oracle_detect_through_f64.argtypes = ([_F64P] + [ctypes.c_int] * 6
+                                                      + [_I32P, _I32P])
+            lib.oracle_detect_through_f64.restype = ctypes.c_double
+            lib.oracle_brute_through_f64.argtypes = ([_F64P] + [ctypes.c_int] * 6
+                                                     + [_I32P, _I32P,
+                                                        ctypes.POINTER(ctypes.c_long)])
+            lib.oracle_brute_through_f64.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -337,3 +348,42 @@ def detect_angle(img, k: int, r: int, gamma: float):
                                         float(gamma), _p(xs, ctypes.c_int32),
                                         _p(ds, ctypes.c_int32))
     return xs, ds, s
+
+
+def dp_through(H: np.ndarray, h: int, w: int, k: int, B: int, j: int, xp: int) -> np.ndarray:
+    """V[k][2n-1][w] of the DP whose band-j states (j = k: band k-1's end
+    points) off the point xp are dead."""
+    n = h // k
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    V = np.empty((k, 2 * n - 1, w), dtype=np.float64)
+    if _load().oracle_dp_through_f64(_p(H, ctypes.c_double), h, w, k, B, int(j), int(xp),
+                                     _p(V, ctypes.c_double)):
+        raise ValueError("bad shape, point or bend")
+    return V
+
+
+def detect_through(img, k: int, B: int, j: int, xp: int):
+    """The extreme polyline through (xp, j*n): (x[k+1], d[k], score)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    if not (0 <= j <= k and 0 <= xp < w):
+        raise ValueError("point outside the image")
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_through_f64(_p(img, ctypes.c_double), h, w, k, B, int(j),
+                                          int(xp), _p(xs, ctypes.c_int32),
+                                          _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def brute_through(img, k: int, B: int, j: int, xp: int):
+    """Brute force over the admissible polylines with x_j = xp."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    visited = ctypes.c_long(0)
+    s = _load().oracle_brute_through_f64(_p(img, ctypes.c_double), h, w, k, B, int(j),
+                                         int(xp), _p(xs, ctypes.c_int32),
+                                         _p(ds, ctypes.c_int32), ctypes.byref(visited))
+    return xs, ds, s, visited.value

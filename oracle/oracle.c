@@ -676,3 +676,131 @@ double oracle_detect_angle_f64(const double *img, int h, int w, int k, int r, do
     free(lohi);
     return s;
 }
+
+/* ---------------------------------------------------------------------------
+ * Subproblems 2-3 (Sec. 2.2-2.3): the extreme polyline through a given point
+ * P = (xp, j*n) on the upper border of band j (j = k: the image's bottom
+ * border).  Plain definition: the maximum over all admissible polylines with
+ * x_j = xp (bend limit B at every vertex, P included), the lexicographically
+ * smallest among the optimal ones.  The paper builds the part below P by the
+ * DP over bands j..k-1 and the part above by the same DP on the top bands
+ * flipped about Ox; this oracle reaches the same optimum with one DP over
+ * all bands in which every state of band j (j = k: of band k-1) whose vertex
+ * on P's border is not xp is dead.  Then V_0 holds the best polylines
+ * through P and the usual read-back (Eq. 5) returns the answer.
+ * ------------------------------------------------------------------------ */
+int oracle_dp_through_f64(const double *H, int h, int w, int k, int B, int j, int xp,
+                          double *V) {
+    if (k < 1 || h % k != 0 || B < 0 || j < 0 || j > k || xp < 0 || xp >= w) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    for (int b = k - 1; b >= 0; --b)
+        for (int d = -(n - 1); d <= n - 1; ++d)
+            for (int x = 0; x < w; ++x) {
+                double *out = &V[((size_t)b * D + (d + n - 1)) * w + x];
+                int xn = x + d;
+                int off_point = (b == j && x != xp) || (j == k && b == k - 1 && xn != xp);
+                if (xn < 0 || xn >= w || off_point) {
+                    *out = ORACLE_NEG;
+                    continue;
+                }
+                double hv = hough_at_f64(H, n, W, b, x, d);
+                if (b == k - 1) {
+                    *out = hv;
+                    continue;
+                }
+                double best = ORACLE_NEG;
+                for (int e = d - B; e <= d + B; ++e) {
+                    if (e < -(n - 1) || e > n - 1) continue;
+                    double v = V[((size_t)(b + 1) * D + (e + n - 1)) * w + xn];
+                    if (v > best) best = v;
+                }
+                *out = (best == ORACLE_NEG) ? ORACLE_NEG : hv + best;
+            }
+    return 0;
+}
+
+double oracle_detect_through_f64(const double *img, int h, int w, int k, int B, int j, int xp,
+                                 int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * (2 * n - 1) * w);
+    double s = NAN;
+    if (H && V) {
+        oracle_fht_recursive_f64(img, h, w, k, H);
+        if (oracle_dp_through_f64(H, h, w, k, B, j, xp, V) == 0)
+            s = oracle_backtrack_f64(V, h, w, k, B, xs, ds);
+    }
+    free(H);
+    free(V);
+    return s;
+}
+
+/* Brute force over every admissible polyline with x_j = xp (tiny images). */
+typedef struct {
+    const double *img;
+    int h, w, k, n, B, j, xp;
+    int32_t *cur_d;
+    int cur_x0;
+    double best;
+    int32_t *best_x;
+    int32_t *best_d;
+    long visited;
+} brute_through_state;
+
+static void brute_through_rec(brute_through_state *st, int i, int x) {
+    if (i == st->j && x != st->xp) return;   /* vertex x_i is x */
+    if (i == st->k) {
+        st->visited++;
+        double sc = oracle_path_score_f64(st->img, st->h, st->w, st->k, st->cur_x0, st->cur_d);
+        if (sc > st->best) {
+            st->best = sc;
+            int xx = st->cur_x0;
+            for (int q = 0; q < st->k; ++q) {
+                st->best_x[q] = xx;
+                st->best_d[q] = st->cur_d[q];
+                xx += st->cur_d[q];
+            }
+            st->best_x[st->k] = xx;
+        }
+        return;
+    }
+    int n = st->n;
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        if (i > 0 && (d < st->cur_d[i - 1] - st->B || d > st->cur_d[i - 1] + st->B)) continue;
+        if (x + d < 0 || x + d >= st->w) continue;
+        st->cur_d[i] = d;
+        brute_through_rec(st, i + 1, x + d);
+    }
+}
+
+double oracle_brute_through_f64(const double *img, int h, int w, int k, int B, int j, int xp,
+                                int32_t *xs, int32_t *ds, long *visited) {
+    brute_through_state st;
+    st.img = img;
+    st.h = h;
+    st.w = w;
+    st.k = k;
+    st.n = h / k;
+    st.B = B;
+    st.j = j;
+    st.xp = xp;
+    st.cur_d = (int32_t *)calloc((size_t)k, sizeof(int32_t));
+    st.best = ORACLE_NEG;
+    st.best_x = xs;
+    st.best_d = ds;
+    st.visited = 0;
+    for (int x0 = 0; x0 < w; ++x0) {
+        st.cur_x0 = x0;
+        brute_through_rec(&st, 0, x0);
+    }
+    free(st.cur_d);
+    if (visited) *visited = st.visited;
+    if (st.best == ORACLE_NEG) {
+        for (int i = 0; i <= k; ++i) xs[i] = -1;
+        for (int i = 0; i < k; ++i) ds[i] = 0;
+    }
+    return st.best;
+}
