@@ -3,7 +3,8 @@
 read-back) in Mpix/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload plain2048|mixed|float8192|plain256|angle2048] [--images I]
+                    [--workload plain2048|mixed|float8192|plain256|angle2048|through2048]
+                    [--images I]
 
 Default workload: synthetic 2048x2048 uint8 images, k=16 bands of 128 rows,
 bend range 16.  A step is one pass of the whole method over a batch of
@@ -48,6 +49,10 @@ WORKLOADS = {
         desc="main problem: u8 2048x2048 bent edges with salt noise, rows smoothed with the "
              "binomial Gaussian r=2, k=16 bands of 128 rows, bend angle <= 10 degrees",
         images=32, dtype="u8"),
+    "through2048": dict(
+        desc="Subproblem 3: u8 2048x2048 (the plain2048 images), k=16 bands of 128 rows, bend 16, "
+             "the best polyline through one point per image on band border 8",
+        images=32, dtype="u8"),
     "learned1024": dict(
         desc="u8 1024x1024 lanes over textured noise, k=16 bands of 64 rows, bend 12: learned "
              "window proposal (4-layer 32-channel bf16 CNN on the 4x downsample, windows of 16) "
@@ -70,6 +75,15 @@ NCU_TRAFFIC_DP_ANGLE_LAUNCH = 4.144896e6 + 0.0
 # Fig. 3 example bends by at most 10 degrees).
 ANGLE_R = 2
 ANGLE_GAMMA = 0.17453292519943295   # 10 degrees in radians
+
+
+# The through-point workload's query: border 8 of 16, at the first planted
+# polyline's vertex there.
+THROUGH_BORDER = 8
+
+
+def through_column(wl):
+    return int(wl.planted[0][0][THROUGH_BORDER])
 
 
 def algorithmic_bytes(h, w, k, bpp):
@@ -187,6 +201,9 @@ def make_workload(name, images, seed, rank):
         return [(w.img, w.k, w.B) for w in (synth.ridge_response(s) for s in seeds)]
     if name == "angle2048":
         return [(w.img, w.k, None) for w in (synth.bent_edges(s) for s in seeds)]
+    if name == "through2048":
+        return [(w.img, w.k, (w.B, THROUGH_BORDER, through_column(w)))
+                for w in (synth.plain_gaussian(s) for s in seeds)]
     shapes = synth.mixed_batch_shapes(seed * 7919 + rank, images)
     return [(synth.plain_uniform(s, h, w, k, B).img, k, B)
             for s, (h, w, k, B) in zip(seeds, shapes)]
@@ -201,6 +218,8 @@ def oracle_rate(items, budget_s):
     for img, k, B in items:
         if B is None:
             oracle.detect_angle(img, k, ANGLE_R, ANGLE_GAMMA)
+        elif isinstance(B, tuple):
+            oracle.detect_through(img, k, *B)
         elif img.dtype == np.float32:
             oracle.detect_f32(img, k, B)
         else:
@@ -435,12 +454,15 @@ def run_ours(args):
 ANGLE_LANES = 8   # streams over which one step spreads its images (4: -4 %, 2: -21 %)
 
 
-def run_angle(args):
-    """The main problem (smoothing + band FHT + bend-angle DP + read-back) on
-    a batch of images per step.  Each image is one fhtdp_detect_polyline_angle
-    call (24 launches); a step spreads the images over ANGLE_LANES streams,
-    each with its own workspace, and is captured once as a CUDA graph that
-    every timed step replays."""
+def run_standalone(args):
+    """The calls that run on the standalone kernels, on a batch of images per
+    step: the main problem (angle2048: smoothing + band FHT + bend-angle DP +
+    read-back, one fhtdp_detect_polyline_angle call of 24 launches per image)
+    or the through-point query (through2048: band FHT + DP with the point's
+    band masked + read-back, one fhtdp_detect_through_point call per image).
+    A step spreads the images over ANGLE_LANES streams, each with its own
+    workspace, and is captured once as a CUDA graph that every timed step
+    replays."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -453,11 +475,13 @@ def run_angle(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     fd.load()
-    spec = WORKLOADS["angle2048"]
+    name = args.workload
+    spec = WORKLOADS[name]
     I = args.images or spec["images"]
-    items = make_workload("angle2048", I, args.seed, rank)
+    items = make_workload(name, I, args.seed, rank)
     h, w = items[0][0].shape
     k = items[0][1]
+    angle = name == "angle2048"
     host = torch.empty((I, h, w), dtype=torch.uint8).pin_memory()
     for j, (img, _, _) in enumerate(items):
         host[j].copy_(torch.from_numpy(img))
@@ -465,7 +489,8 @@ def run_angle(args):
     xs = torch.empty((I, k + 1), dtype=torch.int32, device=dev)
     ds = torch.empty((I, k), dtype=torch.int32, device=dev)
     sc = torch.empty((I, 1), dtype=torch.int32, device=dev)
-    need = fd.angle_workspace_bytes(fd.DTYPE_U8, h, w, k, ANGLE_R)
+    need = (fd.angle_workspace_bytes(fd.DTYPE_U8, h, w, k, ANGLE_R) if angle
+            else fd.through_workspace_bytes(fd.DTYPE_U8, h, w, k))
     lanes = min(args.lanes or ANGLE_LANES, I)
     wss = [torch.empty(need, dtype=torch.uint8, device=dev) for _ in range(lanes)]
     main = torch.cuda.Stream(dev)      # graphs are captured off the default stream
@@ -477,8 +502,14 @@ def run_angle(args):
         for ln in range(lanes):
             side[ln].wait_stream(main)
             for j in range(ln, I, lanes):
-                fd.detect_polyline_angle(src[j], k, ANGLE_R, ANGLE_GAMMA,
-                                         out=(xs[j], ds[j], sc[j]), ws=wss[ln], stream=side[ln])
+                if angle:
+                    fd.detect_polyline_angle(src[j], k, ANGLE_R, ANGLE_GAMMA,
+                                             out=(xs[j], ds[j], sc[j]), ws=wss[ln],
+                                             stream=side[ln])
+                else:
+                    B, jb, xp = items[j][2]
+                    fd.detect_through_point(src[j], k, B, jb, xp, out=(xs[j], ds[j], sc[j]),
+                                            ws=wss[ln], stream=side[ln])
         for ln in range(lanes):
             main.wait_stream(side[ln])
 
@@ -545,37 +576,46 @@ def run_angle(args):
     smooth = torch.empty((h, w), dtype=torch.int32, device=dev)
     hough = torch.empty((k, 2, h // k, w + h // k), dtype=torch.int32, device=dev)
     one = (xs[0], ds[0], sc[0])
-    stages = {
-        "gauss_rows": lambda: fd.gauss_rows(imgs[0], ANGLE_R, out=smooth, stream=main),
-        "fht_bands": lambda: fd.fht_bands(smooth, k, out=hough, ws=ws_tmp, stream=main),
-        "dp_angle": lambda: fd.polyline_dp_angle(hough, h, w, k, ANGLE_GAMMA, stream=main),
-        "backtrack": lambda: fd.backtrack_angle(hough, h, w, k, ANGLE_GAMMA, out=one,
-                                                stream=main),
-    }
+    if angle:
+        stages = {
+            "gauss_rows": lambda: fd.gauss_rows(imgs[0], ANGLE_R, out=smooth, stream=main),
+            "fht_bands": lambda: fd.fht_bands(smooth, k, out=hough, ws=ws_tmp, stream=main),
+            "dp_angle": lambda: fd.polyline_dp_angle(hough, h, w, k, ANGLE_GAMMA, stream=main),
+            "backtrack": lambda: fd.backtrack_angle(hough, h, w, k, ANGLE_GAMMA, out=one,
+                                                    stream=main),
+        }
+    else:
+        B0 = items[0][2][0]
+        stages = {
+            "fht_bands": lambda: fd.fht_bands(imgs[0], k, out=hough, ws=ws_tmp, stream=main),
+            "dp": lambda: fd.polyline_dp(hough, h, w, k, B0, stream=main),
+            "backtrack": lambda: fd.backtrack(hough, h, w, k, B0, out=one, stream=main),
+        }
     stage_ms = {name: [] for name in stages}
     for rep in range(6):
-        for name, fn in stages.items():
+        for sname, fn in stages.items():
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(main)
             fn()
             b.record(main)
             b.synchronize()
             if rep >= 2:
-                stage_ms[name].append(a.elapsed_time(b))
-    stage_ms = {name: statistics.median(v) for name, v in stage_ms.items()}
+                stage_ms[sname].append(a.elapsed_time(b))
+    stage_ms = {sname: statistics.median(v) for sname, v in stage_ms.items()}
     n = h // k
     D = 2 * n - 1
     # minimal DRAM bytes of each stage run on its own
     stage_bytes = {
         "gauss_rows": h * w * (1 + 4),
-        "fht_bands": h * w * 4 + k * 2 * n * (w + n) * 4,
+        "fht_bands": h * w * (4 if angle else 1) + k * 2 * n * (w + n) * 4,
         "dp_angle": (k - 1) * 3 * D * w * 4,
+        "dp": (k - 1) * 3 * D * w * 4,
         "backtrack": D * w * 4,
     }
     # The roofline kernel is the DP (the largest share of the launch list);
     # "backtrack" here is the standalone one-block read-back, not the argmax
-    # + one-warp read-back that fhtdp_detect_polyline_angle runs.
-    top = "dp_angle"
+    # + one-warp read-back that the detection calls run.
+    top = "dp_angle" if angle else "dp"
     hbm, peak_kind = peaks()
     achieved = stage_bytes[top] / (stage_ms[top] / 1e3) / 1e9
 
@@ -587,16 +627,19 @@ def run_angle(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": spec["desc"], "images_per_step": I,
                        "pixels_per_step": pix_rank, "parallelism": "images sharded over ranks",
-                       "lanes": lanes, "r": ANGLE_R, "gamma_rad": ANGLE_GAMMA,
+                       "lanes": lanes,
+                       **({"r": ANGLE_R, "gamma_rad": ANGLE_GAMMA} if angle else
+                          {"B": items[0][2][0], "border": THROUGH_BORDER}),
                        "l2": "inputs %d MB per step %s 129 MB L2, no flush"
                              % (host.numel() // 2**20, ">" if host.numel() > 129e6 else "<")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": NCU_TRAFFIC_DP_ANGLE_LAUNCH * (k - 1) if (h, w, k) == (2048, 2048, 16)
-                                    else None,
+                         "traffic": NCU_TRAFFIC_DP_ANGLE_LAUNCH * (k - 1)
+                                    if angle and (h, w, k) == (2048, 2048, 16) else None,
                          "peak_kind": peak_kind,
-                         "kernel": "dp_band_angle_kernel (the k-1 band launches of one image "
-                                   "and the last-band kernel, timed together)"},
+                         "kernel": "%s (the k-1 band launches of one image and the last-band "
+                                   "kernel, timed together)"
+                                   % ("dp_band_angle_kernel" if angle else "dp_band_tiled_kernel")},
             "stages_ms_one_image": stage_ms,
             "pipeline_frac_of_hbm": sum(algorithmic_bytes(h, w, k, 1) for _ in range(I))
                                     / (total_s / args.steps) / 1e9 / hbm,
@@ -606,7 +649,7 @@ def run_angle(args):
             "clocks": clocks,
         }
         if world == 1 and not args.skip_cpu:
-            rate, done = oracle_rate(make_workload("angle2048", 12, 900000 + args.seed, 0), 12.0)
+            rate, done = oracle_rate(make_workload(name, 12, 900000 + args.seed, 0), 12.0)
             out["cpu_baseline"] = {
                 "value": rate, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                 "sample": "%d images of the workload, whole method, one thread" % done}
@@ -697,8 +740,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "angle2048":
-        run_angle(args)
+    elif args.workload in ("angle2048", "through2048"):
+        run_standalone(args)
     elif args.workload == "learned1024":
         run_learned(args)
     else:

@@ -208,6 +208,24 @@ int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pi
                                 void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Subproblems 2-3 (Sec. 2.2-2.3): the extreme polyline through a given point
+ * P = (xp, j*n) on the upper border of band j, 0 <= j <= k (j = k is the
+ * image's bottom border), 0 <= xp < w.  The result is the best admissible
+ * polyline (bend limit B at every vertex, P included) with x_j = xp, the
+ * lexicographically smallest among the optimal ones; B >= 2n-2 is
+ * Subproblem 2 (no bend limit).  The paper finds the part above P by
+ * flipping the top bands about Ox; one DP over all bands with the states of
+ * P's band off xp marked dead reaches the same optimum.
+ *   dtype  FHTDP_U8 or FHTDP_I32 (FHTDP_F32 returns FHTDP_EINVAL).
+ *   ws     device workspace of at least fhtdp_through_workspace_bytes()
+ *          bytes (0 for invalid arguments).  Outputs as for fhtdp_backtrack.
+ * ---------------------------------------------------------------------- */
+size_t fhtdp_through_workspace_bytes(int dtype, int h, int w, int k);
+int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pitch, int k, int B,
+                               int j, int xp, int32_t *x_out, int32_t *d_out, void *score_out,
+                               void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Learned window proposal (no counterpart in the paper): a 4-layer,
  * 32-channel 3x3 CNN on the 4x4-downsampled image predicts, for each band, a
  * bin of 4 displacements; the DP then searches only a window around it

@@ -85,6 +85,9 @@ _SIGS = {
     "fhtdp_detect_polyline_angle": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                                     + [ctypes.c_double] + [ctypes.c_void_p] * 4
                                     + [ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_through_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
+    "fhtdp_detect_through_point": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 8
+                                   + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_cnn_downsample4": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 3
                               + [ctypes.c_void_p, ctypes.c_void_p]),
     "fhtdp_cnn_conv3x3": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
@@ -411,4 +414,31 @@ def detect_polyline_angle(img, k: int, r: int, gamma: float, out=None, ws=None, 
                                              float(gamma), x.data_ptr(), d.data_ptr(),
                                              score.data_ptr(), ws.data_ptr(), ws.numel(),
                                              _stream(stream)))
+    return x, d, score
+
+
+# ---------------------------------------------------------------------------
+# Subproblems 2-3: the extreme polyline through a given point.
+
+def through_workspace_bytes(dtype: int, h: int, w: int, k: int) -> int:
+    return lib().fhtdp_through_workspace_bytes(dtype, h, w, k)
+
+
+def detect_through_point(img, k: int, B: int, j: int, xp: int, out=None, ws=None, stream=None):
+    """The best polyline through (xp, j * h/k) on a band border (uint8 or
+    int32 image): (x[k+1], d[k], score[1]) with x[j] = xp."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _int_image_code(img)
+    need = through_workspace_bytes(code, h, w, k)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_through_point(None, code, h, w, pitch, k, B, j, xp, None, None,
+                                                None, None, 0, _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    x, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_through_point(img.data_ptr(), code, h, w, pitch, k, B, int(j),
+                                            int(xp), x.data_ptr(), d.data_ptr(),
+                                            score.data_ptr(), ws.data_ptr(), ws.numel(),
+                                            _stream(stream)))
     return x, d, score

@@ -13,7 +13,7 @@ namespace fhtdp {
 // union of the ranges of Eqs. 6 and 7), and both of its ends are
 // non-decreasing in d, so one sweep with two pointers finds every interval.
 // The comparison is the definition itself, evaluated in double.
-bool make_angle_table(int n, double gamma, AngleTable *t) {
+bool make_angle_table(int n, double gamma, WindowTable *t) {
     if (!(gamma >= 0.0) || !std::isfinite(gamma) || n < 1 || 2 * n - 1 > kMaxD) return false;
     const int D = 2 * n - 1;
     double a[kMaxD];
@@ -50,7 +50,7 @@ size_t angle_workspace_bytes(const Shape &s) {
 }
 
 int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
-                 const AngleTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                 const WindowTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
                  void *ws, cudaStream_t stream) {
     char *base = (char *)ws;
     unsigned long long *key = (unsigned long long *)base;
@@ -79,7 +79,7 @@ int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
                                               stream);
         if (!st) st = launch_fht_stages<int32_t, int32_t>(smooth, s.w, s, H, tmp, stream);
     }
-    if (!st) st = launch_dp_angle(H, s, t, stream);
+    if (!st) st = launch_dp_window<int32_t>(H, s, t, stream);
     if (!st) st = launch_backtrack_angle_key(H, s, t, key, x_out, d_out, score_out, stream);
     return st;
 }

@@ -191,7 +191,7 @@ int fhtdp_angle_window(int n, double gamma, int32_t *lohi) {
     g_last_error[0] = 0;
     if (n < 1 || n > 256 || (n & (n - 1)) || !lohi)
         return set_error(FHTDP_EINVAL, "angle window: n a power of two in [1, 256], non-null lohi");
-    AngleTable t;
+    WindowTable t;
     if (!make_angle_table(n, gamma, &t))
         return set_error(FHTDP_EINVAL, "bend angle gamma must be finite and >= 0");
     for (int i = 0; i < 2 * n - 1; ++i) {
@@ -224,9 +224,9 @@ int fhtdp_polyline_dp_angle(void *hough, int dtype, int h, int w, int k, double 
     int st = check_angle_common(dtype, h, w, k, gamma, &s);
     if (st) return st;
     if (!hough) return set_error(FHTDP_EINVAL, "null hough pointer");
-    AngleTable t;
+    WindowTable t;
     make_angle_table(s.n, gamma, &t);
-    return launch_dp_angle((int32_t *)hough, s, t, stream);
+    return launch_dp_window<int32_t>((int32_t *)hough, s, t, stream);
 }
 
 int fhtdp_backtrack_angle(const void *V, int dtype, int h, int w, int k, double gamma,
@@ -237,7 +237,7 @@ int fhtdp_backtrack_angle(const void *V, int dtype, int h, int w, int k, double 
     if (st) return st;
     if (!V || !x_out || !d_out || !score_out)
         return set_error(FHTDP_EINVAL, "null V or output pointer");
-    AngleTable t;
+    WindowTable t;
     make_angle_table(s.n, gamma, &t);
     return launch_backtrack_angle((const int32_t *)V, s, t, x_out, d_out, (int32_t *)score_out,
                                   stream);
@@ -267,10 +267,43 @@ int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pi
     if (!ws || ws_bytes < need)
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
-    AngleTable t;
+    WindowTable t;
     make_angle_table(s.n, gamma, &t);
     return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, (int32_t *)score_out, ws,
                         stream);
+}
+
+// ---------------------------------------------------------------------------
+// Subproblems 2-3: the extreme polyline through a given point.
+size_t fhtdp_through_workspace_bytes(int dtype, int h, int w, int k) {
+    Shape s;
+    if ((dtype != FHTDP_U8 && dtype != FHTDP_I32) || !make_shape(h, w, k, &s)) return 0;
+    return through_workspace_bytes(s);
+}
+
+int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pitch, int k, int B,
+                               int j, int xp, int32_t *x_out, int32_t *d_out, void *score_out,
+                               void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
+        return set_error(FHTDP_EINVAL, "the through-point query takes integer images (dtype %d)",
+                         dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (j < 0 || j > k || xp < 0 || xp >= w)
+        return set_error(FHTDP_EINVAL, "point (%d, border %d) outside [0, %d) x [0, %d]", xp, j,
+                         w, k);
+    if (!img || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    size_t need = through_workspace_bytes(s);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    const PointMask pm{j, xp};
+    return detect_through(img, dtype, pitch, s, B, pm, x_out, d_out, (int32_t *)score_out, ws,
+                          stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,17 +29,21 @@ struct Shape {
     int log2n;
 };
 
-// The bend-angle window of every displacement (Sec. 2.3, Fig. 5, Eqs. 6-7):
-// entry d + n - 1 holds the range [lo, hi] of next displacements e with
-// |atan(e/n) - atan(d/n)| <= gamma.  Passed to kernels by value.
+// The continuation window of every displacement: entry d + n - 1 holds the
+// range [lo, hi] of next displacements e admissible after d.  The bend-angle
+// windows of Sec. 2.3 (Fig. 5, Eqs. 6-7: |atan(e/n) - atan(d/n)| <= gamma)
+// and the integer bend limit |e - d| <= B are both such tables.  Passed to
+// kernels by value.
 constexpr int kMaxD = 511;
-struct AngleTable {
+struct WindowTable {
     int16_t lo[kMaxD], hi[kMaxD];
     int n;
     int maxlen;  // the longest window, hi - lo + 1
 };
 // Fills *t for bands of n rows; false if gamma is negative or not finite.
-bool make_angle_table(int n, double gamma, AngleTable *t);
+bool make_angle_table(int n, double gamma, WindowTable *t);
+// The integer bend limit as a table (B >= 0).
+void make_bend_table(int n, int B, WindowTable *t);
 
 // Largest half-width of the row smoothing (binomial weights up to C(24, 12)).
 constexpr int kMaxGaussR = 12;
@@ -55,8 +59,15 @@ bool make_shape(int h, int w, int k, Shape *out);
 template <typename In, typename Acc>
 int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc *tmp,
                       cudaStream_t stream);
+// A point P = (xp, j*n) on the upper border of band j (j = k: the bottom
+// border) that the polyline must pass (Subproblems 2-3): the DP marks every
+// state whose vertex on that border is not xp dead.
+struct PointMask {
+    int j, xp;
+};
 template <typename Acc>
-int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream);
+int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream,
+                      const PointMask *pm = nullptr);
 // The read-back with a grid-wide argmax into *key (zero before the call).
 template <typename Acc>
 int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long *key,
@@ -75,16 +86,24 @@ int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *ou
 template <typename In>
 int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, int32_t *hough,
                             int32_t *tmp, cudaStream_t stream);
-int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream);
-int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const AngleTable &t,
+// The DP over any window table (int32 or float values), in place, with an
+// optional through-point restriction.
+template <typename Acc>
+int launch_dp_window(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t stream,
+                     const PointMask *pm = nullptr);
+int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const WindowTable &t,
                                unsigned long long *key, int32_t *x_out, int32_t *d_out,
                                int32_t *score_out, cudaStream_t stream);
-int launch_backtrack_angle(const int32_t *V, const Shape &s, const AngleTable &t,
+int launch_backtrack_angle(const int32_t *V, const Shape &s, const WindowTable &t,
                            int32_t *x_out, int32_t *d_out, int32_t *score_out,
                            cudaStream_t stream);
 size_t angle_workspace_bytes(const Shape &s);
+size_t through_workspace_bytes(const Shape &s);
+int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
+                   const PointMask &pm, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                   void *ws, cudaStream_t stream);
 int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
-                 const AngleTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                 const WindowTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
                  void *ws, cudaStream_t stream);
 
 }  // namespace fhtdp

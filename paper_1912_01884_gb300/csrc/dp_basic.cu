@@ -3,14 +3,18 @@
 //
 // Sec. 2.2-2.3, Eqs. 3-4: going up from the last band, every Hough cell
 // (x, d) of band i is increased by the best admissible continuation in band
-// i+1, i.e. the maximum of V_{i+1}(x + d, e) over the bend window
-// |e - d| <= B.  Eq. 5 and the main problem's steps 2-3: the best top point
-// is the maximum of V_0, and the polyline is read back band by band.
+// i+1, i.e. the maximum of V_{i+1}(x + d, e) over the continuation window of
+// d: the integer bend limit |e - d| <= B, or the bend-angle range of Eqs. 6-7
+// (both as a window table).  Eq. 5 and the main problem's steps 2-3: the best
+// top point is the maximum of V_0, and the polyline is read back band by band.
 //
 // These kernels keep the paper's layout and in-place update (one launch per
-// band).  They are the modular path and the one for 256-row bands; the fused
-// engine (engine.cu) is the fast one for bands of up to 128 rows.
+// band).  They are the modular path, the path of 256-row bands, of the main
+// problem's angle windows and of the through-point query; the fused engine
+// (engine.cu) is the fast one for integer bend limits and bands of up to 128
+// rows.
 #include <climits>
+#include <functional>
 
 #include "common.cuh"
 
@@ -36,8 +40,8 @@ struct BendWin {
     __device__ int lo(int d) const { return max(d - B, -(n - 1)); }
     __device__ int hi(int d) const { return min(d + B, n - 1); }
 };
-struct AngleWin {
-    AngleTable t;
+struct TableWin {
+    WindowTable t;
     __device__ int lo(int d) const { return t.lo[d + t.n - 1]; }
     __device__ int hi(int d) const { return t.hi[d + t.n - 1]; }
 };
@@ -59,117 +63,74 @@ __global__ void dp_last_band_kernel(Acc *hv, Shape s) {
 }
 
 
-// Band `band` < k-1, given V of band+1 already in place, with the bend-window
-// maxima taken once per column instead of once per state.  A block owns the
-// continuation columns xn in [xn0, xn0 + C) (the grid covers xn in
-// [-(n-1), W + n - 1), so every state (x, d), x in [0, W), has exactly one
-// owner xn = x + d).  It loads V_{b+1}(xn, e) for all e (dead rows beyond
-// [-(n-1), n-1]) into shared memory, takes the window maxima over
-// |e - d| <= B by doubling (after step j a row holds the maximum of 2^j
-// consecutive rows; a window of L = 2B+1 rows is the maximum of two such
-// runs) and writes V_b(x, d) = H_b(x, d) + M in place.  Max is exact, so the
-// values are those of the scan over the window.
+// The through-point restriction (Subproblems 2-3): every state of `band`
+// whose vertex on the point's border is not xp becomes dead: the link's
+// start x when the point is on the band's upper border, its end x + d when
+// it is on the band's lower border (the image's bottom, end = 1).
 template <typename Acc>
-__global__ void dp_band_tiled_kernel(Acc *hv, Shape s, int band, int B, int C) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    const int D = 2 * s.n - 1, R = D + 2 * B;
-    Acc *a = (Acc *)raw, *b = a + (size_t)R * C;
-    const int xn0 = (int)blockIdx.x * C - (s.n - 1);
-    const Acc dead = Dead<Acc>::value();
-    const bool any_live = xn0 + C > 0 && xn0 < s.w;
-    if (any_live) {
-        for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
-            const int r = i / C, c = i - r * C;
-            const int e = r - B - (s.n - 1), xn = xn0 + c;
-            a[i] = (e >= -(s.n - 1) && e <= s.n - 1 && xn >= 0 && xn < s.w)
-                       ? hv[cell<Acc>(s, band + 1, xn, e)]
-                       : dead;
-        }
-        __syncthreads();
-        const int L = 2 * B + 1;
-        int len = 1;
-        for (; 2 * len <= L; len *= 2) {
-            for (int i = threadIdx.x; i < R * C; i += blockDim.x) {
-                const int r = i / C;
-                b[i] = r + len < R ? vmax(a[i], a[i + len * C]) : a[i];
-            }
-            __syncthreads();
-            Acc *t = a;
-            a = b;
-            b = t;
-        }
-        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-            const int r = i / C, c = i - r * C;
-            const int d = r - (s.n - 1), xn = xn0 + c, x = xn - d;
-            if (x < 0 || x >= s.W) continue;
-            const size_t idx = cell<Acc>(s, band, x, d);
-            // d = 0 has a second copy, row 0 of the "-" half.
-            const size_t dup = ((size_t)band * 2 + 1) * s.n * s.W + x;
-            Acc v = dead;
-            if (x < s.w && xn >= 0 && xn < s.w) {
-                const Acc best = vmax(a[r * C + c], a[(r + L - len) * C + c]);
-                v = (best == dead) ? dead : hv[idx] + best;
-            }
-            hv[idx] = v;
-            if (d == 0) hv[dup] = v;
-        }
-    } else {
-        for (int i = threadIdx.x; i < D * C; i += blockDim.x) {
-            const int r = i / C, c = i - r * C;
-            const int d = r - (s.n - 1), x = xn0 + c - d;
-            if (x < 0 || x >= s.W) continue;
-            hv[cell<Acc>(s, band, x, d)] = dead;
-            if (d == 0) hv[((size_t)band * 2 + 1) * s.n * s.W + x] = dead;
-        }
+__global__ void point_mask_kernel(Acc *hv, Shape s, int band, int xp, int end) {
+    const size_t per_band = (size_t)2 * s.n * s.W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per_band;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % s.W);
+        const int r = (int)(i / s.W);
+        const int sh = r % s.n, sign = r / s.n;
+        const int d = sign ? -sh : sh;
+        if ((end ? x + d : x) != xp) hv[(size_t)band * per_band + i] = Dead<Acc>::value();
     }
 }
 
-// The DP step with the bend-angle windows of the main problem (Sec. 2.3,
-// RangeMaxQ over the range of Eqs. 6-7): V_b(x, d) = H_b(x, d) +
-// max_{lo(d) <= e <= hi(d)} V_{b+1}(x + d, e).  Same tiling as
-// dp_band_tiled_kernel (a block owns C continuation columns xn, and with
-// them the states x = xn - d), but the windows differ in length, so each one
-// is answered as a range-maximum query on a sparse table kept whole in
-// shared memory: level j holds, for every row, the maximum of the 2^j rows
-// from it on, and a window of length L with 2^j <= L < 2^(j+1) is the
+// Band `band` < k-1 of the DP, given V of band+1 already in place (Sec.
+// 2.2-2.3, Eqs. 3-4, RangeMaxQ): V_b(x, d) = H_b(x, d) + max_{lo(d) <= e <=
+// hi(d)} V_{b+1}(x + d, e), dead when x + d leaves the image or every e is
+// dead.  The window table is the integer bend limit |e - d| <= B or the
+// bend-angle range of Eqs. 6-7.  A block owns C continuation columns xn (the
+// grid covers xn in [-(n-1), W + n - 1), so every state (x, d), x in [0, W),
+// has exactly one owner xn = x + d).  The windows differ in length, so each
+// one is answered as a range-maximum query on a sparse table kept whole in
+// shared memory: level j holds, for every displacement, the maximum of the
+// 2^j from it on, and a window of length L with 2^j <= L < 2^(j+1) is the
 // maximum of the level-j runs starting at lo and at hi - 2^j + 1.  Max is
-// exact: the values are those of the scan over the window.
+// exact, so the values are those of the scan over the window, and the one
+// addition per state is the same as the oracle's.
 //
 // A thread owns column c = tid % C and rows r = tid / C + 32 u, u < RPT
 // (32 * RPT >= 2n - 1): its window bounds and H_b values stay in registers,
 // all its loads are issued before the first shared-memory store, and the
-// results leave as plain stores.  `levels` = floor(log2(longest window)) + 1.
-template <int C, int RPT>
+// results leave as plain stores (both copies of d = 0).  `levels` =
+// floor(log2(longest window)) + 1.
+template <typename Acc, int C, int RPT>
 __global__ void __launch_bounds__(32 * C)
-dp_band_angle_kernel(int32_t *hv, Shape s, int band, AngleTable t, int levels) {
-    extern __shared__ __align__(16) int32_t sm[];
+dp_band_window_kernel(Acc *hv, Shape s, int band, WindowTable t, int levels) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Acc *sm = (Acc *)smraw;
     const int D = s.D;
     const int c = threadIdx.x % C, r0 = threadIdx.x / C;
     const int xn0 = (int)blockIdx.x * C - (s.n - 1), xn = xn0 + c;
-    const int32_t dead = Dead<int32_t>::value();
+    const Acc dead = Dead<Acc>::value();
     const size_t dup_row = ((size_t)band * 2 + 1) * s.n * s.W;   // d = 0, "-" half
     if (!(xn0 + C > 0 && xn0 < s.w)) {
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
             if (r >= D || x < 0 || x >= s.W) continue;
-            hv[cell<int32_t>(s, band, x, d)] = dead;
+            hv[cell<Acc>(s, band, x, d)] = dead;
             if (d == 0) hv[dup_row + x] = dead;
         }
         return;
     }
     const bool live_col = xn >= 0 && xn < s.w;
-    int32_t va[RPT], hb[RPT];
+    Acc va[RPT], hb[RPT];
     uint32_t lh[RPT];   // window rows lo | hi << 16
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
         const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
         va[u] = dead;
-        hb[u] = 0;
+        hb[u] = Acc(0);
         lh[u] = 0;
         if (r < D) {
-            if (live_col) va[u] = hv[cell<int32_t>(s, band + 1, xn, d)];
-            if (live_col && x >= 0 && x < s.w) hb[u] = hv[cell<int32_t>(s, band, x, d)];
+            if (live_col) va[u] = hv[cell<Acc>(s, band + 1, xn, d)];
+            if (live_col && x >= 0 && x < s.w) hb[u] = hv[cell<Acc>(s, band, x, d)];
             lh[u] = (uint32_t)(t.lo[r] + s.n - 1) | (uint32_t)(t.hi[r] + s.n - 1) << 16;
         }
     }
@@ -181,8 +142,8 @@ dp_band_angle_kernel(int32_t *hv, Shape s, int band, AngleTable t, int levels) {
     for (int j = 1; j < levels; ++j) {
         __syncthreads();
         const int len = 1 << (j - 1);
-        const int32_t *src = sm + (size_t)(j - 1) * D * C;
-        int32_t *dst = sm + (size_t)j * D * C;
+        const Acc *src = sm + (size_t)(j - 1) * D * C;
+        Acc *dst = sm + (size_t)j * D * C;
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int r = r0 + 32 * u;
@@ -195,15 +156,15 @@ dp_band_angle_kernel(int32_t *hv, Shape s, int band, AngleTable t, int levels) {
     for (int u = 0; u < RPT; ++u) {
         const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
         if (r >= D || x < 0 || x >= s.W) continue;
-        int32_t v = dead;
+        Acc v = dead;
         if (x < s.w && live_col) {
             const int lo = (int)(lh[u] & 0xffffu), hi = (int)(lh[u] >> 16);
             const int j = 31 - __clz(hi - lo + 1);
-            const int32_t *T = sm + (size_t)j * D * C;
-            const int32_t best = vmax(T[lo * C + c], T[(hi - (1 << j) + 1) * C + c]);
+            const Acc *T = sm + (size_t)j * D * C;
+            const Acc best = vmax(T[lo * C + c], T[(hi - (1 << j) + 1) * C + c]);
             v = (best == dead) ? dead : hb[u] + best;
         }
-        hv[cell<int32_t>(s, band, x, d)] = v;
+        hv[cell<Acc>(s, band, x, d)] = v;
         if (d == 0) hv[dup_row + x] = v;
     }
 }
@@ -366,28 +327,10 @@ int grid_for(size_t total) {
 }  // namespace
 
 template <typename Acc>
-int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream) {
-    const size_t per_band = (size_t)2 * s.n * s.W;
-    const int D = 2 * s.n - 1;
-    // A window beyond the displacement range covers all of it.
-    const int Bc = B < D - 1 ? B : D - 1;
-    const int R = D + 2 * Bc;
-    int C = 32;
-    while (C > 1 && (size_t)2 * R * C * sizeof(Acc) > 200 * 1024) C /= 2;
-    const size_t smem = (size_t)2 * R * C * sizeof(Acc);
-    int st = cuda_status(cudaFuncSetAttribute(dp_band_tiled_kernel<Acc>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem),
-                         "cudaFuncSetAttribute");
-    if (st) return st;
-    dp_last_band_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
-    st = launched("dp_last_band_kernel");
-    const int blocks = (s.W + 2 * (s.n - 1) + C - 1) / C;
-    for (int band = s.k - 2; band >= 0 && !st; --band) {
-        dp_band_tiled_kernel<Acc><<<blocks, 512, smem, stream>>>(hv, s, band, Bc, C);
-        st = launched("dp_band_tiled_kernel");
-    }
-    return st;
+int launch_dp_inplace(Acc *hv, const Shape &s, int B, cudaStream_t stream, const PointMask *pm) {
+    WindowTable t;
+    make_bend_table(s.n, B, &t);
+    return launch_dp_window<Acc>(hv, s, t, stream, pm);
 }
 
 template <typename Acc>
@@ -409,16 +352,27 @@ int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long
     return launched("readback_kernel");
 }
 
+void make_bend_table(int n, int B, WindowTable *t) {
+    const int D = 2 * n - 1;
+    for (int i = 0; i < kMaxD; ++i) {
+        const int d = i - (n - 1);
+        t->lo[i] = (int16_t)(i < D ? (d - B > -(n - 1) ? d - B : -(n - 1)) : 0);
+        t->hi[i] = (int16_t)(i < D ? (d + B < n - 1 ? d + B : n - 1) : 0);
+    }
+    t->n = n;
+    t->maxlen = 2 * B + 1 < D ? 2 * B + 1 : D;
+}
+
 namespace {
-template <int C, int RPT>
-int launch_dp_angle_tiles(int32_t *hv, const Shape &s, const AngleTable &t,
-                          cudaStream_t stream) {
+template <typename Acc, int C, int RPT>
+int launch_dp_window_tiles(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t stream,
+                           const std::function<int(int)> &after_band) {
     int levels = 1;
     while ((2 << (levels - 1)) <= t.maxlen) ++levels;   // floor(log2(maxlen)) + 1
-    const size_t smem = (size_t)levels * s.D * C * 4;   // at most 9 * 511 * 8 * 4 = 147 KB
-    static int smem_set = 48 * 1024;                    // dynamic shared memory enabled so far
+    const size_t smem = (size_t)levels * s.D * C * sizeof(Acc);   // <= 9 * 511 * 8 * 4 = 147 KB
+    static int smem_set = 48 * 1024;   // dynamic shared memory enabled so far
     if ((int)smem > smem_set) {
-        int st = cuda_status(cudaFuncSetAttribute(dp_band_angle_kernel<C, RPT>,
+        int st = cuda_status(cudaFuncSetAttribute(dp_band_window_kernel<Acc, C, RPT>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)smem),
                              "cudaFuncSetAttribute");
@@ -428,53 +382,71 @@ int launch_dp_angle_tiles(int32_t *hv, const Shape &s, const AngleTable &t,
     const int blocks = (s.W + 2 * (s.n - 1) + C - 1) / C;
     int st = FHTDP_OK;
     for (int band = s.k - 2; band >= 0 && !st; --band) {
-        dp_band_angle_kernel<C, RPT><<<blocks, 32 * C, smem, stream>>>(hv, s, band, t, levels);
-        st = launched("dp_band_angle_kernel");
+        dp_band_window_kernel<Acc, C, RPT><<<blocks, 32 * C, smem, stream>>>(hv, s, band, t,
+                                                                             levels);
+        st = launched("dp_band_window_kernel");
+        if (!st) st = after_band(band);
     }
     return st;
 }
-
-template <int C>
-int launch_dp_angle_c(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream) {
-    if (s.D <= 32 * 4) return launch_dp_angle_tiles<C, 4>(hv, s, t, stream);
-    if (s.D <= 32 * 8 || C > 8) return launch_dp_angle_tiles<C, 8>(hv, s, t, stream);
-    return launch_dp_angle_tiles<8, 16>(hv, s, t, stream);   // 256-row bands
-}
 }  // namespace
 
-int launch_dp_angle(int32_t *hv, const Shape &s, const AngleTable &t, cudaStream_t stream) {
+template <typename Acc>
+int launch_dp_window(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t stream,
+                     const PointMask *pm) {
     const size_t per_band = (size_t)2 * s.n * s.W;
-    dp_last_band_kernel<int32_t><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
+    // The point's band: j (its upper border), or k-1 for the image's bottom
+    // border, masked right after the band is formed.
+    const std::function<int(int)> mask = [&](int band) -> int {
+        if (!pm || band != (pm->j < s.k ? pm->j : s.k - 1)) return FHTDP_OK;
+        point_mask_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s, band, pm->xp,
+                                                                       pm->j == s.k ? 1 : 0);
+        return launched("point_mask_kernel");
+    };
+    dp_last_band_kernel<Acc><<<grid_for(per_band), 256, 0, stream>>>(hv, s);
     int st = launched("dp_last_band_kernel");
-    if (st) return st;
+    if (!st) st = mask(s.k - 1);
+    if (st || s.k == 1) return st;
     // 16 continuation columns per block (64-byte row segments) while that
-    // still gives two blocks per SM, else 8.
+    // still gives two blocks per SM, else 8; 32 * RPT >= 2n - 1 rows.
     const int span = s.W + 2 * (s.n - 1);
-    if ((span + 15) / 16 >= 2 * 152 && s.D <= 32 * 8) return launch_dp_angle_c<16>(hv, s, t, stream);
-    return launch_dp_angle_c<8>(hv, s, t, stream);
+    const bool wide = (span + 15) / 16 >= 2 * 152 && s.D <= 32 * 8;
+    if (s.D <= 32 * 4)
+        return wide ? launch_dp_window_tiles<Acc, 16, 4>(hv, s, t, stream, mask)
+                    : launch_dp_window_tiles<Acc, 8, 4>(hv, s, t, stream, mask);
+    if (s.D <= 32 * 8)
+        return wide ? launch_dp_window_tiles<Acc, 16, 8>(hv, s, t, stream, mask)
+                    : launch_dp_window_tiles<Acc, 8, 8>(hv, s, t, stream, mask);
+    return launch_dp_window_tiles<Acc, 8, 16>(hv, s, t, stream, mask);   // 256-row bands
 }
 
-int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const AngleTable &t,
+int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const WindowTable &t,
                                unsigned long long *key, int32_t *x_out, int32_t *d_out,
                                int32_t *score_out, cudaStream_t stream) {
     argmax_kernel<int32_t><<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key);
     int st = launched("argmax_kernel");
     if (st) return st;
-    readback_kernel<int32_t, AngleWin><<<1, 32, 0, stream>>>(V, s, AngleWin{t}, key, x_out,
+    readback_kernel<int32_t, TableWin><<<1, 32, 0, stream>>>(V, s, TableWin{t}, key, x_out,
                                                              d_out, score_out);
     return launched("readback_kernel");
 }
 
-int launch_backtrack_angle(const int32_t *V, const Shape &s, const AngleTable &t,
+int launch_backtrack_angle(const int32_t *V, const Shape &s, const WindowTable &t,
                            int32_t *x_out, int32_t *d_out, int32_t *score_out,
                            cudaStream_t stream) {
-    backtrack_kernel<int32_t, AngleWin><<<1, 1024, 0, stream>>>(V, s, AngleWin{t}, x_out,
+    backtrack_kernel<int32_t, TableWin><<<1, 1024, 0, stream>>>(V, s, TableWin{t}, x_out,
                                                                 d_out, score_out);
     return launched("backtrack_kernel");
 }
 
-template int launch_dp_inplace<int32_t>(int32_t *, const Shape &, int, cudaStream_t);
-template int launch_dp_inplace<float>(float *, const Shape &, int, cudaStream_t);
+template int launch_dp_window<int32_t>(int32_t *, const Shape &, const WindowTable &,
+                                       cudaStream_t, const PointMask *);
+template int launch_dp_window<float>(float *, const Shape &, const WindowTable &, cudaStream_t,
+                                     const PointMask *);
+template int launch_dp_inplace<int32_t>(int32_t *, const Shape &, int, cudaStream_t,
+                                        const PointMask *);
+template int launch_dp_inplace<float>(float *, const Shape &, int, cudaStream_t,
+                                      const PointMask *);
 template int launch_backtrack_key<int32_t>(const int32_t *, const Shape &, int,
                                            unsigned long long *, int32_t *, int32_t *, int32_t *,
                                            cudaStream_t);

@@ -128,3 +128,19 @@ def test_angle_entries_reject_bad_arguments_before_launch(lib):
     assert L.fhtdp_polyline_dp_angle(None, 0, 64, 10, 4, 0.3, None) == 1
     assert L.fhtdp_polyline_dp_angle(fake, 0, 96, 10, 1, 0.3, None) == 1
     assert L.fhtdp_backtrack_angle(fake, 0, 64, 10, 4, 0.3, None, fake, fake, None) == 1
+
+
+def test_through_point_rejects_bad_arguments_before_launch(lib):
+    L = lib.lib()
+    fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
+    assert L.fhtdp_through_workspace_bytes(0, 64, 10, 4) > 0
+    assert L.fhtdp_through_workspace_bytes(2, 64, 10, 4) == 0       # float images
+    outs = (fake, fake, fake, fake, 1 << 30, None)
+    for j, xp in ((5, 0), (-1, 0), (1, 10), (1, -1)):
+        assert L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, 2, j, xp, *outs) == 1
+    assert L.fhtdp_detect_through_point(fake, 2, 64, 10, 10, 4, 2, 1, 1, *outs) == 1
+    assert L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, -1, 1, 1, *outs) == 1
+    assert L.fhtdp_detect_through_point(None, 0, 64, 10, 10, 4, 2, 1, 1, *outs) == 1
+    r = L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, 2, 1, 1, fake, fake, fake, fake,
+                                     64, None)
+    assert r == 2 and "workspace" in L.fhtdp_last_error().decode()

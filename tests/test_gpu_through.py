@@ -1,0 +1,86 @@
+"""GPU parity of the through-point query (Subproblems 2-3, Sec. 2.2-2.3):
+the best polyline through a given point on a band border, through the C ABI,
+against the CPU oracle on the same seeded inputs (int32, bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_01884_gb300 import synth
+from helpers import check_path, to_device
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(256, 256, 4), (64, 37, 4), (128, 1000, 1), (512, 300, 2), (16, 5, 16),
+          (8, 3, 4), (2048, 130, 16), (96, 77, 3), (32, 1, 2), (1024, 517, 4)]
+
+
+def _img(h, w, dtype, seed):
+    rng = np.random.default_rng(seed)
+    if dtype == "u8":
+        return rng.integers(0, 256, (h, w)).astype(np.uint8)
+    return rng.integers(-3000, 3000, (h, w)).astype(np.int32)
+
+
+def _through(lib, img, k, B, j, xp):
+    x, d, s = lib.detect_through_point(to_device(img), k, B, j, xp)
+    return x.cpu().numpy(), d.cpu().numpy(), int(s.cpu().numpy()[0])
+
+
+def _assert_parity(lib, img, k, B, j, xp):
+    x, d, s = _through(lib, img, k, B, j, xp)
+    xo, do, so = oracle.detect_through(img, k, B, j, xp)
+    assert list(x) == list(xo) and list(d) == list(do), (B, j, xp)
+    assert s == so
+    assert x[j] == xp
+    check_path(img, k, B, x, d)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "i32"])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("B", [0, 3, 1000])
+def test_through_point_matches_oracle(lib, shape, dtype, B):
+    h, w, k = shape
+    img = _img(h, w, dtype, h * 5 + w + B)
+    for j in sorted({0, k // 2, k}):
+        for xp in sorted({0, w // 3, w - 1}):
+            _assert_parity(lib, img, k, B, j, xp)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_through_point_2048x2048_k16_B16_full_size(lib, seed):
+    """The benchmark's image and query: the point on border 8 at a planted
+    polyline's vertex, and at a random column."""
+    wl = synth.plain_gaussian(seed)
+    xs, _ = wl.planted[0]
+    _assert_parity(lib, wl.img, 16, 16, 8, int(xs[8]))
+    _assert_parity(lib, wl.img, 16, 16, 8, 1000 + 37 * seed)
+
+
+def test_through_the_global_optimum_is_the_global_optimum(lib):
+    wl = synth.plain_uniform(11, 512, 384, 8, 4)
+    gx, gd, gs = lib.detect_polyline(to_device(wl.img), 8, 4)
+    gx = gx.cpu().numpy()
+    for j in range(9):
+        x, d, s = _through(lib, wl.img, 8, 4, j, int(gx[j]))
+        assert list(x) == list(gx) and s == int(gs.cpu().numpy()[0])
+
+
+def test_through_point_reuses_its_workspace(lib):
+    import torch
+    img = _img(256, 300, "u8", 9)
+    need = lib.through_workspace_bytes(lib.DTYPE_U8, 256, 300, 4)
+    ws = torch.full((need,), 0x5A, dtype=torch.uint8, device="cuda")
+    for j, xp in ((1, 17), (3, 250), (1, 17)):
+        x, d, s = lib.detect_through_point(to_device(img), 4, 5, j, xp, ws=ws)
+        xo, do, so = oracle.detect_through(img, 4, 5, j, xp)
+        assert list(x.cpu().numpy()) == list(xo) and int(s.cpu().numpy()[0]) == so
+
+
+def test_through_point_rejects_bad_arguments_on_device(lib):
+    import torch
+    img = torch.zeros((64, 40), dtype=torch.uint8, device="cuda")
+    for args in ((4, 2, 5, 0), (4, 2, -1, 0), (4, 2, 1, 40), (4, 2, 1, -1), (4, -1, 1, 3)):
+        with pytest.raises(lib.FhtdpError):
+            lib.detect_through_point(img, *args)
+    with pytest.raises(TypeError):
+        lib.detect_through_point(img.float(), 4, 2, 1, 3)
