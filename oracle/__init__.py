@@ -25,6 +25,9 @@ Function map (paper passages in the C file's comments):
   dp_through / detect_through / brute_through
                    Sec. 2.2-2.3 Subproblems 2-3: the extreme polyline through a
                    given point on a band border
+  detect_two / brute_apart
+                   Sec. 3: two different extreme polylines (suppression on x_0)
+  detect_horizontal  Sec. 3, Fig. 7: mostly horizontal polylines (transposition)
 """
 from __future__ import annotations
 
@@ -115,6 +118,11 @@ def _load():
                                                      + [_I32P, _I32P,
                                                         ctypes.POINTER(ctypes.c_long)])
             lib.oracle_brute_through_f64.restype = ctypes.c_double
+            lib.oracle_detect_two_f64.argtypes = ([_F64P] + [ctypes.c_int] * 5
+                                                  + [_I32P, _I32P, _F64P])
+            lib.oracle_brute_apart_f64.argtypes = ([_F64P] + [ctypes.c_int] * 6
+                                                   + [_I32P, _I32P])
+            lib.oracle_brute_apart_f64.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -387,3 +395,37 @@ def brute_through(img, k: int, B: int, j: int, xp: int):
                                          int(xp), _p(xs, ctypes.c_int32),
                                          _p(ds, ctypes.c_int32), ctypes.byref(visited))
     return xs, ds, s, visited.value
+
+
+def detect_two(img, k: int, B: int, sep: int):
+    """The optimum and the best polyline whose top vertex is at least `sep`
+    columns from the optimum's: (x[2][k+1], d[2][k], scores[2])."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros((2, k + 1), dtype=np.int32)
+    ds = np.zeros((2, k), dtype=np.int32)
+    sc = np.zeros(2, dtype=np.float64)
+    if _load().oracle_detect_two_f64(_p(img, ctypes.c_double), h, w, k, B, int(sep),
+                                     _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32),
+                                     _p(sc, ctypes.c_double)):
+        raise ValueError("bad shape, bend or separation")
+    return xs, ds, sc
+
+
+def brute_apart(img, k: int, B: int, x0: int, sep: int):
+    """Brute force: the best admissible polyline with |x_0 - x0| >= sep."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_brute_apart_f64(_p(img, ctypes.c_double), h, w, k, B, int(x0), int(sep),
+                                       _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def detect_horizontal(img, k: int, B: int):
+    """Mostly horizontal polylines (Fig. 7): the method on the transposed
+    image, whose bands are the image's vertical strips of w/k columns.
+    Returns (y[k+1], d[k], score): y_i is the row of the polyline on the
+    first column of strip i, d_i = y_{i+1} - y_i."""
+    return detect(np.ascontiguousarray(np.asarray(img).T), k, B)

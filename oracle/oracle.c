@@ -804,3 +804,69 @@ double oracle_brute_through_f64(const double *img, int h, int w, int k, int B, i
     }
     return st.best;
 }
+
+/* ---------------------------------------------------------------------------
+ * Two different extreme polylines (Sec. 3, Figs. 6d and 7a; the paper does
+ * not state the rule).  Reading: the first is the optimum; the second is the
+ * best polyline whose top vertex x_0 lies at least `sep` columns from the
+ * first's (non-maximum suppression on x_0), the lexicographically smallest
+ * among its optima.  Both come from the same V: the second is the argmax of
+ * V_0 over the columns |x - x_0| >= sep, read back as in Eq. 5.
+ * xs: [2][k+1], ds: [2][k], scores: [2] (second: -inf and x = -1 when every
+ * column is suppressed).
+ * ------------------------------------------------------------------------ */
+int oracle_detect_two_f64(const double *img, int h, int w, int k, int B, int sep, int32_t *xs,
+                          int32_t *ds, double *scores) {
+    if (k < 1 || h % k != 0 || B < 0 || sep < 1) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * D * w);
+    double *V2 = (double *)malloc(sizeof(double) * (size_t)k * D * w);
+    if (!H || !V || !V2) {
+        free(H);
+        free(V);
+        free(V2);
+        return -1;
+    }
+    oracle_fht_recursive_f64(img, h, w, k, H);
+    oracle_dp_f64(H, h, w, k, B, V);
+    scores[0] = oracle_backtrack_f64(V, h, w, k, B, xs, ds);
+    /* the second: the same V with the suppressed top columns dead */
+    memcpy(V2, V, sizeof(double) * (size_t)k * D * w);
+    int x0 = xs[0];
+    for (int d = 0; d < D; ++d)
+        for (int x = 0; x < w; ++x)
+            if (x0 >= 0 && abs(x - x0) < sep) V2[(size_t)d * w + x] = ORACLE_NEG;
+    scores[1] = oracle_backtrack_f64(V2, h, w, k, B, xs + k + 1, ds + k);
+    free(H);
+    free(V);
+    free(V2);
+    return 0;
+}
+
+/* Brute force over every admissible polyline whose top vertex is at least
+ * sep columns from x0 (tiny images): the best of the brute-force optima
+ * through each allowed start column, taken in increasing column order. */
+double oracle_brute_apart_f64(const double *img, int h, int w, int k, int B, int x0, int sep,
+                              int32_t *xs, int32_t *ds) {
+    double best = ORACLE_NEG;
+    int32_t *bx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(k + 1));
+    int32_t *bd = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    for (int i = 0; i <= k; ++i) xs[i] = -1;
+    for (int i = 0; i < k; ++i) ds[i] = 0;
+    for (int s0 = 0; s0 < w; ++s0) {
+        if (abs(s0 - x0) < sep) continue;
+        long visited = 0;
+        double s = oracle_brute_through_f64(img, h, w, k, B, 0, s0, bx, bd, &visited);
+        if (s > best) {
+            best = s;
+            for (int i = 0; i <= k; ++i) xs[i] = bx[i];
+            for (int i = 0; i < k; ++i) ds[i] = bd[i];
+        }
+    }
+    free(bx);
+    free(bd);
+    return best;
+}
