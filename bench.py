@@ -3,7 +3,8 @@
 read-back) in Mpix/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload plain2048|mixed|float8192|plain256|angle2048|through2048]
+                    [--workload plain2048|mixed|float8192|plain256|angle2048|through2048|
+                                horizontal2048|two2048]
                     [--images I]
 
 Default workload: synthetic 2048x2048 uint8 images, k=16 bands of 128 rows,
@@ -53,6 +54,14 @@ WORKLOADS = {
         desc="Subproblem 3: u8 2048x2048 (the plain2048 images), k=16 bands of 128 rows, bend 16, "
              "the best polyline through one point per image on band border 8",
         images=32, dtype="u8"),
+    "horizontal2048": dict(
+        desc="mostly horizontal curves: u8 2048x2048 (the plain2048 images transposed), k=16 "
+             "vertical strips of 128 columns, bend 16 (transposition + the fused engine, one "
+             "image per call)", images=32, dtype="u8"),
+    "two2048": dict(
+        desc="two different extreme polylines: u8 2048x2048 (the plain2048 images), k=16, "
+             "bend 16, the second polyline's top vertex at least 64 columns from the first's",
+        images=32, dtype="u8"),
     "learned1024": dict(
         desc="u8 1024x1024 lanes over textured noise, k=16 bands of 64 rows, bend 12: learned "
              "window proposal (4-layer 32-channel bf16 CNN on the 4x downsample, windows of 16) "
@@ -80,6 +89,8 @@ ANGLE_GAMMA = 0.17453292519943295   # 10 degrees in radians
 # The through-point workload's query: border 8 of 16, at the first planted
 # polyline's vertex there.
 THROUGH_BORDER = 8
+# The two-polyline workload's suppression radius on the top vertex.
+TWO_SEPARATION = 64
 
 
 def through_column(wl):
@@ -191,6 +202,7 @@ def max_over_ranks(value, dist, device):
 
 def make_workload(name, images, seed, rank):
     """[(img, k, B)] of one rank."""
+    import numpy as np
     from paper_1912_01884_gb300 import synth
     seeds = image_seeds(images, seed, rank)
     if name == "plain2048":
@@ -201,6 +213,12 @@ def make_workload(name, images, seed, rank):
         return [(w.img, w.k, w.B) for w in (synth.ridge_response(s) for s in seeds)]
     if name == "angle2048":
         return [(w.img, w.k, None) for w in (synth.bent_edges(s) for s in seeds)]
+    if name == "horizontal2048":
+        return [(np.ascontiguousarray(w.img.T), w.k, w.B)
+                for w in (synth.plain_gaussian(s) for s in seeds)]
+    if name == "two2048":
+        return [(w.img, w.k, ("two", w.B, TWO_SEPARATION))
+                for w in (synth.plain_gaussian(s) for s in seeds)]
     if name == "through2048":
         return [(w.img, w.k, (w.B, THROUGH_BORDER, through_column(w)))
                 for w in (synth.plain_gaussian(s) for s in seeds)]
@@ -218,6 +236,8 @@ def oracle_rate(items, budget_s):
     for img, k, B in items:
         if B is None:
             oracle.detect_angle(img, k, ANGLE_R, ANGLE_GAMMA)
+        elif isinstance(B, tuple) and B[0] == "two":
+            oracle.detect_two(img, k, B[1], B[2])
         elif isinstance(B, tuple):
             oracle.detect_through(img, k, *B)
         elif img.dtype == np.float32:
@@ -489,8 +509,17 @@ def run_standalone(args):
     xs = torch.empty((I, k + 1), dtype=torch.int32, device=dev)
     ds = torch.empty((I, k), dtype=torch.int32, device=dev)
     sc = torch.empty((I, 1), dtype=torch.int32, device=dev)
-    need = (fd.angle_workspace_bytes(fd.DTYPE_U8, h, w, k, ANGLE_R) if angle
-            else fd.through_workspace_bytes(fd.DTYPE_U8, h, w, k))
+    if angle:
+        need = fd.angle_workspace_bytes(fd.DTYPE_U8, h, w, k, ANGLE_R)
+    elif name == "horizontal2048":
+        need = fd.horizontal_workspace_bytes(fd.DTYPE_U8, h, w, k, items[0][2])
+    else:
+        need = fd.through_workspace_bytes(fd.DTYPE_U8, h, w, k)
+    two = name == "two2048"
+    if two:   # two polylines per image
+        xs2 = torch.empty((I, 2, k + 1), dtype=torch.int32, device=dev)
+        ds2 = torch.empty((I, 2, k), dtype=torch.int32, device=dev)
+        sc2 = torch.empty((I, 2), dtype=torch.int32, device=dev)
     lanes = min(args.lanes or ANGLE_LANES, I)
     wss = [torch.empty(need, dtype=torch.uint8, device=dev) for _ in range(lanes)]
     main = torch.cuda.Stream(dev)      # graphs are captured off the default stream
@@ -506,6 +535,14 @@ def run_standalone(args):
                     fd.detect_polyline_angle(src[j], k, ANGLE_R, ANGLE_GAMMA,
                                              out=(xs[j], ds[j], sc[j]), ws=wss[ln],
                                              stream=side[ln])
+                elif name == "horizontal2048":
+                    fd.detect_polyline_horizontal(src[j], k, items[j][2],
+                                                  out=(xs[j], ds[j], sc[j]), ws=wss[ln],
+                                                  stream=side[ln])
+                elif two:
+                    fd.detect_two_polylines(src[j], k, items[j][2][1], items[j][2][2],
+                                            out=(xs2[j], ds2[j], sc2[j]), ws=wss[ln],
+                                            stream=side[ln])
                 else:
                     B, jb, xp = items[j][2]
                     fd.detect_through_point(src[j], k, B, jb, xp, out=(xs[j], ds[j], sc[j]),
@@ -547,9 +584,10 @@ def run_standalone(args):
     # End to end: each step copies its images from pinned host memory, runs
     # the graph on them and reads every result back, all inside the timed
     # region (copies on the main stream, ordered before the graph).
-    hx = torch.empty_like(xs, device="cpu").pin_memory()
-    hd = torch.empty_like(ds, device="cpu").pin_memory()
-    hs = torch.empty_like(sc, device="cpu").pin_memory()
+    rx, rd, rs = (xs2, ds2, sc2) if two else (xs, ds, sc)
+    hx = torch.empty_like(rx, device="cpu").pin_memory()
+    hd = torch.empty_like(rd, device="cpu").pin_memory()
+    hs = torch.empty_like(rs, device="cpu").pin_memory()
 
     def e2e_run(nsteps):
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -557,9 +595,9 @@ def run_standalone(args):
         for _ in range(nsteps):
             imgs.copy_(host, non_blocking=True)
             graph.replay()
-            hx.copy_(xs, non_blocking=True)
-            hd.copy_(ds, non_blocking=True)
-            hs.copy_(sc, non_blocking=True)
+            hx.copy_(rx, non_blocking=True)
+            hd.copy_(rd, non_blocking=True)
+            hs.copy_(rs, non_blocking=True)
         t1.record(main)
         main.synchronize()
         return t0.elapsed_time(t1) / 1e3
@@ -584,8 +622,21 @@ def run_standalone(args):
             "backtrack": lambda: fd.backtrack_angle(hough, h, w, k, ANGLE_GAMMA, out=one,
                                                     stream=main),
         }
+    elif name == "horizontal2048":
+        B0 = items[0][2]
+        ws_e = torch.empty(fd.workspace_bytes(fd.DTYPE_U8, w, h, k, B0), dtype=torch.uint8,
+                           device=dev)
+        # the transposed image a horizontal call leaves at the start of its
+        # workspace (row pitch h rounded up to 64)
+        tp = (h + 63) // 64 * 64
+        tr = wss[0][:w * tp].view(w, tp)[:, :h]
+        stages = {
+            "horizontal": lambda: fd.detect_polyline_horizontal(imgs[0], k, B0, out=one,
+                                                                ws=wss[0], stream=main),
+            "engine": lambda: fd.detect_polyline(tr, k, B0, out=one, ws=ws_e, stream=main),
+        }
     else:
-        B0 = items[0][2][0]
+        B0 = items[0][2][1] if two else items[0][2][0]
         stages = {
             "fht_bands": lambda: fd.fht_bands(imgs[0], k, out=hough, ws=ws_tmp, stream=main),
             "dp": lambda: fd.polyline_dp(hough, h, w, k, B0, stream=main),
@@ -611,11 +662,13 @@ def run_standalone(args):
         "dp_angle": (k - 1) * 3 * D * w * 4,
         "dp": (k - 1) * 3 * D * w * 4,
         "backtrack": D * w * 4,
+        "horizontal": algorithmic_bytes(w, h, k, 1) + 2 * h * w,
+        "engine": algorithmic_bytes(w, h, k, 1),
     }
     # The roofline kernel is the DP (the largest share of the launch list);
     # "backtrack" here is the standalone one-block read-back, not the argmax
     # + one-warp read-back that the detection calls run.
-    top = "dp_angle" if angle else "dp"
+    top = "dp_angle" if angle else ("engine" if name == "horizontal2048" else "dp")
     hbm, peak_kind = peaks()
     achieved = stage_bytes[top] / (stage_ms[top] / 1e3) / 1e9
 
@@ -629,6 +682,8 @@ def run_standalone(args):
                        "pixels_per_step": pix_rank, "parallelism": "images sharded over ranks",
                        "lanes": lanes,
                        **({"r": ANGLE_R, "gamma_rad": ANGLE_GAMMA} if angle else
+                          {"B": items[0][2]} if name == "horizontal2048" else
+                          {"B": items[0][2][1], "separation": TWO_SEPARATION} if two else
                           {"B": items[0][2][0], "border": THROUGH_BORDER}),
                        "l2": "inputs %d MB per step %s 129 MB L2, no flush"
                              % (host.numel() // 2**20, ">" if host.numel() > 129e6 else "<")},
@@ -637,9 +692,10 @@ def run_standalone(args):
                          "traffic": NCU_TRAFFIC_DP_ANGLE_LAUNCH * (k - 1)
                                     if angle and (h, w, k) == (2048, 2048, 16) else None,
                          "peak_kind": peak_kind,
-                         "kernel": "%s (the k-1 band launches of one image and the last-band "
-                                   "kernel, timed together)"
-                                   % ("dp_band_angle_kernel" if angle else "dp_band_tiled_kernel")},
+                         "kernel": ("engine_kernel_u8 (one image per launch, the transposed "
+                                    "image)" if top == "engine" else
+                                    "dp_band_window_kernel (the k-1 band launches of one image "
+                                    "and the last-band kernel, timed together)")},
             "stages_ms_one_image": stage_ms,
             "pipeline_frac_of_hbm": sum(algorithmic_bytes(h, w, k, 1) for _ in range(I))
                                     / (total_s / args.steps) / 1e9 / hbm,
@@ -740,7 +796,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("angle2048", "through2048"):
+    elif args.workload in ("angle2048", "through2048", "horizontal2048", "two2048"):
         run_standalone(args)
     elif args.workload == "learned1024":
         run_learned(args)

@@ -226,6 +226,39 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
                                void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Two different extreme polylines (Sec. 3, Figs. 6d and 7a, where the paper
+ * shows two and states no rule).  The first is the optimum of
+ * fhtdp_detect_polyline; the second is the best admissible polyline whose top
+ * vertex x_0 lies at least sep (>= 1) columns from the first's (suppression
+ * on x_0), the lexicographically smallest among its optima.  When no column
+ * is far enough, the second has x = -1 everywhere and score INT32_MIN.
+ *   dtype  FHTDP_U8 or FHTDP_I32.
+ *   x_out [2][k+1], d_out [2][k], score_out [2] int32 (device).
+ *   ws     device workspace of at least fhtdp_two_workspace_bytes() bytes.
+ * ---------------------------------------------------------------------- */
+size_t fhtdp_two_workspace_bytes(int dtype, int h, int w, int k);
+int fhtdp_detect_two_polylines(const void *img, int dtype, int h, int w, int pitch, int k, int B,
+                               int sep, int32_t *x_out, int32_t *d_out, void *score_out,
+                               void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Mostly horizontal curves (Sec. 3, Fig. 7): the method on the transposed
+ * image.  The bands are the image's k vertical strips of n = w/k columns (n a
+ * power of two, 1 <= n <= 256); link i joins row y_i on the strip's first
+ * column to row y_{i+1} = y_i + d_i on its last column, |d_i| <= n-1, every
+ * y_i in [0, h).  The image is transposed into the workspace and run through
+ * the fused engine, so results, ties and errors are those of
+ * fhtdp_detect_polyline on the transposed image (dtype any of the three).
+ *   y_out [k+1], d_out [k], score_out [1] (device).
+ *   ws     device workspace of at least fhtdp_horizontal_workspace_bytes();
+ *          fhtdp_workspace_status is not available for these calls.
+ * ---------------------------------------------------------------------- */
+size_t fhtdp_horizontal_workspace_bytes(int dtype, int h, int w, int k, int B);
+int fhtdp_detect_polyline_horizontal(const void *img, int dtype, int h, int w, int pitch, int k,
+                                     int B, int32_t *y_out, int32_t *d_out, void *score_out,
+                                     void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Learned window proposal (no counterpart in the paper): a 4-layer,
  * 32-channel 3x3 CNN on the 4x4-downsampled image predicts, for each band, a
  * bin of 4 displacements; the DP then searches only a window around it

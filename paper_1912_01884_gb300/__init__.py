@@ -88,6 +88,13 @@ _SIGS = {
     "fhtdp_through_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
     "fhtdp_detect_through_point": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 8
                                    + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_two_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
+    "fhtdp_detect_two_polylines": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 7
+                                   + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_horizontal_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 5),
+    "fhtdp_detect_polyline_horizontal": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
+                                         + [ctypes.c_void_p] * 4
+                                         + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_cnn_downsample4": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 3
                               + [ctypes.c_void_p, ctypes.c_void_p]),
     "fhtdp_cnn_conv3x3": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
@@ -442,3 +449,52 @@ def detect_through_point(img, k: int, B: int, j: int, xp: int, out=None, ws=None
                                             score.data_ptr(), ws.data_ptr(), ws.numel(),
                                             _stream(stream)))
     return x, d, score
+
+
+# ---------------------------------------------------------------------------
+# Two different extreme polylines; mostly horizontal curves.
+
+def detect_two_polylines(img, k: int, B: int, sep: int, out=None, ws=None, stream=None):
+    """The optimum and the best polyline whose top vertex is at least `sep`
+    columns from it (uint8 or int32 image): x [2, k+1], d [2, k], score [2]."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _int_image_code(img)
+    need = lib().fhtdp_two_workspace_bytes(code, h, w, k)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_two_polylines(None, code, h, w, pitch, k, B, sep, None, None,
+                                                None, None, 0, _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    if out is None:
+        out = (torch.empty((2, k + 1), dtype=torch.int32, device=img.device),
+               torch.empty((2, k), dtype=torch.int32, device=img.device),
+               torch.empty(2, dtype=torch.int32, device=img.device))
+    x, d, score = out
+    _check(lib().fhtdp_detect_two_polylines(img.data_ptr(), code, h, w, pitch, k, B, int(sep),
+                                            x.data_ptr(), d.data_ptr(), score.data_ptr(),
+                                            ws.data_ptr(), ws.numel(), _stream(stream)))
+    return x, d, score
+
+
+def horizontal_workspace_bytes(dtype: int, h: int, w: int, k: int, B: int) -> int:
+    return lib().fhtdp_horizontal_workspace_bytes(dtype, h, w, k, B)
+
+
+def detect_polyline_horizontal(img, k: int, B: int, out=None, ws=None, stream=None):
+    """Mostly horizontal polyline over k vertical strips of w/k columns:
+    (y[k+1], d[k], score[1])."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _dtype_code(img)
+    need = horizontal_workspace_bytes(code, h, w, k, B)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_polyline_horizontal(None, code, h, w, pitch, k, B, None, None,
+                                                      None, None, 0, _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    y, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_polyline_horizontal(img.data_ptr(), code, h, w, pitch, k, B,
+                                                  y.data_ptr(), d.data_ptr(), score.data_ptr(),
+                                                  ws.data_ptr(), ws.numel(), _stream(stream)))
+    return y, d, score

@@ -307,6 +307,90 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
 }
 
 // ---------------------------------------------------------------------------
+// Two different extreme polylines (Sec. 3, Figs. 6d and 7a).
+size_t fhtdp_two_workspace_bytes(int dtype, int h, int w, int k) {
+    return fhtdp_through_workspace_bytes(dtype, h, w, k);
+}
+
+int fhtdp_detect_two_polylines(const void *img, int dtype, int h, int w, int pitch, int k, int B,
+                               int sep, int32_t *x_out, int32_t *d_out, void *score_out,
+                               void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
+        return set_error(FHTDP_EINVAL, "the two-polyline query takes integer images (dtype %d)",
+                         dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (sep < 1) return set_error(FHTDP_EINVAL, "separation %d < 1", sep);
+    if (!img || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    size_t need = through_workspace_bytes(s);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    return detect_two(img, dtype, pitch, s, B, sep, x_out, d_out, (int32_t *)score_out, ws,
+                      stream);
+}
+
+// ---------------------------------------------------------------------------
+// Mostly horizontal curves (Sec. 3, Fig. 7): the image transposed into the
+// workspace, then the fused engine.
+namespace {
+int transposed_pitch(int h) { return (h + 63) / 64 * 64; }
+size_t transposed_bytes(int dtype, int h, int w) {
+    const size_t b = (size_t)w * transposed_pitch(h) * (dtype == FHTDP_U8 ? 1 : 4);
+    return (b + 255) & ~(size_t)255;
+}
+}  // namespace
+
+size_t fhtdp_horizontal_workspace_bytes(int dtype, int h, int w, int k, int B) {
+    Shape s;
+    if (!valid_dtype(dtype) || !make_shape(w, h, k, &s) || B < 0) return 0;
+    return transposed_bytes(dtype, h, w) + engine_workspace_bytes(dtype, s, B);
+}
+
+int fhtdp_detect_polyline_horizontal(const void *img, int dtype, int h, int w, int pitch, int k,
+                                     int B, int32_t *y_out, int32_t *d_out, void *score_out,
+                                     void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    if (!make_shape(w, h, k, &s))
+        return set_error(FHTDP_EINVAL,
+                         "invalid shape h=%d w=%d k=%d: horizontal bands need w = k*n with n a "
+                         "power of two in [1, 256], 1 <= h <= 2^20, w <= 2^20",
+                         h, w, k);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (!img || !y_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    const size_t tb = transposed_bytes(dtype, h, w);
+    const size_t need = tb + engine_workspace_bytes(dtype, s, B);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    const int tp = transposed_pitch(h);
+    int st;
+    switch (dtype) {
+        case FHTDP_U8:
+            st = launch_transpose<uint8_t>((const uint8_t *)img, h, w, pitch, (uint8_t *)ws, tp,
+                                           stream);
+            break;
+        case FHTDP_I32:
+            st = launch_transpose<int32_t>((const int32_t *)img, h, w, pitch, (int32_t *)ws, tp,
+                                           stream);
+            break;
+        default:
+            st = launch_transpose<float>((const float *)img, h, w, pitch, (float *)ws, tp, stream);
+    }
+    if (st) return st;
+    return engine_detect(ws, dtype, tp, s, B, y_out, d_out, score_out, (char *)ws + tb,
+                         ws_bytes - tb, stream);
+}
+
+// ---------------------------------------------------------------------------
 // Learned window proposal.
 int fhtdp_cnn_downsample4(const uint8_t *img, int n, int h, int w, void *out,
                           cudaStream_t stream) {

@@ -99,6 +99,22 @@ int launch_backtrack_angle(const int32_t *V, const Shape &s, const WindowTable &
                            cudaStream_t stream);
 size_t angle_workspace_bytes(const Shape &s);
 size_t through_workspace_bytes(const Shape &s);
+// Two different extreme polylines: the optimum and the best one whose top
+// vertex is at least sep columns from the optimum's (outputs [2][...]).
+int detect_two(const void *img, int dtype, int pitch, const Shape &s, int B, int sep,
+               int32_t *x_out, int32_t *d_out, int32_t *score_out, void *ws,
+               cudaStream_t stream);
+// The argmax of V_0 over the columns at least sep from the top vertex that
+// key1 encodes (nothing when key1 is 0), into *key2 (zero before the call).
+int launch_argmax_apart(const int32_t *V, const Shape &s, const unsigned long long *key1,
+                        int sep, unsigned long long *key2, cudaStream_t stream);
+// The read-back from an argmax key with the integer bend limit.
+int launch_readback_key(const int32_t *V, const Shape &s, int B, const unsigned long long *key,
+                        int32_t *x_out, int32_t *d_out, int32_t *score_out, cudaStream_t stream);
+// dst[x][y] = src[y][x] (Sec. 3, Fig. 7: mostly horizontal curves).
+template <typename T>
+int launch_transpose(const T *src, int h, int w, int pitch, T *dst, int dpitch,
+                     cudaStream_t stream);
 int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
                    const PointMask &pm, int32_t *x_out, int32_t *d_out, int32_t *score_out,
                    void *ws, cudaStream_t stream);

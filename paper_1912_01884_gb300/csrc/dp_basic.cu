@@ -209,6 +209,31 @@ __global__ void argmax_kernel(const Acc *V, Shape s, unsigned long long *key) {
     if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
 }
 
+// The second of two different extreme polylines: as argmax_kernel over the
+// columns x with |x - x_0| >= sep, x_0 the top vertex of the optimum in key1.
+__global__ void argmax_apart_kernel(const int32_t *V, Shape s, const unsigned long long *key1,
+                                    int sep, unsigned long long *key2) {
+    const unsigned long long k1 = *key1;
+    if (k1 == 0) return;
+    const int x0 = (int)((0xffffffffu - (unsigned)(k1 & 0xffffffffu)) / s.D);
+    unsigned long long best = 0;
+    const int total = s.w * s.D;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i / s.w, x = i - e * s.w;
+        if (abs(x - x0) < sep) continue;
+        const int32_t v = V[cell<int32_t>(s, 0, x, e - (s.n - 1))];
+        if (v == Dead<int32_t>::value()) continue;
+        const unsigned long long k = ((unsigned long long)vord(v) << 32) |
+                                     (0xffffffffu - (unsigned)(x * s.D + e));
+        best = best > k ? best : k;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = best > other ? best : other;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key2, best);
+}
+
 // One warp: the read-back from the argmax key (Eq. 5); every band's window
 // is scanned by the lanes, the first maximum kept.  No admissible state
 // (key 0): x = -1 everywhere and a dead score.
@@ -418,6 +443,19 @@ int launch_dp_window(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t
         return wide ? launch_dp_window_tiles<Acc, 16, 8>(hv, s, t, stream, mask)
                     : launch_dp_window_tiles<Acc, 8, 8>(hv, s, t, stream, mask);
     return launch_dp_window_tiles<Acc, 8, 16>(hv, s, t, stream, mask);   // 256-row bands
+}
+
+int launch_argmax_apart(const int32_t *V, const Shape &s, const unsigned long long *key1,
+                        int sep, unsigned long long *key2, cudaStream_t stream) {
+    argmax_apart_kernel<<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key1, sep, key2);
+    return launched("argmax_apart_kernel");
+}
+
+int launch_readback_key(const int32_t *V, const Shape &s, int B, const unsigned long long *key,
+                        int32_t *x_out, int32_t *d_out, int32_t *score_out, cudaStream_t stream) {
+    readback_kernel<int32_t, BendWin><<<1, 32, 0, stream>>>(V, s, BendWin{B, s.n}, key, x_out,
+                                                             d_out, score_out);
+    return launched("readback_kernel");
 }
 
 int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const WindowTable &t,

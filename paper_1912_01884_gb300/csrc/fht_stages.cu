@@ -316,3 +316,41 @@ template int launch_fht_stages<float, float>(const float *, int, const Shape &, 
                                              cudaStream_t);
 
 }  // namespace fhtdp
+
+namespace fhtdp {
+namespace {
+// Mostly horizontal curves (Sec. 3, Fig. 7) are the mostly vertical curves of
+// the transposed image: dst[x][y] = src[y][x], through a 32 x 32 shared tile
+// so that both the reads and the writes are row segments.
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ src, int h, int w, int pitch,
+                                 T *__restrict__ dst, int dpitch) {
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int y = y0 + dy, x = x0 + threadIdx.x;
+        if (y < h && x < w) tile[dy][threadIdx.x] = src[(size_t)y * pitch + x];
+    }
+    __syncthreads();
+    for (int dx = threadIdx.y; dx < 32; dx += blockDim.y) {
+        const int x = x0 + dx, y = y0 + threadIdx.x;
+        if (x < w && y < h) dst[(size_t)x * dpitch + y] = tile[threadIdx.x][dx];
+    }
+}
+}  // namespace
+
+template <typename T>
+int launch_transpose(const T *src, int h, int w, int pitch, T *dst, int dpitch,
+                     cudaStream_t stream) {
+    dim3 grid((unsigned)((w + 31) / 32), (unsigned)((h + 31) / 32));   // h, w <= 2^20
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, stream>>>(src, h, w, pitch, dst, dpitch);
+    return launched("transpose_kernel");
+}
+
+template int launch_transpose<uint8_t>(const uint8_t *, int, int, int, uint8_t *, int,
+                                       cudaStream_t);
+template int launch_transpose<int32_t>(const int32_t *, int, int, int, int32_t *, int,
+                                       cudaStream_t);
+template int launch_transpose<float>(const float *, int, int, int, float *, int, cudaStream_t);
+
+}  // namespace fhtdp

@@ -1,6 +1,8 @@
-// Subproblems 2-3 (Sec. 2.2-2.3) on one image: the extreme polyline through a
-// given point P on a band border.  Host side only: the sequence of launches.
+// Queries on the standalone kernels, host side only (the sequences of
+// launches).
 //
+// Subproblems 2-3 (Sec. 2.2-2.3): the extreme polyline through a given point
+// P on a band border.
 // The paper builds the part below P by the DP over bands j..k-1 and the part
 // above P by the same DP on bands 0..j-1 flipped about Ox.  Here one DP runs
 // over all bands and marks every state of P's band whose vertex on P's
@@ -36,6 +38,31 @@ int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
              : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
     if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream, &pm);
     if (!st) st = launch_backtrack_key<int32_t>(H, s, B, key, x_out, d_out, score_out, stream);
+    return st;
+}
+
+// Two different extreme polylines (Sec. 3, Figs. 6d and 7a; the paper gives
+// no rule): the optimum, then the best polyline whose top vertex lies at
+// least sep columns from the optimum's, both read back from the same V.
+// Workspace as for the through-point query; the second key follows the first.
+int detect_two(const void *img, int dtype, int pitch, const Shape &s, int B, int sep,
+               int32_t *x_out, int32_t *d_out, int32_t *score_out, void *ws,
+               cudaStream_t stream) {
+    char *base = (char *)ws;
+    unsigned long long *key1 = (unsigned long long *)base, *key2 = key1 + 1;
+    int32_t *H = (int32_t *)(base + kThroughHead);
+    int32_t *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
+    int st = cuda_status(cudaMemsetAsync(base, 0, kThroughHead, stream), "cudaMemsetAsync");
+    if (st) return st;
+    st = dtype == FHTDP_U8
+             ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream)
+             : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
+    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
+    if (!st) st = launch_backtrack_key<int32_t>(H, s, B, key1, x_out, d_out, score_out, stream);
+    if (!st) st = launch_argmax_apart(H, s, key1, sep, key2, stream);
+    if (!st)
+        st = launch_readback_key(H, s, B, key2, x_out + s.k + 1, d_out + s.k, score_out + 1,
+                                 stream);
     return st;
 }
 

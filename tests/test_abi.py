@@ -144,3 +144,25 @@ def test_through_point_rejects_bad_arguments_before_launch(lib):
     r = L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, 2, 1, 1, fake, fake, fake, fake,
                                      64, None)
     assert r == 2 and "workspace" in L.fhtdp_last_error().decode()
+
+
+def test_two_and_horizontal_reject_bad_arguments_before_launch(lib):
+    L = lib.lib()
+    fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
+    outs = (fake, fake, fake, fake, 1 << 30, None)
+    assert L.fhtdp_two_workspace_bytes(0, 64, 10, 4) > 0
+    assert L.fhtdp_detect_two_polylines(fake, 0, 64, 10, 10, 4, 2, 0, *outs) == 1
+    assert L.fhtdp_detect_two_polylines(fake, 2, 64, 10, 10, 4, 2, 1, *outs) == 1
+    assert L.fhtdp_detect_two_polylines(fake, 0, 64, 10, 10, 4, -1, 1, *outs) == 1
+    r = L.fhtdp_detect_two_polylines(fake, 0, 64, 10, 10, 4, 2, 1, fake, fake, fake, fake, 64,
+                                     None)
+    assert r == 2
+    # horizontal: bands over the width (w = k n)
+    assert L.fhtdp_horizontal_workspace_bytes(0, 10, 64, 4, 2) > 0
+    assert L.fhtdp_horizontal_workspace_bytes(0, 64, 10, 4, 2) == 0
+    assert L.fhtdp_detect_polyline_horizontal(fake, 0, 10, 64, 64, 3, 2, *outs) == 1
+    assert L.fhtdp_detect_polyline_horizontal(fake, 0, 10, 64, 63, 4, 2, *outs) == 1   # pitch
+    assert L.fhtdp_detect_polyline_horizontal(fake, 9, 10, 64, 64, 4, 2, *outs) == 1
+    r = L.fhtdp_detect_polyline_horizontal(fake, 0, 10, 64, 64, 4, 2, fake, fake, fake, fake, 64,
+                                           None)
+    assert r == 2 and "workspace" in L.fhtdp_last_error().decode()
