@@ -254,6 +254,11 @@ int fhtdp_detect_two_polylines(const void *img, int dtype, int h, int w, int pit
  *          fhtdp_workspace_status is not available for these calls.
  * ---------------------------------------------------------------------- */
 size_t fhtdp_horizontal_workspace_bytes(int dtype, int h, int w, int k, int B);
+/* dst[x][y] = src[y][x]: src [h][pitch], dst [w][dpitch] (dpitch >= h), both
+ * device, not overlapping.  A batch of mostly horizontal images is
+ * transposed with this call and then run as one fhtdp_batch_run. */
+int fhtdp_transpose(const void *src, int dtype, int h, int w, int pitch, void *dst, int dpitch,
+                    cudaStream_t stream);
 int fhtdp_detect_polyline_horizontal(const void *img, int dtype, int h, int w, int pitch, int k,
                                      int B, int32_t *y_out, int32_t *d_out, void *score_out,
                                      void *ws, size_t ws_bytes, cudaStream_t stream);

@@ -92,6 +92,8 @@ _SIGS = {
     "fhtdp_detect_two_polylines": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 7
                                    + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_horizontal_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 5),
+    "fhtdp_transpose": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 4
+                        + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "fhtdp_detect_polyline_horizontal": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                                          + [ctypes.c_void_p] * 4
                                          + [ctypes.c_size_t, ctypes.c_void_p]),
@@ -498,3 +500,17 @@ def detect_polyline_horizontal(img, k: int, B: int, out=None, ws=None, stream=No
                                                   y.data_ptr(), d.data_ptr(), score.data_ptr(),
                                                   ws.data_ptr(), ws.numel(), _stream(stream)))
     return y, d, score
+
+
+def transpose(img, out=None, stream=None):
+    """dst[x][y] = img[y][x] on the device (the row pitch of `out` may exceed h)."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _dtype_code(img)
+    if out is None:
+        out = torch.empty((w, h), dtype=img.dtype, device=img.device)
+    if out.dim() != 2 or out.shape[0] != w or out.shape[1] != h or out.stride(1) != 1:
+        raise ValueError("out must be a [w, h] view with unit column stride")
+    _check(lib().fhtdp_transpose(img.data_ptr(), code, h, w, pitch, out.data_ptr(), out.stride(0),
+                                 _stream(stream)))
+    return out

@@ -345,6 +345,29 @@ size_t transposed_bytes(int dtype, int h, int w) {
 }
 }  // namespace
 
+int fhtdp_transpose(const void *src, int dtype, int h, int w, int pitch, void *dst, int dpitch,
+                    cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
+    if (h < 1 || w < 1 || h > (1 << 20) || w > (1 << 20))
+        return set_error(FHTDP_EINVAL, "invalid image %d x %d", h, w);
+    if (pitch < w || dpitch < h)
+        return set_error(FHTDP_EINVAL, "pitch %d < w %d or dst pitch %d < h %d", pitch, w,
+                         dpitch, h);
+    if (!src || !dst || src == dst) return set_error(FHTDP_EINVAL, "null or aliased buffers");
+    switch (dtype) {
+        case FHTDP_U8:
+            return launch_transpose<uint8_t>((const uint8_t *)src, h, w, pitch, (uint8_t *)dst,
+                                             dpitch, stream);
+        case FHTDP_I32:
+            return launch_transpose<int32_t>((const int32_t *)src, h, w, pitch, (int32_t *)dst,
+                                             dpitch, stream);
+        default:
+            return launch_transpose<float>((const float *)src, h, w, pitch, (float *)dst, dpitch,
+                                           stream);
+    }
+}
+
 size_t fhtdp_horizontal_workspace_bytes(int dtype, int h, int w, int k, int B) {
     Shape s;
     if (!valid_dtype(dtype) || !make_shape(w, h, k, &s) || B < 0) return 0;

@@ -166,3 +166,14 @@ def test_two_and_horizontal_reject_bad_arguments_before_launch(lib):
     r = L.fhtdp_detect_polyline_horizontal(fake, 0, 10, 64, 64, 4, 2, fake, fake, fake, fake, 64,
                                            None)
     assert r == 2 and "workspace" in L.fhtdp_last_error().decode()
+
+
+def test_transpose_rejects_bad_arguments_before_launch(lib):
+    L = lib.lib()
+    a, b = ctypes.c_void_p(16), ctypes.c_void_p(4096)
+    assert L.fhtdp_transpose(a, 0, 4, 8, 7, b, 4, None) == 1      # pitch < w
+    assert L.fhtdp_transpose(a, 0, 4, 8, 8, b, 3, None) == 1      # dst pitch < h
+    assert L.fhtdp_transpose(a, 5, 4, 8, 8, b, 4, None) == 1      # dtype
+    assert L.fhtdp_transpose(a, 0, 4, 8, 8, a, 4, None) == 1      # in place
+    assert L.fhtdp_transpose(None, 0, 4, 8, 8, b, 4, None) == 1
+    assert L.fhtdp_transpose(a, 0, 0, 8, 8, b, 4, None) == 1

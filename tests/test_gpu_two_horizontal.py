@@ -104,3 +104,30 @@ def test_two_and_horizontal_reject_bad_arguments_on_device(lib):
         lib.detect_polyline_horizontal(img, 3, 2)             # 40 columns, k = 3
     with pytest.raises(lib.FhtdpError):
         lib.detect_polyline_horizontal(img, 4, -1)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "i32", "f32"])
+@pytest.mark.parametrize("h,w", [(1, 1), (33, 65), (300, 7), (2048, 2048), (31, 1000)])
+def test_transpose_matches_numpy(lib, dtype, h, w):
+    import torch
+    img = _img(h, w, dtype, h + w)
+    out = torch.zeros((w, h + 5), dtype=to_device(img).dtype, device="cuda")
+    lib.transpose(to_device(img), out=out[:, :h])
+    got = out.cpu().numpy()
+    assert np.array_equal(got[:, :h], img.T)
+    assert not got[:, h:].any()
+
+
+def test_batch_of_transposed_images_equals_horizontal_calls(lib):
+    """The batched route for mostly horizontal images: transpose each, run
+    one batch plan; equal to the single-image horizontal call."""
+    imgs = [_img(200 + 40 * j, 256, "u8", 40 + j) for j in range(4)]
+    dev = [to_device(m) for m in imgs]
+    tr = [lib.transpose(m) for m in dev]
+    plan = lib.BatchPlan(tr, [4] * 4, [6] * 4)
+    plan.run()
+    for i, m in enumerate(dev):
+        y, d, s = lib.detect_polyline_horizontal(m, 4, 6)
+        assert list(plan.x[i].cpu().numpy()) == list(y.cpu().numpy())
+        assert list(plan.d[i].cpu().numpy()) == list(d.cpu().numpy())
+        assert int(plan.score[i].cpu().numpy()[0]) == int(s.cpu().numpy()[0])
