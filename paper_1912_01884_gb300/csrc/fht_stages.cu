@@ -337,11 +337,59 @@ __global__ void transpose_kernel(const T *__restrict__ src, int h, int w, int pi
         if (x < w && y < h) dst[(size_t)x * dpitch + y] = tile[threadIdx.x][dx];
     }
 }
+// The uint8 transpose with 4-byte words: 64 x 64 byte tiles and 16 x 16
+// threads; a thread loads one word of each of four tile rows and stores one
+// word (four source rows of one column) of each of four output rows.  Needs
+// both base addresses and both pitches 4-byte aligned; ragged edges go byte
+// by byte.
+__global__ void transpose_u8x4_kernel(const uint8_t *__restrict__ src, int h, int w, int pitch,
+                                      uint8_t *__restrict__ dst, int dpitch) {
+    __shared__ __align__(4) uint8_t tile[64][68];
+    const int x0 = blockIdx.x * 64, y0 = blockIdx.y * 64;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int y = y0 + ty + 16 * i, x = x0 + 4 * tx;
+        uint32_t v = 0;
+        if (y < h) {
+            const uint8_t *p = src + (size_t)y * pitch + x;
+            if (x + 3 < w) {
+                v = *(const uint32_t *)p;
+            } else {
+                for (int b = 0; b < 4; ++b)
+                    if (x + b < w) v |= (uint32_t)p[b] << (8 * b);
+            }
+        }
+        *(uint32_t *)&tile[ty + 16 * i][4 * tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c = ty + 16 * i, x = x0 + c, y = y0 + 4 * tx;
+        if (x >= w || y >= h) continue;
+        const uint32_t v = (uint32_t)tile[4 * tx][c] | (uint32_t)tile[4 * tx + 1][c] << 8 |
+                           (uint32_t)tile[4 * tx + 2][c] << 16 |
+                           (uint32_t)tile[4 * tx + 3][c] << 24;
+        uint8_t *q = dst + (size_t)x * dpitch + y;
+        if (y + 3 < h) {
+            *(uint32_t *)q = v;
+        } else {
+            for (int b = 0; b < 4 && y + b < h; ++b) q[b] = (uint8_t)(v >> (8 * b));
+        }
+    }
+}
 }  // namespace
 
 template <typename T>
 int launch_transpose(const T *src, int h, int w, int pitch, T *dst, int dpitch,
                      cudaStream_t stream) {
+    if (sizeof(T) == 1 && ((uintptr_t)src & 3) == 0 && ((uintptr_t)dst & 3) == 0 &&
+        pitch % 4 == 0 && dpitch % 4 == 0) {
+        dim3 grid((unsigned)((w + 63) / 64), (unsigned)((h + 63) / 64));   // h, w <= 2^20
+        transpose_u8x4_kernel<<<grid, dim3(16, 16), 0, stream>>>(
+            (const uint8_t *)src, h, w, pitch, (uint8_t *)dst, dpitch);
+        return launched("transpose_u8x4_kernel");
+    }
     dim3 grid((unsigned)((w + 31) / 32), (unsigned)((h + 31) / 32));   // h, w <= 2^20
     transpose_kernel<T><<<grid, dim3(32, 8), 0, stream>>>(src, h, w, pitch, dst, dpitch);
     return launched("transpose_kernel");

@@ -107,11 +107,16 @@ def test_two_and_horizontal_reject_bad_arguments_on_device(lib):
 
 
 @pytest.mark.parametrize("dtype", ["u8", "i32", "f32"])
-@pytest.mark.parametrize("h,w", [(1, 1), (33, 65), (300, 7), (2048, 2048), (31, 1000)])
-def test_transpose_matches_numpy(lib, dtype, h, w):
+@pytest.mark.parametrize("h,w", [(1, 1), (33, 65), (300, 7), (2048, 2048), (31, 1000), (67, 64),
+                                 (64, 132)])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_transpose_matches_numpy(lib, dtype, h, w, aligned):
+    """Both uint8 kernels: 4-byte words when both pitches are multiples of 4,
+    bytes otherwise."""
     import torch
     img = _img(h, w, dtype, h + w)
-    out = torch.zeros((w, h + 5), dtype=to_device(img).dtype, device="cuda")
+    pad = (8 - h % 4) if aligned else (5 if (h + 5) % 4 else 6)
+    out = torch.zeros((w, h + pad), dtype=to_device(img).dtype, device="cuda")
     lib.transpose(to_device(img), out=out[:, :h])
     got = out.cpu().numpy()
     assert np.array_equal(got[:, :h], img.T)
