@@ -28,6 +28,8 @@ Function map (paper passages in the C file's comments):
   detect_two / brute_apart
                    Sec. 3: two different extreme polylines (suppression on x_0)
   detect_horizontal  Sec. 3, Fig. 7: mostly horizontal polylines (transposition)
+  detect_padded / brute_padded / path_score_padded
+                   Sec. 2.2: vertices anywhere in the zero-padded band width
 """
 from __future__ import annotations
 
@@ -123,6 +125,14 @@ def _load():
             lib.oracle_brute_apart_f64.argtypes = ([_F64P] + [ctypes.c_int] * 6
                                                    + [_I32P, _I32P])
             lib.oracle_brute_apart_f64.restype = ctypes.c_double
+            lib.oracle_path_score_padded_f64.argtypes = [_F64P] + [ctypes.c_int] * 4 + [_I32P]
+            lib.oracle_path_score_padded_f64.restype = ctypes.c_double
+            lib.oracle_detect_padded_f64.argtypes = [_F64P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
+            lib.oracle_detect_padded_f64.restype = ctypes.c_double
+            lib.oracle_brute_padded_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
+                                                    + [_I32P, _I32P,
+                                                       ctypes.POINTER(ctypes.c_long)])
+            lib.oracle_brute_padded_f64.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -429,3 +439,38 @@ def detect_horizontal(img, k: int, B: int):
     Returns (y[k+1], d[k], score): y_i is the row of the polyline on the
     first column of strip i, d_i = y_{i+1} - y_i."""
     return detect(np.ascontiguousarray(np.asarray(img).T), k, B)
+
+
+def path_score_padded(img, k: int, x0: int, ds) -> float:
+    """Sum along the polyline with vertices in [0, w + n) and zeros right of
+    the image; -inf if it is not admissible."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    d = np.ascontiguousarray(ds, dtype=np.int32)
+    return _load().oracle_path_score_padded_f64(_p(img, ctypes.c_double), h, w, k, int(x0),
+                                                _p(d, ctypes.c_int32))
+
+
+def detect_padded(img, k: int, B: int):
+    """The method with every vertex in [0, w + n) (the zero-padded band
+    width): (x[k+1], d[k], score)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_padded_f64(_p(img, ctypes.c_double), h, w, k, B,
+                                         _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def brute_padded(img, k: int, B: int):
+    """Brute force with vertices in [0, w + n): (x, d, score, visited)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    visited = ctypes.c_long(0)
+    s = _load().oracle_brute_padded_f64(_p(img, ctypes.c_double), h, w, k, B,
+                                        _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32),
+                                        ctypes.byref(visited))
+    return xs, ds, s, visited.value

@@ -870,3 +870,133 @@ double oracle_brute_apart_f64(const double *img, int h, int w, int k, int B, int
     free(bd);
     return best;
 }
+
+/* ---------------------------------------------------------------------------
+ * Vertices in the padding (Sec. 2.2: the Hough columns run over
+ * [0, w + h/k - 1]).  Each band is extended to the right by n zero columns
+ * (Sec. 2.1), and the polyline's vertices may lie anywhere in [0, W),
+ * W = w + n: the pixels a link covers right of the image count as zero.  The
+ * DP, the read-back and the brute force below are those above with the
+ * vertex domain [0, W) in place of [0, w); V: [k][2n-1][W].
+ * ------------------------------------------------------------------------ */
+double oracle_path_score_padded_f64(const double *img, int h, int w, int k, int x0,
+                                    const int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    int32_t *off = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * n);
+    if (!off) return ORACLE_NEG;
+    oracle_off_table(n, off);
+    double acc = 0.0;
+    int x = x0;
+    if (x < 0 || x >= W) acc = ORACLE_NEG;
+    for (int i = 0; i < k && acc != ORACLE_NEG; ++i) {
+        int d = ds[i];
+        int s = d >= 0 ? d : -d;
+        if (s > n - 1 || x + d < 0 || x + d >= W) {
+            acc = ORACLE_NEG;
+            break;
+        }
+        for (int y = 0; y < n; ++y) {
+            int c = x + (d >= 0 ? 1 : -1) * off[(size_t)s * n + y];
+            if (c < w) acc += img[((size_t)i * n + y) * w + c];   /* zero right of the image */
+        }
+        x += d;
+    }
+    free(off);
+    return acc;
+}
+
+int oracle_dp_padded_f64(const double *H, int h, int w, int k, int B, double *V) {
+    if (k < 1 || h % k != 0 || B < 0) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    for (int b = k - 1; b >= 0; --b)
+        for (int d = -(n - 1); d <= n - 1; ++d)
+            for (int x = 0; x < W; ++x) {
+                double *out = &V[((size_t)b * D + (d + n - 1)) * W + x];
+                int xn = x + d;
+                if (xn < 0 || xn >= W) {
+                    *out = ORACLE_NEG;
+                    continue;
+                }
+                double hv = hough_at_f64(H, n, W, b, x, d);
+                if (b == k - 1) {
+                    *out = hv;
+                    continue;
+                }
+                double best = ORACLE_NEG;
+                for (int e = d - B; e <= d + B; ++e) {
+                    if (e < -(n - 1) || e > n - 1) continue;
+                    double v = V[((size_t)(b + 1) * D + (e + n - 1)) * W + xn];
+                    if (v > best) best = v;
+                }
+                *out = (best == ORACLE_NEG) ? ORACLE_NEG : hv + best;
+            }
+    return 0;
+}
+
+double oracle_detect_padded_f64(const double *img, int h, int w, int k, int B, int32_t *xs,
+                                int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * (2 * n - 1) * W);
+    double s = NAN;
+    if (H && V) {
+        oracle_fht_recursive_f64(img, h, w, k, H);
+        oracle_dp_padded_f64(H, h, w, k, B, V);
+        /* V has W columns: the read-back over the vertex domain [0, W) is the
+         * plain read-back with W as the width */
+        s = oracle_backtrack_f64(V, h, W, k, B, xs, ds);
+    }
+    free(H);
+    free(V);
+    return s;
+}
+
+/* Brute force with vertices in [0, W) and zeros right of the image. */
+double oracle_brute_padded_f64(const double *img, int h, int w, int k, int B, int32_t *xs,
+                               int32_t *ds, long *visited) {
+    int n = h / k;
+    int W = w + n;
+    int32_t *cd = (int32_t *)calloc((size_t)k, sizeof(int32_t));
+    double best = ORACLE_NEG;
+    long count = 0;
+    for (int i = 0; i <= k; ++i) xs[i] = -1;
+    for (int i = 0; i < k; ++i) ds[i] = 0;
+    for (int x0 = 0; x0 < W; ++x0) {
+        /* odometer over d in lexicographic order, pruned by the vertex domain
+         * and the bend limit at the end */
+        for (int i = 0; i < k; ++i) cd[i] = -(n - 1);
+        for (;;) {
+            int ok = 1, x = x0;
+            for (int i = 0; i < k && ok; ++i) {
+                if (i > 0 && (cd[i] < cd[i - 1] - B || cd[i] > cd[i - 1] + B)) ok = 0;
+                x += cd[i];
+                if (x < 0 || x >= W) ok = 0;
+            }
+            if (ok) {
+                ++count;
+                double sc = oracle_path_score_padded_f64(img, h, w, k, x0, cd);
+                if (sc > best) {
+                    best = sc;
+                    int xx = x0;
+                    for (int i = 0; i < k; ++i) {
+                        xs[i] = xx;
+                        ds[i] = cd[i];
+                        xx += cd[i];
+                    }
+                    xs[k] = xx;
+                }
+            }
+            int i = k - 1;
+            while (i >= 0 && cd[i] == n - 1) cd[i--] = -(n - 1);
+            if (i < 0) break;
+            ++cd[i];
+        }
+    }
+    free(cd);
+    if (visited) *visited = count;
+    return best;
+}
