@@ -4,7 +4,7 @@ read-back) in Mpix/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload plain2048|mixed|float8192|plain256|angle2048|through2048|
-                                horizontal2048|two2048]
+                                horizontal2048|two2048|padded2048]
                     [--images I]
 
 Default workload: synthetic 2048x2048 uint8 images, k=16 bands of 128 rows,
@@ -58,6 +58,9 @@ WORKLOADS = {
         desc="mostly horizontal curves: u8 2048x2048 (the plain2048 images transposed), k=16 "
              "vertical strips of 128 columns, bend 16 (each step transposes its images and runs "
              "them as one batch)", images=32, dtype="u8"),
+    "padded2048": dict(
+        desc="vertices in the zero padding: u8 2048x2048 (the plain2048 images), k=16 bands of "
+             "128 rows, bend 16, every vertex in [0, w + 128)", images=32, dtype="u8"),
     "two2048": dict(
         desc="two different extreme polylines: u8 2048x2048 (the plain2048 images), k=16, "
              "bend 16, the second polyline's top vertex at least 64 columns from the first's",
@@ -216,6 +219,8 @@ def make_workload(name, images, seed, rank):
     if name == "horizontal2048":
         return [(np.ascontiguousarray(w.img.T), w.k, w.B)
                 for w in (synth.plain_gaussian(s) for s in seeds)]
+    if name == "padded2048":
+        return [(w.img, w.k, ("padded", w.B)) for w in (synth.plain_gaussian(s) for s in seeds)]
     if name == "two2048":
         return [(w.img, w.k, ("two", w.B, TWO_SEPARATION))
                 for w in (synth.plain_gaussian(s) for s in seeds)]
@@ -238,6 +243,8 @@ def oracle_rate(items, budget_s, horizontal=False):
             oracle.detect_angle(img, k, ANGLE_R, ANGLE_GAMMA)
         elif isinstance(B, tuple) and B[0] == "two":
             oracle.detect_two(img, k, B[1], B[2])
+        elif isinstance(B, tuple) and B[0] == "padded":
+            oracle.detect_padded(img, k, B[1])
         elif isinstance(B, tuple):
             oracle.detect_through(img, k, *B)
         elif horizontal:
@@ -573,6 +580,10 @@ def run_standalone(args):
                     fd.detect_two_polylines(src[j], k, items[j][2][1], items[j][2][2],
                                             out=(xs2[j], ds2[j], sc2[j]), ws=wss[ln],
                                             stream=side[ln])
+                elif name == "padded2048":
+                    fd.detect_polyline_padded(src[j], k, items[j][2][1],
+                                              out=(xs[j], ds[j], sc[j]), ws=wss[ln],
+                                              stream=side[ln])
                 else:
                     B, jb, xp = items[j][2]
                     fd.detect_through_point(src[j], k, B, jb, xp, out=(xs[j], ds[j], sc[j]),
@@ -666,7 +677,7 @@ def run_standalone(args):
             "engine": lambda: fd.detect_polyline(tr, k, B0, out=one, ws=ws_e, stream=main),
         }
     else:
-        B0 = items[0][2][1] if two else items[0][2][0]
+        B0 = items[0][2][1] if (two or name == "padded2048") else items[0][2][0]
         stages = {
             "fht_bands": lambda: fd.fht_bands(imgs[0], k, out=hough, ws=ws_tmp, stream=main),
             "dp": lambda: fd.polyline_dp(hough, h, w, k, B0, stream=main),
@@ -714,6 +725,8 @@ def run_standalone(args):
                        **({"r": ANGLE_R, "gamma_rad": ANGLE_GAMMA} if angle else
                           {"B": items[0][2]} if name == "horizontal2048" else
                           {"B": items[0][2][1], "separation": TWO_SEPARATION} if two else
+                          {"B": items[0][2][1], "vertex_domain": "[0, w + n)"}
+                          if name == "padded2048" else
                           {"B": items[0][2][0], "border": THROUGH_BORDER}),
                        "l2": "inputs %d MB per step %s 129 MB L2, no flush"
                              % (host.numel() // 2**20, ">" if host.numel() > 129e6 else "<")},
@@ -826,7 +839,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload in ("angle2048", "through2048", "two2048"):
+    elif args.workload in ("angle2048", "through2048", "two2048", "padded2048"):
         run_standalone(args)
     elif args.workload == "learned1024":
         run_learned(args)

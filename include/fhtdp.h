@@ -226,6 +226,19 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
                                void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Vertices in the zero padding (Sec. 2.2: the Hough columns run over
+ * [0, w + h/k - 1]; Sec. 2.1 extends every band by n zero columns on the
+ * right).  As fhtdp_detect_polyline, but every vertex may lie anywhere in
+ * [0, W), W = w + n: the pixels a link covers right of the image count as
+ * zero, so a curve that runs off the right edge can be followed.  Runs the
+ * standalone kernels.  dtype FHTDP_U8 or FHTDP_I32; ws of at least
+ * fhtdp_through_workspace_bytes() bytes.  Outputs as for fhtdp_backtrack.
+ * ---------------------------------------------------------------------- */
+int fhtdp_detect_polyline_padded(const void *img, int dtype, int h, int w, int pitch, int k,
+                                 int B, int32_t *x_out, int32_t *d_out, void *score_out,
+                                 void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Two different extreme polylines (Sec. 3, Figs. 6d and 7a, where the paper
  * shows two and states no rule).  The first is the optimum of
  * fhtdp_detect_polyline; the second is the best admissible polyline whose top

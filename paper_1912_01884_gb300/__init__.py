@@ -88,6 +88,9 @@ _SIGS = {
     "fhtdp_through_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
     "fhtdp_detect_through_point": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 8
                                    + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_detect_polyline_padded": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
+                                     + [ctypes.c_void_p] * 4
+                                     + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_two_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
     "fhtdp_detect_two_polylines": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 7
                                    + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
@@ -514,3 +517,22 @@ def transpose(img, out=None, stream=None):
     _check(lib().fhtdp_transpose(img.data_ptr(), code, h, w, pitch, out.data_ptr(), out.stride(0),
                                  _stream(stream)))
     return out
+
+
+def detect_polyline_padded(img, k: int, B: int, out=None, ws=None, stream=None):
+    """The method with vertices anywhere in [0, w + h/k) (zeros right of the
+    image), uint8 or int32 image: (x[k+1], d[k], score[1])."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _int_image_code(img)
+    need = through_workspace_bytes(code, h, w, k)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_polyline_padded(None, code, h, w, pitch, k, B, None, None,
+                                                  None, None, 0, _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    x, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_polyline_padded(img.data_ptr(), code, h, w, pitch, k, B,
+                                              x.data_ptr(), d.data_ptr(), score.data_ptr(),
+                                              ws.data_ptr(), ws.numel(), _stream(stream)))
+    return x, d, score

@@ -49,6 +49,7 @@ bool make_shape(int h, int w, int k, Shape *out) {
     s.D = 2 * n - 1;
     s.log2n = 0;
     while ((1 << s.log2n) < n) ++s.log2n;
+    s.vw = w;
     *out = s;
     return true;
 }
@@ -304,6 +305,29 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
     const PointMask pm{j, xp};
     return detect_through(img, dtype, pitch, s, B, pm, x_out, d_out, (int32_t *)score_out, ws,
                           stream);
+}
+
+// ---------------------------------------------------------------------------
+// Vertices in the zero padding (Sec. 2.2).
+int fhtdp_detect_polyline_padded(const void *img, int dtype, int h, int w, int pitch, int k,
+                                 int B, int32_t *x_out, int32_t *d_out, void *score_out,
+                                 void *ws, size_t ws_bytes, cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
+        return set_error(FHTDP_EINVAL, "the padded-vertex call takes integer images (dtype %d)",
+                         dtype);
+    if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
+    if (!img || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    size_t need = through_workspace_bytes(s);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    s.vw = s.W;
+    return detect_padded(img, dtype, pitch, s, B, x_out, d_out, (int32_t *)score_out, ws, stream);
 }
 
 // ---------------------------------------------------------------------------

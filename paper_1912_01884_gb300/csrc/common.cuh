@@ -27,6 +27,9 @@ struct Dead<float> {
 struct Shape {
     int h, w, k, n, W, D;  // D = 2n - 1 displacement values
     int log2n;
+    // Vertex domain [0, vw) of the standalone DP and read-back: w, or W when
+    // vertices may lie in the zero padding right of the image (Sec. 2.2).
+    int vw;
 };
 
 // The continuation window of every displacement: entry d + n - 1 holds the
@@ -99,6 +102,10 @@ int launch_backtrack_angle(const int32_t *V, const Shape &s, const WindowTable &
                            cudaStream_t stream);
 size_t angle_workspace_bytes(const Shape &s);
 size_t through_workspace_bytes(const Shape &s);
+// The method with vertices anywhere in [0, W) (s.vw = W): the standalone
+// FHT, DP and key read-back.
+int detect_padded(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
+                  int32_t *d_out, int32_t *score_out, void *ws, cudaStream_t stream);
 // Two different extreme polylines: the optimum and the best one whose top
 // vertex is at least sep columns from the optimum's (outputs [2][...]).
 int detect_two(const void *img, int dtype, int pitch, const Shape &s, int B, int sep,

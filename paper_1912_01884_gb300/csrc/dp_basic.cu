@@ -57,7 +57,7 @@ __global__ void dp_last_band_kernel(Acc *hv, Shape s) {
         int r = (int)(i / s.W);
         int sh = r % s.n, sign = r / s.n;
         int d = sign ? -sh : sh;
-        if (x >= s.w || x + d < 0 || x + d >= s.w)
+        if (x >= s.vw || x + d < 0 || x + d >= s.vw)
             hv[(size_t)band * per_band + i] = Dead<Acc>::value();
     }
 }
@@ -109,7 +109,7 @@ dp_band_window_kernel(Acc *hv, Shape s, int band, WindowTable t, int levels) {
     const int xn0 = (int)blockIdx.x * C - (s.n - 1), xn = xn0 + c;
     const Acc dead = Dead<Acc>::value();
     const size_t dup_row = ((size_t)band * 2 + 1) * s.n * s.W;   // d = 0, "-" half
-    if (!(xn0 + C > 0 && xn0 < s.w)) {
+    if (!(xn0 + C > 0 && xn0 < s.vw)) {
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
@@ -119,7 +119,7 @@ dp_band_window_kernel(Acc *hv, Shape s, int band, WindowTable t, int levels) {
         }
         return;
     }
-    const bool live_col = xn >= 0 && xn < s.w;
+    const bool live_col = xn >= 0 && xn < s.vw;
     Acc va[RPT], hb[RPT];
     uint32_t lh[RPT];   // window rows lo | hi << 16
 #pragma unroll
@@ -130,7 +130,7 @@ dp_band_window_kernel(Acc *hv, Shape s, int band, WindowTable t, int levels) {
         lh[u] = 0;
         if (r < D) {
             if (live_col) va[u] = hv[cell<Acc>(s, band + 1, xn, d)];
-            if (live_col && x >= 0 && x < s.w) hb[u] = hv[cell<Acc>(s, band, x, d)];
+            if (live_col && x >= 0 && x < s.vw) hb[u] = hv[cell<Acc>(s, band, x, d)];
             lh[u] = (uint32_t)(t.lo[r] + s.n - 1) | (uint32_t)(t.hi[r] + s.n - 1) << 16;
         }
     }
@@ -157,7 +157,7 @@ dp_band_window_kernel(Acc *hv, Shape s, int band, WindowTable t, int levels) {
         const int r = r0 + 32 * u, d = r - (s.n - 1), x = xn - d;
         if (r >= D || x < 0 || x >= s.W) continue;
         Acc v = dead;
-        if (x < s.w && live_col) {
+        if (x < s.vw && live_col) {
             const int lo = (int)(lh[u] & 0xffffu), hi = (int)(lh[u] >> 16);
             const int j = 31 - __clz(hi - lo + 1);
             const Acc *T = sm + (size_t)j * D * C;
@@ -193,9 +193,9 @@ template <typename Acc>
 __global__ void argmax_kernel(const Acc *V, Shape s, unsigned long long *key) {
     const Acc dead = Dead<Acc>::value();
     unsigned long long best = 0;
-    const int total = s.w * s.D;
+    const int total = s.vw * s.D;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int e = i / s.w, x = i - e * s.w;   // x fastest: coalesced rows
+        const int e = i / s.vw, x = i - e * s.vw;   // x fastest: coalesced rows
         const Acc v = V[cell<Acc>(s, 0, x, e - (s.n - 1))];
         if (v == dead) continue;
         const unsigned long long k = ((unsigned long long)vord(v) << 32) |
@@ -217,9 +217,9 @@ __global__ void argmax_apart_kernel(const int32_t *V, Shape s, const unsigned lo
     if (k1 == 0) return;
     const int x0 = (int)((0xffffffffu - (unsigned)(k1 & 0xffffffffu)) / s.D);
     unsigned long long best = 0;
-    const int total = s.w * s.D;
+    const int total = s.vw * s.D;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int e = i / s.w, x = i - e * s.w;
+        const int e = i / s.vw, x = i - e * s.vw;
         if (abs(x - x0) < sep) continue;
         const int32_t v = V[cell<int32_t>(s, 0, x, e - (s.n - 1))];
         if (v == Dead<int32_t>::value()) continue;
@@ -296,7 +296,7 @@ __global__ void backtrack_kernel(const Acc *V, Shape s, Win win, int32_t *x_out,
     const Acc dead = Dead<Acc>::value();
     Acc best = dead;
     int bidx = INT_MAX;
-    const int total = s.w * s.D;   // lexicographic index x * D + (d + n - 1)
+    const int total = s.vw * s.D;   // lexicographic index x * D + (d + n - 1)
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         int x = idx / s.D, d = idx % s.D - (s.n - 1);
         Acc v = V[cell<Acc>(s, 0, x, d)];
@@ -369,7 +369,7 @@ int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_
 template <typename Acc>
 int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long *key,
                          int32_t *x_out, int32_t *d_out, Acc *score_out, cudaStream_t stream) {
-    argmax_kernel<Acc><<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key);
+    argmax_kernel<Acc><<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key);
     int st = launched("argmax_kernel");
     if (st) return st;
     readback_kernel<Acc, BendWin><<<1, 32, 0, stream>>>(V, s, BendWin{B, s.n}, key, x_out, d_out,
@@ -447,7 +447,7 @@ int launch_dp_window(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t
 
 int launch_argmax_apart(const int32_t *V, const Shape &s, const unsigned long long *key1,
                         int sep, unsigned long long *key2, cudaStream_t stream) {
-    argmax_apart_kernel<<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key1, sep, key2);
+    argmax_apart_kernel<<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key1, sep, key2);
     return launched("argmax_apart_kernel");
 }
 
@@ -461,7 +461,7 @@ int launch_readback_key(const int32_t *V, const Shape &s, int B, const unsigned 
 int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const WindowTable &t,
                                unsigned long long *key, int32_t *x_out, int32_t *d_out,
                                int32_t *score_out, cudaStream_t stream) {
-    argmax_kernel<int32_t><<<grid_for((size_t)s.w * s.D), 256, 0, stream>>>(V, s, key);
+    argmax_kernel<int32_t><<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key);
     int st = launched("argmax_kernel");
     if (st) return st;
     readback_kernel<int32_t, TableWin><<<1, 32, 0, stream>>>(V, s, TableWin{t}, key, x_out,

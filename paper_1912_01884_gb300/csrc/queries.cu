@@ -41,6 +41,26 @@ int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
     return st;
 }
 
+// Vertices anywhere in the zero-padded band width (Sec. 2.2: Hough columns
+// up to w + h/k - 1).  The cyclic FHT never wraps for a link with both ends
+// in [0, W), so its values are the plain sums with zeros right of the image;
+// the DP and the read-back run over the vertex domain s.vw = W.
+int detect_padded(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
+                  int32_t *d_out, int32_t *score_out, void *ws, cudaStream_t stream) {
+    char *base = (char *)ws;
+    unsigned long long *key = (unsigned long long *)base;
+    int32_t *H = (int32_t *)(base + kThroughHead);
+    int32_t *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
+    int st = cuda_status(cudaMemsetAsync(base, 0, kThroughHead, stream), "cudaMemsetAsync");
+    if (st) return st;
+    st = dtype == FHTDP_U8
+             ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream)
+             : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
+    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
+    if (!st) st = launch_backtrack_key<int32_t>(H, s, B, key, x_out, d_out, score_out, stream);
+    return st;
+}
+
 // Two different extreme polylines (Sec. 3, Figs. 6d and 7a; the paper gives
 // no rule): the optimum, then the best polyline whose top vertex lies at
 // least sep columns from the optimum's, both read back from the same V.

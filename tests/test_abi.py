@@ -177,3 +177,16 @@ def test_transpose_rejects_bad_arguments_before_launch(lib):
     assert L.fhtdp_transpose(a, 0, 4, 8, 8, a, 4, None) == 1      # in place
     assert L.fhtdp_transpose(None, 0, 4, 8, 8, b, 4, None) == 1
     assert L.fhtdp_transpose(a, 0, 0, 8, 8, b, 4, None) == 1
+
+
+def test_padded_rejects_bad_arguments_before_launch(lib):
+    L = lib.lib()
+    fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
+    outs = (fake, fake, fake, fake, 1 << 30, None)
+    assert L.fhtdp_detect_polyline_padded(fake, 2, 64, 10, 10, 4, 2, *outs) == 1
+    assert L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 10, 3, 2, *outs) == 1
+    assert L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 10, 4, -1, *outs) == 1
+    assert L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 9, 4, 2, *outs) == 1
+    r = L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 10, 4, 2, fake, fake, fake, fake, 64,
+                                       None)
+    assert r == 2
