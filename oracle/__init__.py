@@ -25,6 +25,8 @@ Function map (paper passages in the C file's comments):
   dp_through / detect_through / brute_through
                    Sec. 2.2-2.3 Subproblems 2-3: the extreme polyline through a
                    given point on a band border
+  detect_angle_through / brute_angle_through
+                   Sec. 2.3 Subproblem 3: through a given point with the bend angle
   detect_two / brute_apart
                    Sec. 3: two different extreme polylines (suppression on x_0)
   detect_horizontal  Sec. 3, Fig. 7: mostly horizontal polylines (transposition)
@@ -133,6 +135,14 @@ def _load():
                                                     + [_I32P, _I32P,
                                                        ctypes.POINTER(ctypes.c_long)])
             lib.oracle_brute_padded_f64.restype = ctypes.c_double
+            lib.oracle_detect_angle_through_f64.argtypes = ([_F64P] + [ctypes.c_int] * 4
+                                                            + [ctypes.c_double, ctypes.c_int,
+                                                               ctypes.c_int, _I32P, _I32P])
+            lib.oracle_detect_angle_through_f64.restype = ctypes.c_double
+            lib.oracle_brute_angle_through_f64.argtypes = ([_F64P] + [ctypes.c_int] * 3
+                                                           + [ctypes.c_double, ctypes.c_int,
+                                                              ctypes.c_int, _I32P, _I32P])
+            lib.oracle_brute_angle_through_f64.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -474,3 +484,31 @@ def brute_padded(img, k: int, B: int):
                                         _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32),
                                         ctypes.byref(visited))
     return xs, ds, s, visited.value
+
+
+def detect_angle_through(img, k: int, r: int, gamma: float, j: int, xp: int):
+    """Subproblem 3: the best polyline through (xp, j*n) with bend angles at
+    most gamma, on the row-smoothed image: (x[k+1], d[k], score)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    if not (0 <= j <= k and 0 <= xp < w):
+        raise ValueError("point outside the image")
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_angle_through_f64(_p(img, ctypes.c_double), h, w, k, int(r),
+                                                float(gamma), int(j), int(xp),
+                                                _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def brute_angle_through(img, k: int, gamma: float, j: int, xp: int):
+    """Brute force over polylines with x_j = xp passing the direct angle
+    test, on the image as given (smooth it first for r > 0)."""
+    img = _f64(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_brute_angle_through_f64(_p(img, ctypes.c_double), h, w, k, float(gamma),
+                                               int(j), int(xp), _p(xs, ctypes.c_int32),
+                                               _p(ds, ctypes.c_int32))
+    return xs, ds, s

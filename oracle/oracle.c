@@ -1000,3 +1000,126 @@ double oracle_brute_padded_f64(const double *img, int h, int w, int k, int B, in
     if (visited) *visited = count;
     return best;
 }
+
+/* ---------------------------------------------------------------------------
+ * Subproblem 3 with the bend-angle window (Sec. 2.3): the extreme polyline
+ * through P = (xp, j*n) whose consecutive links bend by at most gamma, on the
+ * row-smoothed image (r = 0: no smoothing).  As oracle_dp_through_f64 with the
+ * angle windows lohi of oracle_angle_window.
+ * ------------------------------------------------------------------------ */
+int oracle_dp_angle_through_f64(const double *H, int h, int w, int k, const int32_t *lohi,
+                                int j, int xp, double *V) {
+    if (k < 1 || h % k != 0 || j < 0 || j > k || xp < 0 || xp >= w) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    for (int b = k - 1; b >= 0; --b)
+        for (int d = -(n - 1); d <= n - 1; ++d)
+            for (int x = 0; x < w; ++x) {
+                double *out = &V[((size_t)b * D + (d + n - 1)) * w + x];
+                int xn = x + d;
+                int off_point = (b == j && x != xp) || (j == k && b == k - 1 && xn != xp);
+                if (xn < 0 || xn >= w || off_point) {
+                    *out = ORACLE_NEG;
+                    continue;
+                }
+                double hv = hough_at_f64(H, n, W, b, x, d);
+                if (b == k - 1) {
+                    *out = hv;
+                    continue;
+                }
+                double best = ORACLE_NEG;
+                for (int e = lohi[2 * (d + n - 1)]; e <= lohi[2 * (d + n - 1) + 1]; ++e) {
+                    double v = V[((size_t)(b + 1) * D + (e + n - 1)) * w + xn];
+                    if (v > best) best = v;
+                }
+                *out = (best == ORACLE_NEG) ? ORACLE_NEG : hv + best;
+            }
+    return 0;
+}
+
+double oracle_detect_angle_through_f64(const double *img, int h, int w, int k, int r,
+                                       double gamma, int j, int xp, int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    double *S = (double *)malloc(sizeof(double) * (size_t)h * w);
+    double *H = (double *)malloc(sizeof(double) * (size_t)k * 2 * n * W);
+    double *V = (double *)malloc(sizeof(double) * (size_t)k * (2 * n - 1) * w);
+    int32_t *lohi = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * n - 1));
+    double s = NAN;
+    if (S && H && V && lohi && oracle_gauss_rows_f64(img, h, w, r, S) == 0 &&
+        oracle_angle_window(n, gamma, lohi) == 0) {
+        oracle_fht_recursive_f64(S, h, w, k, H);
+        if (oracle_dp_angle_through_f64(H, h, w, k, lohi, j, xp, V) == 0)
+            s = oracle_backtrack_angle_f64(V, h, w, k, lohi, xs, ds);
+    }
+    free(S);
+    free(H);
+    free(V);
+    free(lohi);
+    return s;
+}
+
+/* Brute force: every polyline with x_j = xp whose bends pass the direct
+ * angle test (tiny images; the image given is the one scored). */
+typedef struct {
+    const double *img;
+    int h, w, k, n, j, xp;
+    double gamma;
+    int32_t *cur_d;
+    int cur_x0;
+    double best;
+    int32_t *best_x;
+    int32_t *best_d;
+} brute_angle_through_state;
+
+static void brute_angle_through_rec(brute_angle_through_state *st, int i, int x) {
+    if (i == st->j && x != st->xp) return;
+    if (i == st->k) {
+        double sc = oracle_path_score_f64(st->img, st->h, st->w, st->k, st->cur_x0, st->cur_d);
+        if (sc > st->best) {
+            st->best = sc;
+            int xx = st->cur_x0;
+            for (int q = 0; q < st->k; ++q) {
+                st->best_x[q] = xx;
+                st->best_d[q] = st->cur_d[q];
+                xx += st->cur_d[q];
+            }
+            st->best_x[st->k] = xx;
+        }
+        return;
+    }
+    int n = st->n;
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        if (i > 0 && fabs(atan((double)d / n) - atan((double)st->cur_d[i - 1] / n)) > st->gamma)
+            continue;
+        if (x + d < 0 || x + d >= st->w) continue;
+        st->cur_d[i] = d;
+        brute_angle_through_rec(st, i + 1, x + d);
+    }
+}
+
+double oracle_brute_angle_through_f64(const double *img, int h, int w, int k, double gamma, int j,
+                                      int xp, int32_t *xs, int32_t *ds) {
+    brute_angle_through_state st;
+    st.img = img;
+    st.h = h;
+    st.w = w;
+    st.k = k;
+    st.n = h / k;
+    st.j = j;
+    st.xp = xp;
+    st.gamma = gamma;
+    st.cur_d = (int32_t *)calloc((size_t)k, sizeof(int32_t));
+    st.best = ORACLE_NEG;
+    st.best_x = xs;
+    st.best_d = ds;
+    for (int i = 0; i <= k; ++i) xs[i] = -1;
+    for (int i = 0; i < k; ++i) ds[i] = 0;
+    for (int x0 = 0; x0 < w; ++x0) {
+        st.cur_x0 = x0;
+        brute_angle_through_rec(&st, 0, x0);
+    }
+    free(st.cur_d);
+    return st.best;
+}

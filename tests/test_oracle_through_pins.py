@@ -75,3 +75,30 @@ def test_through_rejects_points_outside():
         oracle.detect_through(img, 4, 1, 5, 0)
     with pytest.raises(ValueError):
         oracle.detect_through(img, 4, 1, 0, 5)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_angle_through_dp_equals_brute_force(seed):
+    """Subproblem 3 with the bend angle: the masked angle DP against brute
+    force with the direct angle test, with and without smoothing."""
+    h, w, k = [(8, 6, 4), (16, 7, 4), (12, 5, 3), (16, 6, 2)][seed]
+    img = _img(h, w, 1200 + seed, hi=6 if seed % 2 else 256)
+    for r in (0, 1):
+        scored = oracle.gauss_rows(img, r)
+        for gamma in (0.0, 0.2, 0.7, 2.0):
+            for j in range(k + 1):
+                for xp in (0, w // 2, w - 1):
+                    x, d, s = oracle.detect_angle_through(img, k, r, gamma, j, xp)
+                    bx, bd, bs = oracle.brute_angle_through(scored, k, gamma, j, xp)
+                    assert s == bs, (seed, r, gamma, j, xp)
+                    assert list(x) == list(bx) and list(d) == list(bd)
+                    assert x[j] == xp
+
+
+def test_angle_through_reduces_to_the_integer_through_query():
+    """gamma >= pi/2 admits every bend: the unrestricted through query."""
+    img = _img(32, 20, 1300)
+    for j, xp in ((0, 3), (2, 10), (4, 19)):
+        a = oracle.detect_angle_through(img, 4, 0, 2.0, j, xp)
+        b = oracle.detect_through(img, 4, 14, j, xp)
+        assert a[2] == b[2] and list(a[0]) == list(b[0]) and list(a[1]) == list(b[1])
