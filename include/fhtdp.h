@@ -221,6 +221,16 @@ int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pi
  *          bytes (0 for invalid arguments).  Outputs as for fhtdp_backtrack.
  * ---------------------------------------------------------------------- */
 size_t fhtdp_through_workspace_bytes(int dtype, int h, int w, int k);
+
+/* Subproblem 3 with the bend angle (Sec. 2.3): the best polyline through P =
+ * (xp, j*n) whose consecutive links bend by at most gamma, on the image with
+ * its rows smoothed (half-width r; r = 0 is none).  r, gamma, dtype and the
+ * score as for fhtdp_detect_polyline_angle, j and xp as for
+ * fhtdp_detect_through_point; ws of at least fhtdp_angle_workspace_bytes(). */
+int fhtdp_detect_through_point_angle(const void *img, int dtype, int h, int w, int pitch, int k,
+                                     int r, double gamma, int j, int xp, int32_t *x_out,
+                                     int32_t *d_out, void *score_out, void *ws, size_t ws_bytes,
+                                     cudaStream_t stream);
 int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pitch, int k, int B,
                                int j, int xp, int32_t *x_out, int32_t *d_out, void *score_out,
                                void *ws, size_t ws_bytes, cudaStream_t stream);

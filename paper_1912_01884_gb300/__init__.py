@@ -88,6 +88,10 @@ _SIGS = {
     "fhtdp_through_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 4),
     "fhtdp_detect_through_point": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 8
                                    + [ctypes.c_void_p] * 4 + [ctypes.c_size_t, ctypes.c_void_p]),
+    "fhtdp_detect_through_point_angle": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
+                                         + [ctypes.c_double, ctypes.c_int, ctypes.c_int]
+                                         + [ctypes.c_void_p] * 4
+                                         + [ctypes.c_size_t, ctypes.c_void_p]),
     "fhtdp_detect_polyline_padded": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                                      + [ctypes.c_void_p] * 4
                                      + [ctypes.c_size_t, ctypes.c_void_p]),
@@ -535,4 +539,26 @@ def detect_polyline_padded(img, k: int, B: int, out=None, ws=None, stream=None):
     _check(lib().fhtdp_detect_polyline_padded(img.data_ptr(), code, h, w, pitch, k, B,
                                               x.data_ptr(), d.data_ptr(), score.data_ptr(),
                                               ws.data_ptr(), ws.numel(), _stream(stream)))
+    return x, d, score
+
+
+def detect_through_point_angle(img, k: int, r: int, gamma: float, j: int, xp: int, out=None,
+                               ws=None, stream=None):
+    """Subproblem 3: the best polyline through (xp, j * h/k) with bend angles
+    at most gamma, rows smoothed with half-width r (uint8 or int32 image)."""
+    torch = _torch()
+    h, w, pitch = _image(img)
+    code = _int_image_code(img)
+    need = angle_workspace_bytes(code, h, w, k, r)
+    if need == 0:   # invalid arguments: let the library name the problem
+        _check(lib().fhtdp_detect_through_point_angle(None, code, h, w, pitch, k, int(r),
+                                                      float(gamma), int(j), int(xp), None, None,
+                                                      None, None, 0, _stream(stream)))
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=img.device)
+    x, d, score = out if out is not None else _outputs(k, code, img.device)
+    _check(lib().fhtdp_detect_through_point_angle(img.data_ptr(), code, h, w, pitch, k, int(r),
+                                                  float(gamma), int(j), int(xp), x.data_ptr(),
+                                                  d.data_ptr(), score.data_ptr(), ws.data_ptr(),
+                                                  ws.numel(), _stream(stream)))
     return x, d, score

@@ -49,9 +49,11 @@ size_t angle_workspace_bytes(const Shape &s) {
     return kAngleHead + smooth_bytes(s) + 2 * round_up(hough);
 }
 
+// pm (optional): Subproblem 3, the polyline must pass the point (the DP
+// marks P's band off the point dead).
 int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
                  const WindowTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
-                 void *ws, cudaStream_t stream) {
+                 void *ws, cudaStream_t stream, const PointMask *pm) {
     char *base = (char *)ws;
     unsigned long long *key = (unsigned long long *)base;
     int32_t *smooth = (int32_t *)(base + kAngleHead);
@@ -79,7 +81,7 @@ int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
                                               stream);
         if (!st) st = launch_fht_stages<int32_t, int32_t>(smooth, s.w, s, H, tmp, stream);
     }
-    if (!st) st = launch_dp_window<int32_t>(H, s, t, stream);
+    if (!st) st = launch_dp_window<int32_t>(H, s, t, stream, pm);
     if (!st) st = launch_backtrack_angle_key(H, s, t, key, x_out, d_out, score_out, stream);
     return st;
 }

@@ -274,6 +274,33 @@ int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pi
                         stream);
 }
 
+int fhtdp_detect_through_point_angle(const void *img, int dtype, int h, int w, int pitch, int k,
+                                     int r, double gamma, int j, int xp, int32_t *x_out,
+                                     int32_t *d_out, void *score_out, void *ws, size_t ws_bytes,
+                                     cudaStream_t stream) {
+    g_last_error[0] = 0;
+    Shape s;
+    int st = check_angle_common(dtype, h, w, k, gamma, &s);
+    if (st) return st;
+    if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
+    st = check_gauss(dtype, h, r);
+    if (st) return st;
+    if (j < 0 || j > k || xp < 0 || xp >= w)
+        return set_error(FHTDP_EINVAL, "point (%d, border %d) outside [0, %d) x [0, %d]", xp, j,
+                         w, k);
+    if (!img || !x_out || !d_out || !score_out)
+        return set_error(FHTDP_EINVAL, "null image or output pointer");
+    size_t need = angle_workspace_bytes(s);
+    if (!ws || ws_bytes < need)
+        return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
+                         ws ? ws_bytes : (size_t)0);
+    WindowTable t;
+    make_angle_table(s.n, gamma, &t);
+    const PointMask pm{j, xp};
+    return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, (int32_t *)score_out, ws,
+                        stream, &pm);
+}
+
 // ---------------------------------------------------------------------------
 // Subproblems 2-3: the extreme polyline through a given point.
 size_t fhtdp_through_workspace_bytes(int dtype, int h, int w, int k) {

@@ -127,6 +127,6 @@ int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
                    void *ws, cudaStream_t stream);
 int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
                  const WindowTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
-                 void *ws, cudaStream_t stream);
+                 void *ws, cudaStream_t stream, const PointMask *pm = nullptr);
 
 }  // namespace fhtdp

@@ -190,3 +190,16 @@ def test_padded_rejects_bad_arguments_before_launch(lib):
     r = L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 10, 4, 2, fake, fake, fake, fake, 64,
                                        None)
     assert r == 2
+
+
+def test_through_point_angle_rejects_bad_arguments_before_launch(lib):
+    L = lib.lib()
+    fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
+    outs = (fake, fake, fake, fake, 1 << 30, None)
+    f = L.fhtdp_detect_through_point_angle
+    assert f(fake, 0, 64, 10, 10, 4, 2, 0.3, 5, 0, *outs) == 1       # border > k
+    assert f(fake, 0, 64, 10, 10, 4, 2, 0.3, 1, 10, *outs) == 1      # xp >= w
+    assert f(fake, 0, 64, 10, 10, 4, 2, -0.3, 1, 1, *outs) == 1
+    assert f(fake, 0, 64, 10, 10, 4, 13, 0.3, 1, 1, *outs) == 1
+    assert f(fake, 2, 64, 10, 10, 4, 2, 0.3, 1, 1, *outs) == 1
+    assert f(fake, 0, 64, 10, 10, 4, 2, 0.3, 1, 1, fake, fake, fake, fake, 64, None) == 2

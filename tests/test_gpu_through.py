@@ -84,3 +84,26 @@ def test_through_point_rejects_bad_arguments_on_device(lib):
             lib.detect_through_point(img, *args)
     with pytest.raises(TypeError):
         lib.detect_through_point(img.float(), 4, 2, 1, 3)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:8])
+@pytest.mark.parametrize("gamma", [0.0, 0.2, 0.8])
+def test_through_point_with_bend_angle_matches_oracle(lib, shape, gamma):
+    """Subproblem 3 with the bend angle, rows smoothed with r = 1."""
+    h, w, k = shape
+    img = _img(h, w, "u8", 13 * h + w)
+    for j in sorted({0, k // 2, k}):
+        for xp in sorted({0, w // 2, w - 1}):
+            x, d, s = lib.detect_through_point_angle(to_device(img), k, 1, gamma, j, xp)
+            xo, do, so = oracle.detect_angle_through(img, k, 1, gamma, j, xp)
+            assert list(x.cpu().numpy()) == list(xo) and list(d.cpu().numpy()) == list(do)
+            assert int(s.cpu().numpy()[0]) == so
+            assert x.cpu().numpy()[j] == xp
+
+
+def test_through_point_with_bend_angle_2048x2048_full_size(lib):
+    wl = synth.bent_edges(0)
+    xp = int(wl.planted[1][8 * 128])
+    x, d, s = lib.detect_through_point_angle(to_device(wl.img), 16, 2, 0.17453292519943295, 8, xp)
+    xo, do, so = oracle.detect_angle_through(wl.img, 16, 2, 0.17453292519943295, 8, xp)
+    assert list(x.cpu().numpy()) == list(xo) and int(s.cpu().numpy()[0]) == so
