@@ -34,9 +34,11 @@ __device__ __forceinline__ Acc vmax(Acc a, Acc b) {
 }
 
 // Continuation windows of the read-back: the integer bend limit |e - d| <= B,
-// or the bend-angle table of the main problem.
+// or the bend-angle table of the main problem.  B is clamped to 2n-2 (a wider
+// limit admits nothing more), so d +/- B never overflows.
 struct BendWin {
     int B, n;
+    __host__ __device__ BendWin(int b, int nn) : B(b < 2 * nn - 2 ? b : 2 * nn - 2), n(nn) {}
     __device__ int lo(int d) const { return max(d - B, -(n - 1)); }
     __device__ int hi(int d) const { return min(d + B, n - 1); }
 };
@@ -379,6 +381,7 @@ int launch_backtrack_key(const Acc *V, const Shape &s, int B, unsigned long long
 
 void make_bend_table(int n, int B, WindowTable *t) {
     const int D = 2 * n - 1;
+    if (B > D - 1) B = D - 1;   // a wider limit admits nothing more (and 2B + 1 cannot overflow)
     for (int i = 0; i < kMaxD; ++i) {
         const int d = i - (n - 1);
         t->lo[i] = (int16_t)(i < D ? (d - B > -(n - 1) ? d - B : -(n - 1)) : 0);

@@ -308,3 +308,22 @@ def test_batch_mixed_sizes_including_256_row_bands(lib):
     assert any(s[0] // s[2] == 256 for s in picked)
     wls = [synth.plain_uniform(100 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(picked)]
     _batch_parity(lib, wls)
+
+
+@pytest.mark.parametrize("shape", [(512, 300, 2), (256, 256, 4), (96, 77, 3)])
+def test_huge_bend_limit_equals_the_unrestricted_dp(lib, shape):
+    """B = 2^31 - 1 admits every continuation, like B = 2n - 2, on the
+    standalone calls (256-row bands included) and the fused engine."""
+    h, w, k = shape
+    n = h // k
+    img = _img(shape, "u8", 5 * h + w)
+    big = 2**31 - 1
+    x, d, s = lib.detect_polyline(to_device(img), k, big)
+    xr, dr, sr = lib.detect_polyline(to_device(img), k, 2 * n - 2)
+    assert list(x.cpu().numpy()) == list(xr.cpu().numpy()) and int(s.cpu()[0]) == int(sr.cpu()[0])
+    H = lib.fht_bands(to_device(img), k)
+    V = lib.polyline_dp(H, h, w, k, big)
+    xb, db, sb = lib.backtrack(V, h, w, k, big)
+    xo, do, so = oracle.detect(img, k, 2 * n - 2)
+    assert list(xb.cpu().numpy()) == list(xo) and list(db.cpu().numpy()) == list(do)
+    assert int(sb.cpu().numpy()[0]) == int(so)
