@@ -77,10 +77,11 @@ WORKLOADS = {
 # launch's traffic is this times its images.  None for other workloads, and
 # to be reset whenever the kernel changes until it is captured again.
 NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (299.827456e6 + 1571.180e6) / 48}
-# DRAM bytes (read + write) of one dp_band_angle_kernel launch on a
-# 2048x2048, k = 16 image (profiles/dp_band_angle_kernel_2048x2048_k16_gamma10.md);
-# the DP stage of one image is k - 1 such launches.
-NCU_TRAFFIC_DP_ANGLE_LAUNCH = 4.144896e6 + 0.0
+# The window DP kernel changed (it now takes any window table and value
+# type) after its ncu capture (profiles/dp_band_angle_kernel_2048x2048_k16_gamma10.md,
+# 4.14 MB per band launch), so the standalone workloads report no traffic
+# until it is captured again.
+NCU_TRAFFIC_DP_WINDOW_LAUNCH = None
 
 
 # The main problem's smoothing half-width and bend angle (the paper's
@@ -732,8 +733,8 @@ def run_standalone(args):
                              % (host.numel() // 2**20, ">" if host.numel() > 129e6 else "<")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": NCU_TRAFFIC_DP_ANGLE_LAUNCH * (k - 1)
-                                    if angle and (h, w, k) == (2048, 2048, 16) else None,
+                         "traffic": NCU_TRAFFIC_DP_WINDOW_LAUNCH * (k - 1)
+                                    if NCU_TRAFFIC_DP_WINDOW_LAUNCH and top != "engine" else None,
                          "peak_kind": peak_kind,
                          "kernel": ("engine_kernel_u8 (one image per launch, the transposed "
                                     "image)" if top == "engine" else
