@@ -281,3 +281,40 @@ def test_windowed_dp_equals_windowed_brute_force(seed):
     # the full window is the unrestricted method
     full = np.tile([-(n - 1), n - 1], (k, 1))
     assert oracle.detect_windowed(img, k, 2, full)[2] == oracle.detect(img, k, 2)[2]
+
+
+def test_hand_example_queries():
+    """The pencil-worked answers of the through-point, two-polyline and
+    bend-angle queries on the 4x3 example (tests/golden/hand_4x3.txt)."""
+    with open(os.path.join(GOLDEN, "hand_4x3.txt")) as f:
+        lines = [l.strip() for l in f if l.strip() and not l.startswith("#")]
+    rows = []
+    it = iter(lines)
+    for l in it:
+        if l.startswith("image"):
+            rows = [[float(v) for v in next(it).split()] for _ in range(int(l.split()[1]))]
+            break
+    img = np.array(rows)
+
+    def fields(l):
+        return dict(kv.split("=") for kv in l.split()[1:])
+
+    checked = 0
+    for l in lines:
+        kind = l.split()[0]
+        if kind not in ("through", "two", "angle"):
+            continue
+        f = fields(l)
+        want_x = [int(v) for v in f["x"].split(",")]
+        want_d = [int(v) for v in f["d"].split(",")]
+        if kind == "through":
+            x, d, s = oracle.detect_through(img, 2, int(f["B"]), int(f["j"]), int(f["xp"]))
+        elif kind == "two":
+            xs, ds, sc = oracle.detect_two(img, 2, int(f["B"]), int(f["sep"]))
+            x, d, s = xs[1], ds[1], sc[1]
+        else:
+            x, d, s = oracle.detect_angle(img, 2, 0, float(f["gamma"]))
+        assert s == float(f["score"]), l
+        assert list(x) == want_x and list(d) == want_d, l
+        checked += 1
+    assert checked == 10
