@@ -7,7 +7,10 @@
  * Hough Transform of each of the k horizontal bands of an image (Sec. 2.1), a
  * bottom-up max-plus dynamic programme over the bands with a bend limit
  * (Sec. 2.2-2.3, Eqs. 3-4), and the read-back of the best k-link polyline
- * (Eq. 5 and the main problem's steps 2-3).
+ * (Eq. 5 and the main problem's steps 2-3); and around it the paper's main
+ * problem with row smoothing and a bend angle (Sec. 2.3), the polyline
+ * through a given point (Subproblems 2-3), vertices in the zero padding,
+ * mostly horizontal curves and two different polylines (Sec. 3).
  *
  * Conventions shared by every call
  *   h, w      image height and width in pixels; h = k * n with n a power of
@@ -24,8 +27,10 @@
  *   A link of band i joins column x_i on the band's first row to column
  *   x_{i+1} = x_i + d_i on its last row, |d_i| <= n-1 (the paper's shift of
  *   Eq. 1 is n - d_i); the pixels it covers follow the FHT's dyadic pattern.
- *   Every vertex x_0..x_k lies in [0, w).  The bend limit is the integer
- *   range |d_{i+1} - d_i| <= B (B >= 2n-2 means unrestricted, Sec. 2.2).
+ *   Every vertex x_0..x_k lies in [0, w) (fhtdp_detect_polyline_padded:
+ *   [0, w + n)).  The bend limit is the integer range |d_{i+1} - d_i| <= B
+ *   (B >= 2n-2 means unrestricted, Sec. 2.2); the main-problem calls
+ *   (*_angle) limit the bend angle instead (Sec. 2.3, Eqs. 6-7).
  *   Among optimal polylines the lexicographically smallest
  *   (x_0, d_0, ..., d_{k-1}) is returned (d ordered numerically).
  *   Scores are int32 for integer images and float for float images.
