@@ -11,6 +11,16 @@ Calls (same names as the C entry points, without the ``fhtdp_`` prefix):
   polyline_dp(hough, h, w, k, B)     Sec. 2.2-2.3, Eqs. 3-4, in place
   backtrack(V, h, w, k, B)           Eq. 5 / main problem: (x, d, score)
   detect_polyline(img, k, B)         the whole method: (x, d, score)
+  BatchPlan(images, ks, Bs)          many images in one persistent launch
+  angle_window(n, gamma)             Sec. 2.3, Eqs. 6-7: bend-angle windows (host)
+  gauss_rows(img, r)                 main problem step 1: binomial row smoothing
+  polyline_dp_angle / backtrack_angle / detect_polyline_angle(img, k, r, gamma)
+                                     the main problem with the bend angle
+  detect_through_point(img, k, B, j, xp)               Subproblems 2-3
+  detect_through_point_angle(img, k, r, gamma, j, xp)  Subproblem 3, bend angle
+  detect_polyline_padded(img, k, B)  vertices in the zero padding (Sec. 2.2)
+  detect_two_polylines(img, k, B, sep)                 two different polylines
+  detect_polyline_horizontal(img, k, B), transpose(img)  mostly horizontal curves
 The raw ctypes handle with the exact C signatures is ``lib()``.
 """
 from __future__ import annotations
@@ -25,6 +35,11 @@ __all__ = ["load", "lib", "build", "FhtdpError", "fht_bands", "polyline_dp", "ba
            "detect_polyline", "detect_polyline_noalloc", "workspace_bytes", "launch_count",
            "BatchPlan", "Image",
            "workspace_status", "hough_bytes", "fht_workspace_bytes",
+           "angle_window", "gauss_rows", "polyline_dp_angle", "backtrack_angle",
+           "angle_workspace_bytes", "detect_polyline_angle", "through_workspace_bytes",
+           "detect_through_point", "detect_through_point_angle", "detect_polyline_padded",
+           "detect_two_polylines", "horizontal_workspace_bytes", "detect_polyline_horizontal",
+           "transpose",
            "DTYPE_U8", "DTYPE_I32", "DTYPE_F32", "STATUS"]
 
 DTYPE_U8, DTYPE_I32, DTYPE_F32 = 0, 1, 2
