@@ -154,11 +154,21 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
  *     overlaps on the GPU (different streams, or different host threads on the
  *     same device without ordering) race on the array: order them on one
  *     stream.
- *   - fhtdp_workspace_status is not available for these calls. */
+ *   - A bounded device-side wait that gave up is reported by
+ *     fhtdp_detect_polyline_noalloc_status, not by fhtdp_workspace_status. */
 #define FHTDP_NOALLOC_SCRATCH_BYTES (16u << 20)
 int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, int w, int pitch, int k,
                                   int B, int32_t *x_out, int32_t *d_out, void *score_out,
                                   cudaStream_t stream);
+
+/* The status of the last fhtdp_detect_polyline_noalloc run on the current
+ * device, read from the control block of the built-in scratch: FHTDP_OK, or
+ * FHTDP_ETIMEOUT if one of its bounded device-side waits gave up (its outputs
+ * are then undefined).  Synchronises `stream`, on which that run was
+ * enqueued.  The paper has no counterpart; this exists for the same callers
+ * as fhtdp_detect_polyline_noalloc, which have no workspace of their own to
+ * pass to fhtdp_workspace_status. */
+int fhtdp_detect_polyline_noalloc_status(cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * The main problem of Sec. 2.3 (the Welsh M-estimate of a k-link polyline

@@ -32,7 +32,8 @@ import threading
 from . import _build
 
 __all__ = ["load", "lib", "build", "FhtdpError", "fht_bands", "polyline_dp", "backtrack",
-           "detect_polyline", "detect_polyline_noalloc", "workspace_bytes", "launch_count",
+           "detect_polyline", "detect_polyline_noalloc", "noalloc_status", "workspace_bytes",
+           "launch_count",
            "BatchPlan", "Image",
            "workspace_status", "hough_bytes", "fht_workspace_bytes",
            "angle_window", "gauss_rows", "polyline_dp_angle", "backtrack_angle",
@@ -79,6 +80,7 @@ _SIGS = {
     "fhtdp_debug_inject": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong]),
     "fhtdp_detect_polyline_noalloc": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 6
                                       + [ctypes.c_void_p] * 4),
+    "fhtdp_detect_polyline_noalloc_status": (ctypes.c_int, [ctypes.c_void_p]),
     "fhtdp_batch_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_void_p)]),
     "fhtdp_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
@@ -356,6 +358,14 @@ def detect_polyline_noalloc(img, k: int, B: int, out=None, stream=None):
                                                x.data_ptr(), d.data_ptr(), score.data_ptr(),
                                                _stream(stream)))
     return x, d, score
+
+
+def noalloc_status(stream=None) -> int:
+    """Status of the last detect_polyline_noalloc run on the current device
+    (synchronises the stream): 0, or raises FhtdpError (FHTDP_ETIMEOUT when a
+    device-side wait gave up)."""
+    _check(lib().fhtdp_detect_polyline_noalloc_status(_stream(stream)))
+    return 0
 
 
 def detect_polyline(img, k: int, B: int, out=None, ws=None, stream=None):

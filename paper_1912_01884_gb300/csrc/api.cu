@@ -22,6 +22,8 @@ int launched(const char *what) {
     return cuda_status(cudaGetLastError(), what);
 }
 
+void clear_error() { g_last_error[0] = 0; }
+
 int set_error(int code, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);

@@ -53,6 +53,8 @@ constexpr int kMaxGaussR = 12;
 
 // Host helpers (api.cu).
 int set_error(int code, const char *fmt, ...);
+// Clears the calling thread's last error message (every entry point starts so).
+void clear_error();
 // Checks a launch and counts it (fhtdp_launch_count).
 int launched(const char *what);
 int cuda_status(cudaError_t err, const char *what);

@@ -55,6 +55,9 @@ constexpr int kMaxBandFused = 128;     // band heights handled by the fused kern
 constexpr int kMOff = 128;             // column offset of the skewed M layout
 constexpr int kPad = 16;               // dead rows around V (uint8 path)
 constexpr int kFastB = 16;             // largest bend kept entirely in registers
+// After a copy wait gives up, the last bounded wait for that copy to land
+// before its shared memory is reused (about four seconds).
+constexpr long long kDrainCycles = 8000000000LL;
 
 struct ImgDesc {
     CUtensorMap tmap;         // 2-D map of the image (uint8 images), box 128 x n
@@ -1106,11 +1109,15 @@ struct U8Path {
             if (threadIdx.x == 0 && !prefetched)
                 issue_strip(&im.tmap, n, band, x0 / kTile, st, pipe);
             const bool ok = mbar_wait(pipe.bar, pipe.phase, args.wait_cycles);
-            pipe.phase ^= 1u;
             if (!ok) {
+                // The copy may still be in flight: give it a long (bounded)
+                // last chance to land before Hc is written again.
                 if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                mbar_wait(pipe.bar, pipe.phase, kDrainCycles);
+                pipe.phase ^= 1u;
                 return false;
             }
+            pipe.phase ^= 1u;
             const StagedPixels src{st, n, xs, nb * 128 - 8};
             if (n >= 8) {
                 fht_regs8(F, pitch, im, src, x0);
@@ -1313,8 +1320,12 @@ struct U8Path {
         nb_arrive(kBarFhtDone, kCtlSync);   // F is free for the M tile
         const bool msmem = im.use_mtma && band < im.k - 1;
         if (band != 0) dead_pad(Vn, n);
-        if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles) && threadIdx.x == 0)
-            atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+        if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles)) {
+            // As for the strip: the M copy lands in the V rows, so let it
+            // finish (bounded) before V is formed there.
+            if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+            mbar_wait(pipe.mbar, pipe.mphase, kDrainCycles);
+        }
         pipe.mphase ^= 1u;
         const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
         Acc *mnext = (Acc *)im.mbuf[band & 1];

@@ -52,6 +52,7 @@ using namespace fhtdp;
 extern "C" int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, int w, int pitch,
                                              int k, int B, int32_t *x_out, int32_t *d_out,
                                              void *score_out, cudaStream_t stream) {
+    clear_error();
     Shape s;
     if (dtype != FHTDP_U8 && dtype != FHTDP_I32 && dtype != FHTDP_F32)
         return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
@@ -73,4 +74,15 @@ extern "C" int fhtdp_detect_polyline_noalloc(const void *img, int dtype, int h, 
     if (st) return st;
     return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws,
                          kNoallocScratchBytes, stream);
+}
+
+// The status word of the last fhtdp_detect_polyline_noalloc run sits in the
+// control block at the start of the built-in scratch, as it does at the start
+// of a caller workspace; reading it waits for `stream`.
+extern "C" int fhtdp_detect_polyline_noalloc_status(cudaStream_t stream) {
+    clear_error();
+    void *ws = nullptr;
+    int st = scratch_on_current_device(&ws);
+    if (st) return st;
+    return engine_status(ws, stream);
 }
