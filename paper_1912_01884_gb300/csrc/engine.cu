@@ -67,6 +67,7 @@ struct ImgDesc {
     const void *img;
     long long pitch;          // row stride in elements
     int h, w, k, n, log2n, B, tiles;
+    int tw;                   // column tile width of its work items (uint8: 64, 128 or 256)
     long long item0;          // first work item of this image
     void *mbuf[2];            // ping-pong window maxima, [D][mpitch] of Acc
     int mpitch;
@@ -272,7 +273,7 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 struct WsSlot {
     long long item;
     const ImgDesc *im;
-    int band, tile, prefetched;
+    int band, tile, prefetched, T;
 };
 
 struct NextItem {
@@ -793,34 +794,66 @@ __device__ __forceinline__ void store_window(const ImgDesc &im, Acc *mnext, int 
     im.bp[bp_byte(im, band, c + n - 1, x)] = (uint8_t)(dead ? 0 : KO::index(mk));
 }
 
+// Staged uint8 strip of a tile of T columns: columns [x0 - off, x0 + T + off)
+// in boxes of 128 columns x n rows.
+__host__ __device__ inline int strip_off(int n) { return (n + 15) & ~15; }
+__host__ __device__ inline int strip_boxes(int n, int T) {
+    return (T + 2 * strip_off(n) + 127) / 128;
+}
+// One thread: the band strip of (band, tile) through TMA into `st` (the Hc
+// region, free until the compaction), zero-filled outside the image.
+__device__ inline void issue_strip(const CUtensorMap *map, int n, int band, int tile, int T,
+                                   void *st, Pipe &pipe) {
+    const int xs = tile * T - strip_off(n), nb = strip_boxes(n, T);
+    fence_proxy_async_smem();
+    mbar_expect_tx(pipe.bar, (uint32_t)(nb * n * 128));
+    for (int b = 0; b < nb; ++b)
+        tma_load_2d((uint8_t *)st + (size_t)b * n * 128, map, xs + 128 * b, band * n, pipe.bar);
+}
+
+// Largest band height a uint8 work item of T = 128 or 256 columns handles
+// (its shared-memory regions must fit one CTA).
+template <int T>
+__host__ __device__ constexpr int max_band() { return T >= 256 ? 64 : 128; }
+
 // ---------------------------------------------------------------------------
 // uint8 images.  Shared memory: region A holds the FHT strip F, later V in
 // natural displacement order with kPad dead rows on both sides; region Hc
 // holds the compact packed Hough words, later the generic window's S.
-template <typename Key>
+template <typename Key, bool kMulti>
 struct U8Path {
     using Acc = int32_t;
+    // The tile width of an item: im.tw in the kernel for batches with both
+    // widths, the constant kTile otherwise (every index folds at compile time).
+    __device__ static int tw(const ImgDesc &im) { return kMulti ? im.tw : kTile; }
     using KO = KeyOps<int32_t, Key>;
     static constexpr int kRounds = sizeof(Key) == 4 ? 2 : 4;
 
-    // Strip rows hold T + n + 15 loaded words; the merges read up to T + n + 4.
-    __host__ __device__ static int fpitch(int n) { return (kTile + n + 16 + 3) & ~3; }
+    // Tiles are T = 128 or 256 columns (im.tw).  Strip rows hold T + n + 15
+    // loaded words; the merges read up to T + n + 4.
+    __host__ __device__ static int fpitch(int n, int T) { return (T + n + 16 + 3) & ~3; }
     __host__ __device__ static int frows(int n) { return n < 2 ? 2 : n; }
-    __host__ __device__ static size_t a_bytes(int n) {
-        size_t f = (size_t)frows(n) * fpitch(n) * 4;
-        size_t v = (size_t)(2 * n - 1 + 2 * kPad) * kTile * 4;
+    // V (and the M tile under it) is kept in blocks of 128 columns, each
+    // with the 2n-1 displacement rows and kPad dead rows on both sides, so
+    // that the window's column stride is a compile-time constant for every
+    // tile width: V(row, u) at vblock(n) * (u / 128) + row * 128 + u % 128.
+    __host__ __device__ static int vblock(int n) { return (2 * n - 1 + 2 * kPad) * kTile; }
+    template <int T>
+    __device__ static int vat(int n, int row, int u) {
+        if constexpr (T == kTile) return row * kTile + u;
+        return (u >> 7) * vblock(n) + row * kTile + (u & (kTile - 1));
+    }
+    __host__ __device__ static size_t a_bytes(int n, int T) {
+        size_t f = (size_t)frows(n) * fpitch(n, T) * 4;
+        size_t v = (size_t)vblock(n) * (T / kTile) * 4;
         return ((f > v ? f : v) + 127) / 128 * 128;   // TMA destinations are 128-byte aligned
     }
-    __host__ __device__ static size_t hc_bytes(int n) {
-        size_t hc = (size_t)n * kTile * 4;
-        size_t s = (size_t)((2 * n - 1 + kRounds - 1) / kRounds) * kTile * sizeof(Key);
+    __host__ __device__ static size_t hc_bytes(int n, int T) {
+        size_t hc = (size_t)n * T * 4;
+        size_t s = (size_t)((2 * n - 1 + kRounds - 1) / kRounds) * T * sizeof(Key);
         return hc > s ? hc : s;
     }
-    // Hc sits at a fixed offset (the largest band height's region A), so that
-    // the strip of a next item with another band height can be staged there
-    // while the current item still uses region A.
-    __host__ __device__ static size_t hc_offset() { return a_bytes(kMaxBandFused); }
-    static size_t smem_bytes(int) { return hc_offset() + hc_bytes(kMaxBandFused); }
+    __host__ __device__ static size_t hc_offset();
 
     // Four pixels [c, c+4) of a row as one little-endian word, zero outside
     // [0, w).  c is a multiple of 4; `aligned` says rows start on 4 bytes.
@@ -846,7 +879,7 @@ struct U8Path {
     // The packed strip, word u of row y = pixel (y, x0 + u) | pixel
     // (y, x0 + T - 1 - u) << 16 (bands of 1 or 2 rows).
     __device__ static void load_strip(uint32_t *F, int pitch, const ImgDesc &im, int band, int x0) {
-        const int n = im.n, T = kTile;
+        const int n = im.n, T = tw(im);
         const int G = (T + n - 1 + 15) / 16;   // groups of 16 strip columns per row
         const uint8_t *base = (const uint8_t *)im.img + (size_t)band * n * im.pitch;
         const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 16 == 0);
@@ -981,7 +1014,7 @@ struct U8Path {
     // four at 8..11.  Shift s of the sub-band goes to row 8g + brev3(s).
     __device__ static void fht_regs8(uint32_t *F, int pitch, const ImgDesc &im,
                                      const StagedPixels &src, int x0) {
-        const int n = im.n, T = kTile;
+        const int n = im.n, T = tw(im);
         const int C4 = (T + n - 8 + 3) / 4;
         const int tasks = (n / 8) * C4;
         for (int t = threadIdx.x; t < tasks; t += kThreads) {
@@ -1011,7 +1044,7 @@ struct U8Path {
     template <typename Src>
     __device__ static void fht_regs(uint32_t *F, int pitch, const ImgDesc &im, const Src &src,
                                     int x0) {
-        const int n = im.n, T = kTile;
+        const int n = im.n, T = tw(im);
         const int C8 = (T + n - 4 + 7) / 8;   // chunks covering the level-2 width
         const int tasks = (n / 4) * C8;
         const int lane = threadIdx.x & 31;
@@ -1077,37 +1110,20 @@ struct U8Path {
         csync();
     }
 
-    // Staged strip: columns [x0 - noff, x0 + T + noff) in boxes of 128.
-    __host__ __device__ static int strip_off(int n) { return (n + 15) & ~15; }
-    __host__ __device__ static int strip_boxes(int n) {
-        return (kTile + 2 * strip_off(n) + 127) / 128;
-    }
-
     __host__ __device__ static bool strip_by_tma(const ImgDesc &im) {
         return im.use_tma && im.n >= 4;
-    }
-    // One thread: the band strip of (band, tile) through TMA into `st` (the
-    // Hc region, free until the compaction), zero-filled outside the image.
-    __device__ static void issue_strip(const CUtensorMap *map, int n, int band, int tile,
-                                       void *st, Pipe &pipe) {
-        const int xs = tile * kTile - strip_off(n), nb = strip_boxes(n);
-        fence_proxy_async_smem();
-        mbar_expect_tx(pipe.bar, (uint32_t)(nb * n * 128));
-        for (int b = 0; b < nb; ++b)
-            tma_load_2d((uint8_t *)st + (size_t)b * n * 128, map, xs + 128 * b, band * n,
-                        pipe.bar);
     }
 
     // Returns false if the strip copy did not complete in time.
     __device__ static bool fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0,
                                Pipe &pipe, bool prefetched, const LaunchArgs &args) {
-        const int n = im.n, T = kTile, pitch = fpitch(n);
+        const int n = im.n, T = tw(im), pitch = fpitch(n, T);
         bool compact;
         if (strip_by_tma(im)) {
-            const int xs = x0 - strip_off(n), nb = strip_boxes(n);
+            const int xs = x0 - strip_off(n), nb = strip_boxes(n, T);
             uint8_t *st = (uint8_t *)Hc;
             if (threadIdx.x == 0 && !prefetched)
-                issue_strip(&im.tmap, n, band, x0 / kTile, st, pipe);
+                issue_strip(&im.tmap, n, band, x0 / T, T, st, pipe);
             const bool ok = mbar_wait(pipe.bar, pipe.phase, args.wait_cycles);
             if (!ok) {
                 // The copy may still be in flight: give it a long (bounded)
@@ -1164,25 +1180,27 @@ struct U8Path {
         else return w;
     }
     // The kPad dead rows above and below the V rows.
+    template <int T>
     __device__ static void dead_pad(int32_t *Vn, int n) {
-        const int T = kTile, D = 2 * n - 1;
+        const int D = 2 * n - 1;
         const int32_t dead = Dead<int32_t>::value();
         for (int idx = threadIdx.x; idx < 2 * kPad * (T / 4); idx += kThreads) {
-            const int r = idx / (T / 4), u0 = 4 * (idx - r * (T / 4));
+            const int r = idx / (T / 4), u0 = 4 * (idx % (T / 4));
             const int row = r < kPad ? r : r + D;
-            *(int4 *)&Vn[row * T + u0] = make_int4(dead, dead, dead, dead);
+            *(int4 *)&Vn[vat<T>(n, row, u0)] = make_int4(dead, dead, dead, dead);
         }
     }
     // V keys of an interior tile, in place over the M' tile copied by TMA
     // (none in the last band): V key(c) = M'(c) + (H(c) << 9 | 511 - (c + n - 1)).
     // A dead M' (negative) gives a negative key.
+    template <int T>
     __device__ static void form_v_interior(int32_t *Vn, const uint32_t *Hc, int n, bool last) {
-        const int T = kTile, kc = 512 - n;   // 511 - (c + n - 1) = kc - c
+        const int kc = 512 - n;   // 511 - (c + n - 1) = kc - c
         for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
-            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            const int s = idx / (T / 4), u0 = 4 * (idx % (T / 4));
             const uint4 hw = *(const uint4 *)&Hc[s * T + u0];
-            int4 *pp = (int4 *)&Vn[(s + n - 1 + kPad) * T + u0];
-            int4 *pm = (int4 *)&Vn[(n - 1 - s + kPad) * T + (T - 4 - u0)];
+            int4 *pp = (int4 *)&Vn[vat<T>(n, s + n - 1 + kPad, u0)];
+            int4 *pm = (int4 *)&Vn[vat<T>(n, n - 1 - s + kPad, T - 4 - u0)];
             int4 mp = make_int4(0, 0, 0, 0), mm = mp;
             if (!last) {
                 mp = *pp;
@@ -1203,10 +1221,11 @@ struct U8Path {
     }
     // With msmem the M tile was copied by TMA into the V rows (row e of M at
     // V row e + kPad), and V is formed in place; otherwise M is read from L2.
+    template <int T>
     __device__ static unsigned long long form_v(int32_t *Vn, const uint32_t *Hc,
                                                 const ImgDesc &im, int band, int x0,
                                                 const int32_t *mprev, bool msmem) {
-        const int n = im.n, T = kTile;
+        const int n = im.n;
         const bool last = band == im.k - 1;
         const Acc dead = Dead<Acc>::value();
         int wlo, whi;
@@ -1214,6 +1233,7 @@ struct U8Path {
         unsigned long long best = 0;
         // The M loads of a batch of iterations are issued before any of its
         // shared stores, so their L2 round trips overlap.
+        // At most 128 x 128 / 4 or 64 x 256 / 4 tasks: 8 per thread.
         constexpr int kIt = kMaxBandFused * (kTile / 4) / kThreads;
         constexpr int kLB = 4;
         const int tasks = n * (T / 4);
@@ -1224,13 +1244,14 @@ struct U8Path {
 #pragma unroll
         for (int i = 0; i < kLB; ++i) {
             const int idx = threadIdx.x + (b0 + i) * kThreads;
-            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            const int s = idx / (T / 4), u0 = 4 * (idx % (T / 4));
             mpa[i] = make_int4(0, 0, 0, 0);
             mma[i] = mpa[i];
             if (!last && idx < tasks) {
                 if (msmem) {
-                    mpa[i] = *(const int4 *)&Vn[(s + n - 1 + kPad) * T + u0];
-                    if (s > 0) mma[i] = *(const int4 *)&Vn[(n - 1 - s + kPad) * T + T - 4 - u0];
+                    mpa[i] = *(const int4 *)&Vn[vat<T>(n, s + n - 1 + kPad, u0)];
+                    if (s > 0)
+                        mma[i] = *(const int4 *)&Vn[vat<T>(n, n - 1 - s + kPad, T - 4 - u0)];
                 } else {
                     mpa[i] = __ldcg((const int4 *)(mprev + (size_t)(s + n - 1) * im.mpitch +
                                                    kMOff + x0 + u0));
@@ -1244,7 +1265,7 @@ struct U8Path {
         for (int it = 0; it < kLB; ++it) {
             const int idx = threadIdx.x + (b0 + it) * kThreads;
             if (idx >= tasks) break;
-            const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
+            const int s = idx / (T / 4), u0 = 4 * (idx % (T / 4));
             const uint4 hw = *(const uint4 *)&Hc[s * T + u0];
             const uint32_t hws[4] = {hw.x, hw.y, hw.z, hw.w};
             // "+" half: column x0 + u0 + j, displacement +s.
@@ -1292,9 +1313,10 @@ struct U8Path {
                         vm[j] = vm[j] == dead ? dead : KO::make(vm[j], n - 1 - s);
                     }
                 }
-                *(int4 *)&Vn[(s + n - 1 + kPad) * T + u0] = make_int4(vp[0], vp[1], vp[2], vp[3]);
+                *(int4 *)&Vn[vat<T>(n, s + n - 1 + kPad, u0)] =
+                    make_int4(vp[0], vp[1], vp[2], vp[3]);
                 if (s > 0)
-                    *(int4 *)&Vn[(n - 1 - s + kPad) * T + (T - 4 - u0)] =
+                    *(int4 *)&Vn[vat<T>(n, n - 1 - s + kPad, T - 4 - u0)] =
                         make_int4(vm[3], vm[2], vm[1], vm[0]);
             }
         }
@@ -1311,7 +1333,7 @@ struct U8Path {
     // so that every signal to the control warp is still given.
     __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
                                    const LaunchArgs &args, Pipe &pipe, bool prefetched) {
-        const int n = im.n, T = kTile, D = 2 * n - 1;
+        const int n = im.n, T = tw(im), D = 2 * n - 1;
         const int x0 = tile * T;
         uint32_t *F = (uint32_t *)smem;  // the strip, then V
         int32_t *Vn = (int32_t *)smem;
@@ -1319,7 +1341,10 @@ struct U8Path {
         fht(F, Hc, im, band, x0, pipe, prefetched, args);
         nb_arrive(kBarFhtDone, kCtlSync);   // F is free for the M tile
         const bool msmem = im.use_mtma && band < im.k - 1;
-        if (band != 0) dead_pad(Vn, n);
+        if (band != 0) {
+            if (T == kTile) dead_pad<kTile>(Vn, n);
+            else dead_pad<2 * kTile>(Vn, n);
+        }
         if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles)) {
             // As for the strip: the M copy lands in the V rows, so let it
             // finish (bounded) before V is formed there.
@@ -1335,10 +1360,13 @@ struct U8Path {
         const bool interior = sizeof(Key) == 4 && band != 0 && !im.win && (msmem || band == im.k - 1) &&
                               x0 >= n - 1 && x0 + T + n - 2 < im.w;
         unsigned long long best = 0;
-        if (interior)
-            form_v_interior(Vn, Hc, n, band == im.k - 1);
-        else
-            best = form_v(Vn, Hc, im, band, x0, mprev, msmem);
+        if (T == kTile) {
+            if (interior) form_v_interior<kTile>(Vn, Hc, n, band == im.k - 1);
+            else best = form_v<kTile>(Vn, Hc, im, band, x0, mprev, msmem);
+        } else {
+            if (interior) form_v_interior<2 * kTile>(Vn, Hc, n, band == im.k - 1);
+            else best = form_v<2 * kTile>(Vn, Hc, im, band, x0, mprev, msmem);
+        }
         if (band == 0) {
             // The tile's best key; the control warp counts the tile and reads
             // the polyline back after the image's last one.
@@ -1355,17 +1383,19 @@ struct U8Path {
         // Hc is free from here on unless the window reads S from it.
         if (fast) nb_arrive(kBarHcFree, kCtlSync);
 
-        const int u = threadIdx.x % T, qd = threadIdx.x / T;
+        // T / 128 = 1 or 2 column blocks; kQ = 512 / T threads per column.
+        const int lt = T == 256 ? 8 : 7, kq = kThreads >> lt;
+        const int u = threadIdx.x & (T - 1), qd = threadIdx.x >> lt;
         const int x = x0 + u;
         const int B = im.B;   // already clamped to 2n-2
         const int lo = -(n - 1), hi = n - 1;
-        const int32_t *col = Vn + u;
+        const int32_t *col = Vn + vat<2 * kTile>(n, 0, u);   // row stride kTile
         if constexpr (sizeof(Key) == 4) {
             if (B <= kFastB) {
                 // Shared memory holds keys.  V rows [lo - kPad, hi + kPad] exist
                 // (dead outside [lo, hi]), and B <= kPad: the register window
                 // reads them without bounds checks.
-                const int32_t *kcol = col + (n - 1 + kPad) * T;
+                const int32_t *kcol = col + (n - 1 + kPad) * kTile;
                 // M'(x, c) = key & ~511 (negative when dead), bp = its index.
                 Acc *mcol = mnext + (size_t)(n - 1) * im.mpitch + kMOff + x;
                 const int mstep = im.mpitch - 1;
@@ -1373,7 +1403,7 @@ struct U8Path {
                 // multiples of 4 (whole bp words).  Only the consumer band's
                 // allowed displacements are needed; a thread starts at the word
                 // boundary below them (the extra maxima are never read).
-                const int Q = ((D + 3) / 4 + 3) & ~3;
+                const int Q = 4 * (((D + 3) / 4 + kq - 1) / kq);
                 int clo, chi;
                 band_window(im, band - 1, &clo, &chi);
                 const int ea = max(qd * Q, (clo + n - 1) & ~3);
@@ -1390,7 +1420,7 @@ struct U8Path {
                         case 16: window_u8<33>(ca, c1, kcol, ma, mstep, bw, im.w); break;
                         default: {
                             const Key dk = KO::dead();
-                            auto vkey = [&](int e) -> Key { return kcol[e * T]; };
+                            auto vkey = [&](int e) -> Key { return kcol[e * kTile]; };
                             auto emit = [&](int c, Key mk) {
                                 mcol[(long long)c * mstep] = mk & ~511;
                                 im.bp[bp_byte(im, band, c + n - 1, x)] = (uint8_t)(~mk & 255);
@@ -1415,7 +1445,7 @@ struct U8Path {
         {
             auto vkey = [&](int e) -> Key {
                 if (e < lo || e > hi) return KO::dead();
-                const int v = col[(e + n - 1 + kPad) * T];
+                const int v = col[(e + n - 1 + kPad) * kTile];
                 if constexpr (sizeof(Key) == 4) return v;   // stored as keys
                 return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
             };
@@ -1425,9 +1455,9 @@ struct U8Path {
                 const int P1 = lo + ((round + 1) * D) / kRounds - 1;
                 const int span = P1 - P0 + 1;
                 int clo, chi;
-            band_window(im, band - 1, &clo, &chi);
-            const int c0 = max(P0 + (qd * span) / kQ, clo);
-            const int c1 = min(P0 + ((qd + 1) * span) / kQ - 1, chi);
+                band_window(im, band - 1, &clo, &chi);
+                const int c0 = max(P0 + (qd * span) / kq, clo);
+                const int c1 = min(P0 + ((qd + 1) * span) / kq - 1, chi);
                 const int srow0 = P0 - B;   // S(e) at row e - srow0
                 auto sput = [&](int e, Key v) { S[(size_t)(e - srow0) * T + u] = v; };
                 auto sget = [&](int e) { return S[(size_t)(e - srow0) * T + u]; };
@@ -1441,15 +1471,39 @@ struct U8Path {
         nb_arrive(kBarWinDone, kCtlSync);
     }
 
+};
+
+// Shared-memory layout common to the uint8 items of every tile width: region
+// A from offset 0, Hc at a fixed offset (the largest region A), so that the
+// strip of a next item with another band height or tile width can be staged
+// in Hc while the current item still uses region A.
+template <typename Key>
+__host__ __device__ size_t u8_hc_offset() {
+    const size_t a = U8Path<Key, true>::a_bytes(max_band<128>(), 128);
+    const size_t b = U8Path<Key, true>::a_bytes(max_band<256>(), 256);
+    return a > b ? a : b;
+}
+template <typename Key>
+size_t u8_smem_bytes() {
+    const size_t a = U8Path<Key, true>::hc_bytes(max_band<128>(), 128);
+    const size_t b = U8Path<Key, true>::hc_bytes(max_band<256>(), 256);
+    return u8_hc_offset<Key>() + (a > b ? a : b);
+}
+template <typename Key, bool kMulti>
+__host__ __device__ size_t U8Path<Key, kMulti>::hc_offset() { return u8_hc_offset<Key>(); }
+
+// The control warp of the uint8 engine (items of any tile width).
+template <typename Key>
+struct U8Ctl {
     // An item as the control warp sees it.
     struct Ctrl {
         long long item;
         const ImgDesc *im;
-        int band, tile, n;
+        int band, tile, n, T;
         bool tma;   // its strip goes through TMA
     };
     __device__ static Ctrl decode(const LaunchArgs &args, long long item) {
-        Ctrl c{item, nullptr, 0, 0, 0, false};
+        Ctrl c{item, nullptr, 0, 0, 0, 128, false};
         if (item >= args.items) return c;
         if (args.many) {
             const Item it = args.order[item];
@@ -1458,22 +1512,25 @@ struct U8Path {
             c.tile = it.tile;
             c.n = it.nflags & 0xffff;
             c.tma = ((it.nflags >> 16) & 1) && c.n >= 4;
+            c.T = 64 << ((it.nflags >> 17) & 3);
         } else {
             c.im = &args.one;
             c.band = args.one.k - 1 - (int)(item / args.one.tiles);
             c.tile = (int)(item % args.one.tiles);
             c.n = args.one.n;
             c.tma = args.one.use_tma && c.n >= 4;
+            c.T = args.one.tw;
         }
         return c;
     }
     // Lane 0: the item's strip copy into Hc, and its slot for the compute warps.
     __device__ static void hand_over(const Ctrl &c, WsSlot *slot, void *Hc, Pipe &pipe) {
-        if (c.im && c.tma) issue_strip(&c.im->tmap, c.n, c.band, c.tile, Hc, pipe);
+        if (c.im && c.tma) issue_strip(&c.im->tmap, c.n, c.band, c.tile, c.T, Hc, pipe);
         slot->item = c.item;
         slot->im = c.im;
         slot->band = c.band;
         slot->tile = c.tile;
+        slot->T = c.T;
         slot->prefetched = c.im && c.tma;
     }
 
@@ -1485,7 +1542,7 @@ struct U8Path {
     __device__ static void control(const LaunchArgs &args, unsigned char *smem, WsSlot *slot,
                                    Pipe &pipe) {
         const int lane = threadIdx.x & 31;
-        uint32_t *Hc = (uint32_t *)(smem + hc_offset());
+        uint32_t *Hc = (uint32_t *)(smem + u8_hc_offset<Key>());
         int32_t *Vn = (int32_t *)smem;
         long long first = 0;
         if (lane == 0) first = atomicAdd(&args.ctl->queue, 1);
@@ -1514,9 +1571,11 @@ struct U8Path {
                 if (im.use_mtma && cur.band < im.k - 1) {
                     fence_proxy_async_global();
                     fence_proxy_async_smem();
-                    mbar_expect_tx(pipe.mbar, (uint32_t)(kTile * D * 4));
-                    tma_load_2d(Vn + kPad * kTile, &im.mtmap, kMOff + cur.tile * kTile,
-                                ((cur.band + 1) & 1) * D, pipe.mbar);
+                    mbar_expect_tx(pipe.mbar, (uint32_t)(cur.T * D * 4));
+                    for (int b = 0; b < cur.T / kTile; ++b)
+                        tma_load_2d(Vn + b * U8Path<Key, true>::vblock(n) + kPad * kTile, &im.mtmap,
+                                    kMOff + cur.tile * cur.T + b * kTile,
+                                    ((cur.band + 1) & 1) * D, pipe.mbar);
                 } else {
                     mbar_arrive(pipe.mbar);
                 }
@@ -1535,7 +1594,7 @@ struct U8Path {
                     }
                 } else {
                     __threadfence();
-                    if (atomicAdd(im.done, 1) == im.tiles - 1) readback<Acc>(im, args);
+                    if (atomicAdd(im.done, 1) == im.tiles - 1) readback<int32_t>(im, args);
                 }
             }
             cur = next;
@@ -1785,10 +1844,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 // The uint8 engine: four compute warpgroups (112 registers a thread) and a
 // control warp (32 registers; the rest of its warpgroup exits at once).  The
 // register split adds up to the launch's 640 x 96.
-template <typename Key>
+template <typename Key, bool kMulti>
 __global__ void __launch_bounds__(kWsThreads, 1)
     engine_kernel_u8(const __grid_constant__ LaunchArgs args) {
-    using P = U8Path<Key>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_mbar;
@@ -1806,11 +1864,12 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             nb_sync(kBarNext, kCtlSync);
             const WsSlot sl = s_slot;
             if (sl.item >= args.items) break;
-            P::process(*sl.im, sl.band, sl.tile, smem_raw, args, pipe, sl.prefetched != 0);
+            U8Path<Key, kMulti>::process(*sl.im, sl.band, sl.tile, smem_raw, args, pipe,
+                                         sl.prefetched != 0);
         }
     } else {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 32;" ::: "memory");
-        if (threadIdx.x < kCtlSync) P::control(args, smem_raw, &s_slot, pipe);
+        if (threadIdx.x < kCtlSync) U8Ctl<Key>::control(args, smem_raw, &s_slot, pipe);
     }
 }
 
@@ -1827,6 +1886,7 @@ struct ImgPlan {
     fhtdp_image io;
     Shape s;
     int B, tiles, mpitch;
+    int T;                      // column tile width of its work items
     long long item0;
     size_t flags, best, done;   // offsets in the counter region
     size_t m0, m1, bp;          // offsets in the data region
@@ -1839,18 +1899,26 @@ struct RunLayout {
     size_t data_off, total;
     long long items;
     int max_n, max_h;
+    bool multi_tile;     // some image's tiles are not kTile wide
 };
 
-int tiles_of(const Shape &s) { return (s.w + kTile - 1) / kTile; }
+// Column tile width of an image's work items: uint8 images with bands of at
+// most 64 rows take 256 columns (more work per item and fewer items for the
+// short bands), the others 128.
+int default_tile(int dtype, int n) { return dtype == FHTDP_U8 && n <= 64 ? 256 : kTile; }
+
+int tiles_of(const Shape &s, int T) { return (s.w + T - 1) / T; }
+// Queue-entry code of a tile width: T = 64 << code.
+int tile_code(int T) { return T == 256 ? 2 : T == 64 ? 0 : 1; }
 
 RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
     RunLayout L{};
     size_t off = sizeof(Ctl);
     long long items = 0;
     for (auto &p : imgs) {
-        p.tiles = tiles_of(p.s);
+        p.tiles = tiles_of(p.s, p.T);
         // Row reads of M go up to 4 words past the last tile's columns.
-        p.mpitch = (int)align_up((size_t)kMOff + p.s.w + kTile + 4, 32);
+        p.mpitch = (int)align_up((size_t)kMOff + p.s.w + p.T + 4, 32);
         p.item0 = items;
         items += (long long)p.s.k * p.tiles;
         p.flags = off;
@@ -1860,6 +1928,7 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
         p.done = off;
         off = align_up(off + 4, 8);
         L.max_n = std::max(L.max_n, p.s.n);
+        if (p.T != kTile) L.multi_tile = true;
         L.max_h = std::max(L.max_h, p.s.h);
     }
     L.zero_bytes = align_up(off, 256);
@@ -1946,6 +2015,7 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     im.log2n = p.s.log2n;
     im.B = p.B;
     im.tiles = p.tiles;
+    im.tw = p.T;
     im.item0 = p.item0;
     char *data = ws + L.data_off;
     im.mbuf[0] = data + p.m0;
@@ -2000,19 +2070,13 @@ int launch_kernel(const LaunchArgs &args, int max_n, cudaStream_t stream) {
 }
 
 template <typename Key>
-int launch_kernel_u8(const LaunchArgs &args, int max_n, cudaStream_t stream) {
-    using P = U8Path<Key>;
-    const size_t smem = P::smem_bytes(max_n);
-    auto kern = engine_kernel_u8<Key>;
-    static int smem_set = 0;   // dynamic shared memory enabled for this kernel
-    if ((int)smem > smem_set) {
-        int st = cuda_status(cudaFuncSetAttribute(kern,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P::smem_bytes(kMaxBandFused)),
-                             "cudaFuncSetAttribute");
-        if (st) return st;
-        smem_set = (int)P::smem_bytes(kMaxBandFused);
-    }
+int launch_kernel_u8(const LaunchArgs &args, bool multi, cudaStream_t stream) {
+    const size_t smem = u8_smem_bytes<Key>();
+    auto kern = multi ? engine_kernel_u8<Key, true> : engine_kernel_u8<Key, false>;
+    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "cudaFuncSetAttribute");
+    if (st) return st;
     long long grid = num_sms();
     if (grid > args.items) grid = args.items;
     if (grid < 1) grid = 1;
@@ -2020,13 +2084,15 @@ int launch_kernel_u8(const LaunchArgs &args, int max_n, cudaStream_t stream) {
     return launched("engine_kernel_u8");
 }
 
-int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, cudaStream_t stream) {
+// `multi`: the run holds items of more than one tile width.
+int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, bool multi,
+             cudaStream_t stream) {
     switch (dtype) {
         case FHTDP_U8:
             // 32-bit keys: values below 2^22, and dead keys (negative) that
             // take on at most 512 * (255 h + k) over the bands stay negative.
-            if (256LL * max_h < (1LL << 22)) return launch_kernel_u8<int32_t>(args, max_n, stream);
-            return launch_kernel_u8<long long>(args, max_n, stream);
+            if (256LL * max_h < (1LL << 22)) return launch_kernel_u8<int32_t>(args, multi, stream);
+            return launch_kernel_u8<long long>(args, multi, stream);
         case FHTDP_I32:
             return launch_kernel<int32_t, int32_t, long long>(args, max_n, stream);
         default:
@@ -2093,9 +2159,10 @@ int run_fallback(const void *img, int dtype, int pitch, const Shape &s, int B, i
     return st;
 }
 
-ImgPlan single_plan(const void *img, int pitch, const Shape &s, int B, int32_t *x_out,
-                    int32_t *d_out, void *score_out) {
+ImgPlan single_plan(int dtype, const void *img, int pitch, const Shape &s, int B,
+                    int32_t *x_out, int32_t *d_out, void *score_out) {
     ImgPlan p{};
+    p.T = default_tile(dtype, s.n);
     p.io.img = img;
     p.io.h = s.h;
     p.io.w = s.w;
@@ -2173,9 +2240,8 @@ std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target
 }
 
 size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
-    (void)dtype;
     if (s.n > kMaxBandFused) return 256 + 2 * (size_t)s.k * 2 * s.n * s.W * 4;
-    std::vector<ImgPlan> one{single_plan(nullptr, s.w, s, B, nullptr, nullptr, nullptr)};
+    std::vector<ImgPlan> one{single_plan(dtype, nullptr, s.w, s, B, nullptr, nullptr, nullptr)};
     return plan_layout(one, false).total;
 }
 
@@ -2184,7 +2250,7 @@ int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, 
     (void)ws_bytes;
     if (s.n > kMaxBandFused)
         return run_fallback(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, stream);
-    std::vector<ImgPlan> one{single_plan(img, pitch, s, B, x_out, d_out, score_out)};
+    std::vector<ImgPlan> one{single_plan(dtype, img, pitch, s, B, x_out, d_out, score_out)};
     RunLayout L = plan_layout(one, false);
     char *base = (char *)ws;
     int st = cuda_status(cudaMemsetAsync(base, 0, L.zero_bytes, stream), "cudaMemsetAsync");
@@ -2193,7 +2259,7 @@ int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, 
     args.one = make_desc(one[0], L, base, dtype);
     args.many = nullptr;
     args.order = nullptr;
-    return dispatch(dtype, L.max_h, args, L.max_n, stream);
+    return dispatch(dtype, L.max_h, args, L.max_n, L.multi_tile, stream);
 }
 
 int engine_status(const void *ws, cudaStream_t stream) {
@@ -2223,7 +2289,7 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
                              "image %d: invalid (h=%d w=%d pitch=%d k=%d B=%d or null pointer)",
                              i, io.h, io.w, io.pitch, io.k, io.B);
         }
-        ImgPlan p = single_plan(io.img, io.pitch, s, io.B, io.x_out, io.d_out, io.score_out);
+        ImgPlan p = single_plan(dtype, io.img, io.pitch, s, io.B, io.x_out, io.d_out, io.score_out);
         p.io.d_window = io.d_window;
         if (io.d_window && s.n > kMaxBandFused) {
             delete plan;
@@ -2270,7 +2336,8 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
 // Each queue entry carries its image's band height and TMA flag.
 void set_nflags(BatchPlan *plan) {
     for (Item &it : plan->order)
-        it.nflags = plan->imgs[it.image].s.n | (plan->staging[it.image].use_tma ? 1 << 16 : 0);
+        it.nflags = plan->imgs[it.image].s.n | (plan->staging[it.image].use_tma ? 1 << 16 : 0) |
+                    (tile_code(plan->imgs[it.image].T) << 17);
 }
 
 size_t batch_workspace_bytes(const BatchPlan *plan) { return plan ? plan->L.total : 0; }
@@ -2325,7 +2392,7 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
         LaunchArgs args = base_args(plan->L, base, (int)plan->imgs.size());
         args.many = (const ImgDesc *)(base + plan->L.table_off);
         args.order = (const Item *)(base + plan->L.order_off);
-        st = dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, stream);
+        st = dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, plan->L.multi_tile, stream);
     }
     // Join the lanes back (also after an error, so that `stream` never runs
     // ahead of work it forked).
