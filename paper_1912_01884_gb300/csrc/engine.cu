@@ -55,6 +55,16 @@ constexpr int kMaxBandFused = 128;     // band heights handled by the fused kern
 constexpr int kMOff = 128;             // column offset of the skewed M layout
 constexpr int kPad = 16;               // dead rows around V (uint8 path)
 constexpr int kFastB = 16;             // largest bend kept entirely in registers
+// 256-row bands: DP items take 64 columns; V of such an item ((511 + 2 kPad)
+// rows of 64 words) is followed by the window's suffix maxima.
+constexpr int kTile256 = 64;
+constexpr int kDp256SOff = (511 + 2 * kPad) * kTile256 * 4;
+// Margins of an h256 row (elements): the DP items read up to 128 columns
+// left of column 0 and up to 196 right of the last tile; the row starts at
+// kH256Left so that both stay inside it.
+constexpr int kH256Left = 136, kH256Right = 200;
+// M tile of a 256-row-band DP item: 511 rows in 7 copies of 73.
+constexpr int kMBox256 = 73;
 // After a copy wait gives up, the last bounded wait for that copy to land
 // before its shared memory is reused (about four seconds).
 constexpr long long kDrainCycles = 8000000000LL;
@@ -78,6 +88,15 @@ struct ImgDesc {
     int32_t *x_out, *d_out;
     void *score_out;
     const int32_t *win;       // optional [k][2]: allowed displacements of each band
+    // uint8 images with 256-row bands (kind 1): each band's Hough values are
+    // built from the FHTs of its two 128-row halves (half-band items, stored
+    // in h256), merged by the last dyadic level inside the DP items.
+    int kind;                 // 0: bands of at most 128 rows; 1: 256-row bands
+    int ftiles;               // half-band FHT tiles of 128 columns
+    int hpitch;               // row pitch of h256 in elements
+    uint16_t *h256;           // [k][2 halves][2 signs][128 shifts][hpitch], see h256_row
+    int *fflags;              // [k][2][ftiles] publication flags of the half-band items
+    int moff;                 // column offset of the skewed M layout
 };
 
 // Backpointers: per band, ceil(D/4) groups of w 32-bit words; byte (e & 3)
@@ -273,8 +292,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 struct WsSlot {
     long long item;
     const ImgDesc *im;
-    int band, tile, prefetched, T;
+    int band, tile, prefetched, T, kind;
 };
+
+// Work-item kinds (queue-entry bits 19-20).
+constexpr int kItemBand = 0;    // FHT + DP of a tile of a band of at most 128 rows
+constexpr int kItemHalf0 = 1;   // FHT of the top 128-row half of a 256-row band
+constexpr int kItemHalf1 = 2;   // FHT of the bottom half
+constexpr int kItemDp256 = 3;   // last FHT level + DP of a 64-column tile of a 256-row band
 
 struct NextItem {
     long long item;
@@ -633,6 +658,45 @@ __device__ __forceinline__ void window_u8(int ca, int c1, const int32_t *kcol, i
     if ((last & 3) != 3) bcol[(last >> 2) * bstride] = word;
 }
 
+// Register version for L = 2B+1 <= LMAX that keeps only the suffix maxima S
+// in registers: each block's values are read once for the prefix pass and
+// once more for the next block's suffix maxima (for long windows, where
+// holding the block's values too would not fit).
+template <int LMAX, typename Key, typename VGet, typename Emit>
+__device__ __forceinline__ void window_reread(int c0, int c1, int B, Key dead, VGet vkey,
+                                              Emit emit) {
+    const int L = 2 * B + 1;
+    Key S[LMAX];
+    int a = c0 - B;   // first input of the current block
+    Key run = dead;
+#pragma unroll
+    for (int i = LMAX - 1; i >= 0; --i) {
+        if (i < L) run = kmax(run, vkey(a + i));
+        S[i] = run;
+    }
+    for (int c = c0; c <= c1; c += L) {
+        a += L;
+        Key G = dead;
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i) {
+            if (i < L) {
+                const Key v = vkey(a + i);
+                const Key m = i == 0 ? S[0] : kmax(S[i], G);
+                G = kmax(G, v);
+                if (c + i <= c1) emit(c + i, m);
+            }
+        }
+        if (c + L <= c1) {
+            run = dead;
+#pragma unroll
+            for (int i = LMAX - 1; i >= 0; --i) {
+                if (i < L) run = kmax(run, vkey(a + i));
+                S[i] = run;
+            }
+        }
+    }
+}
+
 // Two-pass version for any L: pass 1 stores the in-block suffix maxima
 // S(e), e in [c0-B, c1-B], through sput/sget; pass 2 runs the in-block prefix
 // maximum G(c+B) and combines.  Blocks are aligned at `a` (a <= c0 - B).
@@ -700,7 +764,13 @@ __device__ void readback(const ImgDesc &im, const LaunchArgs &args) {
             atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
             return;
         }
-        const int e = __ldcg(im.bp + bp_byte(im, i, d + n - 1, xx));
+        int e = __ldcg(im.bp + bp_byte(im, i, d + n - 1, xx));
+        // 256-row bands: the byte holds the index modulo 256; the window
+        // [c - B, c + B] (B <= 127) around c = d + n - 1 has one index per residue.
+        if (n > 128) {
+            const int lo = d + n - 1 - im.B;
+            e = lo + ((e - lo) & 255);
+        }
         d = e - (n - 1);
         im.x_out[i] = xx;
         im.d_out[i] = d;
@@ -800,15 +870,16 @@ __host__ __device__ inline int strip_off(int n) { return (n + 15) & ~15; }
 __host__ __device__ inline int strip_boxes(int n, int T) {
     return (T + 2 * strip_off(n) + 127) / 128;
 }
-// One thread: the band strip of (band, tile) through TMA into `st` (the Hc
-// region, free until the compaction), zero-filled outside the image.
-__device__ inline void issue_strip(const CUtensorMap *map, int n, int band, int tile, int T,
+// One thread: the strip of n image rows from row y0 for (tile, T) through TMA
+// into `st` (the Hc region, free until the compaction), zero-filled outside
+// the image.
+__device__ inline void issue_strip(const CUtensorMap *map, int n, int y0, int tile, int T,
                                    void *st, Pipe &pipe) {
     const int xs = tile * T - strip_off(n), nb = strip_boxes(n, T);
     fence_proxy_async_smem();
     mbar_expect_tx(pipe.bar, (uint32_t)(nb * n * 128));
     for (int b = 0; b < nb; ++b)
-        tma_load_2d((uint8_t *)st + (size_t)b * n * 128, map, xs + 128 * b, band * n, pipe.bar);
+        tma_load_2d((uint8_t *)st + (size_t)b * n * 128, map, xs + 128 * b, y0, pipe.bar);
 }
 
 // Largest band height a uint8 work item of T = 128 or 256 columns handles
@@ -1012,9 +1083,8 @@ struct U8Path {
     // thread takes an 8-row sub-band g and the 4 columns [4c, 4c+4) of the
     // level-3 width; its top four rows are needed at 4..7 columns, the bottom
     // four at 8..11.  Shift s of the sub-band goes to row 8g + brev3(s).
-    __device__ static void fht_regs8(uint32_t *F, int pitch, const ImgDesc &im,
+    __device__ static void fht_regs8(uint32_t *F, int pitch, int n, int T,
                                      const StagedPixels &src, int x0) {
-        const int n = im.n, T = tw(im);
         const int C4 = (T + n - 8 + 3) / 4;
         const int tasks = (n / 8) * C4;
         for (int t = threadIdx.x; t < tasks; t += kThreads) {
@@ -1115,15 +1185,18 @@ struct U8Path {
     }
 
     // Returns false if the strip copy did not complete in time.
+    // n x T: the strip's rows and columns (a 128-row half of a 256-row band
+    // for half-band items, whose strip always comes through TMA).
     __device__ static bool fht(uint32_t *F, uint32_t *Hc, const ImgDesc &im, int band, int x0,
-                               Pipe &pipe, bool prefetched, const LaunchArgs &args) {
-        const int n = im.n, T = tw(im), pitch = fpitch(n, T);
+                               Pipe &pipe, bool prefetched, const LaunchArgs &args, int n,
+                               int log2n, int T) {
+        const int pitch = fpitch(n, T);
         bool compact;
         if (strip_by_tma(im)) {
             const int xs = x0 - strip_off(n), nb = strip_boxes(n, T);
             uint8_t *st = (uint8_t *)Hc;
             if (threadIdx.x == 0 && !prefetched)
-                issue_strip(&im.tmap, n, band, x0 / T, T, st, pipe);
+                issue_strip(&im.tmap, n, band * n, x0 / T, T, st, pipe);
             const bool ok = mbar_wait(pipe.bar, pipe.phase, args.wait_cycles);
             if (!ok) {
                 // The copy may still be in flight: give it a long (bounded)
@@ -1136,22 +1209,22 @@ struct U8Path {
             pipe.phase ^= 1u;
             const StagedPixels src{st, n, xs, nb * 128 - 8};
             if (n >= 8) {
-                fht_regs8(F, pitch, im, src, x0);
-                compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 4, Hc);
+                fht_regs8(F, pitch, n, T, src, x0);
+                compact = !fht_merge<uint32_t>(F, pitch, n, log2n, T, 4, Hc);
             } else {
                 fht_regs(F, pitch, im, src, x0);
-                compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3, Hc);
+                compact = !fht_merge<uint32_t>(F, pitch, n, log2n, T, 3, Hc);
             }
         } else if (n >= 4) {
             const GlobalPixels src{(const uint8_t *)im.img + (size_t)band * n * im.pitch,
                                    im.pitch, im.w,
                                    ((uintptr_t)im.img % 8 == 0) && (im.pitch % 8 == 0)};
             fht_regs(F, pitch, im, src, x0);
-            compact = !fht_merge<uint32_t>(F, pitch, n, im.log2n, T, 3, Hc);
+            compact = !fht_merge<uint32_t>(F, pitch, n, log2n, T, 3, Hc);
         } else {
             load_strip(F, pitch, im, band, x0);
-            compact = im.log2n == 0;
-            fht_levels<uint32_t>(F, pitch, n, im.log2n, T, 1, Hc);
+            compact = log2n == 0;
+            fht_levels<uint32_t>(F, pitch, n, log2n, T, 1, Hc);
         }
         // The last level wrote Hc[s][u] = packed Hough word of shift s at tile
         // column u; where the FHT had no merge level (n = 1, or n = 4 done in
@@ -1160,7 +1233,7 @@ struct U8Path {
             for (int idx = threadIdx.x; idx < n * (T / 4); idx += kThreads) {
                 const int s = idx / (T / 4), u0 = 4 * (idx - s * (T / 4));
                 *(uint4 *)&Hc[s * T + u0] =
-                    *(const uint4 *)&F[(size_t)brev(s, im.log2n) * pitch + u0];
+                    *(const uint4 *)&F[(size_t)brev(s, log2n) * pitch + u0];
             }
             csync();
         }
@@ -1331,15 +1404,24 @@ struct U8Path {
     // is none, just signals that the producers' flags were seen) on the M
     // barrier.  A wait that gives up sets ETIMEOUT and the item carries on,
     // so that every signal to the control warp is still given.
+    // half >= 0: a half-band FHT item of a 256-row band (its FHT only).
     __device__ static void process(const ImgDesc &im, int band, int tile, unsigned char *smem,
-                                   const LaunchArgs &args, Pipe &pipe, bool prefetched) {
-        const int n = im.n, T = tw(im), D = 2 * n - 1;
+                                   const LaunchArgs &args, Pipe &pipe, bool prefetched,
+                                   int half) {
+        const bool hitem = kMulti && half >= 0;
+        const int n = hitem ? 128 : im.n, T = hitem ? kTile : tw(im), D = 2 * n - 1;
         const int x0 = tile * T;
         uint32_t *F = (uint32_t *)smem;  // the strip, then V
         int32_t *Vn = (int32_t *)smem;
         uint32_t *Hc = (uint32_t *)(smem + hc_offset());
-        fht(F, Hc, im, band, x0, pipe, prefetched, args);
+        fht(F, Hc, im, band, x0, pipe, prefetched, args, n, hitem ? 7 : im.log2n, T);
         nb_arrive(kBarFhtDone, kCtlSync);   // F is free for the M tile
+        if (hitem) {
+            store_half(im, band, half, x0, Hc);
+            nb_arrive(kBarHcFree, kCtlSync);
+            nb_arrive(kBarWinDone, kCtlSync);
+            return;
+        }
         const bool msmem = im.use_mtma && band < im.k - 1;
         if (band != 0) {
             if (T == kTile) dead_pad<kTile>(Vn, n);
@@ -1471,6 +1553,199 @@ struct U8Path {
         nb_arrive(kBarWinDone, kCtlSync);
     }
 
+    // ---------------------------------------------------------------------
+    // 256-row bands.  A link over the band's 256 rows is, by the last level
+    // of Sec. 2.1's dyadic recursion, a link of shift s over the top 128 rows
+    // followed by one of shift s over the bottom 128 rows, moved by s + r:
+    //   H(x, 2s + r)    = Htop+(x, s) + Hbot+(x + s + r, s)
+    //   H(x, -(2s + r)) = Htop-(x, s) + Hbot-(x - s - r, s),   s < 128, r in {0, 1}.
+    // Half-band items compute the FHT of one 128-row half for 128 columns
+    // and store it to h256; the DP items of 64 columns apply that last level
+    // while they form V.
+    __device__ static uint16_t *h256_row(const ImgDesc &im, int band, int half, int sign,
+                                         int s) {
+        return im.h256 + ((((size_t)band * 2 + half) * 2 + sign) * 128 + s) * im.hpitch +
+               kH256Left;
+    }
+
+    // The FHT of one 128-row half of a 256-row band on a tile of 128 columns,
+    // from its compact rows in Hc into h256.  Word u of shift s holds the
+    // right-moving sum from column x0 + u in its low half and the
+    // left-moving sum from column x0 + 127 - u in its high half: 8 words
+    // give 8 columns of each sign.
+    __device__ static void store_half(const ImgDesc &im, int band, int half, int x0,
+                                      const uint32_t *Hc) {
+        constexpr int n = 128, T = kTile;
+        for (int idx = threadIdx.x; idx < n * (T / 8); idx += kThreads) {
+            const int sh = idx >> 4, q = idx & 15;
+            const uint4 a = *(const uint4 *)&Hc[sh * T + 8 * q];
+            const uint4 b = *(const uint4 *)&Hc[sh * T + 8 * q + 4];
+            *(uint4 *)(h256_row(im, band, half, 0, sh) + x0 + 8 * q) =
+                make_uint4(__byte_perm(a.x, a.y, 0x5410), __byte_perm(a.z, a.w, 0x5410),
+                           __byte_perm(b.x, b.y, 0x5410), __byte_perm(b.z, b.w, 0x5410));
+            *(uint4 *)(h256_row(im, band, half, 1, sh) + x0 + T - 8 - 8 * q) =
+                make_uint4(__byte_perm(b.w, b.z, 0x7632), __byte_perm(b.y, b.x, 0x7632),
+                           __byte_perm(a.w, a.z, 0x7632), __byte_perm(a.y, a.x, 0x7632));
+        }
+    }
+
+    // The DP of a 64-column tile of a 256-row band: V (Eqs. 3-4) from the two
+    // halves' FHTs and the M tile, then the bend-window maxima (two-pass van
+    // Herk / Gil-Werman).  V(e) of column u is at Vn[(e + n - 1 + kPad) * 64 + u].
+    __device__ static void process_dp256(const ImgDesc &im, int band, int tile,
+                                         unsigned char *smem, const LaunchArgs &args,
+                                         Pipe &pipe) {
+        constexpr int n = 256, T = kTile256, D = 2 * n - 1;
+        const int x0 = tile * T;
+        int32_t *Vn = (int32_t *)smem;
+        nb_arrive(kBarFhtDone, kCtlSync);   // no FHT here: the M tile may come at once
+        const bool last = band == im.k - 1;
+        const int32_t dead = Dead<int32_t>::value();
+        if (band != 0)
+            for (int idx = threadIdx.x; idx < 2 * kPad * (T / 4); idx += kThreads) {
+                const int r = idx / (T / 4), u0 = 4 * (idx % (T / 4));
+                const int row = r < kPad ? r : r + D;
+                *(int4 *)&Vn[row * T + u0] = make_int4(dead, dead, dead, dead);
+            }
+        if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles)) {
+            if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+            mbar_wait(pipe.mbar, pipe.mphase, kDrainCycles);
+        }
+        pipe.mphase ^= 1u;
+        // A task: shift s of the halves, one sign, 4 columns; it forms the
+        // displacements 2s and 2s + 1 (d = 0 once, with sign 0).  The L2
+        // loads of a batch of tasks are issued before any of its work.
+        unsigned long long best = 0;
+        constexpr int kTasks = 2 * 128 * (T / 4), kLB = 4;
+        static_assert(kTasks % (kLB * kThreads) == 0, "whole batches");
+#pragma unroll 1
+        for (int b0 = 0; b0 < kTasks; b0 += kLB * kThreads) {
+            uint2 aw[kLB];
+            uint32_t bw[kLB][3];
+            int base[kLB];
+#pragma unroll
+            for (int i = 0; i < kLB; ++i) {
+                const int idx = b0 + i * kThreads + threadIdx.x;
+                const int q = idx & 15, sh = (idx >> 4) & 127, sign = idx >> 11;
+                const int x = x0 + 4 * q;
+                aw[i] = __ldcg((const uint2 *)(h256_row(im, band, 0, sign, sh) + x));
+                // The bottom half from column base: x + s (right) or x - s - 1 (left).
+                base[i] = sign ? x - sh - 1 : x + sh;
+                const uint32_t *bp =
+                    (const uint32_t *)(h256_row(im, band, 1, sign, sh) + (base[i] & ~1));
+                bw[i][0] = __ldcg(bp);
+                bw[i][1] = __ldcg(bp + 1);
+                bw[i][2] = __ldcg(bp + 2);
+            }
+#pragma unroll
+            for (int i = 0; i < kLB; ++i) {
+            const int idx = b0 + i * kThreads + threadIdx.x;
+            const int q = idx & 15, sh = (idx >> 4) & 127, sign = idx >> 11;
+            const int x = x0 + 4 * q;
+            const int fs = (base[i] & 1) * 16;
+            const uint32_t p0 = __funnelshift_r(bw[i][0], bw[i][1], fs);
+            const uint32_t p1 = __funnelshift_r(bw[i][1], bw[i][2], fs);
+            const int av[4] = {(int)(aw[i].x & 0xffffu), (int)(aw[i].x >> 16),
+                               (int)(aw[i].y & 0xffffu), (int)(aw[i].y >> 16)};
+            const int bv[5] = {(int)(p0 & 0xffffu), (int)(p0 >> 16), (int)(p1 & 0xffffu),
+                               (int)(p1 >> 16),
+                               (int)(fs ? bw[i][2] >> 16 : bw[i][2] & 0xffffu)};
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = 2 * sh + r;
+                if (sign && e == 0) continue;
+                const int d = sign ? -e : e;
+                const int row = d + n - 1 + kPad;
+                // right: x + s + r + j = base + r + j; left: x - s - r + j = base + 1 - r + j
+                const int bo = sign ? 1 - r : r;
+                int4 m4 = make_int4(0, 0, 0, 0);
+                if (!last) m4 = *(const int4 *)&Vn[row * T + 4 * q];
+                const int ms[4] = {m4.x, m4.y, m4.z, m4.w};
+                int v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int xx = x + j;
+                    const bool ok = xx < im.w && xx + d >= 0 && xx + d < im.w;
+                    const int hv = av[j] + bv[j + bo];
+                    const int m = mval(ms[j]);
+                    v[j] = !ok ? dead : last ? hv : (m < 0 ? dead : hv + m);
+                }
+                if (band == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (v[j] != dead) {
+                            const unsigned long long k = argmax_key(ord32(v[j]), x + j, d + n - 1);
+                            best = best > k ? best : k;
+                        }
+                } else {
+                    if constexpr (sizeof(Key) == 4) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            v[j] = v[j] == dead ? dead : KO::make(v[j], d + n - 1);
+                    }
+                    *(int4 *)&Vn[row * T + 4 * q] = make_int4(v[0], v[1], v[2], v[3]);
+                }
+            }
+        }
+        }
+        if (band == 0) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = best > other ? best : other;
+            }
+            if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
+            nb_arrive(kBarHcFree, kCtlSync);
+            nb_arrive(kBarWinDone, kCtlSync);
+            return;
+        }
+        csync();
+        // Window maxima: 8 threads per column, each over 64 consecutive
+        // displacements (c0 + 63 = c1: for B = 32 one block pair of the van
+        // Herk / Gil-Werman scheme); the registers hold the suffix maxima.
+        const int u = threadIdx.x & (T - 1), qd = threadIdx.x / T;
+        const int xw = x0 + u;
+        const int B = im.B;
+        const int lo = -(n - 1), hi = n - 1;
+        Acc *mnext = (Acc *)im.mbuf[band & 1];
+        const int32_t *col = Vn + (n - 1 + kPad) * T + u;
+        auto vkey = [&](int e) -> Key {
+            if (e < lo || e > hi) return KO::dead();
+            const int v = col[e * T];
+            if constexpr (sizeof(Key) == 4) return v;   // stored as keys
+            return v == dead ? KO::dead() : KO::make(v, e + n - 1);
+        };
+        // The backpointer byte keeps the argmax index modulo 256 (the
+        // read-back recovers it from the window, B <= 127).
+        auto emit = [&](int c, Key mk) {
+            mnext[(size_t)(c + n - 1) * im.mpitch + im.moff + xw - c] = mstore(mk);
+            im.bp[bp_byte(im, band, c + n - 1, xw)] = (uint8_t)(mk < 0 ? 0 : KO::index(mk));
+        };
+        const int c0 = lo + 64 * qd, c1 = min(c0 + 63, hi);
+        if (sizeof(Key) == 4 && B <= 32) {
+            if (xw < im.w) {
+                if (B <= 8) window_reread<17, Key>(c0, c1, B, KO::dead(), vkey, emit);
+                else window_reread<65, Key>(c0, c1, B, KO::dead(), vkey, emit);
+            }
+        } else {
+            // Longer windows: the two-pass version with S in shared memory
+            // after V (64 rows per thread), a few of the column's threads at a
+            // time so that S fits (64 KB).
+            constexpr int kGroups = sizeof(Key) == 4 ? 2 : 4, kPer = 8 / kGroups;
+            for (int g = 0; g < kGroups; ++g) {
+                if (qd / kPer == g && xw < im.w) {
+                    Key *S = (Key *)(smem + kDp256SOff) + (size_t)(qd % kPer) * 64 * T;
+                    const int srow0 = c0 - B;   // S(e) at row e - srow0
+                    auto sput = [&](int e, Key v) { S[(size_t)(e - srow0) * T + u] = v; };
+                    auto sget = [&](int e) { return S[(size_t)(e - srow0) * T + u]; };
+                    window_two_pass<Key>(c0, c1, B, lo - B, lo, hi, KO::dead(), vkey, sput, sget,
+                                         emit);
+                }
+                csync();
+            }
+        }
+        nb_arrive(kBarHcFree, kCtlSync);
+        nb_arrive(kBarWinDone, kCtlSync);
+    }
 };
 
 // Shared-memory layout common to the uint8 items of every tile width: region
@@ -1499,11 +1774,39 @@ struct U8Ctl {
     struct Ctrl {
         long long item;
         const ImgDesc *im;
-        int band, tile, n, T;
+        int band, tile, n, T, kind;
         bool tma;   // its strip goes through TMA
     };
+    // Work items of a single image with 256-row bands, in queue order: the
+    // half-band FHT items of band k-1, then per band b from k-1 down to 0
+    // the half-band items of band b-1 (none for b = 0) and the DP items of b.
+    __device__ static void decode256(const ImgDesc &im, long long item, Ctrl &c) {
+        const long long hf = 2LL * im.ftiles, L1 = hf + im.tiles;
+        if (item < hf) {
+            c.band = im.k - 1;
+            c.kind = kItemHalf0 + (int)(item / im.ftiles);
+            c.tile = (int)(item % im.ftiles);
+            return;
+        }
+        const long long j = item - hf;
+        long long lv = j / L1, off = j - lv * L1;
+        if (lv >= im.k - 1) {
+            lv = im.k - 1;
+            off = j - (long long)(im.k - 1) * L1;
+        }
+        const int b = im.k - 1 - (int)lv;
+        if (b > 0 && off < hf) {
+            c.band = b - 1;
+            c.kind = kItemHalf0 + (int)(off / im.ftiles);
+            c.tile = (int)(off % im.ftiles);
+        } else {
+            c.band = b;
+            c.kind = kItemDp256;
+            c.tile = (int)(off - (b > 0 ? hf : 0));
+        }
+    }
     __device__ static Ctrl decode(const LaunchArgs &args, long long item) {
-        Ctrl c{item, nullptr, 0, 0, 0, 128, false};
+        Ctrl c{item, nullptr, 0, 0, 0, 128, kItemBand, false};
         if (item >= args.items) return c;
         if (args.many) {
             const Item it = args.order[item];
@@ -1511,27 +1814,130 @@ struct U8Ctl {
             c.band = it.band;
             c.tile = it.tile;
             c.n = it.nflags & 0xffff;
+            c.kind = (it.nflags >> 19) & 3;
             c.tma = ((it.nflags >> 16) & 1) && c.n >= 4;
             c.T = 64 << ((it.nflags >> 17) & 3);
         } else {
             c.im = &args.one;
-            c.band = args.one.k - 1 - (int)(item / args.one.tiles);
-            c.tile = (int)(item % args.one.tiles);
             c.n = args.one.n;
             c.tma = args.one.use_tma && c.n >= 4;
             c.T = args.one.tw;
+            if (args.one.kind == 1) {
+                decode256(args.one, item, c);
+            } else {
+                c.band = args.one.k - 1 - (int)(item / args.one.tiles);
+                c.tile = (int)(item % args.one.tiles);
+            }
+        }
+        if (c.kind == kItemHalf0 || c.kind == kItemHalf1) {
+            c.n = 128;   // the strip of one half
+            c.T = kTile;
+        } else if (c.kind == kItemDp256) {
+            c.tma = false;   // no strip
         }
         return c;
     }
     // Lane 0: the item's strip copy into Hc, and its slot for the compute warps.
     __device__ static void hand_over(const Ctrl &c, WsSlot *slot, void *Hc, Pipe &pipe) {
-        if (c.im && c.tma) issue_strip(&c.im->tmap, c.n, c.band, c.tile, c.T, Hc, pipe);
+        if (c.im && c.tma) {
+            const int y0 = c.kind == kItemBand ? c.band * c.n
+                                               : c.band * 256 + (c.kind - kItemHalf0) * 128;
+            issue_strip(&c.im->tmap, c.n, y0, c.tile, c.T, Hc, pipe);
+        }
         slot->item = c.item;
         slot->im = c.im;
         slot->band = c.band;
         slot->tile = c.tile;
         slot->T = c.T;
+        slot->kind = c.kind;
         slot->prefetched = c.im && c.tma;
+    }
+
+    // Lanes of the control warp: the flags an item waits for (at most one
+    // per lane; true when there is none), acquired with a bounded spin.
+    __device__ static bool wait_producers(const Ctrl &cur, const LaunchArgs &args, int lane) {
+        const ImgDesc &im = *cur.im;
+        const int *flag = nullptr;
+        if (cur.kind == kItemBand) {
+            // the three band+1 tiles this tile reads
+            const int c = cur.tile - 1 + lane;
+            if (cur.band < im.k - 1 && lane < 3 && c >= 0 && c < im.tiles)
+                flag = im.flags + (size_t)(cur.band + 1) * im.tiles + c;
+        } else if (cur.kind == kItemDp256) {
+            // M(x + d, d), |d| <= 255: band+1 tiles t-4..t+4 (lanes 0..8); the
+            // top half at 128-column tile t/2 and the bottom half at t/2-1..t/2+1
+            // (lanes 9..12)
+            const int ft = cur.tile >> 1;
+            if (lane < 9) {
+                const int c = cur.tile - 4 + lane;
+                if (cur.band < im.k - 1 && c >= 0 && c < im.tiles)
+                    flag = im.flags + (size_t)(cur.band + 1) * im.tiles + c;
+            } else if (lane == 9) {
+                flag = im.fflags + (size_t)(cur.band * 2) * im.ftiles + ft;
+            } else if (lane < 13) {
+                const int c = ft - 11 + lane;
+                if (c >= 0 && c < im.ftiles)
+                    flag = im.fflags + (size_t)(cur.band * 2 + 1) * im.ftiles + c;
+            }
+        }
+        bool ok = true;
+        if (flag) {
+            ok = wait_flag(flag, args.ctl, args.wait_cycles);
+            fence_acq_rel_gpu();
+        }
+        __syncwarp();
+        return __all_sync(0xffffffffu, ok);
+    }
+
+    // Lane 0, after the FHT: the M tile of the item into the V rows (or just
+    // the arrival on the M barrier when it has none).  Half-band items do
+    // not use the M barrier.
+    __device__ static void copy_m_tile(const Ctrl &cur, int32_t *Vn, Pipe &pipe) {
+        const ImgDesc &im = *cur.im;
+        const int n = im.n, D = 2 * n - 1;
+        if (cur.kind == kItemHalf0 || cur.kind == kItemHalf1) return;
+        if (!im.use_mtma || cur.band >= im.k - 1) {
+            mbar_arrive(pipe.mbar);
+            return;
+        }
+        fence_proxy_async_global();
+        fence_proxy_async_smem();
+        const int y0 = ((cur.band + 1) & 1) * D;
+        if (cur.kind == kItemDp256) {
+            mbar_expect_tx(pipe.mbar, (uint32_t)(kTile256 * D * 4));
+            for (int b = 0; b < D / kMBox256; ++b)
+                tma_load_2d(Vn + (kPad + b * kMBox256) * kTile256, &im.mtmap,
+                            im.moff + cur.tile * kTile256, y0 + b * kMBox256, pipe.mbar);
+            return;
+        }
+        mbar_expect_tx(pipe.mbar, (uint32_t)(cur.T * D * 4));
+        for (int b = 0; b < cur.T / kTile; ++b)
+            tma_load_2d(Vn + b * U8Path<Key, true>::vblock(n) + kPad * kTile, &im.mtmap,
+                        im.moff + cur.tile * cur.T + b * kTile, y0, pipe.mbar);
+    }
+
+    // Lane 0, after the item: its publication (band 0: the tile count, and
+    // the read-back after the image's last tile).
+    __device__ static void finish(const Ctrl &cur, const LaunchArgs &args) {
+        const ImgDesc &im = *cur.im;
+        if (cur.kind == kItemHalf0 || cur.kind == kItemHalf1) {
+            fence_acq_rel_gpu();
+            st_release(im.fflags + (size_t)(cur.band * 2 + cur.kind - kItemHalf0) * im.ftiles +
+                           cur.tile,
+                       1);
+            return;
+        }
+        const ImgDesc &first_im = args.many ? args.many[0] : args.one;
+        if (cur.band != 0) {
+            if (!(cur.band == args.skip_band && cur.tile == args.skip_tile &&
+                  im.flags == first_im.flags)) {
+                fence_acq_rel_gpu();
+                st_release(im.flags + (size_t)cur.band * im.tiles + cur.tile, 1);
+            }
+        } else {
+            __threadfence();
+            if (atomicAdd(im.done, 1) == im.tiles - 1) readback<int32_t>(im, args);
+        }
     }
 
     // The control warp: takes the items from the queue one ahead of the
@@ -1553,50 +1959,17 @@ struct U8Ctl {
             long long nx = 0;
             if (lane == 0) nx = atomicAdd(&args.ctl->queue, 1);
             const Ctrl next = decode(args, __shfl_sync(0xffffffffu, nx, 0));
-            const ImgDesc &im = *cur.im;
-            const int n = im.n, D = 2 * n - 1;
-            // Lanes 0..2: the three band+1 tiles this tile reads.
-            bool ok = true;
-            const int c = cur.tile - 1 + lane;
-            if (cur.band < im.k - 1 && lane < 3 && c >= 0 && c < im.tiles) {
-                ok = wait_flag(im.flags + (size_t)(cur.band + 1) * im.tiles + c, args.ctl,
-                               args.wait_cycles);
-                fence_acq_rel_gpu();
-            }
-            __syncwarp();
-            ok = __all_sync(0xffffffffu, ok);
+            const bool ok = wait_producers(cur, args, lane);
             nb_sync(kBarFhtDone, kCtlSync);
             if (lane == 0) {
                 if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
-                if (im.use_mtma && cur.band < im.k - 1) {
-                    fence_proxy_async_global();
-                    fence_proxy_async_smem();
-                    mbar_expect_tx(pipe.mbar, (uint32_t)(cur.T * D * 4));
-                    for (int b = 0; b < cur.T / kTile; ++b)
-                        tma_load_2d(Vn + b * U8Path<Key, true>::vblock(n) + kPad * kTile, &im.mtmap,
-                                    kMOff + cur.tile * cur.T + b * kTile,
-                                    ((cur.band + 1) & 1) * D, pipe.mbar);
-                } else {
-                    mbar_arrive(pipe.mbar);
-                }
+                copy_m_tile(cur, Vn, pipe);
             }
             nb_sync(kBarHcFree, kCtlSync);
             if (lane == 0) hand_over(next, slot, Hc, pipe);
             nb_arrive(kBarNext, kCtlSync);
             nb_sync(kBarWinDone, kCtlSync);
-            if (lane == 0) {
-                const ImgDesc &first_im = args.many ? args.many[0] : args.one;
-                if (cur.band != 0) {
-                    if (!(cur.band == args.skip_band && cur.tile == args.skip_tile &&
-                          im.flags == first_im.flags)) {
-                        fence_acq_rel_gpu();
-                        st_release(im.flags + (size_t)cur.band * im.tiles + cur.tile, 1);
-                    }
-                } else {
-                    __threadfence();
-                    if (atomicAdd(im.done, 1) == im.tiles - 1) readback<int32_t>(im, args);
-                }
-            }
+            if (lane == 0) finish(cur, args);
             cur = next;
         }
     }
@@ -1864,8 +2237,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             nb_sync(kBarNext, kCtlSync);
             const WsSlot sl = s_slot;
             if (sl.item >= args.items) break;
+            if constexpr (kMulti) {
+                if (sl.kind == kItemDp256) {
+                    U8Path<Key, kMulti>::process_dp256(*sl.im, sl.band, sl.tile, smem_raw, args,
+                                                       pipe);
+                    continue;
+                }
+            }
+            const int half = sl.kind == kItemHalf0 ? 0 : sl.kind == kItemHalf1 ? 1 : -1;
             U8Path<Key, kMulti>::process(*sl.im, sl.band, sl.tile, smem_raw, args, pipe,
-                                         sl.prefetched != 0);
+                                         sl.prefetched != 0, half);
         }
     } else {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 32;" ::: "memory");
@@ -1887,9 +2268,11 @@ struct ImgPlan {
     Shape s;
     int B, tiles, mpitch;
     int T;                      // column tile width of its work items
+    int kind;                   // 1: 256-row bands through half-band and DP items
+    int ftiles, hpitch, moff;   // kind 1: half-band tiles, h256 row pitch; M column offset
     long long item0;
-    size_t flags, best, done;   // offsets in the counter region
-    size_t m0, m1, bp;          // offsets in the data region
+    size_t flags, best, done, fflags;   // offsets in the counter region
+    size_t m0, m1, bp, h256;            // offsets in the data region
 };
 
 struct RunLayout {
@@ -1908,6 +2291,15 @@ struct RunLayout {
 int default_tile(int dtype, int n) { return dtype == FHTDP_U8 && n <= 64 ? 256 : kTile; }
 
 int tiles_of(const Shape &s, int T) { return (s.w + T - 1) / T; }
+
+// uint8 images with 256-row bands run in the fused engine when their strips
+// can go through TMA (16-byte aligned rows) and the backpointer byte
+// identifies the argmax inside a window (B <= 127); the others take the
+// standalone kernels.
+bool fused_256(int dtype, const Shape &s, int B, const void *img, long long pitch) {
+    return dtype == FHTDP_U8 && s.n == 256 && B <= 127 && (uintptr_t)img % 16 == 0 &&
+           pitch % 16 == 0;
+}
 // Queue-entry code of a tile width: T = 64 << code.
 int tile_code(int T) { return T == 256 ? 2 : T == 64 ? 0 : 1; }
 
@@ -1917,10 +2309,23 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
     long long items = 0;
     for (auto &p : imgs) {
         p.tiles = tiles_of(p.s, p.T);
-        // Row reads of M go up to 4 words past the last tile's columns.
-        p.mpitch = (int)align_up((size_t)kMOff + p.s.w + p.T + 4, 32);
         p.item0 = items;
         items += (long long)p.s.k * p.tiles;
+        if (p.kind == 1) {
+            // M(x', c) at column moff + x' - c, |c| <= 255; the M tile reads
+            // go up to 64 words past the last tile's columns.
+            p.moff = 256;
+            p.mpitch = (int)align_up((size_t)p.moff + p.s.w + 256 + 4, 32);
+            p.ftiles = (p.s.w + kTile - 1) / kTile;
+            p.hpitch = kH256Left + p.ftiles * kTile + kH256Right;
+            items += 2LL * p.s.k * p.ftiles;
+            p.fflags = off;
+            off = align_up(off + (size_t)p.s.k * 2 * p.ftiles * 4, 8);
+        } else {
+            // Row reads of M go up to 4 words past the last tile's columns.
+            p.moff = kMOff;
+            p.mpitch = (int)align_up((size_t)kMOff + p.s.w + p.T + 4, 32);
+        }
         p.flags = off;
         off = align_up(off + (size_t)p.s.k * p.tiles * 4, 8);
         p.best = off;
@@ -1943,6 +2348,10 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
         d = align_up(p.m1 + (size_t)p.s.D * p.mpitch * 4, 256);
         p.bp = d;
         d = align_up(d + (size_t)p.s.k * bp_groups(p.s.n) * 4 * p.s.w, 256);
+        if (p.kind == 1) {
+            p.h256 = d;
+            d = align_up(d + (size_t)p.s.k * 4 * 128 * p.hpitch * 2, 256);
+        }
     }
     L.data_off = L.order_off + L.order_bytes;
     L.total = L.data_off + d;
@@ -1978,7 +2387,8 @@ bool encode_strip_map(CUtensorMap *map, const void *img, int h, int w, long long
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    cuuint32_t box[2] = {128u, (cuuint32_t)n};
+    // 256-row bands are staged one 128-row half at a time.
+    cuuint32_t box[2] = {128u, (cuuint32_t)(n > 128 ? 128 : n)};
     cuuint32_t estr[2] = {1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(img), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1986,14 +2396,15 @@ bool encode_strip_map(CUtensorMap *map, const void *img, int h, int w, long long
 }
 
 // 2-D int32 tensor map of an image's two adjacent M buffers ([2D][mpitch]),
-// box of 128 columns x D rows: one copy brings a tile's whole M_{b+1}.
-bool encode_m_map(CUtensorMap *map, void *m0, int D, int mpitch) {
-    if ((uintptr_t)m0 % 16 != 0 || mpitch % 4 != 0 || D > 256) return false;
+// box of bw columns x bh rows: for bands of at most 128 rows 128 x D (one
+// copy brings a tile's whole M_{b+1}), for 256-row bands 64 x 73 (seven).
+bool encode_m_map(CUtensorMap *map, void *m0, int D, int mpitch, int bw, int bh) {
+    if ((uintptr_t)m0 % 16 != 0 || mpitch % 4 != 0 || bh > 256 || bw > 256) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)mpitch, (cuuint64_t)(2 * D)};
     cuuint64_t strides[1] = {(cuuint64_t)mpitch * 4};
-    cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)D};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
     cuuint32_t estr[2] = {1u, 1u};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, m0, dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -2004,8 +2415,13 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     ImgDesc im{};
     im.use_tma = dtype == FHTDP_U8 &&
                  encode_strip_map(&im.tmap, p.io.img, p.s.h, p.s.w, p.io.pitch, p.s.n);
-    im.use_mtma = dtype == FHTDP_U8 && p.s.n <= kMaxBandFused && ws &&
-                  encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch);
+    if (p.kind == 1)
+        im.use_mtma = ws && encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch,
+                                         kTile256, kMBox256);
+    else
+        im.use_mtma = dtype == FHTDP_U8 && p.s.n <= kMaxBandFused && ws &&
+                      encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch, kTile,
+                                   p.s.D);
     im.img = p.io.img;
     im.pitch = p.io.pitch;
     im.h = p.s.h;
@@ -2029,6 +2445,14 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     im.d_out = p.io.d_out;
     im.score_out = p.io.score_out;
     im.win = p.io.d_window;
+    im.kind = p.kind;
+    im.moff = p.moff;
+    if (p.kind == 1) {
+        im.ftiles = p.ftiles;
+        im.hpitch = p.hpitch;
+        im.h256 = (uint16_t *)(data + p.h256);
+        im.fflags = (int *)(ws + p.fflags);
+    }
     return im;
 }
 
@@ -2174,6 +2598,10 @@ ImgPlan single_plan(int dtype, const void *img, int pitch, const Shape &s, int B
     p.io.score_out = score_out;
     p.s = s;
     p.B = B < 2 * s.n - 2 ? B : 2 * s.n - 2;   // wider windows change nothing
+    if (fused_256(dtype, s, p.B, img, pitch)) {
+        p.kind = 1;
+        p.T = kTile256;
+    }
     return p;
 }
 
@@ -2212,35 +2640,64 @@ struct BatchPlan {
 // images in flight, so their M buffers stay in L2.  The batch is split into
 // round(total / target) groups of about equal width, so that no narrow
 // remainder group runs its band chain alone at the end.
+// Items of a band level of an image, in tiles of 128 x 128 work (a 256-row
+// band level also holds the half-band FHT items of the band above).
+long long level_weight(const ImgPlan &p) { return p.kind == 1 ? p.tiles + 2LL * p.ftiles : p.tiles; }
+
+// The items of band level lv of one image.  256-row bands: the half-band
+// FHT items of band k-1 open level 0, and each level lv also holds those of
+// the band above (k-2-lv) before its DP items, so that the halves are
+// ready one level ahead.
+void push_level(std::vector<Item> &order, const ImgPlan &p, int i, int lv) {
+    const int b = p.s.k - 1 - lv;
+    if (p.kind == 1) {
+        auto halves = [&](int band) {
+            for (int h = 0; h < 2; ++h)
+                for (int t = 0; t < p.ftiles; ++t)
+                    order.push_back(Item{i, band, t, (kItemHalf0 + h) << 19});
+        };
+        if (lv == 0) halves(b);
+        if (b > 0) halves(b - 1);
+        for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemDp256 << 19});
+        return;
+    }
+    for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemBand << 19});
+}
+
 std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target) {
     std::vector<Item> order;
     long long total = 0;
-    for (const ImgPlan &p : imgs) total += p.tiles;
+    for (const ImgPlan &p : imgs) total += level_weight(p);
     const long long groups = std::max(1LL, (total + target / 2) / std::max(1LL, target));
     size_t first = 0;
     long long done = 0;
     for (long long g = 1; first < imgs.size(); ++g) {
         const long long goal = total * g / groups;
         size_t last = first;
-        while (last < imgs.size() && (last == first || done + imgs[last].tiles / 2 < goal)) {
-            done += imgs[last].tiles;
+        while (last < imgs.size() &&
+               (last == first || done + level_weight(imgs[last]) / 2 < goal)) {
+            done += level_weight(imgs[last]);
             ++last;
         }
         int levels = 0;
         for (size_t i = first; i < last; ++i) levels = std::max(levels, imgs[i].s.k);
         for (int lv = 0; lv < levels; ++lv)
-            for (size_t i = first; i < last; ++i) {
-                if (lv >= imgs[i].s.k) continue;
-                for (int t = 0; t < imgs[i].tiles; ++t)
-                    order.push_back(Item{(int)i, imgs[i].s.k - 1 - lv, t, 0});
-            }
+            for (size_t i = first; i < last; ++i)
+                if (lv < imgs[i].s.k) push_level(order, imgs[i], (int)i, lv);
         first = last;
     }
     return order;
 }
 
 size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
-    if (s.n > kMaxBandFused) return 256 + 2 * (size_t)s.k * 2 * s.n * s.W * 4;
+    const size_t standalone = 256 + 2 * (size_t)s.k * 2 * s.n * s.W * 4;
+    if (s.n > kMaxBandFused) {
+        // Either path may run, depending on the image's alignment.
+        const int Bc = B < 2 * s.n - 2 ? B : 2 * s.n - 2;
+        if (dtype != FHTDP_U8 || Bc > 127) return standalone;
+        std::vector<ImgPlan> one{single_plan(dtype, nullptr, 16, s, B, nullptr, nullptr, nullptr)};
+        return std::max(standalone, plan_layout(one, false).total);
+    }
     std::vector<ImgPlan> one{single_plan(dtype, nullptr, s.w, s, B, nullptr, nullptr, nullptr)};
     return plan_layout(one, false).total;
 }
@@ -2248,15 +2705,17 @@ size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                   int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream) {
     (void)ws_bytes;
-    if (s.n > kMaxBandFused)
-        return run_fallback(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, stream);
     std::vector<ImgPlan> one{single_plan(dtype, img, pitch, s, B, x_out, d_out, score_out)};
+    if (s.n > kMaxBandFused && one[0].kind != 1)
+        return run_fallback(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, stream);
     RunLayout L = plan_layout(one, false);
     char *base = (char *)ws;
     int st = cuda_status(cudaMemsetAsync(base, 0, L.zero_bytes, stream), "cudaMemsetAsync");
     if (st) return st;
     LaunchArgs args = base_args(L, base, 1);
     args.one = make_desc(one[0], L, base, dtype);
+    if (one[0].kind == 1 && (!args.one.use_tma || !args.one.use_mtma))
+        return set_error(FHTDP_ECUDA, "tensor maps of a 256-row-band image could not be encoded");
     args.many = nullptr;
     args.order = nullptr;
     return dispatch(dtype, L.max_h, args, L.max_n, L.multi_tile, stream);
@@ -2297,7 +2756,7 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
                              "image %d: displacement windows need bands of at most %d rows", i,
                              kMaxBandFused);
         }
-        if (s.n > kMaxBandFused)
+        if (s.n > kMaxBandFused && p.kind != 1)
             plan->separate.push_back(p);
         else
             plan->imgs.push_back(p);
@@ -2336,7 +2795,8 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
 // Each queue entry carries its image's band height and TMA flag.
 void set_nflags(BatchPlan *plan) {
     for (Item &it : plan->order)
-        it.nflags = plan->imgs[it.image].s.n | (plan->staging[it.image].use_tma ? 1 << 16 : 0) |
+        it.nflags = (it.nflags & (3 << 19)) | plan->imgs[it.image].s.n |
+                    (plan->staging[it.image].use_tma ? 1 << 16 : 0) |
                     (tile_code(plan->imgs[it.image].T) << 17);
 }
 
@@ -2350,8 +2810,13 @@ int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream
         return set_error(FHTDP_EWORKSPACE, "batch workspace needs %zu bytes, got %zu",
                          plan->L.total, ws_bytes);
     plan->staging.clear();
-    for (auto &p : plan->imgs)
+    for (auto &p : plan->imgs) {
         plan->staging.push_back(make_desc(p, plan->L, (char *)ws, plan->dtype));
+        const ImgDesc &im = plan->staging.back();
+        if (p.kind == 1 && (!im.use_tma || !im.use_mtma))
+            return set_error(FHTDP_ECUDA,
+                             "tensor maps of a 256-row-band image could not be encoded");
+    }
     set_nflags(plan);
     plan->bound_ws = ws;
     int st = cuda_status(cudaMemcpyAsync((char *)ws + plan->L.table_off, plan->staging.data(),

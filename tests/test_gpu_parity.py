@@ -327,3 +327,70 @@ def test_huge_bend_limit_equals_the_unrestricted_dp(lib, shape):
     xo, do, so = oracle.detect(img, k, 2 * n - 2)
     assert list(xb.cpu().numpy()) == list(xo) and list(db.cpu().numpy()) == list(do)
     assert int(sb.cpu().numpy()[0]) == int(so)
+
+
+# --------------------------------------------------------------------------
+# 256-row bands in the fused engine: half-band FHT items + 64-column DP
+# items (uint8 rows 16-byte aligned, B <= 127); the rest take the standalone
+# kernels.
+# --------------------------------------------------------------------------
+def _padded_device(img, pitch):
+    """A device view of img whose rows are `pitch` bytes apart."""
+    import torch
+    h, w = img.shape
+    buf = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+    buf[:, :w] = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    return buf[:, :w]
+
+
+@pytest.mark.parametrize("h,w,pitch,k,B", [
+    (512, 704, 704, 2, 32),     # config-3 bend (n/8)
+    (256, 64, 64, 1, 0),        # one band, one DP tile
+    (256, 1, 16, 1, 5),         # a one-pixel-wide image
+    (768, 1000, 1008, 3, 127),  # largest fused bend; ragged width
+    (1024, 300, 304, 4, 16),
+    (256, 130, 144, 1, 3),      # one band over two half-band tiles
+    (512, 200, 208, 2, 1),
+])
+def test_detect_256_row_bands_fused(lib, h, w, pitch, k, B):
+    img = np.random.default_rng(h + w + B).integers(0, 256, (h, w)).astype(np.uint8)
+    x, d, s = lib.detect_polyline(_padded_device(img, pitch), k, B)
+    x, d, s = x.cpu().numpy(), d.cpu().numpy(), s.cpu().numpy()[0]
+    check_path(img, k, B, x, d)
+    xo, do, so = oracle.detect(img, k, B)
+    assert list(x) == list(xo) and list(d) == list(do) and int(s) == int(so)
+
+
+def test_detect_256_row_bands_planted_polyline(lib):
+    """Exact recovery with 256-row bands (the FHT's own line pattern at 200
+    over noise <= 40), bends up to 32."""
+    h, w, k, B = 1024, 512, 4, 32
+    n = h // k
+    rng = synth.Rng(9, 77)
+    img = rng.ints(h * w, 0, 40).reshape(h, w).astype(np.uint8)
+    xs, ds = synth.random_polyline(rng, h, w, k, B)
+    off = oracle.off_table(n)
+    for i, dd in enumerate(ds):
+        for y in range(n):
+            img[i * n + y, xs[i] + np.sign(dd) * off[abs(int(dd)), y]] = 200
+    x, d, s = _detect(lib, img, k, B)
+    assert int(s) == 200 * h and list(x) == list(xs) and list(d) == list(ds)
+
+
+def test_batch_of_256_row_bands_runs_in_one_launch(lib):
+    """A batch of 256-row-band images (and shorter bands) runs as one
+    persistent launch, with no standalone kernel beside it."""
+    import torch
+    shapes = [(512, 512, 2, 32), (1024, 768, 4, 32), (256, 256, 1, 8), (768, 1024, 3, 127),
+              (512, 640, 4, 16), (256, 512, 8, 4)]
+    wls = [synth.plain_uniform(300 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(shapes)]
+    imgs = [to_device(wl.img) for wl in wls]
+    plan = lib.BatchPlan(imgs, [wl.k for wl in wls], [wl.B for wl in wls])
+    torch.cuda.synchronize()
+    l0 = lib.launch_count()
+    plan.run()
+    torch.cuda.synchronize()
+    assert lib.launch_count() - l0 == 1
+    _check_batch(plan, wls)
+    plan.run()
+    _check_batch(plan, wls)
