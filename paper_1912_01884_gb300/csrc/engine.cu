@@ -697,6 +697,39 @@ __device__ __forceinline__ void window_reread(int c0, int c1, int B, Key dead, V
     }
 }
 
+// Window maxima of the 32 displacements [c0, c0 + 31] for 16 <= B <= 32
+// (L = 2B + 1 > 32), one block pair of the van Herk / Gil-Werman scheme:
+// M(c0 + i) = max(S[i], G(i)) with S[i] the maximum of V over
+// [c0 - B + i, c0 + B] and G(i) that over [c0 + B + 1, c0 + B + i] (empty for
+// i = 0).  Only S[0..31] is kept (in registers).  Output i < count stores M'
+// (the key with its index bits cleared) to mcol[i * mstride] and packs its
+// argmax byte (the index modulo 256) into the word bcol[(i >> 2) * bstride].
+template <typename VGet>
+__device__ __forceinline__ void window_span32(int c0, int count, int B, VGet vkey,
+                                              int32_t *mcol, int mstride, uint32_t *bcol,
+                                              int bstride) {
+    const int L = 2 * B + 1;
+    int32_t S[32];
+    int32_t run = INT32_MIN;
+    const int a = c0 - B;
+#pragma unroll
+    for (int j = 64; j >= 0; --j) {
+        if (j < L) run = max(run, vkey(a + j));
+        if (j < 32) S[j] = run;
+    }
+    int32_t G = INT32_MIN;
+    uint32_t word = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int32_t m = max(S[i], G);
+        G = max(G, vkey(c0 + B + 1 + i));
+        if (i < count) mcol[i * mstride] = m & ~511;
+        const uint32_t b = ~(uint32_t)m & 0xffu;
+        word = (i & 3) == 0 ? b : word | (b << (8 * (i & 3)));
+        if ((i & 3) == 3) bcol[(i >> 2) * bstride] = word;
+    }
+}
+
 // Two-pass version for any L: pass 1 stores the in-block suffix maxima
 // S(e), e in [c0-B, c1-B], through sput/sget; pass 2 runs the in-block prefix
 // maximum G(c+B) and combines.  Blocks are aligned at `a` (a <= c0 - B).
@@ -1699,14 +1732,34 @@ struct U8Path {
             return;
         }
         csync();
-        // Window maxima: 8 threads per column, each over 64 consecutive
-        // displacements (c0 + 63 = c1: for B = 32 one block pair of the van
-        // Herk / Gil-Werman scheme); the registers hold the suffix maxima.
-        const int u = threadIdx.x & (T - 1), qd = threadIdx.x / T;
-        const int xw = x0 + u;
+        // Window maxima.  32-bit keys with 16 <= B <= 32: 16 threads per
+        // column, 32 displacements each (window_span32), two columns per
+        // thread.  Otherwise 8 threads per column over 64 displacements.
         const int B = im.B;
         const int lo = -(n - 1), hi = n - 1;
         Acc *mnext = (Acc *)im.mbuf[band & 1];
+        if (sizeof(Key) == 4 && B >= 16 && B <= 32) {
+            const int qd = threadIdx.x >> 5;   // displacements [lo + 32 qd, lo + 32 qd + 31]
+            const int c0 = lo + 32 * qd;
+            for (int u = threadIdx.x & 31; u < T; u += 32) {
+                const int xw = x0 + u;
+                if (xw >= im.w) continue;
+                const int32_t *col = Vn + (n - 1 + kPad) * T + u;
+                auto vkey = [&](int e) -> int32_t {
+                    return (e < lo || e > hi) ? INT32_MIN : col[e * T];
+                };
+                int32_t *mcol = mnext + (size_t)(c0 + n - 1) * im.mpitch + im.moff + xw - c0;
+                uint32_t *bw = (uint32_t *)im.bp +
+                               ((size_t)band * bp_groups(n) + ((c0 + n - 1) >> 2)) * im.w + xw;
+                // the last thread's 32nd displacement (c = n) does not exist
+                window_span32(c0, min(32, hi - c0 + 1), B, vkey, mcol, im.mpitch - 1, bw, im.w);
+            }
+            nb_arrive(kBarHcFree, kCtlSync);
+            nb_arrive(kBarWinDone, kCtlSync);
+            return;
+        }
+        const int u = threadIdx.x & (T - 1), qd = threadIdx.x / T;
+        const int xw = x0 + u;
         const int32_t *col = Vn + (n - 1 + kPad) * T + u;
         auto vkey = [&](int e) -> Key {
             if (e < lo || e > hi) return KO::dead();
@@ -1721,11 +1774,8 @@ struct U8Path {
             im.bp[bp_byte(im, band, c + n - 1, xw)] = (uint8_t)(mk < 0 ? 0 : KO::index(mk));
         };
         const int c0 = lo + 64 * qd, c1 = min(c0 + 63, hi);
-        if (sizeof(Key) == 4 && B <= 32) {
-            if (xw < im.w) {
-                if (B <= 8) window_reread<17, Key>(c0, c1, B, KO::dead(), vkey, emit);
-                else window_reread<65, Key>(c0, c1, B, KO::dead(), vkey, emit);
-            }
+        if (sizeof(Key) == 4 && B < 16) {
+            if (xw < im.w) window_reread<17, Key>(c0, c1, B, KO::dead(), vkey, emit);
         } else {
             // Longer windows: the two-pass version with S in shared memory
             // after V (64 rows per thread), a few of the column's threads at a
