@@ -402,20 +402,39 @@ int fhtdp_batch_upload(fhtdp_batch_plan *plan, void *ws, size_t ws_bytes, cudaSt
 int fhtdp_batch_run(const fhtdp_batch_plan *plan, void *ws, cudaStream_t stream);
 /* Number of work items (image, band, column tile) of a run. */
 long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
-/* Tunes the plan's work-queue order on its bound workspace (after
- * fhtdp_batch_upload): the queue takes images in groups whose band levels
- * hold about `target` column tiles, so that the band chains of a group advance
- * together; wider groups wait less for dependencies, narrower ones keep fewer
- * window-maximum buffers in L2.  The call runs the batch `reps` times (plus one
- * warm-up) for each of a few widths between half and three times the SM count
- * (and the whole batch as one group), keeps the fastest, uploads its order and
- * writes its width to *target_out (may be NULL).  The outputs are those of an
- * ordinary run.  It synchronises `stream` (not for use under stream capture).
- * Column tile width and FHT fusion depth are fixed by the kernel's shared
- * memory layout and are not tuned.  The paper has no counterpart: it tunes the
- * GPU schedule of its method, not the method. */
+/* Tunes the plan on its bound workspace (after fhtdp_batch_upload) by timing
+ * runs: the call runs the batch `reps` times (plus one warm-up) per candidate
+ * and keeps the fastest of each choice in turn:
+ *   1. the work-queue schedule: groups of images whose band levels hold about
+ *      `target` column tiles and advance together, or band chains (an active
+ *      set of about `target` tiles per step that images join, most bands
+ *      first, as others finish); widths from half to six times the SM count
+ *      and the whole batch;
+ *   2. for each band height of uint8 images, the column tile width of its
+ *      work items (128, or 256 for bands of at most 64 rows) and the number
+ *      of FHT levels done in registers before the shared-memory merges (2 or
+ *      3; 256-row bands: of their 128-row halves);
+ *   3. the schedule again.
+ * It uploads the chosen layout and queue, and writes the width to
+ * *target_out (may be NULL); fhtdp_batch_choice reports the rest.  The
+ * outputs are those of an ordinary run.  It synchronises `stream` (not for use
+ * under stream capture).  The paper has no counterpart: this tunes the GPU
+ * schedule of its method, not the method. */
 int fhtdp_batch_autotune(fhtdp_batch_plan *plan, void *ws, int reps, cudaStream_t stream,
                          long long *target_out);
+/* The plan's current choices: the queue schedule (*mode: 0 groups, 1 band
+ * chains) and width, and for its images of band height n the column tile
+ * width and register FHT depth (0 and 0 when it has none).  Any pointer may
+ * be NULL.  The paper has no counterpart (see fhtdp_batch_autotune). */
+int fhtdp_batch_choice(const fhtdp_batch_plan *plan, int n, int *mode, long long *target,
+                       int *tile, int *depth);
+/* Sets, by hand, the column tile width and register FHT depth of the plan's
+ * uint8 images of band height n (the choices of step 2 of
+ * fhtdp_batch_autotune; FHTDP_EINVAL for one that band height does not
+ * allow) and enqueues the upload of the new layout and queue into the bound
+ * workspace `ws`.  The paper has no counterpart (see fhtdp_batch_autotune). */
+int fhtdp_batch_configure(fhtdp_batch_plan *plan, void *ws, int n, int tile, int depth,
+                          cudaStream_t stream);
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan);
 
 #ifdef __cplusplus

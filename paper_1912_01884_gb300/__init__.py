@@ -91,6 +91,9 @@ _SIGS = {
     "fhtdp_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "fhtdp_batch_plan_destroy": (None, [ctypes.c_void_p]),
+    "fhtdp_batch_choice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
+    "fhtdp_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 3
+                              + [ctypes.c_void_p]),
     "fhtdp_angle_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     "fhtdp_gauss_rows": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
                          + [ctypes.c_void_p, ctypes.c_void_p]),
@@ -328,12 +331,30 @@ class BatchPlan:
         return workspace_status(self.ws, stream)
 
     def autotune(self, reps=3, stream=None):
-        """Picks the work-queue group width by timing runs (synchronises the
-        stream); returns the chosen width in column tiles per band level."""
+        """Tunes the queue schedule and width and, per band height, the tile
+        width and register FHT depth by timing runs (synchronises the stream);
+        returns the chosen width in column tiles per band level or step."""
         t = ctypes.c_longlong(0)
         _check(lib().fhtdp_batch_autotune(self._plan, self.ws.data_ptr(), int(reps),
                                           _stream(stream), ctypes.byref(t)))
         return t.value
+
+    def choice(self, n: int):
+        """The plan's schedule ("groups" or "chains"), width, and the tile
+        width and register FHT depth of its images of band height n."""
+        mode, target = ctypes.c_int(0), ctypes.c_longlong(0)
+        tile, depth = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().fhtdp_batch_choice(self._plan, int(n), ctypes.byref(mode),
+                                        ctypes.byref(target), ctypes.byref(tile),
+                                        ctypes.byref(depth)))
+        return {"schedule": "chains" if mode.value else "groups", "width": target.value,
+                "tile": tile.value, "depth": depth.value}
+
+    def configure(self, n: int, tile: int, depth: int, stream=None):
+        """Sets the tile width and register FHT depth of the images of band
+        height n by hand (the tuner's per-height choices)."""
+        _check(lib().fhtdp_batch_configure(self._plan, self.ws.data_ptr(), int(n), int(tile),
+                                           int(depth), _stream(stream)))
 
     def close(self):
         if self._plan:

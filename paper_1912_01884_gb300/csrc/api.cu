@@ -599,6 +599,21 @@ int fhtdp_batch_autotune(fhtdp_batch_plan *plan, void *ws, int reps, cudaStream_
     return batch_autotune(plan->impl, ws, reps, stream, target_out);
 }
 
+int fhtdp_batch_choice(const fhtdp_batch_plan *plan, int n, int *mode, long long *target,
+                       int *tile, int *depth) {
+    g_last_error[0] = 0;
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    batch_choice(plan->impl, n, mode, target, tile, depth);
+    return FHTDP_OK;
+}
+
+int fhtdp_batch_configure(fhtdp_batch_plan *plan, void *ws, int n, int tile, int depth,
+                          cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    return batch_configure(plan->impl, ws, n, tile, depth, stream);
+}
+
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan) {
     if (!plan) return;
     batch_destroy(plan->impl);

@@ -78,6 +78,7 @@ struct ImgDesc {
     long long pitch;          // row stride in elements
     int h, w, k, n, log2n, B, tiles;
     int tw;                   // column tile width of its work items (uint8: 64, 128 or 256)
+    int depth;                // uint8: FHT levels done in registers before the merges (2 or 3)
     long long item0;          // first work item of this image
     void *mbuf[2];            // ping-pong window maxima, [D][mpitch] of Acc
     int mpitch;
@@ -1145,9 +1146,8 @@ struct U8Path {
     // columns after them (from the next lane, which holds chunk c+1), and
     // stores the 4 shifts of the sub-band to rows 4g + brev2(s).
     template <typename Src>
-    __device__ static void fht_regs(uint32_t *F, int pitch, const ImgDesc &im, const Src &src,
+    __device__ static void fht_regs(uint32_t *F, int pitch, int n, int T, const Src &src,
                                     int x0) {
-        const int n = im.n, T = tw(im);
         const int C8 = (T + n - 4 + 7) / 8;   // chunks covering the level-2 width
         const int tasks = (n / 4) * C8;
         const int lane = threadIdx.x & 31;
@@ -1241,18 +1241,18 @@ struct U8Path {
             }
             pipe.phase ^= 1u;
             const StagedPixels src{st, n, xs, nb * 128 - 8};
-            if (n >= 8) {
+            if (n >= 8 && im.depth == 3) {
                 fht_regs8(F, pitch, n, T, src, x0);
                 compact = !fht_merge<uint32_t>(F, pitch, n, log2n, T, 4, Hc);
             } else {
-                fht_regs(F, pitch, im, src, x0);
+                fht_regs(F, pitch, n, T, src, x0);
                 compact = !fht_merge<uint32_t>(F, pitch, n, log2n, T, 3, Hc);
             }
         } else if (n >= 4) {
             const GlobalPixels src{(const uint8_t *)im.img + (size_t)band * n * im.pitch,
                                    im.pitch, im.w,
                                    ((uintptr_t)im.img % 8 == 0) && (im.pitch % 8 == 0)};
-            fht_regs(F, pitch, im, src, x0);
+            fht_regs(F, pitch, n, T, src, x0);
             compact = !fht_merge<uint32_t>(F, pitch, n, log2n, T, 3, Hc);
         } else {
             load_strip(F, pitch, im, band, x0);
@@ -1649,7 +1649,7 @@ struct U8Path {
         // displacements 2s and 2s + 1 (d = 0 once, with sign 0).  The L2
         // loads of a batch of tasks are issued before any of its work.
         unsigned long long best = 0;
-        constexpr int kTasks = 2 * 128 * (T / 4), kLB = 4;
+        constexpr int kTasks = 2 * 128 * (T / 4), kLB = 8;
         static_assert(kTasks % (kLB * kThreads) == 0, "whole batches");
 #pragma unroll 1
         for (int b0 = 0; b0 < kTasks; b0 += kLB * kThreads) {
@@ -2318,6 +2318,7 @@ struct ImgPlan {
     Shape s;
     int B, tiles, mpitch;
     int T;                      // column tile width of its work items
+    int depth;                  // uint8: FHT levels in registers (2 or 3)
     int kind;                   // 1: 256-row bands through half-band and DP items
     int ftiles, hpitch, moff;   // kind 1: half-band tiles, h256 row pitch; M column offset
     long long item0;
@@ -2353,12 +2354,26 @@ bool fused_256(int dtype, const Shape &s, int B, const void *img, long long pitc
 // Queue-entry code of a tile width: T = 64 << code.
 int tile_code(int T) { return T == 256 ? 2 : T == 64 ? 0 : 1; }
 
-RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
+// Tile widths a uint8 image's items may take (the tuner's choices): bands of
+// at most 64 rows 128 or 256, 128-row bands 128, 256-row bands 64.
+bool tile_choice(int dtype, const ImgPlan &p, int T) {
+    if (dtype != FHTDP_U8 || p.kind == 1) return T == p.T;
+    return T == kTile || (T == 2 * kTile && p.s.n <= max_band<2 * kTile>());
+}
+
+// With `reserve`, every image's counters and buffers are sized for the
+// largest of its tile-width choices (most tiles, widest M rows), so that the
+// workspace fits any choice the tuner makes.
+RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table, bool reserve = false,
+                      int dtype = FHTDP_U8) {
     RunLayout L{};
     size_t off = sizeof(Ctl);
     long long items = 0;
     for (auto &p : imgs) {
+        const int T0 = p.T;
+        if (reserve && tile_choice(dtype, p, kTile)) p.T = kTile;   // the most tiles
         p.tiles = tiles_of(p.s, p.T);
+        if (reserve && tile_choice(dtype, p, 2 * kTile)) p.T = 2 * kTile;   // the widest rows
         p.item0 = items;
         items += (long long)p.s.k * p.tiles;
         if (p.kind == 1) {
@@ -2376,6 +2391,7 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table) {
             p.moff = kMOff;
             p.mpitch = (int)align_up((size_t)kMOff + p.s.w + p.T + 4, 32);
         }
+        p.T = T0;
         p.flags = off;
         off = align_up(off + (size_t)p.s.k * p.tiles * 4, 8);
         p.best = off;
@@ -2482,6 +2498,7 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     im.B = p.B;
     im.tiles = p.tiles;
     im.tw = p.T;
+    im.depth = p.depth;
     im.item0 = p.item0;
     char *data = ws + L.data_off;
     im.mbuf[0] = data + p.m0;
@@ -2637,6 +2654,7 @@ ImgPlan single_plan(int dtype, const void *img, int pitch, const Shape &s, int B
                     int32_t *x_out, int32_t *d_out, void *score_out) {
     ImgPlan p{};
     p.T = default_tile(dtype, s.n);
+    p.depth = 3;
     p.io.img = img;
     p.io.h = s.h;
     p.io.w = s.w;
@@ -2674,22 +2692,20 @@ struct BatchPlan {
     std::vector<ImgDesc> staging;   // image table as uploaded
     std::vector<Item> order;        // work queue as uploaded
     void *bound_ws = nullptr;
-    long long target = 0;           // queue group width (tiles per band level)
+    long long target = 0;           // queue width (tiles per band level or step)
+    int mode = 0;                   // queue schedule, see queue_order
+    size_t reserve = 0;             // bytes of the fused part for any tile-width choice
+    size_t ws_total = 0;            // workspace bytes (the reserve and the side lanes)
     ~BatchPlan() {
         for (cudaStream_t st : side) cudaStreamDestroy(st);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
 };
 
-// Queue order of a batch.  Images are taken in groups whose band levels
-// hold about `target` tiles each; inside a group the items go band level by
-// band level (the last band of every image first), image by image, tile by
-// tile.  Every item therefore comes after the band+1 tiles it waits for, so
-// the queue cannot deadlock, and the band chains of a whole group advance
-// together instead of one image at a time.  Groups bound the number of
-// images in flight, so their M buffers stay in L2.  The batch is split into
-// round(total / target) groups of about equal width, so that no narrow
-// remainder group runs its band chain alone at the end.
+// Queue orders of a batch.  Both put every item after the band+1 tiles it
+// waits for, so the queue cannot deadlock, and both bound the images in
+// flight, whose window-maximum buffers should stay in L2.
+//
 // Items of a band level of an image, in tiles of 128 x 128 work (a 256-row
 // band level also holds the half-band FHT items of the band above).
 long long level_weight(const ImgPlan &p) { return p.kind == 1 ? p.tiles + 2LL * p.ftiles : p.tiles; }
@@ -2714,7 +2730,13 @@ void push_level(std::vector<Item> &order, const ImgPlan &p, int i, int lv) {
     for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemBand << 19});
 }
 
-std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target) {
+// Groups: images are taken in groups whose band levels hold about `target`
+// tiles each; inside a group the items go band level by band level (the last
+// band of every image first), image by image, tile by tile, so the band
+// chains of a whole group advance together.  The batch is split into
+// round(total / target) groups of about equal width, so that no narrow
+// remainder group runs its band chain alone at the end.
+std::vector<Item> queue_grouped(const std::vector<ImgPlan> &imgs, long long target) {
     std::vector<Item> order;
     long long total = 0;
     for (const ImgPlan &p : imgs) total += level_weight(p);
@@ -2737,6 +2759,53 @@ std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target
         first = last;
     }
     return order;
+}
+
+// Band chains: an active set of images advances one band level per step,
+// each step holding every active image's next level, image by image, tile
+// by tile.  Images join the set, the longest chains (most bands) first,
+// whenever its width (tiles per step) drops below `target`, so that steps
+// keep about the same width while images of different heights finish at
+// different times, and the longest chains start with the batch.
+std::vector<Item> queue_chains(const std::vector<ImgPlan> &imgs, long long target) {
+    // the longest band chains first, so that they start with the batch
+    std::vector<int> by_k(imgs.size());
+    for (size_t i = 0; i < imgs.size(); ++i) by_k[i] = (int)i;
+    std::stable_sort(by_k.begin(), by_k.end(),
+                     [&](int a, int b) { return imgs[a].s.k > imgs[b].s.k; });
+    std::vector<Item> order;
+    struct Active {
+        int image, level;
+    };
+    std::vector<Active> active;
+    size_t next = 0;
+    long long width = 0;
+    target = std::max(1LL, target);
+    while (next < imgs.size() || !active.empty()) {
+        while (next < imgs.size() && (active.empty() || width < target)) {
+            active.push_back(Active{by_k[next], 0});
+            width += level_weight(imgs[by_k[next]]);
+            ++next;
+        }
+        std::vector<Active> still;
+        for (Active &a : active) {
+            const ImgPlan &p = imgs[a.image];
+            push_level(order, p, a.image, a.level);
+            if (++a.level < p.s.k)
+                still.push_back(a);
+            else
+                width -= level_weight(p);
+        }
+        active.swap(still);
+    }
+    return order;
+}
+
+// The queue order of a schedule: 0 groups of images advancing together
+// (queue_grouped), 1 band chains joining as others finish, longest first
+// (queue_chains).
+std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target, int mode) {
+    return mode ? queue_chains(imgs, target) : queue_grouped(imgs, target);
 }
 
 size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
@@ -2812,14 +2881,18 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
             plan->imgs.push_back(p);
     }
     plan->L = plan_layout(plan->imgs, true);
+    {
+        std::vector<ImgPlan> any = plan->imgs;
+        plan->reserve = plan_layout(any, true, true, dtype).total;
+    }
     // Scratch of the standalone path: up to kSideLanes lanes, each a stream
     // that runs its images one after the other on its own slice.
     size_t sep = 0;
     for (auto &p : plan->separate) sep = std::max(sep, engine_workspace_bytes(dtype, p.s, p.io.B));
     plan->sep_bytes = align_up(sep, 256);
     plan->lanes = (int)std::min<size_t>(kSideLanes, plan->separate.size());
-    plan->separate_off = align_up(plan->L.total, 256);
-    if (sep) plan->L.total = plan->separate_off + plan->sep_bytes * plan->lanes;
+    plan->separate_off = align_up(plan->reserve, 256);
+    plan->ws_total = sep ? plan->separate_off + plan->sep_bytes * plan->lanes : plan->reserve;
     for (int l = 0; l < plan->lanes; ++l) {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -2837,7 +2910,7 @@ int batch_create(const fhtdp_image *images, int count, int dtype, BatchPlan **ou
         plan->ev.push_back(e);
     }
     plan->target = num_sms();
-    plan->order = queue_order(plan->imgs, plan->target);
+    plan->order = queue_order(plan->imgs, plan->target, plan->mode);
     *out = plan;
     return FHTDP_OK;
 }
@@ -2850,15 +2923,12 @@ void set_nflags(BatchPlan *plan) {
                     (tile_code(plan->imgs[it.image].T) << 17);
 }
 
-size_t batch_workspace_bytes(const BatchPlan *plan) { return plan ? plan->L.total : 0; }
+size_t batch_workspace_bytes(const BatchPlan *plan) { return plan ? plan->ws_total : 0; }
 
 long long batch_items(const BatchPlan *plan) { return plan ? plan->L.items : 0; }
 
-int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream) {
-    if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
-    if (ws_bytes < plan->L.total)
-        return set_error(FHTDP_EWORKSPACE, "batch workspace needs %zu bytes, got %zu",
-                         plan->L.total, ws_bytes);
+// The image table and the queue of the plan's current layout into `ws`.
+int upload_tables(BatchPlan *plan, void *ws, cudaStream_t stream) {
     plan->staging.clear();
     for (auto &p : plan->imgs) {
         plan->staging.push_back(make_desc(p, plan->L, (char *)ws, plan->dtype));
@@ -2868,7 +2938,6 @@ int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream
                              "tensor maps of a 256-row-band image could not be encoded");
     }
     set_nflags(plan);
-    plan->bound_ws = ws;
     int st = cuda_status(cudaMemcpyAsync((char *)ws + plan->L.table_off, plan->staging.data(),
                                          sizeof(ImgDesc) * plan->staging.size(),
                                          cudaMemcpyHostToDevice, stream),
@@ -2878,6 +2947,15 @@ int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream
                                        sizeof(Item) * plan->order.size(),
                                        cudaMemcpyHostToDevice, stream),
                        "cudaMemcpyAsync");
+}
+
+int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
+    if (ws_bytes < plan->ws_total)
+        return set_error(FHTDP_EWORKSPACE, "batch workspace needs %zu bytes, got %zu",
+                         plan->ws_total, ws_bytes);
+    plan->bound_ws = ws;
+    return upload_tables(plan, ws, stream);
 }
 
 int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
@@ -2921,70 +2999,189 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
     return st ? st : FHTDP_OK;
 }
 
-// Times the bound batch for a few queue group widths (from half a wave to the
-// whole batch in one group: fewer, wider groups wait less for dependencies
-// but keep more window-maximum buffers in flight in L2), keeps the fastest
-// and uploads its order.  Synchronises `stream` after every candidate.
+// Tunes the bound batch by timing runs (synchronising `stream` after every
+// candidate) and keeps the fastest of each choice in turn:
+//   1. the queue schedule (groups or band chains) and its width, from half a
+//      wave to the whole batch at once (wider steps wait less for
+//      dependencies but keep more window-maximum buffers in flight in L2);
+//   2. for each band height of the uint8 images, the column tile width of
+//      its items (128 or 256 columns where shared memory allows) and the
+//      number of FHT levels done in registers before the shared-memory merges
+//      (2 or 3), applied to every image of that height;
+//   3. the schedule again, for the tile widths chosen.
+// Leaves the workspace with the chosen layout and queue uploaded.
 int batch_autotune(BatchPlan *plan, void *ws, int reps, cudaStream_t stream, long long *chosen) {
     if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
     if (ws != plan->bound_ws)
         return set_error(FHTDP_EINVAL, "workspace differs from the one given to fhtdp_batch_upload");
     if (reps < 1) reps = 1;
-    long long total = 0;
-    for (const ImgPlan &p : plan->imgs) total += p.tiles;
-    const long long sms = num_sms();
-    if (plan->imgs.empty() || total == 0) {
+    if (plan->imgs.empty()) {
         if (chosen) *chosen = plan->target;
         return FHTDP_OK;
     }
-    // Candidates by the number of groups they give, each width once.
-    std::vector<long long> cands;
-    std::vector<long long> groups_seen;
-    const long long widths[] = {sms / 2, 3 * sms / 4, sms, 3 * sms / 2, 2 * sms, 3 * sms, total};
-    for (long long t : widths) {
-        if (t < 1) continue;
-        const long long g = std::max(1LL, (total + t / 2) / t);
-        if (std::find(groups_seen.begin(), groups_seen.end(), g) != groups_seen.end()) continue;
-        groups_seen.push_back(g);
-        cands.push_back(t);
-    }
-    char *base = (char *)ws;
-    auto upload = [&](long long t) {
-        plan->order = queue_order(plan->imgs, t);
-        set_nflags(plan);
-        return cuda_status(cudaMemcpyAsync(base + plan->L.order_off, plan->order.data(),
-                                           sizeof(Item) * plan->order.size(),
-                                           cudaMemcpyHostToDevice, stream),
-                           "cudaMemcpyAsync");
-    };
+    const long long sms = num_sms();
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = cuda_status(cudaEventCreate(&e0), "cudaEventCreate");
     if (!st) st = cuda_status(cudaEventCreate(&e1), "cudaEventCreate");
-    long long best_t = plan->target;
-    float best_ms = -1.0f;
-    for (size_t c = 0; c < cands.size() && !st; ++c) {
-        st = upload(cands[c]);
-        if (!st) st = batch_run(plan, ws, stream);   // warm-up
-        if (!st) st = cuda_status(cudaEventRecord(e0, stream), "cudaEventRecord");
-        for (int r = 0; r < reps && !st; ++r) st = batch_run(plan, ws, stream);
-        if (!st) st = cuda_status(cudaEventRecord(e1, stream), "cudaEventRecord");
-        if (!st) st = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
-        float ms = 0.0f;
-        if (!st) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
-        if (!st && (best_ms < 0.0f || ms < best_ms)) {
-            best_ms = ms;
-            best_t = cands[c];
+    // Runs of the current layout and queue: warm-up, then `reps` timed; the
+    // first candidate raises `reps` so that each candidate is timed over
+    // about 8 ms (short batches are otherwise within the timing noise).
+    bool sized = false;
+    auto time_runs = [&](float *ms) -> int {
+        int r = batch_run(plan, ws, stream);
+        if (!r) r = cuda_status(cudaEventRecord(e0, stream), "cudaEventRecord");
+        for (int i = 0; i < reps && !r; ++i) r = batch_run(plan, ws, stream);
+        if (!r) r = cuda_status(cudaEventRecord(e1, stream), "cudaEventRecord");
+        if (!r) r = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        if (!r) r = cuda_status(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+        if (!r) *ms /= reps;
+        if (!r && !sized) {
+            sized = true;
+            if (*ms > 0.0f) reps = std::max(reps, std::min(64, (int)(8.0f / *ms)));
         }
+        return r;
+    };
+    // Lays the plan out again (tile widths may have changed) and uploads it.
+    auto apply = [&](long long t, int mode) -> int {
+        plan->L = plan_layout(plan->imgs, true);
+        if (plan->L.total > plan->reserve)
+            return set_error(FHTDP_EWORKSPACE, "tuned layout exceeds the reserved workspace");
+        plan->order = queue_order(plan->imgs, t, mode);
+        return upload_tables(plan, ws, stream);
+    };
+    float best_ms = -1.0f;
+    auto tune_schedule = [&]() -> int {
+        long long total = 0;
+        for (const ImgPlan &p : plan->imgs) total += level_weight(p);
+        std::vector<long long> cands;
+        const long long widths[] = {sms / 2, 3 * sms / 4, sms, 3 * sms / 2, 2 * sms, 3 * sms,
+                                    4 * sms, 6 * sms, total};
+        for (long long t : widths) {
+            if (t < 1) continue;
+            t = std::min(t, total);   // every width of at least the batch gives one order
+            if (std::find(cands.begin(), cands.end(), t) == cands.end()) cands.push_back(t);
+        }
+        long long bt = plan->target;
+        int bm = plan->mode;
+        float bms = -1.0f;
+        int r = 0;
+        for (size_t c = 0; c < 2 * cands.size() && !r; ++c) {
+            const int mode = (int)(c / cands.size());
+            const long long t = cands[c % cands.size()];
+            r = apply(t, mode);
+            float ms = 0.0f;
+            if (!r) r = time_runs(&ms);
+            if (!r && (bms < 0.0f || ms < bms)) {
+                bms = ms;
+                bt = t;
+                bm = mode;
+            }
+        }
+        plan->target = bt;
+        plan->mode = bm;
+        best_ms = bms;
+        return r;
+    };
+    if (!st) st = tune_schedule();
+    if (!st && plan->dtype == FHTDP_U8) {
+        std::vector<int> heights;
+        for (const ImgPlan &p : plan->imgs)
+            if (std::find(heights.begin(), heights.end(), p.s.n) == heights.end())
+                heights.push_back(p.s.n);
+        for (size_t hi = 0; hi < heights.size() && !st; ++hi) {
+            const int n = heights[hi];
+            if (n < 4) continue;   // no register levels to choose, one tile width
+            ImgPlan *first = nullptr;
+            for (ImgPlan &p : plan->imgs)
+                if (p.s.n == n) {
+                    first = &p;
+                    break;
+                }
+            const int T0 = first->T, D0 = first->depth;
+            int bT = T0, bD = D0;
+            const int Ts[2] = {kTile, 2 * kTile};
+            for (int ti = 0; ti < 2 && !st; ++ti)
+                for (int depth = 2; depth <= 3 && !st; ++depth) {
+                    const int T = first->kind == 1 ? T0 : Ts[ti];
+                    if (ti == 1 && first->kind == 1) continue;
+                    if (!tile_choice(plan->dtype, *first, T)) continue;
+                    if (depth == 3 && n < 8) continue;
+                    if (T == T0 && depth == D0) continue;   // timed already
+                    for (ImgPlan &p : plan->imgs)
+                        if (p.s.n == n) {
+                            p.T = T;
+                            p.depth = depth;
+                        }
+                    st = apply(plan->target, plan->mode);
+                    float ms = 0.0f;
+                    if (!st) st = time_runs(&ms);
+                    if (!st && ms < best_ms) {
+                        best_ms = ms;
+                        bT = T;
+                        bD = depth;
+                    }
+                }
+            for (ImgPlan &p : plan->imgs)
+                if (p.s.n == n) {
+                    p.T = bT;
+                    p.depth = bD;
+                }
+        }
+        if (!st) st = tune_schedule();
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    // Whatever happened, leave the plan and the workspace with one order.
-    const int us = upload(best_t);
+    // Whatever happened, leave the plan and the workspace with one layout.
+    const int us = apply(plan->target, plan->mode);
     if (!st) st = us;
     if (!st) st = cuda_status(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
-    plan->target = best_t;
-    if (chosen) *chosen = best_t;
+    if (chosen) *chosen = plan->target;
     return st;
+}
+
+// Sets the tile width and register FHT depth of the plan's images of band
+// height n and uploads the new layout and queue into its bound workspace.
+int batch_configure(BatchPlan *plan, void *ws, int n, int tile, int depth, cudaStream_t stream) {
+    if (!plan || !ws) return set_error(FHTDP_EINVAL, "null plan or workspace");
+    if (ws != plan->bound_ws)
+        return set_error(FHTDP_EINVAL, "workspace differs from the one given to fhtdp_batch_upload");
+    bool any = false;
+    for (const ImgPlan &p : plan->imgs) {
+        if (p.s.n != n) continue;
+        any = true;
+        if (!tile_choice(plan->dtype, p, tile))
+            return set_error(FHTDP_EINVAL, "tile width %d not available for band height %d",
+                             tile, n);
+        if (depth < 2 || depth > 3 || (depth == 3 && n < 8))
+            return set_error(FHTDP_EINVAL, "register depth %d not available for band height %d",
+                             depth, n);
+    }
+    if (!any) return set_error(FHTDP_EINVAL, "no image of band height %d in the fused launch", n);
+    for (ImgPlan &p : plan->imgs)
+        if (p.s.n == n) {
+            p.T = tile;
+            p.depth = depth;
+        }
+    plan->L = plan_layout(plan->imgs, true);
+    plan->order = queue_order(plan->imgs, plan->target, plan->mode);
+    return upload_tables(plan, ws, stream);
+}
+
+// The plan's queue schedule and width, and the tile width and register
+// depth of its images of band height n (0 when it has none).
+void batch_choice(const BatchPlan *plan, int n, int *mode, long long *target, int *tile,
+                  int *depth) {
+    if (mode) *mode = plan->mode;
+    if (target) *target = plan->target;
+    int T = 0, dd = 0;
+    for (const ImgPlan &p : plan->imgs)
+        if (p.s.n == n) {
+            T = p.T;
+            dd = p.depth;
+            break;
+        }
+    if (tile) *tile = T;
+    if (depth) *depth = dd;
 }
 
 void batch_destroy(BatchPlan *plan) { delete plan; }

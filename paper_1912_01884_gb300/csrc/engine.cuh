@@ -15,6 +15,9 @@ long long batch_items(const BatchPlan *plan);
 int batch_upload(BatchPlan *plan, void *ws, size_t ws_bytes, cudaStream_t stream);
 int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream);
 int batch_autotune(BatchPlan *plan, void *ws, int reps, cudaStream_t stream, long long *chosen);
+void batch_choice(const BatchPlan *plan, int n, int *mode, long long *target, int *tile,
+                  int *depth);
+int batch_configure(BatchPlan *plan, void *ws, int n, int tile, int depth, cudaStream_t stream);
 void batch_destroy(BatchPlan *plan);
 void debug_inject(int band, int tile, long long wait_cycles);
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,

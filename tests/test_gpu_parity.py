@@ -394,3 +394,32 @@ def test_batch_of_256_row_bands_runs_in_one_launch(lib):
     _check_batch(plan, wls)
     plan.run()
     _check_batch(plan, wls)
+
+
+def test_batch_every_tile_width_and_register_depth_is_exact(lib):
+    """Every per-band-height choice the tuner can make (tile width 128 or
+    256 columns, 2 or 3 FHT levels in registers; 256-row bands: the depth of
+    their halves) gives the oracle's results."""
+    # widths that are multiples of 16 take the TMA strip (where the register
+    # depth applies); 700 takes plain loads
+    shapes = [(512, 704, 16, 4), (512, 304, 8, 8), (1024, 528, 8, 16), (512, 256, 2, 32),
+              (256, 272, 32, 1), (256, 208, 64, 1), (512, 700, 16, 3)]
+    wls = [synth.plain_uniform(400 + j, h, w, k, B) for j, (h, w, k, B) in enumerate(shapes)]
+    imgs = [to_device(wl.img) for wl in wls]
+    plan = lib.BatchPlan(imgs, [wl.k for wl in wls], [wl.B for wl in wls])
+    variants = {32: [(128, 2), (128, 3), (256, 2), (256, 3)],
+                64: [(128, 2), (128, 3), (256, 2), (256, 3)],
+                128: [(128, 2), (128, 3)], 256: [(64, 2), (64, 3)],
+                8: [(128, 2), (128, 3), (256, 3)], 4: [(128, 2), (256, 2)]}
+    for n, choices in variants.items():
+        for tile, depth in choices:
+            plan.configure(n, tile, depth)
+            assert plan.choice(n)["tile"] == tile and plan.choice(n)["depth"] == depth
+            for t in plan.x:
+                t.fill_(-7)
+            plan.run()
+            _check_batch(plan, wls)
+    with pytest.raises(lib.FhtdpError):
+        plan.configure(128, 256, 3)   # 128-row bands do not fit 256 columns
+    with pytest.raises(lib.FhtdpError):
+        plan.configure(4, 128, 3)     # 4-row bands have only 2 register levels
