@@ -3,30 +3,37 @@
 read-back) in Mpix/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload plain2048|mixed|float8192|plain256|angle2048|through2048|
-                                horizontal2048|two2048|padded2048]
-                    [--images I]
+                    [--workload mixed|plain2048|float8192|plain256|angle2048|through2048|
+                                horizontal2048|two2048|padded2048|learned1024]
+                    [--images I] [--no-extras] [--skip-cpu]
 
-Default workload: synthetic 2048x2048 uint8 images, k=16 bands of 128 rows,
-bend range 16.  A step is one pass of the whole method over a batch of
---images distinct seeded images per GPU: one persistent kernel launch, inputs
-already resident in HBM.  Each batch is larger than the 129 MB L2, so no
-flush is needed between steps.  Under torchrun each rank takes its own
-images (weak scaling, no data-path collective) and rank 0 prints one JSON
-line.  ``--impl reference`` times the CPU oracle (the method as a plain C
-program) on a bounded sample of the same workload on the host cores; the
-paper has no code of its own to run.
+Default workload: the mixed batch of 256 synthetic uint8 images (heights 512..4096,
+widths 512..3072, bands of 32..256 rows, bend range 1/8 of the band height).
+A step is one pass of the whole method over the batch of distinct seeded
+images per GPU: one persistent kernel launch, replayed from a CUDA graph,
+inputs already resident in HBM.  Each batch is larger than the 129 MB L2, so
+no flush is needed between steps.  The same JSON line carries the 2048x2048
+single-size batch and the 8192x8192 float response map as extra keys
+(--no-extras omits them).  Under torchrun each rank takes its own images (weak
+scaling, no data-path collective) and rank 0 prints one JSON line.
+``--impl reference`` times the CPU oracle (the method as a plain C program)
+on bounded samples of the same workload on the host cores; the paper has no
+code of its own to run.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -34,12 +41,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpix/s end-to-end band-FHT+DP (exact) and % HBM roofline; batched/learned vs plain"
 
 WORKLOADS = {
+    "mixed": dict(
+        desc="mixed batch: 256 u8 images, h in 512..4096, w in 512..3072 (step 256), band "
+             "height 32..256, bend = band/8, uniform noise 0..40 + 1 polyline of 200",
+        images=256, dtype="u8"),
     "plain2048": dict(
         desc="u8 2048x2048, k=16 bands of 128 rows, bend |d_{i+1}-d_i|<=16, Gaussian noise + 3 "
              "polylines", images=32, dtype="u8"),
-    "mixed": dict(
-        desc="mixed batch: u8, h in 512..4096, w in 512..3072 (step 256), band height 32..256, "
-             "bend = band/8, uniform noise + 1 polyline", images=256, dtype="u8"),
     "float8192": dict(
         desc="f32 8192x8192 ridge response, k=64 bands of 128 rows, bend 24", images=1,
         dtype="f32"),
@@ -70,13 +78,14 @@ WORKLOADS = {
              "window proposal (4-layer 32-channel bf16 CNN on the 4x downsample, windows of 16) "
              "+ pruned DP + full-DP fallback, against the plain DP", images=512, dtype="u8"),
 }
+# Workloads measured by the default run besides the headline one (N = 1).
+EXTRAS = ("plain2048", "float8192")
 
-# DRAM bytes (read + write) per image of engine_kernel_u8 on the default
-# workload from the ncu capture summarised in
-# profiles/engine_kernel_u8_2048x2048_k16_B16.md (48 images per launch); a
-# launch's traffic is this times its images.  None for other workloads, and
-# to be reset whenever the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES_PER_IMAGE = {"plain2048": (299.827456e6 + 1571.180e6) / 48}
+# DRAM bytes (read + write) per pixel of the fused engine's launch on each
+# batched workload, from the ncu captures summarised in profiles/; a launch's
+# traffic is this times its pixels.  None where no capture of the current
+# kernel exists (reset whenever the kernel changes until it is captured again).
+NCU_TRAFFIC_BYTES_PER_PIXEL = {}
 # The window DP kernel changed (it now takes any window table and value
 # type) after its ncu capture (profiles/dp_band_angle_kernel_2048x2048_k16_gamma10.md,
 # 4.14 MB per band launch), so the standalone workloads report no traffic
@@ -113,11 +122,13 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="plain2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="mixed", choices=sorted(WORKLOADS))
     ap.add_argument("--images", type=int, default=0, help="images per step per GPU")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU baseline leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="omit the extra workloads of the default run")
     ap.add_argument("--lanes", type=int, default=0,
                     help="angle2048: streams a step spreads its images over (default 8)")
     return ap.parse_args()
@@ -141,18 +152,68 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clocks and throttle reasons sampled during the timed region: through
+    NVML (every 10 ms, read-only queries) where libnvidia-ml loads, else with
+    nvidia-smi every 200 ms."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    # NVML clock-event reason bits (public NVML API constants)
+    BITS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+            0x4: "sw_power_cap"}
+    PERIOD_S = 0.01
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, uuid=None):
         self.gpu = gpu_index
+        self.uuid = uuid
         self.proc = None
         self.file = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
+        self.smax = None
+        self.stop_flag = threading.Event()
+
+    def _nvml_open(self):
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            h = ctypes.c_void_p()
+            found = False
+            if self.uuid:   # the CUDA device itself, whatever CUDA_VISIBLE_DEVICES says
+                found = lib.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h)) == 0
+            if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu),
+                                                               ctypes.byref(h)) != 0:
+                return None
+            self.reasons_fn = (getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or
+                               getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None))
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:   # NVML_CLOCK_SM
+                self.smax = float(mx.value)
+            return lib, h
+        except OSError:
+            return None
+
+    def _nvml_loop(self):
+        lib, h = self.nvml
+        clk = ctypes.c_uint()
+        reasons = ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            ok = lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0
+            rr = (self.reasons_fn is not None and
+                  self.reasons_fn(h, ctypes.byref(reasons)) == 0)
+            if ok:
+                self.samples.append((float(clk.value), int(reasons.value) if rr else 0))
+            time.sleep(self.PERIOD_S)
 
     def start(self):
+        self.nvml = self._nvml_open()
+        if self.nvml:
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
@@ -163,6 +224,17 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            sm = [c for c, _ in self.samples]
+            reasons = set()
+            for _, r in self.samples:
+                for bit, name in self.BITS.items():
+                    if r & bit:
+                        reasons.add(name)
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.smax,
+                    "reasons": sorted(reasons), "samples": len(sm), "source": "nvml, 10 ms"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.25)
@@ -184,7 +256,7 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def image_seeds(images, seed, rank):
@@ -233,32 +305,89 @@ def make_workload(name, images, seed, rank):
             for s, (h, w, k, B) in zip(seeds, shapes)]
 
 
+def oracle_one(item, horizontal=False):
+    """The oracle on one image of a workload (the whole method)."""
+    import numpy as np
+    import oracle
+    img, k, B = item
+    if B is None:
+        oracle.detect_angle(img, k, ANGLE_R, ANGLE_GAMMA)
+    elif isinstance(B, tuple) and B[0] == "two":
+        oracle.detect_two(img, k, B[1], B[2])
+    elif isinstance(B, tuple) and B[0] == "padded":
+        oracle.detect_padded(img, k, B[1])
+    elif isinstance(B, tuple):
+        oracle.detect_through(img, k, *B)
+    elif horizontal:
+        oracle.detect_horizontal(img, k, B)
+    elif img.dtype == np.float32:
+        oracle.detect_f32(img, k, B)
+    else:
+        oracle.detect(img, k, B)
+    return img.size
+
+
 def oracle_rate(items, budget_s, horizontal=False):
     """The oracle as it stands, one thread, on images of the workload until
     `budget_s` has passed: (Mpix/s, images done)."""
-    import numpy as np
-    import oracle
     done, pix, t0 = 0, 0, time.perf_counter()
-    for img, k, B in items:
-        if B is None:
-            oracle.detect_angle(img, k, ANGLE_R, ANGLE_GAMMA)
-        elif isinstance(B, tuple) and B[0] == "two":
-            oracle.detect_two(img, k, B[1], B[2])
-        elif isinstance(B, tuple) and B[0] == "padded":
-            oracle.detect_padded(img, k, B[1])
-        elif isinstance(B, tuple):
-            oracle.detect_through(img, k, *B)
-        elif horizontal:
-            oracle.detect_horizontal(img, k, B)
-        elif img.dtype == np.float32:
-            oracle.detect_f32(img, k, B)
-        else:
-            oracle.detect(img, k, B)
+    for item in items:
+        pix += oracle_one(item, horizontal)
         done += 1
-        pix += img.size
         if time.perf_counter() - t0 > budget_s:
             break
     return pix / (time.perf_counter() - t0) / 1e6, done
+
+
+def host_threads():
+    """Threads for the all-core oracle leg (the host's cores, at most 64)."""
+    return max(1, min(64, os.cpu_count() or 1))
+
+
+def oracle_rate_threads(items, threads, horizontal=False):
+    """The oracle as it stands on `items`, one image per task over `threads`
+    host threads (its C calls release the interpreter lock): (Mpix/s, images)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        pix = sum(ex.map(lambda it: oracle_one(it, horizontal), items))
+    return pix / (time.perf_counter() - t0) / 1e6, len(items)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(name, seed):
+    """The oracle on bounded samples of the workload: one thread (images until
+    12 s have passed) and every host core (two images per thread)."""
+    horizontal = name == "horizontal2048"
+    one_rate, one_done = oracle_rate(make_workload(name, 8, 900000 + seed, 0), 12.0, horizontal)
+    th = host_threads()
+    sample = make_workload(name, 2 * th, 950000 + seed, 0)
+    all_rate, all_done = oracle_rate_threads(sample, th, horizontal)
+    return {"value": all_rate, "unit": "Mpix/s", "cores": th, "kind": "oracle",
+            "sample": "%d images of the workload, whole method, one image per task on %d host "
+                      "threads" % (all_done, th),
+            "single_thread": {"value": one_rate, "unit": "Mpix/s", "cores": 1,
+                              "sample": "%d images of the workload, one thread" % one_done},
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
 
 
 def run_reference(args):
@@ -268,15 +397,18 @@ def run_reference(args):
     import oracle
     oracle.build()
     spec = WORKLOADS[args.workload]
-    items = make_workload(args.workload, args.steps + args.warmup, 700000 + args.seed, 0)
+    th = host_threads()
     hor = args.workload == "horizontal2048"
-    for item in items[:args.warmup]:
-        oracle_rate([item], 0, hor)
+    # Each step: a bounded sample of the workload, one image per host thread.
+    items = make_workload(args.workload, (args.steps + args.warmup) * th, 700000 + args.seed, 0)
+    steps = [items[i * th:(i + 1) * th] for i in range(args.steps + args.warmup)]
+    for st in steps[:args.warmup]:
+        oracle_rate_threads(st, th, hor)
     t0 = time.perf_counter()
     pix = 0
-    for item in items[args.warmup:]:
-        oracle_rate([item], 0, hor)
-        pix += item[0].size
+    for st in steps[args.warmup:]:
+        oracle_rate_threads(st, th, hor)
+        pix += sum(it[0].size for it in st)
     dt = time.perf_counter() - t0
     value = pix / dt / 1e6
     print(json.dumps({
@@ -285,16 +417,238 @@ def run_reference(args):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if spec["dtype"] == "u8" else "f32",
         "data": "synthetic",
-        "config": {"workload": spec["desc"], "images_per_step": 1},
-        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                         "sample": "1 image of the workload per step, whole method, one thread"},
+        "config": {"workload": spec["desc"], "images_per_step": th},
+        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": th, "kind": "oracle",
+                         "sample": "%d images of the workload per step, whole method, one "
+                                   "image per task on %d host threads" % (th, th),
+                         "nproc": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
+def gpu_uuid(dev):
+    """NVML name of a CUDA device ("GPU-<uuid>"), or None."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except (AttributeError, RuntimeError):
+        return None
+
+
+class BatchBench:
+    """One batched workload on this rank's GPU: its images resident in HBM,
+    a tuned batch plan, and a CUDA graph of one step (one persistent launch)."""
+
+    def __init__(self, name, images, seed, rank, dev):
+        import numpy as np
+        import torch
+        import paper_1912_01884_gb300 as fd
+        self.fd, self.torch, self.dev = fd, torch, dev
+        self.name = name
+        spec = WORKLOADS[name]
+        self.items = make_workload(name, images, seed, rank)
+        self.tdt = torch.float32 if spec["dtype"] == "f32" else torch.uint8
+        self.esize = 4 if spec["dtype"] == "f32" else 1
+        self.horizontal = name == "horizontal2048"
+        # Inputs: one pinned host buffer and one device buffer, image after
+        # image (each 256-byte aligned); outputs in flat device buffers.
+        self.offs, total = [], 0
+        for img, _, _ in self.items:
+            self.offs.append(total)
+            total += (img.size * self.esize + 255) // 256 * 256
+        self.host = torch.empty(total, dtype=torch.uint8).pin_memory()
+        for (img, _, _), o in zip(self.items, self.offs):
+            self.host[o:o + img.size * self.esize].view(self.tdt).view(img.shape).copy_(
+                torch.from_numpy(img))
+        self.dbuf = self.host.to(dev)
+        self.views = self._views(self.dbuf)
+        self.ks = [k for _, k, _ in self.items]
+        self.Bs = [B for _, _, B in self.items]
+        self.xs = torch.empty(sum(k + 1 for k in self.ks), dtype=torch.int32, device=dev)
+        self.ds = torch.empty(sum(self.ks), dtype=torch.int32, device=dev)
+        self.sc = torch.empty(len(self.items), dtype=torch.float32 if self.tdt == torch.float32
+                              else torch.int32, device=dev)
+        xo = np.cumsum([0] + [k + 1 for k in self.ks])
+        do = np.cumsum([0] + self.ks)
+        self.outs = ([self.xs[xo[i]:xo[i + 1]] for i in range(len(self.items))],
+                     [self.ds[do[i]:do[i + 1]] for i in range(len(self.items))],
+                     [self.sc[i:i + 1] for i in range(len(self.items))])
+        self.stream = torch.cuda.Stream(dev)   # graphs are captured off the default stream
+        if self.horizontal:
+            # every step transposes its images (fhtdp_transpose) into buffers
+            # that one batch plan runs over
+            self.tviews = [torch.empty((img.shape[1], img.shape[0]), dtype=self.tdt, device=dev)
+                           for img, _, _ in self.items]
+            self.plan = fd.BatchPlan(self.tviews, self.ks, self.Bs, out=self.outs,
+                                     stream=self.stream)
+        else:
+            self.plan = fd.BatchPlan(self.views, self.ks, self.Bs, out=self.outs,
+                                     stream=self.stream)
+        # Untimed set-up: the library's tuner picks the queue schedule and, per
+        # band height, the tile width and register depth.
+        self.width = self.plan.autotune(reps=2, stream=self.stream)
+        self.pixels = sum(img.size for img, _, _ in self.items)
+        self.alg = sum(algorithmic_bytes(img.shape[0], img.shape[1], k, self.esize)
+                       for img, k, _ in self.items)
+
+    def _views(self, buf):
+        return [buf[o:o + img.size * self.esize].view(self.tdt).view(img.shape)
+                for (img, _, _), o in zip(self.items, self.offs)]
+
+    def enqueue(self, plan=None, src=None):
+        """One step on self.stream: the whole batch, one persistent launch."""
+        if self.horizontal:
+            for v, t in zip(src or self.views, self.tviews):
+                self.fd.transpose(v, out=t, stream=self.stream)
+        (plan or self.plan).run(stream=self.stream)
+
+    def capture(self):
+        """A CUDA graph of one step; returns the launches it holds."""
+        torch = self.torch
+        self.enqueue()   # first use outside the capture
+        torch.cuda.synchronize(self.dev)
+        l0 = self.fd.launch_count()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            self.enqueue()
+        return self.fd.launch_count() - l0
+
+    def choices(self):
+        ns = sorted(set(img.shape[0] // k for img, k, _ in self.items))
+        if self.horizontal:
+            ns = sorted(set(img.shape[1] // k for img, k, _ in self.items))
+        ch = {n: self.plan.choice(n) for n in ns}
+        first = next(iter(ch.values()))
+        return {"schedule": first["schedule"], "width": first["width"],
+                "per_band_height": {str(n): {"tile": c["tile"], "fht_register_levels": c["depth"]}
+                                    for n, c in ch.items()}}
+
+    def timed_replays(self, steps, warmup, barrier):
+        """Device time of `steps` graph replays (CUDA events on the replay
+        stream), after `warmup` untimed ones."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):   # replay() launches on the current stream
+            for _ in range(warmup):
+                self.graph.replay()
+            barrier()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            # an NVTX range names the timed launches for profilers
+            torch.cuda.nvtx.range_push("timed_" + self.name)
+            for e0, e1 in ev:
+                e0.record(self.stream)
+                self.graph.replay()
+                e1.record(self.stream)
+            torch.cuda.nvtx.range_pop()
+            barrier()
+        self.plan.status(stream=self.stream)
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+
+    def e2e(self, steps, barrier):
+        """End to end through the public API: every step copies its inputs from
+        pinned host memory and reads its results back inside the timed region.
+        Two input buffers (and a plan on each) let the copy of step i+1 run on
+        a copy stream while step i computes; events order each buffer's copy,
+        use and re-use."""
+        torch, fd = self.torch, self.fd
+        dbuf2 = torch.empty_like(self.dbuf)
+        views2 = self._views(dbuf2)
+        if self.horizontal:
+            plan2 = self.plan
+        else:
+            plan2 = fd.BatchPlan(views2, self.ks, self.Bs, out=self.outs, stream=self.stream)
+            plan2.autotune(reps=1, stream=self.stream)
+        plans, bufs, srcs = (self.plan, plan2), (self.dbuf, dbuf2), (self.views, views2)
+        copy_stream = torch.cuda.Stream(self.dev)
+        hx = torch.empty_like(self.xs, device="cpu").pin_memory()
+        hd = torch.empty_like(self.ds, device="cpu").pin_memory()
+        hs = torch.empty_like(self.sc, device="cpu").pin_memory()
+        stream = self.stream
+
+        def run(nsteps):
+            copied = [torch.cuda.Event() for _ in range(2)]
+            used = [torch.cuda.Event() for _ in range(2)]
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            copy_stream.wait_event(t0)
+            with torch.cuda.stream(copy_stream):
+                bufs[0].copy_(self.host, non_blocking=True)
+            copied[0].record(copy_stream)
+            for i in range(nsteps):
+                b = i % 2
+                if i + 1 < nsteps:   # next step's inputs, once that buffer is free
+                    nb = 1 - b
+                    if i >= 1:
+                        copy_stream.wait_event(used[nb])
+                    with torch.cuda.stream(copy_stream):
+                        bufs[nb].copy_(self.host, non_blocking=True)
+                    copied[nb].record(copy_stream)
+                stream.wait_event(copied[b])
+                self.enqueue(plans[b], srcs[b])
+                used[b].record(stream)
+                with torch.cuda.stream(stream):
+                    hx.copy_(self.xs, non_blocking=True)
+                    hd.copy_(self.ds, non_blocking=True)
+                    hs.copy_(self.sc, non_blocking=True)
+            t1.record(stream)
+            stream.synchronize()
+            return t0.elapsed_time(t1) / 1e3
+
+        run(2)
+        barrier()
+        t = run(steps)
+        barrier()
+        h2d = self.dbuf.numel()
+        d2h = (hx.numel() + hd.numel() + hs.numel()) * 4
+        return t, h2d, d2h
+
+    def single_image_ms(self):
+        """Median latency of one image per launch (the first image)."""
+        torch, fd = self.torch, self.fd
+        img0, k0, B0 = self.views[0], self.ks[0], self.Bs[0]
+        dcode = fd.DTYPE_F32 if self.tdt == torch.float32 else fd.DTYPE_U8
+        if self.horizontal:
+            ws1 = torch.empty(fd.horizontal_workspace_bytes(dcode, img0.shape[0], img0.shape[1],
+                                                            k0, B0), dtype=torch.uint8,
+                              device=self.dev)
+            detect_one = fd.detect_polyline_horizontal
+        else:
+            ws1 = torch.empty(fd.workspace_bytes(dcode, img0.shape[0], img0.shape[1], k0, B0),
+                              dtype=torch.uint8, device=self.dev)
+            detect_one = fd.detect_polyline
+        one = (self.outs[0][0], self.outs[1][0], self.outs[2][0])
+        for _ in range(3):
+            detect_one(img0, k0, B0, out=one, ws=ws1, stream=self.stream)
+        lat = []
+        for _ in range(8):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            detect_one(img0, k0, B0, out=one, ws=ws1, stream=self.stream)
+            e1.record(self.stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        return statistics.median(lat)
+
+
+def roofline(bb, per_step_s):
+    """Roofline of the fused engine's launch (one per step): algorithmic
+    bytes per launch over its CUDA-event time, against the measured HBM
+    copy bandwidth; traffic from the ncu capture of the same kernel."""
+    hbm, peak_kind = peaks()
+    achieved = bb.alg / per_step_s / 1e9
+    tpp = NCU_TRAFFIC_BYTES_PER_PIXEL.get(bb.name)
+    kern = ("engine_kernel (float images, one persistent launch per step)"
+            if bb.tdt == bb.torch.float32 else
+            "engine_kernel_u8 (one persistent launch per step%s)"
+            % (", after one transpose_kernel per image" if bb.horizontal else ""))
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": tpp * bb.pixels if tpp else None,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bb.alg, "kernel": kern}
+
+
 def run_ours(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -307,203 +661,72 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     fd.load()
     spec = WORKLOADS[args.workload]
-    I = args.images or spec["images"]
-    items = make_workload(args.workload, I, args.seed, rank)
-    tdt = torch.float32 if spec["dtype"] == "f32" else torch.uint8
-    esize = 4 if spec["dtype"] == "f32" else 1
-
-    # Inputs: one pinned host buffer and one device buffer, image after image
-    # (each image 256-byte aligned); outputs in flat device buffers.
-    offs, total = [], 0
-    for img, _, _ in items:
-        offs.append(total)
-        total += (img.size * esize + 255) // 256 * 256
-    host_bytes = torch.empty(total, dtype=torch.uint8).pin_memory()
-    for (img, _, _), o in zip(items, offs):
-        host_bytes[o:o + img.size * esize].view(tdt).view(img.shape).copy_(torch.from_numpy(img))
-    dev_bytes = host_bytes.to(dev)
-    views_d = [dev_bytes[o:o + img.size * esize].view(tdt).view(img.shape)
-               for (img, _, _), o in zip(items, offs)]
-    ks = [k for _, k, _ in items]
-    Bs = [B for _, _, B in items]
-    xs = torch.empty(sum(k + 1 for k in ks), dtype=torch.int32, device=dev)
-    ds = torch.empty(sum(ks), dtype=torch.int32, device=dev)
-    sc = torch.empty(len(items), dtype=torch.float32 if tdt == torch.float32 else torch.int32,
-                     device=dev)
-    xo = np.cumsum([0] + [k + 1 for k in ks])
-    do = np.cumsum([0] + ks)
-    outs = ([xs[xo[i]:xo[i + 1]] for i in range(len(items))],
-            [ds[do[i]:do[i + 1]] for i in range(len(items))],
-            [sc[i:i + 1] for i in range(len(items))])
-    stream = torch.cuda.current_stream(dev)
-    # Mostly horizontal curves: every step transposes its images (one
-    # fhtdp_transpose each) into buffers that one batch plan runs over.
-    horizontal = args.workload == "horizontal2048"
-    if horizontal:
-        tviews = [torch.empty((img.shape[1], img.shape[0]), dtype=tdt, device=dev)
-                  for img, _, _ in items]
-        plan = fd.BatchPlan(tviews, ks, Bs, out=outs, stream=stream)
-    else:
-        plan = fd.BatchPlan(views_d, ks, Bs, out=outs, stream=stream)
-    # Untimed set-up: the library's queue tuner picks the group width.
-    group_width = plan.autotune(reps=2, stream=stream)
-    hx = torch.empty_like(xs, device="cpu").pin_memory()
-    hd = torch.empty_like(ds, device="cpu").pin_memory()
-    hs = torch.empty_like(sc, device="cpu").pin_memory()
-
-    def step(src_views=None):
-        if horizontal:
-            for v, t in zip(src_views or views_d, tviews):
-                fd.transpose(v, out=t, stream=stream)
-        plan.run(stream=stream)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
-        step()
+    bb = BatchBench(args.workload, args.images or spec["images"], args.seed, rank, dev)
+    launches_per_step = bb.capture()
     barrier()
-
-    # --- device-resident throughput -------------------------------------
-    sampler = ClockSampler(local)
+    # --- device-resident throughput: graph replays, clocks sampled ---------
+    sampler = ClockSampler(local, gpu_uuid(dev))
     sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    l0 = fd.launch_count()
-    barrier()
-    for e0, e1 in ev:
-        e0.record(stream)
-        step()
-        e1.record(stream)
-    barrier()
-    launches = fd.launch_count() - l0
+    total_s = bb.timed_replays(args.steps, args.warmup, barrier)
     clocks = sampler.stop()
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
-    pix_rank = sum(img.size for img, _, _ in items)
-    pix = pix_rank * world * args.steps
-    value = pix / total_s / 1e6
-
+    total_s = max_over_ranks(total_s, dist, dev)
+    value = bb.pixels * world * args.steps / total_s / 1e6
     # --- end to end through the public API: H2D + detect + D2H -----------
-    # Every step copies its inputs from pinned host memory and reads its
-    # results back inside the timed region.  Two input buffers (and a plan on
-    # each) let the copy of step i+1 run on a copy stream while step i
-    # computes; events order each buffer's copy, use and re-use.
-    h2d = dev_bytes.numel()
-    d2h = (hx.numel() + hd.numel() + hs.numel()) * 4
-    dev_bytes2 = torch.empty_like(dev_bytes)
-    views_d2 = [dev_bytes2[o:o + img.size * esize].view(tdt).view(img.shape)
-                for (img, _, _), o in zip(items, offs)]
-    if horizontal:   # one plan over the transposed buffers, fed from either input buffer
-        plan2 = plan
-    else:
-        plan2 = fd.BatchPlan(views_d2, ks, Bs, out=outs, stream=stream)
-        plan2.autotune(reps=1, stream=stream)
-    plans, bufs = (plan, plan2), (dev_bytes, dev_bytes2)
-    src_of = (views_d, views_d2)
-    copy_stream = torch.cuda.Stream(dev)
-
-    def e2e_run(nsteps):
-        copied = [torch.cuda.Event() for _ in range(2)]
-        used = [torch.cuda.Event() for _ in range(2)]
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        copy_stream.wait_event(t0)
-        with torch.cuda.stream(copy_stream):
-            bufs[0].copy_(host_bytes, non_blocking=True)
-        copied[0].record(copy_stream)
-        for i in range(nsteps):
-            b = i % 2
-            if i + 1 < nsteps:   # next step's inputs, once that buffer is free
-                nb = 1 - b
-                if i >= 1:
-                    copy_stream.wait_event(used[nb])
-                with torch.cuda.stream(copy_stream):
-                    bufs[nb].copy_(host_bytes, non_blocking=True)
-                copied[nb].record(copy_stream)
-            stream.wait_event(copied[b])
-            if horizontal:
-                step(src_of[b])
-            else:
-                plans[b].run(stream=stream)
-            used[b].record(stream)
-            hx.copy_(xs, non_blocking=True)
-            hd.copy_(ds, non_blocking=True)
-            hs.copy_(sc, non_blocking=True)
-        t1.record(stream)
-        stream.synchronize()
-        return t0.elapsed_time(t1) / 1e3
-
-    e2e_run(2)
-    barrier()
-    e2e_s = max_over_ranks(e2e_run(args.steps), dist, dev)
-    barrier()
-    e2e_value = pix / e2e_s / 1e6
-
-    # --- roofline of the engine kernel (one persistent launch per step) ---
-    hbm, peak_kind = peaks()
-    alg = sum(algorithmic_bytes(img.shape[0], img.shape[1], k, esize) for img, k, _ in items)
-    per_launch_s = total_s / args.steps
-    achieved = alg / per_launch_s / 1e9
-    traffic = NCU_TRAFFIC_BYTES_PER_IMAGE.get(args.workload)
-
-    # --- single-image latency (one image per launch, same kernels) --------
-    img0, k0, B0 = views_d[0], ks[0], Bs[0]
-    dcode = fd.DTYPE_F32 if tdt == torch.float32 else fd.DTYPE_U8
-    if horizontal:
-        ws1 = torch.empty(fd.horizontal_workspace_bytes(dcode, img0.shape[0], img0.shape[1], k0,
-                                                        B0), dtype=torch.uint8, device=dev)
-        detect_one = fd.detect_polyline_horizontal
-    else:
-        ws1 = torch.empty(fd.workspace_bytes(dcode, img0.shape[0], img0.shape[1], k0, B0),
-                          dtype=torch.uint8, device=dev)
-        detect_one = fd.detect_polyline
-    one = (outs[0][0], outs[1][0], outs[2][0])
-    for _ in range(3):
-        detect_one(img0, k0, B0, out=one, ws=ws1, stream=stream)
-    lat = []
-    for _ in range(8):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        detect_one(img0, k0, B0, out=one, ws=ws1, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        lat.append(e0.elapsed_time(e1))
-    plan.status(stream=stream)
-
+    e2e_s, h2d, d2h = bb.e2e(args.steps, barrier)
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_value = bb.pixels * world * args.steps / e2e_s / 1e6
+    lat = bb.single_image_ms()
+    out = None
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if tdt == torch.float32 else "int32", "data": "synthetic",
-            "config": {"workload": spec["desc"], "images_per_step": len(items),
-                       "pixels_per_step": pix_rank, "parallelism": "images sharded over ranks",
+            "dtype": "f32" if bb.tdt == torch.float32 else "int32", "data": "synthetic",
+            "config": {"workload": spec["desc"], "images_per_step": len(bb.items),
+                       "pixels_per_step": bb.pixels, "parallelism": "images sharded over ranks",
                        "l2": "inputs %d MB per step %s 129 MB L2, no flush"
-                             % (h2d // 2**20, ">" if h2d > 129e6 else "<"),
-                       "queue_group_width": group_width},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm,
-                         "traffic": traffic * len(items) if traffic else None,
-                         "peak_kind": peak_kind,
-                         "kernel": "engine_kernel_u8 (one persistent launch per step%s)"
-                                   % (", after one transpose_kernel per image" if horizontal
-                                      else "")},
-            "single_image_ms": statistics.median(lat),
+                             % (bb.dbuf.numel() // 2**20, ">" if bb.dbuf.numel() > 129e6 else "<"),
+                       "timing": "CUDA-graph replay of one step per timed step",
+                       "tuned": bb.choices()},
+            "roofline": roofline(bb, total_s / args.steps),
+            "single_image_ms": lat,
             "e2e": {"value": e2e_value, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches_per_step * args.steps),
             "clocks": clocks,
         }
+    del bb
+    torch.cuda.empty_cache()
+    # --- extra workloads of the default run (one GPU) ----------------------
+    if world == 1 and not args.no_extras and args.workload == "mixed":
+        for name in EXTRAS:
+            eb = BatchBench(name, WORKLOADS[name]["images"], args.seed, rank, dev)
+            eb.capture()
+            # at least ~100 ms of timed work, so that the clock samples cover it
+            probe = eb.timed_replays(2, 1, barrier) / 2
+            steps = int(min(400, max(args.steps, 0.1 / max(probe, 1e-6))))
+            s_ = ClockSampler(local, gpu_uuid(dev))
+            s_.start()
+            t = eb.timed_replays(steps, max(args.warmup, 3), barrier)
+            ck = s_.stop()
+            out[name] = {"value": eb.pixels * steps / t / 1e6, "unit": "Mpix/s",
+                         "ms_per_step": t / steps * 1e3, "steps": steps,
+                         "images_per_step": len(eb.items), "workload": WORKLOADS[name]["desc"],
+                         "roofline": roofline(eb, t / steps), "tuned": eb.choices(),
+                         "clocks": ck}
+            del eb
+            torch.cuda.empty_cache()
+    if rank == 0:
         if world == 1 and not args.skip_cpu:
-            rate, done = oracle_rate(make_workload(args.workload, 8, 900000 + args.seed, 0), 12.0,
-                                     horizontal)
-            out["cpu_baseline"] = {
-                "value": rate, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                "sample": "%d images of the workload, whole method, one thread" % done}
+            out["cpu_baseline"] = cpu_baseline(args.workload, args.seed)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -608,7 +831,7 @@ def run_standalone(args):
     for _ in range(args.warmup):
         graph.replay()
     barrier()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, gpu_uuid(dev))
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -749,10 +972,7 @@ def run_standalone(args):
             "clocks": clocks,
         }
         if world == 1 and not args.skip_cpu:
-            rate, done = oracle_rate(make_workload(name, 12, 900000 + args.seed, 0), 12.0)
-            out["cpu_baseline"] = {
-                "value": rate, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-                "sample": "%d images of the workload, whole method, one thread" % done}
+            out["cpu_baseline"] = cpu_baseline(name, args.seed)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -66,3 +66,30 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "Mpix/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["higher_is_better"] is True and d["metric"] == bench.METRIC
+
+
+def test_all_core_oracle_leg_runs_images_on_threads():
+    items = bench.make_workload("plain256", 4, 3, 0)
+    rate, done = bench.oracle_rate_threads(items, 2)
+    assert done == 4 and rate > 0
+    assert bench.host_threads() >= 1
+    assert isinstance(bench.cpu_model(), str)
+
+
+def test_mixed_workload_is_the_default_and_spans_every_band_height():
+    args = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        assert bench.parse().workload == "mixed"
+    finally:
+        sys.argv = args
+    from paper_1912_01884_gb300 import synth
+    ns = {h // k for h, w, k, B in synth.mixed_batch_shapes(0, 256)}
+    assert ns == {32, 64, 128, 256}
+
+
+def test_clock_sampler_without_a_gpu_reports_why():
+    s = bench.ClockSampler(0)
+    s.start()
+    r = s.stop()
+    assert "reasons" in r
