@@ -97,7 +97,13 @@ struct ImgDesc {
     int hpitch;               // row pitch of h256 in elements
     uint16_t *h256;           // [k][2 halves][2 signs][128 shifts][hpitch], see h256_row
     int *fflags;              // [k][2][ftiles] publication flags of the half-band items
+                              // (int32 / float images: [k][ftiles], their FHT items)
     int moff;                 // column offset of the skewed M layout
+    // int32 / float images (kind 2): Hough rows of every band stored by the
+    // FHT items, [k][2 signs][n][hwpitch] of 4-byte values; `tmap` then
+    // describes them for the DP items' TMA copies (boxes of 32 x n).
+    void *hw;
+    int hwpitch;
 };
 
 // Backpointers: per band, ceil(D/4) groups of w 32-bit words; byte (e & 3)
@@ -209,9 +215,10 @@ __device__ __forceinline__ void fence_acq_rel_gpu() {
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 // Barrier of the kThreads compute threads (every thread of the 512-thread
-// kernel; the compute warps of the uint8 kernel).
+// kernel; the compute warps of the uint8 kernel), or of NT threads.
+template <int NT = kThreads>
 __device__ __forceinline__ void csync() {
-    asm volatile("bar.sync %0, %1;" ::"n"(kBarCompute), "n"(kThreads) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"n"(kBarCompute), "n"(NT) : "memory");
 }
 __device__ __forceinline__ void nb_arrive(int id, int count) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -388,11 +395,13 @@ __device__ __forceinline__ void merge4(const uint4 &a4, const uint4 &b0, const u
 
 // With `out`, the last level writes shift s to row s of out (pitch T)
 // instead of in place.
-template <typename W>
+// NT threads take part; `out` rows are opitch words apart (default T).
+template <typename W, int NT = kThreads>
 __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first = 1,
-                           W *out = nullptr) {
+                           W *out = nullptr, int opitch = 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = kThreads / 32;
+    const int nwarps = NT / 32;
+    if (!opitch) opitch = T;
     for (int l = first; l <= log2n; ++l) {
         const int m = 1 << l, half = m >> 1;
         const int width = T + n - m;
@@ -421,8 +430,8 @@ __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first =
                 }
                 if (to_out) {   // one sub-band: shifts 2sp, 2sp+1 at width T
                     if (live) {
-                        *(uint4 *)&out[(size_t)(2 * sp) * T + u] = oa;
-                        *(uint4 *)&out[(size_t)(2 * sp + 1) * T + u] = ob;
+                        *(uint4 *)&out[(size_t)(2 * sp) * opitch + u] = oa;
+                        *(uint4 *)&out[(size_t)(2 * sp + 1) * opitch + u] = ob;
                     }
                     continue;
                 }
@@ -434,7 +443,7 @@ __device__ void fht_levels(W *F, int pitch, int n, int log2n, int T, int first =
                 __syncwarp();
             }
         }
-        csync();
+        csync<NT>();
     }
 }
 
@@ -492,10 +501,12 @@ __device__ __forceinline__ void merge4x4(const uint4 &j0, const uint4 *j1, const
 
 // Levels l+1 and l+2 (sub-bands of m = 2^l rows merged into 4m rows).  With
 // `out` (only when 4m = n) shift s goes to row s of out (pitch T).
-template <typename W>
-__device__ void fht_radix4(W *F, int pitch, int n, int l, int T, W *out = nullptr) {
+template <typename W, int NT = kThreads>
+__device__ void fht_radix4(W *F, int pitch, int n, int l, int T, W *out = nullptr,
+                           int opitch = 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = kThreads / 32;
+    const int nwarps = NT / 32;
+    if (!opitch) opitch = T;
     const int m = 1 << l;
     const int width = T + n - 4 * m;
     for (int p = warp; p < n / 4; p += nwarps) {
@@ -528,7 +539,8 @@ __device__ void fht_radix4(W *F, int pitch, int n, int l, int T, W *out = nullpt
             if (out) {
                 if (live) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) *(uint4 *)&out[(size_t)(4 * q + t) * T + u] = o4[t];
+                    for (int t = 0; t < 4; ++t)
+                        *(uint4 *)&out[(size_t)(4 * q + t) * opitch + u] = o4[t];
                 }
                 continue;
             }
@@ -542,21 +554,21 @@ __device__ void fht_radix4(W *F, int pitch, int n, int l, int T, W *out = nullpt
             __syncwarp();
         }
     }
-    csync();
+    csync<NT>();
 }
 
 // All levels from `first` (sub-bands of 2^(first-1) rows already merged),
 // two at a time where possible.  With `out` the last level writes shift s to
 // row s of out; returns whether there was a level to do so.
-template <typename W>
+template <typename W, int NT = kThreads>
 __device__ bool fht_merge(W *F, int pitch, int n, int log2n, int T, int first,
-                          W *out = nullptr) {
+                          W *out = nullptr, int opitch = 0) {
     int l = first - 1;   // current sub-band size 2^l
     while (l + 2 <= log2n) {
-        fht_radix4<W>(F, pitch, n, l, T, l + 2 == log2n ? out : nullptr);
+        fht_radix4<W, NT>(F, pitch, n, l, T, l + 2 == log2n ? out : nullptr, opitch);
         l += 2;
     }
-    if (l < log2n) fht_levels<W>(F, pitch, n, log2n, T, l + 1, out);
+    if (l < log2n) fht_levels<W, NT>(F, pitch, n, log2n, T, l + 1, out, opitch);
     return first <= log2n;
 }
 
@@ -728,6 +740,32 @@ __device__ __forceinline__ void window_span32(int c0, int count, int B, VGet vke
         const uint32_t b = ~(uint32_t)m & 0xffu;
         word = (i & 3) == 0 ? b : word | (b << (8 * (i & 3)));
         if ((i & 3) == 3) bcol[(i >> 2) * bstride] = word;
+    }
+}
+
+// Window maxima of the NOUT displacements [c0, c0 + NOUT - 1] for windows
+// of L = 2B + 1 >= NOUT (any B beyond that), one block pair of the van Herk /
+// Gil-Werman scheme: S[i] (registers) is the maximum over [c0 - B + i, c0 + B]
+// and G that over [c0 + B + 1, c0 + B + i]; output i < count goes to emit(i, m).
+template <int NOUT, typename Key, typename VGet, typename Emit>
+__device__ __forceinline__ void window_span(int c0, int count, int B, Key dead, VGet vkey,
+                                            Emit emit) {
+    const int L = 2 * B + 1;
+    const int a = c0 - B;
+    Key run = dead;
+    for (int j = L - 1; j >= NOUT; --j) run = kmax(run, vkey(a + j));
+    Key S[NOUT];
+#pragma unroll
+    for (int j = NOUT - 1; j >= 0; --j) {
+        run = kmax(run, vkey(a + j));
+        S[j] = run;
+    }
+    Key G = dead;
+#pragma unroll
+    for (int i = 0; i < NOUT; ++i) {
+        const Key m = kmax(S[i], G);
+        G = kmax(G, vkey(c0 + B + 1 + i));
+        if (i < count) emit(i, m);
     }
 }
 
@@ -2026,22 +2064,38 @@ struct U8Ctl {
 };
 
 // ---------------------------------------------------------------------------
-// int32 / float images: the halves run one after the other in F; the "+"
-// half is kept in Hp.  V is formed in place (V(+s) over Hp, V(-s) over the
-// mirrored "-" half in F), and the window's S lives in the columns
-// [T, 2T) of F.
-template <typename In, typename Acc, typename Key>
-struct WidePath {
-    using KO = KeyOps<Acc, Key>;
-    static constexpr int kRounds = sizeof(Key) == 4 ? 2 : 4;
+// int32 / float images.  Two kinds of work items per band level: FHT items
+// compute a band's Hough values for 64 columns, both slope signs, and store
+// them to the image's hw rows; DP items of 32 columns bring their Hough rows
+// and their M tile by TMA, form V (Eqs. 3-4), compute the bend-window maxima
+// (Sec. 2.3) with 64-bit keys and publish.  Items are small (256 threads, at
+// most 102 KB of shared memory), two CTAs share an SM, and one band level of
+// an image spreads over many CTAs, so that the band chain of a single large
+// image advances quickly.  The float sums follow the same tree as the
+// oracle's float32 recursion (top half + bottom half at every level).
+constexpr int kWThreads = 256;
+constexpr int kWTileF = 64;    // FHT item columns
+constexpr int kWTileD = 32;    // DP item columns
+constexpr int kItemWideFht = 1, kItemWideDp = 3;
 
-    __host__ __device__ static int fpitch(int n) {
-        int p = (kTile + n + 8 + 3) & ~3;
-        return p > 2 * kTile ? p : 2 * kTile;
+template <typename In, typename Acc, typename Key>
+struct WideEngine {
+    using KO = KeyOps<Acc, Key>;
+    static constexpr int NT = kWThreads;
+
+    __host__ __device__ static int fpitch(int n) { return (kWTileF + n + 8 + 3) & ~3; }
+    __host__ __device__ static size_t fht_smem(int n) {
+        return (size_t)(n < 2 ? 2 : n) * fpitch(n) * 4;
     }
-    __host__ __device__ static int frows(int n) { return n < 2 ? 2 : n; }
-    __host__ __device__ static size_t f_bytes(int n) { return (size_t)frows(n) * fpitch(n) * 4; }
-    static size_t smem_bytes(int n) { return f_bytes(n) + (size_t)n * kTile * 4; }
+    __host__ __device__ static size_t dp_smem(int n) {
+        return (size_t)(2 * n + 2 * n - 1) * kWTileD * 4;
+    }
+    static size_t smem_bytes(int max_n) {
+        return std::max(fht_smem(max_n), dp_smem(max_n));
+    }
+    __device__ static Acc *hw_row(const ImgDesc &im, int band, int sign, int s) {
+        return (Acc *)im.hw + (((size_t)band * 2 + sign) * im.n + s) * im.hwpitch;
+    }
 
     // Pixels [c, c+4) of a row, zero outside [0, w); c is a multiple of 4.
     __device__ static void load4(const In *row, int c, int w, bool aligned, Acc out[4]) {
@@ -2056,23 +2110,24 @@ struct WidePath {
         for (int j = 0; j < 4; ++j) out[j] = (Acc)pix(row, c + j, w);
     }
 
-    // The "+" half first: its last level writes Hp[s][u] (natural shift
-    // order); then the "-" half, which stays in F with shift s in row
-    // brev(s).  The strip loads of a thread are issued in batches before any
-    // of their shared stores, so that their latencies overlap.
-    __device__ static void fht(Acc *F, Acc *Hp, const ImgDesc &im, int band, int x0) {
-        const int n = im.n, T = kTile, pitch = fpitch(n);
+    // FHT item: the band's Hough values of columns [x0, x0 + 64), both signs,
+    // into hw.  Sign 0 ("+") runs on the strip as it is and its last level
+    // writes the rows of hw directly; sign 1 ("-") runs on the mirrored strip
+    // (word u = pixel x0 + 63 - u), and its rows, bit-reversed in F, are
+    // copied out mirrored back.
+    __device__ static void fht_item(const ImgDesc &im, int band, int ft, unsigned char *smem) {
+        const int n = im.n, T = kWTileF, pitch = fpitch(n), x0 = ft * T;
+        Acc *F = (Acc *)smem;
         const int G = (T + n - 1 + 3) / 4;
         const In *base = (const In *)im.img + (size_t)band * n * im.pitch;
         const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 4 == 0);
         constexpr int kLB = 8;
         for (int sign = 0; sign < 2; ++sign) {
-            // "+": word u = pixel x0 + u; "-": word u = pixel x0 + T - 1 - u.
-            for (int b0 = threadIdx.x; b0 < n * G; b0 += kLB * kThreads) {
+            for (int b0 = threadIdx.x; b0 < n * G; b0 += kLB * NT) {
                 Acc v[kLB][4];
 #pragma unroll
                 for (int i = 0; i < kLB; ++i) {
-                    const int idx = b0 + i * kThreads;
+                    const int idx = b0 + i * NT;
                     if (idx < n * G) {
                         const int y = idx / G, u0 = 4 * (idx - y * G);
                         load4(base + (size_t)y * im.pitch, sign == 0 ? x0 + u0 : x0 + T - 4 - u0,
@@ -2081,186 +2136,247 @@ struct WidePath {
                 }
 #pragma unroll
                 for (int i = 0; i < kLB; ++i) {
-                    const int idx = b0 + i * kThreads;
+                    const int idx = b0 + i * NT;
                     if (idx < n * G) {
                         const int y = idx / G, u0 = 4 * (idx - y * G);
                         const bool fw = sign == 0;
-                        *(float4 *)&F[(size_t)y * pitch + u0] =
-                            make_float4(__uint_as_float(to_bits(fw ? v[i][0] : v[i][3])),
-                                        __uint_as_float(to_bits(fw ? v[i][1] : v[i][2])),
-                                        __uint_as_float(to_bits(fw ? v[i][2] : v[i][1])),
-                                        __uint_as_float(to_bits(fw ? v[i][3] : v[i][0])));
+                        *(uint4 *)&F[(size_t)y * pitch + u0] =
+                            make_uint4(to_bits(fw ? v[i][0] : v[i][3]),
+                                       to_bits(fw ? v[i][1] : v[i][2]),
+                                       to_bits(fw ? v[i][2] : v[i][1]),
+                                       to_bits(fw ? v[i][3] : v[i][0]));
                     }
                 }
             }
-            csync();
+            csync<NT>();
             if (sign == 0) {
-                if (!fht_merge<Acc>(F, pitch, n, im.log2n, T, 1, Hp)) {   // n = 1
-                    for (int idx = threadIdx.x; idx < T / 4; idx += kThreads)
-                        *(float4 *)&Hp[4 * idx] = *(const float4 *)&F[4 * idx];
-                    csync();
+                if (!fht_merge<Acc, NT>(F, pitch, n, im.log2n, T, 1, hw_row(im, band, 0, 0) + x0,
+                                         im.hwpitch)) {   // n = 1: the row itself
+                    for (int u = threadIdx.x; u < T; u += NT) hw_row(im, band, 0, 0)[x0 + u] = F[u];
                 }
             } else {
-                fht_merge<Acc>(F, pitch, n, im.log2n, T, 1);
+                fht_merge<Acc, NT>(F, pitch, n, im.log2n, T, 1);
+                // shift s of the mirrored strip at word u: the left-moving sum
+                // from column x0 + 63 - u, in row brev(s) of F
+                for (int idx = threadIdx.x; idx < n * (T / 4); idx += NT) {
+                    const int sh = idx / (T / 4), u0 = 4 * (idx % (T / 4));
+                    const uint4 w4 =
+                        *(const uint4 *)&F[(size_t)brev(sh, im.log2n) * pitch + T - 4 - u0];
+                    *(uint4 *)(hw_row(im, band, 1, sh) + x0 + u0) =
+                        make_uint4(w4.w, w4.z, w4.y, w4.x);
+                }
             }
+            csync<NT>();
         }
     }
 
-    // V(x0 + u, e) after form_v; e inside [-(n-1), n-1].
-    __device__ static Acc vval(const Acc *F, const Acc *Hp, int pitch, int log2n, int u, int e) {
-        if (e >= 0) return Hp[(size_t)e * kTile + u];
-        return F[(size_t)brev(-e, log2n) * pitch + (kTile - 1 - u)];
-    }
-
-    // V = H + M_{b+1}(x + e, e) (dead outside the image or the window); m is
-    // the M word of (x, e), loaded ahead by the caller (ignored in the last
-    // band, which has no M).
-    __device__ static Acc link_value(Acc h, Acc m, const ImgDesc &im, int band, int x, int e,
-                                     int wlo, int whi) {
-        const Acc dead = Dead<Acc>::value();
-        const bool ok = x < im.w && x + e >= 0 && x + e < im.w && e >= wlo && e <= whi;
-        if (!ok) return dead;
-        if (band == im.k - 1) return h;
-        return m == dead ? dead : h + m;
-    }
-
-    // The M loads of a batch of iterations are issued before any of its
-    // shared stores (every address lies inside the M buffer).
-    __device__ static unsigned long long form_v(Acc *F, Acc *Hp, const ImgDesc &im, int band,
-                                                const Acc *mprev, int x0) {
-        const int n = im.n, T = kTile, pitch = fpitch(n);
+    // DP item: columns [x0, x0 + 32) of band `band`.
+    __device__ static void dp_item(const ImgDesc &im, int band, int tile, unsigned char *smem,
+                                   Pipe &pipe, const LaunchArgs &args) {
+        const int n = im.n, D = 2 * n - 1, T = kWTileD, x0 = tile * T;
         const bool last = band == im.k - 1;
-        int wlo, whi;
-        band_window(im, band, &wlo, &whi);
-        unsigned long long best = 0;
-        constexpr int kLB = 8;
+        Acc *Ht = (Acc *)smem;          // [2][n][T]: Hough rows of both signs
+        Acc *Vt = Ht + 2 * n * T;       // [D][T]: the M tile, then V
         const Acc dead = Dead<Acc>::value();
-        for (int b0 = threadIdx.x; b0 < n * T; b0 += kLB * kThreads) {
-            Acc mp[kLB], mm[kLB];
-#pragma unroll
-            for (int i = 0; i < kLB; ++i) {
-                const int idx = b0 + i * kThreads;
-                mp[i] = mm[i] = dead;
-                if (idx < n * T && !last) {
-                    const int s = idx / T, up = idx - s * T;
-                    mp[i] = __ldcg(mprev + (size_t)(s + n - 1) * im.mpitch + kMOff + x0 + up);
-                    mm[i] = __ldcg(mprev + (size_t)(n - 1 - s) * im.mpitch + kMOff + x0 + T - 1 -
-                                   up);
-                }
+        if (threadIdx.x < 32) {
+            // M(x + d, d): band+1 tiles over [x0 - (n-1), x0 + T + n - 2] (lanes
+            // 0..30); the FHT item of these columns (lane 31)
+            const int lane = threadIdx.x;
+            const int t0 = (x0 - (n - 1)) >= 0 ? (x0 - (n - 1)) / T : -((n - 1 - x0 + T - 1) / T);
+            const int *flag = nullptr;
+            if (lane < 31) {
+                const int c = t0 + lane;
+                if (!last && c >= 0 && c < im.tiles && c * T <= x0 + T + n - 2)
+                    flag = im.flags + (size_t)(band + 1) * im.tiles + c;
+            } else {
+                flag = im.fflags + (size_t)band * im.ftiles + x0 / kWTileF;
             }
-#pragma unroll
-            for (int i = 0; i < kLB; ++i) {
-                const int idx = b0 + i * kThreads;
-                if (idx >= n * T) break;
-                const int s = idx / T, up = idx - s * T;
-                const int slot = brev(s, im.log2n);
-                const int xp = x0 + up, xm = x0 + T - 1 - up;
-                const Acc vp = link_value(Hp[idx], mp[i], im, band, xp, s, wlo, whi);
-                const Acc vm = s > 0 ? link_value(F[(size_t)slot * pitch + up], mm[i], im, band,
-                                                  xm, -s, wlo, whi)
-                                     : dead;
-                if (band == 0) {
-                    if (vp != dead) {
-                        const unsigned long long k = argmax_key(ord32(vp), xp, s + n - 1);
-                        best = best > k ? best : k;
-                    }
-                    if (vm != dead) {
-                        const unsigned long long k = argmax_key(ord32(vm), xm, n - 1 - s);
-                        best = best > k ? best : k;
-                    }
-                } else {
-                    Hp[idx] = vp;
-                    F[(size_t)slot * pitch + up] = vm;
-                }
+            bool ok = true;
+            if (flag) {
+                ok = wait_flag(flag, args.ctl, args.wait_cycles);
+                fence_acq_rel_gpu();
+            }
+            __syncwarp();
+            ok = __all_sync(0xffffffffu, ok);
+            if (lane == 0) {
+                if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                fence_proxy_async_global();
+                fence_proxy_async_smem();
+                mbar_expect_tx(pipe.mbar, (uint32_t)((2 * n + (last ? 0 : D)) * T * 4));
+                tma_load_2d(Ht, &im.tmap, x0, band * 2 * n, pipe.mbar);
+                tma_load_2d(Ht + n * T, &im.tmap, x0, (band * 2 + 1) * n, pipe.mbar);
+                if (!last)
+                    tma_load_2d(Vt, &im.mtmap, im.moff + x0, ((band + 1) & 1) * D, pipe.mbar);
             }
         }
-        return best;
-    }
-
-    __device__ static bool process(const ImgDesc &im, int band, int tile, unsigned char *smem,
-                                   const LaunchArgs &args, Pipe &pipe, bool) {
-        const int n = im.n, T = kTile, D = 2 * n - 1;
-        const int pitch = fpitch(n);
-        const int x0 = tile * T;
-        Acc *F = (Acc *)smem;
-        Acc *Hp = (Acc *)(smem + f_bytes(n));
-        fht(F, Hp, im, band, x0);
-        wait_deps(im, band, tile, args);
-        const Acc *mprev = (const Acc *)im.mbuf[(band + 1) & 1];
-        Acc *mnext = (Acc *)im.mbuf[band & 1];
-        const unsigned long long best = form_v(F, Hp, im, band, mprev, x0);
-        auto take_next = [&] { stage_next(args, pipe.next, atomicAdd(&args.ctl->queue, 1)); };
+        if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles)) {
+            if (threadIdx.x == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+            mbar_wait(pipe.mbar, pipe.mphase, kDrainCycles);
+        }
+        pipe.mphase ^= 1u;
+        // V(x, e) = H(x, e) + M(x + e, e), dead outside the image (Eqs. 3-4).
+        unsigned long long best = 0;
+        for (int idx = threadIdx.x; idx < D * (T / 4); idx += NT) {
+            const int ei = idx / (T / 4), u0 = 4 * (idx % (T / 4));
+            const int e = ei - (n - 1), sh = e < 0 ? -e : e;
+            const uint4 h4 = *(const uint4 *)&Ht[((e < 0 ? n : 0) + sh) * T + u0];
+            uint4 m4 = make_uint4(0, 0, 0, 0);
+            if (!last) m4 = *(const uint4 *)&Vt[ei * T + u0];
+            const uint32_t hb[4] = {h4.x, h4.y, h4.z, h4.w};
+            const uint32_t mb[4] = {m4.x, m4.y, m4.z, m4.w};
+            Acc v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = x0 + u0 + j;
+                const bool ok = x < im.w && x + e >= 0 && x + e < im.w;
+                const Acc h = from_bits<Acc>(hb[j]), m = from_bits<Acc>(mb[j]);
+                v[j] = !ok ? dead : last ? h : (m == dead ? dead : h + m);
+            }
+            if (band == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (v[j] != dead) {
+                        const unsigned long long k = argmax_key(ord32(v[j]), x0 + u0 + j, ei);
+                        best = best > k ? best : k;
+                    }
+            } else {
+                *(uint4 *)&Vt[ei * T + u0] =
+                    make_uint4(to_bits(v[0]), to_bits(v[1]), to_bits(v[2]), to_bits(v[3]));
+            }
+        }
         if (band == 0) {
-            finish_band0<Acc>(best, im, args, take_next);
-            return true;
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = best > other ? best : other;
+            }
+            if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
+            csync<NT>();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                if (atomicAdd(im.done, 1) == im.tiles - 1) readback<Acc>(im, args);
+            }
+            return;
         }
-        csync();
-
-        const int u = threadIdx.x % T, qd = threadIdx.x / T;
+        csync<NT>();
+        // Window maxima: 8 threads per column, 32 displacements each.
+        const int u = threadIdx.x & (T - 1), q = threadIdx.x / T;
         const int x = x0 + u;
-        const int B = im.B;
-        const int lo = -(n - 1), hi = n - 1;
-        auto vkey = [&](int e) -> Key {
-            if (e < lo || e > hi) return KO::dead();
-            const Acc v = vval(F, Hp, pitch, im.log2n, u, e);
-            return v == Dead<Acc>::value() ? KO::dead() : KO::make(v, e + n - 1);
-        };
-        auto emit = [&](int c, Key mk) { store_window<Acc, Key>(im, mnext, band, x, c, mk); };
-        // S(row, u): a Key per (row, column) packed into the columns [T, 2T) of F.
-        auto s_at = [&](int row) -> Key * {
-            const int wi = (row * T + u) * (int)(sizeof(Key) / 4);
-            return (Key *)(F + (size_t)(wi / T) * pitch + T + (wi % T));
-        };
-        for (int round = 0; round < kRounds; ++round) {
-            const int P0 = lo + (round * D) / kRounds;
-            const int P1 = lo + ((round + 1) * D) / kRounds - 1;
-            const int span = P1 - P0 + 1;
-            int clo, chi;
-            band_window(im, band - 1, &clo, &chi);
-            const int c0 = max(P0 + (qd * span) / kQ, clo);
-            const int c1 = min(P0 + ((qd + 1) * span) / kQ - 1, chi);
-            const int srow0 = P0 - B;
-            auto sput = [&](int e, Key v) { *s_at(e - srow0) = v; };
-            auto sget = [&](int e) { return *s_at(e - srow0); };
-            if (c0 <= c1 && x < im.w)
-                window_two_pass<Key>(c0, c1, B, lo - B, lo, hi, KO::dead(), vkey, sput, sget,
-                                         emit);
-            csync();
+        const int lo = -(n - 1), hi = n - 1, B = im.B;
+        const int c0 = lo + 32 * q;
+        if (x < im.w && c0 <= hi) {
+            const Acc *col = Vt + (n - 1) * T + u;
+            auto vkey = [&](int e) -> Key {
+                if (e < lo || e > hi) return KO::dead();
+                const Acc v = col[e * T];
+                return v == dead ? KO::dead() : KO::make(v, e + n - 1);
+            };
+            Acc *mnext = (Acc *)im.mbuf[band & 1];
+            Acc *mcol = mnext + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
+            uint32_t *bcol = (uint32_t *)im.bp +
+                             ((size_t)band * bp_groups(n) + ((c0 + n - 1) >> 2)) * im.w + x;
+            const int count = min(32, hi - c0 + 1);
+            uint32_t word = 0;
+            auto emit = [&](int i, Key mk) {
+                const bool dk = mk == KO::dead();
+                mcol[(long long)i * (im.mpitch - 1)] = dk ? dead : KO::value(mk);
+                const uint32_t b = dk ? 0u : (uint32_t)KO::index(mk);
+                word = (i & 3) == 0 ? b : word | (b << (8 * (i & 3)));
+                if ((i & 3) == 3 || i == count - 1) bcol[(size_t)(i >> 2) * im.w] = word;
+            };
+            // Runs of NOUT outputs, NOUT the largest power of two up to 16 that
+            // the window length L = 2B + 1 covers (one block pair per run).
+            auto runs = [&](auto nout) {
+                constexpr int NOUT = decltype(nout)::value;
+                for (int r0 = 0; r0 < count; r0 += NOUT)
+                    window_span<NOUT, Key>(c0 + r0, count - r0, B, KO::dead(), vkey,
+                                           [&](int i, Key mk) { emit(r0 + i, mk); });
+            };
+            const int L = 2 * B + 1;
+            if (L >= 16) runs(std::integral_constant<int, 16>());
+            else if (L >= 8) runs(std::integral_constant<int, 8>());
+            else if (L >= 4) runs(std::integral_constant<int, 4>());
+            else if (L >= 2) runs(std::integral_constant<int, 2>());
+            else runs(std::integral_constant<int, 1>());
         }
-        publish(im, band, tile, args);
-        if (threadIdx.x == 0) take_next();
-        return true;
+        fence_acq_rel_gpu();
+        csync<NT>();
+        if (threadIdx.x == 0) {
+            const ImgDesc &first = args.many ? args.many[0] : args.one;
+            if (!(band == args.skip_band && tile == args.skip_tile && im.flags == first.flags))
+                st_release(im.flags + (size_t)band * im.tiles + tile, 1);
+        }
     }
 };
 
+// The work items of a single int32 / float image, in queue order: the FHT
+// items of band k-1, then per band b from k-1 down to 0 the FHT items of band
+// b-1 (none for b = 0) and the DP items of b.
+__device__ inline void decode_wide_one(const ImgDesc &im, long long item, int *kind, int *band,
+                                       int *tile) {
+    const long long hf = im.ftiles, L1 = hf + im.tiles;
+    if (item < hf) {
+        *kind = kItemWideFht;
+        *band = im.k - 1;
+        *tile = (int)item;
+        return;
+    }
+    const long long j = item - hf;
+    long long lv = j / L1, off = j - lv * L1;
+    if (lv >= im.k - 1) {
+        lv = im.k - 1;
+        off = j - (long long)(im.k - 1) * L1;
+    }
+    const int b = im.k - 1 - (int)lv;
+    if (b > 0 && off < hf) {
+        *kind = kItemWideFht;
+        *band = b - 1;
+        *tile = (int)off;
+    } else {
+        *kind = kItemWideDp;
+        *band = b;
+        *tile = (int)(off - (b > 0 ? hf : 0));
+    }
+}
+
 template <typename In, typename Acc, typename Key>
-__global__ void __launch_bounds__(kThreads, 1)
-    engine_kernel(const __grid_constant__ LaunchArgs args) {
-    using P = WidePath<In, Acc, Key>;
+__global__ void __launch_bounds__(kWThreads, 2)
+    engine_kernel_wide(const __grid_constant__ LaunchArgs args) {
+    using P = WideEngine<In, Acc, Key>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ __align__(16) NextItem s_next;
+    __shared__ long long s_item;
     if (threadIdx.x == 0) {
-        mbar_init(&s_bar, 1);
         mbar_init(&s_mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        stage_next(args, &s_next, atomicAdd(&args.ctl->queue, 1));
-        cp_async_wait_all();
     }
-    csync();
-    Pipe pipe{&s_bar, 0u, &s_mbar, 0u, &s_next};
+    Pipe pipe{nullptr, 0u, &s_mbar, 0u, nullptr};
     for (;;) {
-        const long long item = s_next.item;
-        const bool prefetched = s_next.prefetched != 0;
-        const ImgDesc *imp = nullptr;
-        int band = 0, tile = 0;
-        if (item < args.items) decode_staged(args, s_next, &imp, &band, &tile);
-        csync();   // thread 0 rewrites s_next inside process
+        if (threadIdx.x == 0) s_item = atomicAdd(&args.ctl->queue, 1);
+        csync<kWThreads>();
+        const long long item = s_item;
+        csync<kWThreads>();   // s_item is rewritten at the next item
         if (item >= args.items) break;
-        if (!P::process(*imp, band, tile, smem_raw, args, pipe, prefetched)) return;
-        if (threadIdx.x == 0) cp_async_wait_all();
-        csync();
+        const ImgDesc *im;
+        int kind, band, tile;
+        if (args.many) {
+            const Item it = args.order[item];
+            im = &args.many[it.image];
+            kind = (it.nflags >> 19) & 3;
+            band = it.band;
+            tile = it.tile;
+        } else {
+            im = &args.one;
+            decode_wide_one(args.one, item, &kind, &band, &tile);
+        }
+        if (kind == kItemWideFht) {
+            P::fht_item(*im, band, tile, smem_raw);
+            if (threadIdx.x == 0) {
+                fence_acq_rel_gpu();
+                st_release(im->fflags + (size_t)band * im->ftiles + tile, 1);
+            }
+        } else {
+            P::dp_item(*im, band, tile, smem_raw, pipe, args);
+        }
     }
 }
 
@@ -2386,6 +2502,14 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table, bool reserve 
             items += 2LL * p.s.k * p.ftiles;
             p.fflags = off;
             off = align_up(off + (size_t)p.s.k * 2 * p.ftiles * 4, 8);
+        } else if (p.kind == 2) {
+            p.moff = kMOff;
+            p.mpitch = (int)align_up((size_t)kMOff + p.s.w + kWTileD + 4, 32);
+            p.ftiles = (p.s.w + kWTileF - 1) / kWTileF;
+            p.hpitch = p.ftiles * kWTileF;
+            items += (long long)p.s.k * p.ftiles;
+            p.fflags = off;
+            off = align_up(off + (size_t)p.s.k * p.ftiles * 4, 8);
         } else {
             // Row reads of M go up to 4 words past the last tile's columns.
             p.moff = kMOff;
@@ -2417,6 +2541,9 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table, bool reserve 
         if (p.kind == 1) {
             p.h256 = d;
             d = align_up(d + (size_t)p.s.k * 4 * 128 * p.hpitch * 2, 256);
+        } else if (p.kind == 2) {
+            p.h256 = d;   // the Hough rows, [k][2][n][hpitch] of 4 bytes
+            d = align_up(d + (size_t)p.s.k * 2 * p.s.n * p.hpitch * 4, 256);
         }
     }
     L.data_off = L.order_off + L.order_bytes;
@@ -2477,13 +2604,34 @@ bool encode_m_map(CUtensorMap *map, void *m0, int D, int mpitch, int bw, int bh)
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D tensor map of `rows` rows of `pitch` 4-byte values, box bw x bh (the
+// Hough rows of an int32 / float image).
+bool encode_rows_map(CUtensorMap *map, void *base, int pitch, int rows, int bw, int bh) {
+    if ((uintptr_t)base % 16 != 0 || pitch % 4 != 0 || bh > 256 || bw > 256) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     ImgDesc im{};
     im.use_tma = dtype == FHTDP_U8 &&
                  encode_strip_map(&im.tmap, p.io.img, p.s.h, p.s.w, p.io.pitch, p.s.n);
+    // (int32 / float images: tmap describes their Hough rows, below)
     if (p.kind == 1)
         im.use_mtma = ws && encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch,
                                          kTile256, kMBox256);
+    else if (p.kind == 2)
+        im.use_mtma = ws && encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch,
+                                         kWTileD, p.s.D) &&
+                      encode_rows_map(&im.tmap, ws + L.data_off + p.h256, p.hpitch,
+                                      2 * p.s.k * p.s.n, kWTileD, p.s.n);
     else
         im.use_mtma = dtype == FHTDP_U8 && p.s.n <= kMaxBandFused && ws &&
                       encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch, kTile,
@@ -2519,6 +2667,11 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
         im.hpitch = p.hpitch;
         im.h256 = (uint16_t *)(data + p.h256);
         im.fflags = (int *)(ws + p.fflags);
+    } else if (p.kind == 2) {
+        im.ftiles = p.ftiles;
+        im.hwpitch = p.hpitch;
+        im.hw = data + p.h256;
+        im.fflags = (int *)(ws + p.fflags);
     }
     return im;
 }
@@ -2536,28 +2689,23 @@ int num_sms() {
     return cached[dev];
 }
 
-template <typename In, typename Acc, typename Key>
-int launch_kernel(const LaunchArgs &args, int max_n, cudaStream_t stream) {
-    using P = WidePath<In, Acc, Key>;
+template <typename In, typename Acc>
+int launch_kernel_wide(const LaunchArgs &args, int max_n, cudaStream_t stream) {
+    using P = WideEngine<In, Acc, long long>;
     const size_t smem = P::smem_bytes(max_n);
-    auto kern = engine_kernel<In, Acc, Key>;
-    static int smem_set = 0;   // dynamic shared memory enabled for this kernel
-    if ((int)smem > smem_set) {
-        int st = cuda_status(cudaFuncSetAttribute(kern,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)P::smem_bytes(kMaxBandFused)),
-                             "cudaFuncSetAttribute");
-        if (st) return st;
-        smem_set = (int)P::smem_bytes(kMaxBandFused);
-    }
+    auto kern = engine_kernel_wide<In, Acc, long long>;
+    int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "cudaFuncSetAttribute");
+    if (st) return st;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWThreads, smem);
     if (per_sm < 1) per_sm = 1;
     long long grid = (long long)num_sms() * per_sm;
     if (grid > args.items) grid = args.items;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kThreads, smem, stream>>>(args);
-    return launched("engine_kernel");
+    kern<<<(unsigned)grid, kWThreads, smem, stream>>>(args);
+    return launched("engine_kernel_wide");
 }
 
 template <typename Key>
@@ -2585,9 +2733,9 @@ int dispatch(int dtype, int max_h, const LaunchArgs &args, int max_n, bool multi
             if (256LL * max_h < (1LL << 22)) return launch_kernel_u8<int32_t>(args, multi, stream);
             return launch_kernel_u8<long long>(args, multi, stream);
         case FHTDP_I32:
-            return launch_kernel<int32_t, int32_t, long long>(args, max_n, stream);
+            return launch_kernel_wide<int32_t, int32_t>(args, max_n, stream);
         default:
-            return launch_kernel<float, float, long long>(args, max_n, stream);
+            return launch_kernel_wide<float, float>(args, max_n, stream);
     }
 }
 
@@ -2669,6 +2817,9 @@ ImgPlan single_plan(int dtype, const void *img, int pitch, const Shape &s, int B
     if (fused_256(dtype, s, p.B, img, pitch)) {
         p.kind = 1;
         p.T = kTile256;
+    } else if (dtype != FHTDP_U8 && s.n <= kMaxBandFused) {
+        p.kind = 2;   // FHT items and narrow DP items
+        p.T = kWTileD;
     }
     return p;
 }
@@ -2708,7 +2859,11 @@ struct BatchPlan {
 //
 // Items of a band level of an image, in tiles of 128 x 128 work (a 256-row
 // band level also holds the half-band FHT items of the band above).
-long long level_weight(const ImgPlan &p) { return p.kind == 1 ? p.tiles + 2LL * p.ftiles : p.tiles; }
+long long level_weight(const ImgPlan &p) {
+    if (p.kind == 1) return p.tiles + 2LL * p.ftiles;
+    if (p.kind == 2) return std::max(1LL, (long long)((p.tiles + 3) / 4 + (p.ftiles + 1) / 2));
+    return p.tiles;
+}
 
 // The items of band level lv of one image.  256-row bands: the half-band
 // FHT items of band k-1 open level 0, and each level lv also holds those of
@@ -2725,6 +2880,16 @@ void push_level(std::vector<Item> &order, const ImgPlan &p, int i, int lv) {
         if (lv == 0) halves(b);
         if (b > 0) halves(b - 1);
         for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemDp256 << 19});
+        return;
+    }
+    if (p.kind == 2) {
+        auto ffts = [&](int band) {
+            for (int t = 0; t < p.ftiles; ++t)
+                order.push_back(Item{i, band, t, kItemWideFht << 19});
+        };
+        if (lv == 0) ffts(b);
+        if (b > 0) ffts(b - 1);
+        for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemWideDp << 19});
         return;
     }
     for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemBand << 19});
