@@ -753,12 +753,22 @@ __device__ __forceinline__ void window_span(int c0, int count, int B, Key dead, 
     const int L = 2 * B + 1;
     const int a = c0 - B;
     Key run = dead;
-    for (int j = L - 1; j >= NOUT; --j) run = kmax(run, vkey(a + j));
+    int j = L - 1;
+    // the part of the block beyond the first NOUT values: 8 loads at a time
+    for (; j - 7 >= NOUT; j -= 8) {
+        Key k[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) k[i] = vkey(a + j - i);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) k[i] = kmax(k[i], k[i + 1]);
+        run = kmax(run, kmax(kmax(k[0], k[2]), kmax(k[4], k[6])));
+    }
+    for (; j >= NOUT; --j) run = kmax(run, vkey(a + j));
     Key S[NOUT];
 #pragma unroll
-    for (int j = NOUT - 1; j >= 0; --j) {
-        run = kmax(run, vkey(a + j));
-        S[j] = run;
+    for (int jj = NOUT - 1; jj >= 0; --jj) {
+        run = kmax(run, vkey(a + jj));
+        S[jj] = run;
     }
     Key G = dead;
 #pragma unroll
@@ -2066,16 +2076,16 @@ struct U8Ctl {
 // ---------------------------------------------------------------------------
 // int32 / float images.  Two kinds of work items per band level: FHT items
 // compute a band's Hough values for 64 columns, both slope signs, and store
-// them to the image's hw rows; DP items of 32 columns bring their Hough rows
-// and their M tile by TMA, form V (Eqs. 3-4), compute the bend-window maxima
-// (Sec. 2.3) with 64-bit keys and publish.  Items are small (256 threads, at
+// them to the image's hw rows; DP items of 16 columns bring their Hough rows
+// and their M tile by TMA, form V (Eqs. 3-4) as 64-bit window keys, compute
+// the bend-window maxima (Sec. 2.3) and publish.  Items are small (256 threads, at
 // most 102 KB of shared memory), two CTAs share an SM, and one band level of
 // an image spreads over many CTAs, so that the band chain of a single large
 // image advances quickly.  The float sums follow the same tree as the
 // oracle's float32 recursion (top half + bottom half at every level).
 constexpr int kWThreads = 256;
 constexpr int kWTileF = 64;    // FHT item columns
-constexpr int kWTileD = 32;    // DP item columns
+constexpr int kWTileD = 16;    // DP item columns
 constexpr int kItemWideFht = 1, kItemWideDp = 3;
 
 template <typename In, typename Acc, typename Key>
@@ -2087,8 +2097,15 @@ struct WideEngine {
     __host__ __device__ static size_t fht_smem(int n) {
         return (size_t)(n < 2 ? 2 : n) * fpitch(n) * 4;
     }
+    // Hough rows [2][n][T] (each sign from a 128-byte boundary, as TMA
+    // destinations are) and the M tile [D][T] (4-byte values), then the
+    // window keys [D][T] (8 bytes).
+    __host__ __device__ static int dp_sign1(int n) { return (n * kWTileD + 31) & ~31; }
+    __host__ __device__ static size_t dp_keys_off(int n) {
+        return ((size_t)(2 * dp_sign1(n) + (2 * n - 1) * kWTileD) * 4 + 127) / 128 * 128;
+    }
     __host__ __device__ static size_t dp_smem(int n) {
-        return (size_t)(2 * n + 2 * n - 1) * kWTileD * 4;
+        return dp_keys_off(n) + (size_t)(2 * n - 1) * kWTileD * sizeof(Key);
     }
     static size_t smem_bytes(int max_n) {
         return std::max(fht_smem(max_n), dp_smem(max_n));
@@ -2110,6 +2127,88 @@ struct WideEngine {
         for (int j = 0; j < 4; ++j) out[j] = (Acc)pix(row, c + j, w);
     }
 
+    // N consecutive strip words of band row y from word u: sign 0 reads
+    // pixels x0 + u.., sign 1 the mirrored strip (word u = pixel x0 + 63 - u).
+    template <int N>
+    __device__ static void strip_words(const In *row, int w, bool aligned, int x0, int u,
+                                       int sign, Acc (&P)[N]) {
+        constexpr int NW = (N + 3) / 4;
+        Acc q[4 * NW];
+        if (sign == 0) {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) load4(row, x0 + u + 4 * k, w, aligned, &q[4 * k]);
+#pragma unroll
+            for (int j = 0; j < N; ++j) P[j] = q[j];
+        } else {
+            // words u .. u + 4NW - 1 are pixels x0 + 63 - u down to x0 + 64 - u - 4NW
+            const int c = x0 + kWTileF - u - 4 * NW;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) load4(row, c + 4 * k, w, aligned, &q[4 * k]);
+#pragma unroll
+            for (int j = 0; j < N; ++j) P[j] = q[4 * NW - 1 - j];
+        }
+    }
+    // Levels 1 and 2 on four rows y0..y0+3 of a sub-band: out[s][u] (s < 4,
+    // u < W) from the rows' words u .. u + W + 2 (the recursion's sums, in
+    // its order).
+    template <int W>
+    __device__ static void levels12(const In *base, long long pitch, int w, bool aligned,
+                                    int x0, int u, int sign, int y0, Acc (&out)[4][W]) {
+        Acc A[2][W], Bq[2][W + 2];
+        {
+            Acc p0[W], p1[W + 1];
+            strip_words<W>(base + (size_t)y0 * pitch, w, aligned, x0, u, sign, p0);
+            strip_words<W + 1>(base + (size_t)(y0 + 1) * pitch, w, aligned, x0, u, sign, p1);
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                A[0][j] = p0[j] + p1[j];
+                A[1][j] = p0[j] + p1[j + 1];
+            }
+        }
+        {
+            Acc p2[W + 2], p3[W + 3];
+            strip_words<W + 2>(base + (size_t)(y0 + 2) * pitch, w, aligned, x0, u, sign, p2);
+            strip_words<W + 3>(base + (size_t)(y0 + 3) * pitch, w, aligned, x0, u, sign, p3);
+#pragma unroll
+            for (int j = 0; j < W + 2; ++j) {
+                Bq[0][j] = p2[j] + p3[j];
+                Bq[1][j] = p2[j] + p3[j + 1];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            out[0][j] = A[0][j] + Bq[0][j];
+            out[1][j] = A[0][j] + Bq[0][j + 1];
+            out[2][j] = A[1][j] + Bq[1][j + 1];
+            out[3][j] = A[1][j] + Bq[1][j + 2];
+        }
+    }
+    // Levels 1-3 in registers straight from the image (n >= 8): a task is an
+    // 8-row sub-band g and the 4 words [4c, 4c + 4) of the level-3 width;
+    // shift s of the sub-band goes to row 8g + brev3(s) of F.
+    __device__ static void fht_regs8(Acc *F, int pitch, const ImgDesc &im, const In *base,
+                                     bool aligned, int x0, int sign) {
+        const int n = im.n, T = kWTileF;
+        const int C4 = (T + n - 8 + 3) / 4;
+        const int tasks = (n / 8) * C4;
+        for (int t = threadIdx.x; t < tasks; t += NT) {
+            const int g = t / C4, c = t - g * C4;
+            Acc B2[4][8], T2[4][4];
+            levels12<8>(base, im.pitch, im.w, aligned, x0, 4 * c, sign, 8 * g + 4, B2);
+            levels12<4>(base, im.pitch, im.w, aligned, x0, 4 * c, sign, 8 * g, T2);
+            Acc *row0 = F + (size_t)(8 * g) * pitch + 4 * c;
+#pragma unroll
+            for (int sh = 0; sh < 8; ++sh) {
+                const int h = sh >> 1, o = (sh + 1) >> 1;
+                const int r = ((sh & 1) << 2) | (sh & 2) | ((sh >> 2) & 1);
+                *(uint4 *)&row0[(size_t)r * pitch] =
+                    make_uint4(to_bits(T2[h][0] + B2[h][o + 0]), to_bits(T2[h][1] + B2[h][o + 1]),
+                               to_bits(T2[h][2] + B2[h][o + 2]), to_bits(T2[h][3] + B2[h][o + 3]));
+            }
+        }
+        csync<NT>();
+    }
+
     // FHT item: the band's Hough values of columns [x0, x0 + 64), both signs,
     // into hw.  Sign 0 ("+") runs on the strip as it is and its last level
     // writes the rows of hw directly; sign 1 ("-") runs on the mirrored strip
@@ -2123,6 +2222,11 @@ struct WideEngine {
         const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 4 == 0);
         constexpr int kLB = 8;
         for (int sign = 0; sign < 2; ++sign) {
+            int first = 1;   // the first level left to merge in shared memory
+            if (n >= 8) {
+                fht_regs8(F, pitch, im, base, aligned, x0, sign);
+                first = 4;
+            } else
             for (int b0 = threadIdx.x; b0 < n * G; b0 += kLB * NT) {
                 Acc v[kLB][4];
 #pragma unroll
@@ -2150,12 +2254,17 @@ struct WideEngine {
             }
             csync<NT>();
             if (sign == 0) {
-                if (!fht_merge<Acc, NT>(F, pitch, n, im.log2n, T, 1, hw_row(im, band, 0, 0) + x0,
-                                         im.hwpitch)) {   // n = 1: the row itself
-                    for (int u = threadIdx.x; u < T; u += NT) hw_row(im, band, 0, 0)[x0 + u] = F[u];
+                if (!fht_merge<Acc, NT>(F, pitch, n, im.log2n, T, first,
+                                         hw_row(im, band, 0, 0) + x0, im.hwpitch)) {
+                    // no merge level (n = 1, or n = 8 done in registers): rows
+                    // brev(s) hold the shifts
+                    for (int idx = threadIdx.x; idx < n * T; idx += NT) {
+                        const int sh = idx / T, u = idx - sh * T;
+                        hw_row(im, band, 0, sh)[x0 + u] = F[(size_t)brev(sh, im.log2n) * pitch + u];
+                    }
                 }
             } else {
-                fht_merge<Acc, NT>(F, pitch, n, im.log2n, T, 1);
+                fht_merge<Acc, NT>(F, pitch, n, im.log2n, T, first);
                 // shift s of the mirrored strip at word u: the left-moving sum
                 // from column x0 + 63 - u, in row brev(s) of F
                 for (int idx = threadIdx.x; idx < n * (T / 4); idx += NT) {
@@ -2170,13 +2279,15 @@ struct WideEngine {
         }
     }
 
-    // DP item: columns [x0, x0 + 32) of band `band`.
+    // DP item: columns [x0, x0 + 16) of band `band`.
     __device__ static void dp_item(const ImgDesc &im, int band, int tile, unsigned char *smem,
                                    Pipe &pipe, const LaunchArgs &args) {
         const int n = im.n, D = 2 * n - 1, T = kWTileD, x0 = tile * T;
         const bool last = band == im.k - 1;
         Acc *Ht = (Acc *)smem;          // [2][n][T]: Hough rows of both signs
-        Acc *Vt = Ht + 2 * n * T;       // [D][T]: the M tile, then V
+        const int h1 = dp_sign1(n);     // offset of sign 1
+        Acc *Mt = Ht + 2 * h1;          // [D][T]: the M tile
+        Key *Kt = (Key *)(smem + dp_keys_off(n));   // [D][T]: window keys of V
         const Acc dead = Dead<Acc>::value();
         if (threadIdx.x < 32) {
             // M(x + d, d): band+1 tiles over [x0 - (n-1), x0 + T + n - 2] (lanes
@@ -2204,9 +2315,9 @@ struct WideEngine {
                 fence_proxy_async_smem();
                 mbar_expect_tx(pipe.mbar, (uint32_t)((2 * n + (last ? 0 : D)) * T * 4));
                 tma_load_2d(Ht, &im.tmap, x0, band * 2 * n, pipe.mbar);
-                tma_load_2d(Ht + n * T, &im.tmap, x0, (band * 2 + 1) * n, pipe.mbar);
+                tma_load_2d(Ht + h1, &im.tmap, x0, (band * 2 + 1) * n, pipe.mbar);
                 if (!last)
-                    tma_load_2d(Vt, &im.mtmap, im.moff + x0, ((band + 1) & 1) * D, pipe.mbar);
+                    tma_load_2d(Mt, &im.mtmap, im.moff + x0, ((band + 1) & 1) * D, pipe.mbar);
             }
         }
         if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles)) {
@@ -2214,14 +2325,15 @@ struct WideEngine {
             mbar_wait(pipe.mbar, pipe.mphase, kDrainCycles);
         }
         pipe.mphase ^= 1u;
-        // V(x, e) = H(x, e) + M(x + e, e), dead outside the image (Eqs. 3-4).
+        // V(x, e) = H(x, e) + M(x + e, e), dead outside the image (Eqs. 3-4),
+        // kept as window keys (value and index e + n - 1 in one 64-bit integer).
         unsigned long long best = 0;
         for (int idx = threadIdx.x; idx < D * (T / 4); idx += NT) {
             const int ei = idx / (T / 4), u0 = 4 * (idx % (T / 4));
             const int e = ei - (n - 1), sh = e < 0 ? -e : e;
-            const uint4 h4 = *(const uint4 *)&Ht[((e < 0 ? n : 0) + sh) * T + u0];
+            const uint4 h4 = *(const uint4 *)&Ht[(e < 0 ? h1 : 0) + sh * T + u0];
             uint4 m4 = make_uint4(0, 0, 0, 0);
-            if (!last) m4 = *(const uint4 *)&Vt[ei * T + u0];
+            if (!last) m4 = *(const uint4 *)&Mt[ei * T + u0];
             const uint32_t hb[4] = {h4.x, h4.y, h4.z, h4.w};
             const uint32_t mb[4] = {m4.x, m4.y, m4.z, m4.w};
             Acc v[4];
@@ -2240,8 +2352,11 @@ struct WideEngine {
                         best = best > k ? best : k;
                     }
             } else {
-                *(uint4 *)&Vt[ei * T + u0] =
-                    make_uint4(to_bits(v[0]), to_bits(v[1]), to_bits(v[2]), to_bits(v[3]));
+                Key kk[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) kk[j] = v[j] == dead ? KO::dead() : KO::make(v[j], ei);
+                *(longlong2 *)&Kt[ei * T + u0] = make_longlong2(kk[0], kk[1]);
+                *(longlong2 *)&Kt[ei * T + u0 + 2] = make_longlong2(kk[2], kk[3]);
             }
         }
         if (band == 0) {
@@ -2258,23 +2373,19 @@ struct WideEngine {
             return;
         }
         csync<NT>();
-        // Window maxima: 8 threads per column, 32 displacements each.
+        // Window maxima: 16 threads per column, 16 displacements each.
         const int u = threadIdx.x & (T - 1), q = threadIdx.x / T;
         const int x = x0 + u;
         const int lo = -(n - 1), hi = n - 1, B = im.B;
-        const int c0 = lo + 32 * q;
+        const int c0 = lo + 16 * q;
         if (x < im.w && c0 <= hi) {
-            const Acc *col = Vt + (n - 1) * T + u;
-            auto vkey = [&](int e) -> Key {
-                if (e < lo || e > hi) return KO::dead();
-                const Acc v = col[e * T];
-                return v == dead ? KO::dead() : KO::make(v, e + n - 1);
-            };
+            const Key *col = Kt + (n - 1) * T + u;
+            auto vkey = [&](int e) -> Key { return (e < lo || e > hi) ? KO::dead() : col[e * T]; };
             Acc *mnext = (Acc *)im.mbuf[band & 1];
             Acc *mcol = mnext + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
             uint32_t *bcol = (uint32_t *)im.bp +
                              ((size_t)band * bp_groups(n) + ((c0 + n - 1) >> 2)) * im.w + x;
-            const int count = min(32, hi - c0 + 1);
+            const int count = min(16, hi - c0 + 1);
             uint32_t word = 0;
             auto emit = [&](int i, Key mk) {
                 const bool dk = mk == KO::dead();
