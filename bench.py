@@ -85,7 +85,11 @@ EXTRAS = ("plain2048", "float8192")
 # batched workload, from the ncu captures summarised in profiles/; a launch's
 # traffic is this times its pixels.  None where no capture of the current
 # kernel exists (reset whenever the kernel changes until it is captured again).
-NCU_TRAFFIC_BYTES_PER_PIXEL = {}
+NCU_TRAFFIC_BYTES_PER_PIXEL = {
+    "mixed": (4.85e9 + 10.78e9) / 1064894464,        # profiles/engine_kernel_u8_mixed256.md
+    "plain2048": (252.65e6 + 1.02e9) / (32 * 2048 * 2048),
+    "float8192": (269.83e6 + 637.90e6) / (8192 * 8192),   # profiles/engine_kernel_wide_float8192.md
+}
 # The window DP kernel changed (it now takes any window table and value
 # type) after its ncu capture (profiles/dp_band_angle_kernel_2048x2048_k16_gamma10.md,
 # 4.14 MB per band launch), so the standalone workloads report no traffic
