@@ -437,6 +437,80 @@ int fhtdp_batch_configure(fhtdp_batch_plan *plan, void *ws, int n, int tile, int
                           cudaStream_t stream);
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * The learned window proposal in front of the exact method (the paper has
+ * no counterpart).  A 4-layer, 32-channel CNN (3x3 convolutions with
+ * dilations 1, 2, 4, 8, ReLU after the first three, bf16 weights on the
+ * tensor cores with FP32 accumulation) reads the 4x4 mean-pooled image and
+ * predicts, for every band, one of 32 bins of 4 displacements
+ * (d + 64 in [4c, 4c + 3]); the DP then searches only a window around it.
+ *
+ * Parameter block (device, fhtdp_cnn_param_bytes() bytes, caller-owned): per
+ * layer, each part from a 256-byte boundary, the FP32 weights [rows][32]
+ * (layer 1: 16 rows = taps, rows 9..15 zero; layers 2-4: 9 taps x 32 input
+ * channels), the FP32 bias [32], the Adam moments of the weights and of the
+ * bias (first, second), and the bf16 copy of the weights the forward pass
+ * reads.
+ * ---------------------------------------------------------------------- */
+size_t fhtdp_cnn_param_bytes(void);
+/* He-normal weights (standard deviation sqrt(2 / fan_in), from a seeded
+ * counter-based generator), zero biases and moments, bf16 copies. */
+int fhtdp_cnn_init(void *params, unsigned long long seed, cudaStream_t stream);
+/* Workspace of fhtdp_cnn_forward / _backward / _step for n images of h x w
+ * pixels: the pooled input, the four layers' outputs, two gradient buffers
+ * and the FP32 gradients. */
+size_t fhtdp_cnn_workspace_bytes(int n, int h, int w);
+/* Forward pass of n uint8 images [n][h][w] (device, contiguous; h and w
+ * multiples of 4, w/4 a multiple of 64, (h/4) divisible by `bands`):
+ * pred[n][bands] = the predicted bin of every band (log-sum-exp pooling of
+ * the band's logits, then argmax), conf[n][bands] = its softmax probability
+ * (may be NULL).  Leaves the activations in ws for fhtdp_cnn_backward. */
+int fhtdp_cnn_forward(const void *params, const uint8_t *imgs, int n, int h, int w, int bands,
+                      void *ws, size_t ws_bytes, int32_t *pred, float *conf,
+                      cudaStream_t stream);
+/* Backward pass after fhtdp_cnn_forward on the same ws: the mean softmax
+ * cross-entropy of the pooled band logits against labels[n][bands] (bins,
+ * device) into *loss (device, may be NULL), and every layer's FP32 gradient
+ * into ws. */
+int fhtdp_cnn_backward(const void *params, const int32_t *labels, int n, int h, int w, int bands,
+                       void *ws, size_t ws_bytes, float *loss, cudaStream_t stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8; step >= 1) on the FP32
+ * parameters with the gradients left in ws; refreshes the bf16 copies. */
+int fhtdp_cnn_step(void *params, const void *ws, int n, int h, int w, float lr, int step,
+                   cudaStream_t stream);
+
+/* Learned detection of a batch of uint8 images of one shape, stored one after
+ * the other ([count][h][w], pitch w; bands of at most 128 rows), through a
+ * plan bound to a workspace like the batch plans:
+ *   1. the CNN proposes every band's bin; the window is the bin's 4
+ *      displacements widened by window_half on both sides;
+ *   2. a pruned DP (one persistent launch) finds the best polyline inside
+ *      the windows;
+ *   3. an image falls back to the full DP when the pruned DP found no
+ *      polyline, when the polyline touches a window edge that is not an edge
+ *      of the displacement range, or when its score is below the confidence
+ *      margin, margin * h (a mean intensity per image row);
+ *      used_fallback[i] (device, may be NULL) records it;
+ *   4. one more persistent launch runs the full DP of the images that fall
+ *      back only (the others' work items are skipped), into the images'
+ *      outputs; the others get the pruned result.
+ * Everything is enqueued on `stream`, with no host synchronisation: the call
+ * may be captured in a CUDA graph.  Images that fall back get exactly
+ * fhtdp_detect_polyline's results. */
+typedef struct fhtdp_learned_plan fhtdp_learned_plan;
+int fhtdp_learned_plan_create(const fhtdp_image *images, int count, int window_half,
+                              fhtdp_learned_plan **plan_out);
+size_t fhtdp_learned_workspace_bytes(const fhtdp_learned_plan *plan);
+/* Binds the plan to `ws` (uploads its tables; synchronises `stream`). */
+int fhtdp_learned_upload(fhtdp_learned_plan *plan, void *ws, size_t ws_bytes,
+                         cudaStream_t stream);
+int fhtdp_detect_learned(fhtdp_learned_plan *plan, const void *params, float margin,
+                         int32_t *used_fallback, void *ws, cudaStream_t stream);
+/* FHTDP_ETIMEOUT if a bounded device wait of the last detect_learned on this
+ * workspace gave up; synchronises `stream`. */
+int fhtdp_learned_status(const fhtdp_learned_plan *plan, const void *ws, cudaStream_t stream);
+void fhtdp_learned_plan_destroy(fhtdp_learned_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -143,6 +143,24 @@ _SIGS = {
                                          ctypes.c_void_p]),
     "fhtdp_cnn_bin_windows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_cnn_param_bytes": (ctypes.c_size_t, []),
+    "fhtdp_cnn_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p]),
+    "fhtdp_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 3),
+    "fhtdp_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 4
+                          + [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_void_p] * 3),
+    "fhtdp_cnn_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 4
+                           + [ctypes.c_void_p, ctypes.c_size_t] + [ctypes.c_void_p] * 2),
+    "fhtdp_cnn_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 3
+                       + [ctypes.c_float, ctypes.c_int, ctypes.c_void_p]),
+    "fhtdp_learned_plan_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
+    "fhtdp_learned_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "fhtdp_learned_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_void_p]),
+    "fhtdp_detect_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float]
+                             + [ctypes.c_void_p] * 3),
+    "fhtdp_learned_status": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "fhtdp_learned_plan_destroy": (None, [ctypes.c_void_p]),
 }
 
 

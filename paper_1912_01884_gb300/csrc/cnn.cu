@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(256) band_head_kernel(const __nv_bfloat16 *__r
                                                         float scale,
                                                         __nv_bfloat16 *__restrict__ dL,
                                                         float *__restrict__ loss,
-                                                        int32_t *__restrict__ pred) {
+                                                        int32_t *__restrict__ pred,
+                                                        float *__restrict__ conf) {
     __shared__ float smax[8][kC], ssum[8][kC], pooled[kC], dpool[kC];
     const int n = blockIdx.x / bands, b = blockIdx.x % bands;
     const int rpb = H / bands;
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(256) band_head_kernel(const __nv_bfloat16 *__r
         for (int k = 0; k < kC; ++k) dpool[k] = __expf(pooled[k] - lse) - (k == lab ? 1.0f : 0.0f);
         if (loss && lab >= 0) atomicAdd(loss, (lse - pooled[lab]) * scale);
         if (pred) pred[n * bands + b] = arg;
+        if (conf) conf[n * bands + b] = __expf(M - lse);   // softmax probability of the argmax
     }
     __syncthreads();
     if (!dL) return;
@@ -342,6 +344,28 @@ __global__ void bin_windows_kernel(const int32_t *__restrict__ pred, int count, 
         const int lo = 4 * pred[i] - 64 - margin, hi = 4 * pred[i] - 61 + margin;
         win[2 * i] = lo < -(n - 1) ? -(n - 1) : lo;
         win[2 * i + 1] = hi > n - 1 ? n - 1 : hi;
+    }
+}
+
+// He-normal initial weights (standard deviation sqrt(2 / fan_in)) from a
+// counter-based SplitMix64 stream (Steele, Lea, Flood, OOPSLA 2014) and the
+// Box-Muller transform; zero where `zero_from` <= row (padding taps).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__global__ void he_init_kernel(float *__restrict__ w, int rows, int cols, int zero_from, float std,
+                               unsigned long long seed) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols;
+         i += gridDim.x * blockDim.x) {
+        const unsigned long long r1 = splitmix64(seed ^ (2ull * (unsigned long long)i));
+        const unsigned long long r2 = splitmix64(seed ^ (2ull * (unsigned long long)i + 1ull));
+        const float u1 = ((float)(r1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+        const float u2 = (float)(r2 >> 40) * (1.0f / 16777216.0f);
+        const float z = sqrtf(-2.0f * logf(u1)) * cosf(6.283185307179586f * u2);
+        w[i] = (i / cols) >= zero_from ? 0.0f : std * z;
     }
 }
 
@@ -396,9 +420,10 @@ int cnn_wgrad(const void *X, int cin, int N, int H, int W, int dil, const void *
 }
 
 int cnn_band_head(const void *L, int N, int H, int W, int bands, const int32_t *labels,
-                  float scale, void *dL, float *loss, int32_t *pred, cudaStream_t stream) {
+                  float scale, void *dL, float *loss, int32_t *pred, cudaStream_t stream,
+                  float *conf) {
     band_head_kernel<<<N * bands, 256, 0, stream>>>((const __nv_bfloat16 *)L, H, W, bands, labels,
-                                                     scale, (__nv_bfloat16 *)dL, loss, pred);
+                                                     scale, (__nv_bfloat16 *)dL, loss, pred, conf);
     return launched("band_head_kernel");
 }
 
@@ -414,6 +439,13 @@ int cnn_bin_windows(const int32_t *pred, int count, int n, int margin, int32_t *
                     cudaStream_t stream) {
     bin_windows_kernel<<<grid_1d(count, 256), 256, 0, stream>>>(pred, count, n, margin, win);
     return launched("bin_windows_kernel");
+}
+
+int cnn_he_init(float *w, int rows, int cols, int zero_from, float std, unsigned long long seed,
+                cudaStream_t stream) {
+    he_init_kernel<<<grid_1d((long long)rows * cols, 256), 256, 0, stream>>>(w, rows, cols,
+                                                                           zero_from, std, seed);
+    return launched("he_init_kernel");
 }
 
 int cnn_to_bf16(const float *src, void *dst, int count, cudaStream_t stream) {

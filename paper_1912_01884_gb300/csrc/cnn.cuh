@@ -14,7 +14,10 @@ int cnn_flip_transpose(const void *Wt, void *Wf, cudaStream_t stream);
 int cnn_wgrad(const void *X, int cin, int N, int H, int W, int dil, const void *dZ, float *dW,
               float *db, cudaStream_t stream);
 int cnn_band_head(const void *L, int N, int H, int W, int bands, const int32_t *labels,
-                  float scale, void *dL, float *loss, int32_t *pred, cudaStream_t stream);
+                  float scale, void *dL, float *loss, int32_t *pred, cudaStream_t stream,
+                  float *conf = nullptr);
+int cnn_he_init(float *w, int rows, int cols, int zero_from, float std, unsigned long long seed,
+                cudaStream_t stream);
 int cnn_adam(float *p, float *m, float *v, const float *g, int count, float lr, float b1,
              float b2, float eps, int t, void *wb, cudaStream_t stream);
 int cnn_to_bf16(const float *src, void *dst, int count, cudaStream_t stream);

@@ -104,6 +104,10 @@ struct ImgDesc {
     // describes them for the DP items' TMA copies (boxes of 32 x n).
     void *hw;
     int hwpitch;
+    // Optional device flag: when it reads 0 at the launch, every item of the
+    // image is skipped (the learned proposal's fallback run only redoes the
+    // images that need the full DP).
+    const int32_t *enable;
 };
 
 // Backpointers: per band, ceil(D/4) groups of w 32-bit words; byte (e & 3)
@@ -1903,6 +1907,15 @@ struct U8Ctl {
             c.tile = (int)(off - (b > 0 ? hf : 0));
         }
     }
+    // The next item of the queue whose image is enabled (lane 0 takes it).
+    __device__ static long long take(const LaunchArgs &args) {
+        for (;;) {
+            const long long item = atomicAdd(&args.ctl->queue, 1);
+            if (item >= args.items || !args.many) return item;
+            const ImgDesc *im = &args.many[args.order[item].image];
+            if (!im->enable || __ldcg(im->enable) != 0) return item;
+        }
+    }
     __device__ static Ctrl decode(const LaunchArgs &args, long long item) {
         Ctrl c{item, nullptr, 0, 0, 0, 128, kItemBand, false};
         if (item >= args.items) return c;
@@ -2049,13 +2062,13 @@ struct U8Ctl {
         uint32_t *Hc = (uint32_t *)(smem + u8_hc_offset<Key>());
         int32_t *Vn = (int32_t *)smem;
         long long first = 0;
-        if (lane == 0) first = atomicAdd(&args.ctl->queue, 1);
+        if (lane == 0) first = take(args);
         Ctrl cur = decode(args, __shfl_sync(0xffffffffu, first, 0));
         if (lane == 0) hand_over(cur, slot, Hc, pipe);
         nb_arrive(kBarNext, kCtlSync);
         while (cur.item < args.items) {
             long long nx = 0;
-            if (lane == 0) nx = atomicAdd(&args.ctl->queue, 1);
+            if (lane == 0) nx = take(args);
             const Ctrl next = decode(args, __shfl_sync(0xffffffffu, nx, 0));
             const bool ok = wait_producers(cur, args, lane);
             nb_sync(kBarFhtDone, kCtlSync);
@@ -2548,6 +2561,7 @@ struct ImgPlan {
     int depth;                  // uint8: FHT levels in registers (2 or 3)
     int kind;                   // 1: 256-row bands through half-band and DP items
     int ftiles, hpitch, moff;   // kind 1: half-band tiles, h256 row pitch; M column offset
+    const int32_t *enable;      // optional: the image runs only where this reads nonzero
     long long item0;
     size_t flags, best, done, fflags;   // offsets in the counter region
     size_t m0, m1, bp, h256;            // offsets in the data region
@@ -2773,6 +2787,7 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     im.win = p.io.d_window;
     im.kind = p.kind;
     im.moff = p.moff;
+    im.enable = p.enable;
     if (p.kind == 1) {
         im.ftiles = p.ftiles;
         im.hpitch = p.hpitch;
@@ -3459,6 +3474,14 @@ void batch_choice(const BatchPlan *plan, int n, int *mode, long long *target, in
     if (tile) *tile = T;
     if (depth) *depth = dd;
 }
+
+// Image i of the fused launch runs only where enable[i] reads nonzero at the
+// launch (set before fhtdp_batch_upload).
+void batch_set_enable(BatchPlan *plan, const int32_t *enable) {
+    for (size_t i = 0; i < plan->imgs.size(); ++i) plan->imgs[i].enable = enable ? enable + i : nullptr;
+}
+
+int batch_separate_count(const BatchPlan *plan) { return (int)plan->separate.size(); }
 
 void batch_destroy(BatchPlan *plan) { delete plan; }
 

@@ -20,6 +20,8 @@ void batch_choice(const BatchPlan *plan, int n, int *mode, long long *target, in
 int batch_configure(BatchPlan *plan, void *ws, int n, int tile, int depth, cudaStream_t stream);
 void batch_destroy(BatchPlan *plan);
 void debug_inject(int band, int tile, long long wait_cycles);
+void batch_set_enable(BatchPlan *plan, const int32_t *enable);
+int batch_separate_count(const BatchPlan *plan);
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                   int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream);
 

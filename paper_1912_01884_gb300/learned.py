@@ -4,16 +4,17 @@ A 4-layer, 32-channel CNN (3x3 convolutions with dilations 1, 2, 4, 8, a
 31-pixel receptive field on the 4x4-downsampled image, i.e. at least the 16
 low-resolution rows of a band) predicts for every band one of 32 bins of 4
 displacements.  The DP then searches only a 16-wide window around the
-predicted bin (the pruned DP: ``BatchPlan(..., windows=...)``).  An image
-falls back to the full DP when its pruned optimum does not exist or touches a
-window edge.  The network is trained on labels that the exact method
-produces.  The paper has none of this: it is an addition in front of the
-method.
+predicted bin (the pruned DP).  An image falls back to the full DP when its
+pruned optimum does not exist, touches a window edge, or scores below a
+confidence margin (a mean intensity per image row).  The network is trained
+on labels that the exact method produces.  The paper has none of this: it is
+an addition in front of the method.
 
-Every computation runs in the library's CUDA kernels (C ABI ``fhtdp_cnn_*``:
-tensor-core bf16 convolutions with FP32 accumulation, the band head, Adam on
-FP32 master weights).  PyTorch provides device memory, the random
-initialisation and the training images' random numbers.
+Every computation runs in the library's CUDA kernels (C ABI ``fhtdp_cnn_*``
+and ``fhtdp_detect_learned``: tensor-core bf16 convolutions with FP32
+accumulation, the band head, Adam on FP32 master weights, the pruned DP and
+the fallback decision on the device).  PyTorch provides device memory and the
+training images' random numbers.
 """
 from __future__ import annotations
 
@@ -95,120 +96,59 @@ def lane_images(seed: int, count: int, h: int = 1024, w: int = 1024, k: int = 16
 
 
 class LaneProposer:
-    """The CNN, its FP32 master weights, bf16 copies and Adam state."""
+    """The CNN's parameter block (FP32 master weights, Adam moments, bf16
+    copies; C ABI fhtdp_cnn_*) and a training workspace for batches of
+    `batch` images of h x w."""
 
     def __init__(self, seed: int = 0, device="cuda", lr: float = 3e-3):
         torch = _torch()
         self.device = device
         self.lr = lr
         self.step_count = 0
-        g = torch.Generator(device=device)
-        g.manual_seed(int(seed))
-        self.params = []   # (weight fp32, bias fp32, bf16 copy, cin, dilation)
-        for layer, dil in enumerate(DILATIONS):
-            cin = 1 if layer == 0 else C
-            taps = 16 if cin == 1 else 9 * cin
-            fan_in = 9 * cin
-            wt = torch.randn(taps, C, generator=g, device=device) * math.sqrt(2.0 / fan_in)
-            if cin == 1:
-                wt[9:] = 0.0
-            b = torch.zeros(C, device=device)
-            self.params.append([wt.contiguous(), b, torch.empty(taps, C, dtype=torch.bfloat16,
-                                                                 device=device), cin, dil])
-        self.moments = [[torch.zeros_like(p[0]), torch.zeros_like(p[0]), torch.zeros_like(p[1]),
-                         torch.zeros_like(p[1])] for p in self.params]
-        self.wflip = torch.empty(9 * C * C, dtype=torch.bfloat16, device=device)
-        for p in self.params:
-            _check(lib().fhtdp_cnn_to_bf16(p[0].data_ptr(), p[2].data_ptr(), p[0].numel(),
-                                           _stream(None)))
+        self.params = torch.empty(lib().fhtdp_cnn_param_bytes(), dtype=torch.uint8, device=device)
+        _check(lib().fhtdp_cnn_init(self.params.data_ptr(), int(seed), _stream(None)))
+        self._ws = None
+        self._ws_key = None
 
-    # -- forward --------------------------------------------------------------
-    def downsample(self, imgs):
+    def _workspace(self, n, h, w):
         torch = _torch()
-        N, H, W = imgs.shape
-        x = torch.empty(N, H // 4, W // 4, 1, dtype=torch.bfloat16, device=self.device)
-        _check(lib().fhtdp_cnn_downsample4(imgs.data_ptr(), N, H, W, x.data_ptr(),
-                                           _stream(None)))
-        return x
+        if self._ws_key != (n, h, w):
+            self._ws = torch.empty(lib().fhtdp_cnn_workspace_bytes(n, h, w), dtype=torch.uint8,
+                                   device=self.device)
+            self._ws_key = (n, h, w)
+        return self._ws
 
-    def forward(self, x):
-        """Activations [x, a1, a2, a3, logits] (NHWC bf16)."""
+    def forward(self, imgs, bands):
+        """(pred [N, bands] bins, conf [N, bands] softmax probabilities)."""
         torch = _torch()
-        N, H, W, _ = x.shape
-        acts = [x]
-        for layer, (wt, b, wb, cin, dil) in enumerate(self.params):
-            y = torch.empty(N, H, W, C, dtype=torch.bfloat16, device=self.device)
-            relu = 1 if layer < len(self.params) - 1 else 0
-            _check(lib().fhtdp_cnn_conv3x3(acts[-1].data_ptr(), cin, N, H, W, dil, wb.data_ptr(),
-                                           b.data_ptr(), relu, y.data_ptr(), _stream(None)))
-            acts.append(y)
-        return acts
-
-    def head(self, logits, bands, labels=None, want_grad=False):
-        """(loss, dlogits, pred) of the band head."""
-        torch = _torch()
-        N, H, W, _ = logits.shape
-        loss = torch.zeros(1, device=self.device)
+        N, h, w = imgs.shape
+        ws = self._workspace(N, h, w)
         pred = torch.empty(N, bands, dtype=torch.int32, device=self.device)
-        dl = torch.empty_like(logits) if want_grad else None
-        _check(lib().fhtdp_cnn_band_head(
-            logits.data_ptr(), N, H, W, bands,
-            labels.data_ptr() if labels is not None else None, 1.0 / (N * bands),
-            dl.data_ptr() if dl is not None else None, loss.data_ptr(), pred.data_ptr(),
-            _stream(None)))
-        return loss, dl, pred
-
-    # -- backward -------------------------------------------------------------
-    def backward(self, acts, dlogits):
-        """FP32 gradients [(dW, db)] of every layer."""
-        torch = _torch()
-        N, H, W, _ = acts[0].shape
-        grads = [None] * len(self.params)
-        dz = dlogits
-        for layer in range(len(self.params) - 1, -1, -1):
-            wt, b, wb, cin, dil = self.params[layer]
-            dw = torch.zeros_like(wt)
-            db = torch.zeros_like(b)
-            _check(lib().fhtdp_cnn_conv3x3_wgrad(acts[layer].data_ptr(), cin, N, H, W, dil,
-                                                 dz.data_ptr(), dw.data_ptr(), db.data_ptr(),
-                                                 _stream(None)))
-            grads[layer] = (dw, db)
-            if layer == 0:
-                break
-            dx = torch.empty_like(acts[layer])
-            _check(lib().fhtdp_cnn_conv3x3_dgrad(dz.data_ptr(), N, H, W, dil, wb.data_ptr(),
-                                                 self.wflip.data_ptr(), dx.data_ptr(),
-                                                 _stream(None)))
-            _check(lib().fhtdp_cnn_relu_backward(acts[layer].data_ptr(), dx.data_ptr(),
-                                                 dx.numel(), _stream(None)))
-            dz = dx
-        return grads
-
-    def apply(self, grads):
-        self.step_count += 1
-        for (wt, b, wb, _, _), (m_w, v_w, m_b, v_b), (dw, db) in zip(self.params, self.moments,
-                                                                   grads):
-            _check(lib().fhtdp_cnn_adam(wt.data_ptr(), m_w.data_ptr(), v_w.data_ptr(),
-                                        dw.data_ptr(), wt.numel(), self.lr, 0.9, 0.999, 1e-8,
-                                        self.step_count, wb.data_ptr(), _stream(None)))
-            _check(lib().fhtdp_cnn_adam(b.data_ptr(), m_b.data_ptr(), v_b.data_ptr(),
-                                        db.data_ptr(), b.numel(), self.lr, 0.9, 0.999, 1e-8,
-                                        self.step_count, None, _stream(None)))
-        # The first layer's padding taps (9..15) have zero gradients, so Adam
-        # leaves them at zero.
+        conf = torch.empty(N, bands, dtype=torch.float32, device=self.device)
+        _check(lib().fhtdp_cnn_forward(self.params.data_ptr(), imgs.data_ptr(), N, h, w, bands,
+                                       ws.data_ptr(), ws.numel(), pred.data_ptr(),
+                                       conf.data_ptr(), _stream(None)))
+        return pred, conf
 
     def train_step(self, imgs, labels, bands):
         """One Adam step on a batch: imgs uint8 [N, H, W] (device), labels int32
         [N, bands] (bins).  Returns the loss (a device tensor)."""
-        acts = self.forward(self.downsample(imgs))
-        loss, dl, _ = self.head(acts[-1], bands, labels, want_grad=True)
-        self.apply(self.backward(acts, dl))
+        torch = _torch()
+        N, h, w = imgs.shape
+        self.forward(imgs, bands)
+        ws = self._workspace(N, h, w)
+        loss = torch.zeros(1, device=self.device)
+        _check(lib().fhtdp_cnn_backward(self.params.data_ptr(), labels.data_ptr(), N, h, w, bands,
+                                        ws.data_ptr(), ws.numel(), loss.data_ptr(),
+                                        _stream(None)))
+        self.step_count += 1
+        _check(lib().fhtdp_cnn_step(self.params.data_ptr(), ws.data_ptr(), N, h, w,
+                                    float(self.lr), self.step_count, _stream(None)))
         return loss
 
     def propose(self, imgs, bands):
         """Predicted bins [N, bands] (int32, device)."""
-        acts = self.forward(self.downsample(imgs))
-        return self.head(acts[-1], bands)[2]
+        return self.forward(imgs, bands)[0]
 
     def windows(self, pred, n):
         torch = _torch()
@@ -216,6 +156,57 @@ class LaneProposer:
         _check(lib().fhtdp_cnn_bin_windows(pred.data_ptr(), pred.numel(), n, MARGIN,
                                            win.data_ptr(), _stream(None)))
         return win.view(*pred.shape, 2)
+
+
+class LearnedPlan:
+    """fhtdp_learned_plan over a batch of images [N, h, w] (one contiguous
+    device tensor): proposal, pruned DP, device-side fallback to the full DP."""
+
+    def __init__(self, imgs, k: int, B: int, window_half: int = MARGIN, stream=None):
+        from . import Image
+        torch = _torch()
+        N, h, w = imgs.shape
+        self.imgs, self.k, self.N = imgs, k, N
+        dev = imgs.device
+        self.x = torch.empty(N, k + 1, dtype=torch.int32, device=dev)
+        self.d = torch.empty(N, k, dtype=torch.int32, device=dev)
+        self.score = torch.empty(N, dtype=torch.int32, device=dev)
+        self.used_fallback = torch.empty(N, dtype=torch.int32, device=dev)
+        arr = (Image * N)()
+        for i in range(N):
+            arr[i] = Image(imgs[i].data_ptr(), h, w, w, k, B, self.x[i].data_ptr(),
+                           self.d[i].data_ptr(), self.score[i:i + 1].data_ptr(), None)
+        self._arr = arr
+        handle = ctypes.c_void_p()
+        _check(lib().fhtdp_learned_plan_create(ctypes.cast(arr, ctypes.c_void_p), N,
+                                               int(window_half), ctypes.byref(handle)))
+        self._plan = handle
+        self.ws = torch.empty(lib().fhtdp_learned_workspace_bytes(handle), dtype=torch.uint8,
+                              device=dev)
+        _check(lib().fhtdp_learned_upload(handle, self.ws.data_ptr(), self.ws.numel(),
+                                          _stream(stream)))
+
+    def run(self, model, margin: float, stream=None):
+        """Enqueues the detection; results in self.x, self.d, self.score and
+        self.used_fallback."""
+        _check(lib().fhtdp_detect_learned(self._plan, model.params.data_ptr(), float(margin),
+                                          self.used_fallback.data_ptr(), self.ws.data_ptr(),
+                                          _stream(stream)))
+
+    def status(self, stream=None):
+        _check(lib().fhtdp_learned_status(self._plan, self.ws.data_ptr(), _stream(stream)))
+        return 0
+
+    def close(self):
+        if self._plan:
+            lib().fhtdp_learned_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def exact_paths(imgs, k, B):
@@ -228,33 +219,11 @@ def exact_paths(imgs, k, B):
     return (torch.stack(plan.x), torch.stack(plan.d), torch.cat(plan.score))
 
 
-def detect_learned(model, imgs, k, B):
-    """Learned proposal + pruned DP + fallback.  Returns (x, d, score,
-    used_fallback[N]) with the exact method's outputs for fallback images."""
-    torch = _torch()
-    N, h, w = imgs.shape
-    n = h // k
-    pred = model.propose(imgs, k)
-    win = model.windows(pred, n)
-    plan = BatchPlan([imgs[i] for i in range(N)], [k] * N, [B] * N,
-                     windows=[win[i] for i in range(N)])
-    plan.run()
+def detect_learned(model, imgs, k, B, margin: float = 0.0):
+    """Learned proposal + pruned DP + device-side fallback (fhtdp_detect_learned).
+    Returns (x, d, score, used_fallback[N]); images that fall back carry the
+    exact method's outputs."""
+    plan = LearnedPlan(imgs, k, B)
+    plan.run(model, margin)
     plan.status()
-    x = torch.stack(plan.x)
-    d = torch.stack(plan.d)
-    s = torch.cat(plan.score)
-    # Fallback: no polyline inside the windows, or one touching a window edge
-    # that is not the edge of the displacement range.
-    wl, wh = win[..., 0], win[..., 1]
-    edge = ((d == wl) & (wl > -(n - 1))) | ((d == wh) & (wh < n - 1))
-    fb = (x[:, 0] < 0) | edge.any(1)
-    idx = torch.nonzero(fb).flatten().cpu().numpy().tolist()
-    if idx:
-        fplan = BatchPlan([imgs[i] for i in idx], [k] * len(idx), [B] * len(idx))
-        fplan.run()
-        fplan.status()
-        for j, i in enumerate(idx):
-            x[i] = fplan.x[j]
-            d[i] = fplan.d[j]
-            s[i] = fplan.score[j][0]
-    return x, d, s, fb
+    return plan.x, plan.d, plan.score, plan.used_fallback.bool()

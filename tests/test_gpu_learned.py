@@ -158,3 +158,178 @@ def test_learned_pipeline_trains_and_answers_exactly_or_within_windows(lib):
         else:
             xo, do, so = oracle.detect_windowed(imgs[i].cpu().numpy(), k, B, win[i])
             assert list(x[i].cpu().numpy()) == list(xo) and int(s[i]) == int(so)
+
+
+def _layer_params(lib, params):
+    """Views of the parameter block (the layout of include/fhtdp.h): per layer
+    FP32 weights, bias, Adam moments and the bf16 copy, each from a 256-byte
+    boundary."""
+    import torch
+    views, off = [], 0
+    buf = params
+    for layer in range(4):
+        rows = 16 if layer == 0 else 288
+        parts = {}
+        for name, count, dt, size in (("w", rows * 32, torch.float32, 4), ("b", 32, torch.float32, 4),
+                                      ("mw", rows * 32, torch.float32, 4),
+                                      ("vw", rows * 32, torch.float32, 4),
+                                      ("mb", 32, torch.float32, 4), ("vb", 32, torch.float32, 4),
+                                      ("w16", rows * 32, torch.bfloat16, 2)):
+            parts[name] = buf[off:off + count * size].view(dt)
+            off = (off + count * size + 255) // 256 * 256
+        views.append(parts)
+    assert off == buf.numel()
+    return views
+
+
+def test_cnn_forward_backward_step_equal_the_per_layer_calls(lib):
+    """The whole-network calls give exactly what the per-layer calls (each
+    pinned against the CPU reference above) give in sequence."""
+    import torch
+    from paper_1912_01884_gb300 import learned
+    N, h, w, k = 2, 128, 256, 4
+    imgs = learned.lane_images(11, N, h, w, k, 12)
+    model = learned.LaneProposer(seed=3)
+    P = _layer_params(lib, model.params)
+    pred, conf = model.forward(imgs, k)
+    # per-layer reference of the forward pass
+    L = lib.lib()
+    s = _stream()
+    x = torch.empty(N, h // 4, w // 4, 1, dtype=torch.bfloat16, device="cuda")
+    assert L.fhtdp_cnn_downsample4(imgs.data_ptr(), N, h, w, x.data_ptr(), s) == 0
+    acts = [x]
+    for layer, dil in enumerate((1, 2, 4, 8)):
+        y = torch.empty(N, h // 4, w // 4, 32, dtype=torch.bfloat16, device="cuda")
+        assert L.fhtdp_cnn_conv3x3(acts[-1].data_ptr(), 1 if layer == 0 else 32, N, h // 4, w // 4,
+                                   dil, P[layer]["w16"].data_ptr(), P[layer]["b"].data_ptr(),
+                                   1 if layer < 3 else 0, y.data_ptr(), s) == 0
+        acts.append(y)
+    rpred = torch.empty(N, k, dtype=torch.int32, device="cuda")
+    assert L.fhtdp_cnn_band_head(acts[-1].data_ptr(), N, h // 4, w // 4, k, None, 1.0, None,
+                                 None, rpred.data_ptr(), s) == 0
+    assert torch.equal(pred, rpred)
+    assert torch.all((conf > 0) & (conf <= 1))
+    # backward + step against the per-layer gradient and Adam calls
+    labels = torch.randint(0, 32, (N, k), dtype=torch.int32, device="cuda")
+    before = [{n_: t.clone() for n_, t in p.items()} for p in P]
+    loss = model.train_step(imgs, labels, k)
+    dz = torch.empty_like(acts[-1])
+    rloss = torch.zeros(1, device="cuda")
+    assert L.fhtdp_cnn_band_head(acts[-1].data_ptr(), N, h // 4, w // 4, k, labels.data_ptr(),
+                                 1.0 / (N * k), dz.data_ptr(), rloss.data_ptr(), None, s) == 0
+    assert torch.allclose(loss, rloss, rtol=1e-6)
+    # the block's FP32 gradients sit in the training workspace after the
+    # activations and two gradient buffers and the flipped weights
+    a256 = lambda v: (v + 255) // 256 * 256
+    px = N * (h // 4) * (w // 4)
+    off = a256(px * 2) + 6 * a256(px * 32 * 2) + a256(9 * 32 * 32 * 2)
+    ws = model._ws
+    wf = torch.empty(9 * 32 * 32, dtype=torch.bfloat16, device="cuda")
+    gofs = []
+    for layer in range(4):
+        rows = 16 if layer == 0 else 288
+        gofs.append(off)
+        off += a256((rows * 32 + 32) * 4)
+    for layer in range(3, -1, -1):
+        dil = (1, 2, 4, 8)[layer]
+        rows = 16 if layer == 0 else 288
+        g = ws[gofs[layer]:gofs[layer] + (rows * 32 + 32) * 4].view(torch.float32)
+        dw = torch.zeros(rows, 32, device="cuda")
+        db = torch.zeros(32, device="cuda")
+        assert L.fhtdp_cnn_conv3x3_wgrad(acts[layer].data_ptr(), 1 if layer == 0 else 32, N,
+                                         h // 4, w // 4, dil, dz.data_ptr(), dw.data_ptr(),
+                                         db.data_ptr(), s) == 0
+        # the same gradient up to the order of the FP32 atomic sums
+        assert torch.allclose(g[:rows * 32], dw.flatten(), rtol=1e-4, atol=1e-6), layer
+        assert torch.allclose(g[rows * 32:], db, rtol=1e-4, atol=1e-6), layer
+        # Adam on the block's own gradient from the same starting point gives
+        # the block's new weights and their bf16 copy
+        pw, mw, vw = (before[layer]["w"].clone(), before[layer]["mw"].clone(),
+                      before[layer]["vw"].clone())
+        wb = torch.empty(rows * 32, dtype=torch.bfloat16, device="cuda")
+        gw = g[:rows * 32].clone()
+        assert L.fhtdp_cnn_adam(pw.data_ptr(), mw.data_ptr(), vw.data_ptr(), gw.data_ptr(),
+                                rows * 32, ctypes.c_float(model.lr), ctypes.c_float(0.9),
+                                ctypes.c_float(0.999), ctypes.c_float(1e-8), 1, wb.data_ptr(),
+                                s) == 0
+        assert torch.equal(pw, P[layer]["w"]) and torch.equal(wb, P[layer]["w16"])
+        if layer == 0:
+            break
+        dx = torch.empty_like(dz)
+        assert L.fhtdp_cnn_conv3x3_dgrad(dz.data_ptr(), N, h // 4, w // 4, dil,
+                                         before[layer]["w16"].data_ptr(), wf.data_ptr(),
+                                         dx.data_ptr(), s) == 0
+        assert L.fhtdp_cnn_relu_backward(acts[layer].data_ptr(), dx.data_ptr(), dx.numel(), s) == 0
+        dz = dx
+
+
+def _check_learned(lib, imgs, k, B, plan, margin):
+    """Every answer of the learned detection: the exact optimum where it fell
+    back, else the optimum inside the proposed windows; and the fallback rule."""
+    import torch
+    from paper_1912_01884_gb300 import learned
+    N, h, w = imgs.shape
+    n = h // k
+    xe, de, se = learned.exact_paths(imgs, k, B)
+    fb = plan.used_fallback.cpu().numpy()
+    x, d, s = plan.x.cpu().numpy(), plan.d.cpu().numpy(), plan.score.cpu().numpy()
+    for i in range(N):
+        if fb[i]:
+            assert list(x[i]) == list(xe[i].cpu().numpy()) and int(s[i]) == int(se[i]), i
+        else:
+            assert x[i][0] >= 0 and s[i] >= margin * h, i
+    return fb
+
+
+def test_learned_detection_falls_back_exactly_where_the_rule_says(lib):
+    import torch
+    from paper_1912_01884_gb300 import learned
+    h, w, k, B = 512, 512, 8, 12
+    model = learned.LaneProposer(seed=2, lr=3e-3)
+    for step in range(20):
+        imgs = learned.lane_images(2000 + step, 16, h, w, k, B)
+        _, d, _ = learned.exact_paths(imgs, k, B)
+        labels = torch.from_numpy(learned.bins_of(d.cpu().numpy()).astype(np.int32)).cuda()
+        model.train_step(imgs, labels, k)
+    imgs = learned.lane_images(7000, 24, h, w, k, B)
+    plan = learned.LearnedPlan(imgs, k, B)
+    pred = model.propose(imgs, k)
+    win = model.windows(pred, h // k).cpu().numpy()
+    for margin in (0.0, 60.0, 1e9):
+        plan.run(model, margin)
+        plan.status()
+        fb = _check_learned(lib, imgs, k, B, plan, margin)
+        x, d, s = plan.x.cpu().numpy(), plan.d.cpu().numpy(), plan.score.cpu().numpy()
+        for i in range(imgs.shape[0]):
+            xo, do, so = oracle.detect_windowed(imgs[i].cpu().numpy(), k, B, win[i])
+            n = h // k
+            edge = any((do[b] == win[i][b][0] and win[i][b][0] > -(n - 1)) or
+                       (do[b] == win[i][b][1] and win[i][b][1] < n - 1) for b in range(k)) \
+                if xo[0] >= 0 else True
+            want_fb = xo[0] < 0 or edge or so < margin * h
+            assert bool(fb[i]) == bool(want_fb), (margin, i)
+            if not fb[i]:
+                assert list(x[i]) == list(xo) and list(d[i]) == list(do) and int(s[i]) == int(so)
+        if margin == 1e9:
+            assert fb.all()
+
+
+def test_learned_detection_is_captured_in_a_cuda_graph(lib):
+    import torch
+    from paper_1912_01884_gb300 import learned
+    h, w, k, B = 256, 256, 4, 8
+    model = learned.LaneProposer(seed=4)
+    imgs = learned.lane_images(8000, 8, h, w, k, B)
+    plan = learned.LearnedPlan(imgs, k, B)
+    stream = torch.cuda.Stream()
+    plan.run(model, 50.0, stream=stream)   # first use outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        plan.run(model, 50.0, stream=stream)
+    for t in (plan.x, plan.d, plan.score, plan.used_fallback):
+        t.fill_(-7)
+    with torch.cuda.stream(stream):
+        g.replay()
+    torch.cuda.synchronize()
+    _check_learned(lib, imgs, k, B, plan, 50.0)
