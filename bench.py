@@ -983,9 +983,12 @@ def run_standalone(args):
 
 
 def run_learned(args):
-    """Trains the proposal network on images labelled by the exact method,
-    then times the plain DP and the learned pipeline on held-out batches and
-    reports the exact-optimum hit rate and the score gap."""
+    """Trains the proposal network on images labelled by the exact method
+    (Adam, batches of 32, learning rate 3e-3, then 1e-3 and 3e-4), then on a
+    held-out batch reports, for each fallback rule, the exact-optimum hit rate,
+    the fallback rate and the score gap, and times the learned pipeline
+    (fhtdp_detect_learned) against the plain exact DP on the same batch, both
+    with CUDA events on one stream."""
     import numpy as np
     import torch
 
@@ -997,66 +1000,84 @@ def run_learned(args):
     fd.load()
     h = w = 1024
     k, B = 16, 12
-    batch = args.images or WORKLOADS["learned1024"]["images"]
-    train_steps = max(1, 49152 // batch)
-    model = learned.LaneProposer(seed=args.seed)
+    N = args.images or WORKLOADS["learned1024"]["images"]
+    bs, train_steps = 32, 1500
+    model = learned.LaneProposer(seed=args.seed, lr=3e-3)
     t0 = time.perf_counter()
     losses = []
     for step in range(train_steps):
-        imgs = learned.lane_images(10 * args.seed + 1000 + step, batch, h, w, k, B)
+        if step == int(train_steps * 0.6):
+            model.lr = 1e-3
+        if step == int(train_steps * 0.85):
+            model.lr = 3e-4
+        imgs = learned.lane_images(10 * args.seed + 1000 + step, bs, h, w, k, B)
         _, d, _ = learned.exact_paths(imgs, k, B)
         labels = torch.from_numpy(learned.bins_of(d.cpu().numpy()).astype(np.int32)).cuda()
-        losses.append(float(model.train_step(imgs, labels, k).cpu()))
+        loss = model.train_step(imgs, labels, k)
+        if step < 5 or step >= train_steps - 20:
+            losses.append(float(loss.cpu()))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
 
-    plain_ms, learned_ms, hits, total, fallbacks, gaps = [], [], 0, 0, 0, []
-    for j in range(args.warmup + args.steps):
-        imgs = learned.lane_images(10**6 + 97 * args.seed + j, batch, h, w, k, B)
-        plan = fd.BatchPlan([imgs[i] for i in range(batch)], [k] * batch, [B] * batch)
-        plan.run()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        plan.run()
-        e1.record()
-        torch.cuda.synchronize()
-        xe, de, se = torch.stack(plan.x), torch.stack(plan.d), torch.cat(plan.score)
-        t1 = time.perf_counter()
-        x, d, s, fb = learned.detect_learned(model, imgs, k, B)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        if j < args.warmup:
-            continue
-        plain_ms.append(e0.elapsed_time(e1))
-        learned_ms.append((t2 - t1) * 1e3)
-        same = (s == se) & (x == xe).all(1) & (d == de).all(1)
-        hits += int(same.sum())
-        total += batch
-        fallbacks += int(fb.sum())
-        sd, se_ = s.double().cpu().numpy(), se.double().cpu().numpy()
-        gaps.extend(((se_ - sd) / se_).tolist())
-    pix = batch * h * w
-    plain = pix / (np.mean(plain_ms) / 1e3) / 1e6
-    value = pix / (np.mean(learned_ms) / 1e3) / 1e6
+    imgs = learned.lane_images(10**6 + 97 * args.seed, N, h, w, k, B)
+    xe, de, se = learned.exact_paths(imgs, k, B)
+    win = model.windows(model.propose(imgs, k), h // k)
+    in_windows = float(((de >= win[..., 0]) & (de <= win[..., 1])).all(1).float().mean())
+    plan = learned.LearnedPlan(imgs, k, B)
+    rules = {}
+    for margin, min_conf in ((0.0, 0.0), (0.0, 0.5), (0.0, 0.8), (100.0, 0.0)):
+        plan.run(model, margin, min_conf)
+        plan.status()
+        hit = (plan.score == se) & (plan.x == xe).all(1) & (plan.d == de).all(1)
+        gap = (se - plan.score).double() / se.double()
+        rules["margin%g_conf%g" % (margin, min_conf)] = {
+            "exact_optimum_hit_rate": float(hit.float().mean()),
+            "fallback_rate": float(plan.used_fallback.float().mean()),
+            "score_gap_mean": float(gap.mean()), "score_gap_max": float(gap.max())}
+
+    stream = torch.cuda.Stream()
+    plain = fd.BatchPlan([imgs[i] for i in range(N)], [k] * N, [B] * N, stream=stream)
+    plain.autotune(reps=2, stream=stream)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    pix = N * h * w
+    plain_ms = timed(lambda: plain.run(stream=stream))
+    learned_ms = {m: timed(lambda m=m: plan.run(model, m[0], m[1], stream=stream))
+                  for m in ((0.0, 0.0), (100.0, 0.0))}
+    cnn_ms = timed(lambda: model.forward(imgs, k))
+    value = pix / learned_ms[(0.0, 0.0)] / 1e3
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": float(np.mean(learned_ms)), "higher_is_better": True,
+            "ms_per_step": learned_ms[(0.0, 0.0)], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32 DP, bf16 CNN",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS["learned1024"]["desc"], "images_per_step": batch},
-            "learned": {"plain_dp_mpix_s": plain, "learned_pipeline_mpix_s": value,
-                        "speedup_vs_plain": value / plain,
-                        "exact_optimum_hit_rate": hits / total,
-                        "fallback_rate": fallbacks / total,
-                        "score_gap_mean": float(np.mean(gaps)), "score_gap_max": float(np.max(gaps)),
-                        "train_images": train_steps * batch, "train_seconds": train_s,
-                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-5:])),
-                        "timing": "plain: CUDA events around one persistent launch; learned: "
-                                  "wall clock of CNN + windows + pruned DP + host fallback "
-                                  "decision + fallback DP"},
+            "config": {"workload": WORKLOADS["learned1024"]["desc"], "images_per_step": N},
+            "learned": {"plain_dp_mpix_s": pix / plain_ms / 1e3,
+                        "learned_mpix_s_margin0": value,
+                        "learned_mpix_s_margin100": pix / learned_ms[(100.0, 0.0)] / 1e3,
+                        "cnn_forward_ms": cnn_ms, "plain_dp_ms": plain_ms,
+                        "speedup_vs_plain": plain_ms / learned_ms[(0.0, 0.0)],
+                        "windows_contain_optimum": in_windows, "rules": rules,
+                        "train_images": train_steps * bs, "train_seconds": train_s,
+                        "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:])),
+                        "timing": "CUDA events over --steps back-to-back launches on one "
+                                  "stream; learned = CNN + windows + pruned DP + device "
+                                  "fallback decision + fallback DP"},
         }), flush=True)
 
 

@@ -488,8 +488,9 @@ int fhtdp_cnn_step(void *params, const void *ws, int n, int h, int w, float lr, 
  *      the windows;
  *   3. an image falls back to the full DP when the pruned DP found no
  *      polyline, when the polyline touches a window edge that is not an edge
- *      of the displacement range, or when its score is below the confidence
- *      margin, margin * h (a mean intensity per image row);
+ *      of the displacement range, when its score is below the confidence
+ *      margin, margin * h (a mean intensity per image row), or when the
+ *      network gave some band's bin a softmax probability below min_conf;
  *      used_fallback[i] (device, may be NULL) records it;
  *   4. one more persistent launch runs the full DP of the images that fall
  *      back only (the others' work items are skipped), into the images'
@@ -505,7 +506,7 @@ size_t fhtdp_learned_workspace_bytes(const fhtdp_learned_plan *plan);
 int fhtdp_learned_upload(fhtdp_learned_plan *plan, void *ws, size_t ws_bytes,
                          cudaStream_t stream);
 int fhtdp_detect_learned(fhtdp_learned_plan *plan, const void *params, float margin,
-                         int32_t *used_fallback, void *ws, cudaStream_t stream);
+                         float min_conf, int32_t *used_fallback, void *ws, cudaStream_t stream);
 /* FHTDP_ETIMEOUT if a bounded device wait of the last detect_learned on this
  * workspace gave up; synchronises `stream`. */
 int fhtdp_learned_status(const fhtdp_learned_plan *plan, const void *ws, cudaStream_t stream);

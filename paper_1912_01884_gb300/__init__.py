@@ -157,8 +157,8 @@ _SIGS = {
     "fhtdp_learned_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "fhtdp_learned_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                             ctypes.c_void_p]),
-    "fhtdp_detect_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float]
-                             + [ctypes.c_void_p] * 3),
+    "fhtdp_detect_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                                            ctypes.c_float] + [ctypes.c_void_p] * 3),
     "fhtdp_learned_status": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "fhtdp_learned_plan_destroy": (None, [ctypes.c_void_p]),
 }

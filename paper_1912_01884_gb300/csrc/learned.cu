@@ -134,14 +134,18 @@ int forward(const char *P, const uint8_t *imgs, int n, int h, int w, int bands, 
 // The fallback decision of the learned detection: image i falls back to the
 // full DP when its pruned DP found no polyline inside the windows, when the
 // polyline touches a window edge that is not an edge of the displacement
-// range (a better link may lie just outside), or when its score is below
-// margin * h (the confidence margin, in mean intensity per image row).
-__global__ void decide_kernel(int N, int k, int n, int h, float margin, const int32_t *__restrict__ x,
-                              const int32_t *__restrict__ d, const int32_t *__restrict__ s,
-                              const int32_t *__restrict__ win, int32_t *__restrict__ fb,
+// range (a better link may lie just outside), when its score is below
+// margin * h (the confidence margin, in mean intensity per image row), or
+// when the network gave some band's bin a softmax probability below
+// min_conf.
+__global__ void decide_kernel(int N, int k, int n, int h, float margin, float min_conf,
+                              const int32_t *__restrict__ x, const int32_t *__restrict__ d,
+                              const int32_t *__restrict__ s, const int32_t *__restrict__ win,
+                              const float *__restrict__ conf, int32_t *__restrict__ fb,
                               int32_t *__restrict__ used) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         bool f = x[(size_t)i * (k + 1)] < 0 || (float)s[i] < margin * (float)h;
+        for (int b = 0; b < k && !f; ++b) f = conf[(size_t)i * k + b] < min_conf;
         for (int b = 0; b < k && !f; ++b) {
             const int lo = win[((size_t)i * k + b) * 2], hi = win[((size_t)i * k + b) * 2 + 1];
             const int db = d[(size_t)i * k + b];
@@ -405,7 +409,7 @@ int fhtdp_learned_upload(fhtdp_learned_plan *p, void *ws, size_t ws_bytes, cudaS
 }
 
 int fhtdp_detect_learned(fhtdp_learned_plan *p, const void *params, float margin,
-                         int32_t *used_fallback, void *ws, cudaStream_t stream) {
+                         float min_conf, int32_t *used_fallback, void *ws, cudaStream_t stream) {
     clear_error();
     if (!p || !params || !ws) return set_error(FHTDP_EINVAL, "null plan, params or workspace");
     if (ws != p->bound)
@@ -431,8 +435,8 @@ int fhtdp_detect_learned(fhtdp_learned_plan *p, const void *params, float margin
     //    others' items are skipped) and the pruned results of the rest
     if (!st) {
         decide_kernel<<<(p->N + 255) / 256, 256, 0, stream>>>(
-            p->N, p->k, n, p->h, margin, (const int32_t *)(W + p->off_x),
-            (const int32_t *)(W + p->off_d), (const int32_t *)(W + p->off_s), win,
+            p->N, p->k, n, p->h, margin, min_conf, (const int32_t *)(W + p->off_x),
+            (const int32_t *)(W + p->off_d), (const int32_t *)(W + p->off_s), win, conf,
             (int32_t *)(W + p->off_fb), used_fallback);
         st = launched("decide_kernel");
     }

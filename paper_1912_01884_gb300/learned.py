@@ -6,7 +6,8 @@ low-resolution rows of a band) predicts for every band one of 32 bins of 4
 displacements.  The DP then searches only a 16-wide window around the
 predicted bin (the pruned DP).  An image falls back to the full DP when its
 pruned optimum does not exist, touches a window edge, or scores below a
-confidence margin (a mean intensity per image row).  The network is trained
+confidence margin (a mean intensity per image row), or where the network's
+own confidence in a band's bin is low.  The network is trained
 on labels that the exact method produces.  The paper has none of this: it is
 an addition in front of the method.
 
@@ -186,12 +187,12 @@ class LearnedPlan:
         _check(lib().fhtdp_learned_upload(handle, self.ws.data_ptr(), self.ws.numel(),
                                           _stream(stream)))
 
-    def run(self, model, margin: float, stream=None):
+    def run(self, model, margin: float, min_conf: float = 0.0, stream=None):
         """Enqueues the detection; results in self.x, self.d, self.score and
         self.used_fallback."""
         _check(lib().fhtdp_detect_learned(self._plan, model.params.data_ptr(), float(margin),
-                                          self.used_fallback.data_ptr(), self.ws.data_ptr(),
-                                          _stream(stream)))
+                                          float(min_conf), self.used_fallback.data_ptr(),
+                                          self.ws.data_ptr(), _stream(stream)))
 
     def status(self, stream=None):
         _check(lib().fhtdp_learned_status(self._plan, self.ws.data_ptr(), _stream(stream)))
@@ -219,11 +220,11 @@ def exact_paths(imgs, k, B):
     return (torch.stack(plan.x), torch.stack(plan.d), torch.cat(plan.score))
 
 
-def detect_learned(model, imgs, k, B, margin: float = 0.0):
+def detect_learned(model, imgs, k, B, margin: float = 0.0, min_conf: float = 0.0):
     """Learned proposal + pruned DP + device-side fallback (fhtdp_detect_learned).
     Returns (x, d, score, used_fallback[N]); images that fall back carry the
     exact method's outputs."""
     plan = LearnedPlan(imgs, k, B)
-    plan.run(model, margin)
+    plan.run(model, margin, min_conf)
     plan.status()
     return plan.x, plan.d, plan.score, plan.used_fallback.bool()
