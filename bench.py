@@ -90,11 +90,9 @@ NCU_TRAFFIC_BYTES_PER_PIXEL = {
     "plain2048": (252.65e6 + 1.02e9) / (32 * 2048 * 2048),
     "float8192": (269.83e6 + 637.90e6) / (8192 * 8192),   # profiles/engine_kernel_wide_float8192.md
 }
-# The window DP kernel changed (it now takes any window table and value
-# type) after its ncu capture (profiles/dp_band_angle_kernel_2048x2048_k16_gamma10.md,
-# 4.14 MB per band launch), so the standalone workloads report no traffic
-# until it is captured again.
-NCU_TRAFFIC_DP_WINDOW_LAUNCH = None
+# DRAM bytes of one dp_band_window_kernel band launch on the 2048x2048, k = 16
+# workloads (profiles/dp_band_window_kernel_angle2048.md).
+NCU_TRAFFIC_DP_WINDOW_LAUNCH = 4.14e6
 
 
 # The main problem's smoothing half-width and bend angle (the paper's
