@@ -1964,9 +1964,9 @@ struct U8Ctl {
         slot->prefetched = c.im && c.tma;
     }
 
-    // Lanes of the control warp: the flags an item waits for (at most one
-    // per lane; true when there is none), acquired with a bounded spin.
-    __device__ static bool wait_producers(const Ctrl &cur, const LaunchArgs &args, int lane) {
+    // The flag lane `lane` of the control warp waits for before the item's
+    // M tile is copied (at most one per lane; null when there is none).
+    __device__ static const int *producer_flag(const Ctrl &cur, int lane) {
         const ImgDesc &im = *cur.im;
         const int *flag = nullptr;
         if (cur.kind == kItemBand) {
@@ -1991,6 +1991,12 @@ struct U8Ctl {
                     flag = im.fflags + (size_t)(cur.band * 2 + 1) * im.ftiles + c;
             }
         }
+        return flag;
+    }
+    // Lanes of the control warp: the item's producer flags, acquired with a
+    // bounded spin (true when all are set).
+    __device__ static bool wait_producers(const Ctrl &cur, const LaunchArgs &args, int lane) {
+        const int *flag = producer_flag(cur, lane);
         bool ok = true;
         if (flag) {
             ok = wait_flag(flag, args.ctl, args.wait_cycles);
@@ -1998,6 +2004,27 @@ struct U8Ctl {
         }
         __syncwarp();
         return __all_sync(0xffffffffu, ok);
+    }
+    // Lanes of the control warp, while the compute warps finish item
+    // `busy`: polls the producer flags of the next item until all are set
+    // (true; acquired) or the compute warps report `busy` done (false; the
+    // flags may then include busy's own, which is published only after it).
+    __device__ static bool poll_producers(const Ctrl &nx, const LaunchArgs &args, int lane,
+                                          const volatile long long *done, long long busy) {
+        const int *flag = producer_flag(nx, lane);
+        const long long t0 = clock64();
+        for (;;) {
+            const bool set = !flag || ld_acquire(flag) != 0;
+            if (__all_sync(0xffffffffu, set)) {
+                if (flag) fence_acq_rel_gpu();
+                __syncwarp();
+                return true;
+            }
+            if (*done == busy || clock64() - t0 > args.wait_cycles ||
+                *(volatile const int *)&args.ctl->status != FHTDP_OK)
+                return false;
+            __nanosleep(64);
+        }
     }
 
     // Lane 0, after the FHT: the M tile of the item into the V rows (or just
@@ -2052,25 +2079,29 @@ struct U8Ctl {
     }
 
     // The control warp: takes the items from the queue one ahead of the
-    // compute warps, copies each strip as soon as Hc is free, waits for an
-    // item's producers during its FHT, copies its M tile as soon as the FHT is
-    // done, and releases its flag once its window maxima are stored (band 0:
-    // counts the tile and reads the polyline back after the image's last).
+    // compute warps, copies each strip as soon as Hc is free, copies an
+    // item's M tile as soon as its FHT is done, and releases its flag once its
+    // window maxima are stored (band 0: counts the tile and reads the
+    // polyline back after the image's last).  The producer flags of the next
+    // item are polled while the compute warps finish the current one, so
+    // that the M copy seldom waits for them; whatever is not yet set then
+    // (possibly the current item's own flag) is waited for after the
+    // current item's publication.
     __device__ static void control(const LaunchArgs &args, unsigned char *smem, WsSlot *slot,
-                                   Pipe &pipe) {
+                                   Pipe &pipe, const volatile long long *done) {
         const int lane = threadIdx.x & 31;
         uint32_t *Hc = (uint32_t *)(smem + u8_hc_offset<Key>());
         int32_t *Vn = (int32_t *)smem;
-        long long first = 0;
-        if (lane == 0) first = take(args);
-        Ctrl cur = decode(args, __shfl_sync(0xffffffffu, first, 0));
+        long long idx = 0;
+        if (lane == 0) idx = take(args);
+        Ctrl cur = decode(args, __shfl_sync(0xffffffffu, idx, 0));
         if (lane == 0) hand_over(cur, slot, Hc, pipe);
         nb_arrive(kBarNext, kCtlSync);
+        if (lane == 0 && cur.item < args.items) idx = take(args);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        bool ok = cur.item < args.items ? wait_producers(cur, args, lane) : true;
         while (cur.item < args.items) {
-            long long nx = 0;
-            if (lane == 0) nx = take(args);
-            const Ctrl next = decode(args, __shfl_sync(0xffffffffu, nx, 0));
-            const bool ok = wait_producers(cur, args, lane);
+            const Ctrl next = decode(args, idx);
             nb_sync(kBarFhtDone, kCtlSync);
             if (lane == 0) {
                 if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
@@ -2079,8 +2110,15 @@ struct U8Ctl {
             nb_sync(kBarHcFree, kCtlSync);
             if (lane == 0) hand_over(next, slot, Hc, pipe);
             nb_arrive(kBarNext, kCtlSync);
+            const bool ready = next.item >= args.items ||
+                               poll_producers(next, args, lane, done, cur.item);
             nb_sync(kBarWinDone, kCtlSync);
-            if (lane == 0) finish(cur, args);
+            if (lane == 0) {
+                finish(cur, args);
+                if (next.item < args.items) idx = take(args);
+            }
+            idx = __shfl_sync(0xffffffffu, idx, 0);
+            ok = ready || wait_producers(next, args, lane);
             cur = next;
         }
     }
@@ -2514,9 +2552,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ __align__(16) WsSlot s_slot;
+    __shared__ volatile long long s_done;   // the last item thread 0 finished
     if (threadIdx.x == 0) {
         mbar_init(&s_bar, 1);
         mbar_init(&s_mbar, 1);
+        s_done = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -2531,16 +2571,19 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 if (sl.kind == kItemDp256) {
                     U8Path<Key, kMulti>::process_dp256(*sl.im, sl.band, sl.tile, smem_raw, args,
                                                        pipe);
+                    if (threadIdx.x == 0) s_done = sl.item;
                     continue;
                 }
             }
             const int half = sl.kind == kItemHalf0 ? 0 : sl.kind == kItemHalf1 ? 1 : -1;
             U8Path<Key, kMulti>::process(*sl.im, sl.band, sl.tile, smem_raw, args, pipe,
                                          sl.prefetched != 0, half);
+            // a hint for the control warp's polling (ordering comes from kBarWinDone)
+            if (threadIdx.x == 0) s_done = sl.item;
         }
     } else {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 32;" ::: "memory");
-        if (threadIdx.x < kCtlSync) U8Ctl<Key>::control(args, smem_raw, &s_slot, pipe);
+        if (threadIdx.x < kCtlSync) U8Ctl<Key>::control(args, smem_raw, &s_slot, pipe, &s_done);
     }
 }
 
