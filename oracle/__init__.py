@@ -32,6 +32,11 @@ Function map (paper passages in the C file's comments):
   detect_horizontal  Sec. 3, Fig. 7: mostly horizontal polylines (transposition)
   detect_padded / brute_padded / path_score_padded
                    Sec. 2.2: vertices anywhere in the zero-padded band width
+  gauss_rows_f32 / detect_angle_f32 / detect_angle_through_f32 /
+  detect_through_f32 / detect_padded_f32 / detect_two_f32 /
+  detect_horizontal_f32
+                   the same queries on float32 images in float32 arithmetic
+                   (the decisions of the library's float path)
 """
 from __future__ import annotations
 
@@ -143,6 +148,21 @@ def _load():
                                                            + [ctypes.c_double, ctypes.c_int,
                                                               ctypes.c_int, _I32P, _I32P])
             lib.oracle_brute_angle_through_f64.restype = ctypes.c_double
+            lib.oracle_gauss_rows_f32.argtypes = [_F32P] + [ctypes.c_int] * 3 + [_F32P]
+            lib.oracle_detect_angle_f32.argtypes = ([_F32P] + [ctypes.c_int] * 4
+                                                    + [ctypes.c_double, _I32P, _I32P])
+            lib.oracle_detect_angle_f32.restype = ctypes.c_double
+            lib.oracle_detect_angle_through_f32.argtypes = ([_F32P] + [ctypes.c_int] * 4
+                                                            + [ctypes.c_double, ctypes.c_int,
+                                                               ctypes.c_int, _I32P, _I32P])
+            lib.oracle_detect_angle_through_f32.restype = ctypes.c_double
+            lib.oracle_detect_through_f32.argtypes = ([_F32P] + [ctypes.c_int] * 6
+                                                      + [_I32P, _I32P])
+            lib.oracle_detect_through_f32.restype = ctypes.c_double
+            lib.oracle_detect_padded_f32.argtypes = [_F32P] + [ctypes.c_int] * 4 + [_I32P, _I32P]
+            lib.oracle_detect_padded_f32.restype = ctypes.c_double
+            lib.oracle_detect_two_f32.argtypes = ([_F32P] + [ctypes.c_int] * 5
+                                                  + [_I32P, _I32P, _F64P])
             _lib = lib
     return _lib
 
@@ -512,3 +532,88 @@ def brute_angle_through(img, k: int, gamma: float, j: int, xp: int):
                                                int(j), int(xp), _p(xs, ctypes.c_int32),
                                                _p(ds, ctypes.c_int32))
     return xs, ds, s
+
+
+def _f32(img) -> np.ndarray:
+    return np.ascontiguousarray(img, dtype=np.float32)
+
+
+def gauss_rows_f32(img, r: int) -> np.ndarray:
+    """gauss_rows in float32: products and sums rounded to float, t from -r
+    to r."""
+    img = _f32(img)
+    h, w = img.shape
+    out = np.empty_like(img)
+    if _load().oracle_gauss_rows_f32(_p(img, ctypes.c_float), h, w, int(r),
+                                     _p(out, ctypes.c_float)):
+        raise ValueError("r must be >= 0")
+    return out
+
+
+def detect_angle_f32(img, k: int, r: int, gamma: float):
+    """The main problem on a float32 image in float32: (x, d, score)."""
+    img = _f32(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_angle_f32(_p(img, ctypes.c_float), h, w, k, int(r), float(gamma),
+                                        _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def detect_angle_through_f32(img, k: int, r: int, gamma: float, j: int, xp: int):
+    """Subproblem 3 with the bend angle on a float32 image in float32."""
+    img = _f32(img)
+    h, w, _ = _band_rows(img, k)
+    if not (0 <= j <= k and 0 <= xp < w):
+        raise ValueError("point outside the image")
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_angle_through_f32(_p(img, ctypes.c_float), h, w, k, int(r),
+                                                float(gamma), int(j), int(xp),
+                                                _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def detect_through_f32(img, k: int, B: int, j: int, xp: int):
+    """The extreme polyline through (xp, j*n) on a float32 image in float32."""
+    img = _f32(img)
+    h, w, _ = _band_rows(img, k)
+    if not (0 <= j <= k and 0 <= xp < w):
+        raise ValueError("point outside the image")
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_through_f32(_p(img, ctypes.c_float), h, w, k, B, int(j), int(xp),
+                                          _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def detect_padded_f32(img, k: int, B: int):
+    """Vertices in [0, w + n) on a float32 image in float32."""
+    img = _f32(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros(k + 1, dtype=np.int32)
+    ds = np.zeros(k, dtype=np.int32)
+    s = _load().oracle_detect_padded_f32(_p(img, ctypes.c_float), h, w, k, B,
+                                         _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32))
+    return xs, ds, s
+
+
+def detect_two_f32(img, k: int, B: int, sep: int):
+    """Two different extreme polylines on a float32 image in float32."""
+    img = _f32(img)
+    h, w, _ = _band_rows(img, k)
+    xs = np.zeros((2, k + 1), dtype=np.int32)
+    ds = np.zeros((2, k), dtype=np.int32)
+    sc = np.zeros(2, dtype=np.float64)
+    if _load().oracle_detect_two_f32(_p(img, ctypes.c_float), h, w, k, B, int(sep),
+                                     _p(xs, ctypes.c_int32), _p(ds, ctypes.c_int32),
+                                     _p(sc, ctypes.c_double)):
+        raise ValueError("bad shape, bend or separation")
+    return xs, ds, sc
+
+
+def detect_horizontal_f32(img, k: int, B: int):
+    """Mostly horizontal polylines on a float32 image in float32: detect_f32
+    on the transposed image."""
+    return detect_f32(np.ascontiguousarray(np.asarray(img, dtype=np.float32).T), k, B)

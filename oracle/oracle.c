@@ -10,9 +10,11 @@
  * header, table or constant with the CUDA sources.
  *
  * Everything is plain loops in double precision (exact for every integer
- * image the library accepts), plus a float32 copy of the FHT recursion and of
- * the DP: the float path of the library takes its argmax decisions in float32,
- * so the oracle takes the same decisions in the same precision.
+ * image the library accepts), plus float32 copies of the FHT recursion, of
+ * the DP and of the queries (smoothing and bend angle, through-point, padded
+ * vertices, two polylines): the float path of the library takes its argmax
+ * decisions in float32, so the oracle takes the same decisions in the same
+ * precision.
  *
  * Conventions (the paper is silent or garbled on each; the readings are the
  * ones listed with the design notes):
@@ -1122,4 +1124,262 @@ double oracle_brute_angle_through_f64(const double *img, int h, int w, int k, do
     }
     free(st.cur_d);
     return st.best;
+}
+
+/* ---------------------------------------------------------------------------
+ * The queries of Secs. 2.2-2.3 and 3 on float32 images, in float32: the
+ * decisions the library's float path takes for them.  Each is the float64
+ * definition above with every value, sum and comparison in float, and the
+ * Hough images from the float32 recursion (oracle_fht_recursive_f32, whose
+ * summation tree the CUDA path follows).
+ * ------------------------------------------------------------------------ */
+
+/* Sec. 2.3 step 1 in float32: out(y, x) = sum over t = -r..r, in that order,
+ * of (float)C(2r, r + t) * img(y, x + t), each product rounded to float and
+ * added to a float accumulator that starts at 0; pixels outside the row are
+ * skipped (adding their zero product would not change a float sum). */
+int oracle_gauss_rows_f32(const float *img, int h, int w, int r, float *out) {
+    if (r < 0) return -1;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            float acc = 0.0f;
+            for (int t = -r; t <= r; ++t) {
+                int c = x + t;
+                if (c < 0 || c >= w) continue;
+                float prod = (float)binom(2 * r, r + t) * img[(size_t)y * w + c];
+                acc = acc + prod;
+            }
+            out[(size_t)y * w + x] = acc;
+        }
+    return 0;
+}
+
+/* The DP of Sec. 2.3 in float32 with per-displacement windows lohi (the
+ * angle windows of oracle_angle_window) and, when j >= 0, the point P =
+ * (xp, j*n) of Subproblem 3 (states off P dead, as oracle_dp_through_f64). */
+static int dp_table_point_f32(const float *H, int h, int w, int k, const int32_t *lohi, int j,
+                              int xp, float *V) {
+    if (k < 1 || h % k != 0) return -1;
+    if (j >= 0 && (j > k || xp < 0 || xp >= w)) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    for (int b = k - 1; b >= 0; --b)
+        for (int d = -(n - 1); d <= n - 1; ++d)
+            for (int x = 0; x < w; ++x) {
+                float *out = &V[((size_t)b * D + (d + n - 1)) * w + x];
+                int xn = x + d;
+                int off_point =
+                    j >= 0 && ((b == j && x != xp) || (j == k && b == k - 1 && xn != xp));
+                if (xn < 0 || xn >= w || off_point) {
+                    *out = (float)ORACLE_NEG;
+                    continue;
+                }
+                float hv = hough_at_f32(H, n, W, b, x, d);
+                if (b == k - 1) {
+                    *out = hv;
+                    continue;
+                }
+                float best = (float)ORACLE_NEG;
+                for (int e = lohi[2 * (d + n - 1)]; e <= lohi[2 * (d + n - 1) + 1]; ++e) {
+                    float v = V[((size_t)(b + 1) * D + (e + n - 1)) * w + xn];
+                    if (v > best) best = v;
+                }
+                *out = (best == (float)ORACLE_NEG) ? (float)ORACLE_NEG : hv + best;
+            }
+    return 0;
+}
+
+int oracle_dp_angle_f32(const float *H, int h, int w, int k, const int32_t *lohi, float *V) {
+    return dp_table_point_f32(H, h, w, k, lohi, -1, 0, V);
+}
+
+/* The read-back of Eq. 5 with the angle windows, in float32. */
+double oracle_backtrack_angle_f32(const float *V, int h, int w, int k, const int32_t *lohi,
+                                  int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int D = 2 * n - 1;
+    float best = (float)ORACLE_NEG;
+    int bx = 0, bd = 0;
+    for (int x = 0; x < w; ++x)
+        for (int d = -(n - 1); d <= n - 1; ++d) {
+            float v = V[(size_t)(d + n - 1) * w + x];
+            if (v > best) {
+                best = v;
+                bx = x;
+                bd = d;
+            }
+        }
+    if (best == (float)ORACLE_NEG) {
+        for (int i = 0; i <= k; ++i) xs[i] = -1;
+        for (int i = 0; i < k; ++i) ds[i] = 0;
+        return ORACLE_NEG;
+    }
+    xs[0] = bx;
+    ds[0] = bd;
+    for (int i = 1; i < k; ++i) {
+        int xi = xs[i - 1] + ds[i - 1];
+        xs[i] = xi;
+        int p = ds[i - 1] + n - 1;
+        float bv = (float)ORACLE_NEG;
+        int be = lohi[2 * p];
+        for (int e = lohi[2 * p]; e <= lohi[2 * p + 1]; ++e) {
+            float v = V[((size_t)i * D + (e + n - 1)) * w + xi];
+            if (v > bv) {
+                bv = v;
+                be = e;
+            }
+        }
+        ds[i] = be;
+    }
+    xs[k] = xs[k - 1] + ds[k - 1];
+    return (double)best;
+}
+
+/* The main problem (j < 0) or Subproblem 3 through (xp, j*n), in float32:
+ * smoothing, the float32 recursion, the windowed DP and the read-back. */
+static double detect_angle_point_f32(const float *img, int h, int w, int k, int r, double gamma,
+                                     int j, int xp, int32_t *xs, int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    float *S = (float *)malloc(sizeof(float) * (size_t)h * w);
+    float *H = (float *)malloc(sizeof(float) * (size_t)k * 2 * n * W);
+    float *V = (float *)malloc(sizeof(float) * (size_t)k * (2 * n - 1) * w);
+    int32_t *lohi = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * n - 1));
+    double s = NAN;
+    if (S && H && V && lohi && oracle_gauss_rows_f32(img, h, w, r, S) == 0 &&
+        oracle_angle_window(n, gamma, lohi) == 0) {
+        oracle_fht_recursive_f32(S, h, w, k, H);
+        if (dp_table_point_f32(H, h, w, k, lohi, j, xp, V) == 0)
+            s = oracle_backtrack_angle_f32(V, h, w, k, lohi, xs, ds);
+    }
+    free(S);
+    free(H);
+    free(V);
+    free(lohi);
+    return s;
+}
+
+double oracle_detect_angle_f32(const float *img, int h, int w, int k, int r, double gamma,
+                               int32_t *xs, int32_t *ds) {
+    return detect_angle_point_f32(img, h, w, k, r, gamma, -1, 0, xs, ds);
+}
+
+double oracle_detect_angle_through_f32(const float *img, int h, int w, int k, int r,
+                                       double gamma, int j, int xp, int32_t *xs, int32_t *ds) {
+    if (j < 0 || j > k || xp < 0 || xp >= w) return NAN;
+    return detect_angle_point_f32(img, h, w, k, r, gamma, j, xp, xs, ds);
+}
+
+/* Subproblems 2-3 with the bend limit B, in float32: the window of d is
+ * [d - B, d + B] clipped to the displacement range. */
+static void bend_table(int n, int B, int32_t *lohi) {
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        int lo = d - B, hi = d + B;
+        lohi[2 * (d + n - 1)] = lo < -(n - 1) ? -(n - 1) : lo;
+        lohi[2 * (d + n - 1) + 1] = hi > n - 1 ? n - 1 : hi;
+    }
+}
+
+double oracle_detect_through_f32(const float *img, int h, int w, int k, int B, int j, int xp,
+                                 int32_t *xs, int32_t *ds) {
+    if (k < 1 || h % k != 0 || B < 0 || j < 0 || j > k || xp < 0 || xp >= w) return NAN;
+    int n = h / k;
+    int W = w + n;
+    float *H = (float *)malloc(sizeof(float) * (size_t)k * 2 * n * W);
+    float *V = (float *)malloc(sizeof(float) * (size_t)k * (2 * n - 1) * w);
+    int32_t *lohi = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(2 * n - 1));
+    double s = NAN;
+    if (H && V && lohi) {
+        bend_table(n, B, lohi);
+        oracle_fht_recursive_f32(img, h, w, k, H);
+        if (dp_table_point_f32(H, h, w, k, lohi, j, xp, V) == 0)
+            s = oracle_backtrack_f32(V, h, w, k, B, xs, ds);
+    }
+    free(H);
+    free(V);
+    free(lohi);
+    return s;
+}
+
+/* Vertices in the padding (Sec. 2.2), float32: the DP over the vertex
+ * domain [0, W) as oracle_dp_padded_f64, and the read-back with W as the
+ * width. */
+int oracle_dp_padded_f32(const float *H, int h, int w, int k, int B, float *V) {
+    if (k < 1 || h % k != 0 || B < 0) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    for (int b = k - 1; b >= 0; --b)
+        for (int d = -(n - 1); d <= n - 1; ++d)
+            for (int x = 0; x < W; ++x) {
+                float *out = &V[((size_t)b * D + (d + n - 1)) * W + x];
+                int xn = x + d;
+                if (xn < 0 || xn >= W) {
+                    *out = (float)ORACLE_NEG;
+                    continue;
+                }
+                float hv = hough_at_f32(H, n, W, b, x, d);
+                if (b == k - 1) {
+                    *out = hv;
+                    continue;
+                }
+                float best = (float)ORACLE_NEG;
+                for (int e = d - B; e <= d + B; ++e) {
+                    if (e < -(n - 1) || e > n - 1) continue;
+                    float v = V[((size_t)(b + 1) * D + (e + n - 1)) * W + xn];
+                    if (v > best) best = v;
+                }
+                *out = (best == (float)ORACLE_NEG) ? (float)ORACLE_NEG : hv + best;
+            }
+    return 0;
+}
+
+double oracle_detect_padded_f32(const float *img, int h, int w, int k, int B, int32_t *xs,
+                                int32_t *ds) {
+    int n = h / k;
+    int W = w + n;
+    float *H = (float *)malloc(sizeof(float) * (size_t)k * 2 * n * W);
+    float *V = (float *)malloc(sizeof(float) * (size_t)k * (2 * n - 1) * W);
+    double s = NAN;
+    if (H && V) {
+        oracle_fht_recursive_f32(img, h, w, k, H);
+        oracle_dp_padded_f32(H, h, w, k, B, V);
+        s = oracle_backtrack_f32(V, h, W, k, B, xs, ds);
+    }
+    free(H);
+    free(V);
+    return s;
+}
+
+/* Two different extreme polylines (Sec. 3), float32: as
+ * oracle_detect_two_f64 on the float32 V. */
+int oracle_detect_two_f32(const float *img, int h, int w, int k, int B, int sep, int32_t *xs,
+                          int32_t *ds, double *scores) {
+    if (k < 1 || h % k != 0 || B < 0 || sep < 1) return -1;
+    int n = h / k;
+    int W = w + n;
+    int D = 2 * n - 1;
+    float *H = (float *)malloc(sizeof(float) * (size_t)k * 2 * n * W);
+    float *V = (float *)malloc(sizeof(float) * (size_t)k * D * w);
+    float *V2 = (float *)malloc(sizeof(float) * (size_t)k * D * w);
+    if (!H || !V || !V2) {
+        free(H);
+        free(V);
+        free(V2);
+        return -1;
+    }
+    oracle_fht_recursive_f32(img, h, w, k, H);
+    oracle_dp_f32(H, h, w, k, B, V);
+    scores[0] = oracle_backtrack_f32(V, h, w, k, B, xs, ds);
+    memcpy(V2, V, sizeof(float) * (size_t)k * D * w);
+    int x0 = xs[0];
+    for (int d = 0; d < D; ++d)
+        for (int x = 0; x < w; ++x)
+            if (x0 >= 0 && abs(x - x0) < sep) V2[(size_t)d * w + x] = (float)ORACLE_NEG;
+    scores[1] = oracle_backtrack_f32(V2, h, w, k, B, xs + k + 1, ds + k);
+    free(H);
+    free(V);
+    free(V2);
+    return 0;
 }
