@@ -188,12 +188,16 @@ int fhtdp_detect_polyline_noalloc_status(cudaStream_t stream);
  *             Eqs. 6-7; the pi/4 limit of Eqs. 6-7 is |e| <= n-1).
  *             gamma = 0 keeps the displacement fixed; gamma >= pi/2 admits
  *             every e.
- *   dtype     FHTDP_U8 or FHTDP_I32 (integer images; FHTDP_F32 returns
- *             FHTDP_EINVAL).  Sums are int32: uint8 images need
+ *   dtype     FHTDP_U8 or FHTDP_I32: sums are int32; uint8 images need
  *             255 * 4^r * h < 2^31 (checked); int32 images need
  *             max|pixel| * 4^r * h < 2^31 (the caller guarantees it).
- *   Scores are int32 and refer to the smoothed image.  Ties are broken as in
- *   fhtdp_detect_polyline (the lexicographically smallest polyline).
+ *             FHTDP_F32: everything in float32, each smoothing product
+ *             weight * pixel rounded and added in the order t = -r..r, the
+ *             FHT sums in the tree of fhtdp_fht_bands, the argmax decisions
+ *             taken on the float32 values.
+ *   Scores are int32 (integer images) or float (float images) and refer to
+ *   the smoothed image.  Ties are broken as in fhtdp_detect_polyline (the
+ *   lexicographically smallest polyline).
  * ---------------------------------------------------------------------- */
 /* The window of every displacement, on the host: lohi[2n-1][2] (HOST
  * memory, written by the call), row d + n - 1 = {lo(d), hi(d)}.  n is a
@@ -201,12 +205,14 @@ int fhtdp_detect_polyline_noalloc_status(cudaStream_t stream);
 int fhtdp_angle_window(int n, double gamma, int32_t *lohi);
 
 /* Step 1: out[y][x] = sum_t C(2r, r+t) img[y][x+t] (device; out is a dense
- * int32 [h][w] array, pitch w, that must not overlap img). */
-int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r, int32_t *out,
+ * [h][w] array, pitch w, of int32 for integer images or float for float
+ * images, that must not overlap img). */
+int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r, void *out,
                      cudaStream_t stream);
 
-/* Step 2: the DP of fhtdp_polyline_dp over int32 Hough images (laid out as
- * fhtdp_fht_bands leaves them), in place, with the bend-angle windows. */
+/* Step 2: the DP of fhtdp_polyline_dp over Hough images (int32, or float for
+ * FHTDP_F32; laid out as fhtdp_fht_bands leaves them), in place, with the
+ * bend-angle windows. */
 int fhtdp_polyline_dp_angle(void *hough, int dtype, int h, int w, int k, double gamma,
                             cudaStream_t stream);
 
@@ -231,7 +237,8 @@ int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pi
  * Subproblem 2 (no bend limit).  The paper finds the part above P by
  * flipping the top bands about Ox; one DP over all bands with the states of
  * P's band off xp marked dead reaches the same optimum.
- *   dtype  FHTDP_U8 or FHTDP_I32 (FHTDP_F32 returns FHTDP_EINVAL).
+ *   dtype  any of the three; float32 images are computed and decided in
+ *          float32 as in fhtdp_detect_polyline.
  *   ws     device workspace of at least fhtdp_through_workspace_bytes()
  *          bytes (0 for invalid arguments).  Outputs as for fhtdp_backtrack.
  * ---------------------------------------------------------------------- */
@@ -256,7 +263,7 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
  * right).  As fhtdp_detect_polyline, but every vertex may lie anywhere in
  * [0, W), W = w + n: the pixels a link covers right of the image count as
  * zero, so a curve that runs off the right edge can be followed.  Runs the
- * standalone kernels.  dtype FHTDP_U8 or FHTDP_I32; ws of at least
+ * standalone kernels.  dtype any of the three; ws of at least
  * fhtdp_through_workspace_bytes() bytes.  Outputs as for fhtdp_backtrack.
  * ---------------------------------------------------------------------- */
 int fhtdp_detect_polyline_padded(const void *img, int dtype, int h, int w, int pitch, int k,
@@ -269,9 +276,10 @@ int fhtdp_detect_polyline_padded(const void *img, int dtype, int h, int w, int p
  * fhtdp_detect_polyline; the second is the best admissible polyline whose top
  * vertex x_0 lies at least sep (>= 1) columns from the first's (suppression
  * on x_0), the lexicographically smallest among its optima.  When no column
- * is far enough, the second has x = -1 everywhere and score INT32_MIN.
- *   dtype  FHTDP_U8 or FHTDP_I32.
- *   x_out [2][k+1], d_out [2][k], score_out [2] int32 (device).
+ * is far enough, the second has x = -1 everywhere and score INT32_MIN (or
+ * -infinity for float images).
+ *   dtype  any of the three.
+ *   x_out [2][k+1], d_out [2][k], score_out [2] int32 or float (device).
  *   ws     device workspace of at least fhtdp_two_workspace_bytes() bytes.
  * ---------------------------------------------------------------------- */
 size_t fhtdp_two_workspace_bytes(int dtype, int h, int w, int k);

@@ -437,36 +437,33 @@ def angle_window(n: int, gamma: float):
     return out
 
 
-def _int_image_code(img) -> int:
-    code = _dtype_code(img)
-    if code == DTYPE_F32:
-        raise TypeError("the angle path takes uint8 or int32 images")
-    return code
-
-
 def gauss_rows(img, r: int, out=None, stream=None):
-    """Every row convolved with the binomial weights C(2r, r+t): int32 [h, w]."""
+    """Every row convolved with the binomial weights C(2r, r+t): [h, w], int32
+    for uint8 / int32 images, float32 for float32 ones."""
     torch = _torch()
     h, w, pitch = _image(img)
-    code = _int_image_code(img)
+    code = _dtype_code(img)
     if out is None:
-        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+        out = torch.empty((h, w), dtype=_acc_dtype(code), device=img.device)
     _check(lib().fhtdp_gauss_rows(img.data_ptr(), code, h, w, pitch, int(r), out.data_ptr(),
                                   _stream(stream)))
     return out
 
 
 def polyline_dp_angle(hough, h: int, w: int, k: int, gamma: float, stream=None):
-    """The DP with bend-angle windows in place over int32 Hough images."""
-    _check(lib().fhtdp_polyline_dp_angle(hough.data_ptr(), DTYPE_I32, h, w, k, float(gamma),
+    """The DP with bend-angle windows in place over int32 or float32 Hough
+    images."""
+    code = DTYPE_F32 if hough.dtype == _torch().float32 else DTYPE_I32
+    _check(lib().fhtdp_polyline_dp_angle(hough.data_ptr(), code, h, w, k, float(gamma),
                                          _stream(stream)))
     return hough
 
 
 def backtrack_angle(V, h: int, w: int, k: int, gamma: float, out=None, stream=None):
     """(x[k+1], d[k], score[1]) read back with the bend-angle windows."""
-    x, d, score = out if out is not None else _outputs(k, DTYPE_I32, V.device)
-    _check(lib().fhtdp_backtrack_angle(V.data_ptr(), DTYPE_I32, h, w, k, float(gamma),
+    code = DTYPE_F32 if V.dtype == _torch().float32 else DTYPE_I32
+    x, d, score = out if out is not None else _outputs(k, code, V.device)
+    _check(lib().fhtdp_backtrack_angle(V.data_ptr(), code, h, w, k, float(gamma),
                                        x.data_ptr(), d.data_ptr(), score.data_ptr(),
                                        _stream(stream)))
     return x, d, score
@@ -477,11 +474,11 @@ def angle_workspace_bytes(dtype: int, h: int, w: int, k: int, r: int) -> int:
 
 
 def detect_polyline_angle(img, k: int, r: int, gamma: float, out=None, ws=None, stream=None):
-    """Steps 1-3 of the main problem on one device image (uint8 or int32):
-    (x[k+1], d[k], score[1]), the score of the smoothed image."""
+    """Steps 1-3 of the main problem on one device image (uint8, int32 or
+    float32): (x[k+1], d[k], score[1]), the score of the smoothed image."""
     torch = _torch()
     h, w, pitch = _image(img)
-    code = _int_image_code(img)
+    code = _dtype_code(img)
     need = angle_workspace_bytes(code, h, w, k, r)
     if need == 0:   # invalid arguments: let the library name the problem
         _check(lib().fhtdp_detect_polyline_angle(None, code, h, w, pitch, k, int(r),
@@ -509,7 +506,7 @@ def detect_through_point(img, k: int, B: int, j: int, xp: int, out=None, ws=None
     int32 image): (x[k+1], d[k], score[1]) with x[j] = xp."""
     torch = _torch()
     h, w, pitch = _image(img)
-    code = _int_image_code(img)
+    code = _dtype_code(img)
     need = through_workspace_bytes(code, h, w, k)
     if need == 0:   # invalid arguments: let the library name the problem
         _check(lib().fhtdp_detect_through_point(None, code, h, w, pitch, k, B, j, xp, None, None,
@@ -529,10 +526,11 @@ def detect_through_point(img, k: int, B: int, j: int, xp: int, out=None, ws=None
 
 def detect_two_polylines(img, k: int, B: int, sep: int, out=None, ws=None, stream=None):
     """The optimum and the best polyline whose top vertex is at least `sep`
-    columns from it (uint8 or int32 image): x [2, k+1], d [2, k], score [2]."""
+    columns from it (uint8, int32 or float32 image): x [2, k+1], d [2, k],
+    score [2]."""
     torch = _torch()
     h, w, pitch = _image(img)
-    code = _int_image_code(img)
+    code = _dtype_code(img)
     need = lib().fhtdp_two_workspace_bytes(code, h, w, k)
     if need == 0:   # invalid arguments: let the library name the problem
         _check(lib().fhtdp_detect_two_polylines(None, code, h, w, pitch, k, B, sep, None, None,
@@ -542,7 +540,7 @@ def detect_two_polylines(img, k: int, B: int, sep: int, out=None, ws=None, strea
     if out is None:
         out = (torch.empty((2, k + 1), dtype=torch.int32, device=img.device),
                torch.empty((2, k), dtype=torch.int32, device=img.device),
-               torch.empty(2, dtype=torch.int32, device=img.device))
+               torch.empty(2, dtype=_acc_dtype(code), device=img.device))
     x, d, score = out
     _check(lib().fhtdp_detect_two_polylines(img.data_ptr(), code, h, w, pitch, k, B, int(sep),
                                             x.data_ptr(), d.data_ptr(), score.data_ptr(),
@@ -589,10 +587,10 @@ def transpose(img, out=None, stream=None):
 
 def detect_polyline_padded(img, k: int, B: int, out=None, ws=None, stream=None):
     """The method with vertices anywhere in [0, w + h/k) (zeros right of the
-    image), uint8 or int32 image: (x[k+1], d[k], score[1])."""
+    image), uint8, int32 or float32 image: (x[k+1], d[k], score[1])."""
     torch = _torch()
     h, w, pitch = _image(img)
-    code = _int_image_code(img)
+    code = _dtype_code(img)
     need = through_workspace_bytes(code, h, w, k)
     if need == 0:   # invalid arguments: let the library name the problem
         _check(lib().fhtdp_detect_polyline_padded(None, code, h, w, pitch, k, B, None, None,
@@ -609,10 +607,10 @@ def detect_polyline_padded(img, k: int, B: int, out=None, ws=None, stream=None):
 def detect_through_point_angle(img, k: int, r: int, gamma: float, j: int, xp: int, out=None,
                                ws=None, stream=None):
     """Subproblem 3: the best polyline through (xp, j * h/k) with bend angles
-    at most gamma, rows smoothed with half-width r (uint8 or int32 image)."""
+    at most gamma, rows smoothed with half-width r (uint8, int32 or float32 image)."""
     torch = _torch()
     h, w, pitch = _image(img)
-    code = _int_image_code(img)
+    code = _dtype_code(img)
     need = angle_workspace_bytes(code, h, w, k, r)
     if need == 0:   # invalid arguments: let the library name the problem
         _check(lib().fhtdp_detect_through_point_angle(None, code, h, w, pitch, k, int(r),

@@ -43,47 +43,54 @@ size_t round_up(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t smooth_bytes(const Shape &s) { return s.n == 1 ? round_up((size_t)s.h * s.w * 4) : 0; }
 }  // namespace
 
-// [head][smoothed image h*w int32, n = 1 only][Hough/V k*2n*W int32][FHT scratch, same]
+// [head][smoothed image h*w, n = 1 only][Hough/V k*2n*W][FHT scratch, same]
+// (4-byte values: int32 for integer images, float for float ones)
 size_t angle_workspace_bytes(const Shape &s) {
     const size_t hough = (size_t)s.k * 2 * s.n * s.W * 4;
     return kAngleHead + smooth_bytes(s) + 2 * round_up(hough);
 }
 
-// pm (optional): Subproblem 3, the polyline must pass the point (the DP
-// marks P's band off the point dead).
-int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
-                 const WindowTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
-                 void *ws, cudaStream_t stream, const PointMask *pm) {
+namespace {
+// The launches of detect_angle for one value type: Acc = int32_t for integer
+// images (In = uint8_t or int32_t), float for float32 images.
+template <typename In, typename Acc>
+int detect_angle_t(const In *img, int pitch, const Shape &s, int r, const WindowTable &t,
+                   int32_t *x_out, int32_t *d_out, Acc *score_out, void *ws,
+                   cudaStream_t stream, const PointMask *pm) {
     char *base = (char *)ws;
     unsigned long long *key = (unsigned long long *)base;
-    int32_t *smooth = (int32_t *)(base + kAngleHead);
-    int32_t *H = (int32_t *)(base + kAngleHead + smooth_bytes(s));
-    int32_t *tmp = H + round_up((size_t)s.k * 2 * s.n * s.W * 4) / 4;
+    Acc *smooth = (Acc *)(base + kAngleHead);
+    Acc *H = (Acc *)(base + kAngleHead + smooth_bytes(s));
+    Acc *tmp = H + round_up((size_t)s.k * 2 * s.n * s.W * 4) / 4;
     int st = cuda_status(cudaMemsetAsync(base, 0, kAngleHead, stream), "cudaMemsetAsync");
     if (st) return st;
     if (r == 0) {   // no smoothing: the FHT reads the image itself
-        st = dtype == FHTDP_U8
-                 ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp,
-                                                       stream)
-                 : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp,
-                                                       stream);
+        st = launch_fht_stages<In, Acc>(img, pitch, s, H, tmp, stream);
     } else if (s.n >= 2) {   // smoothing fused into the first FHT level
-        st = dtype == FHTDP_U8
-                 ? launch_fht_stages_gauss<uint8_t>((const uint8_t *)img, pitch, s, r, H, tmp,
-                                                    stream)
-                 : launch_fht_stages_gauss<int32_t>((const int32_t *)img, pitch, s, r, H, tmp,
-                                                    stream);
+        st = launch_fht_stages_gauss<In, Acc>(img, pitch, s, r, H, tmp, stream);
     } else {   // one-row bands: smooth into the workspace, then the FHT
-        st = dtype == FHTDP_U8
-                 ? launch_gauss_rows<uint8_t>((const uint8_t *)img, pitch, s.h, s.w, r, smooth,
-                                              stream)
-                 : launch_gauss_rows<int32_t>((const int32_t *)img, pitch, s.h, s.w, r, smooth,
-                                              stream);
-        if (!st) st = launch_fht_stages<int32_t, int32_t>(smooth, s.w, s, H, tmp, stream);
+        st = launch_gauss_rows<In, Acc>(img, pitch, s.h, s.w, r, smooth, stream);
+        if (!st) st = launch_fht_stages<Acc, Acc>(smooth, s.w, s, H, tmp, stream);
     }
-    if (!st) st = launch_dp_window<int32_t>(H, s, t, stream, pm);
-    if (!st) st = launch_backtrack_angle_key(H, s, t, key, x_out, d_out, score_out, stream);
+    if (!st) st = launch_dp_window<Acc>(H, s, t, stream, pm);
+    if (!st) st = launch_backtrack_angle_key<Acc>(H, s, t, key, x_out, d_out, score_out, stream);
     return st;
+}
+}  // namespace
+
+// pm (optional): Subproblem 3, the polyline must pass the point (the DP
+// marks P's band off the point dead).
+int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
+                 const WindowTable &t, int32_t *x_out, int32_t *d_out, void *score_out,
+                 void *ws, cudaStream_t stream, const PointMask *pm) {
+    if (dtype == FHTDP_U8)
+        return detect_angle_t<uint8_t, int32_t>((const uint8_t *)img, pitch, s, r, t, x_out,
+                                                d_out, (int32_t *)score_out, ws, stream, pm);
+    if (dtype == FHTDP_I32)
+        return detect_angle_t<int32_t, int32_t>((const int32_t *)img, pitch, s, r, t, x_out,
+                                                d_out, (int32_t *)score_out, ws, stream, pm);
+    return detect_angle_t<float, float>((const float *)img, pitch, s, r, t, x_out, d_out,
+                                        (float *)score_out, ws, stream, pm);
 }
 
 }  // namespace fhtdp

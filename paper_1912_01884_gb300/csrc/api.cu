@@ -174,8 +174,7 @@ int fhtdp_detect_polyline(const void *img, int dtype, int h, int w, int pitch, i
 // The main problem (Sec. 2.3): smoothing and bend-angle windows.
 namespace {
 int check_angle_common(int dtype, int h, int w, int k, double gamma, Shape *s) {
-    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
-        return set_error(FHTDP_EINVAL, "the angle path takes integer images (dtype %d)", dtype);
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
     if (!make_shape(h, w, k, s)) return bad_shape(h, w, k);
     if (!(gamma >= 0.0) || !std::isfinite(gamma))
         return set_error(FHTDP_EINVAL, "bend angle gamma must be finite and >= 0");
@@ -204,11 +203,10 @@ int fhtdp_angle_window(int n, double gamma, int32_t *lohi) {
     return FHTDP_OK;
 }
 
-int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r, int32_t *out,
+int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r, void *out,
                      cudaStream_t stream) {
     g_last_error[0] = 0;
-    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
-        return set_error(FHTDP_EINVAL, "smoothing takes integer images (dtype %d)", dtype);
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
     if (h < 1 || w < 1 || h > (1 << 20) || w > (1 << 20))
         return set_error(FHTDP_EINVAL, "invalid image %d x %d", h, w);
     if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
@@ -216,8 +214,13 @@ int fhtdp_gauss_rows(const void *img, int dtype, int h, int w, int pitch, int r,
     int st = check_gauss(dtype, h, r);
     if (st) return st;
     if (dtype == FHTDP_U8)
-        return launch_gauss_rows<uint8_t>((const uint8_t *)img, pitch, h, w, r, out, stream);
-    return launch_gauss_rows<int32_t>((const int32_t *)img, pitch, h, w, r, out, stream);
+        return launch_gauss_rows<uint8_t, int32_t>((const uint8_t *)img, pitch, h, w, r,
+                                                   (int32_t *)out, stream);
+    if (dtype == FHTDP_I32)
+        return launch_gauss_rows<int32_t, int32_t>((const int32_t *)img, pitch, h, w, r,
+                                                   (int32_t *)out, stream);
+    return launch_gauss_rows<float, float>((const float *)img, pitch, h, w, r, (float *)out,
+                                           stream);
 }
 
 int fhtdp_polyline_dp_angle(void *hough, int dtype, int h, int w, int k, double gamma,
@@ -229,6 +232,7 @@ int fhtdp_polyline_dp_angle(void *hough, int dtype, int h, int w, int k, double 
     if (!hough) return set_error(FHTDP_EINVAL, "null hough pointer");
     WindowTable t;
     make_angle_table(s.n, gamma, &t);
+    if (dtype == FHTDP_F32) return launch_dp_window<float>((float *)hough, s, t, stream);
     return launch_dp_window<int32_t>((int32_t *)hough, s, t, stream);
 }
 
@@ -242,15 +246,16 @@ int fhtdp_backtrack_angle(const void *V, int dtype, int h, int w, int k, double 
         return set_error(FHTDP_EINVAL, "null V or output pointer");
     WindowTable t;
     make_angle_table(s.n, gamma, &t);
-    return launch_backtrack_angle((const int32_t *)V, s, t, x_out, d_out, (int32_t *)score_out,
-                                  stream);
+    if (dtype == FHTDP_F32)
+        return launch_backtrack_angle<float>((const float *)V, s, t, x_out, d_out,
+                                             (float *)score_out, stream);
+    return launch_backtrack_angle<int32_t>((const int32_t *)V, s, t, x_out, d_out,
+                                           (int32_t *)score_out, stream);
 }
 
 size_t fhtdp_angle_workspace_bytes(int dtype, int h, int w, int k, int r) {
     Shape s;
-    if ((dtype != FHTDP_U8 && dtype != FHTDP_I32) || !make_shape(h, w, k, &s) || r < 0 ||
-        r > kMaxGaussR)
-        return 0;
+    if (!valid_dtype(dtype) || !make_shape(h, w, k, &s) || r < 0 || r > kMaxGaussR) return 0;
     return angle_workspace_bytes(s);
 }
 
@@ -272,8 +277,7 @@ int fhtdp_detect_polyline_angle(const void *img, int dtype, int h, int w, int pi
                          ws ? ws_bytes : (size_t)0);
     WindowTable t;
     make_angle_table(s.n, gamma, &t);
-    return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, (int32_t *)score_out, ws,
-                        stream);
+    return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, score_out, ws, stream);
 }
 
 int fhtdp_detect_through_point_angle(const void *img, int dtype, int h, int w, int pitch, int k,
@@ -299,15 +303,14 @@ int fhtdp_detect_through_point_angle(const void *img, int dtype, int h, int w, i
     WindowTable t;
     make_angle_table(s.n, gamma, &t);
     const PointMask pm{j, xp};
-    return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, (int32_t *)score_out, ws,
-                        stream, &pm);
+    return detect_angle(img, dtype, pitch, s, r, t, x_out, d_out, score_out, ws, stream, &pm);
 }
 
 // ---------------------------------------------------------------------------
 // Subproblems 2-3: the extreme polyline through a given point.
 size_t fhtdp_through_workspace_bytes(int dtype, int h, int w, int k) {
     Shape s;
-    if ((dtype != FHTDP_U8 && dtype != FHTDP_I32) || !make_shape(h, w, k, &s)) return 0;
+    if (!valid_dtype(dtype) || !make_shape(h, w, k, &s)) return 0;
     return through_workspace_bytes(s);
 }
 
@@ -316,9 +319,7 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
                                void *ws, size_t ws_bytes, cudaStream_t stream) {
     g_last_error[0] = 0;
     Shape s;
-    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
-        return set_error(FHTDP_EINVAL, "the through-point query takes integer images (dtype %d)",
-                         dtype);
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
     if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
     if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
     if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
@@ -332,8 +333,7 @@ int fhtdp_detect_through_point(const void *img, int dtype, int h, int w, int pit
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
     const PointMask pm{j, xp};
-    return detect_through(img, dtype, pitch, s, B, pm, x_out, d_out, (int32_t *)score_out, ws,
-                          stream);
+    return detect_through(img, dtype, pitch, s, B, pm, x_out, d_out, score_out, ws, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,9 +343,7 @@ int fhtdp_detect_polyline_padded(const void *img, int dtype, int h, int w, int p
                                  void *ws, size_t ws_bytes, cudaStream_t stream) {
     g_last_error[0] = 0;
     Shape s;
-    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
-        return set_error(FHTDP_EINVAL, "the padded-vertex call takes integer images (dtype %d)",
-                         dtype);
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
     if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
     if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
     if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
@@ -356,7 +354,7 @@ int fhtdp_detect_polyline_padded(const void *img, int dtype, int h, int w, int p
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
     s.vw = s.W;
-    return detect_padded(img, dtype, pitch, s, B, x_out, d_out, (int32_t *)score_out, ws, stream);
+    return detect_padded(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -370,9 +368,7 @@ int fhtdp_detect_two_polylines(const void *img, int dtype, int h, int w, int pit
                                void *ws, size_t ws_bytes, cudaStream_t stream) {
     g_last_error[0] = 0;
     Shape s;
-    if (dtype != FHTDP_U8 && dtype != FHTDP_I32)
-        return set_error(FHTDP_EINVAL, "the two-polyline query takes integer images (dtype %d)",
-                         dtype);
+    if (!valid_dtype(dtype)) return set_error(FHTDP_EINVAL, "unknown dtype %d", dtype);
     if (!make_shape(h, w, k, &s)) return bad_shape(h, w, k);
     if (pitch < w) return set_error(FHTDP_EINVAL, "pitch %d < w %d", pitch, w);
     if (B < 0) return set_error(FHTDP_EINVAL, "bend limit B=%d < 0", B);
@@ -383,8 +379,7 @@ int fhtdp_detect_two_polylines(const void *img, int dtype, int h, int w, int pit
     if (!ws || ws_bytes < need)
         return set_error(FHTDP_EWORKSPACE, "workspace needs %zu bytes, got %zu", need,
                          ws ? ws_bytes : (size_t)0);
-    return detect_two(img, dtype, pitch, s, B, sep, x_out, d_out, (int32_t *)score_out, ws,
-                      stream);
+    return detect_two(img, dtype, pitch, s, B, sep, x_out, d_out, score_out, ws, stream);
 }
 
 // ---------------------------------------------------------------------------

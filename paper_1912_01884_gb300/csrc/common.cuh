@@ -81,54 +81,57 @@ template <typename Acc>
 int launch_backtrack(const Acc *V, const Shape &s, int B, int32_t *x_out, int32_t *d_out,
                      Acc *score_out, cudaStream_t stream);
 
-// The main problem (Sec. 2.3): row smoothing of an integer image into a dense
-// int32 [h][w] image, the DP with bend-angle windows, and its read-backs.
-template <typename In>
-int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *out,
+// The main problem (Sec. 2.3): row smoothing into a dense [h][w] image
+// (int32 for integer images, float for float ones), the DP with bend-angle
+// windows, and its read-backs.
+template <typename In, typename Acc>
+int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, Acc *out,
                       cudaStream_t stream);
 // The band FHTs of the smoothed image without storing it: the smoothing is
 // fused into the first level (bands of n >= 2 rows).
-template <typename In>
-int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, int32_t *hough,
-                            int32_t *tmp, cudaStream_t stream);
+template <typename In, typename Acc>
+int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, Acc *hough, Acc *tmp,
+                            cudaStream_t stream);
 // The DP over any window table (int32 or float values), in place, with an
 // optional through-point restriction.
 template <typename Acc>
 int launch_dp_window(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t stream,
                      const PointMask *pm = nullptr);
-int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const WindowTable &t,
+template <typename Acc>
+int launch_backtrack_angle_key(const Acc *V, const Shape &s, const WindowTable &t,
                                unsigned long long *key, int32_t *x_out, int32_t *d_out,
-                               int32_t *score_out, cudaStream_t stream);
-int launch_backtrack_angle(const int32_t *V, const Shape &s, const WindowTable &t,
-                           int32_t *x_out, int32_t *d_out, int32_t *score_out,
-                           cudaStream_t stream);
+                               Acc *score_out, cudaStream_t stream);
+template <typename Acc>
+int launch_backtrack_angle(const Acc *V, const Shape &s, const WindowTable &t, int32_t *x_out,
+                           int32_t *d_out, Acc *score_out, cudaStream_t stream);
 size_t angle_workspace_bytes(const Shape &s);
 size_t through_workspace_bytes(const Shape &s);
 // The method with vertices anywhere in [0, W) (s.vw = W): the standalone
 // FHT, DP and key read-back.
 int detect_padded(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
-                  int32_t *d_out, int32_t *score_out, void *ws, cudaStream_t stream);
+                  int32_t *d_out, void *score_out, void *ws, cudaStream_t stream);
 // Two different extreme polylines: the optimum and the best one whose top
 // vertex is at least sep columns from the optimum's (outputs [2][...]).
 int detect_two(const void *img, int dtype, int pitch, const Shape &s, int B, int sep,
-               int32_t *x_out, int32_t *d_out, int32_t *score_out, void *ws,
-               cudaStream_t stream);
+               int32_t *x_out, int32_t *d_out, void *score_out, void *ws, cudaStream_t stream);
 // The argmax of V_0 over the columns at least sep from the top vertex that
 // key1 encodes (nothing when key1 is 0), into *key2 (zero before the call).
-int launch_argmax_apart(const int32_t *V, const Shape &s, const unsigned long long *key1,
-                        int sep, unsigned long long *key2, cudaStream_t stream);
+template <typename Acc>
+int launch_argmax_apart(const Acc *V, const Shape &s, const unsigned long long *key1, int sep,
+                        unsigned long long *key2, cudaStream_t stream);
 // The read-back from an argmax key with the integer bend limit.
-int launch_readback_key(const int32_t *V, const Shape &s, int B, const unsigned long long *key,
-                        int32_t *x_out, int32_t *d_out, int32_t *score_out, cudaStream_t stream);
+template <typename Acc>
+int launch_readback_key(const Acc *V, const Shape &s, int B, const unsigned long long *key,
+                        int32_t *x_out, int32_t *d_out, Acc *score_out, cudaStream_t stream);
 // dst[x][y] = src[y][x] (Sec. 3, Fig. 7: mostly horizontal curves).
 template <typename T>
 int launch_transpose(const T *src, int h, int w, int pitch, T *dst, int dpitch,
                      cudaStream_t stream);
 int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
-                   const PointMask &pm, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                   const PointMask &pm, int32_t *x_out, int32_t *d_out, void *score_out,
                    void *ws, cudaStream_t stream);
 int detect_angle(const void *img, int dtype, int pitch, const Shape &s, int r,
-                 const WindowTable &t, int32_t *x_out, int32_t *d_out, int32_t *score_out,
+                 const WindowTable &t, int32_t *x_out, int32_t *d_out, void *score_out,
                  void *ws, cudaStream_t stream, const PointMask *pm = nullptr);
 
 }  // namespace fhtdp

@@ -213,7 +213,8 @@ __global__ void argmax_kernel(const Acc *V, Shape s, unsigned long long *key) {
 
 // The second of two different extreme polylines: as argmax_kernel over the
 // columns x with |x - x_0| >= sep, x_0 the top vertex of the optimum in key1.
-__global__ void argmax_apart_kernel(const int32_t *V, Shape s, const unsigned long long *key1,
+template <typename Acc>
+__global__ void argmax_apart_kernel(const Acc *V, Shape s, const unsigned long long *key1,
                                     int sep, unsigned long long *key2) {
     const unsigned long long k1 = *key1;
     if (k1 == 0) return;
@@ -223,8 +224,8 @@ __global__ void argmax_apart_kernel(const int32_t *V, Shape s, const unsigned lo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int e = i / s.vw, x = i - e * s.vw;
         if (abs(x - x0) < sep) continue;
-        const int32_t v = V[cell<int32_t>(s, 0, x, e - (s.n - 1))];
-        if (v == Dead<int32_t>::value()) continue;
+        const Acc v = V[cell<Acc>(s, 0, x, e - (s.n - 1))];
+        if (v == Dead<Acc>::value()) continue;
         const unsigned long long k = ((unsigned long long)vord(v) << 32) |
                                      (0xffffffffu - (unsigned)(x * s.D + e));
         best = best > k ? best : k;
@@ -448,37 +449,57 @@ int launch_dp_window(Acc *hv, const Shape &s, const WindowTable &t, cudaStream_t
     return launch_dp_window_tiles<Acc, 8, 16>(hv, s, t, stream, mask);   // 256-row bands
 }
 
-int launch_argmax_apart(const int32_t *V, const Shape &s, const unsigned long long *key1,
-                        int sep, unsigned long long *key2, cudaStream_t stream) {
-    argmax_apart_kernel<<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key1, sep, key2);
+template <typename Acc>
+int launch_argmax_apart(const Acc *V, const Shape &s, const unsigned long long *key1, int sep,
+                        unsigned long long *key2, cudaStream_t stream) {
+    argmax_apart_kernel<Acc><<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key1, sep,
+                                                                                key2);
     return launched("argmax_apart_kernel");
 }
 
-int launch_readback_key(const int32_t *V, const Shape &s, int B, const unsigned long long *key,
-                        int32_t *x_out, int32_t *d_out, int32_t *score_out, cudaStream_t stream) {
-    readback_kernel<int32_t, BendWin><<<1, 32, 0, stream>>>(V, s, BendWin{B, s.n}, key, x_out,
-                                                             d_out, score_out);
+template <typename Acc>
+int launch_readback_key(const Acc *V, const Shape &s, int B, const unsigned long long *key,
+                        int32_t *x_out, int32_t *d_out, Acc *score_out, cudaStream_t stream) {
+    readback_kernel<Acc, BendWin><<<1, 32, 0, stream>>>(V, s, BendWin{B, s.n}, key, x_out, d_out,
+                                                         score_out);
     return launched("readback_kernel");
 }
 
-int launch_backtrack_angle_key(const int32_t *V, const Shape &s, const WindowTable &t,
+template <typename Acc>
+int launch_backtrack_angle_key(const Acc *V, const Shape &s, const WindowTable &t,
                                unsigned long long *key, int32_t *x_out, int32_t *d_out,
-                               int32_t *score_out, cudaStream_t stream) {
-    argmax_kernel<int32_t><<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key);
+                               Acc *score_out, cudaStream_t stream) {
+    argmax_kernel<Acc><<<grid_for((size_t)s.vw * s.D), 256, 0, stream>>>(V, s, key);
     int st = launched("argmax_kernel");
     if (st) return st;
-    readback_kernel<int32_t, TableWin><<<1, 32, 0, stream>>>(V, s, TableWin{t}, key, x_out,
-                                                             d_out, score_out);
+    readback_kernel<Acc, TableWin><<<1, 32, 0, stream>>>(V, s, TableWin{t}, key, x_out, d_out,
+                                                         score_out);
     return launched("readback_kernel");
 }
 
-int launch_backtrack_angle(const int32_t *V, const Shape &s, const WindowTable &t,
-                           int32_t *x_out, int32_t *d_out, int32_t *score_out,
-                           cudaStream_t stream) {
-    backtrack_kernel<int32_t, TableWin><<<1, 1024, 0, stream>>>(V, s, TableWin{t}, x_out,
-                                                                d_out, score_out);
+template <typename Acc>
+int launch_backtrack_angle(const Acc *V, const Shape &s, const WindowTable &t, int32_t *x_out,
+                           int32_t *d_out, Acc *score_out, cudaStream_t stream) {
+    backtrack_kernel<Acc, TableWin><<<1, 1024, 0, stream>>>(V, s, TableWin{t}, x_out, d_out,
+                                                            score_out);
     return launched("backtrack_kernel");
 }
+
+#define FHTDP_INSTANTIATE_QUERIES(Acc)                                                          \
+    template int launch_argmax_apart<Acc>(const Acc *, const Shape &,                           \
+                                          const unsigned long long *, int,                      \
+                                          unsigned long long *, cudaStream_t);                  \
+    template int launch_readback_key<Acc>(const Acc *, const Shape &, int,                      \
+                                          const unsigned long long *, int32_t *, int32_t *,     \
+                                          Acc *, cudaStream_t);                                 \
+    template int launch_backtrack_angle_key<Acc>(const Acc *, const Shape &,                    \
+                                                 const WindowTable &, unsigned long long *,     \
+                                                 int32_t *, int32_t *, Acc *, cudaStream_t);    \
+    template int launch_backtrack_angle<Acc>(const Acc *, const Shape &, const WindowTable &,   \
+                                             int32_t *, int32_t *, Acc *, cudaStream_t);
+FHTDP_INSTANTIATE_QUERIES(int32_t)
+FHTDP_INSTANTIATE_QUERIES(float)
+#undef FHTDP_INSTANTIATE_QUERIES
 
 template int launch_dp_window<int32_t>(int32_t *, const Shape &, const WindowTable &,
                                        cudaStream_t, const PointMask *);

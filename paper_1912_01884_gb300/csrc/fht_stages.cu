@@ -125,15 +125,18 @@ GaussWeights binomial_weights(int r) {
 }
 
 // Pixel c of an image row after the row smoothing (zero in the padding
-// columns c >= w and outside the row).
-template <typename In>
-__device__ __forceinline__ int32_t smoothed(const In *row, int w, int r, const GaussWeights &g,
-                                            int c) {
-    if (c >= w) return 0;
-    int32_t acc = 0;
+// columns c >= w and outside the row).  Acc = int32_t: exact integer sums;
+// Acc = float: each product weight * pixel rounded, then added in the order
+// t = -r .. r to an accumulator starting at 0 (the float32 reading of the
+// smoothing step).
+template <typename In, typename Acc>
+__device__ __forceinline__ Acc smoothed(const In *row, int w, int r, const GaussWeights &g,
+                                        int c) {
+    if (c >= w) return Acc(0);
+    Acc acc = 0;
     for (int t = -r; t <= r; ++t) {
         const int cc = c + t;
-        if (cc >= 0 && cc < w) acc += g.c[t + r] * (int32_t)row[cc];
+        if (cc >= 0 && cc < w) acc += (Acc)g.c[t + r] * (Acc)row[cc];
     }
     return acc;
 }
@@ -147,11 +150,11 @@ constexpr int kL2Chunk = 1024;   // columns per block of the smoothing level-2 p
 // and the bottom row B at x-1..x+chunk (columns mod W; a column that wraps
 // around is smoothed from global memory), and writes the four level-2 rows
 // of the pair: shifts 0 and 1 of both signs, A(x) + B(x) and A(x) + B(x +/- 1).
-template <typename In>
+template <typename In, typename Acc>
 __global__ void fht_level2_gauss_kernel(const In *img, int pitch, Shape s, int r,
-                                        GaussWeights g, int32_t *out) {
+                                        GaussWeights g, Acc *out) {
     constexpr int kRaw = kL2Chunk + 2 + 2 * kMaxGaussR;
-    __shared__ int32_t rawa[kRaw], rawb[kRaw], sa[kL2Chunk], sb[kL2Chunk + 2];
+    __shared__ Acc rawa[kRaw], rawb[kRaw], sa[kL2Chunk], sb[kL2Chunk + 2];
     const int half = s.n >> 1;
     const int pair = blockIdx.x;
     const int band = pair / half, j = pair - band * half;
@@ -163,33 +166,35 @@ __global__ void fht_level2_gauss_kernel(const In *img, int pitch, Shape s, int r
     for (int i = threadIdx.x; i < cols + 2 + 2 * r; i += blockDim.x) {
         const int c = base + i;
         const bool in = c >= 0 && c < s.w;
-        rawa[i] = in ? (int32_t)ra[c] : 0;
-        rawb[i] = in ? (int32_t)rb[c] : 0;
+        rawa[i] = in ? (Acc)ra[c] : Acc(0);
+        rawb[i] = in ? (Acc)rb[c] : Acc(0);
     }
     __syncthreads();
+    // Pixels outside the row add a zero product, which leaves an integer or
+    // float sum unchanged (a float sum that starts at +0 never holds -0).
     for (int i = threadIdx.x; i < cols + 2; i += blockDim.x) {
         const int c = x0 - 1 + i, cw = wrap(c, s.W);
-        int32_t vb = 0;
+        Acc vb = 0;
         if (cw != c) {
-            vb = smoothed(rb, s.w, r, g, cw);
+            vb = smoothed<In, Acc>(rb, s.w, r, g, cw);
         } else if (c < s.w) {
-            for (int t = 0; t <= 2 * r; ++t) vb += g.c[t] * rawb[i + t];
+            for (int t = 0; t <= 2 * r; ++t) vb += (Acc)g.c[t] * rawb[i + t];
         }
         sb[i] = vb;
         if (i < cols && c + 1 < s.w) {
-            int32_t va = 0;
-            for (int t = 0; t <= 2 * r; ++t) va += g.c[t] * rawa[i + 1 + t];
+            Acc va = 0;
+            for (int t = 0; t <= 2 * r; ++t) va += (Acc)g.c[t] * rawa[i + 1 + t];
             sa[i] = va;
         } else if (i < cols) {
             sa[i] = 0;
         }
     }
     __syncthreads();
-    int32_t *plus = out + ((size_t)(band * 2) * s.n + 2 * j) * s.W;
-    int32_t *minus = out + ((size_t)(band * 2 + 1) * s.n + 2 * j) * s.W;
+    Acc *plus = out + ((size_t)(band * 2) * s.n + 2 * j) * s.W;
+    Acc *minus = out + ((size_t)(band * 2 + 1) * s.n + 2 * j) * s.W;
     for (int i = threadIdx.x; i < cols; i += blockDim.x) {
         const int x = x0 + i;
-        const int32_t A = sa[i], B = sb[i + 1];
+        const Acc A = sa[i], B = sb[i + 1];
         plus[x] = A + B;
         plus[s.W + x] = A + sb[i + 2];
         minus[x] = A + B;
@@ -207,45 +212,48 @@ constexpr int kGaussSeg = 1024;   // output columns per block (4 per thread)
 
 // Main problem, step 1 (Sec. 2.3): every row convolved with the discrete
 // Gaussian of half-width r, the unnormalised binomial weights (integer
-// arithmetic, so the sums are exact); pixels outside the row count as zero.
-// A block stages one row segment and its 2r-pixel halo in shared memory as
-// int32 and writes kGaussSeg outputs of the dense [h][w] result.
-template <typename In>
+// arithmetic for integer images, so the sums are exact; float images in the
+// float order of `smoothed`); pixels outside the row count as zero.  A block
+// stages one row segment and its 2r-pixel halo in shared memory and writes
+// kGaussSeg outputs of the dense [h][w] result.
+template <typename In, typename Acc>
 __global__ void gauss_rows_kernel(const In *__restrict__ img, int pitch, int w, int r,
-                                  GaussWeights g, int32_t *__restrict__ out) {
-    __shared__ int32_t seg[kGaussSeg + 2 * kMaxGaussR];
+                                  GaussWeights g, Acc *__restrict__ out) {
+    __shared__ Acc seg[kGaussSeg + 2 * kMaxGaussR];
     const int y = blockIdx.x;
     const int x0 = blockIdx.y * kGaussSeg;
     const In *row = img + (size_t)y * pitch;
     for (int i = threadIdx.x; i < kGaussSeg + 2 * r; i += blockDim.x) {
         const int c = x0 - r + i;
-        seg[i] = (c >= 0 && c < w) ? (int32_t)row[c] : 0;
+        seg[i] = (c >= 0 && c < w) ? (Acc)row[c] : Acc(0);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kGaussSeg; i += blockDim.x) {
         const int x = x0 + i;
         if (x >= w) break;
-        int32_t acc = 0;
-        for (int t = 0; t <= 2 * r; ++t) acc += g.c[t] * seg[i + t];
+        Acc acc = 0;
+        for (int t = 0; t <= 2 * r; ++t) acc += (Acc)g.c[t] * seg[i + t];
         out[(size_t)y * w + x] = acc;
     }
 }
 
 }  // namespace
 
-template <typename In>
-int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, int32_t *out,
+template <typename In, typename Acc>
+int launch_gauss_rows(const In *img, int pitch, int h, int w, int r, Acc *out,
                       cudaStream_t stream) {
     const GaussWeights g = binomial_weights(r);
     dim3 grid((unsigned)h, (unsigned)((w + kGaussSeg - 1) / kGaussSeg));   // rows in x: h <= 2^20
-    gauss_rows_kernel<In><<<grid, 256, 0, stream>>>(img, pitch, w, r, g, out);
+    gauss_rows_kernel<In, Acc><<<grid, 256, 0, stream>>>(img, pitch, w, r, g, out);
     return launched("gauss_rows_kernel");
 }
 
-template int launch_gauss_rows<uint8_t>(const uint8_t *, int, int, int, int, int32_t *,
-                                        cudaStream_t);
-template int launch_gauss_rows<int32_t>(const int32_t *, int, int, int, int, int32_t *,
-                                        cudaStream_t);
+template int launch_gauss_rows<uint8_t, int32_t>(const uint8_t *, int, int, int, int, int32_t *,
+                                                 cudaStream_t);
+template int launch_gauss_rows<int32_t, int32_t>(const int32_t *, int, int, int, int, int32_t *,
+                                                 cudaStream_t);
+template int launch_gauss_rows<float, float>(const float *, int, int, int, int, float *,
+                                             cudaStream_t);
 
 namespace {
 // The passes after level 2 (which the caller wrote into pass_dst(s, 0, ...)):
@@ -294,20 +302,22 @@ int launch_fht_stages(const In *img, int pitch, const Shape &s, Acc *hough, Acc 
     return st ? st : fht_upper_levels<Acc>(s, hough, tmp, stream);
 }
 
-template <typename In>
-int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, int32_t *hough,
-                            int32_t *tmp, cudaStream_t stream) {
+template <typename In, typename Acc>
+int launch_fht_stages_gauss(const In *img, int pitch, const Shape &s, int r, Acc *hough, Acc *tmp,
+                            cudaStream_t stream) {
     dim3 grid((unsigned)(s.k * (s.n / 2)), (unsigned)((s.W + kL2Chunk - 1) / kL2Chunk));
-    fht_level2_gauss_kernel<In><<<grid, 256, 0, stream>>>(img, pitch, s, r, binomial_weights(r),
-                                                          pass_dst(s, 0, hough, tmp));
+    fht_level2_gauss_kernel<In, Acc><<<grid, 256, 0, stream>>>(
+        img, pitch, s, r, binomial_weights(r), pass_dst(s, 0, hough, tmp));
     int st = launched("fht_level2_gauss_kernel");
-    return st ? st : fht_upper_levels<int32_t>(s, hough, tmp, stream);
+    return st ? st : fht_upper_levels<Acc>(s, hough, tmp, stream);
 }
 
-template int launch_fht_stages_gauss<uint8_t>(const uint8_t *, int, const Shape &, int, int32_t *,
-                                              int32_t *, cudaStream_t);
-template int launch_fht_stages_gauss<int32_t>(const int32_t *, int, const Shape &, int, int32_t *,
-                                              int32_t *, cudaStream_t);
+template int launch_fht_stages_gauss<uint8_t, int32_t>(const uint8_t *, int, const Shape &, int,
+                                                       int32_t *, int32_t *, cudaStream_t);
+template int launch_fht_stages_gauss<int32_t, int32_t>(const int32_t *, int, const Shape &, int,
+                                                       int32_t *, int32_t *, cudaStream_t);
+template int launch_fht_stages_gauss<float, float>(const float *, int, const Shape &, int,
+                                                   float *, float *, cudaStream_t);
 template int launch_fht_stages<uint8_t, int32_t>(const uint8_t *, int, const Shape &, int32_t *,
                                                  int32_t *, cudaStream_t);
 template int launch_fht_stages<int32_t, int32_t>(const int32_t *, int, const Shape &, int32_t *,

@@ -9,6 +9,8 @@
 // border is not xp dead, so the optimum over V_0 is the best polyline through
 // P with the bend limit at every vertex, P included, and the usual read-back
 // (Eq. 5) returns it.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace fhtdp {
@@ -19,26 +21,72 @@ constexpr size_t kThroughHead = 256;   // the argmax key, cleared by every call
 size_t round_up256(size_t v) { return (v + 255) & ~(size_t)255; }
 }  // namespace
 
-// [head][Hough/V k*2n*W 4-byte][FHT scratch, same]
+// [head][Hough/V k*2n*W 4-byte values][FHT scratch, same]
 size_t through_workspace_bytes(const Shape &s) {
     return kThroughHead + 2 * round_up256((size_t)s.k * 2 * s.n * s.W * 4);
 }
 
-int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
-                   const PointMask &pm, int32_t *x_out, int32_t *d_out, int32_t *score_out,
-                   void *ws, cudaStream_t stream) {
+namespace {
+// The band FHTs of an image of any dtype into H (int32 for integer images,
+// float for float32 ones).
+template <typename Acc>
+int fht_any(const void *img, int dtype, int pitch, const Shape &s, Acc *H, Acc *tmp,
+            cudaStream_t stream) {
+    if constexpr (std::is_same<Acc, float>::value) {
+        return launch_fht_stages<float, float>((const float *)img, pitch, s, H, tmp, stream);
+    } else {
+        return dtype == FHTDP_U8
+                   ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp,
+                                                         stream)
+                   : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp,
+                                                         stream);
+    }
+}
+
+template <typename Acc>
+int detect_through_t(const void *img, int dtype, int pitch, const Shape &s, int B,
+                     const PointMask *pm, int32_t *x_out, int32_t *d_out, Acc *score_out,
+                     void *ws, cudaStream_t stream) {
     char *base = (char *)ws;
     unsigned long long *key = (unsigned long long *)base;
-    int32_t *H = (int32_t *)(base + kThroughHead);
-    int32_t *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
+    Acc *H = (Acc *)(base + kThroughHead);
+    Acc *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
     int st = cuda_status(cudaMemsetAsync(base, 0, kThroughHead, stream), "cudaMemsetAsync");
     if (st) return st;
-    st = dtype == FHTDP_U8
-             ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream)
-             : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
-    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream, &pm);
-    if (!st) st = launch_backtrack_key<int32_t>(H, s, B, key, x_out, d_out, score_out, stream);
+    st = fht_any<Acc>(img, dtype, pitch, s, H, tmp, stream);
+    if (!st) st = launch_dp_inplace<Acc>(H, s, B, stream, pm);
+    if (!st) st = launch_backtrack_key<Acc>(H, s, B, key, x_out, d_out, score_out, stream);
     return st;
+}
+
+template <typename Acc>
+int detect_two_t(const void *img, int dtype, int pitch, const Shape &s, int B, int sep,
+                 int32_t *x_out, int32_t *d_out, Acc *score_out, void *ws, cudaStream_t stream) {
+    char *base = (char *)ws;
+    unsigned long long *key1 = (unsigned long long *)base, *key2 = key1 + 1;
+    Acc *H = (Acc *)(base + kThroughHead);
+    Acc *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
+    int st = cuda_status(cudaMemsetAsync(base, 0, kThroughHead, stream), "cudaMemsetAsync");
+    if (st) return st;
+    st = fht_any<Acc>(img, dtype, pitch, s, H, tmp, stream);
+    if (!st) st = launch_dp_inplace<Acc>(H, s, B, stream);
+    if (!st) st = launch_backtrack_key<Acc>(H, s, B, key1, x_out, d_out, score_out, stream);
+    if (!st) st = launch_argmax_apart<Acc>(H, s, key1, sep, key2, stream);
+    if (!st)
+        st = launch_readback_key<Acc>(H, s, B, key2, x_out + s.k + 1, d_out + s.k, score_out + 1,
+                                      stream);
+    return st;
+}
+}  // namespace
+
+int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
+                   const PointMask &pm, int32_t *x_out, int32_t *d_out, void *score_out,
+                   void *ws, cudaStream_t stream) {
+    if (dtype == FHTDP_F32)
+        return detect_through_t<float>(img, dtype, pitch, s, B, &pm, x_out, d_out,
+                                       (float *)score_out, ws, stream);
+    return detect_through_t<int32_t>(img, dtype, pitch, s, B, &pm, x_out, d_out,
+                                     (int32_t *)score_out, ws, stream);
 }
 
 // Vertices anywhere in the zero-padded band width (Sec. 2.2: Hough columns
@@ -46,19 +94,12 @@ int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
 // in [0, W), so its values are the plain sums with zeros right of the image;
 // the DP and the read-back run over the vertex domain s.vw = W.
 int detect_padded(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
-                  int32_t *d_out, int32_t *score_out, void *ws, cudaStream_t stream) {
-    char *base = (char *)ws;
-    unsigned long long *key = (unsigned long long *)base;
-    int32_t *H = (int32_t *)(base + kThroughHead);
-    int32_t *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
-    int st = cuda_status(cudaMemsetAsync(base, 0, kThroughHead, stream), "cudaMemsetAsync");
-    if (st) return st;
-    st = dtype == FHTDP_U8
-             ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream)
-             : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
-    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
-    if (!st) st = launch_backtrack_key<int32_t>(H, s, B, key, x_out, d_out, score_out, stream);
-    return st;
+                  int32_t *d_out, void *score_out, void *ws, cudaStream_t stream) {
+    if (dtype == FHTDP_F32)
+        return detect_through_t<float>(img, dtype, pitch, s, B, nullptr, x_out, d_out,
+                                       (float *)score_out, ws, stream);
+    return detect_through_t<int32_t>(img, dtype, pitch, s, B, nullptr, x_out, d_out,
+                                     (int32_t *)score_out, ws, stream);
 }
 
 // Two different extreme polylines (Sec. 3, Figs. 6d and 7a; the paper gives
@@ -66,24 +107,12 @@ int detect_padded(const void *img, int dtype, int pitch, const Shape &s, int B, 
 // least sep columns from the optimum's, both read back from the same V.
 // Workspace as for the through-point query; the second key follows the first.
 int detect_two(const void *img, int dtype, int pitch, const Shape &s, int B, int sep,
-               int32_t *x_out, int32_t *d_out, int32_t *score_out, void *ws,
-               cudaStream_t stream) {
-    char *base = (char *)ws;
-    unsigned long long *key1 = (unsigned long long *)base, *key2 = key1 + 1;
-    int32_t *H = (int32_t *)(base + kThroughHead);
-    int32_t *tmp = H + round_up256((size_t)s.k * 2 * s.n * s.W * 4) / 4;
-    int st = cuda_status(cudaMemsetAsync(base, 0, kThroughHead, stream), "cudaMemsetAsync");
-    if (st) return st;
-    st = dtype == FHTDP_U8
-             ? launch_fht_stages<uint8_t, int32_t>((const uint8_t *)img, pitch, s, H, tmp, stream)
-             : launch_fht_stages<int32_t, int32_t>((const int32_t *)img, pitch, s, H, tmp, stream);
-    if (!st) st = launch_dp_inplace<int32_t>(H, s, B, stream);
-    if (!st) st = launch_backtrack_key<int32_t>(H, s, B, key1, x_out, d_out, score_out, stream);
-    if (!st) st = launch_argmax_apart(H, s, key1, sep, key2, stream);
-    if (!st)
-        st = launch_readback_key(H, s, B, key2, x_out + s.k + 1, d_out + s.k, score_out + 1,
-                                 stream);
-    return st;
+               int32_t *x_out, int32_t *d_out, void *score_out, void *ws, cudaStream_t stream) {
+    if (dtype == FHTDP_F32)
+        return detect_two_t<float>(img, dtype, pitch, s, B, sep, x_out, d_out, (float *)score_out,
+                                   ws, stream);
+    return detect_two_t<int32_t>(img, dtype, pitch, s, B, sep, x_out, d_out,
+                                 (int32_t *)score_out, ws, stream);
 }
 
 }  // namespace fhtdp

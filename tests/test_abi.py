@@ -108,10 +108,11 @@ def test_angle_entries_reject_bad_arguments_before_launch(lib):
     L = lib.lib()
     fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
     assert L.fhtdp_angle_workspace_bytes(0, 64, 10, 4, 2) > 0
-    assert L.fhtdp_angle_workspace_bytes(2, 64, 10, 4, 2) == 0      # float images
+    assert L.fhtdp_angle_workspace_bytes(2, 64, 10, 4, 2) > 0       # float images
+    assert L.fhtdp_angle_workspace_bytes(3, 64, 10, 4, 2) == 0      # unknown dtype
     assert L.fhtdp_angle_workspace_bytes(0, 64, 10, 4, 13) == 0     # r > 12
     args = (fake, fake, fake, fake, 1 << 30, None)
-    assert L.fhtdp_detect_polyline_angle(fake, 2, 64, 10, 10, 4, 2, 0.3, *args) == 1
+    assert L.fhtdp_detect_polyline_angle(fake, 3, 64, 10, 10, 4, 2, 0.3, *args) == 1
     assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, -1, 0.3, *args) == 1
     assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, 2, -0.3, *args) == 1
     assert L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, 2, float("nan"), *args) == 1
@@ -122,7 +123,7 @@ def test_angle_entries_reject_bad_arguments_before_launch(lib):
     r = L.fhtdp_detect_polyline_angle(fake, 0, 64, 10, 10, 4, 2, 0.3, fake, fake, fake, fake,
                                       64, None)
     assert r == 2 and "workspace" in L.fhtdp_last_error().decode()
-    assert L.fhtdp_gauss_rows(fake, 2, 4, 4, 4, 1, fake, None) == 1
+    assert L.fhtdp_gauss_rows(fake, 3, 4, 4, 4, 1, fake, None) == 1
     assert L.fhtdp_gauss_rows(fake, 0, 4, 4, 3, 1, fake, None) == 1
     assert L.fhtdp_gauss_rows(None, 0, 4, 4, 4, 1, fake, None) == 1
     assert L.fhtdp_polyline_dp_angle(None, 0, 64, 10, 4, 0.3, None) == 1
@@ -134,11 +135,12 @@ def test_through_point_rejects_bad_arguments_before_launch(lib):
     L = lib.lib()
     fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
     assert L.fhtdp_through_workspace_bytes(0, 64, 10, 4) > 0
-    assert L.fhtdp_through_workspace_bytes(2, 64, 10, 4) == 0       # float images
+    assert L.fhtdp_through_workspace_bytes(2, 64, 10, 4) > 0        # float images
+    assert L.fhtdp_through_workspace_bytes(3, 64, 10, 4) == 0       # unknown dtype
     outs = (fake, fake, fake, fake, 1 << 30, None)
     for j, xp in ((5, 0), (-1, 0), (1, 10), (1, -1)):
         assert L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, 2, j, xp, *outs) == 1
-    assert L.fhtdp_detect_through_point(fake, 2, 64, 10, 10, 4, 2, 1, 1, *outs) == 1
+    assert L.fhtdp_detect_through_point(fake, 3, 64, 10, 10, 4, 2, 1, 1, *outs) == 1
     assert L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, -1, 1, 1, *outs) == 1
     assert L.fhtdp_detect_through_point(None, 0, 64, 10, 10, 4, 2, 1, 1, *outs) == 1
     r = L.fhtdp_detect_through_point(fake, 0, 64, 10, 10, 4, 2, 1, 1, fake, fake, fake, fake,
@@ -152,7 +154,7 @@ def test_two_and_horizontal_reject_bad_arguments_before_launch(lib):
     outs = (fake, fake, fake, fake, 1 << 30, None)
     assert L.fhtdp_two_workspace_bytes(0, 64, 10, 4) > 0
     assert L.fhtdp_detect_two_polylines(fake, 0, 64, 10, 10, 4, 2, 0, *outs) == 1
-    assert L.fhtdp_detect_two_polylines(fake, 2, 64, 10, 10, 4, 2, 1, *outs) == 1
+    assert L.fhtdp_detect_two_polylines(fake, 3, 64, 10, 10, 4, 2, 1, *outs) == 1
     assert L.fhtdp_detect_two_polylines(fake, 0, 64, 10, 10, 4, -1, 1, *outs) == 1
     r = L.fhtdp_detect_two_polylines(fake, 0, 64, 10, 10, 4, 2, 1, fake, fake, fake, fake, 64,
                                      None)
@@ -183,7 +185,7 @@ def test_padded_rejects_bad_arguments_before_launch(lib):
     L = lib.lib()
     fake = ctypes.c_void_p(16)      # never dereferenced: rejected before launch
     outs = (fake, fake, fake, fake, 1 << 30, None)
-    assert L.fhtdp_detect_polyline_padded(fake, 2, 64, 10, 10, 4, 2, *outs) == 1
+    assert L.fhtdp_detect_polyline_padded(fake, 3, 64, 10, 10, 4, 2, *outs) == 1
     assert L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 10, 3, 2, *outs) == 1
     assert L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 10, 4, -1, *outs) == 1
     assert L.fhtdp_detect_polyline_padded(fake, 0, 64, 10, 9, 4, 2, *outs) == 1
@@ -201,5 +203,5 @@ def test_through_point_angle_rejects_bad_arguments_before_launch(lib):
     assert f(fake, 0, 64, 10, 10, 4, 2, 0.3, 1, 10, *outs) == 1      # xp >= w
     assert f(fake, 0, 64, 10, 10, 4, 2, -0.3, 1, 1, *outs) == 1
     assert f(fake, 0, 64, 10, 10, 4, 13, 0.3, 1, 1, *outs) == 1
-    assert f(fake, 2, 64, 10, 10, 4, 2, 0.3, 1, 1, *outs) == 1
+    assert f(fake, 3, 64, 10, 10, 4, 2, 0.3, 1, 1, *outs) == 1
     assert f(fake, 0, 64, 10, 10, 4, 2, 0.3, 1, 1, fake, fake, fake, fake, 64, None) == 2

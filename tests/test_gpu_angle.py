@@ -174,7 +174,7 @@ def test_detect_angle_rejects_bad_arguments_on_device(lib):
     with pytest.raises(lib.FhtdpError):
         lib.detect_polyline_angle(tall, 16, 10, 0.3)        # 255 * 4^10 * 4096 >= 2^31
     with pytest.raises(TypeError):
-        lib.detect_polyline_angle(img.float(), 4, 2, 0.3)
+        lib.detect_polyline_angle(img.double(), 4, 2, 0.3)
     small = torch.zeros(64, dtype=torch.uint8, device="cuda")
     with pytest.raises(lib.FhtdpError) as e:
         lib.detect_polyline_angle(img, 4, 2, 0.3, ws=small)

@@ -67,4 +67,4 @@ def test_padded_rejects_bad_arguments_on_device(lib):
     with pytest.raises(lib.FhtdpError):
         lib.detect_polyline_padded(img, 4, -1)
     with pytest.raises(TypeError):
-        lib.detect_polyline_padded(img.float(), 4, 2)
+        lib.detect_polyline_padded(img.double(), 4, 2)

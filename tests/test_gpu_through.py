@@ -83,7 +83,7 @@ def test_through_point_rejects_bad_arguments_on_device(lib):
         with pytest.raises(lib.FhtdpError):
             lib.detect_through_point(img, *args)
     with pytest.raises(TypeError):
-        lib.detect_through_point(img.float(), 4, 2, 1, 3)
+        lib.detect_through_point(img.double(), 4, 2, 1, 3)
 
 
 @pytest.mark.parametrize("shape", SHAPES[:8])

@@ -99,7 +99,7 @@ def test_two_and_horizontal_reject_bad_arguments_on_device(lib):
     with pytest.raises(lib.FhtdpError):
         lib.detect_two_polylines(img, 4, -1, 3)
     with pytest.raises(TypeError):
-        lib.detect_two_polylines(img.float(), 4, 2, 3)
+        lib.detect_two_polylines(img.double(), 4, 2, 3)
     with pytest.raises(lib.FhtdpError):
         lib.detect_polyline_horizontal(img, 3, 2)             # 40 columns, k = 3
     with pytest.raises(lib.FhtdpError):
