@@ -86,9 +86,9 @@ EXTRAS = ("plain2048", "float8192")
 # traffic is this times its pixels.  None where no capture of the current
 # kernel exists (reset whenever the kernel changes until it is captured again).
 NCU_TRAFFIC_BYTES_PER_PIXEL = {
-    "mixed": (4.85e9 + 10.78e9) / 1064894464,        # profiles/engine_kernel_u8_mixed256.md
-    "plain2048": (252.65e6 + 1.02e9) / (32 * 2048 * 2048),
-    "float8192": (269.83e6 + 637.90e6) / (8192 * 8192),   # profiles/engine_kernel_wide_float8192.md
+    "mixed": None,        # engine_kernel_u8 changed (control warp) since its capture
+    "plain2048": None,
+    "float8192": None,    # engine_kernel_wide changed (strip prefetch) since its capture
 }
 # DRAM bytes of one dp_band_window_kernel band launch on the 2048x2048, k = 16
 # workloads (profiles/dp_band_window_kernel_angle2048.md).

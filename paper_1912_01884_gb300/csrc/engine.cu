@@ -233,6 +233,12 @@ __device__ __forceinline__ void nb_sync(int id, int count) {
 
 // Bounded wait on a publication flag: gives up after `limit` cycles, or at
 // once when another wait of this launch has already given up.
+// A hint to bring the 128-byte line holding p into L2 (callers pass only
+// lines that hold bytes of their buffers).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ bool wait_flag(const int *flag, const Ctl *ctl, long long limit) {
     long long t0 = clock64();
     while (ld_acquire(flag) == 0) {
@@ -2265,6 +2271,27 @@ struct WideEngine {
     // writes the rows of hw directly; sign 1 ("-") runs on the mirrored strip
     // (word u = pixel x0 + 63 - u), and its rows, bit-reversed in F, are
     // copied out mirrored back.
+    // The strip of an FHT item (columns [x0, x0 + T + n - 1) of the band's
+    // rows, clipped to the image) requested into L2, every 128-byte line at
+    // once, at the item's start: the register levels read the strip task by
+    // task, and their first reads would otherwise wait on DRAM one task
+    // after another.
+    __device__ static void prefetch_strip(const ImgDesc &im, int band, int ft) {
+        const int n = im.n, x0 = ft * kWTileF;
+        const In *base = (const In *)im.img + (size_t)band * n * im.pitch;
+        const int c_lo = x0, c_hi = min(x0 + kWTileF + n - 1, im.w);   // [c_lo, c_hi)
+        if (c_lo >= c_hi) return;
+        const size_t bytes = (size_t)(c_hi - c_lo) * sizeof(In);
+        const int lines = (int)((bytes + 127) / 128) + 1;
+        for (int i = threadIdx.x; i < n * lines; i += NT) {
+            const int y = i / lines, l = i - y * lines;
+            const uintptr_t a = (uintptr_t)(base + (size_t)y * im.pitch + c_lo);
+            const uintptr_t line = (a & ~(uintptr_t)127) + (uintptr_t)l * 128;
+            // only lines that hold a byte of the row's range
+            if (line < a + bytes) prefetch_l2((const void *)line);
+        }
+    }
+
     __device__ static void fht_item(const ImgDesc &im, int band, int ft, unsigned char *smem) {
         const int n = im.n, T = kWTileF, pitch = fpitch(n), x0 = ft * T;
         Acc *F = (Acc *)smem;
@@ -2272,6 +2299,7 @@ struct WideEngine {
         const In *base = (const In *)im.img + (size_t)band * n * im.pitch;
         const bool aligned = ((uintptr_t)im.img % 16 == 0) && (im.pitch % 4 == 0);
         constexpr int kLB = 8;
+        prefetch_strip(im, band, ft);
         for (int sign = 0; sign < 2; ++sign) {
             int first = 1;   // the first level left to merge in shared memory
             if (n >= 8) {
