@@ -202,6 +202,7 @@ template <typename T>
 __device__ __forceinline__ T kmax(T a, T b) {
     return a > b ? a : b;
 }
+__device__ __forceinline__ float kmax(float a, float b) { return fmaxf(a, b); }
 
 __device__ __forceinline__ int brev(int r, int bits) {
     return bits ? (int)(__brev((unsigned)r) >> (32 - bits)) : 0;
@@ -2143,6 +2144,7 @@ struct U8Ctl {
 constexpr int kWThreads = 256;
 constexpr int kWTileF = 64;    // FHT item columns
 constexpr int kWTileD = 16;    // DP item columns
+constexpr int kWPad = 48;      // dead rows above and below V in a DP item
 constexpr int kItemWideFht = 1, kItemWideDp = 3;
 
 template <typename In, typename Acc, typename Key>
@@ -2155,14 +2157,12 @@ struct WideEngine {
         return (size_t)(n < 2 ? 2 : n) * fpitch(n) * 4;
     }
     // Hough rows [2][n][T] (each sign from a 128-byte boundary, as TMA
-    // destinations are) and the M tile [D][T] (4-byte values), then the
-    // window keys [D][T] (8 bytes).
+    // destinations are), then V [kWPad + D + kWPad][T]: the M tile lands in
+    // its D middle rows and V is formed there in place; the pad rows hold
+    // dead values, so that the window reads past [-(n-1), n-1] unchecked.
     __host__ __device__ static int dp_sign1(int n) { return (n * kWTileD + 31) & ~31; }
-    __host__ __device__ static size_t dp_keys_off(int n) {
-        return ((size_t)(2 * dp_sign1(n) + (2 * n - 1) * kWTileD) * 4 + 127) / 128 * 128;
-    }
     __host__ __device__ static size_t dp_smem(int n) {
-        return dp_keys_off(n) + (size_t)(2 * n - 1) * kWTileD * sizeof(Key);
+        return (size_t)(2 * dp_sign1(n) + (2 * n - 1 + 2 * kWPad) * kWTileD) * 4;
     }
     static size_t smem_bytes(int max_n) {
         return std::max(fht_smem(max_n), dp_smem(max_n));
@@ -2365,8 +2365,8 @@ struct WideEngine {
         const bool last = band == im.k - 1;
         Acc *Ht = (Acc *)smem;          // [2][n][T]: Hough rows of both signs
         const int h1 = dp_sign1(n);     // offset of sign 1
-        Acc *Mt = Ht + 2 * h1;          // [D][T]: the M tile
-        Key *Kt = (Key *)(smem + dp_keys_off(n));   // [D][T]: window keys of V
+        Acc *Vt = Ht + 2 * h1;          // [kWPad + D + kWPad][T]: M tile, then V
+        Acc *Mt = Vt + kWPad * T;       // row e + n - 1: displacement e
         const Acc dead = Dead<Acc>::value();
         if (threadIdx.x < 32) {
             // M(x + d, d): band+1 tiles over [x0 - (n-1), x0 + T + n - 2] (lanes
@@ -2395,8 +2395,15 @@ struct WideEngine {
                 mbar_expect_tx(pipe.mbar, (uint32_t)((2 * n + (last ? 0 : D)) * T * 4));
                 tma_load_2d(Ht, &im.tmap, x0, band * 2 * n, pipe.mbar);
                 tma_load_2d(Ht + h1, &im.tmap, x0, (band * 2 + 1) * n, pipe.mbar);
-                if (!last)
-                    tma_load_2d(Mt, &im.mtmap, im.moff + x0, ((band + 1) & 1) * D, pipe.mbar);
+                if (!last) tma_load_2d(Mt, &im.mtmap, im.moff + x0, (band + 1) * D, pipe.mbar);
+            }
+        } else if (band != 0) {
+            // the dead pad rows (outside the copies' destinations)
+            for (int idx = threadIdx.x - 32; idx < 2 * kWPad * (T / 4); idx += NT - 32) {
+                const int r = idx / (T / 4), u0 = 4 * (idx % (T / 4));
+                const int row = r < kWPad ? r : r + D;
+                *(uint4 *)&Vt[row * T + u0] =
+                    make_uint4(to_bits(dead), to_bits(dead), to_bits(dead), to_bits(dead));
             }
         }
         if (!mbar_wait(pipe.mbar, pipe.mphase, args.wait_cycles)) {
@@ -2405,7 +2412,7 @@ struct WideEngine {
         }
         pipe.mphase ^= 1u;
         // V(x, e) = H(x, e) + M(x + e, e), dead outside the image (Eqs. 3-4),
-        // kept as window keys (value and index e + n - 1 in one 64-bit integer).
+        // in place of the M tile.
         unsigned long long best = 0;
         for (int idx = threadIdx.x; idx < D * (T / 4); idx += NT) {
             const int ei = idx / (T / 4), u0 = 4 * (idx % (T / 4));
@@ -2431,11 +2438,8 @@ struct WideEngine {
                         best = best > k ? best : k;
                     }
             } else {
-                Key kk[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) kk[j] = v[j] == dead ? KO::dead() : KO::make(v[j], ei);
-                *(longlong2 *)&Kt[ei * T + u0] = make_longlong2(kk[0], kk[1]);
-                *(longlong2 *)&Kt[ei * T + u0 + 2] = make_longlong2(kk[2], kk[3]);
+                *(uint4 *)&Mt[ei * T + u0] =
+                    make_uint4(to_bits(v[0]), to_bits(v[1]), to_bits(v[2]), to_bits(v[3]));
             }
         }
         if (band == 0) {
@@ -2445,48 +2449,48 @@ struct WideEngine {
             }
             if ((threadIdx.x & 31) == 0 && best) atomicMax(im.best, best);
             csync<NT>();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                if (atomicAdd(im.done, 1) == im.tiles - 1) readback<Acc>(im, args);
+            if (threadIdx.x < 32) {
+                int is_last = 0;
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    is_last = atomicAdd(im.done, 1) == im.tiles - 1;
+                }
+                if (__shfl_sync(0xffffffffu, is_last, 0)) readback_values(im, args);
             }
             return;
         }
         csync<NT>();
-        // Window maxima: 16 threads per column, 16 displacements each.
+        // Window maxima (values only: the read-back recomputes the argmax),
+        // 16 threads per column, 16 displacements each.
         const int u = threadIdx.x & (T - 1), q = threadIdx.x / T;
         const int x = x0 + u;
         const int lo = -(n - 1), hi = n - 1, B = im.B;
         const int c0 = lo + 16 * q;
         if (x < im.w && c0 <= hi) {
-            const Key *col = Kt + (n - 1) * T + u;
-            auto vkey = [&](int e) -> Key { return (e < lo || e > hi) ? KO::dead() : col[e * T]; };
-            Acc *mnext = (Acc *)im.mbuf[band & 1];
-            Acc *mcol = mnext + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
-            uint32_t *bcol = (uint32_t *)im.bp +
-                             ((size_t)band * bp_groups(n) + ((c0 + n - 1) >> 2)) * im.w + x;
+            const Acc *col = Mt + (n - 1) * T + u;   // V(e) at col[e * T]
+            Acc *mcol = mband(im, band) + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
             const int count = min(16, hi - c0 + 1);
-            uint32_t word = 0;
-            auto emit = [&](int i, Key mk) {
-                const bool dk = mk == KO::dead();
-                mcol[(long long)i * (im.mpitch - 1)] = dk ? dead : KO::value(mk);
-                const uint32_t b = dk ? 0u : (uint32_t)KO::index(mk);
-                word = (i & 3) == 0 ? b : word | (b << (8 * (i & 3)));
-                if ((i & 3) == 3 || i == count - 1) bcol[(size_t)(i >> 2) * im.w] = word;
-            };
+            auto emit = [&](int i, Acc m) { mcol[(long long)i * (im.mpitch - 1)] = m; };
             // Runs of NOUT outputs, NOUT the largest power of two up to 16 that
             // the window length L = 2B + 1 covers (one block pair per run).
-            auto runs = [&](auto nout) {
+            auto runs = [&](auto nout, auto vkey) {
                 constexpr int NOUT = decltype(nout)::value;
                 for (int r0 = 0; r0 < count; r0 += NOUT)
-                    window_span<NOUT, Key>(c0 + r0, count - r0, B, KO::dead(), vkey,
-                                           [&](int i, Key mk) { emit(r0 + i, mk); });
+                    window_span<NOUT, Acc>(c0 + r0, count - r0, B, dead, vkey,
+                                           [&](int i, Acc m) { emit(r0 + i, m); });
             };
-            const int L = 2 * B + 1;
-            if (L >= 16) runs(std::integral_constant<int, 16>());
-            else if (L >= 8) runs(std::integral_constant<int, 8>());
-            else if (L >= 4) runs(std::integral_constant<int, 4>());
-            else if (L >= 2) runs(std::integral_constant<int, 2>());
-            else runs(std::integral_constant<int, 1>());
+            auto pick = [&](auto vkey) {
+                const int L = 2 * B + 1;
+                if (L >= 16) runs(std::integral_constant<int, 16>(), vkey);
+                else if (L >= 8) runs(std::integral_constant<int, 8>(), vkey);
+                else if (L >= 4) runs(std::integral_constant<int, 4>(), vkey);
+                else if (L >= 2) runs(std::integral_constant<int, 2>(), vkey);
+                else runs(std::integral_constant<int, 1>(), vkey);
+            };
+            // A run reads V over [c - B, c + B + 16]: inside the pad rows when
+            // B + 16 <= kWPad.
+            if (B + 16 <= kWPad) pick([&](int e) -> Acc { return col[e * T]; });
+            else pick([&](int e) -> Acc { return (e < lo || e > hi) ? dead : col[e * T]; });
         }
         fence_acq_rel_gpu();
         csync<NT>();
@@ -2496,36 +2500,151 @@ struct WideEngine {
                 st_release(im.flags + (size_t)band * im.tiles + tile, 1);
         }
     }
+
+    // The window maxima of band b: [D][mpitch], one array per band (the
+    // read-back recomputes each band's argmax from them and the Hough rows).
+    __device__ static Acc *mband(const ImgDesc &im, int band) {
+        return (Acc *)im.mbuf[0] + (size_t)band * (2 * im.n - 1) * im.mpitch;
+    }
+
+    // Eq. 5 by one warp, from the best top point: at band i the smallest e
+    // with |e - d_{i-1}| <= B maximising V_i(x_i, e) = H_i(x_i, e) +
+    // M_{i+1}(x_i + e, e), recomputed from the stored Hough rows and window
+    // maxima with the same additions as the DP item (lanes over e, then a
+    // warp maximum of (value, smallest e) keys).
+    __device__ static void readback_values(const ImgDesc &im, const LaunchArgs &args) {
+        const int lane = threadIdx.x & 31, n = im.n, D = 2 * n - 1;
+        const Acc dead = Dead<Acc>::value();
+        __threadfence();
+        unsigned long long key = 0;
+        if (lane == 0) key = atomicAdd(im.best, 0ull);
+        key = __shfl_sync(0xffffffffu, key, 0);
+        if (key == 0) {   // no admissible polyline
+            if (lane == 0) {
+                *(Acc *)im.score_out = dead;
+                for (int i = 0; i <= im.k; ++i) im.x_out[i] = -1;
+                for (int i = 0; i < im.k; ++i) im.d_out[i] = 0;
+            }
+            return;
+        }
+        const unsigned lin = 0xffffffffu - (unsigned)(key & 0xffffffffu);
+        int xx = (int)(lin >> 9), d = (int)(lin & 511) - (n - 1);
+        if (lane == 0) {
+            im.x_out[0] = xx;
+            im.d_out[0] = d;
+            *(Acc *)im.score_out = from_ord32<Acc>((uint32_t)(key >> 32));
+        }
+        for (int i = 1; i < im.k; ++i) {
+            xx += d;
+            // Only reachable with inconsistent DP data (a wait gave up): stop
+            // instead of reading outside the arrays.
+            if (xx < 0 || xx >= im.w || d < -(n - 1) || d > n - 1) {
+                if (lane == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                return;
+            }
+            const int lo = max(-(n - 1), d - im.B), hi = min(n - 1, d + im.B);
+            const Acc *mb = i + 1 < im.k ? mband(im, i + 1) : nullptr;
+            unsigned long long bk = 0;
+            for (int e = lo + lane; e <= hi; e += 32) {
+                const int sh = e < 0 ? -e : e;
+                const Acc h = from_bits<Acc>(__ldcg((const uint32_t *)hw_row(im, i, e < 0, sh) + xx));
+                Acc v = h;
+                if (mb) {
+                    if (xx + e < 0 || xx + e >= im.w) {
+                        v = dead;
+                    } else {
+                        // M_{i+1}(xx + e, e): row e + n - 1, skewed column moff + xx
+                        const Acc m = from_bits<Acc>(__ldcg(
+                            (const uint32_t *)mb + (size_t)(e + n - 1) * im.mpitch + im.moff + xx));
+                        v = m == dead ? dead : h + m;
+                    }
+                }
+                if (v != dead) {
+                    const unsigned long long k =
+                        ((unsigned long long)ord32(v) << 32) | (0xffffffffu - (unsigned)(e + n - 1));
+                    bk = bk > k ? bk : k;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
+                bk = bk > other ? bk : other;
+            }
+            if (bk == 0) {   // inconsistent data, as above
+                if (lane == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                return;
+            }
+            d = (int)(0xffffffffu - (unsigned)(bk & 0xffffffffu)) - (n - 1);
+            if (lane == 0) {
+                im.x_out[i] = xx;
+                im.d_out[i] = d;
+            }
+        }
+        if (lane == 0) im.x_out[im.k] = xx + d;
+    }
 };
 
-// The work items of a single int32 / float image, in queue order: the FHT
-// items of band k-1, then per band b from k-1 down to 0 the FHT items of band
-// b-1 (none for b = 0) and the DP items of b.
+// The work items of an int32 / float image, in queue order, by band level:
+// level 0 opens with the FHT items of band k-1; level lv (band b = k-1-lv)
+// holds the DP items of band b and, spread evenly among them, the FHT items
+// of band b - kWAhead (level 0: of bands k-2 .. k-1-kWAhead).  An FHT item
+// takes several DP items' time, so it is queued kWAhead levels before the
+// DP items that read its rows, and spreading them keeps a level's DP items
+// from waiting behind a block of FHT items.  Every item still comes after
+// all the items it waits for.
+constexpr int kWAhead = 2;
+struct WideLevels {
+    int k;
+    long long F, P;   // FHT and DP items of one band
+    __host__ __device__ long long fht_in(int lv) const {   // FHT items spread in level lv
+        if (lv == 0) return (long long)(kWAhead < k - 1 ? kWAhead : k - 1) * F;
+        return k - 1 - lv - kWAhead >= 0 ? F : 0;
+    }
+    // First item of level lv (lv = k: the item count).
+    __host__ __device__ long long start(int lv) const {
+        if (lv == 0) return 0;
+        const long long l0 = F + fht_in(0) + P;
+        int full = lv - 1 < k - 1 - kWAhead ? lv - 1 : k - 1 - kWAhead;   // levels 1.. with F
+        if (full < 0) full = 0;
+        return l0 + (long long)full * (F + P) + (long long)(lv - 1 - full) * P;
+    }
+    // Item `off` of level lv.
+    __host__ __device__ void at(int lv, long long off, int *kind, int *band, int *tile) const {
+        const int b = k - 1 - lv;
+        if (lv == 0) {
+            if (off < F) {
+                *kind = kItemWideFht;
+                *band = k - 1;
+                *tile = (int)off;
+                return;
+            }
+            off -= F;
+        }
+        const long long Fl = fht_in(lv), S = Fl + P;
+        const long long c0 = off * Fl / S, c1 = (off + 1) * Fl / S;
+        if (c1 > c0) {   // the FHT item number c0 of the level
+            *kind = kItemWideFht;
+            *band = lv == 0 ? k - 2 - (int)(c0 / F) : b - kWAhead;
+            *tile = (int)(c0 % F);
+        } else {
+            *kind = kItemWideDp;
+            *band = b;
+            *tile = (int)(off - c0);
+        }
+    }
+    __host__ __device__ void decode(long long item, int *kind, int *band, int *tile) const {
+        int lo = 0, hi = k - 1;   // the last level that starts at or before item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (start(mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        at(lo, item - start(lo), kind, band, tile);
+    }
+};
+
 __device__ inline void decode_wide_one(const ImgDesc &im, long long item, int *kind, int *band,
                                        int *tile) {
-    const long long hf = im.ftiles, L1 = hf + im.tiles;
-    if (item < hf) {
-        *kind = kItemWideFht;
-        *band = im.k - 1;
-        *tile = (int)item;
-        return;
-    }
-    const long long j = item - hf;
-    long long lv = j / L1, off = j - lv * L1;
-    if (lv >= im.k - 1) {
-        lv = im.k - 1;
-        off = j - (long long)(im.k - 1) * L1;
-    }
-    const int b = im.k - 1 - (int)lv;
-    if (b > 0 && off < hf) {
-        *kind = kItemWideFht;
-        *band = b - 1;
-        *tile = (int)off;
-    } else {
-        *kind = kItemWideDp;
-        *band = b;
-        *tile = (int)(off - (b > 0 ? hf : 0));
-    }
+    WideLevels{im.k, im.ftiles, im.tiles}.decode(item, kind, band, tile);
 }
 
 template <typename In, typename Acc, typename Key>
@@ -2730,10 +2849,18 @@ RunLayout plan_layout(std::vector<ImgPlan> &imgs, bool with_table, bool reserve 
     size_t d = 0;
     for (auto &p : imgs) {
         p.m0 = d;   // the two M buffers are adjacent: one tensor map covers both
-        p.m1 = d + (size_t)p.s.D * p.mpitch * 4;
-        d = align_up(p.m1 + (size_t)p.s.D * p.mpitch * 4, 256);
-        p.bp = d;
-        d = align_up(d + (size_t)p.s.k * bp_groups(p.s.n) * 4 * p.s.w, 256);
+        if (p.kind == 2) {
+            // int32 / float images: one M array per band and no backpointers
+            // (the read-back recomputes each band's argmax)
+            p.m1 = d;
+            d = align_up(d + (size_t)p.s.k * p.s.D * p.mpitch * 4, 256);
+            p.bp = d;
+        } else {
+            p.m1 = d + (size_t)p.s.D * p.mpitch * 4;
+            d = align_up(p.m1 + (size_t)p.s.D * p.mpitch * 4, 256);
+            p.bp = d;
+            d = align_up(d + (size_t)p.s.k * bp_groups(p.s.n) * 4 * p.s.w, 256);
+        }
         if (p.kind == 1) {
             p.h256 = d;
             d = align_up(d + (size_t)p.s.k * 4 * 128 * p.hpitch * 2, 256);
@@ -2784,14 +2911,17 @@ bool encode_strip_map(CUtensorMap *map, const void *img, int h, int w, long long
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 2-D int32 tensor map of an image's two adjacent M buffers ([2D][mpitch]),
-// box of bw columns x bh rows: for bands of at most 128 rows 128 x D (one
-// copy brings a tile's whole M_{b+1}), for 256-row bands 64 x 73 (seven).
-bool encode_m_map(CUtensorMap *map, void *m0, int D, int mpitch, int bw, int bh) {
+// 2-D int32 tensor map of an image's adjacent M buffers ([arrays * D][mpitch]:
+// two ping-pong buffers, or one per band for int32 / float images), box of bw
+// columns x bh rows: for uint8 bands of at most 128 rows 128 x D (one copy
+// brings a tile's whole M_{b+1}), for 256-row bands 64 x 73 (seven), for
+// int32 / float images 16 x D.
+bool encode_m_map(CUtensorMap *map, void *m0, int D, int mpitch, int bw, int bh,
+                  int arrays = 2) {
     if ((uintptr_t)m0 % 16 != 0 || mpitch % 4 != 0 || bh > 256 || bw > 256) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
     if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)mpitch, (cuuint64_t)(2 * D)};
+    cuuint64_t dims[2] = {(cuuint64_t)mpitch, (cuuint64_t)arrays * D};
     cuuint64_t strides[1] = {(cuuint64_t)mpitch * 4};
     cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
     cuuint32_t estr[2] = {1u, 1u};
@@ -2825,7 +2955,7 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
                                          kTile256, kMBox256);
     else if (p.kind == 2)
         im.use_mtma = ws && encode_m_map(&im.mtmap, ws + L.data_off + p.m0, p.s.D, p.mpitch,
-                                         kWTileD, p.s.D) &&
+                                         kWTileD, p.s.D, p.s.k) &&
                       encode_rows_map(&im.tmap, ws + L.data_off + p.h256, p.hpitch,
                                       2 * p.s.k * p.s.n, kWTileD, p.s.n);
     else
@@ -3080,13 +3210,13 @@ void push_level(std::vector<Item> &order, const ImgPlan &p, int i, int lv) {
         return;
     }
     if (p.kind == 2) {
-        auto ffts = [&](int band) {
-            for (int t = 0; t < p.ftiles; ++t)
-                order.push_back(Item{i, band, t, kItemWideFht << 19});
-        };
-        if (lv == 0) ffts(b);
-        if (b > 0) ffts(b - 1);
-        for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemWideDp << 19});
+        const WideLevels wl{p.s.k, p.ftiles, p.tiles};
+        const long long len = wl.start(lv + 1) - wl.start(lv);
+        for (long long off = 0; off < len; ++off) {
+            int kind, band, tile;
+            wl.at(lv, off, &kind, &band, &tile);
+            order.push_back(Item{i, band, tile, kind << 19});
+        }
         return;
     }
     for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemBand << 19});
