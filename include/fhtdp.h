@@ -323,9 +323,18 @@ int fhtdp_detect_polyline_horizontal(const void *img, int dtype, int h, int w, i
 /* uint8 [n][h][w] -> bf16 [n][h/4][w/4], the 4x4 mean divided by 255. */
 int fhtdp_cnn_downsample4(const uint8_t *img, int n, int h, int w, void *out, cudaStream_t stream);
 /* y = act(conv3x3_dil(x, wt) + bias), act = ReLU when relu != 0; cin 1 or 32,
- * cout 32, zero padding ("same"). */
+ * cout 32, zero padding ("same").  32 input channels run on tcgen05.mma (128
+ * pixels x 32 channels per CTA, K = 9 x 32, FP32 accumulators in tensor
+ * memory); a bounded wait for the MMAs that gives up records FHTDP_ETIMEOUT
+ * for fhtdp_cnn_status. */
 int fhtdp_cnn_conv3x3(const void *x, int cin, int n, int h, int w, int dil, const void *wt,
                       const float *bias, int relu, void *y, cudaStream_t stream);
+/* Device status of the tensor-core convolutions since the last clear: 0, or
+ * FHTDP_ETIMEOUT when a wait for the MMAs gave up (the results are then
+ * undefined); clear != 0 resets it.  Synchronises the device (not for use
+ * under stream capture).  Returns a negative FHTDP_ECUDA-coded value only if
+ * the status cannot be read. */
+int fhtdp_cnn_status(int clear);
 /* dx = gradient of a 32-channel layer's input from the gradient dz of its
  * pre-activation output; wflip is caller scratch of 9*32*32 bf16. */
 int fhtdp_cnn_conv3x3_dgrad(const void *dz, int n, int h, int w, int dil, const void *wt,
@@ -416,8 +425,10 @@ long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
  *   1. the work-queue schedule: groups of images whose band levels hold about
  *      `target` column tiles and advance together, or band chains (an active
  *      set of about `target` tiles per step that images join, most bands
- *      first, as others finish); widths from half to six times the SM count
- *      and the whole batch;
+ *      first, as others finish), with the band heights interleaved (each
+ *      height's images joining most bands first) or not, and with images of
+ *      256-row bands advancing every step or every second step; widths from
+ *      half to six times the SM count and the whole batch;
  *   2. for each band height of uint8 images, the column tile width of its
  *      work items (128, or 256 for bands of at most 64 rows) and the number
  *      of FHT levels done in registers before the shared-memory merges (2 or
@@ -431,7 +442,8 @@ long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
 int fhtdp_batch_autotune(fhtdp_batch_plan *plan, void *ws, int reps, cudaStream_t stream,
                          long long *target_out);
 /* The plan's current choices: the queue schedule (*mode: 0 groups, 1 band
- * chains) and width, and for its images of band height n the column tile
+ * chains, 2 band chains with the band heights interleaved, 3 band chains
+ * with 256-row bands every second step, 4 both) and width, and for its images of band height n the column tile
  * width and register FHT depth (0 and 0 when it has none).  Any pointer may
  * be NULL.  The paper has no counterpart (see fhtdp_batch_autotune). */
 int fhtdp_batch_choice(const fhtdp_batch_plan *plan, int n, int *mode, long long *target,

@@ -143,6 +143,7 @@ _SIGS = {
                                          ctypes.c_void_p]),
     "fhtdp_cnn_bin_windows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "fhtdp_cnn_status": (ctypes.c_int, [ctypes.c_int]),
     "fhtdp_cnn_param_bytes": (ctypes.c_size_t, []),
     "fhtdp_cnn_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p]),
     "fhtdp_cnn_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int] * 3),
@@ -358,14 +359,16 @@ class BatchPlan:
         return t.value
 
     def choice(self, n: int):
-        """The plan's schedule ("groups" or "chains"), width, and the tile
+        """The plan's schedule ("groups", "chains", "chains-mixed", "chains-slow256" or
+        "chains-mixed-slow256"), width, and the tile
         width and register FHT depth of its images of band height n."""
         mode, target = ctypes.c_int(0), ctypes.c_longlong(0)
         tile, depth = ctypes.c_int(0), ctypes.c_int(0)
         _check(lib().fhtdp_batch_choice(self._plan, int(n), ctypes.byref(mode),
                                         ctypes.byref(target), ctypes.byref(tile),
                                         ctypes.byref(depth)))
-        return {"schedule": "chains" if mode.value else "groups", "width": target.value,
+        return {"schedule": ("groups", "chains", "chains-mixed", "chains-slow256",
+                             "chains-mixed-slow256")[mode.value], "width": target.value,
                 "tile": tile.value, "depth": depth.value}
 
     def configure(self, n: int, tile: int, depth: int, stream=None):

@@ -1018,6 +1018,15 @@ struct U8Path {
         return hc > s ? hc : s;
     }
     __host__ __device__ static size_t hc_offset();
+    // Short bands: the V rows of a tile and the FHT's region F side by side
+    // in region A (F after V), so that the M tile can land in the V rows
+    // while the FHT runs.
+    __host__ __device__ static size_t v_bytes(int n, int T) {
+        return ((size_t)vblock(n) * (T / kTile) * 4 + 127) / 128 * 128;
+    }
+    __host__ __device__ static bool early_m(int n, int T) {
+        return v_bytes(n, T) + (size_t)frows(n) * fpitch(n, T) * 4 <= hc_offset();
+    }
 
     // Four pixels [c, c+4) of a row as one little-endian word, zero outside
     // [0, w).  c is a multiple of 4; `aligned` says rows start on 4 bytes.
@@ -1503,11 +1512,13 @@ struct U8Path {
         const bool hitem = kMulti && half >= 0;
         const int n = hitem ? 128 : im.n, T = hitem ? kTile : tw(im), D = 2 * n - 1;
         const int x0 = tile * T;
-        uint32_t *F = (uint32_t *)smem;  // the strip, then V
+        // the FHT's region; after V when both fit (the M tile may then come
+        // during the FHT)
+        uint32_t *F = (uint32_t *)(smem + (!hitem && early_m(n, T) ? v_bytes(n, T) : 0));
         int32_t *Vn = (int32_t *)smem;
         uint32_t *Hc = (uint32_t *)(smem + hc_offset());
         fht(F, Hc, im, band, x0, pipe, prefetched, args, n, hitem ? 7 : im.log2n, T);
-        nb_arrive(kBarFhtDone, kCtlSync);   // F is free for the M tile
+        nb_arrive(kBarFhtDone, kCtlSync);   // F is free for the M tile (if it overlaps V)
         if (hitem) {
             store_half(im, band, half, x0, Hc);
             nb_arrive(kBarHcFree, kCtlSync);
@@ -2034,6 +2045,10 @@ struct U8Ctl {
         }
     }
 
+    // Items whose M tile may land while their FHT runs (F beside the V rows).
+    __device__ static bool early_copy(const Ctrl &c) {
+        return c.kind == kItemBand && U8Path<Key, true>::early_m(c.n, c.T);
+    }
     // Lane 0, after the FHT: the M tile of the item into the V rows (or just
     // the arrival on the M barrier when it has none).  Half-band items do
     // not use the M barrier.
@@ -2087,7 +2102,8 @@ struct U8Ctl {
 
     // The control warp: takes the items from the queue one ahead of the
     // compute warps, copies each strip as soon as Hc is free, copies an
-    // item's M tile as soon as its FHT is done, and releases its flag once its
+    // item's M tile as soon as its FHT is done (short bands: as soon as the
+    // previous item's window maxima are stored), and releases its flag once its
     // window maxima are stored (band 0: counts the tile and reads the
     // polyline back after the image's last).  The producer flags of the next
     // item are polled while the compute warps finish the current one, so
@@ -2107,24 +2123,40 @@ struct U8Ctl {
         if (lane == 0 && cur.item < args.items) idx = take(args);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         bool ok = cur.item < args.items ? wait_producers(cur, args, lane) : true;
+        bool copied = false;   // cur's M tile is on its way already
         while (cur.item < args.items) {
             const Ctrl next = decode(args, idx);
+            // The V rows are free once the previous item's window maxima are
+            // stored; where F lies beside them the M copy need not wait for
+            // the FHT.
+            const bool early = early_copy(cur);
+            if (early && !copied && lane == 0) {
+                if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
+                copy_m_tile(cur, Vn, pipe);
+            }
             nb_sync(kBarFhtDone, kCtlSync);
-            if (lane == 0) {
+            if (!early && lane == 0) {
                 if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
                 copy_m_tile(cur, Vn, pipe);
             }
             nb_sync(kBarHcFree, kCtlSync);
             if (lane == 0) hand_over(next, slot, Hc, pipe);
             nb_arrive(kBarNext, kCtlSync);
+            // The item after next is taken now (its index is used only after
+            // this item's window), so that the queue's round trip overlaps
+            // the polling.  A CTA works its items in queue order, so holding
+            // one more keeps the queue free of deadlock.
+            long long ahead = 0;
+            if (lane == 0 && next.item < args.items) ahead = take(args);
             const bool ready = next.item >= args.items ||
                                poll_producers(next, args, lane, done, cur.item);
             nb_sync(kBarWinDone, kCtlSync);
-            if (lane == 0) {
-                finish(cur, args);
-                if (next.item < args.items) idx = take(args);
-            }
-            idx = __shfl_sync(0xffffffffu, idx, 0);
+            // next's producers seen and the V rows free: its M copy goes out
+            // before this item's publication.
+            copied = ready && next.item < args.items && early_copy(next);
+            if (copied && lane == 0) copy_m_tile(next, Vn, pipe);
+            if (lane == 0) finish(cur, args);
+            idx = __shfl_sync(0xffffffffu, ahead, 0);
             ok = ready || wait_producers(next, args, lane);
             cur = next;
         }
@@ -2583,36 +2615,41 @@ struct WideEngine {
     }
 };
 
-// The work items of an int32 / float image, in queue order, by band level:
-// level 0 opens with the FHT items of band k-1; level lv (band b = k-1-lv)
-// holds the DP items of band b and, spread evenly among them, the FHT items
-// of band b - kWAhead (level 0: of bands k-2 .. k-1-kWAhead).  An FHT item
-// takes several DP items' time, so it is queued kWAhead levels before the
-// DP items that read its rows, and spreading them keeps a level's DP items
-// from waiting behind a block of FHT items.  Every item still comes after
-// all the items it waits for.
+// The work items of an image whose bands need FHT items of their own (int32
+// / float images; the half-band items of 256-row uint8 bands), in queue
+// order, by band level: level 0 opens with the FHT items of band k-1; level
+// lv (band b = k-1-lv) holds the DP items of band b and, spread evenly among
+// them (or in a block before them), the FHT items of band b - A (level 0: of
+// bands k-2 .. k-1-A).  An FHT
+// item takes several DP items' time, so it is queued A levels before the DP
+// items that read its rows, and spreading them keeps a level's DP items from
+// waiting behind a block of FHT items.  Every item still comes after all the
+// items it waits for.
 constexpr int kWAhead = 2;
 struct WideLevels {
     int k;
     long long F, P;   // FHT and DP items of one band
+    int A = kWAhead;  // levels between an FHT item and the DP items that read it
+    bool spread = true;   // false: a level's FHT items before its DP items
     __host__ __device__ long long fht_in(int lv) const {   // FHT items spread in level lv
-        if (lv == 0) return (long long)(kWAhead < k - 1 ? kWAhead : k - 1) * F;
-        return k - 1 - lv - kWAhead >= 0 ? F : 0;
+        if (lv == 0) return (long long)(A < k - 1 ? A : k - 1) * F;
+        return k - 1 - lv - A >= 0 ? F : 0;
     }
     // First item of level lv (lv = k: the item count).
     __host__ __device__ long long start(int lv) const {
         if (lv == 0) return 0;
         const long long l0 = F + fht_in(0) + P;
-        int full = lv - 1 < k - 1 - kWAhead ? lv - 1 : k - 1 - kWAhead;   // levels 1.. with F
+        int full = lv - 1 < k - 1 - A ? lv - 1 : k - 1 - A;   // levels 1.. with F
         if (full < 0) full = 0;
         return l0 + (long long)full * (F + P) + (long long)(lv - 1 - full) * P;
     }
-    // Item `off` of level lv.
+    // Item `off` of level lv: FHT item `tile` of `band` (kind 0), or DP item
+    // `tile` of `band` (kind 1).
     __host__ __device__ void at(int lv, long long off, int *kind, int *band, int *tile) const {
         const int b = k - 1 - lv;
         if (lv == 0) {
             if (off < F) {
-                *kind = kItemWideFht;
+                *kind = 0;
                 *band = k - 1;
                 *tile = (int)off;
                 return;
@@ -2620,13 +2657,14 @@ struct WideLevels {
             off -= F;
         }
         const long long Fl = fht_in(lv), S = Fl + P;
-        const long long c0 = off * Fl / S, c1 = (off + 1) * Fl / S;
+        const long long c0 = spread ? off * Fl / S : (off < Fl ? off : Fl);
+        const long long c1 = spread ? (off + 1) * Fl / S : (off < Fl ? off + 1 : Fl);
         if (c1 > c0) {   // the FHT item number c0 of the level
-            *kind = kItemWideFht;
-            *band = lv == 0 ? k - 2 - (int)(c0 / F) : b - kWAhead;
+            *kind = 0;
+            *band = lv == 0 ? k - 2 - (int)(c0 / F) : b - A;
             *tile = (int)(c0 % F);
         } else {
-            *kind = kItemWideDp;
+            *kind = 1;
             *band = b;
             *tile = (int)(off - c0);
         }
@@ -2644,7 +2682,9 @@ struct WideLevels {
 
 __device__ inline void decode_wide_one(const ImgDesc &im, long long item, int *kind, int *band,
                                        int *tile) {
-    WideLevels{im.k, im.ftiles, im.tiles}.decode(item, kind, band, tile);
+    int fd;
+    WideLevels{im.k, im.ftiles, im.tiles}.decode(item, &fd, band, tile);
+    *kind = fd ? kItemWideDp : kItemWideFht;
 }
 
 template <typename In, typename Acc, typename Key>
@@ -3198,23 +3238,25 @@ long long level_weight(const ImgPlan &p) {
 // ready one level ahead.
 void push_level(std::vector<Item> &order, const ImgPlan &p, int i, int lv) {
     const int b = p.s.k - 1 - lv;
-    if (p.kind == 1) {
-        auto halves = [&](int band) {
-            for (int h = 0; h < 2; ++h)
-                for (int t = 0; t < p.ftiles; ++t)
-                    order.push_back(Item{i, band, t, (kItemHalf0 + h) << 19});
-        };
-        if (lv == 0) halves(b);
-        if (b > 0) halves(b - 1);
-        for (int t = 0; t < p.tiles; ++t) order.push_back(Item{i, b, t, kItemDp256 << 19});
-        return;
-    }
-    if (p.kind == 2) {
-        const WideLevels wl{p.s.k, p.ftiles, p.tiles};
+    if (p.kind == 1 || p.kind == 2) {
+        // FHT items of a band: both halves' tiles (256-row bands) or its tiles
+        // (256-row bands: the halves of band b-1 in a block before the DP items
+        // of band b; their DP items wait mostly for those of band b+1)
+        const long long F = p.kind == 1 ? 2LL * p.ftiles : p.ftiles;
+        const WideLevels wl{p.s.k, F, p.tiles, p.kind == 1 ? 1 : kWAhead, p.kind != 1};
         const long long len = wl.start(lv + 1) - wl.start(lv);
         for (long long off = 0; off < len; ++off) {
-            int kind, band, tile;
-            wl.at(lv, off, &kind, &band, &tile);
+            int dp, band, tile;
+            wl.at(lv, off, &dp, &band, &tile);
+            int kind;
+            if (p.kind == 2) {
+                kind = dp ? kItemWideDp : kItemWideFht;
+            } else if (dp) {
+                kind = kItemDp256;
+            } else {
+                kind = kItemHalf0 + tile / p.ftiles;
+                tile %= p.ftiles;
+            }
             order.push_back(Item{i, band, tile, kind << 19});
         }
         return;
@@ -3259,29 +3301,60 @@ std::vector<Item> queue_grouped(const std::vector<ImgPlan> &imgs, long long targ
 // whenever its width (tiles per step) drops below `target`, so that steps
 // keep about the same width while images of different heights finish at
 // different times, and the longest chains start with the batch.
-std::vector<Item> queue_chains(const std::vector<ImgPlan> &imgs, long long target) {
+// With `mixed`, the images of each band height join in that order (longest
+// chains first), but the band heights are interleaved in proportion to their
+// image counts, so that every step holds a mix of them: the images with the
+// fewest and heaviest bands (256 rows: nine producer tiles per DP item) do
+// not all end up in the last steps, waiting on one another.
+// With `slow256`, images of 256-row bands advance one level every second
+// step: a DP item of such a band waits for nine DP items of the band below,
+// which are then two steps ahead of it in the queue.
+std::vector<Item> queue_chains(const std::vector<ImgPlan> &imgs, long long target,
+                               bool mixed = false, bool slow256 = false) {
     // the longest band chains first, so that they start with the batch
     std::vector<int> by_k(imgs.size());
     for (size_t i = 0; i < imgs.size(); ++i) by_k[i] = (int)i;
     std::stable_sort(by_k.begin(), by_k.end(),
                      [&](int a, int b) { return imgs[a].s.k > imgs[b].s.k; });
+    if (mixed) {
+        // rank of each image within its band height, as a fraction of the
+        // height's image count
+        std::vector<double> key(imgs.size());
+        std::vector<int> heights;
+        for (const ImgPlan &p : imgs)
+            if (std::find(heights.begin(), heights.end(), p.s.n) == heights.end())
+                heights.push_back(p.s.n);
+        for (int n : heights) {
+            int count = 0, rank = 0;
+            for (int i : by_k) count += imgs[i].s.n == n;
+            for (int i : by_k)
+                if (imgs[i].s.n == n) key[i] = (rank++ + 0.5) / count;
+        }
+        std::stable_sort(by_k.begin(), by_k.end(), [&](int a, int b) { return key[a] < key[b]; });
+    }
     std::vector<Item> order;
     struct Active {
         int image, level;
+        long long step0;   // the step it joined
     };
     std::vector<Active> active;
+    long long step = 0;
     size_t next = 0;
     long long width = 0;
     target = std::max(1LL, target);
     while (next < imgs.size() || !active.empty()) {
         while (next < imgs.size() && (active.empty() || width < target)) {
-            active.push_back(Active{by_k[next], 0});
+            active.push_back(Active{by_k[next], 0, step});
             width += level_weight(imgs[by_k[next]]);
             ++next;
         }
         std::vector<Active> still;
         for (Active &a : active) {
             const ImgPlan &p = imgs[a.image];
+            if (slow256 && p.kind == 1 && (step - a.step0) % 2 != 0) {
+                still.push_back(a);
+                continue;
+            }
             push_level(order, p, a.image, a.level);
             if (++a.level < p.s.k)
                 still.push_back(a);
@@ -3289,15 +3362,19 @@ std::vector<Item> queue_chains(const std::vector<ImgPlan> &imgs, long long targe
                 width -= level_weight(p);
         }
         active.swap(still);
+        ++step;
     }
     return order;
 }
 
 // The queue order of a schedule: 0 groups of images advancing together
-// (queue_grouped), 1 band chains joining as others finish, longest first
-// (queue_chains).
+// (queue_grouped); band chains joining as others finish, longest first
+// (queue_chains): 1 as they are, 2 with the band heights interleaved, 3 with
+// 256-row bands advancing every second step, 4 both.
+constexpr int kSchedules = 5;
 std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target, int mode) {
-    return mode ? queue_chains(imgs, target) : queue_grouped(imgs, target);
+    return mode ? queue_chains(imgs, target, mode == 2 || mode == 4, mode >= 3)
+                : queue_grouped(imgs, target);
 }
 
 size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
@@ -3557,7 +3634,7 @@ int batch_autotune(BatchPlan *plan, void *ws, int reps, cudaStream_t stream, lon
         int bm = plan->mode;
         float bms = -1.0f;
         int r = 0;
-        for (size_t c = 0; c < 2 * cands.size() && !r; ++c) {
+        for (size_t c = 0; c < kSchedules * cands.size() && !r; ++c) {
             const int mode = (int)(c / cands.size());
             const long long t = cands[c % cands.size()];
             r = apply(t, mode);
