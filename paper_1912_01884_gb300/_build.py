@@ -14,7 +14,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfhtdp.so")
 
 SOURCES = ["api.cu", "fht_stages.cu", "dp_basic.cu", "angle.cu", "queries.cu", "engine.cu",
-           "noalloc.cu", "cnn.cu", "learned.cu"]
+           "noalloc.cu", "cnn.cu", "conv_tc.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills", "-I", INCLUDE, "-I", CSRC]

@@ -480,6 +480,12 @@ int fhtdp_cnn_conv3x3(const void *x, int cin, int n, int h, int w, int dil, cons
     return cnn_conv3x3(x, cin, n, h, w, dil, wt, bias, relu, y, stream);
 }
 
+int fhtdp_cnn_status(int clear) {
+    g_last_error[0] = 0;
+    const int st = cnn_tc_status(clear);
+    return st == FHTDP_ECUDA ? -FHTDP_ECUDA : st;
+}
+
 int fhtdp_cnn_conv3x3_dgrad(const void *dz, int n, int h, int w, int dil, const void *wt,
                             void *wflip, void *dx, cudaStream_t stream) {
     g_last_error[0] = 0;

@@ -8,8 +8,10 @@
 // weights bf16 [tap][ci][co] with tap = ky*3 + kx (layer 1: [16][32], taps
 // 9..15 zero), FP32 master weights and FP32 accumulation.  The 3x3 dilated
 // convolutions ("same" zero padding) run as implicit GEMMs on the tensor
-// cores (bf16 WMMA 16x16x16 tiles): a CTA takes 64 pixels of one image row
-// and all 32 output channels; K = 9 taps x 32 input channels.
+// cores: the 32-channel layers (forward and data gradient) with tcgen05.mma
+// (conv_tc.cu), the single-channel first layer and the weight gradient with
+// bf16 WMMA 16x16x16 tiles: a CTA takes 64 pixels of one image row and all
+// 32 output channels; K = 9 taps x 32 input channels.
 #include <mma.h>
 
 #include <cuda_bf16.h>
@@ -389,6 +391,9 @@ int cnn_downsample4(const uint8_t *img, int N, int H, int W, void *out, cudaStre
 
 int cnn_conv3x3(const void *X, int cin, int N, int H, int W, int dil, const void *Wt,
                 const float *bias, int relu, void *Y, cudaStream_t stream) {
+    // 32 input channels: the tcgen05 kernel; the single-channel first layer
+    // (1/32 of the work) keeps the WMMA one
+    if (cin == kC) return cnn_conv3x3_tc(X, N, H, W, dil, Wt, bias, relu, Y, stream);
     const long long blocks = (long long)N * H * (W / kSeg);
     if (relu)
         conv3x3_kernel<true><<<(unsigned)blocks, 256, 0, stream>>>(

@@ -1,0 +1,254 @@
+// 3x3 dilated convolutions of the learned window proposal with 32 input and
+// 32 output channels on the fifth-generation tensor cores (tcgen05.mma,
+// accumulators in tensor memory).  The paper has no counterpart: the network
+// is an addition in front of the exact method.
+//
+// One CTA (4 warps) computes 128 output pixels of one image row for all 32
+// output channels: an implicit GEMM D[p][co] = sum over taps t and input
+// channels ci of X(p + off(t))[ci] * W[t][ci][co], M = 128, N = 32, K = 9 x 32,
+// as 18 MMAs of K = 16 (bf16 operands, FP32 accumulation).
+//
+// Shared memory holds operands in the no-swizzle K-major layout of the MMA:
+// "core matrices" of 8 rows x 16 bytes (8 bf16 along K) stored as 128
+// contiguous bytes.
+//  - A: the three input rows y - dil, y, y + dil, pixels [x0 - 8, x0 + 136)
+//    (zero outside the image), as [row][channel chunk][pixel][8 channels]:
+//    rows of a core matrix are consecutive pixels (16 bytes apart), the next
+//    8 pixels 128 bytes on, the next channel chunk kAChunk bytes on.  The
+//    operand of tap (ky, kx) is the same buffer from pixel 8 + (kx - 1) * dil:
+//    every tap reads the staged rows in place.
+//  - B: the weights as [tap][channel chunk][co][8 ci] (512 bytes per chunk).
+// D (128 lanes x 32 FP32 columns of tensor memory) is read back by the four
+// warps, one lane quarter each (tcgen05.ld 32x32b), then bias, ReLU and bf16.
+#include <cuda_bf16.h>
+
+#include "cnn.cuh"
+
+namespace fhtdp {
+namespace {
+
+constexpr int kTcC = 32;                 // channels
+constexpr int kTcM = 128;                // output pixels of a CTA
+constexpr int kTcHalo = 8;               // largest dilation
+constexpr int kTcPix = kTcM + 2 * kTcHalo;             // staged pixels of a row
+constexpr int kAChunk = kTcPix * 16;                    // bytes of one channel chunk
+constexpr int kARow = 4 * kAChunk;                      // bytes of one staged row
+constexpr int kABytes = 3 * kARow;                      // 27,648
+constexpr int kBBytes = 9 * 4 * kTcC * 16;              // 18,432
+constexpr int kTcThreads = 128;
+constexpr unsigned kTmemCols = 32;
+
+// Device status of the tensor-core convolutions: FHTDP_ETIMEOUT once a
+// bounded wait for the MMAs gave up (read with fhtdp_cnn_status).
+__device__ int g_conv_tc_status;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading
+// (K-direction) and stride (M/N-direction) byte offsets of the core
+// matrices, each in 16-byte units; bit 46 is the descriptor version.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3ffffu) >> 4) | ((uint64_t)((lbo & 0x3ffffu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3ffffu) >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), bf16
+// A and B (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at
+// bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcC >> 3) << 17) |
+                            ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+// Bounded parity wait: false when `limit` cycles passed first.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    // src-size 0 fills the 16 bytes with zeros
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+template <bool kRelu>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(
+    const __nv_bfloat16 *__restrict__ X, int H, int W, int dil,
+    const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
+    __nv_bfloat16 *__restrict__ Y, long long wait_cycles) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *As = smem;
+    unsigned char *Bs = smem + kABytes;
+    __shared__ __align__(8) uint64_t s_done;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = (W + kTcM - 1) / kTcM;
+    const int n = blockIdx.x / (H * segs);
+    const int rem = blockIdx.x % (H * segs);
+    const int y = rem / segs, x0 = (rem % segs) * kTcM;
+
+    if (tid == 0) {
+        mbar_init(&s_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // A: rows y + (r - 1) dil, pixels x0 - 8 + q, channel chunk c.
+    for (int i = tid; i < 3 * 4 * kTcPix; i += kTcThreads) {
+        const int c = i & 3, q = (i >> 2) % kTcPix, r = (i >> 2) / kTcPix;
+        const int yy = y + (r - 1) * dil, xx = x0 - kTcHalo + q;
+        const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const __nv_bfloat16 *src =
+            ok ? X + ((((size_t)n * H + yy) * W + xx) * kTcC + 8 * c) : X;
+        cp_async16(smem_u32(As + r * kARow + c * kAChunk + q * 16), src, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // B: W[t][ci][co] -> [t][ci / 8][co][ci % 8].
+    for (int i = tid; i < 9 * kTcC * kTcC; i += kTcThreads) {
+        const int co = i & 31, ci = (i >> 5) & 31, t = i >> 10;
+        ((__nv_bfloat16 *)Bs)[((t * 4 + (ci >> 3)) * kTcC + co) * 8 + (ci & 7)] = Wt[i];
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // generic-proxy shared stores -> visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    if (tid == 0) {
+        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+        for (int t = 0; t < 9; ++t) {
+            const int ky = t / 3, kx = t % 3;
+            const uint32_t abase = a0 + ky * kARow + (kTcHalo + (kx - 1) * dil) * 16;
+            for (int j = 0; j < 2; ++j) {
+                const uint64_t ad = sdesc(abase + 2 * j * kAChunk, kAChunk, 128);
+                const uint64_t bd = sdesc(b0 + (t * 4 + 2 * j) * 512, 512, 128);
+                const uint32_t acc = (t | j) != 0;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                    : "memory");
+            }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&s_done))
+            : "memory");
+    }
+    __syncwarp();
+    bool ok = mbar_wait(&s_done, 0, wait_cycles);
+    if (!ok) {
+        if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
+        // the MMAs may still run: give them a last (bounded) chance before
+        // tensor memory is read and freed
+        mbar_wait(&s_done, 0, 4 * wait_cycles);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int x = x0 + tid;   // lane quarter `warp` = pixels 32 warp .. 32 warp + 31
+    if (x < W) {
+        uint32_t packed[16];
+#pragma unroll
+        for (int c = 0; c < kTcC; c += 2) {
+            float v0 = __uint_as_float(r[c]) + (bias ? __ldg(bias + c) : 0.0f);
+            float v1 = __uint_as_float(r[c + 1]) + (bias ? __ldg(bias + c + 1) : 0.0f);
+            if (kRelu) {
+                v0 = v0 > 0.0f ? v0 : 0.0f;
+                v1 = v1 > 0.0f ? v1 : 0.0f;
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            packed[c / 2] = *(const uint32_t *)&h;
+        }
+        uint4 *dst = (uint4 *)(Y + (((size_t)n * H + y) * W + x) * kTcC);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
+                                packed[4 * q + 3]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+}
+
+}  // namespace
+
+size_t cnn_conv_tc_smem() { return (size_t)kABytes + kBBytes; }
+
+int cnn_conv3x3_tc(const void *X, int N, int H, int W, int dil, const void *Wt,
+                   const float *bias, int relu, void *Y, cudaStream_t stream) {
+    if (dil < 1 || dil > kTcHalo || W < 1 || H < 1 || N < 1)
+        return set_error(FHTDP_EINVAL, "conv3x3: dilation 1..8 and a non-empty image");
+    const size_t smem = cnn_conv_tc_smem();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3x3_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaFuncSetAttribute(conv3x3_tc_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const long long blocks = (long long)N * H * ((W + kTcM - 1) / kTcM);
+    const long long wait = 4000000000LL;   // about two seconds
+    if (relu)
+        conv3x3_tc_kernel<true><<<(unsigned)blocks, kTcThreads, smem, stream>>>(
+            (const __nv_bfloat16 *)X, H, W, dil, (const __nv_bfloat16 *)Wt, bias,
+            (__nv_bfloat16 *)Y, wait);
+    else
+        conv3x3_tc_kernel<false><<<(unsigned)blocks, kTcThreads, smem, stream>>>(
+            (const __nv_bfloat16 *)X, H, W, dil, (const __nv_bfloat16 *)Wt, bias,
+            (__nv_bfloat16 *)Y, wait);
+    return launched("conv3x3_tc_kernel");
+}
+
+int cnn_tc_status(int clear) {
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_conv_tc_status, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e, "cudaMemcpyFromSymbol");
+    if (clear) {
+        const int z = 0;
+        e = cudaMemcpyToSymbol(g_conv_tc_status, &z, sizeof(int));
+        if (e != cudaSuccess) return cuda_status(e, "cudaMemcpyToSymbol");
+    }
+    return v;
+}
+
+}  // namespace fhtdp

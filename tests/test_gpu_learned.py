@@ -56,6 +56,34 @@ def test_conv_forward_matches_reference(lib, cin, dil):
     _close(_np(y), np.maximum(ref, 0))
 
 
+@pytest.mark.parametrize("W,dil,relu,bias", [(192, 3, 0, False), (256, 8, 1, True),
+                                             (64, 5, 1, True), (320, 1, 0, True)])
+def test_conv_tensor_core_tiles_and_ragged_rows(lib, W, dil, relu, bias):
+    """32-channel layers run 128-pixel tiles on tcgen05: rows that end inside
+    a tile (192, 320), a row narrower than a tile (64), every dilation's halo
+    inside the staged rows, with and without bias and ReLU; no wait gave up."""
+    import torch
+    rng = np.random.default_rng(W + dil)
+    N, H = 3, 9
+    x = _bf16(rng.standard_normal((N, H, W, 32)))
+    w = rng.standard_normal((9, 32, 32)) * 0.2
+    wb = _bf16(w.reshape(-1, 32))
+    b = rng.standard_normal(32).astype(np.float32)
+    bd = torch.from_numpy(b).cuda() if bias else None
+    y = torch.full((N, H, W, 32), 7.0, dtype=torch.bfloat16, device="cuda")
+    xd, wd = x.cuda(), wb.cuda()
+    L = lib.lib()
+    assert L.fhtdp_cnn_status(1) == 0
+    assert L.fhtdp_cnn_conv3x3(xd.data_ptr(), 32, N, H, W, dil, wd.data_ptr(),
+                               bd.data_ptr() if bias else None, relu, y.data_ptr(),
+                               _stream()) == 0
+    torch.cuda.synchronize()
+    assert L.fhtdp_cnn_status(0) == 0
+    ref = cnn_ref.conv3x3(_np(x), _np(wb).reshape(9, 32, 32),
+                          b.astype(np.float64) if bias else np.zeros(32), dil)
+    _close(_np(y), np.maximum(ref, 0) if relu else ref)
+
+
 def test_conv_gradients_match_reference(lib):
     import torch
     rng = np.random.default_rng(5)
