@@ -419,6 +419,7 @@ int cnn_flip_transpose(const void *Wt, void *Wf, cudaStream_t stream) {
 
 int cnn_wgrad(const void *X, int cin, int N, int H, int W, int dil, const void *dZ, float *dW,
               float *db, cudaStream_t stream) {
+    if (cin == kC) return cnn_wgrad_tc(X, N, H, W, dil, dZ, dW, db, stream);
     conv3x3_wgrad_kernel<<<2 * 152, 256, 0, stream>>>((const __nv_bfloat16 *)X, cin, N, H, W, dil,
                                                       (const __nv_bfloat16 *)dZ, dW, db);
     return launched("conv3x3_wgrad_kernel");

@@ -25,6 +25,8 @@ int cnn_to_bf16(const float *src, void *dst, int count, cudaStream_t stream);
 // with `clear` resets) their device status, synchronising.
 int cnn_conv3x3_tc(const void *X, int N, int H, int W, int dil, const void *Wt,
                    const float *bias, int relu, void *Y, cudaStream_t stream);
+int cnn_wgrad_tc(const void *X, int N, int H, int W, int dil, const void *dZ, float *dW,
+                 float *db, cudaStream_t stream);
 int cnn_tc_status(int clear);
 int cnn_bin_windows(const int32_t *pred, int count, int n, int margin, int32_t *win,
                     cudaStream_t stream);

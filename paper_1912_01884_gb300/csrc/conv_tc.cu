@@ -22,6 +22,8 @@
 // warps, one lane quarter each (tcgen05.ld 32x32b), then bias, ReLU and bf16.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "cnn.cuh"
 
 namespace fhtdp {
@@ -46,9 +48,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor, no swizzle: start address, leading
-// (K-direction) and stride (M/N-direction) byte offsets of the core
-// matrices, each in 16-byte units; bit 46 is the descriptor version.
+// Shared-memory matrix descriptor, no swizzle: start address, leading and
+// stride byte offsets of the core matrices, each in 16-byte units; bit 46 is
+// the descriptor version.  Without swizzling the leading offset is the step
+// between core matrices along K and the stride offset the step along M / N,
+// for K-major and MN-major operands alike.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((addr & 0x3ffffu) >> 4) | ((uint64_t)((lbo & 0x3ffffu) >> 4) << 16) |
            ((uint64_t)((sbo & 0x3ffffu) >> 4) << 32) | (1ull << 46);
@@ -209,7 +213,181 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(
                      : "memory");
 }
 
+// Weight and bias gradients of a 32-channel layer: dW[t][ci][co] += sum over
+// pixels p of X(p + off(t))[ci] * dZ(p)[co], db[co] += sum of dZ(p)[co].  As
+// GEMMs with the pixels as K: M = 128 rows (t', ci) for four taps t = 4g + t'
+// (g = 0, 1, 2; rows of taps past 8 are never read), N = 32 (co).  A CTA
+// loops over 128-pixel row segments and keeps the three accumulators in
+// tensor memory (96 columns); at the end each thread adds its row's 32
+// values of each group to dW.  Both operands are MN-major (channels
+// contiguous, as stored): core matrices of 8 channels (16 bytes) x 8 pixels,
+//   A: [g][t' * 4 + chunk][pixel][8 ci]  (next 8 rows of M: kWgChunk bytes,
+//                                          next 8 pixels of K: 128 bytes)
+//   B: [chunk][pixel][8 co]              (the same strides).
+constexpr int kWgP = 128;                       // pixels of a segment (K per stage)
+constexpr int kWgChunk = kWgP * 16;             // bytes of a chunk of a segment
+constexpr int kWgABytes = 3 * 16 * kWgChunk;    // 98,304
+constexpr int kWgBBytes = 4 * kWgChunk;         // 8,192
+constexpr unsigned kWgCols = 128;               // three 32-column accumulators
+constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);   // A and B MN-major
+
+__global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(
+    const __nv_bfloat16 *__restrict__ X, int N, int H, int W, int dil,
+    const __nv_bfloat16 *__restrict__ dZ, float *__restrict__ dW, float *__restrict__ db,
+    long long wait_cycles) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *As = smem;
+    unsigned char *Bs = smem + kWgABytes;
+    __shared__ __align__(8) uint64_t s_done;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&s_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(kWgCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int segs = (W + kWgP - 1) / kWgP;
+    const long long units = (long long)N * H * segs;
+    float bsum = 0.0f;   // thread c < 32: channel c of db over this CTA's pixels
+    uint32_t phase = 0;
+    bool first = true, ok = true;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const int n = (int)(u / ((long long)H * segs));
+        const int rem = (int)(u % ((long long)H * segs));
+        const int y = rem / segs, x0 = (rem % segs) * kWgP;
+        // A: taps 0..8 (group g = t / 4, t' = t % 4), 4 chunks, 128 pixels
+        for (int i = tid; i < 9 * 4 * kWgP; i += kTcThreads) {
+            const int c = i & 3, p = (i >> 2) % kWgP, t = (i >> 2) / kWgP;
+            const int ky = t / 3, kx = t % 3;
+            const int yy = y + (ky - 1) * dil, xx = x0 + p + (kx - 1) * dil;
+            const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const __nv_bfloat16 *src =
+                v ? X + ((((size_t)n * H + yy) * W + xx) * kTcC + 8 * c) : X;
+            const int g = t >> 2, mb = (t & 3) * 4 + c;
+            cp_async16(smem_u32(As + (g * 16 + mb) * kWgChunk + p * 16), src, v);
+        }
+        // B: dZ of the segment's pixels (zero past the row's end)
+        for (int i = tid; i < 4 * kWgP; i += kTcThreads) {
+            const int c = i & 3, p = i >> 2;
+            const bool v = x0 + p < W;
+            const __nv_bfloat16 *src =
+                v ? dZ + ((((size_t)n * H + y) * W + x0 + p) * kTcC + 8 * c) : dZ;
+            cp_async16(smem_u32(Bs + c * kWgChunk + p * 16), src, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid < kTcC) {   // db: column tid of B over the segment
+            const __nv_bfloat16 *col = (const __nv_bfloat16 *)(Bs + (tid >> 3) * kWgChunk) + (tid & 7);
+            float sacc = 0.0f;
+            for (int p = 0; p < kWgP; ++p) sacc += __bfloat162float(col[p * 8]);
+            bsum += sacc;
+        }
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            for (int g = 0; g < 3; ++g)
+                for (int j = 0; j < kWgP / 16; ++j) {
+                    // MN-major, no swizzle: the leading offset steps along K
+                    // (8 pixels), the stride offset along M / N (8 channels)
+                    const uint64_t ad = sdesc(a0 + g * 16 * kWgChunk + j * 256, 128, kWgChunk);
+                    const uint64_t bd = sdesc(b0 + j * 256, 128, kWgChunk);
+                    const uint32_t acc = first && j == 0 ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                            tmem + 32u * g),
+                        "l"(ad), "l"(bd), "r"(kIdescMN), "r"(acc)
+                        : "memory");
+                }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&s_done))
+                : "memory");
+        }
+        first = false;
+        __syncwarp();
+        // the stage is rewritten next: wait for the MMAs that read it
+        const bool w = mbar_wait(&s_done, phase, wait_cycles);
+        if (!w) {
+            if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
+            mbar_wait(&s_done, phase, 4 * wait_cycles);
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // every thread is done with the stage (db sums included); one
+        // decision for the whole CTA
+        ok = __syncthreads_and(w) != 0;
+        if (!ok) break;
+    }
+    if (!first && ok) {
+        // row 32 warp + lane of group g is tap 4g + warp, input channel lane
+        for (int g = 0; g < 3; ++g) {
+            const int t = 4 * g + warp;
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+                "%26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                  "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                  "=r"(r[30]), "=r"(r[31])
+                : "r"(tmem + ((uint32_t)(32 * warp) << 16) + 32u * g));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (t < 9) {
+                float *dst = dW + ((size_t)t * kTcC + lane) * kTcC;
+#pragma unroll
+                for (int co = 0; co < kTcC; ++co) atomicAdd(dst + co, __uint_as_float(r[co]));
+            }
+        }
+        if (db && tid < kTcC) atomicAdd(db + tid, bsum);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kWgCols)
+                     : "memory");
+}
+
 }  // namespace
+
+int cnn_wgrad_tc(const void *X, int N, int H, int W, int dil, const void *dZ, float *dW,
+                 float *db, cudaStream_t stream) {
+    if (dil < 1 || dil > kTcHalo || W < 1 || H < 1 || N < 1)
+        return set_error(FHTDP_EINVAL, "conv3x3 wgrad: dilation 1..8 and a non-empty image");
+    const size_t smem = (size_t)kWgABytes + kWgBBytes;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long units = (long long)N * H * ((W + kWgP - 1) / kWgP);
+    const long long grid = std::min<long long>(units, 2LL * (sms > 0 ? sms : 152));
+    conv3x3_wgrad_tc_kernel<<<(unsigned)grid, kTcThreads, smem, stream>>>(
+        (const __nv_bfloat16 *)X, N, H, W, dil, (const __nv_bfloat16 *)dZ, dW, db,
+        4000000000LL);
+    return launched("conv3x3_wgrad_tc_kernel");
+}
 
 size_t cnn_conv_tc_smem() { return (size_t)kABytes + kBBytes; }
 

@@ -114,6 +114,28 @@ def test_conv_gradients_match_reference(lib):
     assert np.all(dw1.cpu().numpy()[9:] == 0)
 
 
+def test_wgrad_tensor_core_accumulates_over_many_segments(lib):
+    """The tcgen05 weight gradient keeps its accumulators in tensor memory
+    across the row segments a CTA takes (more segments than CTAs), with rows
+    that end inside a segment and a wide dilation."""
+    import torch
+    rng = np.random.default_rng(11)
+    N, H, W, dil = 4, 64, 320, 7
+    x = _bf16(rng.standard_normal((N, H, W, 32)))
+    dz = _bf16(rng.standard_normal((N, H, W, 32)) * 0.5)
+    dw = torch.zeros(9 * 32, 32, device="cuda")
+    db = torch.zeros(32, device="cuda")
+    L = lib.lib()
+    assert L.fhtdp_cnn_status(1) == 0
+    assert L.fhtdp_cnn_conv3x3_wgrad(x.cuda().data_ptr(), 32, N, H, W, dil, dz.cuda().data_ptr(),
+                                     dw.data_ptr(), db.data_ptr(), _stream()) == 0
+    torch.cuda.synchronize()
+    assert L.fhtdp_cnn_status(0) == 0
+    rw, rb = cnn_ref.conv3x3_wgrad(_np(x), _np(dz), dil)
+    assert np.allclose(dw.cpu().numpy().reshape(9, 32, 32), rw, rtol=1e-3, atol=1e-2)
+    assert np.allclose(db.cpu().numpy(), rb, rtol=1e-3, atol=1e-2)
+
+
 def test_band_head_matches_reference(lib):
     import torch
     rng = np.random.default_rng(6)
