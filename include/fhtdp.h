@@ -425,10 +425,10 @@ long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
  *   1. the work-queue schedule: groups of images whose band levels hold about
  *      `target` column tiles and advance together, or band chains (an active
  *      set of about `target` tiles per step that images join, most bands
- *      first, as others finish), with the band heights interleaved (each
- *      height's images joining most bands first) or not, and with images of
- *      256-row bands advancing every step or every second step; widths from
- *      half to six times the SM count and the whole batch;
+ *      first, as others finish), with the images of 256-row bands spread
+ *      evenly through that join order or not, and advancing every step or
+ *      every second step; widths from half to six times the SM count and the
+ *      whole batch;
  *   2. for each band height of uint8 images, the column tile width of its
  *      work items (128, or 256 for bands of at most 64 rows) and the number
  *      of FHT levels done in registers before the shared-memory merges (2 or
@@ -442,7 +442,7 @@ long long fhtdp_batch_items(const fhtdp_batch_plan *plan);
 int fhtdp_batch_autotune(fhtdp_batch_plan *plan, void *ws, int reps, cudaStream_t stream,
                          long long *target_out);
 /* The plan's current choices: the queue schedule (*mode: 0 groups, 1 band
- * chains, 2 band chains with the band heights interleaved, 3 band chains
+ * chains, 2 band chains with the 256-row-band images spread, 3 band chains
  * with 256-row bands every second step, 4 both) and width, and for its images of band height n the column tile
  * width and register FHT depth (0 and 0 when it has none).  Any pointer may
  * be NULL.  The paper has no counterpart (see fhtdp_batch_autotune). */

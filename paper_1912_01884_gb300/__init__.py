@@ -359,16 +359,16 @@ class BatchPlan:
         return t.value
 
     def choice(self, n: int):
-        """The plan's schedule ("groups", "chains", "chains-mixed", "chains-slow256" or
-        "chains-mixed-slow256"), width, and the tile
+        """The plan's schedule ("groups", "chains", "chains-spread256", "chains-slow256" or
+        "chains-spread256-slow256"), width, and the tile
         width and register FHT depth of its images of band height n."""
         mode, target = ctypes.c_int(0), ctypes.c_longlong(0)
         tile, depth = ctypes.c_int(0), ctypes.c_int(0)
         _check(lib().fhtdp_batch_choice(self._plan, int(n), ctypes.byref(mode),
                                         ctypes.byref(target), ctypes.byref(tile),
                                         ctypes.byref(depth)))
-        return {"schedule": ("groups", "chains", "chains-mixed", "chains-slow256",
-                             "chains-mixed-slow256")[mode.value], "width": target.value,
+        return {"schedule": ("groups", "chains", "chains-spread256", "chains-slow256",
+                             "chains-spread256-slow256")[mode.value], "width": target.value,
                 "tile": tile.value, "depth": depth.value}
 
     def configure(self, n: int, tile: int, depth: int, stream=None):

@@ -1925,14 +1925,19 @@ struct U8Ctl {
             c.tile = (int)(off - (b > 0 ? hf : 0));
         }
     }
-    // The next item of the queue whose image is enabled (lane 0 takes it).
-    __device__ static long long take(const LaunchArgs &args) {
+    // The first item from `item` on (an index just taken from the queue)
+    // whose image is enabled, taking more as needed (lane 0).
+    __device__ static long long skip_disabled(const LaunchArgs &args, long long item) {
         for (;;) {
-            const long long item = atomicAdd(&args.ctl->queue, 1);
             if (item >= args.items || !args.many) return item;
             const ImgDesc *im = &args.many[args.order[item].image];
             if (!im->enable || __ldcg(im->enable) != 0) return item;
+            item = atomicAdd(&args.ctl->queue, 1);
         }
+    }
+    // The next item of the queue whose image is enabled (lane 0 takes it).
+    __device__ static long long take(const LaunchArgs &args) {
+        return skip_disabled(args, atomicAdd(&args.ctl->queue, 1));
     }
     __device__ static Ctrl decode(const LaunchArgs &args, long long item) {
         Ctrl c{item, nullptr, 0, 0, 0, 128, kItemBand, false};
@@ -2045,9 +2050,11 @@ struct U8Ctl {
         }
     }
 
-    // Items whose M tile may land while their FHT runs (F beside the V rows).
+    // Items whose M tile may be copied before their FHT ends: F beside the
+    // V rows, or no FHT at all (the DP items of 256-row bands).
     __device__ static bool early_copy(const Ctrl &c) {
-        return c.kind == kItemBand && U8Path<Key, true>::early_m(c.n, c.T);
+        return (c.kind == kItemBand && U8Path<Key, true>::early_m(c.n, c.T)) ||
+               c.kind == kItemDp256;
     }
     // Lane 0, after the FHT: the M tile of the item into the V rows (or just
     // the arrival on the M barrier when it has none).  Half-band items do
@@ -2125,10 +2132,10 @@ struct U8Ctl {
         bool ok = cur.item < args.items ? wait_producers(cur, args, lane) : true;
         bool copied = false;   // cur's M tile is on its way already
         while (cur.item < args.items) {
-            const Ctrl next = decode(args, idx);
             // The V rows are free once the previous item's window maxima are
-            // stored; where F lies beside them the M copy need not wait for
-            // the FHT.
+            // stored; where F lies beside them (or there is no FHT) the M
+            // copy need not wait for the FHT.  The copy goes out before
+            // anything else the control warp does for the item.
             const bool early = early_copy(cur);
             if (early && !copied && lane == 0) {
                 if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
@@ -2139,15 +2146,16 @@ struct U8Ctl {
                 if (!ok) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
                 copy_m_tile(cur, Vn, pipe);
             }
+            const Ctrl next = decode(args, idx);
             nb_sync(kBarHcFree, kCtlSync);
             if (lane == 0) hand_over(next, slot, Hc, pipe);
             nb_arrive(kBarNext, kCtlSync);
-            // The item after next is taken now (its index is used only after
-            // this item's window), so that the queue's round trip overlaps
-            // the polling.  A CTA works its items in queue order, so holding
-            // one more keeps the queue free of deadlock.
+            // The item after next is taken now and its index read only after
+            // this item's window, so that the queue's round trip overlaps the
+            // polling.  A CTA works its items in queue order, so holding one
+            // more keeps the queue free of deadlock.
             long long ahead = 0;
-            if (lane == 0 && next.item < args.items) ahead = take(args);
+            if (lane == 0 && next.item < args.items) ahead = atomicAdd(&args.ctl->queue, 1);
             const bool ready = next.item >= args.items ||
                                poll_producers(next, args, lane, done, cur.item);
             nb_sync(kBarWinDone, kCtlSync);
@@ -2155,7 +2163,10 @@ struct U8Ctl {
             // before this item's publication.
             copied = ready && next.item < args.items && early_copy(next);
             if (copied && lane == 0) copy_m_tile(next, Vn, pipe);
-            if (lane == 0) finish(cur, args);
+            if (lane == 0) {
+                finish(cur, args);
+                if (next.item < args.items) ahead = skip_disabled(args, ahead);
+            }
             idx = __shfl_sync(0xffffffffu, ahead, 0);
             ok = ready || wait_producers(next, args, lane);
             cur = next;
@@ -3301,11 +3312,10 @@ std::vector<Item> queue_grouped(const std::vector<ImgPlan> &imgs, long long targ
 // whenever its width (tiles per step) drops below `target`, so that steps
 // keep about the same width while images of different heights finish at
 // different times, and the longest chains start with the batch.
-// With `mixed`, the images of each band height join in that order (longest
-// chains first), but the band heights are interleaved in proportion to their
-// image counts, so that every step holds a mix of them: the images with the
-// fewest and heaviest bands (256 rows: nine producer tiles per DP item) do
-// not all end up in the last steps, waiting on one another.
+// With `mixed`, the images of 256-row bands (at most 16 bands, but heavy DP
+// items that wait for nine producer tiles each) are spread evenly through
+// the join order of the others (which stays longest chain first), so that
+// they do not all end up in the last steps, waiting on one another.
 // With `slow256`, images of 256-row bands advance one level every second
 // step: a DP item of such a band waits for nine DP items of the band below,
 // which are then two steps ahead of it in the queue.
@@ -3317,18 +3327,14 @@ std::vector<Item> queue_chains(const std::vector<ImgPlan> &imgs, long long targe
     std::stable_sort(by_k.begin(), by_k.end(),
                      [&](int a, int b) { return imgs[a].s.k > imgs[b].s.k; });
     if (mixed) {
-        // rank of each image within its band height, as a fraction of the
-        // height's image count
+        // rank of each image within its group (256-row bands or the others),
+        // as a fraction of the group's size
         std::vector<double> key(imgs.size());
-        std::vector<int> heights;
-        for (const ImgPlan &p : imgs)
-            if (std::find(heights.begin(), heights.end(), p.s.n) == heights.end())
-                heights.push_back(p.s.n);
-        for (int n : heights) {
+        for (int heavy = 0; heavy < 2; ++heavy) {
             int count = 0, rank = 0;
-            for (int i : by_k) count += imgs[i].s.n == n;
+            for (int i : by_k) count += (imgs[i].kind == 1) == (heavy == 1);
             for (int i : by_k)
-                if (imgs[i].s.n == n) key[i] = (rank++ + 0.5) / count;
+                if ((imgs[i].kind == 1) == (heavy == 1)) key[i] = (rank++ + 0.5) / count;
         }
         std::stable_sort(by_k.begin(), by_k.end(), [&](int a, int b) { return key[a] < key[b]; });
     }
@@ -3369,8 +3375,9 @@ std::vector<Item> queue_chains(const std::vector<ImgPlan> &imgs, long long targe
 
 // The queue order of a schedule: 0 groups of images advancing together
 // (queue_grouped); band chains joining as others finish, longest first
-// (queue_chains): 1 as they are, 2 with the band heights interleaved, 3 with
-// 256-row bands advancing every second step, 4 both.
+// (queue_chains): 1 as they are, 2 with the images of 256-row bands spread
+// through the join order, 3 with 256-row bands advancing every second step,
+// 4 both.
 constexpr int kSchedules = 5;
 std::vector<Item> queue_order(const std::vector<ImgPlan> &imgs, long long target, int mode) {
     return mode ? queue_chains(imgs, target, mode == 2 || mode == 4, mode >= 3)
