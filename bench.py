@@ -86,9 +86,9 @@ EXTRAS = ("plain2048", "float8192")
 # traffic is this times its pixels.  None where no capture of the current
 # kernel exists (reset whenever the kernel changes until it is captured again).
 NCU_TRAFFIC_BYTES_PER_PIXEL = {
-    "mixed": None,        # engine_kernel_u8 changed (control warp) since its capture
-    "plain2048": None,
-    "float8192": None,    # engine_kernel_wide changed (strip prefetch) since its capture
+    "mixed": 15.0235e9 / 1064894464,     # engine_kernel_u8<int, 1>: 4.463 + 10.560 GB
+    "plain2048": 1.2498e9 / 134217728,   # engine_kernel_u8<int, 0>: 0.220 + 1.029 GB
+    "float8192": 1.2906e9 / 67108864,    # engine_kernel_wide: 0.275 + 1.015 GB
 }
 # DRAM bytes of one dp_band_window_kernel band launch on the 2048x2048, k = 16
 # workloads (profiles/dp_band_window_kernel_angle2048.md).
