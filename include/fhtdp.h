@@ -455,6 +455,17 @@ int fhtdp_batch_choice(const fhtdp_batch_plan *plan, int n, int *mode, long long
  * workspace `ws`.  The paper has no counterpart (see fhtdp_batch_autotune). */
 int fhtdp_batch_configure(fhtdp_batch_plan *plan, void *ws, int n, int tile, int depth,
                           cudaStream_t stream);
+/* Sec. 2.3, Eqs. 6-7 (main problem step 2): the plan's runs take the
+ * bend-angle windows of gamma (radians, >= 0) instead of the images' integer
+ * bend limits: after a link of displacement d the next one's e satisfies
+ * |atan(e/n) - atan(d/n)| <= gamma (the table of fhtdp_angle_window), and the
+ * polyline read back is the same as fhtdp_polyline_dp_angle +
+ * fhtdp_backtrack_angle give.  The images are the rows already smoothed
+ * (fhtdp_gauss_rows, step 1): int32 or float32, all of one band height n in
+ * 2..128.  Host only (no device work); FHTDP_EINVAL otherwise.  All the
+ * images' band chains then run in one persistent launch: the window maxima
+ * come from maxima of a fixed half-width that cover every window. */
+int fhtdp_batch_angle(fhtdp_batch_plan *plan, double gamma);
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan);
 
 /* ------------------------------------------------------------------------

@@ -94,6 +94,7 @@ _SIGS = {
     "fhtdp_batch_choice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "fhtdp_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 3
                               + [ctypes.c_void_p]),
+    "fhtdp_batch_angle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "fhtdp_angle_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     "fhtdp_gauss_rows": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
                          + [ctypes.c_void_p, ctypes.c_void_p]),
@@ -376,6 +377,12 @@ class BatchPlan:
         height n by hand (the tuner's per-height choices)."""
         _check(lib().fhtdp_batch_configure(self._plan, self.ws.data_ptr(), int(n), int(tile),
                                            int(depth), _stream(stream)))
+
+    def angle(self, gamma: float):
+        """Bend-angle windows of gamma radians for every run of the plan (Sec.
+        2.3): the images must be smoothed rows (gauss_rows), int32 or
+        float32, all of one band height in 2..128."""
+        _check(lib().fhtdp_batch_angle(self._plan, float(gamma)))
 
     def close(self):
         if self._plan:

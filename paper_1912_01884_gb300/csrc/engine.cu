@@ -142,6 +142,13 @@ struct LaunchArgs {
     // Fault injection for tests (fhtdp_debug_inject): the tile (band, tile)
     // of the first image never publishes; -1 disables.
     int skip_band, skip_tile;
+    // int32 / float images, one image: with use_table the bend-angle windows
+    // of Sec. 2.3 (Eqs. 6-7) replace |e - d| <= B, e in [tab.lo[d + n - 1],
+    // tab.hi[d + n - 1]].  The DP items answer them from maxima of fixed
+    // half-width B0 (every window that no end of the displacement range
+    // clips is at least 2 B0 + 1 long), with wpad dead rows above and below V.
+    int use_table, B0, wpad;
+    WindowTable tab;
 };
 
 // ---------------------------------------------------------------------------
@@ -2200,15 +2207,19 @@ struct WideEngine {
         return (size_t)(n < 2 ? 2 : n) * fpitch(n) * 4;
     }
     // Hough rows [2][n][T] (each sign from a 128-byte boundary, as TMA
-    // destinations are), then V [kWPad + D + kWPad][T]: the M tile lands in
-    // its D middle rows and V is formed there in place; the pad rows hold
-    // dead values, so that the window reads past [-(n-1), n-1] unchecked.
+    // destinations are), then V [wpad + D + wpad][T]: the M tile lands in its
+    // D middle rows and V is formed there in place; the pad rows hold dead
+    // values, so that the window reads past [-(n-1), n-1] unchecked.  With a
+    // window table, the centred maxima Mc [D + 2 wpad][T] follow.
     __host__ __device__ static int dp_sign1(int n) { return (n * kWTileD + 31) & ~31; }
-    __host__ __device__ static size_t dp_smem(int n) {
-        return (size_t)(2 * dp_sign1(n) + (2 * n - 1 + 2 * kWPad) * kWTileD) * 4;
+    __host__ __device__ static size_t dp_mc_off(int n, int wpad) {
+        return (size_t)(2 * dp_sign1(n) + (2 * n - 1 + 2 * wpad) * kWTileD) * 4;
     }
-    static size_t smem_bytes(int max_n) {
-        return std::max(fht_smem(max_n), dp_smem(max_n));
+    __host__ __device__ static size_t dp_smem(int n, int wpad, bool table) {
+        return dp_mc_off(n, wpad) + (table ? (size_t)(2 * n - 1 + 2 * wpad) * kWTileD * 4 : 0);
+    }
+    static size_t smem_bytes(int max_n, int wpad, bool table) {
+        return std::max(fht_smem(max_n), dp_smem(max_n, wpad, table));
     }
     __device__ static Acc *hw_row(const ImgDesc &im, int band, int sign, int s) {
         return (Acc *)im.hw + (((size_t)band * 2 + sign) * im.n + s) * im.hwpitch;
@@ -2406,10 +2417,11 @@ struct WideEngine {
                                    Pipe &pipe, const LaunchArgs &args) {
         const int n = im.n, D = 2 * n - 1, T = kWTileD, x0 = tile * T;
         const bool last = band == im.k - 1;
+        const int wpad = args.wpad;
         Acc *Ht = (Acc *)smem;          // [2][n][T]: Hough rows of both signs
         const int h1 = dp_sign1(n);     // offset of sign 1
-        Acc *Vt = Ht + 2 * h1;          // [kWPad + D + kWPad][T]: M tile, then V
-        Acc *Mt = Vt + kWPad * T;       // row e + n - 1: displacement e
+        Acc *Vt = Ht + 2 * h1;          // [wpad + D + wpad][T]: M tile, then V
+        Acc *Mt = Vt + wpad * T;        // row e + n - 1: displacement e
         const Acc dead = Dead<Acc>::value();
         if (threadIdx.x < 32) {
             // M(x + d, d): band+1 tiles over [x0 - (n-1), x0 + T + n - 2] (lanes
@@ -2442,9 +2454,9 @@ struct WideEngine {
             }
         } else if (band != 0) {
             // the dead pad rows (outside the copies' destinations)
-            for (int idx = threadIdx.x - 32; idx < 2 * kWPad * (T / 4); idx += NT - 32) {
+            for (int idx = threadIdx.x - 32; idx < 2 * wpad * (T / 4); idx += NT - 32) {
                 const int r = idx / (T / 4), u0 = 4 * (idx % (T / 4));
-                const int row = r < kWPad ? r : r + D;
+                const int row = r < wpad ? r : r + D;
                 *(uint4 *)&Vt[row * T + u0] =
                     make_uint4(to_bits(dead), to_bits(dead), to_bits(dead), to_bits(dead));
             }
@@ -2507,33 +2519,77 @@ struct WideEngine {
         // 16 threads per column, 16 displacements each.
         const int u = threadIdx.x & (T - 1), q = threadIdx.x / T;
         const int x = x0 + u;
-        const int lo = -(n - 1), hi = n - 1, B = im.B;
-        const int c0 = lo + 16 * q;
-        if (x < im.w && c0 <= hi) {
-            const Acc *col = Mt + (n - 1) * T + u;   // V(e) at col[e * T]
-            Acc *mcol = mband(im, band) + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
-            const int count = min(16, hi - c0 + 1);
-            auto emit = [&](int i, Acc m) { mcol[(long long)i * (im.mpitch - 1)] = m; };
-            // Runs of NOUT outputs, NOUT the largest power of two up to 16 that
-            // the window length L = 2B + 1 covers (one block pair per run).
-            auto runs = [&](auto nout, auto vkey) {
+        const int lo = -(n - 1), hi = n - 1;
+        const int B = args.use_table ? args.B0 : im.B;
+        const Acc *col = Mt + (n - 1) * T + u;   // V(e) at col[e * T]
+        // Runs of NOUT outputs from c0 (count of them) of the maxima over
+        // [c - B, c + B], NOUT the largest power of two up to 16 that the
+        // window length L = 2B + 1 covers (one block pair per run).
+        auto maxima = [&](int c0, int count, auto vkey, auto emit) {
+            auto runs = [&](auto nout) {
                 constexpr int NOUT = decltype(nout)::value;
                 for (int r0 = 0; r0 < count; r0 += NOUT)
                     window_span<NOUT, Acc>(c0 + r0, count - r0, B, dead, vkey,
                                            [&](int i, Acc m) { emit(r0 + i, m); });
             };
-            auto pick = [&](auto vkey) {
+            const int L = 2 * B + 1;
+            if (L >= 16) runs(std::integral_constant<int, 16>());
+            else if (L >= 8) runs(std::integral_constant<int, 8>());
+            else if (L >= 4) runs(std::integral_constant<int, 4>());
+            else if (L >= 2) runs(std::integral_constant<int, 2>());
+            else runs(std::integral_constant<int, 1>());
+        };
+        auto vpad = [&](int e) -> Acc { return col[e * T]; };   // dead pad rows outside
+        const int c0 = lo + 16 * q;
+        if (!args.use_table) {
+            if (x < im.w && c0 <= hi) {
+                Acc *mcol = mband(im, band) + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
+                const int count = min(16, hi - c0 + 1);
+                auto emit = [&](int i, Acc m) { mcol[(long long)i * (im.mpitch - 1)] = m; };
+                // A run reads V over [c - B, c + B + 16]: inside the pad rows
+                // when B + 16 <= wpad.
+                if (B + 16 <= wpad) maxima(c0, count, vpad, emit);
+                else
+                    maxima(c0, count,
+                           [&](int e) -> Acc { return (e < lo || e > hi) ? dead : col[e * T]; },
+                           emit);
+            }
+        } else {
+            // Bend-angle windows (Sec. 2.3): the centred maxima Mc(p) over
+            // [p - B0, p + B0] for p in [-(n-1) - B0, n-1 + B0] (they read V
+            // over [-(n-1) - 2 B0, n-1 + 2 B0 + 16], inside the pad rows),
+            // then each window [lo(c), hi(c)] as the maximum of the pieces
+            // that cover it: centres lo + B0, lo + B0 + L, ... and hi - B0.  A
+            // window shorter than L = 2 B0 + 1 is cut by an end of the range:
+            // the piece from its other end reaches only dead rows beyond it.
+            Acc *Mc = (Acc *)(smem + dp_mc_off(n, wpad)) + u;   // row p + (n-1) + B0
+            const int NC = D + 2 * B;
+            for (int i0 = 16 * q; i0 < NC; i0 += 16 * (NT / T))
+                maxima(i0 - (n - 1) - B, min(16, NC - i0), vpad,
+                       [&](int i, Acc m) { Mc[(size_t)(i0 + i) * T] = m; });
+            csync<NT>();
+            if (x < im.w && c0 <= hi) {
+                Acc *mcol = mband(im, band) + (size_t)(c0 + n - 1) * im.mpitch + im.moff + x - c0;
+                const int count = min(16, hi - c0 + 1);
                 const int L = 2 * B + 1;
-                if (L >= 16) runs(std::integral_constant<int, 16>(), vkey);
-                else if (L >= 8) runs(std::integral_constant<int, 8>(), vkey);
-                else if (L >= 4) runs(std::integral_constant<int, 4>(), vkey);
-                else if (L >= 2) runs(std::integral_constant<int, 2>(), vkey);
-                else runs(std::integral_constant<int, 1>(), vkey);
-            };
-            // A run reads V over [c - B, c + B + 16]: inside the pad rows when
-            // B + 16 <= kWPad.
-            if (B + 16 <= kWPad) pick([&](int e) -> Acc { return col[e * T]; });
-            else pick([&](int e) -> Acc { return (e < lo || e > hi) ? dead : col[e * T]; });
+                auto mc = [&](int p) -> Acc { return Mc[(size_t)(p + n - 1 + B) * T]; };
+                for (int i = 0; i < count; ++i) {
+                    const int c = c0 + i;
+                    const int wl = args.tab.lo[c + n - 1], wh = args.tab.hi[c + n - 1];
+                    Acc m = dead;
+                    if (wh - wl + 1 >= L) {
+                        for (int p = wl + B; p < wh - B; p += L) m = kmax(m, mc(p));
+                        m = kmax(m, mc(wh - B));
+                    } else if (wh == hi) {
+                        m = mc(wl + B);
+                    } else if (wl == lo) {
+                        m = mc(wh - B);
+                    } else {   // not produced by the host's choice of B0; kept exact
+                        for (int e = wl; e <= wh; ++e) m = kmax(m, col[e * T]);
+                    }
+                    mcol[(long long)i * (im.mpitch - 1)] = m;
+                }
+            }
         }
         fence_acq_rel_gpu();
         csync<NT>();
@@ -2585,17 +2641,18 @@ struct WideEngine {
                 if (lane == 0) atomicExch(&args.ctl->status, FHTDP_ETIMEOUT);
                 return;
             }
-            const int lo = max(-(n - 1), d - im.B), hi = min(n - 1, d + im.B);
+            const int lo = args.use_table ? args.tab.lo[d + n - 1] : max(-(n - 1), d - im.B);
+            const int hi = args.use_table ? args.tab.hi[d + n - 1] : min(n - 1, d + im.B);
             const Acc *mb = i + 1 < im.k ? mband(im, i + 1) : nullptr;
             unsigned long long bk = 0;
             for (int e = lo + lane; e <= hi; e += 32) {
                 const int sh = e < 0 ? -e : e;
-                const Acc h = from_bits<Acc>(__ldcg((const uint32_t *)hw_row(im, i, e < 0, sh) + xx));
-                Acc v = h;
-                if (mb) {
-                    if (xx + e < 0 || xx + e >= im.w) {
-                        v = dead;
-                    } else {
+                Acc v = dead;   // the link must end inside the image (every band)
+                if (xx + e >= 0 && xx + e < im.w) {
+                    const Acc h =
+                        from_bits<Acc>(__ldcg((const uint32_t *)hw_row(im, i, e < 0, sh) + xx));
+                    v = h;
+                    if (mb) {
                         // M_{i+1}(xx + e, e): row e + n - 1, skewed column moff + xx
                         const Acc m = from_bits<Acc>(__ldcg(
                             (const uint32_t *)mb + (size_t)(e + n - 1) * im.mpitch + im.moff + xx));
@@ -3070,7 +3127,7 @@ int num_sms() {
 template <typename In, typename Acc>
 int launch_kernel_wide(const LaunchArgs &args, int max_n, cudaStream_t stream) {
     using P = WideEngine<In, Acc, long long>;
-    const size_t smem = P::smem_bytes(max_n);
+    const size_t smem = P::smem_bytes(max_n, args.wpad, args.use_table != 0);
     auto kern = engine_kernel_wide<In, Acc, long long>;
     int st = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem),
@@ -3139,6 +3196,7 @@ LaunchArgs base_args(const RunLayout &L, char *ws, int count) {
     args.wait_cycles = 4000000000LL;   // about two seconds at GB300 clocks
     args.skip_band = -1;
     args.skip_tile = -1;
+    args.wpad = kWPad;
     consume_injection(&args);
     return args;
 }
@@ -3223,6 +3281,8 @@ struct BatchPlan {
     void *bound_ws = nullptr;
     long long target = 0;           // queue width (tiles per band level or step)
     int mode = 0;                   // queue schedule, see queue_order
+    bool use_table = false;         // bend-angle windows (fhtdp_batch_angle)
+    WindowTable tab{};
     size_t reserve = 0;             // bytes of the fused part for any tile-width choice
     size_t ws_total = 0;            // workspace bytes (the reserve and the side lanes)
     ~BatchPlan() {
@@ -3416,6 +3476,54 @@ int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, 
     return dispatch(dtype, L.max_h, args, L.max_n, L.multi_tile, stream);
 }
 
+// The window table's cover in the DP items: the shortest window that no end
+// of the range clips (else the shortest of all), made odd, is 2 B0 + 1; every
+// window at least as long is covered by pieces of that length, every shorter
+// one is clipped.  The centred maxima read V up to 2 B0 + 16 rows beyond the
+// range, so the dead pad holds that many rows (even, for the copies' 128-byte
+// alignment).
+void set_table(LaunchArgs &args, const WindowTable &t) {
+    const int n = t.n, D = 2 * n - 1;
+    int L0 = D, L0c = D;
+    bool any = false;
+    for (int i = 0; i < D; ++i) {
+        const int len = t.hi[i] - t.lo[i] + 1;
+        L0c = std::min(L0c, len);
+        if (t.lo[i] > -(n - 1) && t.hi[i] < n - 1) {
+            L0 = any ? std::min(L0, len) : len;
+            any = true;
+        }
+    }
+    if (!any) L0 = L0c;
+    if (L0 < 1) L0 = 1;
+    const int Lp = L0 % 2 ? L0 : L0 - 1;
+    args.use_table = 1;
+    args.tab = t;
+    args.B0 = (Lp - 1) / 2;
+    args.wpad = std::max(kWPad, (2 * args.B0 + 16 + 1) & ~1);
+}
+
+// One int32 / float image with the bend-angle windows of table t (bands of 2
+// to 128 rows): the persistent engine with window-table DP items.
+int engine_detect_table(const void *img, int dtype, int pitch, const Shape &s,
+                        const WindowTable &t, int32_t *x_out, int32_t *d_out, void *score_out,
+                        void *ws, cudaStream_t stream) {
+    if (dtype == FHTDP_U8 || s.n < 2 || s.n > kMaxBandFused || t.n != s.n)
+        return set_error(FHTDP_EINVAL, "window-table engine: int32 / float, bands of 2..128 rows");
+    std::vector<ImgPlan> one{single_plan(dtype, img, pitch, s, 2 * s.n - 2, x_out, d_out,
+                                         score_out)};
+    RunLayout L = plan_layout(one, false);
+    char *base = (char *)ws;
+    int st = cuda_status(cudaMemsetAsync(base, 0, L.zero_bytes, stream), "cudaMemsetAsync");
+    if (st) return st;
+    LaunchArgs args = base_args(L, base, 1);
+    args.one = make_desc(one[0], L, base, dtype);
+    args.many = nullptr;
+    args.order = nullptr;
+    set_table(args, t);
+    return dispatch(dtype, L.max_h, args, L.max_n, false, stream);
+}
+
 int engine_status(const void *ws, cudaStream_t stream) {
     int status = 0;
     int st = cuda_status(cudaMemcpyAsync(&status, (const char *)ws + offsetof(Ctl, status),
@@ -3561,6 +3669,7 @@ int batch_run(const BatchPlan *plan, void *ws, cudaStream_t stream) {
         LaunchArgs args = base_args(plan->L, base, (int)plan->imgs.size());
         args.many = (const ImgDesc *)(base + plan->L.table_off);
         args.order = (const Item *)(base + plan->L.order_off);
+        if (plan->use_table) set_table(args, plan->tab);
         st = dispatch(plan->dtype, plan->L.max_h, args, plan->L.max_n, plan->L.multi_tile, stream);
     }
     // Join the lanes back (also after an error, so that `stream` never runs
@@ -3767,6 +3876,23 @@ void batch_set_enable(BatchPlan *plan, const int32_t *enable) {
 }
 
 int batch_separate_count(const BatchPlan *plan) { return (int)plan->separate.size(); }
+
+int batch_angle(BatchPlan *plan, double gamma) {
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    if (plan->dtype == FHTDP_U8 || !plan->separate.empty() || plan->imgs.empty())
+        return set_error(FHTDP_EINVAL,
+                         "bend-angle batches: int32 / float images with bands of 2..128 rows");
+    const int n = plan->imgs[0].s.n;
+    for (const ImgPlan &p : plan->imgs)
+        if (p.s.n != n || p.kind != 2 || n < 2)
+            return set_error(FHTDP_EINVAL,
+                             "bend-angle batches: one band height of 2..128 rows for all images");
+    WindowTable t;
+    if (!make_angle_table(n, gamma, &t)) return set_error(FHTDP_EINVAL, "gamma must be >= 0");
+    plan->tab = t;
+    plan->use_table = true;
+    return FHTDP_OK;
+}
 
 void batch_destroy(BatchPlan *plan) { delete plan; }
 

@@ -22,7 +22,11 @@ void batch_destroy(BatchPlan *plan);
 void debug_inject(int band, int tile, long long wait_cycles);
 void batch_set_enable(BatchPlan *plan, const int32_t *enable);
 int batch_separate_count(const BatchPlan *plan);
+int batch_angle(BatchPlan *plan, double gamma);
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                   int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream);
+int engine_detect_table(const void *img, int dtype, int pitch, const Shape &s,
+                        const WindowTable &t, int32_t *x_out, int32_t *d_out, void *score_out,
+                        void *ws, cudaStream_t stream);
 
 }  // namespace fhtdp

@@ -179,3 +179,86 @@ def test_detect_angle_rejects_bad_arguments_on_device(lib):
     with pytest.raises(lib.FhtdpError) as e:
         lib.detect_polyline_angle(img, 4, 2, 0.3, ws=small)
     assert e.value.code == 2
+
+
+# ---------------------------------------------------------------------------
+# The main problem for a batch in one persistent launch (fhtdp_batch_angle):
+# rows smoothed by fhtdp_gauss_rows, then the engine with the window table.
+
+BATCH_CASES = [
+    # (band height n, [(h, w)...], k from h / n)
+    (128, [(256, 256), (512, 300), (2048, 130), (1024, 517)]),
+    (64, [(64, 37), (256, 1), (192, 700), (128, 129)]),
+    (16, [(16, 5), (64, 77), (48, 1000)]),
+    (2, [(8, 3), (4, 40)]),
+]
+
+
+def _batch_angle(lib, imgs, n, r, gamma, tune=False):
+    import torch
+    sm = [lib.gauss_rows(to_device(im), r) for im in imgs]
+    ks = [im.shape[0] // n for im in imgs]
+    plan = lib.BatchPlan(sm, ks, [2 * n - 2] * len(imgs))
+    plan.angle(gamma)
+    if tune:
+        plan.autotune(reps=1)
+    plan.run()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    return plan
+
+
+@pytest.mark.parametrize("case", range(len(BATCH_CASES)))
+@pytest.mark.parametrize("gamma", GAMMAS)
+def test_batch_angle_int32_matches_oracle(lib, case, gamma):
+    n, shapes = BATCH_CASES[case]
+    imgs = [_img(h, w, "i32", 7 * h + w + case) for h, w in shapes]
+    plan = _batch_angle(lib, imgs, n, 1, gamma)
+    for i, im in enumerate(imgs):
+        xo, do, so = oracle.detect_angle(im, im.shape[0] // n, 1, gamma)
+        assert list(plan.x[i].cpu().numpy()) == list(xo), (i, gamma)
+        assert list(plan.d[i].cpu().numpy()) == list(do), (i, gamma)
+        assert int(plan.score[i].cpu().numpy().reshape(-1)[0]) == int(so)
+
+
+@pytest.mark.parametrize("case", range(len(BATCH_CASES)))
+def test_batch_angle_float_matches_oracle(lib, case):
+    n, shapes = BATCH_CASES[case]
+    rng = np.random.default_rng(case)
+    imgs = [(np.abs(rng.standard_normal((h, w))) * 2.5).astype(np.float32) for h, w in shapes]
+    for gamma in (0.1, math.radians(10), 0.8):
+        plan = _batch_angle(lib, imgs, n, 2, gamma)
+        for i, im in enumerate(imgs):
+            xo, do, so = oracle.detect_angle_f32(im, im.shape[0] // n, 2, gamma)
+            assert list(plan.x[i].cpu().numpy()) == list(xo), (i, gamma)
+            assert list(plan.d[i].cpu().numpy()) == list(do), (i, gamma)
+            s = float(plan.score[i].cpu().numpy().reshape(-1)[0])
+            assert abs(s - so) <= 1e-5 * abs(so)
+
+
+def test_batch_angle_2048x2048_tuned_full_size(lib):
+    """The bench's main-problem batch shape (bent edges, r = 2, 10 degrees),
+    tuned, against the oracle on every image."""
+    imgs = [synth.bent_edges(s).img for s in range(4)]
+    plan = _batch_angle(lib, imgs, 128, 2, math.radians(10), tune=True)
+    for i, im in enumerate(imgs):
+        xo, do, so = oracle.detect_angle(im, 16, 2, math.radians(10))
+        assert list(plan.x[i].cpu().numpy()) == list(xo)
+        assert list(plan.d[i].cpu().numpy()) == list(do)
+        assert int(plan.score[i].cpu().numpy().reshape(-1)[0]) == int(so)
+
+
+def test_batch_angle_rejects_mixed_heights_and_uint8(lib):
+    import torch
+    a = torch.zeros((64, 40), dtype=torch.int32, device="cuda")
+    b = torch.zeros((128, 40), dtype=torch.int32, device="cuda")
+    plan = lib.BatchPlan([a, b], [4, 4], [2, 2])   # band heights 16 and 32
+    with pytest.raises(lib.FhtdpError):
+        plan.angle(0.2)
+    u = torch.zeros((64, 40), dtype=torch.uint8, device="cuda")
+    plan = lib.BatchPlan([u], [4], [2])
+    with pytest.raises(lib.FhtdpError):
+        plan.angle(0.2)
+    plan = lib.BatchPlan([a], [4], [2])
+    with pytest.raises(lib.FhtdpError):
+        plan.angle(-1.0)
