@@ -95,6 +95,7 @@ _SIGS = {
     "fhtdp_batch_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 3
                               + [ctypes.c_void_p]),
     "fhtdp_batch_angle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "fhtdp_batch_points": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "fhtdp_angle_window": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     "fhtdp_gauss_rows": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5
                          + [ctypes.c_void_p, ctypes.c_void_p]),
@@ -377,6 +378,16 @@ class BatchPlan:
         height n by hand (the tuner's per-height choices)."""
         _check(lib().fhtdp_batch_configure(self._plan, self.ws.data_ptr(), int(n), int(tile),
                                            int(depth), _stream(stream)))
+
+    def points(self, points, stream=None):
+        """Through-point queries (Subproblems 2-3): points[i] = (border j,
+        column xp) for image i, or None for no restriction (uint8 images with
+        bands of at most 128 rows)."""
+        arr = (ctypes.c_int32 * (2 * len(self.images)))()
+        for i, pt in enumerate(points):
+            arr[2 * i], arr[2 * i + 1] = (-1, 0) if pt is None else (int(pt[0]), int(pt[1]))
+        _check(lib().fhtdp_batch_points(self._plan, self.ws.data_ptr(),
+                                        ctypes.cast(arr, ctypes.c_void_p), _stream(stream)))
 
     def angle(self, gamma: float):
         """Bend-angle windows of gamma radians for every run of the plan (Sec.

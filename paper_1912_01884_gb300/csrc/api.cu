@@ -615,6 +615,13 @@ int fhtdp_batch_configure(fhtdp_batch_plan *plan, void *ws, int n, int tile, int
     return batch_configure(plan->impl, ws, n, tile, depth, stream);
 }
 
+int fhtdp_batch_points(fhtdp_batch_plan *plan, void *ws, const int32_t *points,
+                       cudaStream_t stream) {
+    g_last_error[0] = 0;
+    if (!plan) return set_error(FHTDP_EINVAL, "null plan");
+    return batch_points(plan->impl, ws, points, stream);
+}
+
 int fhtdp_batch_angle(fhtdp_batch_plan *plan, double gamma) {
     g_last_error[0] = 0;
     if (!plan) return set_error(FHTDP_EINVAL, "null plan");

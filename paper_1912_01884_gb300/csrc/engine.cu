@@ -108,6 +108,12 @@ struct ImgDesc {
     // image is skipped (the learned proposal's fallback run only redoes the
     // images that need the full DP).
     const int32_t *enable;
+    // Subproblems 2-3 (uint8 images, bands of at most 128 rows): when mask1 >
+    // 0, every state of band mask1 - 1 whose vertex on the point's border is
+    // not mask_x is dead: the link's start x (mask_end = 0, the point on the
+    // band's upper border) or its end x + d (mask_end = 1, the image's bottom
+    // border).
+    int mask1, mask_x, mask_end;
 };
 
 // Backpointers: per band, ceil(D/4) groups of w 32-bit words; byte (e & 3)
@@ -1458,7 +1464,8 @@ struct U8Path {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int x = xp + j;
-                const bool ok = x < im.w && x + s < im.w && s >= wlo && s <= whi;
+                bool ok = x < im.w && x + s < im.w && s >= wlo && s <= whi;
+                if (band + 1 == im.mask1) ok = ok && (im.mask_end ? x + s : x) == im.mask_x;
                 // A window maximum below zero marks a dead continuation
                 // (uint8 sums are never negative).
                 const int m = mval(mps[j]);
@@ -1466,7 +1473,8 @@ struct U8Path {
                                           : (m < 0 ? dead : (int)(hws[j] & 0xffffu) + m);
                 // "-" half of word j: column x0 + T - 1 - u0 - j, displacement -s.
                 const int xm = x0 + T - 1 - u0 - j;
-                const bool okm = s > 0 && xm < im.w && xm - s >= 0 && -s >= wlo && -s <= whi;
+                bool okm = s > 0 && xm < im.w && xm - s >= 0 && -s >= wlo && -s <= whi;
+                if (band + 1 == im.mask1) okm = okm && (im.mask_end ? xm - s : xm) == im.mask_x;
                 const int mmv = mval(mms[3 - j]);
                 vm[j] = !okm ? dead : last ? (int)(hws[j] >> 16)
                                            : (mmv < 0 ? dead : (int)(hws[j] >> 16) + mmv);
@@ -1549,7 +1557,8 @@ struct U8Path {
         const bool fast = sizeof(Key) == 4 && im.B <= kFastB;
         // Interior tiles (every x - s and x + s of the tile inside the image)
         // of a band without windows need no masks.
-        const bool interior = sizeof(Key) == 4 && band != 0 && !im.win && (msmem || band == im.k - 1) &&
+        const bool interior = sizeof(Key) == 4 && band != 0 && !im.win && band + 1 != im.mask1 &&
+                              (msmem || band == im.k - 1) &&
                               x0 >= n - 1 && x0 + T + n - 2 < im.w;
         unsigned long long best = 0;
         if (T == kTile) {
@@ -2860,6 +2869,7 @@ struct ImgPlan {
     int kind;                   // 1: 256-row bands through half-band and DP items
     int ftiles, hpitch, moff;   // kind 1: half-band tiles, h256 row pitch; M column offset
     const int32_t *enable;      // optional: the image runs only where this reads nonzero
+    int mask1, mask_x, mask_end;   // optional point of Subproblems 2-3 (see ImgDesc)
     long long item0;
     size_t flags, best, done, fflags;   // offsets in the counter region
     size_t m0, m1, bp, h256;            // offsets in the data region
@@ -3097,6 +3107,9 @@ ImgDesc make_desc(const ImgPlan &p, const RunLayout &L, char *ws, int dtype) {
     im.kind = p.kind;
     im.moff = p.moff;
     im.enable = p.enable;
+    im.mask1 = p.mask1;
+    im.mask_x = p.mask_x;
+    im.mask_end = p.mask_end;
     if (p.kind == 1) {
         im.ftiles = p.ftiles;
         im.hpitch = p.hpitch;
@@ -3457,10 +3470,28 @@ size_t engine_workspace_bytes(int dtype, const Shape &s, int B) {
     return plan_layout(one, false).total;
 }
 
+// The point of Subproblems 2-3 on an image's plan: the states of band j whose
+// start is not xp die, or for j = k those of band k-1 whose end is not xp.
+void set_point(ImgPlan &p, int j, int xp) {
+    p.mask1 = (j < p.s.k ? j : p.s.k - 1) + 1;
+    p.mask_x = xp;
+    p.mask_end = j == p.s.k ? 1 : 0;
+}
+
+bool engine_takes_point(int dtype, const Shape &s) {
+    return dtype == FHTDP_U8 && s.n <= kMaxBandFused;
+}
+
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
-                  int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream) {
+                  int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream,
+                  const PointMask *pm) {
     (void)ws_bytes;
     std::vector<ImgPlan> one{single_plan(dtype, img, pitch, s, B, x_out, d_out, score_out)};
+    if (pm) {
+        if (!engine_takes_point(dtype, s) || one[0].kind != 0)
+            return set_error(FHTDP_EINVAL, "the fused engine takes points on uint8 images only");
+        set_point(one[0], pm->j, pm->xp);
+    }
     if (s.n > kMaxBandFused && one[0].kind != 1)
         return run_fallback(img, dtype, pitch, s, B, x_out, d_out, score_out, ws, stream);
     RunLayout L = plan_layout(one, false);
@@ -3876,6 +3907,29 @@ void batch_set_enable(BatchPlan *plan, const int32_t *enable) {
 }
 
 int batch_separate_count(const BatchPlan *plan) { return (int)plan->separate.size(); }
+
+int batch_points(BatchPlan *plan, void *ws, const int32_t *points, cudaStream_t stream) {
+    if (!plan || !points) return set_error(FHTDP_EINVAL, "null plan or points");
+    if (ws != plan->bound_ws)
+        return set_error(FHTDP_EINVAL, "workspace differs from the one given to fhtdp_batch_upload");
+    if (!plan->separate.empty())
+        return set_error(FHTDP_EINVAL, "points: the batch has images outside the fused engine");
+    // The images in the caller's order are the plan's images (none separate).
+    for (size_t i = 0; i < plan->imgs.size(); ++i) {
+        const int j = points[2 * i], xp = points[2 * i + 1];
+        const ImgPlan &p = plan->imgs[i];
+        if (j < 0) continue;
+        if (j > p.s.k || xp < 0 || xp >= p.s.w || p.kind != 0 || plan->dtype != FHTDP_U8)
+            return set_error(FHTDP_EINVAL,
+                             "point %zu: border 0..k, column 0..w-1, uint8 bands of <= 128 rows", i);
+    }
+    for (size_t i = 0; i < plan->imgs.size(); ++i) {
+        ImgPlan &p = plan->imgs[i];
+        p.mask1 = 0;
+        if (points[2 * i] >= 0) set_point(p, points[2 * i], points[2 * i + 1]);
+    }
+    return upload_tables(plan, ws, stream);
+}
 
 int batch_angle(BatchPlan *plan, double gamma) {
     if (!plan) return set_error(FHTDP_EINVAL, "null plan");

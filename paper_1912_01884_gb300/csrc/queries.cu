@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "engine.cuh"
 
 namespace fhtdp {
 
@@ -21,9 +22,16 @@ constexpr size_t kThroughHead = 256;   // the argmax key, cleared by every call
 size_t round_up256(size_t v) { return (v + 255) & ~(size_t)255; }
 }  // namespace
 
-// [head][Hough/V k*2n*W 4-byte values][FHT scratch, same]
+// [head][Hough/V k*2n*W 4-byte values][FHT scratch, same]; uint8 images with
+// bands of at most 128 rows run the through-point query in the fused engine,
+// whose workspace is smaller for all but the narrowest images.
 size_t through_workspace_bytes(const Shape &s) {
-    return kThroughHead + 2 * round_up256((size_t)s.k * 2 * s.n * s.W * 4);
+    size_t need = kThroughHead + 2 * round_up256((size_t)s.k * 2 * s.n * s.W * 4);
+    if (engine_takes_point(FHTDP_U8, s)) {
+        const size_t eng = engine_workspace_bytes(FHTDP_U8, s, 0);
+        if (eng > need) need = eng;
+    }
+    return need;
 }
 
 namespace {
@@ -82,6 +90,11 @@ int detect_two_t(const void *img, int dtype, int pitch, const Shape &s, int B, i
 int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
                    const PointMask &pm, int32_t *x_out, int32_t *d_out, void *score_out,
                    void *ws, cudaStream_t stream) {
+    // uint8 images with bands of at most 128 rows: the fused engine with P's
+    // band masked in its V formation (the same DP as below)
+    if (engine_takes_point(dtype, s))
+        return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws,
+                             through_workspace_bytes(s), stream, &pm);
     if (dtype == FHTDP_F32)
         return detect_through_t<float>(img, dtype, pitch, s, B, &pm, x_out, d_out,
                                        (float *)score_out, ws, stream);

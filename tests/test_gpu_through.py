@@ -107,3 +107,52 @@ def test_through_point_with_bend_angle_2048x2048_full_size(lib):
     x, d, s = lib.detect_through_point_angle(to_device(wl.img), 16, 2, 0.17453292519943295, 8, xp)
     xo, do, so = oracle.detect_angle_through(wl.img, 16, 2, 0.17453292519943295, 8, xp)
     assert list(x.cpu().numpy()) == list(xo) and int(s.cpu().numpy()[0]) == so
+
+
+def test_batch_points_match_oracle(lib):
+    """fhtdp_batch_points: several uint8 images of different shapes in one
+    persistent launch, each with its own point (top border, a middle border,
+    the bottom border) or none, against the oracle image by image; then new
+    points on the same plan."""
+    import torch
+    shapes = [(256, 256, 4), (64, 37, 4), (512, 300, 4), (16, 5, 16), (2048, 130, 16),
+              (96, 77, 3), (1024, 517, 8)]
+    imgs = [_img(h, w, "u8", 31 * h + w) for h, w, _ in shapes]
+    ks = [k for _, _, k in shapes]
+    Bs = [3, 1000, 0, 2, 16, 5, 9]
+    plan = lib.BatchPlan([to_device(im) for im in imgs], ks, Bs)
+    for rnd in range(2):
+        pts = []
+        for i, (h, w, k) in enumerate(shapes):
+            j = [0, k // 2, k, None][(i + rnd) % 4]
+            pts.append(None if j is None else (j, (w * (i + 1 + rnd)) // 7 % w))
+        plan.points(pts)
+        if rnd == 1:
+            plan.autotune(reps=1)
+        plan.run()
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        for i, (im, k, B, pt) in enumerate(zip(imgs, ks, Bs, pts)):
+            x = plan.x[i].cpu().numpy()
+            d = plan.d[i].cpu().numpy()
+            s = int(plan.score[i].cpu().numpy().reshape(-1)[0])
+            if pt is None:
+                xo, do, so = oracle.detect(im, k, B)
+            else:
+                xo, do, so = oracle.detect_through(im, k, B, *pt)
+                assert x[pt[0]] == pt[1]
+            assert list(x) == list(xo) and list(d) == list(do), (rnd, i, pt)
+            assert s == so
+
+
+def test_batch_points_rejects_bad_points(lib):
+    import torch
+    a = torch.zeros((64, 40), dtype=torch.uint8, device="cuda")
+    plan = lib.BatchPlan([a], [4], [2])
+    for bad in [(5, 0), (0, 40), (2, -1)]:
+        with pytest.raises(lib.FhtdpError):
+            plan.points([bad])
+    f = torch.zeros((64, 40), dtype=torch.float32, device="cuda")
+    plan = lib.BatchPlan([f], [4], [2])
+    with pytest.raises(lib.FhtdpError):
+        plan.points([(1, 3)])
