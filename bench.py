@@ -67,6 +67,10 @@ WORKLOADS = {
         desc="Subproblem 3: u8 2048x2048 (the plain2048 images), k=16 bands of 128 rows, bend 16, "
              "the best polyline through one point per image on band border 8",
         images=32, dtype="u8"),
+    "through2048batch": dict(
+        desc="Subproblem 3, batched: the through2048 images and points (u8 2048x2048, k=16, bend "
+             "16, one point per image on band border 8) in one persistent launch "
+             "(fhtdp_batch_points)", images=32, dtype="u8"),
     "horizontal2048": dict(
         desc="mostly horizontal curves: u8 2048x2048 (the plain2048 images transposed), k=16 "
              "vertical strips of 128 columns, bend 16 (each step transposes its images and runs "
@@ -304,7 +308,7 @@ def make_workload(name, images, seed, rank):
     if name == "two2048":
         return [(w.img, w.k, ("two", w.B, TWO_SEPARATION))
                 for w in (synth.plain_gaussian(s) for s in seeds)]
-    if name == "through2048":
+    if name in ("through2048", "through2048batch"):
         return [(w.img, w.k, (w.B, THROUGH_BORDER, through_column(w)))
                 for w in (synth.plain_gaussian(s) for s in seeds)]
     shapes = synth.mixed_batch_shapes(seed * 7919 + rank, images)
@@ -473,6 +477,11 @@ class BatchBench:
         self.views = self._views(self.dbuf)
         self.ks = [k for _, k, _ in self.items]
         self.Bs = [B for _, _, B in self.items]
+        # through-point batches: (B, border, column) per image
+        self.points = None
+        if name == "through2048batch":
+            self.points = [(B[1], B[2]) for B in self.Bs]
+            self.Bs = [B[0] for B in self.Bs]
         self.xs = torch.empty(sum(k + 1 for k in self.ks), dtype=torch.int32, device=dev)
         self.ds = torch.empty(sum(self.ks), dtype=torch.int32, device=dev)
         self.sc = torch.empty(len(self.items), dtype=torch.float32 if self.tdt == torch.float32
@@ -493,6 +502,8 @@ class BatchBench:
         else:
             self.plan = fd.BatchPlan(self.views, self.ks, self.Bs, out=self.outs,
                                      stream=self.stream)
+        if self.points:
+            self.plan.points(self.points, stream=self.stream)
         # Untimed set-up: the library's tuner picks the queue schedule and, per
         # band height, the tile width and register depth.
         self.width = self.plan.autotune(reps=2, stream=self.stream)
@@ -566,6 +577,8 @@ class BatchBench:
             plan2 = self.plan
         else:
             plan2 = fd.BatchPlan(views2, self.ks, self.Bs, out=self.outs, stream=self.stream)
+            if self.points:
+                plan2.points(self.points, stream=self.stream)
             plan2.autotune(reps=1, stream=self.stream)
         plans, bufs, srcs = (self.plan, plan2), (self.dbuf, dbuf2), (self.views, views2)
         copy_stream = torch.cuda.Stream(self.dev)
