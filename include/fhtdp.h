@@ -468,13 +468,14 @@ int fhtdp_batch_configure(fhtdp_batch_plan *plan, void *ws, int n, int tile, int
 int fhtdp_batch_angle(fhtdp_batch_plan *plan, double gamma);
 /* Sec. 2.2-2.3, Subproblems 2-3: the plan's runs find, for image i, the best
  * polyline through the point (points[2i + 1], points[2i] n) on band border
- * points[2i] (0..k; k is the image's bottom border), as
- * fhtdp_detect_through_point does; points[2i] < 0 leaves image i
- * unrestricted.  `points` is host memory read during the call ([count][2]
- * int32, the images in the order given to fhtdp_batch_plan_create).  uint8
- * images with bands of at most 128 rows only (FHTDP_EINVAL otherwise, and for
- * a point outside [0, w) x [0, k]).  Enqueues the upload of the image table
- * into the bound workspace `ws` on `stream`. */
+ * points[2i] (1..k; k is the image's bottom border; a point on the top border
+ * is for fhtdp_detect_through_point), as fhtdp_detect_through_point does;
+ * points[2i] < 0 leaves image i unrestricted.  `points` is host memory read
+ * during the call ([count][2] int32, the images in the order given to
+ * fhtdp_batch_plan_create).  uint8 images with at least two bands of at most
+ * 128 rows only (FHTDP_EINVAL otherwise, and for a point outside [0, w) x
+ * [1, k]).  Enqueues the upload of the image table into the bound workspace
+ * `ws` on `stream`. */
 int fhtdp_batch_points(fhtdp_batch_plan *plan, void *ws, const int32_t *points,
                        cudaStream_t stream);
 void fhtdp_batch_plan_destroy(fhtdp_batch_plan *plan);

@@ -380,9 +380,9 @@ class BatchPlan:
                                            int(depth), _stream(stream)))
 
     def points(self, points, stream=None):
-        """Through-point queries (Subproblems 2-3): points[i] = (border j,
-        column xp) for image i, or None for no restriction (uint8 images with
-        bands of at most 128 rows)."""
+        """Through-point queries (Subproblems 2-3): points[i] = (border j in
+        1..k, column xp) for image i, or None for no restriction (uint8 images
+        with at least two bands of at most 128 rows)."""
         arr = (ctypes.c_int32 * (2 * len(self.images)))()
         for i, pt in enumerate(points):
             arr[2 * i], arr[2 * i + 1] = (-1, 0) if pt is None else (int(pt[0]), int(pt[1]))

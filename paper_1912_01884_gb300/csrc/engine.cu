@@ -1464,8 +1464,7 @@ struct U8Path {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int x = xp + j;
-                bool ok = x < im.w && x + s < im.w && s >= wlo && s <= whi;
-                if (band + 1 == im.mask1) ok = ok && (im.mask_end ? x + s : x) == im.mask_x;
+                const bool ok = x < im.w && x + s < im.w && s >= wlo && s <= whi;
                 // A window maximum below zero marks a dead continuation
                 // (uint8 sums are never negative).
                 const int m = mval(mps[j]);
@@ -1473,8 +1472,7 @@ struct U8Path {
                                           : (m < 0 ? dead : (int)(hws[j] & 0xffffu) + m);
                 // "-" half of word j: column x0 + T - 1 - u0 - j, displacement -s.
                 const int xm = x0 + T - 1 - u0 - j;
-                bool okm = s > 0 && xm < im.w && xm - s >= 0 && -s >= wlo && -s <= whi;
-                if (band + 1 == im.mask1) okm = okm && (im.mask_end ? xm - s : xm) == im.mask_x;
+                const bool okm = s > 0 && xm < im.w && xm - s >= 0 && -s >= wlo && -s <= whi;
                 const int mmv = mval(mms[3 - j]);
                 vm[j] = !okm ? dead : last ? (int)(hws[j] >> 16)
                                            : (mmv < 0 ? dead : (int)(hws[j] >> 16) + mmv);
@@ -1511,6 +1509,21 @@ struct U8Path {
         }
         }
         return best;
+    }
+
+    // Subproblems 2-3: the states of the point's band whose vertex on the
+    // point's border is not mask_x become dead (their link's start x, or for
+    // the image's bottom border its end x + e), in V once it is formed: the
+    // same restriction as the standalone point mask.
+    template <int T>
+    __device__ static void mask_point(int32_t *Vn, const ImgDesc &im, int x0) {
+        const int n = im.n, D = 2 * n - 1;
+        for (int idx = threadIdx.x; idx < D * T; idx += kThreads) {
+            const int ei = idx / T, u = idx - ei * T;
+            const int x = x0 + u;
+            if ((im.mask_end ? x + ei - (n - 1) : x) != im.mask_x)
+                Vn[vat<T>(n, ei + kPad, u)] = INT32_MIN;   // dead in keys and in values
+        }
     }
 
     // Thread 0: takes the next work item and, when its strip can go to Hc
@@ -1557,7 +1570,7 @@ struct U8Path {
         const bool fast = sizeof(Key) == 4 && im.B <= kFastB;
         // Interior tiles (every x - s and x + s of the tile inside the image)
         // of a band without windows need no masks.
-        const bool interior = sizeof(Key) == 4 && band != 0 && !im.win && band + 1 != im.mask1 &&
+        const bool interior = sizeof(Key) == 4 && band != 0 && !im.win &&
                               (msmem || band == im.k - 1) &&
                               x0 >= n - 1 && x0 + T + n - 2 < im.w;
         unsigned long long best = 0;
@@ -1581,6 +1594,11 @@ struct U8Path {
             return;
         }
         csync();
+        if (band + 1 == im.mask1) {   // the through-point band (never band 0)
+            if (T == kTile) mask_point<kTile>(Vn, im, x0);
+            else mask_point<2 * kTile>(Vn, im, x0);
+            csync();
+        }
         // Hc is free from here on unless the window reads S from it.
         if (fast) nb_arrive(kBarHcFree, kCtlSync);
 
@@ -3478,8 +3496,11 @@ void set_point(ImgPlan &p, int j, int xp) {
     p.mask_end = j == p.s.k ? 1 : 0;
 }
 
-bool engine_takes_point(int dtype, const Shape &s) {
-    return dtype == FHTDP_U8 && s.n <= kMaxBandFused;
+// The fused engine masks the point's band in V after forming it, which band
+// 0 never stores: points on borders 1..k of uint8 images with at least two
+// bands of at most 128 rows.
+bool engine_takes_point(int dtype, const Shape &s, int j) {
+    return dtype == FHTDP_U8 && s.n <= kMaxBandFused && s.k >= 2 && j >= 1;
 }
 
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
@@ -3488,7 +3509,7 @@ int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, 
     (void)ws_bytes;
     std::vector<ImgPlan> one{single_plan(dtype, img, pitch, s, B, x_out, d_out, score_out)};
     if (pm) {
-        if (!engine_takes_point(dtype, s) || one[0].kind != 0)
+        if (!engine_takes_point(dtype, s, pm->j) || one[0].kind != 0)
             return set_error(FHTDP_EINVAL, "the fused engine takes points on uint8 images only");
         set_point(one[0], pm->j, pm->xp);
     }
@@ -3919,9 +3940,11 @@ int batch_points(BatchPlan *plan, void *ws, const int32_t *points, cudaStream_t 
         const int j = points[2 * i], xp = points[2 * i + 1];
         const ImgPlan &p = plan->imgs[i];
         if (j < 0) continue;
-        if (j > p.s.k || xp < 0 || xp >= p.s.w || p.kind != 0 || plan->dtype != FHTDP_U8)
+        if (j > p.s.k || xp < 0 || xp >= p.s.w || p.kind != 0 ||
+            !engine_takes_point(plan->dtype, p.s, j))
             return set_error(FHTDP_EINVAL,
-                             "point %zu: border 0..k, column 0..w-1, uint8 bands of <= 128 rows", i);
+                             "point %zu: border 1..k, column 0..w-1, uint8, 2+ bands of <= 128 rows",
+                             i);
     }
     for (size_t i = 0; i < plan->imgs.size(); ++i) {
         ImgPlan &p = plan->imgs[i];

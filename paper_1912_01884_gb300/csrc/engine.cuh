@@ -26,7 +26,7 @@ int batch_angle(BatchPlan *plan, double gamma);
 int engine_detect(const void *img, int dtype, int pitch, const Shape &s, int B, int32_t *x_out,
                   int32_t *d_out, void *score_out, void *ws, size_t ws_bytes, cudaStream_t stream,
                   const PointMask *pm = nullptr);
-bool engine_takes_point(int dtype, const Shape &s);
+bool engine_takes_point(int dtype, const Shape &s, int j = 1);
 int batch_points(BatchPlan *plan, void *ws, const int32_t *points, cudaStream_t stream);
 int engine_detect_table(const void *img, int dtype, int pitch, const Shape &s,
                         const WindowTable &t, int32_t *x_out, int32_t *d_out, void *score_out,

@@ -90,9 +90,10 @@ int detect_two_t(const void *img, int dtype, int pitch, const Shape &s, int B, i
 int detect_through(const void *img, int dtype, int pitch, const Shape &s, int B,
                    const PointMask &pm, int32_t *x_out, int32_t *d_out, void *score_out,
                    void *ws, cudaStream_t stream) {
-    // uint8 images with bands of at most 128 rows: the fused engine with P's
-    // band masked in its V formation (the same DP as below)
-    if (engine_takes_point(dtype, s))
+    // uint8 images with bands of at most 128 rows, P on borders 1..k: the
+    // fused engine with P's band masked once its V is formed (the same DP as
+    // below)
+    if (engine_takes_point(dtype, s, pm.j))
         return engine_detect(img, dtype, pitch, s, B, x_out, d_out, score_out, ws,
                              through_workspace_bytes(s), stream, &pm);
     if (dtype == FHTDP_F32)

@@ -124,7 +124,7 @@ def test_batch_points_match_oracle(lib):
     for rnd in range(2):
         pts = []
         for i, (h, w, k) in enumerate(shapes):
-            j = [0, k // 2, k, None][(i + rnd) % 4]
+            j = [1, k // 2, k, None][(i + rnd) % 4]   # border 0 is for the single call
             pts.append(None if j is None else (j, (w * (i + 1 + rnd)) // 7 % w))
         plan.points(pts)
         if rnd == 1:
@@ -149,7 +149,7 @@ def test_batch_points_rejects_bad_points(lib):
     import torch
     a = torch.zeros((64, 40), dtype=torch.uint8, device="cuda")
     plan = lib.BatchPlan([a], [4], [2])
-    for bad in [(5, 0), (0, 40), (2, -1)]:
+    for bad in [(5, 0), (1, 40), (2, -1), (0, 3)]:   # border 0: the single call
         with pytest.raises(lib.FhtdpError):
             plan.points([bad])
     f = torch.zeros((64, 40), dtype=torch.float32, device="cuda")
