@@ -95,9 +95,9 @@ EXTRAS = ("plain2048", "float8192")
 # traffic is this times its pixels.  None where no capture of the current
 # kernel exists (reset whenever the kernel changes until it is captured again).
 NCU_TRAFFIC_BYTES_PER_PIXEL = {
-    "mixed": 15.0235e9 / 1064894464,     # engine_kernel_u8<int, 1>: 4.463 + 10.560 GB
-    "plain2048": 1.2498e9 / 134217728,   # engine_kernel_u8<int, 0>: 0.220 + 1.029 GB
-    "float8192": 1.2906e9 / 67108864,    # engine_kernel_wide: 0.275 + 1.015 GB
+    "mixed": 15.0048e9 / 1064894464,     # engine_kernel_u8<int, 1>: 4.445 + 10.559 GB
+    "plain2048": 1.2455e9 / 134217728,   # engine_kernel_u8<int, 0>: 0.216 + 1.030 GB
+    "float8192": 1.2905e9 / 67108864,    # engine_kernel_wide: 0.275 + 1.015 GB
 }
 # DRAM bytes of one dp_band_window_kernel band launch on the 2048x2048, k = 16
 # workloads (profiles/dp_band_window_kernel_angle2048.md).
