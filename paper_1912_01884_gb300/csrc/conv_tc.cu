@@ -3,10 +3,12 @@
 // accumulators in tensor memory).  The paper has no counterpart: the network
 // is an addition in front of the exact method.
 //
-// One CTA (4 warps) computes 128 output pixels of one image row for all 32
-// output channels: an implicit GEMM D[p][co] = sum over taps t and input
-// channels ci of X(p + off(t))[ci] * W[t][ci][co], M = 128, N = 32, K = 9 x 32,
-// as 18 MMAs of K = 16 (bf16 operands, FP32 accumulation).
+// A tile is 128 output pixels of one image row for all 32 output channels:
+// an implicit GEMM D[p][co] = sum over taps t and input channels ci of
+// X(p + off(t))[ci] * W[t][ci][co], M = 128, N = 32, K = 9 x 32, as 18 MMAs of
+// K = 16 (bf16 operands, FP32 accumulation).  Persistent CTAs (4 warps, three
+// per SM) load the weights once and pipeline their tiles (see
+// conv3x3_tc_persist_kernel).
 //
 // Shared memory holds operands in the no-swizzle K-major layout of the MMA:
 // "core matrices" of 8 rows x 16 bytes (8 bf16 along K) stored as 128
@@ -92,35 +94,27 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
                  : "memory");
 }
 
-template <bool kRelu>
-__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(
-    const __nv_bfloat16 *__restrict__ X, int H, int W, int dil,
-    const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
-    __nv_bfloat16 *__restrict__ Y, long long wait_cycles) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *As = smem;
-    unsigned char *Bs = smem + kABytes;
-    __shared__ __align__(8) uint64_t s_done;
-    __shared__ uint32_t s_tmem;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int segs = (W + kTcM - 1) / kTcM;
-    const int n = blockIdx.x / (H * segs);
-    const int rem = blockIdx.x % (H * segs);
-    const int y = rem / segs, x0 = (rem % segs) * kTcM;
+// The forward as a persistent kernel: a CTA loads the weights once and takes
+// the tiles (image, row, 128-pixel segment) u = blockIdx.x, blockIdx.x +
+// gridDim.x, ...  Two stage buffers and two accumulators (64 columns of tensor
+// memory) overlap the MMAs of tile i with the loads of tile i+1 and the
+// epilogue of tile i-1:
+//   wait for tile i's rows; MMAs of tile i into accumulator i % 2;
+//   wait for tile i-1's MMAs, its epilogue from accumulator (i-1) % 2;
+//   the rows of tile i+1 into the stage tile i-1 used.
+__device__ __forceinline__ void tc_tile_coords(long long u, int H, int segs, int *n, int *y,
+                                               int *x0) {
+    *n = (int)(u / ((long long)H * segs));
+    const int rem = (int)(u % ((long long)H * segs));
+    *y = rem / segs;
+    *x0 = (rem % segs) * kTcM;
+}
 
-    if (tid == 0) {
-        mbar_init(&s_done, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&s_tmem)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    // A: rows y + (r - 1) dil, pixels x0 - 8 + q, channel chunk c.
-    for (int i = tid; i < 3 * 4 * kTcPix; i += kTcThreads) {
+// All threads: the three rows of tile (n, y, x0) into stage As (cp.async,
+// zero outside the image), one commit group.
+__device__ __forceinline__ void tc_stage_rows(const __nv_bfloat16 *X, int H, int W, int dil, int n,
+                                              int y, int x0, unsigned char *As) {
+    for (int i = threadIdx.x; i < 3 * 4 * kTcPix; i += kTcThreads) {
         const int c = i & 3, q = (i >> 2) % kTcPix, r = (i >> 2) / kTcPix;
         const int yy = y + (r - 1) * dil, xx = x0 - kTcHalo + q;
         const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
@@ -129,49 +123,40 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(
         cp_async16(smem_u32(As + r * kARow + c * kAChunk + q * 16), src, ok);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    // B: W[t][ci][co] -> [t][ci / 8][co][ci % 8].
-    for (int i = tid; i < 9 * kTcC * kTcC; i += kTcThreads) {
-        const int co = i & 31, ci = (i >> 5) & 31, t = i >> 10;
-        ((__nv_bfloat16 *)Bs)[((t * 4 + (ci >> 3)) * kTcC + co) * 8 + (ci & 7)] = Wt[i];
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    // generic-proxy shared stores -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = s_tmem;
+}
 
-    if (tid == 0) {
-        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-        for (int t = 0; t < 9; ++t) {
-            const int ky = t / 3, kx = t % 3;
-            const uint32_t abase = a0 + ky * kARow + (kTcHalo + (kx - 1) * dil) * 16;
-            for (int j = 0; j < 2; ++j) {
-                const uint64_t ad = sdesc(abase + 2 * j * kAChunk, kAChunk, 128);
-                const uint64_t bd = sdesc(b0 + (t * 4 + 2 * j) * 512, 512, 128);
-                const uint32_t acc = (t | j) != 0;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-                    : "memory");
-            }
+// Thread 0: the 18 MMAs of one tile from stage As and the weights Bs into
+// accumulator `acc_tmem`, completion on `bar`.
+__device__ __forceinline__ void tc_issue(const unsigned char *As, const unsigned char *Bs,
+                                         int dil, uint32_t acc_tmem, uint64_t *bar) {
+    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+    for (int t = 0; t < 9; ++t) {
+        const int ky = t / 3, kx = t % 3;
+        const uint32_t abase = a0 + ky * kARow + (kTcHalo + (kx - 1) * dil) * 16;
+        for (int j = 0; j < 2; ++j) {
+            const uint64_t ad = sdesc(abase + 2 * j * kAChunk, kAChunk, 128);
+            const uint64_t bd = sdesc(b0 + (t * 4 + 2 * j) * 512, 512, 128);
+            const uint32_t acc = (t | j) != 0;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                : "memory");
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&s_done))
-            : "memory");
     }
-    __syncwarp();
-    bool ok = mbar_wait(&s_done, 0, wait_cycles);
-    if (!ok) {
-        if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
-        // the MMAs may still run: give them a last (bounded) chance before
-        // tensor memory is read and freed
-        mbar_wait(&s_done, 0, 4 * wait_cycles);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// All threads: the epilogue of a tile from accumulator `acc_tmem` (warp w
+// reads lanes 32w..32w+31, i.e. pixels x0 + 32w + lane): bias, ReLU, bf16.
+template <bool kRelu>
+__device__ __forceinline__ void tc_epilogue(uint32_t acc_tmem, const float *bias,
+                                            __nv_bfloat16 *Y, int H, int W, int n, int y,
+                                            int x0) {
+    const int warp = threadIdx.x >> 5;
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -183,33 +168,118 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(
           "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
           "=r"(r[31])
-        : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+        : "r"(acc_tmem + ((uint32_t)(32 * warp) << 16)));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int x = x0 + tid;   // lane quarter `warp` = pixels 32 warp .. 32 warp + 31
-    if (x < W) {
-        uint32_t packed[16];
+    const int x = x0 + threadIdx.x;
+    if (x >= W) return;
+    uint32_t packed[16];
 #pragma unroll
-        for (int c = 0; c < kTcC; c += 2) {
-            float v0 = __uint_as_float(r[c]) + (bias ? __ldg(bias + c) : 0.0f);
-            float v1 = __uint_as_float(r[c + 1]) + (bias ? __ldg(bias + c + 1) : 0.0f);
-            if (kRelu) {
-                v0 = v0 > 0.0f ? v0 : 0.0f;
-                v1 = v1 > 0.0f ? v1 : 0.0f;
-            }
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            packed[c / 2] = *(const uint32_t *)&h;
+    for (int c = 0; c < kTcC; c += 2) {
+        float v0 = __uint_as_float(r[c]) + (bias ? __ldg(bias + c) : 0.0f);
+        float v1 = __uint_as_float(r[c + 1]) + (bias ? __ldg(bias + c + 1) : 0.0f);
+        if (kRelu) {
+            v0 = v0 > 0.0f ? v0 : 0.0f;
+            v1 = v1 > 0.0f ? v1 : 0.0f;
         }
-        uint4 *dst = (uint4 *)(Y + (((size_t)n * H + y) * W + x) * kTcC);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
-                                packed[4 * q + 3]);
+        const __nv_bfloat162 hv = __floats2bfloat162_rn(v0, v1);
+        packed[c / 2] = *(const uint32_t *)&hv;
     }
+    uint4 *dst = (uint4 *)(Y + (((size_t)n * H + y) * W + x) * kTcC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+}
+
+template <bool kRelu>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_persist_kernel(
+    const __nv_bfloat16 *__restrict__ X, int N, int H, int W, int dil,
+    const __nv_bfloat16 *__restrict__ Wt, const float *__restrict__ bias,
+    __nv_bfloat16 *__restrict__ Y, long long wait_cycles) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Bs = smem;                       // weights
+    unsigned char *As[2] = {smem + kBBytes, smem + kBBytes + kABytes};   // stages
+    __shared__ __align__(8) uint64_t s_done[2];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = (W + kTcM - 1) / kTcM;
+    const long long units = (long long)N * H * segs;
+    if (tid == 0) {
+        mbar_init(&s_done[0], 1);
+        mbar_init(&s_done[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(2 * kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < 9 * kTcC * kTcC; i += kTcThreads) {
+        const int co = i & 31, ci = (i >> 5) & 31, t = i >> 10;
+        ((__nv_bfloat16 *)Bs)[((t * 4 + (ci >> 3)) * kTcC + co) * 8 + (ci & 7)] = Wt[i];
+    }
+    int n, y, x0;
+    if (blockIdx.x < units) {
+        tc_tile_coords(blockIdx.x, H, segs, &n, &y, &x0);
+        tc_stage_rows(X, H, W, dil, n, y, x0, As[0]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    uint32_t ph[2] = {0u, 0u};
+    long long prev = -1;
+    int b = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x, b ^= 1) {
+        // tile u's rows (and, the first time, the weights) -> the tensor core
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) tc_issue(As[b], Bs, dil, tmem + kTmemCols * b, &s_done[b]);
+        __syncwarp();
+        if (prev >= 0) {   // tile prev: its MMAs, then its epilogue
+            const bool w = mbar_wait(&s_done[b ^ 1], ph[b ^ 1], wait_cycles);
+            if (!w) {
+                if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
+                mbar_wait(&s_done[b ^ 1], ph[b ^ 1], 4 * wait_cycles);
+            }
+            ph[b ^ 1] ^= 1u;
+            ok = __syncthreads_and(w) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_tile_coords(prev, H, segs, &n, &y, &x0);
+            tc_epilogue<kRelu>(tmem + kTmemCols * (b ^ 1), bias, Y, H, W, n, y, x0);
+        }
+        // the stage tile prev read is free: the rows of the next tile
+        const long long next = u + gridDim.x;
+        if (next < units) {
+            tc_tile_coords(next, H, segs, &n, &y, &x0);
+            tc_stage_rows(X, H, W, dil, n, y, x0, As[b ^ 1]);
+        }
+        prev = u;
+    }
+    if (ok && prev >= 0) {   // the last tile took accumulator b ^ 1
+        const bool w = mbar_wait(&s_done[b ^ 1], ph[b ^ 1], wait_cycles);
+        if (!w) {
+            if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
+            mbar_wait(&s_done[b ^ 1], ph[b ^ 1], 4 * wait_cycles);
+        }
+        if (__syncthreads_and(w)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_tile_coords(prev, H, segs, &n, &y, &x0);
+            tc_epilogue<kRelu>(tmem + kTmemCols * (b ^ 1), bias, Y, H, W, n, y, x0);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
+                     "r"(2 * kTmemCols)
                      : "memory");
 }
 
@@ -389,32 +459,35 @@ int cnn_wgrad_tc(const void *X, int N, int H, int W, int dil, const void *dZ, fl
     return launched("conv3x3_wgrad_tc_kernel");
 }
 
-size_t cnn_conv_tc_smem() { return (size_t)kABytes + kBBytes; }
-
 int cnn_conv3x3_tc(const void *X, int N, int H, int W, int dil, const void *Wt,
                    const float *bias, int relu, void *Y, cudaStream_t stream) {
     if (dil < 1 || dil > kTcHalo || W < 1 || H < 1 || N < 1)
         return set_error(FHTDP_EINVAL, "conv3x3: dilation 1..8 and a non-empty image");
-    const size_t smem = cnn_conv_tc_smem();
+    // persistent CTAs: the weights and two stages (73.7 KB), three per SM
+    const size_t smem = (size_t)kBBytes + 2 * kABytes;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(conv3x3_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaFuncSetAttribute(conv3x3_tc_kernel<false>,
+        cudaFuncSetAttribute(conv3x3_tc_persist_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(conv3x3_tc_persist_kernel<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    const long long blocks = (long long)N * H * ((W + kTcM - 1) / kTcM);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long units = (long long)N * H * ((W + kTcM - 1) / kTcM);
+    const long long grid = std::min<long long>(units, 3LL * (sms > 0 ? sms : 152));
     const long long wait = 4000000000LL;   // about two seconds
     if (relu)
-        conv3x3_tc_kernel<true><<<(unsigned)blocks, kTcThreads, smem, stream>>>(
-            (const __nv_bfloat16 *)X, H, W, dil, (const __nv_bfloat16 *)Wt, bias,
+        conv3x3_tc_persist_kernel<true><<<(unsigned)grid, kTcThreads, smem, stream>>>(
+            (const __nv_bfloat16 *)X, N, H, W, dil, (const __nv_bfloat16 *)Wt, bias,
             (__nv_bfloat16 *)Y, wait);
     else
-        conv3x3_tc_kernel<false><<<(unsigned)blocks, kTcThreads, smem, stream>>>(
-            (const __nv_bfloat16 *)X, H, W, dil, (const __nv_bfloat16 *)Wt, bias,
+        conv3x3_tc_persist_kernel<false><<<(unsigned)grid, kTcThreads, smem, stream>>>(
+            (const __nv_bfloat16 *)X, N, H, W, dil, (const __nv_bfloat16 *)Wt, bias,
             (__nv_bfloat16 *)Y, wait);
-    return launched("conv3x3_tc_kernel");
+    return launched("conv3x3_tc_persist_kernel");
 }
 
 int cnn_tc_status(int clear) {
