@@ -285,34 +285,65 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_persist_kernel(
 
 // Weight and bias gradients of a 32-channel layer: dW[t][ci][co] += sum over
 // pixels p of X(p + off(t))[ci] * dZ(p)[co], db[co] += sum of dZ(p)[co].  As
-// GEMMs with the pixels as K: M = 128 rows (t', ci) for four taps t = 4g + t'
-// (g = 0, 1, 2; rows of taps past 8 are never read), N = 32 (co).  A CTA
-// loops over 128-pixel row segments and keeps the three accumulators in
-// tensor memory (96 columns); at the end each thread adds its row's 32
-// values of each group to dW.  Both operands are MN-major (channels
-// contiguous, as stored): core matrices of 8 channels (16 bytes) x 8 pixels,
-//   A: [g][t' * 4 + chunk][pixel][8 ci]  (next 8 rows of M: kWgChunk bytes,
-//                                          next 8 pixels of K: 128 bytes)
-//   B: [chunk][pixel][8 co]              (the same strides).
-constexpr int kWgP = 128;                       // pixels of a segment (K per stage)
-constexpr int kWgChunk = kWgP * 16;             // bytes of a chunk of a segment
-constexpr int kWgABytes = 3 * 16 * kWgChunk;    // 98,304
+// GEMMs with the pixels as K, one per column tap kx: M = 128 rows (ky, ci) for
+// ky = 0..3, N = 32 (co).  The A operand is the forward kernel's stage of the
+// three input rows y - dil, y, y + dil ([row][channel chunk][pixel][8 ci],
+// pixels [x0 - 8, x0 + 136)) read in place from pixel 8 + (kx - 1) dil, so a
+// segment is copied once for all nine taps; a fourth staged "row" holds a
+// chunk of ones, so accumulator rows 96..103 of every tap group are db, and
+// rows 104..127 (its other chunks, never written) are never read.  Both
+// operands are MN-major (channels contiguous, as stored): core matrices of 8
+// channels (16 bytes) x 8 pixels; for A the next 8 rows of M are kAChunk
+// bytes on (row ky of the stage is four chunks on) and the next 8 pixels of K
+// 128 bytes on; B is dZ as [chunk][pixel][8 co] (kWgChunk, 128).
+// Persistent CTAs (4 warps, two per SM) walk 128-pixel row segments through
+// two stages: segment i + 1's copies are in flight while segment i's land and
+// segment i - 1's MMAs run; the three accumulators (96 columns of tensor
+// memory) stay put, and at the end warp ky adds its row's 32 values of each
+// tap group to dW (warp 3: db).
+constexpr int kWgP = kTcM;                      // pixels of a segment (K per stage)
+constexpr int kWgChunk = kWgP * 16;             // bytes of a chunk of dZ
+constexpr int kWgABytes = 4 * kARow;            // 36,864: three rows and the ones
 constexpr int kWgBBytes = 4 * kWgChunk;         // 8,192
+constexpr int kWgStage = kWgABytes + kWgBBytes; // 45,056
+constexpr int kWgThreads = kTcThreads;
 constexpr unsigned kWgCols = 128;               // three 32-column accumulators
 constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);   // A and B MN-major
 
-__global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(
+// cp.async of segment u (image, row, 128 pixels) into one stage: the three
+// rows of X (zero outside the image) and dZ (zero past the row's end).
+__device__ __forceinline__ void wg_stage(const __nv_bfloat16 *X, const __nv_bfloat16 *dZ, int H,
+                                         int W, int dil, int segs, long long u,
+                                         unsigned char *st) {
+    int n, y, x0;
+    tc_tile_coords(u, H, segs, &n, &y, &x0);
+    for (int i = threadIdx.x; i < 3 * 4 * kTcPix; i += kWgThreads) {
+        const int c = i & 3, q = (i >> 2) % kTcPix, r = (i >> 2) / kTcPix;
+        const int yy = y + (r - 1) * dil, xx = x0 - kTcHalo + q;
+        const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const __nv_bfloat16 *src = v ? X + ((((size_t)n * H + yy) * W + xx) * kTcC + 8 * c) : X;
+        cp_async16(smem_u32(st + r * kARow + c * kAChunk + q * 16), src, v);
+    }
+    for (int i = threadIdx.x; i < 4 * kWgP; i += kWgThreads) {
+        const int c = i & 3, p = i >> 2;
+        const bool v = x0 + p < W;
+        const __nv_bfloat16 *src = v ? dZ + ((((size_t)n * H + y) * W + x0 + p) * kTcC + 8 * c) : dZ;
+        cp_async16(smem_u32(st + kWgABytes + c * kWgChunk + p * 16), src, v);
+    }
+}
+
+__global__ void __launch_bounds__(kWgThreads) conv3x3_wgrad_tc_kernel(
     const __nv_bfloat16 *__restrict__ X, int N, int H, int W, int dil,
     const __nv_bfloat16 *__restrict__ dZ, float *__restrict__ dW, float *__restrict__ db,
     long long wait_cycles) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *As = smem;
-    unsigned char *Bs = smem + kWgABytes;
-    __shared__ __align__(8) uint64_t s_done;
+    unsigned char *St[2] = {smem, smem + kWgStage};
+    __shared__ __align__(8) uint64_t s_done[2];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        mbar_init(&s_done, 1);
+        mbar_init(&s_done[0], 1);
+        mbar_init(&s_done[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -322,57 +353,55 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // the ones chunk (row 3, chunk 0) of both stages, bf16 1.0 = 0x3f80; the
+    // stage copies never write it
+    for (int i = tid; i < 2 * kTcPix; i += kWgThreads)
+        *(uint4 *)(St[i / kTcPix] + 3 * kARow + (i % kTcPix) * 16) =
+            make_uint4(0x3f803f80u, 0x3f803f80u, 0x3f803f80u, 0x3f803f80u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
     const int segs = (W + kWgP - 1) / kWgP;
     const long long units = (long long)N * H * segs;
-    float bsum = 0.0f;   // thread c < 32: channel c of db over this CTA's pixels
-    uint32_t phase = 0;
+    uint32_t ph[2] = {0u, 0u};
+    bool pend[2] = {false, false};
     bool first = true, ok = true;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-        const int n = (int)(u / ((long long)H * segs));
-        const int rem = (int)(u % ((long long)H * segs));
-        const int y = rem / segs, x0 = (rem % segs) * kWgP;
-        // A: taps 0..8 (group g = t / 4, t' = t % 4), 4 chunks, 128 pixels
-        for (int i = tid; i < 9 * 4 * kWgP; i += kTcThreads) {
-            const int c = i & 3, p = (i >> 2) % kWgP, t = (i >> 2) / kWgP;
-            const int ky = t / 3, kx = t % 3;
-            const int yy = y + (ky - 1) * dil, xx = x0 + p + (kx - 1) * dil;
-            const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
-            const __nv_bfloat16 *src =
-                v ? X + ((((size_t)n * H + yy) * W + xx) * kTcC + 8 * c) : X;
-            const int g = t >> 2, mb = (t & 3) * 4 + c;
-            cp_async16(smem_u32(As + (g * 16 + mb) * kWgChunk + p * 16), src, v);
-        }
-        // B: dZ of the segment's pixels (zero past the row's end)
-        for (int i = tid; i < 4 * kWgP; i += kTcThreads) {
-            const int c = i & 3, p = i >> 2;
-            const bool v = x0 + p < W;
-            const __nv_bfloat16 *src =
-                v ? dZ + ((((size_t)n * H + y) * W + x0 + p) * kTcC + 8 * c) : dZ;
-            cp_async16(smem_u32(Bs + c * kWgChunk + p * 16), src, v);
+    long long u = blockIdx.x;
+    int b = 0;
+    if (u < units) wg_stage(X, dZ, H, W, dil, segs, u, St[0]);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (; u < units; u += gridDim.x, b ^= 1) {
+        const long long nu = u + gridDim.x;
+        if (nu < units) {
+            // stage b ^ 1 is rewritten: wait for the MMAs that read it
+            if (pend[b ^ 1]) {
+                const bool w = mbar_wait(&s_done[b ^ 1], ph[b ^ 1], wait_cycles);
+                if (!w) {
+                    if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
+                    mbar_wait(&s_done[b ^ 1], ph[b ^ 1], 4 * wait_cycles);
+                }
+                ph[b ^ 1] ^= 1u;
+                pend[b ^ 1] = false;
+                ok = __syncthreads_and(w) != 0;
+                if (!ok) break;
+            }
+            wg_stage(X, dZ, H, W, dil, segs, nu, St[b ^ 1]);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // stage b has landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid < kTcC) {   // db: column tid of B over the segment
-            const __nv_bfloat16 *col = (const __nv_bfloat16 *)(Bs + (tid >> 3) * kWgChunk) + (tid & 7);
-            float sacc = 0.0f;
-            for (int p = 0; p < kWgP; ++p) sacc += __bfloat162float(col[p * 8]);
-            bsum += sacc;
-        }
         if (tid == 0) {
-            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-            for (int g = 0; g < 3; ++g)
+            const uint32_t a0 = smem_u32(St[b]), b0 = a0 + kWgABytes;
+            for (int g = 0; g < 3; ++g)   // column tap kx = g
                 for (int j = 0; j < kWgP / 16; ++j) {
                     // MN-major, no swizzle: the leading offset steps along K
                     // (8 pixels), the stride offset along M / N (8 channels)
-                    const uint64_t ad = sdesc(a0 + g * 16 * kWgChunk + j * 256, 128, kWgChunk);
+                    const uint32_t abase = a0 + (kTcHalo + (g - 1) * dil) * 16;
+                    const uint64_t ad = sdesc(abase + j * 256, 128, kAChunk);
                     const uint64_t bd = sdesc(b0 + j * 256, 128, kWgChunk);
                     const uint32_t acc = first && j == 0 ? 0u : 1u;
                     asm volatile(
@@ -384,28 +413,30 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(
                 }
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&s_done))
+                    smem_u32(&s_done[b]))
                 : "memory");
         }
-        first = false;
         __syncwarp();
-        // the stage is rewritten next: wait for the MMAs that read it
-        const bool w = mbar_wait(&s_done, phase, wait_cycles);
-        if (!w) {
-            if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
-            mbar_wait(&s_done, phase, 4 * wait_cycles);
-        }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // every thread is done with the stage (db sums included); one
-        // decision for the whole CTA
-        ok = __syncthreads_and(w) != 0;
-        if (!ok) break;
+        pend[b] = true;
+        first = false;
     }
+    // the MMAs complete in order: wait for the pending ones (both stages)
+    for (int s = 0; s < 2 && ok; ++s)
+        if (pend[s]) {
+            const bool w = mbar_wait(&s_done[s], ph[s], wait_cycles);
+            if (!w) {
+                if (lane == 0) atomicExch(&g_conv_tc_status, FHTDP_ETIMEOUT);
+                mbar_wait(&s_done[s], ph[s], 4 * wait_cycles);
+            }
+            ok = __syncthreads_and(w) != 0;
+        }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!first && ok) {
-        // row 32 warp + lane of group g is tap 4g + warp, input channel lane
+        // row 32 warp + lane of group g is tap 3 warp + g (ky = warp, kx = g),
+        // input channel lane; warp 3, lanes 0..7 hold db
         for (int g = 0; g < 3; ++g) {
-            const int t = 4 * g + warp;
+            const int t = 3 * warp + g;
             uint32_t r[32];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
@@ -419,13 +450,15 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_wgrad_tc_kernel(
                   "=r"(r[30]), "=r"(r[31])
                 : "r"(tmem + ((uint32_t)(32 * warp) << 16) + 32u * g));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (t < 9) {
+            if (warp < 3) {
                 float *dst = dW + ((size_t)t * kTcC + lane) * kTcC;
 #pragma unroll
                 for (int co = 0; co < kTcC; ++co) atomicAdd(dst + co, __uint_as_float(r[co]));
+            } else if (g == 0 && lane == 0 && db) {
+#pragma unroll
+                for (int co = 0; co < kTcC; ++co) atomicAdd(db + co, __uint_as_float(r[co]));
             }
         }
-        if (db && tid < kTcC) atomicAdd(db + tid, bsum);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -441,7 +474,7 @@ int cnn_wgrad_tc(const void *X, int N, int H, int W, int dil, const void *dZ, fl
                  float *db, cudaStream_t stream) {
     if (dil < 1 || dil > kTcHalo || W < 1 || H < 1 || N < 1)
         return set_error(FHTDP_EINVAL, "conv3x3 wgrad: dilation 1..8 and a non-empty image");
-    const size_t smem = (size_t)kWgABytes + kWgBBytes;
+    const size_t smem = 2 * (size_t)kWgStage;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -453,7 +486,7 @@ int cnn_wgrad_tc(const void *X, int N, int H, int W, int dil, const void *dZ, fl
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long units = (long long)N * H * ((W + kWgP - 1) / kWgP);
     const long long grid = std::min<long long>(units, 2LL * (sms > 0 ? sms : 152));
-    conv3x3_wgrad_tc_kernel<<<(unsigned)grid, kTcThreads, smem, stream>>>(
+    conv3x3_wgrad_tc_kernel<<<(unsigned)grid, kWgThreads, smem, stream>>>(
         (const __nv_bfloat16 *)X, N, H, W, dil, (const __nv_bfloat16 *)dZ, dW, db,
         4000000000LL);
     return launched("conv3x3_wgrad_tc_kernel");

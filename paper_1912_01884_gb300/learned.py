@@ -220,6 +220,33 @@ def exact_paths(imgs, k, B):
     return (torch.stack(plan.x), torch.stack(plan.d), torch.cat(plan.score))
 
 
+CONF_GRID = tuple(round(0.5 + 0.02 * i, 2) for i in range(16)) + (0.85, 0.9)
+
+
+def calibrate_min_conf(model, imgs, k, B, target: float = 0.995, margin: float = 0.0,
+                       grid=CONF_GRID):
+    """Calibrates the band-confidence threshold of the fallback rule on images
+    held apart from those it is later used on: the smallest threshold of
+    `grid` under which the learned detection returns the exact optimum for at
+    least `target` of `imgs` (the largest one when none does).  Raising the
+    threshold only adds fallbacks, so the hit rate does not fall along the
+    grid.  Returns (min_conf, hit rate, fallback rate) on `imgs`."""
+    xe, de, se = exact_paths(imgs, k, B)
+    plan = LearnedPlan(imgs, k, B)
+    try:
+        for c in grid:
+            plan.run(model, margin, c)
+            plan.status()
+            hit = float(((plan.score == se) & (plan.x == xe).all(1) &
+                         (plan.d == de).all(1)).float().mean())
+            fb = float(plan.used_fallback.float().mean())
+            if hit >= target:
+                break
+        return c, hit, fb
+    finally:
+        plan.close()
+
+
 def detect_learned(model, imgs, k, B, margin: float = 0.0, min_conf: float = 0.0):
     """Learned proposal + pruned DP + device-side fallback (fhtdp_detect_learned).
     Returns (x, d, score, used_fallback[N]); images that fall back carry the
