@@ -323,10 +323,10 @@ int fhtdp_detect_polyline_horizontal(const void *img, int dtype, int h, int w, i
 /* uint8 [n][h][w] -> bf16 [n][h/4][w/4], the 4x4 mean divided by 255. */
 int fhtdp_cnn_downsample4(const uint8_t *img, int n, int h, int w, void *out, cudaStream_t stream);
 /* y = act(conv3x3_dil(x, wt) + bias), act = ReLU when relu != 0; cin 1 or 32,
- * cout 32, zero padding ("same").  32 input channels run on tcgen05.mma (128
- * pixels x 32 channels per CTA, K = 9 x 32, FP32 accumulators in tensor
- * memory); a bounded wait for the MMAs that gives up records FHTDP_ETIMEOUT
- * for fhtdp_cnn_status. */
+ * cout 32, zero padding ("same").  32 input channels run on tcgen05.mma
+ * (persistent CTAs over tiles of 128 pixels x 32 channels, K = 9 x 32, FP32
+ * accumulators in tensor memory); a bounded wait for the MMAs that gives up
+ * records FHTDP_ETIMEOUT for fhtdp_cnn_status. */
 int fhtdp_cnn_conv3x3(const void *x, int cin, int n, int h, int w, int dil, const void *wt,
                       const float *bias, int relu, void *y, cudaStream_t stream);
 /* Device status of the tensor-core convolutions since the last clear: 0, or
@@ -342,7 +342,9 @@ int fhtdp_cnn_conv3x3_dgrad(const void *dz, int n, int h, int w, int dil, const 
 /* dy *= (y > 0): the ReLU of a layer, in place, from its output y. */
 int fhtdp_cnn_relu_backward(const void *y, void *dy, long long count, cudaStream_t stream);
 /* dw += sum over pixels of x(shifted by the tap) * dz (FP32 [taps][cin][32]),
- * db += sum of dz (FP32 [32], may be NULL).  Accumulates: clear first. */
+ * db += sum of dz (FP32 [32], may be NULL).  Accumulates: clear first.  32
+ * input channels run on tcgen05.mma (the pixels as K, FP32 accumulators in
+ * tensor memory; the sums' order across CTAs varies between runs). */
 int fhtdp_cnn_conv3x3_wgrad(const void *x, int cin, int n, int h, int w, int dil, const void *dz,
                             float *dw, float *db, cudaStream_t stream);
 /* Band head: pooled[n][b][c] = log-sum-exp of logits[n][rows of band b][:][c];
