@@ -475,12 +475,12 @@ int cnn_wgrad_tc(const void *X, int N, int H, int W, int dil, const void *dZ, fl
     if (dil < 1 || dil > kTcHalo || W < 1 || H < 1 || N < 1)
         return set_error(FHTDP_EINVAL, "conv3x3 wgrad: dilation 1..8 and a non-empty image");
     const size_t smem = 2 * (size_t)kWgStage;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr = true;
-    }
+    // set on every call: the attribute belongs to the current device
+    int st = cuda_status(cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "cudaFuncSetAttribute");
+    if (st) return st;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -498,14 +498,13 @@ int cnn_conv3x3_tc(const void *X, int N, int H, int W, int dil, const void *Wt,
         return set_error(FHTDP_EINVAL, "conv3x3: dilation 1..8 and a non-empty image");
     // persistent CTAs: the weights and two stages (73.7 KB), three per SM
     const size_t smem = (size_t)kBBytes + 2 * kABytes;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(conv3x3_tc_persist_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(conv3x3_tc_persist_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    // set on every call: the attribute belongs to the current device
+    int st = cuda_status(cudaFuncSetAttribute(relu ? conv3x3_tc_persist_kernel<true>
+                                                   : conv3x3_tc_persist_kernel<false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                         "cudaFuncSetAttribute");
+    if (st) return st;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
