@@ -205,3 +205,42 @@ def test_through_point_angle_rejects_bad_arguments_before_launch(lib):
     assert f(fake, 0, 64, 10, 10, 4, 13, 0.3, 1, 1, *outs) == 1
     assert f(fake, 3, 64, 10, 10, 4, 2, 0.3, 1, 1, *outs) == 1
     assert f(fake, 0, 64, 10, 10, 4, 2, 0.3, 1, 1, fake, fake, fake, fake, 64, None) == 2
+
+
+def test_cnn_and_learned_entries_reject_bad_arguments_before_launch(lib):
+    """The learned proposal's calls check their arguments on the host: a width
+    that is not a multiple of 64, a channel count other than 1 or 32, a
+    dilation outside 1..8, null buffers, shapes the band head or the
+    downsample cannot take, and null plans (every case returns EINVAL with a
+    message before anything is enqueued)."""
+    L = lib.lib()
+    f = ctypes.c_void_p(256)      # never dereferenced: rejected before any launch
+    bad = [
+        lambda: L.fhtdp_cnn_conv3x3(f, 32, 1, 6, 160, 2, f, None, 1, f, None),    # w % 64
+        lambda: L.fhtdp_cnn_conv3x3(f, 16, 1, 6, 192, 2, f, None, 1, f, None),    # cin
+        lambda: L.fhtdp_cnn_conv3x3(f, 32, 1, 6, 192, 9, f, None, 1, f, None),    # dil > 8
+        lambda: L.fhtdp_cnn_conv3x3(f, 32, 1, 6, 192, 0, f, None, 1, f, None),    # dil < 1
+        lambda: L.fhtdp_cnn_conv3x3(None, 32, 1, 6, 192, 2, f, None, 1, f, None),  # null x
+        lambda: L.fhtdp_cnn_conv3x3(f, 32, 0, 6, 192, 2, f, None, 1, f, None),    # no image
+        lambda: L.fhtdp_cnn_conv3x3_wgrad(f, 32, 1, 6, 100, 1, f, f, None, None),  # w % 64
+        lambda: L.fhtdp_cnn_conv3x3_wgrad(f, 3, 1, 6, 128, 1, f, f, None, None),   # cin
+        lambda: L.fhtdp_cnn_conv3x3_wgrad(f, 32, 1, 6, 128, 1, f, None, None, None),  # null dw
+        lambda: L.fhtdp_cnn_conv3x3_dgrad(f, 1, 6, 63, 1, f, f, f, None),          # w % 64
+        lambda: L.fhtdp_cnn_downsample4(f, 1, 6, 64, f, None),                      # h % 4
+        lambda: L.fhtdp_cnn_band_head(f, 1, 10, 64, 4, None, 1.0, None, None, None, None),
+        lambda: L.fhtdp_cnn_adam(f, f, f, f, 0, 1e-3, 0.9, 0.999, 1e-8, 1, None, None),
+        lambda: L.fhtdp_cnn_adam(f, f, f, f, 8, 1e-3, 0.9, 0.999, 1e-8, 0, None, None),
+        lambda: L.fhtdp_cnn_bin_windows(f, 4, 64, -1, f, None),                     # margin
+        lambda: L.fhtdp_cnn_relu_backward(f, f, -1, None),
+        lambda: L.fhtdp_cnn_init(None, 0, None),
+        lambda: L.fhtdp_cnn_step(f, f, 0, 64, 64, 1e-3, 1, None),                   # n < 1
+        lambda: L.fhtdp_detect_learned(None, f, 0.0, 0.5, f, f, None),
+        lambda: L.fhtdp_learned_upload(None, f, 1 << 20, None),
+        lambda: L.fhtdp_learned_status(None, f, None),
+    ]
+    for i, call in enumerate(bad):
+        assert call() == 1, i
+        assert L.fhtdp_last_error().decode(), i
+    out = ctypes.c_void_p()
+    assert L.fhtdp_learned_plan_create(None, 0, 6, ctypes.byref(out)) == 1
+    assert not out.value
