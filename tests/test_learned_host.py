@@ -1,4 +1,5 @@
-"""Host logic of the learned proposal that needs no GPU: the calibration of
+"""Host logic of the learned proposal that needs no GPU: the label bins, the
+training images' recipe (generated on the CPU), and the calibration of
 the fallback rule's confidence threshold, run against a fake plan whose hit
 rate rises with the threshold as the device rule's does (each image falls
 back, and is then exact, once the threshold exceeds its lowest band
@@ -67,3 +68,32 @@ def test_calibration_returns_the_largest_threshold_when_none_reaches_the_target(
     _install(monkeypatch, conf, exact)
     c, hit, fb = learned.calibrate_min_conf(None, None, 4, 2, target=0.995)
     assert c == learned.CONF_GRID[-1] and hit == pytest.approx(0.9) and fb == 0.0
+
+
+def test_label_bins_cover_the_displacements_four_at_a_time():
+    d = np.arange(-63, 64)
+    b = learned.bins_of(d)
+    assert b.min() == 0 and b.max() == learned.BINS - 1
+    assert np.all(np.diff(b) >= 0)
+    assert np.all(4 * b <= d + 64) and np.all(d + 64 <= 4 * b + 3)
+
+
+def test_lane_images_follow_their_recipe_on_the_host():
+    """The training images (generated on the CPU here): seeded, uint8, noise
+    and field at most 60, and two lanes of intensity 70..140 whose pixels
+    move at most one column from row to row."""
+    args = dict(h=64, w=128, k=4, B=3, device="cpu")
+    a = learned.lane_images(7, 3, **args)
+    assert a.dtype == torch.uint8 and tuple(a.shape) == (3, 64, 128)
+    assert torch.equal(a, learned.lane_images(7, 3, **args))
+    assert not torch.equal(a, learned.lane_images(8, 3, **args))
+    img = a.numpy().astype(int)
+    bright = img >= 70
+    assert np.all(img[~bright] <= 60) and np.all(img[bright] <= 140)
+    counts = bright.sum(2)
+    assert np.all((counts >= 1) & (counts <= 2))
+    for n in range(3):
+        for r in range(63):
+            prev = np.flatnonzero(bright[n, r])
+            for c in np.flatnonzero(bright[n, r + 1]):
+                assert np.abs(prev - c).min() <= 1, (n, r, c)
